@@ -1,0 +1,389 @@
+"""Seeded synthetic structure-from-motion scenes.
+
+This module is the one input generator shared by the oracle tests, the CUDA
+parity tests, ``bench.py`` and ``smoke()``.  It places pinhole cameras and 3D
+points, projects the points (plus per-observation Gaussian pixel noise), forms
+every pairwise combination of the cameras that see a point (the completed
+tracks of the paper's track completion, Appendix "Tracks"), replaces a fraction
+of keypoint pairs by uniform-random outlier pixels, and groups the keypoint
+pairs by image pair.  It holds none of the method's arithmetic: no objective,
+gradient, optimizer or estimator lives here.
+
+Conventions (shared with the C ABI):
+  * world-to-camera pose: ``x_cam = R @ X + t``; camera centre ``o = -R^T t``;
+  * pixel ``u = f * x/z + cx``, ``v = f * y/z + cy``; principal point at the
+    image centre (Sec. 3.1, camera assumptions);
+  * an image pair is ``(i, j)`` with ``i < j``; in a keypoint pair the first
+    keypoint lies in image ``i`` and the second in image ``j``;
+  * keypoint pairs are sorted by (image pair, track) and ``kp_img_pair`` is
+    non-decreasing.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from itertools import combinations
+
+import numpy as np
+
+__all__ = ["Scene", "make_scene", "scene_c1", "scene_c2", "perturb_params",
+           "gt_relative_poses", "CONFIGS"]
+
+
+@dataclass
+class Scene:
+    name: str
+    seed: int
+    width: int
+    height: int
+    focal: np.ndarray        # [N] float64
+    cx: np.ndarray           # [N]
+    cy: np.ndarray           # [N]
+    R_gt: np.ndarray         # [N,3,3] world-to-camera
+    t_gt: np.ndarray         # [N,3]
+    points: np.ndarray       # [T,3] one point per track
+    pair_i: np.ndarray       # [P] int32, pair_i < pair_j
+    pair_j: np.ndarray       # [P] int32
+    kp_img_pair: np.ndarray  # [Z] int32, non-decreasing
+    kp1_px: np.ndarray       # [Z,2] float32, keypoint in image pair_i
+    kp2_px: np.ndarray       # [Z,2] float32, keypoint in image pair_j
+    kp_track: np.ndarray     # [Z] int32
+    kp_inlier: np.ndarray    # [Z] bool, False where the pair was replaced by an outlier
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_cams(self) -> int:
+        return int(self.focal.shape[0])
+
+    @property
+    def n_pairs(self) -> int:
+        return int(self.pair_i.shape[0])
+
+    @property
+    def n_kp(self) -> int:
+        return int(self.kp_img_pair.shape[0])
+
+    @property
+    def centers_gt(self) -> np.ndarray:
+        return -np.einsum("nji,nj->ni", self.R_gt, self.t_gt)
+
+    def seg_off(self) -> np.ndarray:
+        """CSR offsets of the keypoint pairs of each image pair, [P+1] int64."""
+        counts = np.bincount(self.kp_img_pair, minlength=self.n_pairs)
+        off = np.zeros(self.n_pairs + 1, dtype=np.int64)
+        np.cumsum(counts, out=off[1:])
+        return off
+
+
+# --------------------------------------------------------------------------
+# camera placement helpers (scene construction only)
+# --------------------------------------------------------------------------
+
+def _frame_looking(forward: np.ndarray, up: np.ndarray) -> np.ndarray:
+    """Rows are the camera x, y, z axes in world coordinates (right-handed)."""
+    z = forward / np.linalg.norm(forward)
+    x = np.cross(z, up)
+    nx = np.linalg.norm(x)
+    if nx < 1e-9:  # forward parallel to up: pick any perpendicular axis
+        x = np.cross(z, np.array([1.0, 0.0, 0.0]))
+        nx = np.linalg.norm(x)
+    x = x / nx
+    y = np.cross(z, x)
+    return np.stack([x, y, z])
+
+
+def _rot_axis(axis: int, ang: float) -> np.ndarray:
+    c, s = np.cos(ang), np.sin(ang)
+    if axis == 0:
+        return np.array([[1, 0, 0], [0, c, -s], [0, s, c]])
+    if axis == 1:
+        return np.array([[c, 0, s], [0, 1, 0], [-s, 0, c]])
+    return np.array([[c, -s, 0], [s, c, 0], [0, 0, 1]])
+
+
+def _project(R, t, f, cx, cy, X):
+    """Project points X [M,3] into cameras [N]: returns (u, v, depth) of shape [M,N]."""
+    Xc = np.einsum("nij,mj->mni", R, X) + t[None, :, :]
+    z = Xc[..., 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        u = f[None, :] * Xc[..., 0] / z + cx[None, :]
+        v = f[None, :] * Xc[..., 1] / z + cy[None, :]
+    return u, v, z
+
+
+# --------------------------------------------------------------------------
+# track -> keypoint pairs
+# --------------------------------------------------------------------------
+
+def _tracks_to_pairs(rng, track_cams, track_uv, width, height, outlier_frac,
+                     min_pairs_per_image_pair):
+    """All C(k,2) camera combinations of every track, grouped by image pair.
+
+    track_cams: list of int arrays (sorted camera ids per track)
+    track_uv:   list of [k,2] arrays (noisy pixels, one per observation)
+    """
+    by_k = {}
+    for tid, cams in enumerate(track_cams):
+        by_k.setdefault(len(cams), []).append(tid)
+    ci, cj, p1, p2, tr = [], [], [], [], []
+    for k, tids in by_k.items():
+        tids = np.asarray(tids)
+        cams = np.stack([track_cams[t] for t in tids])      # [n,k]
+        uv = np.stack([track_uv[t] for t in tids])          # [n,k,2]
+        comb = np.array(list(combinations(range(k), 2)))    # [c,2]
+        a, b = comb[:, 0], comb[:, 1]
+        ci.append(cams[:, a].reshape(-1))
+        cj.append(cams[:, b].reshape(-1))
+        p1.append(uv[:, a].reshape(-1, 2))
+        p2.append(uv[:, b].reshape(-1, 2))
+        tr.append(np.repeat(tids, len(comb)))
+    ci = np.concatenate(ci).astype(np.int64)
+    cj = np.concatenate(cj).astype(np.int64)
+    p1 = np.concatenate(p1)
+    p2 = np.concatenate(p2)
+    tr = np.concatenate(tr).astype(np.int64)
+    return _group_pairs(rng, ci, cj, p1, p2, tr, width, height, outlier_frac,
+                        min_pairs_per_image_pair)
+
+
+def _grouped_tracks_to_pairs(rng, cams_by_k, uv_by_k, width, height, outlier_frac,
+                             min_pairs_per_image_pair):
+    """Same as _tracks_to_pairs with tracks already grouped by length: lists of
+    [n,k] camera arrays and [n,k,2] pixel arrays; track ids run over the groups
+    in order."""
+    ci, cj, p1, p2, tr = [], [], [], [], []
+    base = 0
+    for cams, uv in zip(cams_by_k, uv_by_k):
+        n, k = cams.shape
+        comb = np.array(list(combinations(range(k), 2)))
+        a, b = comb[:, 0], comb[:, 1]
+        ci.append(cams[:, a].reshape(-1))
+        cj.append(cams[:, b].reshape(-1))
+        p1.append(uv[:, a].reshape(-1, 2))
+        p2.append(uv[:, b].reshape(-1, 2))
+        tr.append(np.repeat(np.arange(base, base + n), len(comb)))
+        base += n
+    ci = np.concatenate(ci).astype(np.int64)
+    cj = np.concatenate(cj).astype(np.int64)
+    p1 = np.concatenate(p1)
+    p2 = np.concatenate(p2)
+    tr = np.concatenate(tr).astype(np.int64)
+    return _group_pairs(rng, ci, cj, p1, p2, tr, width, height, outlier_frac,
+                        min_pairs_per_image_pair)
+
+
+def _group_pairs(rng, ci, cj, p1, p2, tr, width, height, outlier_frac,
+                 min_pairs_per_image_pair):
+    n_cam_key = int(max(ci.max(), cj.max())) + 1
+    key = ci * n_cam_key + cj
+    order = np.lexsort((tr, key))
+    ci, cj, p1, p2, tr, key = ci[order], cj[order], p1[order], p2[order], tr[order], key[order]
+    uniq, inv, counts = np.unique(key, return_inverse=True, return_counts=True)
+    keep_pair = counts >= min_pairs_per_image_pair
+    keep_kp = keep_pair[inv]
+    ci, cj, p1, p2, tr, inv = ci[keep_kp], cj[keep_kp], p1[keep_kp], p2[keep_kp], tr[keep_kp], inv[keep_kp]
+    new_index = np.cumsum(keep_pair) - 1
+    kp_img_pair = new_index[inv]
+    uniq = uniq[keep_pair]
+    pair_i = (uniq // n_cam_key).astype(np.int32)
+    pair_j = (uniq % n_cam_key).astype(np.int32)
+    # outliers: the second keypoint of the pair becomes a uniform random pixel
+    z = len(kp_img_pair)
+    is_out = rng.random(z) < outlier_frac
+    n_out = int(is_out.sum())
+    p2 = p2.copy()
+    p2[is_out, 0] = rng.uniform(0.0, width, n_out)
+    p2[is_out, 1] = rng.uniform(0.0, height, n_out)
+    return dict(pair_i=pair_i, pair_j=pair_j,
+                kp_img_pair=kp_img_pair.astype(np.int32),
+                kp1_px=p1.astype(np.float32), kp2_px=p2.astype(np.float32),
+                kp_track=tr.astype(np.int32), kp_inlier=~is_out)
+
+
+# --------------------------------------------------------------------------
+# configurations
+# --------------------------------------------------------------------------
+
+def scene_c1(seed: int = 0, n_points: int = 2000, sigma_px: float = 0.5,
+             outlier_frac: float = 0.05, n_cams: int = 20) -> Scene:
+    """Tiny scene: 20 cameras on a circle of radius 5 looking at the origin
+    with yaw jitter U(-10deg, 10deg), f = 500 px, 640x480, points uniform in a
+    unit cube, each seen by k ~ U{2..6} random cameras."""
+    rng = np.random.default_rng(seed)
+    W, H = 640, 480
+    N = n_cams
+    f = np.full(N, 500.0)
+    cx = np.full(N, W / 2.0)
+    cy = np.full(N, H / 2.0)
+    R = np.zeros((N, 3, 3))
+    t = np.zeros((N, 3))
+    up = np.array([0.0, 1.0, 0.0])
+    for k in range(N):
+        th = 2.0 * np.pi * k / N
+        C = 5.0 * np.array([np.cos(th), 0.0, np.sin(th)])
+        Rk = _frame_looking(-C, up)
+        yaw = np.deg2rad(rng.uniform(-10.0, 10.0))
+        Rk = _rot_axis(1, yaw) @ Rk
+        R[k] = Rk
+        t[k] = -Rk @ C
+    X = rng.uniform(-0.5, 0.5, size=(n_points, 3))
+    u, v, z = _project(R, t, f, cx, cy, X)
+    track_cams, track_uv = [], []
+    for p in range(n_points):
+        k = int(rng.integers(2, 7))
+        cams = np.sort(rng.choice(N, size=k, replace=False))
+        uv = np.stack([u[p, cams], v[p, cams]], axis=1) + rng.normal(0.0, sigma_px, size=(k, 2))
+        track_cams.append(cams)
+        track_uv.append(uv)
+    g = _tracks_to_pairs(rng, track_cams, track_uv, W, H, outlier_frac, 8)
+    return Scene(name="c1", seed=seed, width=W, height=H, focal=f, cx=cx, cy=cy,
+                 R_gt=R, t_gt=t, points=X, meta=dict(sigma_px=sigma_px,
+                 outlier_frac=outlier_frac), **g)
+
+
+def _bspline(ctrl: np.ndarray, s: np.ndarray):
+    """Uniform cubic B-spline through (approximating) the control points, with
+    end points clamped by tripling; returns positions and tangents at s in [0,1]."""
+    P = np.concatenate([ctrl[:1], ctrl[:1], ctrl, ctrl[-1:], ctrl[-1:]])
+    nseg = len(P) - 3
+    x = np.clip(s, 0.0, 1.0 - 1e-12) * nseg
+    i = np.floor(x).astype(int)
+    u = (x - i)[:, None]
+    b0 = (1 - u) ** 3 / 6
+    b1 = (3 * u ** 3 - 6 * u ** 2 + 4) / 6
+    b2 = (-3 * u ** 3 + 3 * u ** 2 + 3 * u + 1) / 6
+    b3 = u ** 3 / 6
+    d0 = -(1 - u) ** 2 / 2
+    d1 = (9 * u ** 2 - 12 * u) / 6
+    d2 = (-9 * u ** 2 + 6 * u + 3) / 6
+    d3 = u ** 2 / 2
+    pos = b0 * P[i] + b1 * P[i + 1] + b2 * P[i + 2] + b3 * P[i + 3]
+    tan = d0 * P[i] + d1 * P[i + 1] + d2 * P[i + 2] + d3 * P[i + 3]
+    return pos, tan
+
+
+def scene_c2(seed: int = 0, n_cams: int = 300, n_points: int = 100_000,
+             sigma_px: float = 1.0, outlier_frac: float = 0.10,
+             box=(50.0, 50.0, 10.0), max_depth: float = 30.0,
+             track_mean: float = 4.0, jitter_deg: float = 15.0,
+             focal_range=(400.0, 900.0), chunk: int = 8192) -> Scene:
+    """Scene at scale: cameras on a smooth random trajectory (cubic B-spline
+    through 8 random control points inside a 50x50x10 box) looking along the
+    tangent with +-15deg jitter, f ~ U(400, 900) px, points uniform in the box,
+    track length 2 + Geometric (mean ``track_mean``) capped by visibility (in
+    front, inside the image, depth <= 30)."""
+    rng = np.random.default_rng(seed)
+    W, H = 640, 480
+    N = n_cams
+    bx = np.asarray(box, dtype=np.float64)
+    ctrl = rng.uniform(0.0, 1.0, size=(8, 3)) * bx
+    pos, tan = _bspline(ctrl, np.linspace(0.0, 1.0, N))
+    up = np.array([0.0, 0.0, 1.0])
+    R = np.zeros((N, 3, 3))
+    t = np.zeros((N, 3))
+    for k in range(N):
+        fwd = tan[k].copy()
+        fwd[2] *= 0.2  # keep the view roughly level
+        if np.linalg.norm(fwd) < 1e-9:
+            fwd = np.array([1.0, 0.0, 0.0])
+        Rk = _frame_looking(fwd, up)
+        yaw = np.deg2rad(rng.uniform(-jitter_deg, jitter_deg))
+        pitch = np.deg2rad(rng.uniform(-jitter_deg, jitter_deg))
+        Rk = _rot_axis(1, yaw) @ _rot_axis(0, pitch) @ Rk
+        R[k] = Rk
+        t[k] = -Rk @ pos[k]
+    f = rng.uniform(focal_range[0], focal_range[1], size=N)
+    cx = np.full(N, W / 2.0)
+    cy = np.full(N, H / 2.0)
+    X = rng.uniform(0.0, 1.0, size=(n_points, 3)) * bx
+    p_geom = 1.0 / (track_mean - 1.0)   # k = 2 + (Geometric(p) - 1), mean track_mean
+    groups = {}                          # k -> list of (cams [n,k], uv [n,k,2], point ids [n])
+    for s0 in range(0, n_points, chunk):
+        Xs = X[s0:s0 + chunk]
+        u, v, z = _project(R, t, f, cx, cy, Xs)
+        vis = (z > 0.1) & (z <= max_depth) & (u >= 0) & (u < W) & (v >= 0) & (v < H)
+        nvis = vis.sum(axis=1)
+        want = 2 + rng.geometric(p_geom, size=len(Xs)) - 1
+        k = np.minimum(want, nvis)
+        keys = rng.random(vis.shape)
+        keys[~vis] = np.inf
+        order = np.argsort(keys, axis=1)
+        for kk in np.unique(k[k >= 2]):
+            rows = np.nonzero(k == kk)[0]
+            cams = np.sort(order[rows, :kk], axis=1)
+            uv = np.stack([u[rows[:, None], cams], v[rows[:, None], cams]], axis=2)
+            groups.setdefault(int(kk), []).append((cams, uv, s0 + rows))
+    track_cams, track_uv, track_pts = [], [], []
+    for kk in sorted(groups):
+        cams = np.concatenate([g[0] for g in groups[kk]])
+        uv = np.concatenate([g[1] for g in groups[kk]])
+        pts = np.concatenate([g[2] for g in groups[kk]])
+        # per-observation noise (shared by every pair that uses the observation)
+        uv = uv + rng.normal(0.0, sigma_px, size=uv.shape)
+        track_cams.append(cams)
+        track_uv.append(uv)
+        track_pts.append(pts)
+    g = _grouped_tracks_to_pairs(rng, track_cams, track_uv, W, H, outlier_frac, 8)
+    track_pts = np.concatenate(track_pts)
+    return Scene(name="c2", seed=seed, width=W, height=H, focal=f, cx=cx, cy=cy,
+                 R_gt=R, t_gt=t, points=X[track_pts],
+                 meta=dict(sigma_px=sigma_px, outlier_frac=outlier_frac,
+                           n_points_sampled=n_points), **g)
+
+
+CONFIGS = {
+    # the small case the oracle finishes in seconds
+    "c1": dict(fn=scene_c1, kwargs={}),
+    # the scene at scale as specified (about 0.9-1.2M keypoint pairs)
+    "c2": dict(fn=scene_c2, kwargs={}),
+    # the scene at scale with the point count raised so that the number of
+    # keypoint pairs is about 5M, the pair count the workload is quoted at
+    "c2_5m": dict(fn=scene_c2, kwargs=dict(n_points=605_000)),
+}
+
+
+def make_scene(config: str = "c1", seed: int = 0, **overrides) -> Scene:
+    spec = CONFIGS[config]
+    kw = dict(spec["kwargs"])
+    kw.update(overrides)
+    sc = spec["fn"](seed=seed, **kw)
+    sc.name = config
+    return sc
+
+
+# --------------------------------------------------------------------------
+# inputs for the per-stage evaluations (seeded; no method arithmetic)
+# --------------------------------------------------------------------------
+
+def gt_relative_poses(scene: Scene, rot_noise_deg: float = 0.0,
+                      dir_noise_deg: float = 0.0, seed: int = 0):
+    """Relative rotations R^{i->j} = R_j R_i^T and unit relative translations
+    t^{i->j} (direction of t_j - R^{i->j} t_i) of every image pair, optionally
+    perturbed by small random rotations.  Returns float64 arrays [P,3,3], [P,3]."""
+    rng = np.random.default_rng(seed)
+    Ri = scene.R_gt[scene.pair_i]
+    Rj = scene.R_gt[scene.pair_j]
+    Rij = Rj @ np.transpose(Ri, (0, 2, 1))
+    tij = scene.t_gt[scene.pair_j] - np.einsum("pab,pb->pa", Rij, scene.t_gt[scene.pair_i])
+    tij /= np.linalg.norm(tij, axis=1, keepdims=True)
+    P = scene.n_pairs
+    if rot_noise_deg > 0:
+        for p in range(P):
+            Rij[p] = _small_rotation(rng, rot_noise_deg) @ Rij[p]
+    if dir_noise_deg > 0:
+        for p in range(P):
+            tij[p] = _small_rotation(rng, dir_noise_deg) @ tij[p]
+    return Rij, tij
+
+
+def _small_rotation(rng, deg):
+    axis = rng.normal(size=3)
+    axis /= np.linalg.norm(axis)
+    ang = np.deg2rad(deg) * rng.normal()
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    return np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * K @ K
+
+
+def perturb_params(base: np.ndarray, sigma: float, seed: int) -> np.ndarray:
+    """Gaussian perturbation of a parameter array (seeded)."""
+    rng = np.random.default_rng(seed)
+    return base + rng.normal(0.0, sigma, size=base.shape)
