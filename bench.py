@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Throughput of the epipolar-adjustment step (FastMap, Sec. 3.3): keypoint-pair
+loss+grad evaluations per second on one B300.
+
+A step is one full pass of the hot path over every keypoint pair of the scene
+through the C ABI (fm_step, one iteration): the per-image-pair essential
+matrices, the direct L1 loss and its gradient over all keypoint pairs (Eq. 7),
+the per-image-pair chain rule, the fixed-order loss reduction and the
+per-camera Adam update.
+
+Workload: the seeded synthetic scene "c2_5m" -- 300 cameras on a smooth random
+trajectory through a 50x50x10 box, f ~ U(400, 900) px, 640x480, track length
+2 + Geometric (mean 4), sigma = 1 px, 10% outliers, with the point count raised
+to ~605k so that the scene has ~5.0M keypoint pairs.  The keypoint stream
+(80 MB) fits in the 126 MB L2, so L2 is flushed (a 256 MB write) before every
+timed step and the flush is outside the timed interval.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own replica of the scene (the
+path is single-GPU; replicas only): value = all ranks' pairs / max rank time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+_ONE_THREAD = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+if "--cpu-worker" in sys.argv or ("--impl" in sys.argv and "reference" in sys.argv):
+    os.environ.update(_ONE_THREAD)   # the oracle legs run on one host thread
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "keypoint-pair loss+grad evals/s (HBM roofline %); time-to-accuracy learned vs plain"
+UNIT = "keypoint-pair evals/s"
+BYTES_PER_PAIR = 16          # float4 (x1, y1, x2, y2) read once per evaluation
+PROFILE = os.path.join(ROOT, "profiles", "k_ea_direct_c2_5m.txt")
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2_5m")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ["fm_ea.cu", "fm_internal.h", "fm_device.cuh"]:
+        h.update(open(os.path.join(ROOT, "paper_2505_04612_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per k_ea_direct launch from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    if not os.path.exists(PROFILE):
+        return None
+    kv = {}
+    for line in open(PROFILE):
+        if "=" in line and not line.lstrip().startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_sha") != source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        reasons = set()
+        for r in rows:
+            for key, name in [("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")]:
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "power_w_max": max(r["power"] for r in rows), "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def make_workload(config, seed):
+    from synthetic.scenes import make_scene
+    sc = make_scene(config, seed)
+    R = sc.R_gt
+    p = np.concatenate([R[:, :, 0], R[:, :, 1], sc.t_gt], axis=1)
+    rng = np.random.default_rng(1000 + seed)
+    p = p + rng.normal(0.0, 0.01, size=p.shape)
+    return sc, p.astype(np.float32)
+
+
+def cpu_baseline(sc, params, budget_s):
+    """The FP64 oracle (as it stands) on a bounded sample: the first image
+    pairs of the scene holding ~500k keypoint pairs, L1 loss + gradient, in a
+    worker process limited to one host thread."""
+    off = sc.seg_off()
+    n_pairs = int(np.searchsorted(off, 500_000))
+    z = int(off[n_pairs])
+    with tempfile.TemporaryDirectory() as d:
+        f = os.path.join(d, "sample.npz")
+        np.savez(f, kp1=sc.kp1_px[:z], kp2=sc.kp2_px[:z], kpp=sc.kp_img_pair[:z], pi=sc.pair_i[:n_pairs],
+                 pj=sc.pair_j[:n_pairs], focal=sc.focal, cx=sc.cx, cy=sc.cy, params=params,
+                 budget=np.float64(budget_s))
+        env = dict(os.environ, **_ONE_THREAD)
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", f],
+                             capture_output=True, text=True, env=env, timeout=600)
+    if out.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": out.stderr[-400:]}
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{z} keypoint pairs of the first {n_pairs} image pairs, {r['evals']} L1 loss+grad "
+                      f"evaluations in {r['seconds']:.1f} s (float64 numpy, 1 thread)"}
+
+
+def cpu_worker(path):
+    from oracle import epipolar as ep
+    d = np.load(path)
+    f64 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    x1, x2 = ep.calibrated_pairs(d["kp1"], d["kp2"], d["kpp"], d["pi"], d["pj"], f64(d["focal"]), f64(d["cx"]),
+                                 f64(d["cy"]))
+    p = d["params"].reshape(-1, 9).astype(np.float64)
+    evals, t0 = 0, time.perf_counter()
+    while True:
+        ep.direct_loss_grad(p, d["pi"], d["pj"], x1, x2, d["kpp"], loss="l1")
+        evals += 1
+        el = time.perf_counter() - t0
+        if el > float(d["budget"]) or evals >= 50:
+            break
+    print(json.dumps({"value": len(d["kpp"]) * evals / el, "evals": evals, "seconds": el}))
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc, params = make_workload(a.config, a.seed)
+    from oracle import epipolar as ep
+    from oracle.adam import Adam
+    off = sc.seg_off()
+    n_pairs = int(np.searchsorted(off, 200_000))
+    z = int(off[n_pairs])
+    sel = slice(0, z)
+    x1, x2 = ep.calibrated_pairs(sc.kp1_px[sel], sc.kp2_px[sel], sc.kp_img_pair[sel], sc.pair_i, sc.pair_j,
+                                 np.float32(sc.focal).astype(np.float64), np.float32(sc.cx).astype(np.float64),
+                                 np.float32(sc.cy).astype(np.float64))
+    p = params.reshape(-1, 9).astype(np.float64)
+    pi, pj = sc.pair_i[:n_pairs], sc.pair_j[:n_pairs]
+    opt = Adam(p.shape, lr=1e-4)
+    for _ in range(a.warmup):
+        L, g, _ = ep.direct_loss_grad(p, pi, pj, x1, x2, sc.kp_img_pair[sel], loss="l1")
+        p = opt.step(p, g)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        L, g, _ = ep.direct_loss_grad(p, pi, pj, x1, x2, sc.kp_img_pair[sel], loss="l1")
+        p = opt.step(p, g)
+    el = time.perf_counter() - t0
+    value = z * a.steps / el
+    sample = (f"{z} keypoint pairs of the first {n_pairs} image pairs of the workload per step "
+              f"(L1 loss + gradient + Adam, float64 numpy, 1 thread)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * el / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(sc, a),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(sc, a):
+    return {"workload": f"{a.config}: epipolar adjustment step (L1, Eq. 7, + Adam), {sc.n_cams} cameras, "
+                        f"{sc.n_pairs} image pairs, {sc.n_kp} keypoint pairs, seed {a.seed}",
+            "n_cams": sc.n_cams, "n_img_pairs": sc.n_pairs, "n_kp_pairs": sc.n_kp,
+            "l2": "flushed before every timed step (256 MB write); flush not timed",
+            "parallelism": "replicas" if a.gpus > 1 else "single GPU"}
+
+
+def main():
+    a = args_()
+    if a.cpu_worker:
+        return cpu_worker(a.cpu_worker)
+    if a.impl == "reference":
+        return run_reference(a)
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2505_04612_b300 import build as B
+    B.build()
+    from paper_2505_04612_b300 import fastmap as F
+
+    sc, params = make_workload(a.config, a.seed)
+    pr = F.problem_from_scene(sc)
+    Z = sc.n_kp
+    p_dev = torch.from_numpy(params.reshape(-1)).to(dev)
+    pr.set_params(F.FM_STAGE_EPIPOLAR, p_dev)
+    pr.set_ea_loss(F.FM_EA_L1)
+    pr.track_loss(1, 4096)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    adam = dict(lr=1e-4)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(a.warmup):
+        flush.zero_()
+        pr.step(F.FM_STAGE_EPIPOLAR, 1, **adam)
+
+    def timed_pass():
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        barrier()
+        for k in range(a.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            pr.step(F.FM_STAGE_EPIPOLAR, 1, **adam)
+            ev[k][1].record(stream)
+        barrier()
+        return sum(e0.elapsed_time(e1) for e0, e1 in ev)
+
+    # pass A: the number (no per-kernel events inside the steps)
+    pr.timing(False)
+    with Clocks(local) as clk:
+        total_ms = timed_pass()
+    launches = pr.timing_read()
+    gpu_launches = int(sum(v[0] for v in launches.values()))
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    # pass B: per-kernel device time from the library's event pairs on its stream
+    pr.timing(True)
+    timed_pass()
+    kt = pr.timing_read()
+    pr.timing(False)
+    losses = pr.loss_history(8)
+
+    # end to end through the C ABI with pinned host buffers (params in, loss + grad out)
+    host_p = torch.from_numpy(params.reshape(-1).copy()).pin_memory()
+    host_g = torch.empty_like(host_p).pin_memory()
+    e2e_ms = 0.0
+    for k in range(max(a.warmup, 1) + a.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L, g = pr.loss_grad(F.FM_STAGE_EPIPOLAR, host_p, grad_out=host_g)
+        dt = time.perf_counter() - t0
+        if k >= max(a.warmup, 1):
+            e2e_ms += 1e3 * dt
+    e2 = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2, op=dist.ReduceOp.MAX)
+    e2e_ms = float(e2.item())
+
+    if rank == 0:
+        peak, peak_kind = peaks()
+        n_ea, ms_ea = kt.get("k_ea_direct", (0, 0.0))
+        avg_ea = ms_ea / max(n_ea, 1)
+        achieved = BYTES_PER_PAIR * Z / (avg_ea * 1e-3) / 1e9
+        value = world * Z * a.steps / (total_ms * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(sc, a),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": profiled_traffic(),
+                         "kernel": "k_ea_direct", "bytes_per_launch": BYTES_PER_PAIR * Z,
+                         "avg_launch_us": avg_ea * 1e3, "peak_kind": f"{peak_kind} copy bandwidth"},
+            "e2e": {"value": world * Z * a.steps / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(host_p.numel() * 4), "d2h_bytes_per_step": int(host_g.numel() * 4 + 4),
+                    "call": "fm_loss_grad with host params / host loss and gradient"},
+            "gpu_launches": gpu_launches,
+            "kernels_us_per_launch": {k: 1e3 * v[1] / max(v[0], 1) for k, v in kt.items()},
+            "clocks": clk.summary(),
+            "last_losses": losses[-3:],
+        }
+        if not a.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(sc, params, a.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    pr.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,263 @@
+/*
+ * fastmap.h -- C ABI of the B300 (sm_103a) first-order solver for FastMap
+ * (arxiv 2505.04612, "FastMap: Revisiting Structure from Motion through
+ * First-Order Optimization").
+ *
+ * The library evaluates, on one GPU, the loss and gradient of the paper's
+ * first-order objectives and takes Adam steps on them:
+ *   - global rotation      (Sec. 3.3, Eqs. 3-4)
+ *   - global translation   (Sec. 3.3, Eqs. 5-6)
+ *   - epipolar adjustment  (Sec. 3.3, Eqs. 7-9; Appendix "Epipolar
+ *                           Adjustment", Eqs. 15-17)
+ *
+ * Conventions used by every entry point
+ *   - Pose of camera c is world-to-camera: x_cam = R_c X + t_c.
+ *   - Image pair n = (i_n, j_n), i_n != j_n; in a keypoint pair of image pair
+ *     n the first keypoint lies in image i_n and the second in image j_n.
+ *   - Keypoints are pixels (u, v); calibration uses a pinhole with focal f
+ *     and principal point (cx, cy):  x~ = ((u - cx)/f, (v - cy)/f, 1)
+ *     (Sec. 3.3, "normalized homogeneous coordinates"; Sec. 3.1, camera
+ *     assumptions).
+ *   - Parameters of a stage are one float32 row per camera:
+ *       FM_STAGE_ROTATION     6 floats  (a1, a2): the 6D representation,
+ *                             R = [b1 b2 b3], b1 = a1/|a1|,
+ *                             b2 = normalise(a2 - (b1.a2) b1), b3 = b1 x b2
+ *       FM_STAGE_TRANSLATION  3 floats  o: camera centre, one block of
+ *                             n_cams rows per initialisation run
+ *       FM_STAGE_EPIPOLAR     9 floats  (a1, a2, t): 6D rotation + translation
+ *   - Matrices are row-major float32.
+ *   - All floating point arithmetic on the GPU is float32.
+ *
+ * Memory and ownership
+ *   - fm_problem_create copies everything it needs; the caller keeps
+ *     ownership of its arrays and may free them after the call returns.
+ *   - Pointers are host pointers unless the argument or flag says device.
+ *   - Output buffers always belong to the caller.
+ *   - Every entry point runs on the CUDA stream given at creation and
+ *     returns after the work is enqueued, unless it writes a host buffer, in
+ *     which case it synchronises that stream first.
+ *
+ * Errors
+ *   - Every entry point returns an fm_status; no C++ exception crosses the
+ *     ABI and the library never exits or aborts.
+ *   - fm_last_error(problem) describes the last failure on that problem;
+ *     fm_last_error(NULL) describes the last failure of fm_problem_create on
+ *     the calling thread.
+ *   - Results are deterministic: no floating-point atomics are used, so the
+ *     same inputs give bitwise identical outputs on the same GPU.
+ */
+#ifndef FASTMAP_H
+#define FASTMAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fm_problem fm_problem;   /* opaque; owned by the library */
+
+typedef enum {
+  FM_OK = 0,
+  FM_ERR_INVALID_ARG = 1,   /* a size, index, pointer or value is invalid */
+  FM_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  FM_ERR_OOM = 3,           /* device memory could not be allocated */
+  FM_ERR_NAN = 4,           /* a non-finite value was produced or given */
+  FM_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+  FM_ERR_NOT_CONVERGED = 6,
+  FM_ERR_STATE = 7          /* the call needs state that has not been set */
+} fm_status;
+
+typedef enum {
+  FM_STAGE_ROTATION = 0,
+  FM_STAGE_TRANSLATION = 1,
+  FM_STAGE_EPIPOLAR = 2
+} fm_stage;
+
+/* Robust loss of the epipolar stage.
+ *   FM_EA_L1       direct, per keypoint pair:  (1/Z) sum w_m |r_m|      (Eq. 7)
+ *   FM_EA_L2       direct, per keypoint pair:  (1/Z) sum w_m r_m^2      (Eqs. 8-9)
+ *   FM_EA_COMPACT  per image pair:  (1/Z) sum_n e_n^T W_n e_n           (Eqs. 8-9,
+ *                  right-hand side; W_n = sum_m w_m vec(x~2 x~1^T)vec(.)^T,
+ *                  Eq. 17, rebuilt whenever the weights change) -- the same
+ *                  objective as FM_EA_L2 at a per-step cost independent of Z
+ * with r_m = x~2^T E_n x~1 and E_n = [t_ij/|t_ij|]_x R_ij,
+ * R_ij = R_j R_i^T, t_ij = t_j - R_ij t_i.  w_m = 1 until fm_ea_set_weights
+ * sets per-pair weights; Z is the number of keypoint pairs, or the value
+ * given to fm_ea_set_weights. */
+typedef enum {
+  FM_EA_L1 = 0,
+  FM_EA_L2 = 1,
+  FM_EA_COMPACT = 2
+} fm_ea_loss;
+
+/* Problem description (Sec. 3.3: the inputs of the pose stages are the image
+ * pairs, their inlier keypoint pairs and the calibrated intrinsics). */
+typedef struct {
+  int32_t n_cams;              /* N >= 2 */
+  int32_t n_img_pairs;         /* P >= 1 */
+  int64_t n_kp_pairs;          /* Z >= 0, Z < 2^31 - 2^20 */
+  const int32_t* pair_cam_i;   /* [P] first image of each image pair */
+  const int32_t* pair_cam_j;   /* [P] second image; != pair_cam_i */
+  const int32_t* kp_img_pair;  /* [Z] image pair of each keypoint pair,
+                                  NON-DECREASING (keypoint pairs grouped by
+                                  image pair, image pairs in index order) */
+  const float* kp1_px;         /* [Z*2] (u, v) of the keypoint in image i_n */
+  const float* kp2_px;         /* [Z*2] (u, v) of the keypoint in image j_n */
+  const int32_t* kp_track;     /* [Z] track id, or NULL (used by no entry
+                                  point yet; copied if given) */
+  const float* focal;          /* [N] > 0 */
+  const float* cx;             /* [N] */
+  const float* cy;             /* [N] */
+  const float* rel_R;          /* [P*9] R^{i->j}, or NULL */
+  const float* rel_t;          /* [P*3] unit t^{i->j}, or NULL */
+  int32_t inputs_on_device;    /* 1: every pointer above is device memory */
+  void* cuda_stream;           /* cudaStream_t to run on; NULL = default */
+} fm_problem_desc;
+
+typedef struct {
+  int32_t n_cams;
+  int32_t n_img_pairs;
+  int64_t n_kp_pairs;
+  int32_t n_empty_img_pairs;   /* image pairs with no keypoint pair */
+  int32_t pairs_per_lane;      /* keypoint pairs per thread in the direct kernel */
+  int64_t n_records;           /* per-(warp run, image pair) partial sums */
+  int64_t device_bytes;        /* device memory held by the problem */
+} fm_problem_info;
+
+/* Adam (the paper's cited adaptive first-order method, Sec. 1, Sec. 3.2; no
+ * constants are given there).  Bias-corrected, as Kingma & Ba define it. */
+typedef struct {
+  float lr;
+  float beta1;
+  float beta2;
+  float eps;
+} fm_adam_opts;
+
+/* Creates a problem on the current CUDA device.  Validates the description
+ * (sizes, camera indices of the image pairs, intrinsics on the host side;
+ * ordering and range of kp_img_pair and finiteness of the keypoints on the
+ * device) and returns FM_ERR_INVALID_ARG / FM_ERR_NAN on bad input.
+ * Calibrates the keypoints (Sec. 3.3, x~ = K^-1 [u, v, 1]^T) and builds the
+ * image-pair and camera tables (Sec. 3.4: one fused evaluation per step).
+ * Synchronises the stream.  On success *out owns device memory until
+ * fm_problem_destroy. */
+fm_status fm_problem_create(const fm_problem_desc* desc, fm_problem** out);
+
+/* Releases every resource of the problem (NULL is a no-op).  Synchronises. */
+void fm_problem_destroy(fm_problem* problem);
+
+/* Text of the last error (see the Errors paragraph above); never NULL. */
+const char* fm_last_error(const fm_problem* problem);
+
+/* Sizes and memory use of a problem. */
+fm_status fm_problem_info_get(const fm_problem* problem, fm_problem_info* out);
+
+/* Replaces the parameters of a stage (layout above) and resets the stage's
+ * Adam moments and step counter.  params_on_device: 1 if params is a device
+ * pointer.  FM_ERR_NAN if a value is not finite. */
+fm_status fm_set_params(fm_problem* problem, fm_stage stage, const float* params,
+                        int32_t params_on_device);
+
+/* Copies the current parameters of a stage into params_out (host or device
+ * as flagged).  Synchronises when params_out is a host pointer. */
+fm_status fm_get_params(const fm_problem* problem, fm_stage stage, float* params_out,
+                        int32_t out_on_device);
+
+/* Relative rotations R^{i->j} [P*9] and unit relative translations t^{i->j}
+ * [P*3] of the image pairs (the inputs of Eqs. 3 and 5); either may be NULL
+ * to keep the current one.  Replacing rel_t invalidates the translation
+ * targets, which are rebuilt from the rotation-stage parameters on the next
+ * translation-stage call. */
+fm_status fm_set_rel_poses(fm_problem* problem, const float* rel_R, const float* rel_t,
+                           int32_t on_device);
+
+/* Number m of independent translation runs solved together (Appendix
+ * "Multiple Initializations"); 1 <= m <= 64.  The translation-stage
+ * parameters become [m*N*3] (one block of N centres per run), losses [m];
+ * the parameters must be set again afterwards. */
+fm_status fm_translation_set_runs(fm_problem* problem, int32_t n_runs);
+
+/* Selects the robust loss of the epipolar stage (default FM_EA_L1). */
+fm_status fm_ea_set_loss(fm_problem* problem, fm_ea_loss loss);
+
+/* Per-keypoint-pair weights w_m of the epipolar stage (Eq. 9: IRLS weights
+ * 1/|eps^_m|; a weight of 0 removes a filtered pair), in the order of the
+ * keypoint pairs given at creation, and the normaliser 1/Z of the loss.
+ * weights == NULL restores unit weights and inv_z = 1/n_kp_pairs.  Rebuilds
+ * the compact matrices W_n (Eq. 17), stored together with their expansion
+ * around the essential matrices of the current epipolar-stage parameters, so
+ * those parameters must be set first (FM_ERR_STATE otherwise). */
+fm_status fm_ea_set_weights(fm_problem* problem, const float* weights,
+                            int32_t weights_on_device, float inv_z);
+
+/* IRLS reweighting and outlier filtering at the current epipolar-stage
+ * parameters (Sec. 3.3: weights from the absolute epipolar error eps^ of the
+ * previous round, Eq. 9; periodic filtering of pairs with a large error).
+ * For every keypoint pair, eps^ = x~2^T E_n x~1; the pair is kept when
+ * |eps^| < tau and then weighted 1/max(|eps^|, delta) when irls != 0, or 1
+ * when irls == 0; filtered pairs get weight 0.  Sets inv_z = 1/#kept,
+ * rebuilds W_n, and writes #kept to *n_kept (may be NULL).  Synchronises. */
+fm_status fm_ea_reweight(fm_problem* problem, float tau, float delta, int32_t irls,
+                         int64_t* n_kept);
+
+/* Copies the current per-pair weights (host or device as flagged) and the
+ * loss normaliser.  FM_ERR_STATE when no weights are set.  Synchronises. */
+fm_status fm_ea_get_weights(fm_problem* problem, float* weights_out, int32_t out_on_device,
+                            float* inv_z);
+
+/* Loss and gradient of a stage at the given parameters (Eqs. 3-4 for the
+ * rotation stage; Eqs. 5-6 for the translation stage, with targets
+ * o^{i->j} = -R_j^T t^{i->j} from the rotation-stage parameters; Eq. 7 or
+ * Eqs. 8-9 for the epipolar stage, with the loss chosen by fm_ea_set_loss).
+ * params: [N*dim] (layout above; [m*N*3] for m translation runs); grad: same
+ * layout, or NULL; loss: host array of one value ([m] for the translation
+ * stage), or NULL.  mem_on_device: 1 if params and grad are device pointers.
+ * The stage's own parameters and Adam state are not touched.  Synchronises
+ * when loss or a host grad is requested. */
+fm_status fm_loss_grad(fm_problem* problem, fm_stage stage, const float* params,
+                       float* loss, float* grad, int32_t mem_on_device);
+
+/* n_iters Adam steps on the stage's parameters, each one a full evaluation of
+ * the loss and gradient (over all keypoint pairs for the epipolar stage)
+ * followed by the update (Sec. 3.2-3.4).  loss (host, or NULL; [m] for the
+ * translation stage) receives the loss of the last evaluation, i.e. at the
+ * parameters before the last update; passing NULL keeps the call
+ * asynchronous. */
+fm_status fm_step(fm_problem* problem, fm_stage stage, const fm_adam_opts* opts,
+                  int32_t n_iters, float* loss);
+
+/* ---------------------------------------------------------- observability
+ * (no counterpart in the paper, which times whole stages by wall clock) */
+
+/* Per-kernel device time: with timing on, the library records a CUDA event
+ * pair around every kernel it launches (on its stream) and accumulates the
+ * elapsed time per kernel name.  Enabling or disabling resets the counters. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+} fm_kernel_time;
+
+fm_status fm_timing_enable(fm_problem* problem, int32_t enable);
+
+/* Writes up to capacity entries (one per kernel name launched since timing
+ * was enabled) and their count to *count.  Synchronises the stream. */
+fm_status fm_timing_read(fm_problem* problem, fm_kernel_time* out, int32_t capacity,
+                         int32_t* count);
+
+/* Loss trace: with every > 0, fm_step also reduces the loss (fixed order, on
+ * the device, no host synchronisation) every `every` iterations into a ring
+ * of `capacity` values; every = 0 turns it off and clears the ring. */
+fm_status fm_track_loss(fm_problem* problem, int32_t every, int32_t capacity);
+
+/* Copies the most recent min(capacity, recorded) traced losses, oldest
+ * first, into out and their number into *count (for the translation stage,
+ * the loss of run 0).  Synchronises the stream. */
+fm_status fm_loss_history(fm_problem* problem, float* out, int32_t capacity, int32_t* count);
+
+#ifdef __cplusplus
+}  /* extern "C" */
+#endif
+
+#endif /* FASTMAP_H */

@@ -12,16 +12,19 @@
 """
 import numpy as np
 
-from .so3 import rot_from_6d, rot_from_6d_vjp
+from .so3 import project_to_rotation, rot_from_6d, rot_from_6d_vjp
 
 
-def loss_grad(params6, pair_i, pair_j, rel_R):
+def loss_grad(params6, pair_i, pair_j, rel_R, project=True):
     """L_R and its gradient with respect to the 6D parameters [N,6].
 
     With M = R_j^T R_ij R_i, c = (tr M - 1)/2 and d = arccos(c):
     dd/dc = -1/sqrt(1 - c^2); tr M = <R_j, R_ij R_i> so
     d tr/dR_j = R_ij R_i and d tr/dR_i = R_ij^T R_j.
     Where 1 - c^2 <= 0 (d = 0 or pi) the subgradient 0 is used.
+    project: take each given R_ij as its nearest rotation first (arccos near 1
+    is ill-conditioned, so a 1e-7 departure from orthogonality of a float32
+    input would otherwise move d by ~1e-7/d).
     """
     params6 = np.asarray(params6, dtype=np.float64)
     n = params6.shape[0]
@@ -29,6 +32,8 @@ def loss_grad(params6, pair_i, pair_j, rel_R):
     R = rot_from_6d(params6)
     Ri, Rj = R[pair_i], R[pair_j]
     Rij = np.asarray(rel_R, dtype=np.float64)
+    if project:
+        Rij = project_to_rotation(Rij)
     K = Rij @ Ri
     c = (np.einsum("pab,pab->p", Rj, K) - 1.0) / 2.0
     cc = np.clip(c, -1.0, 1.0)

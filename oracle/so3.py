@@ -70,6 +70,21 @@ def geodesic(R, Rp):
     return np.arccos(np.clip(c, -1.0, 1.0))
 
 
+def project_to_rotation(M):
+    """Nearest rotation (Frobenius) of each 3x3 matrix: U diag(1, 1, det(U V^T)) V^T
+    from the SVD M = U S V^T.  A float32 copy of a rotation is a rotation only
+    to ~1e-7; the geodesic distance of Eq. 4 is defined for rotations, so the
+    oracle evaluates it on the rotation the given matrix stands for."""
+    M = np.asarray(M, dtype=np.float64)
+    U, _, Vt = np.linalg.svd(M)
+    d = np.sign(np.linalg.det(U @ Vt))
+    D = np.zeros(M.shape)
+    D[..., 0, 0] = 1.0
+    D[..., 1, 1] = 1.0
+    D[..., 2, 2] = d
+    return U @ D @ Vt
+
+
 def angle_axis(axis, ang):
     """Rodrigues' formula (used by tests to build exact rotations)."""
     axis = np.asarray(axis, dtype=np.float64)

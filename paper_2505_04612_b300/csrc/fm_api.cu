@@ -1,0 +1,823 @@
+// Host runtime of the C ABI declared in include/fastmap.h.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fm_internal.h"
+
+namespace fm {
+const char* const kKernelNames[kKCount] = {
+    "k_calibrate", "k_seg_offsets", "k_run_tables", "k_ea_tables", "k_ea_direct",
+    "k_ea_segments", "k_rot_pairs", "k_trn_targets", "k_trn_pairs", "k_cam", "k_sum_fixed",
+    "k_ea_reweight", "k_w_build", "k_ea_compact"};
+}
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+cudaEvent_t take_event(fm_problem* pr) {
+  if (!pr->event_pool.empty()) {
+    cudaEvent_t e = pr->event_pool.back();
+    pr->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Counts every kernel launch; with timing on, brackets it with an event pair
+// on the problem's stream.
+struct Timed {
+  fm_problem* pr;
+  int kid;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Timed(fm_problem* p, int k) : pr(p), kid(k) {
+    if (pr->timing) {
+      a = take_event(pr);
+      b = take_event(pr);
+      cudaEventRecord(a, pr->stream);
+    }
+  }
+  ~Timed() {
+    pr->k_launches[kid] += 1;
+    if (pr->timing) {
+      cudaEventRecord(b, pr->stream);
+      pr->pending.push_back({kid, a, b});
+    }
+  }
+};
+
+void drain_timing(fm_problem* pr, bool accumulate) {
+  if (pr->pending.empty()) return;
+  cudaStreamSynchronize(pr->stream);
+  for (auto& t : pr->pending) {
+    float ms = 0.f;
+    if (accumulate && cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) pr->k_ms[t.kid] += ms;
+    pr->event_pool.push_back(t.start);
+    pr->event_pool.push_back(t.stop);
+  }
+  cudaGetLastError();
+  pr->pending.clear();
+}
+
+fm_status fail(fm_problem* pr, fm_status st, const std::string& msg) {
+  if (pr) pr->last_error = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+#define FM_CUDA(pr, expr)                                                              \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail((pr), FM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define FM_LAUNCHED(pr)                                                                \
+  do {                                                                                 \
+    cudaError_t e_ = cudaGetLastError();                                               \
+    if (e_ != cudaSuccess)                                                             \
+      return fail((pr), FM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+fm_status dalloc(fm_problem* pr, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(pr, e == cudaErrorMemoryAllocation ? FM_ERR_OOM : FM_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  pr->device_bytes += (int64_t)(sizeof(T) * count);
+  return FM_OK;
+}
+
+#define FM_ALLOC(pr, p, n)                 \
+  do {                                     \
+    fm_status s_ = dalloc((pr), &(p), (n)); \
+    if (s_ != FM_OK) return s_;            \
+  } while (0)
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+int stage_dim(fm_stage st) {
+  return st == FM_STAGE_ROTATION ? 6 : (st == FM_STAGE_TRANSLATION ? 3 : 9);
+}
+
+// copy n elements from a host or device pointer into a host vector
+template <typename T>
+cudaError_t fetch(std::vector<T>& out, const T* src, size_t n, bool on_device) {
+  out.resize(n);
+  if (n == 0) return cudaSuccess;
+  if (on_device) return cudaMemcpy(out.data(), src, sizeof(T) * n, cudaMemcpyDeviceToHost);
+  std::memcpy(out.data(), src, sizeof(T) * n);
+  return cudaSuccess;
+}
+
+fm_status check_err_bits(fm_problem* pr) {
+  int bits = 0;
+  FM_CUDA(pr, cudaMemcpyAsync(&bits, pr->d_err, sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
+  FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+  if (bits == 0) return FM_OK;
+  FM_CUDA(pr, cudaMemsetAsync(pr->d_err, 0, sizeof(int), pr->stream));
+  std::string msg;
+  if (bits & fm::kErrKpRange) msg += "kp_img_pair outside [0, n_img_pairs); ";
+  if (bits & fm::kErrKpOrder) msg += "kp_img_pair is not non-decreasing; ";
+  if (bits & fm::kErrKpNonFinite) msg += "a keypoint coordinate is not finite; ";
+  if (bits & fm::kErrParamNonFinite) msg += "a parameter is not finite; ";
+  fm_status st = (bits & (fm::kErrKpNonFinite | fm::kErrParamNonFinite)) &&
+                         !(bits & (fm::kErrKpRange | fm::kErrKpOrder))
+                     ? FM_ERR_NAN
+                     : FM_ERR_INVALID_ARG;
+  return fail(pr, st, msg);
+}
+
+void release(fm_problem* pr) {
+  if (!pr) return;
+  cudaStreamSynchronize(pr->stream);
+  dfree(pr->pair_i); dfree(pr->pair_j); dfree(pr->seg_off);
+  dfree(pr->cam_seg_off); dfree(pr->cam_seg);
+  dfree(pr->kp); dfree(pr->kp_track); dfree(pr->focal); dfree(pr->cx); dfree(pr->cy);
+  dfree(pr->run_seg); dfree(pr->wrun_info); dfree(pr->seg_rec); dfree(pr->rec);
+  dfree(pr->seg_tab); dfree(pr->seg_grad); dfree(pr->seg_loss);
+  dfree(pr->ea_w); dfree(pr->ea_params);
+  dfree(pr->ea_adam.m); dfree(pr->ea_adam.v); dfree(pr->ea_adam.t);
+  dfree(pr->rel_R); dfree(pr->rel_t); dfree(pr->rot_params);
+  dfree(pr->rot_adam.m); dfree(pr->rot_adam.v); dfree(pr->rot_adam.t);
+  dfree(pr->trn_target); dfree(pr->trn_params);
+  dfree(pr->trn_adam.m); dfree(pr->trn_adam.v); dfree(pr->trn_adam.t);
+  dfree(pr->scratch_params); dfree(pr->scratch_grad); dfree(pr->d_loss); dfree(pr->d_err);
+  dfree(pr->loss_hist);
+  dfree(pr->W);
+  dfree(pr->d_kept);
+  drain_timing(pr, false);
+  for (cudaEvent_t e : pr->event_pool) cudaEventDestroy(e);
+  pr->event_pool.clear();
+  if (pr->h_loss) cudaFreeHost(pr->h_loss);
+  pr->h_loss = nullptr;
+}
+
+fm_status alloc_adam(fm_problem* pr, fm::AdamState& a, size_t n) {
+  FM_ALLOC(pr, a.m, n);
+  FM_ALLOC(pr, a.v, n);
+  FM_ALLOC(pr, a.t, 1);
+  return FM_OK;
+}
+
+fm_status reset_adam(fm_problem* pr, fm::AdamState& a, size_t n) {
+  FM_CUDA(pr, cudaMemsetAsync(a.m, 0, sizeof(float) * n, pr->stream));
+  FM_CUDA(pr, cudaMemsetAsync(a.v, 0, sizeof(float) * n, pr->stream));
+  FM_CUDA(pr, cudaMemsetAsync(a.t, 0, sizeof(int), pr->stream));
+  return FM_OK;
+}
+
+fm_status build(fm_problem* pr, const fm_problem_desc* d) {
+  const int N = pr->N, P = pr->P;
+  const int64_t Z = pr->Z;
+  const bool dev = d->inputs_on_device != 0;
+  cudaStream_t s = pr->stream;
+
+  // ---- small arrays: validate on the host
+  std::vector<int> hi, hj;
+  std::vector<float> hf, hcx, hcy;
+  FM_CUDA(pr, fetch(hi, d->pair_cam_i, P, dev));
+  FM_CUDA(pr, fetch(hj, d->pair_cam_j, P, dev));
+  FM_CUDA(pr, fetch(hf, d->focal, N, dev));
+  FM_CUDA(pr, fetch(hcx, d->cx, N, dev));
+  FM_CUDA(pr, fetch(hcy, d->cy, N, dev));
+  for (int n = 0; n < P; ++n) {
+    if (hi[n] < 0 || hi[n] >= N || hj[n] < 0 || hj[n] >= N)
+      return fail(pr, FM_ERR_INVALID_ARG, "image pair " + std::to_string(n) + " has a camera index outside [0, n_cams)");
+    if (hi[n] == hj[n])
+      return fail(pr, FM_ERR_INVALID_ARG, "image pair " + std::to_string(n) + " joins a camera to itself");
+  }
+  for (int c = 0; c < N; ++c) {
+    if (!(std::isfinite(hf[c]) && hf[c] > 0.f))
+      return fail(pr, FM_ERR_INVALID_ARG, "focal[" + std::to_string(c) + "] must be finite and > 0");
+    if (!(std::isfinite(hcx[c]) && std::isfinite(hcy[c])))
+      return fail(pr, FM_ERR_INVALID_ARG, "principal point of camera " + std::to_string(c) + " is not finite");
+  }
+  // camera -> incident image pairs, ordered by image pair (deterministic sums)
+  std::vector<int> coff(N + 1, 0), cseg(2 * (size_t)P);
+  for (int n = 0; n < P; ++n) { coff[hi[n] + 1]++; coff[hj[n] + 1]++; }
+  for (int c = 0; c < N; ++c) coff[c + 1] += coff[c];
+  {
+    std::vector<int> fill(coff.begin(), coff.end() - 1);
+    for (int n = 0; n < P; ++n) {
+      cseg[fill[hi[n]]++] = n;
+      cseg[fill[hj[n]]++] = (int)((unsigned)n | 0x80000000u);
+    }
+  }
+
+  FM_ALLOC(pr, pr->pair_i, P);
+  FM_ALLOC(pr, pr->pair_j, P);
+  FM_ALLOC(pr, pr->focal, N);
+  FM_ALLOC(pr, pr->cx, N);
+  FM_ALLOC(pr, pr->cy, N);
+  FM_ALLOC(pr, pr->cam_seg_off, N + 1);
+  FM_ALLOC(pr, pr->cam_seg, 2 * (size_t)P);
+  FM_ALLOC(pr, pr->seg_off, P + 1);
+  FM_ALLOC(pr, pr->d_err, 1);
+  FM_CUDA(pr, cudaMemcpyAsync(pr->pair_i, hi.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
+  FM_CUDA(pr, cudaMemcpyAsync(pr->pair_j, hj.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
+  FM_CUDA(pr, cudaMemcpyAsync(pr->focal, hf.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s));
+  FM_CUDA(pr, cudaMemcpyAsync(pr->cx, hcx.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s));
+  FM_CUDA(pr, cudaMemcpyAsync(pr->cy, hcy.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s));
+  FM_CUDA(pr, cudaMemcpyAsync(pr->cam_seg_off, coff.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, s));
+  FM_CUDA(pr, cudaMemcpyAsync(pr->cam_seg, cseg.data(), sizeof(int) * 2 * (size_t)P, cudaMemcpyHostToDevice, s));
+  FM_CUDA(pr, cudaMemsetAsync(pr->d_err, 0, sizeof(int), s));
+
+  // ---- keypoints: stage host inputs on the device, calibrate, offsets
+  FM_ALLOC(pr, pr->kp, Z);
+  const float* kp1 = d->kp1_px;
+  const float* kp2 = d->kp2_px;
+  const int* kpp = d->kp_img_pair;
+  float* tmp1 = nullptr;
+  float* tmp2 = nullptr;
+  int* tmpp = nullptr;
+  if (!dev && Z > 0) {
+    FM_ALLOC(pr, tmp1, 2 * Z);
+    FM_ALLOC(pr, tmp2, 2 * Z);
+    FM_ALLOC(pr, tmpp, Z);
+    FM_CUDA(pr, cudaMemcpyAsync(tmp1, kp1, sizeof(float) * 2 * Z, cudaMemcpyHostToDevice, s));
+    FM_CUDA(pr, cudaMemcpyAsync(tmp2, kp2, sizeof(float) * 2 * Z, cudaMemcpyHostToDevice, s));
+    FM_CUDA(pr, cudaMemcpyAsync(tmpp, kpp, sizeof(int) * Z, cudaMemcpyHostToDevice, s));
+    kp1 = tmp1;
+    kp2 = tmp2;
+    kpp = tmpp;
+  }
+  if (d->kp_track && Z > 0) {
+    FM_ALLOC(pr, pr->kp_track, Z);
+    FM_CUDA(pr, cudaMemcpyAsync(pr->kp_track, d->kp_track, sizeof(int) * Z,
+                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  }
+  {
+    Timed t(pr, fm::kKCalibrate);
+    fm::launch_calibrate(kp1, kp2, kpp, pr->pair_i, pr->pair_j, pr->focal, pr->cx, pr->cy, Z, P,
+                         pr->kp, pr->d_err, s);
+  }
+  FM_LAUNCHED(pr);
+  {
+    Timed t(pr, fm::kKSegOffsets);
+    fm::launch_seg_offsets(kpp, Z, P, pr->seg_off, pr->d_err, s);
+  }
+  FM_LAUNCHED(pr);
+  fm_status st = check_err_bits(pr);
+  if (tmp1) { cudaFree(tmp1); pr->device_bytes -= (int64_t)sizeof(float) * 2 * Z; }
+  if (tmp2) { cudaFree(tmp2); pr->device_bytes -= (int64_t)sizeof(float) * 2 * Z; }
+  if (tmpp) { cudaFree(tmpp); pr->device_bytes -= (int64_t)sizeof(int) * Z; }
+  if (st != FM_OK) return st;
+
+  {
+    std::vector<int> so(P + 1);
+    FM_CUDA(pr, cudaMemcpy(so.data(), pr->seg_off, sizeof(int) * (P + 1), cudaMemcpyDeviceToHost));
+    int e = 0;
+    for (int n = 0; n < P; ++n) e += (so[n] == so[n + 1]);
+    pr->n_empty = e;
+  }
+
+  // ---- tables of the direct epipolar kernel
+  pr->n_wruns = (int)((Z + fm::kEaWarpPairs - 1) / fm::kEaWarpPairs);
+  FM_ALLOC(pr, pr->run_seg, (size_t)pr->n_wruns * 32);
+  FM_ALLOC(pr, pr->wrun_info, pr->n_wruns);
+  FM_ALLOC(pr, pr->seg_rec, 2 * (size_t)P);
+  if (pr->n_wruns > 0) {
+    int64_t* d_total = nullptr;
+    FM_ALLOC(pr, d_total, 1);
+    {
+      Timed t(pr, fm::kKRunTables);
+      fm::launch_run_tables(pr->seg_off, P, Z, pr->n_wruns, pr->run_seg, pr->wrun_info, nullptr, s);
+    }
+    FM_LAUNCHED(pr);
+    fm::launch_exclusive_scan_info(pr->wrun_info, pr->n_wruns, d_total, s);
+    FM_LAUNCHED(pr);
+    int64_t total = 0;
+    FM_CUDA(pr, cudaMemcpyAsync(&total, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    FM_CUDA(pr, cudaStreamSynchronize(s));
+    cudaFree(d_total);
+    pr->device_bytes -= (int64_t)sizeof(int64_t);
+    pr->n_rec = total;
+  } else {
+    pr->n_rec = 0;
+  }
+  FM_ALLOC(pr, pr->rec, 3 * (size_t)(pr->n_rec > 0 ? pr->n_rec : 1));
+  fm::launch_seg_records(pr->seg_off, pr->run_seg, pr->wrun_info, P, pr->seg_rec, s);
+  FM_LAUNCHED(pr);
+
+  // ---- per-stage state
+  FM_ALLOC(pr, pr->seg_tab, 3 * (size_t)P);
+  FM_ALLOC(pr, pr->seg_grad, (size_t)fm::kSegGradEa * P);
+  FM_ALLOC(pr, pr->seg_loss, (size_t)P);
+  FM_ALLOC(pr, pr->ea_params, 9 * (size_t)N);
+  FM_ALLOC(pr, pr->rot_params, 6 * (size_t)N);
+  FM_ALLOC(pr, pr->trn_params, 3 * (size_t)N);
+  FM_ALLOC(pr, pr->trn_target, 3 * (size_t)P);
+  FM_ALLOC(pr, pr->rel_R, 9 * (size_t)P);
+  FM_ALLOC(pr, pr->rel_t, 3 * (size_t)P);
+  fm_status a;
+  if ((a = alloc_adam(pr, pr->ea_adam, 9 * (size_t)N)) != FM_OK) return a;
+  if ((a = alloc_adam(pr, pr->rot_adam, 6 * (size_t)N)) != FM_OK) return a;
+  if ((a = alloc_adam(pr, pr->trn_adam, 3 * (size_t)N)) != FM_OK) return a;
+  FM_ALLOC(pr, pr->scratch_params, 9 * (size_t)N);
+  FM_ALLOC(pr, pr->scratch_grad, 9 * (size_t)N);
+  FM_ALLOC(pr, pr->d_loss, 1);
+  FM_ALLOC(pr, pr->W, 64 * (size_t)P);
+  FM_ALLOC(pr, pr->d_kept, 1);
+  FM_CUDA(pr, cudaMallocHost((void**)&pr->h_loss, sizeof(float)));
+  pr->ea_inv_z = Z > 0 ? (float)(1.0 / (double)Z) : 0.f;
+  if (d->rel_R) {
+    FM_CUDA(pr, cudaMemcpyAsync(pr->rel_R, d->rel_R, sizeof(float) * 9 * P,
+                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    pr->rel_R_set = true;
+  }
+  if (d->rel_t) {
+    FM_CUDA(pr, cudaMemcpyAsync(pr->rel_t, d->rel_t, sizeof(float) * 3 * P,
+                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    pr->rel_t_set = true;
+  }
+  FM_CUDA(pr, cudaStreamSynchronize(s));
+  return FM_OK;
+}
+
+// device pointer of a stage's parameters and Adam state
+struct StageBuf {
+  float* params;
+  fm::AdamState* adam;
+  size_t count;
+  bool* set;
+};
+
+StageBuf stage_buf(fm_problem* pr, fm_stage st) {
+  if (st == FM_STAGE_ROTATION) return {pr->rot_params, &pr->rot_adam, 6 * (size_t)pr->N, &pr->rot_params_set};
+  if (st == FM_STAGE_TRANSLATION)
+    return {pr->trn_params, &pr->trn_adam, 3 * (size_t)pr->N * pr->trn_runs, &pr->trn_params_set};
+  return {pr->ea_params, &pr->ea_adam, 9 * (size_t)pr->N, &pr->ea_params_set};
+}
+
+bool valid_stage(int st) { return st >= FM_STAGE_ROTATION && st <= FM_STAGE_EPIPOLAR; }
+
+fm_status ensure_targets(fm_problem* pr) {
+  if (pr->trn_target_valid) return FM_OK;
+  if (!pr->rot_params_set) return fail(pr, FM_ERR_STATE, "translation stage needs rotation-stage parameters (fm_set_params(FM_STAGE_ROTATION))");
+  if (!pr->rel_t_set) return fail(pr, FM_ERR_STATE, "translation stage needs relative translations (rel_t)");
+  {
+    Timed t(pr, fm::kKTrnTargets);
+    fm::launch_trn_targets(pr->rot_params, pr->pair_j, pr->rel_t, pr->P, pr->trn_target, pr->stream);
+  }
+  FM_LAUNCHED(pr);
+  pr->trn_target_valid = true;
+  return FM_OK;
+}
+
+// One evaluation of a stage: per-image-pair pass, then the per-camera pass
+// (Adam when adam != null, else the gradient into grad_dev); the loss of every
+// run is reduced into loss_a and loss_b when they are not null.
+fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad_dev,
+                   const fm_adam_opts* adam, fm::AdamState* state, float* loss_a,
+                   float* loss_b = nullptr) {
+  cudaStream_t s = pr->stream;
+  const int P = pr->P, N = pr->N;
+  int runs = 1;
+  int* step = adam ? state->t : nullptr;
+  if (st == FM_STAGE_EPIPOLAR && pr->ea_loss == FM_EA_COMPACT) {
+    if (!pr->W_valid) return fail(pr, FM_ERR_STATE, "the compact loss needs W (fm_ea_set_weights or fm_ea_reweight)");
+    {
+      Timed t(pr, fm::kKEaCompact);
+      fm::launch_ea_compact(pr, params, pr->ea_inv_z, step, s);
+    }
+    FM_LAUNCHED(pr);
+  } else if (st == FM_STAGE_EPIPOLAR) {
+    {
+      Timed t(pr, fm::kKEaTables);
+      fm::launch_ea_tables(params, pr->pair_i, pr->pair_j, pr->seg_off, P, pr->seg_tab, step, s);
+    }
+    FM_LAUNCHED(pr);
+    if (pr->n_wruns > 0) {
+      Timed t(pr, fm::kKEaDirect);
+      fm::launch_ea_direct(pr, pr->ea_w, pr->ea_loss, s);
+    }
+    FM_LAUNCHED(pr);
+    {
+      Timed t(pr, fm::kKEaSegments);
+      fm::launch_ea_segments(pr, params, pr->ea_loss, pr->ea_inv_z, s);
+    }
+    FM_LAUNCHED(pr);
+  } else if (st == FM_STAGE_ROTATION) {
+    if (!pr->rel_R_set) return fail(pr, FM_ERR_STATE, "rotation stage needs relative rotations (rel_R)");
+    {
+      Timed t(pr, fm::kKRotPairs);
+      fm::launch_rot_pairs(params, pr->pair_i, pr->pair_j, pr->rel_R, P, pr->seg_grad, pr->seg_loss, step, s);
+    }
+    FM_LAUNCHED(pr);
+  } else {
+    fm_status e = ensure_targets(pr);
+    if (e != FM_OK) return e;
+    runs = pr->trn_runs;
+    {
+      Timed t(pr, fm::kKTrnPairs);
+      fm::launch_trn_pairs(params, pr->pair_i, pr->pair_j, pr->trn_target, N, P, runs, pr->seg_grad,
+                           pr->seg_loss, step, s);
+    }
+    FM_LAUNCHED(pr);
+  }
+  for (float* dst : {loss_a, loss_b}) {
+    if (!dst) continue;
+    Timed t(pr, fm::kKLossSum);
+    fm::launch_sum_fixed(pr->seg_loss, P, runs, dst, s);
+  }
+  FM_LAUNCHED(pr);
+  if (adam || grad_dev) {
+    fm::CamUpdate u;
+    u.cam_seg_off = pr->cam_seg_off;
+    u.cam_seg = pr->cam_seg;
+    u.seg_grad = pr->seg_grad;
+    u.params = params;
+    u.params_out = adam ? const_cast<float*>(params) : nullptr;
+    u.grad_out = grad_dev;
+    u.m = state ? state->m : nullptr;
+    u.v = state ? state->v : nullptr;
+    u.step = step;
+    u.lr = adam ? adam->lr : 0.f;
+    u.b1 = adam ? adam->beta1 : 0.f;
+    u.b2 = adam ? adam->beta2 : 0.f;
+    u.eps = adam ? adam->eps : 0.f;
+    u.N = N;
+    u.P = P;
+    u.runs = runs;
+    {
+      Timed t(pr, fm::kKCamUpdate);
+      fm::launch_cam_update((int)st, u, s);
+    }
+    FM_LAUNCHED(pr);
+  }
+  return FM_OK;
+}
+
+fm_status resize_runs(fm_problem* pr, int runs) {
+  if (runs == pr->trn_runs) return FM_OK;
+  const size_t n = 3 * (size_t)pr->N * runs;
+  dfree(pr->trn_params);
+  dfree(pr->trn_adam.m);
+  dfree(pr->trn_adam.v);
+  dfree(pr->seg_grad);
+  dfree(pr->seg_loss);
+  dfree(pr->scratch_params);
+  dfree(pr->scratch_grad);
+  dfree(pr->d_loss);
+  if (pr->h_loss) cudaFreeHost(pr->h_loss);
+  pr->h_loss = nullptr;
+  FM_ALLOC(pr, pr->trn_params, n);
+  FM_ALLOC(pr, pr->trn_adam.m, n);
+  FM_ALLOC(pr, pr->trn_adam.v, n);
+  const size_t sg = std::max((size_t)fm::kSegGradEa * pr->P, (size_t)fm::kSegGradTrn * pr->P * runs);
+  FM_ALLOC(pr, pr->seg_grad, sg);
+  FM_ALLOC(pr, pr->seg_loss, (size_t)pr->P * runs);
+  const size_t sp = std::max((size_t)9 * pr->N, n);
+  FM_ALLOC(pr, pr->scratch_params, sp);
+  FM_ALLOC(pr, pr->scratch_grad, sp);
+  FM_ALLOC(pr, pr->d_loss, runs);
+  FM_CUDA(pr, cudaMallocHost((void**)&pr->h_loss, sizeof(float) * runs));
+  pr->trn_runs = runs;
+  pr->trn_params_set = false;
+  return FM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fm_status fm_problem_create(const fm_problem_desc* d, fm_problem** out) {
+  if (!out) return fail(nullptr, FM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(nullptr, FM_ERR_INVALID_ARG, "desc is NULL");
+  if (d->n_cams < 2) return fail(nullptr, FM_ERR_INVALID_ARG, "n_cams must be >= 2");
+  if (d->n_img_pairs < 1) return fail(nullptr, FM_ERR_INVALID_ARG, "n_img_pairs must be >= 1");
+  if (d->n_kp_pairs < 0 || d->n_kp_pairs >= (int64_t(1) << 31) - (int64_t(1) << 20))
+    return fail(nullptr, FM_ERR_INVALID_ARG, "n_kp_pairs must be in [0, 2^31 - 2^20)");
+  if (!d->pair_cam_i || !d->pair_cam_j || !d->focal || !d->cx || !d->cy)
+    return fail(nullptr, FM_ERR_INVALID_ARG, "pair_cam_i, pair_cam_j, focal, cx and cy are required");
+  if (d->n_kp_pairs > 0 && (!d->kp1_px || !d->kp2_px || !d->kp_img_pair))
+    return fail(nullptr, FM_ERR_INVALID_ARG, "kp1_px, kp2_px and kp_img_pair are required when n_kp_pairs > 0");
+  fm_problem* pr = new (std::nothrow) fm_problem();
+  if (!pr) return fail(nullptr, FM_ERR_OOM, "host allocation failed");
+  pr->N = d->n_cams;
+  pr->P = d->n_img_pairs;
+  pr->Z = d->n_kp_pairs;
+  pr->stream = (cudaStream_t)d->cuda_stream;
+  cudaError_t e = cudaGetDevice(&pr->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&pr->sm_count, cudaDevAttrMultiProcessorCount, pr->device);
+  if (e != cudaSuccess) {
+    std::string msg = std::string("no usable CUDA device: ") + cudaGetErrorString(e);
+    delete pr;
+    return fail(nullptr, FM_ERR_CUDA, msg);
+  }
+  fm_status st = build(pr, d);
+  if (st != FM_OK) {
+    g_create_error = pr->last_error;
+    release(pr);
+    delete pr;
+    return st;
+  }
+  *out = pr;
+  return FM_OK;
+}
+
+void fm_problem_destroy(fm_problem* pr) {
+  if (!pr) return;
+  release(pr);
+  delete pr;
+}
+
+const char* fm_last_error(const fm_problem* pr) {
+  return pr ? pr->last_error.c_str() : g_create_error.c_str();
+}
+
+fm_status fm_problem_info_get(const fm_problem* pr, fm_problem_info* out) {
+  if (!pr || !out) return FM_ERR_INVALID_ARG;
+  out->n_cams = pr->N;
+  out->n_img_pairs = pr->P;
+  out->n_kp_pairs = pr->Z;
+  out->n_empty_img_pairs = pr->n_empty;
+  out->pairs_per_lane = fm::kEaPairsPerLane;
+  out->n_records = pr->n_rec;
+  out->device_bytes = pr->device_bytes;
+  return FM_OK;
+}
+
+fm_status fm_set_params(fm_problem* pr, fm_stage st, const float* params, int32_t on_device) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!valid_stage(st)) return fail(pr, FM_ERR_INVALID_ARG, "unknown stage");
+  if (!params) return fail(pr, FM_ERR_INVALID_ARG, "params is NULL");
+  StageBuf b = stage_buf(pr, st);
+  FM_CUDA(pr, cudaMemcpyAsync(b.params, params, sizeof(float) * b.count,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, pr->stream));
+  fm::launch_check_finite(b.params, (int64_t)b.count, pr->d_err, fm::kErrParamNonFinite, pr->stream);
+  FM_LAUNCHED(pr);
+  fm_status e = check_err_bits(pr);
+  if (e != FM_OK) return e;
+  e = reset_adam(pr, *b.adam, b.count);
+  if (e != FM_OK) return e;
+  *b.set = true;
+  if (st == FM_STAGE_ROTATION) pr->trn_target_valid = false;
+  return FM_OK;
+}
+
+fm_status fm_get_params(const fm_problem* cpr, fm_stage st, float* out, int32_t on_device) {
+  fm_problem* pr = const_cast<fm_problem*>(cpr);
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!valid_stage(st)) return fail(pr, FM_ERR_INVALID_ARG, "unknown stage");
+  if (!out) return fail(pr, FM_ERR_INVALID_ARG, "params_out is NULL");
+  StageBuf b = stage_buf(pr, st);
+  if (!*b.set) return fail(pr, FM_ERR_STATE, "the stage's parameters have not been set");
+  FM_CUDA(pr, cudaMemcpyAsync(out, b.params, sizeof(float) * b.count,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, pr->stream));
+  if (!on_device) FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+  return FM_OK;
+}
+
+fm_status fm_set_rel_poses(fm_problem* pr, const float* rel_R, const float* rel_t, int32_t on_device) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (rel_R) {
+    FM_CUDA(pr, cudaMemcpyAsync(pr->rel_R, rel_R, sizeof(float) * 9 * pr->P, k, pr->stream));
+    pr->rel_R_set = true;
+  }
+  if (rel_t) {
+    FM_CUDA(pr, cudaMemcpyAsync(pr->rel_t, rel_t, sizeof(float) * 3 * pr->P, k, pr->stream));
+    pr->rel_t_set = true;
+    pr->trn_target_valid = false;
+  }
+  return FM_OK;
+}
+
+fm_status fm_translation_set_runs(fm_problem* pr, int32_t n_runs) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (n_runs < 1 || n_runs > 64) return fail(pr, FM_ERR_INVALID_ARG, "n_runs must be in [1, 64]");
+  FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+  return resize_runs(pr, n_runs);
+}
+
+fm_status fm_ea_set_loss(fm_problem* pr, fm_ea_loss loss) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (loss != FM_EA_L1 && loss != FM_EA_L2 && loss != FM_EA_COMPACT)
+    return fail(pr, FM_ERR_INVALID_ARG, "unknown epipolar loss");
+  pr->ea_loss = loss;
+  return FM_OK;
+}
+
+// W_n together with its expansion around the essential matrices e0 of the
+// current epipolar-stage parameters (see fm_irls.cu)
+fm_status rebuild_W(fm_problem* pr) {
+  if (!pr->ea_params_set) return fail(pr, FM_ERR_STATE, "set the epipolar-stage parameters before the weights");
+  {
+    Timed t(pr, fm::kKEaTables);
+    fm::launch_ea_tables(pr->ea_params, pr->pair_i, pr->pair_j, pr->seg_off, pr->P, pr->seg_tab, nullptr,
+                         pr->stream);
+  }
+  FM_LAUNCHED(pr);
+  {
+    Timed t(pr, fm::kKWBuild);
+    fm::launch_w_build(pr, pr->ea_w, pr->W, pr->stream);
+  }
+  FM_LAUNCHED(pr);
+  pr->W_valid = true;
+  return FM_OK;
+}
+
+fm_status fm_ea_set_weights(fm_problem* pr, const float* w, int32_t on_device, float inv_z) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!w) {
+    dfree(pr->ea_w);
+    pr->ea_inv_z = pr->Z > 0 ? (float)(1.0 / (double)pr->Z) : 0.f;
+    return rebuild_W(pr);
+  }
+  if (!(std::isfinite(inv_z) && inv_z >= 0.f)) return fail(pr, FM_ERR_INVALID_ARG, "inv_z must be finite and >= 0");
+  if (!pr->ea_w) FM_ALLOC(pr, pr->ea_w, (size_t)pr->Z);
+  if (pr->Z > 0) {
+    FM_CUDA(pr, cudaMemcpyAsync(pr->ea_w, w, sizeof(float) * pr->Z,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, pr->stream));
+    fm::launch_check_finite(pr->ea_w, pr->Z, pr->d_err, fm::kErrParamNonFinite, pr->stream);
+    FM_LAUNCHED(pr);
+    fm_status e = check_err_bits(pr);
+    if (e != FM_OK) return e;
+  }
+  pr->ea_inv_z = inv_z;
+  return rebuild_W(pr);
+}
+
+fm_status fm_ea_reweight(fm_problem* pr, float tau, float delta, int32_t irls, int64_t* n_kept) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!(tau > 0.f) || !(delta > 0.f) || !std::isfinite(delta))
+    return fail(pr, FM_ERR_INVALID_ARG, "tau > 0 and finite delta > 0 required");
+  if (!pr->ea_params_set) return fail(pr, FM_ERR_STATE, "the epipolar-stage parameters have not been set");
+  cudaStream_t s = pr->stream;
+  if (!pr->ea_w) FM_ALLOC(pr, pr->ea_w, (size_t)pr->Z);
+  {
+    Timed t(pr, fm::kKEaTables);
+    fm::launch_ea_tables(pr->ea_params, pr->pair_i, pr->pair_j, pr->seg_off, pr->P, pr->seg_tab, nullptr, s);
+  }
+  FM_LAUNCHED(pr);
+  FM_CUDA(pr, cudaMemsetAsync(pr->d_kept, 0, sizeof(unsigned long long), s));
+  {
+    Timed t(pr, fm::kKEaReweight);
+    fm::launch_ea_reweight(pr, tau, delta, irls, pr->ea_w, pr->d_kept, s);
+  }
+  FM_LAUNCHED(pr);
+  fm_status e = rebuild_W(pr);
+  if (e != FM_OK) return e;
+  unsigned long long kept = 0;
+  FM_CUDA(pr, cudaMemcpyAsync(&kept, pr->d_kept, sizeof(kept), cudaMemcpyDeviceToHost, s));
+  FM_CUDA(pr, cudaStreamSynchronize(s));
+  pr->ea_inv_z = kept > 0 ? (float)(1.0 / (double)kept) : 0.f;
+  if (n_kept) *n_kept = (int64_t)kept;
+  return FM_OK;
+}
+
+fm_status fm_ea_get_weights(fm_problem* pr, float* out, int32_t on_device, float* inv_z) {
+  if (!pr || !out) return FM_ERR_INVALID_ARG;
+  if (!pr->ea_w) return fail(pr, FM_ERR_STATE, "no per-pair weights are set");
+  if (pr->Z > 0)
+    FM_CUDA(pr, cudaMemcpyAsync(out, pr->ea_w, sizeof(float) * pr->Z,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, pr->stream));
+  FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+  if (inv_z) *inv_z = pr->ea_inv_z;
+  return FM_OK;
+}
+
+fm_status fm_loss_grad(fm_problem* pr, fm_stage st, const float* params, float* loss, float* grad,
+                       int32_t mem_on_device) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!valid_stage(st)) return fail(pr, FM_ERR_INVALID_ARG, "unknown stage");
+  if (!params) return fail(pr, FM_ERR_INVALID_ARG, "params is NULL");
+  cudaStream_t s = pr->stream;
+  const size_t count = (size_t)stage_dim(st) * pr->N * (st == FM_STAGE_TRANSLATION ? pr->trn_runs : 1);
+  const float* p = params;
+  if (!mem_on_device) {
+    FM_CUDA(pr, cudaMemcpyAsync(pr->scratch_params, params, sizeof(float) * count, cudaMemcpyHostToDevice, s));
+    p = pr->scratch_params;
+  }
+  float* g = nullptr;
+  if (grad) g = mem_on_device ? grad : pr->scratch_grad;
+  fm_status e = evaluate(pr, st, p, g, nullptr, nullptr, loss ? pr->d_loss : nullptr);
+  if (e != FM_OK) return e;
+  const int runs = (st == FM_STAGE_TRANSLATION) ? pr->trn_runs : 1;
+  if (grad && !mem_on_device)
+    FM_CUDA(pr, cudaMemcpyAsync(grad, g, sizeof(float) * count, cudaMemcpyDeviceToHost, s));
+  if (loss) FM_CUDA(pr, cudaMemcpyAsync(pr->h_loss, pr->d_loss, sizeof(float) * runs, cudaMemcpyDeviceToHost, s));
+  if (loss || (grad && !mem_on_device)) {
+    FM_CUDA(pr, cudaStreamSynchronize(s));
+    if (loss) std::memcpy(loss, pr->h_loss, sizeof(float) * runs);
+  }
+  return FM_OK;
+}
+
+fm_status fm_step(fm_problem* pr, fm_stage st, const fm_adam_opts* opts, int32_t n_iters, float* loss) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!valid_stage(st)) return fail(pr, FM_ERR_INVALID_ARG, "unknown stage");
+  if (!opts) return fail(pr, FM_ERR_INVALID_ARG, "opts is NULL");
+  if (!(opts->lr > 0.f && opts->beta1 >= 0.f && opts->beta1 < 1.f && opts->beta2 >= 0.f &&
+        opts->beta2 < 1.f && opts->eps >= 0.f))
+    return fail(pr, FM_ERR_INVALID_ARG, "invalid Adam options");
+  if (n_iters < 0) return fail(pr, FM_ERR_INVALID_ARG, "n_iters must be >= 0");
+  StageBuf b = stage_buf(pr, st);
+  if (!*b.set) return fail(pr, FM_ERR_STATE, "the stage's parameters have not been set");
+  const int runs = (st == FM_STAGE_TRANSLATION) ? pr->trn_runs : 1;
+  for (int it = 0; it < n_iters; ++it) {
+    const bool last = (it == n_iters - 1);
+    float* trace = nullptr;
+    if (pr->loss_every > 0) {
+      if (pr->iter_count % pr->loss_every == 0) {
+        trace = pr->loss_hist + (size_t)(pr->loss_count % pr->loss_cap) * 64;
+        pr->loss_count += 1;
+      }
+      pr->iter_count += 1;
+    }
+    fm_status e = evaluate(pr, st, b.params, nullptr, opts, b.adam, (last && loss) ? pr->d_loss : nullptr,
+                           trace);
+    if (e != FM_OK) return e;
+  }
+  if (st == FM_STAGE_ROTATION && n_iters > 0) pr->trn_target_valid = false;
+  if (loss && n_iters > 0) {
+    FM_CUDA(pr, cudaMemcpyAsync(pr->h_loss, pr->d_loss, sizeof(float) * runs, cudaMemcpyDeviceToHost, pr->stream));
+    FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+    std::memcpy(loss, pr->h_loss, sizeof(float) * runs);
+  }
+  return FM_OK;
+}
+
+fm_status fm_timing_enable(fm_problem* pr, int32_t enable) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  drain_timing(pr, false);
+  for (int k = 0; k < fm::kKCount; ++k) {
+    pr->k_ms[k] = 0.0;
+    pr->k_launches[k] = 0;
+  }
+  pr->timing = enable != 0;
+  return FM_OK;
+}
+
+fm_status fm_timing_read(fm_problem* pr, fm_kernel_time* out, int32_t capacity, int32_t* count) {
+  if (!pr || !count || (capacity > 0 && !out)) return FM_ERR_INVALID_ARG;
+  drain_timing(pr, true);
+  FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+  int n = 0;
+  for (int k = 0; k < fm::kKCount; ++k) {
+    if (pr->k_launches[k] == 0) continue;
+    if (n < capacity) {
+      std::memset(out[n].name, 0, sizeof(out[n].name));
+      std::strncpy(out[n].name, fm::kKernelNames[k], sizeof(out[n].name) - 1);
+      out[n].launches = pr->k_launches[k];
+      out[n].total_ms = pr->timing ? pr->k_ms[k] : 0.0;
+    }
+    ++n;
+  }
+  *count = n;
+  return FM_OK;
+}
+
+fm_status fm_track_loss(fm_problem* pr, int32_t every, int32_t capacity) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (every < 0 || (every > 0 && capacity < 1)) return fail(pr, FM_ERR_INVALID_ARG, "every >= 0 and capacity >= 1 required");
+  FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+  dfree(pr->loss_hist);
+  pr->loss_every = 0;
+  pr->loss_cap = 0;
+  pr->loss_count = 0;
+  pr->iter_count = 0;
+  if (every == 0) return FM_OK;
+  FM_ALLOC(pr, pr->loss_hist, (size_t)capacity * 64);
+  pr->loss_every = every;
+  pr->loss_cap = capacity;
+  return FM_OK;
+}
+
+fm_status fm_loss_history(fm_problem* pr, float* out, int32_t capacity, int32_t* count) {
+  if (!pr || !count || (capacity > 0 && !out)) return FM_ERR_INVALID_ARG;
+  if (pr->loss_every == 0) {
+    *count = 0;
+    return FM_OK;
+  }
+  const int64_t have = std::min<int64_t>(pr->loss_count, pr->loss_cap);
+  const int64_t n = std::min<int64_t>(have, capacity);
+  std::vector<float> ring((size_t)pr->loss_cap * 64);
+  FM_CUDA(pr, cudaMemcpyAsync(ring.data(), pr->loss_hist, sizeof(float) * ring.size(),
+                              cudaMemcpyDeviceToHost, pr->stream));
+  FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+  for (int64_t k = 0; k < n; ++k) {
+    const int64_t idx = pr->loss_count - n + k;
+    out[k] = ring[(size_t)(idx % pr->loss_cap) * 64];   // run 0 of the translation stage
+  }
+  *count = (int32_t)n;
+  return FM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+// Per-camera assembly and optimiser step: a camera's gradient is the sum,
+// over the image pairs it belongs to (camera CSR, fixed order), of the
+// per-image-pair gradients; rotations then go through the adjoint of the 6D
+// map (Sec. 3.3), and Adam updates the camera's parameters in place.
+// One warp per camera; lanes stride over the incident image pairs and a
+// butterfly reduction combines them, so the order of additions is fixed.
+#include "fm_device.cuh"
+#include "fm_internal.h"
+
+namespace fm {
+namespace {
+
+// STAGE 0 rotation (part 9: dR, params 6D), 1 translation (part 3: do,
+// params o), 2 epipolar (part 12: dR, dt; params 6D + t)
+template <int STAGE>
+struct Layout;
+template <> struct Layout<0> { static constexpr int PART = 9, PDIM = 6; static constexpr bool ROT = true; };
+template <> struct Layout<1> { static constexpr int PART = 3, PDIM = 3; static constexpr bool ROT = false; };
+template <> struct Layout<2> { static constexpr int PART = 12, PDIM = 9; static constexpr bool ROT = true; };
+
+constexpr int kCamWarps = 4;
+
+template <int STAGE, bool ADAM>
+__global__ void __launch_bounds__(kCamWarps * 32) k_cam(CamUpdate u) {
+  using L = Layout<STAGE>;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kCamWarps + (threadIdx.x >> 5);
+  const int run = blockIdx.y;
+  if (c >= u.N) return;
+  const float* prm = u.params + ((size_t)run * u.N + c) * L::PDIM;
+  float p[L::PDIM];
+#pragma unroll
+  for (int k = 0; k < L::PDIM; ++k) p[k] = prm[k];
+  float acc[L::PART];
+#pragma unroll
+  for (int k = 0; k < L::PART; ++k) acc[k] = 0.f;
+  const int b = u.cam_seg_off[c], e = u.cam_seg_off[c + 1];
+  const float* sg = u.seg_grad + (size_t)run * u.P * 2 * L::PART;
+  for (int idx = b + lane; idx < e; idx += 32) {
+    const unsigned v = (unsigned)u.cam_seg[idx];
+    const int n = (int)(v & 0x7fffffffu);
+    const int role = (int)(v >> 31);
+    const float* g = sg + ((size_t)n * 2 + role) * L::PART;
+#pragma unroll
+    for (int k = 0; k < L::PART; ++k) acc[k] += g[k];
+  }
+#pragma unroll
+  for (int k = 0; k < L::PART; ++k) acc[k] = warp_sum(acc[k]);
+  float g[L::PDIM];
+  if (L::ROT) {
+    Rot6 s;
+    rot6_forward(p, s);
+    rot6_adjoint(p, s, acc, g);
+    if (STAGE == 2) {
+      g[6] = acc[9];
+      g[7] = acc[10];
+      g[8] = acc[11];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < L::PDIM; ++k) g[k] = acc[k];
+  }
+  __syncwarp();
+  const size_t off = ((size_t)run * u.N + c) * L::PDIM;
+  if (!ADAM) {
+    if (lane < L::PDIM) {
+      float gv = g[0];
+#pragma unroll
+      for (int k = 1; k < L::PDIM; ++k)
+        if (lane == k) gv = g[k];
+      u.grad_out[off + lane] = gv;
+    }
+    return;
+  }
+  if (lane < L::PDIM) {
+    float gv = g[0], pv = p[0];
+#pragma unroll
+    for (int k = 1; k < L::PDIM; ++k)
+      if (lane == k) { gv = g[k]; pv = p[k]; }
+    if (u.grad_out) u.grad_out[off + lane] = gv;
+    const float t = (float)(*u.step);
+    const float bc1 = 1.f - powf(u.b1, t);
+    const float bc2 = 1.f - powf(u.b2, t);
+    float m = u.m[off + lane], v = u.v[off + lane];
+    m = u.b1 * m + (1.f - u.b1) * gv;
+    v = u.b2 * v + (1.f - u.b2) * gv * gv;
+    u.m[off + lane] = m;
+    u.v[off + lane] = v;
+    u.params_out[off + lane] = pv - u.lr * (m / bc1) / (sqrtf(v / bc2) + u.eps);
+  }
+}
+
+// fixed-order sum of n values per run (one CTA per run)
+__global__ void k_sum_fixed(const float* __restrict__ x, int n, float* __restrict__ out) {
+  __shared__ float part[1024];
+  const float* xr = x + (size_t)blockIdx.x * n;
+  float s = 0.f;
+  for (int k = threadIdx.x; k < n; k += 1024) s += xr[k];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int d = 512; d > 0; d >>= 1) {
+    if ((int)threadIdx.x < d) part[threadIdx.x] += part[threadIdx.x + d];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = part[0];
+}
+
+template <int STAGE>
+void launch_stage(const CamUpdate& u, cudaStream_t s) {
+  dim3 grid((u.N + kCamWarps - 1) / kCamWarps, u.runs);
+  if (u.params_out) k_cam<STAGE, true><<<grid, kCamWarps * 32, 0, s>>>(u);
+  else k_cam<STAGE, false><<<grid, kCamWarps * 32, 0, s>>>(u);
+}
+
+}  // namespace
+
+void launch_cam_update(int stage, const CamUpdate& u, cudaStream_t s) {
+  if (stage == FM_STAGE_ROTATION) launch_stage<0>(u, s);
+  else if (stage == FM_STAGE_TRANSLATION) launch_stage<1>(u, s);
+  else launch_stage<2>(u, s);
+}
+
+void launch_sum_fixed(const float* x, int n, int runs, float* out, cudaStream_t s) {
+  k_sum_fixed<<<runs, 1024, 0, s>>>(x, n, out);
+}
+
+}  // namespace fm

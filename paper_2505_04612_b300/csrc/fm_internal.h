@@ -1,0 +1,192 @@
+// Internal declarations shared by the host runtime and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fastmap.h"
+
+namespace fm {
+
+// ---------------------------------------------------------------- constants
+constexpr int kEaPairsPerLane = 15;              // U: keypoint pairs per lane (odd)
+constexpr int kEaWarpPairs = 32 * kEaPairsPerLane;  // keypoint pairs per warp run
+constexpr int kEaSegCap = 32;                    // image pairs per warp run staged in smem
+constexpr int kEaWarpsPerCta = 4;
+constexpr int kSegGradEa = 24;                   // dR_i, dt_i, dR_j, dt_j
+constexpr int kSegGradRot = 18;                  // dR_i, dR_j
+constexpr int kSegGradTrn = 6;                   // do_i, do_j
+
+// error bits raised by device-side validation
+enum : int {
+  kErrKpOrder = 1,       // kp_img_pair decreasing
+  kErrKpRange = 2,       // kp_img_pair outside [0, P)
+  kErrKpNonFinite = 4,   // keypoint not finite
+  kErrParamNonFinite = 8,
+};
+
+enum KernelId : int {
+  kKCalibrate = 0, kKSegOffsets, kKRunTables, kKEaTables, kKEaDirect, kKEaSegments,
+  kKRotPairs, kKTrnTargets, kKTrnPairs, kKCamUpdate, kKLossSum, kKEaReweight, kKWBuild,
+  kKEaCompact, kKCount
+};
+extern const char* const kKernelNames[kKCount];
+
+struct PendingTiming {
+  int kid;
+  cudaEvent_t start, stop;
+};
+
+struct AdamState {
+  float* m = nullptr;
+  float* v = nullptr;
+  int* t = nullptr;      // device step counter (incremented on the device)
+};
+
+}  // namespace fm
+
+struct fm_problem {
+  int N = 0, P = 0;
+  int64_t Z = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sm_count = 0;
+  std::string last_error;
+  int64_t device_bytes = 0;
+
+  // image-pair graph
+  int* pair_i = nullptr;         // [P]
+  int* pair_j = nullptr;         // [P]
+  int* seg_off = nullptr;        // [P+1] keypoint-pair offsets of each image pair
+  int* cam_seg_off = nullptr;    // [N+1]
+  int* cam_seg = nullptr;        // [2P] image pair | role << 31 (role 1: camera is j)
+  int n_empty = 0;
+
+  // keypoints
+  float4* kp = nullptr;          // [Z] calibrated (x1, y1, x2, y2)
+  int* kp_track = nullptr;       // [Z] or null
+  float* focal = nullptr;
+  float* cx = nullptr;
+  float* cy = nullptr;
+
+  // direct epipolar kernel tables
+  int n_wruns = 0;               // warp runs of kEaWarpPairs keypoint pairs
+  int* run_seg = nullptr;        // [n_wruns*32] image pair of each lane's first pair
+  int4* wrun_info = nullptr;     // [n_wruns] {first image pair, #image pairs, record base, 0}
+  int* seg_rec = nullptr;        // [2P] {first record, #records} per image pair
+  int64_t n_rec = 0;
+  float4* rec = nullptr;         // [n_rec*3] per-(warp run, image pair) partial sums
+  float4* seg_tab = nullptr;     // [P*3] E (9) + end offset per image pair
+
+  // per image pair outputs of the segment pass
+  float* seg_grad = nullptr;     // [max(m,1)*P*24]
+  float* seg_loss = nullptr;     // [max(m,1)*P]
+
+  // epipolar stage
+  int ea_loss = FM_EA_L1;
+  float* ea_w = nullptr;         // [Z] weights or null
+  float ea_inv_z = 0.f;
+  float* W = nullptr;            // [P*45] packed upper triangle of W_n (Eq. 17)
+  bool W_valid = false;
+  unsigned long long* d_kept = nullptr;
+  float* ea_params = nullptr;    // [N*9]
+  fm::AdamState ea_adam;
+  bool ea_params_set = false;
+
+  // rotation stage
+  float* rel_R = nullptr;        // [P*9]
+  float* rel_t = nullptr;        // [P*3]
+  bool rel_R_set = false;
+  bool rel_t_set = false;
+  float* rot_params = nullptr;   // [N*6]
+  fm::AdamState rot_adam;
+  bool rot_params_set = false;
+
+  // translation stage
+  int trn_runs = 1;
+  float* trn_target = nullptr;   // [P*3] o^{i->j}
+  bool trn_target_valid = false;
+  float* trn_params = nullptr;   // [m*N*3]
+  fm::AdamState trn_adam;
+  bool trn_params_set = false;
+
+  // observability
+  bool timing = false;
+  std::vector<fm::PendingTiming> pending;
+  std::vector<cudaEvent_t> event_pool;
+  int64_t k_launches[fm::kKCount] = {};
+  double k_ms[fm::kKCount] = {};
+  int loss_every = 0;
+  int loss_cap = 0;
+  int64_t loss_count = 0;     // traced values written so far
+  int64_t iter_count = 0;     // fm_step iterations while tracing
+  float* loss_hist = nullptr; // [loss_cap * max(m,1)]
+
+  // scratch
+  float* scratch_params = nullptr;  // [max(m,1)*N*9] parameters of fm_loss_grad
+  float* scratch_grad = nullptr;    // [max(m,1)*N*9]
+  float* d_loss = nullptr;          // [max(m,1)]
+  float* h_loss = nullptr;          // pinned [max(m,1)]
+  int* d_err = nullptr;             // device error bits
+};
+
+namespace fm {
+
+// ---------------------------------------------------------------- launchers
+// setup (fm_setup.cu)
+void launch_calibrate(const float* kp1, const float* kp2, const int* kp_pair, const int* pi,
+                      const int* pj, const float* f, const float* cx, const float* cy,
+                      int64_t Z, int P, float4* out, int* err, cudaStream_t s);
+void launch_seg_offsets(const int* kp_pair, int64_t Z, int P, int* seg_off, int* err,
+                        cudaStream_t s);
+void launch_run_tables(const int* seg_off, int P, int64_t Z, int n_wruns, int* run_seg,
+                       int4* wrun_info, int* counts_scratch, cudaStream_t s);
+void launch_seg_records(const int* seg_off, const int* run_seg, const int4* wrun_info, int P,
+                        int* seg_rec, cudaStream_t s);
+void launch_check_finite(const float* x, int64_t n, int* err, int bit, cudaStream_t s);
+void launch_exclusive_scan_info(int4* wrun_info, int n, int64_t* total_out_dev, cudaStream_t s);
+
+// epipolar (fm_ea.cu)
+void launch_ea_tables(const float* params, const int* pi, const int* pj, const int* seg_off,
+                      int P, float4* seg_tab, int* step_counter, cudaStream_t s);
+void launch_ea_direct(const fm_problem* pr, const float* weights, int loss, cudaStream_t s);
+void launch_ea_segments(const fm_problem* pr, const float* params, int loss, float inv_z,
+                        cudaStream_t s);
+
+// IRLS / compact form (fm_irls.cu)
+void launch_ea_reweight(const fm_problem* pr, float tau, float delta, int irls, float* w,
+                        unsigned long long* kept, cudaStream_t s);
+void launch_w_build(const fm_problem* pr, const float* w, float* W, cudaStream_t s);
+void launch_ea_compact(const fm_problem* pr, const float* params, float inv_z, int* step_counter,
+                       cudaStream_t s);
+
+// rotation / translation (fm_pose.cu)
+void launch_rot_pairs(const float* params, const int* pi, const int* pj, const float* rel_R,
+                      int P, float* seg_grad, float* seg_loss, int* step_counter,
+                      cudaStream_t s);
+void launch_trn_targets(const float* rot_params, const int* pj, const float* rel_t, int P,
+                        float* target, cudaStream_t s);
+void launch_trn_pairs(const float* o, const int* pi, const int* pj, const float* target, int N,
+                      int P, int runs, float* seg_grad, float* seg_loss, int* step_counter,
+                      cudaStream_t s);
+
+// per-camera reduction, 6D adjoint and Adam (fm_cam.cu)
+struct CamUpdate {
+  const int* cam_seg_off;
+  const int* cam_seg;
+  const float* seg_grad;   // [runs][P][2*part]
+  const float* params;     // [runs][N][pdim] parameters the gradient was taken at
+  float* params_out;       // Adam: updated in place (== params); else null
+  float* grad_out;         // gradient output or null
+  float* m;
+  float* v;
+  const int* step;
+  float lr, b1, b2, eps;
+  int N, P, runs;
+};
+void launch_cam_update(int stage, const CamUpdate& u, cudaStream_t s);
+void launch_sum_fixed(const float* x, int n, int runs, float* out, cudaStream_t s);
+
+}  // namespace fm

@@ -1,0 +1,196 @@
+// IRLS reweighting, outlier filtering and the compact quadratic form of the
+// epipolar objective (Sec. 3.3, Eqs. 8-9; Appendix "Epipolar Adjustment",
+// Eqs. 15-17).
+//
+//   k_ea_reweight  per keypoint pair: eps^ = x~2^T E_n x~1 at the current
+//                  poses; the pair is kept if |eps^| < tau (the periodic
+//                  filtering with a decreasing threshold) and weighted
+//                  1/max(|eps^|, delta) (IRLS), or 1 (mask only);
+//   k_w_build      per image pair: W_n = sum_m w_m vec(x~2 x~1^T) vec(...)^T,
+//                  the 45 unique entries of the symmetric 9x9 matrix, plus the
+//                  quadratic form's value and gradient at the reference
+//                  essential matrix e0 of the current poses:
+//                  b_n = W_n e0 = sum_m w_m r0_m v_m, c_n = e0^T W_n e0 = sum_m w_m r0_m^2
+//                  with r0_m = v_m . e0 the pair's residual, and e0 itself;
+//   k_ea_compact   per image pair: e = e0 + d, and
+//                      e^T W e = c + 2 d.b + d^T W d,   W e = b + W d,
+//                  loss inv_z e^T W e, dL/dE = 2 inv_z W e, then the chain rule
+//                  to the two cameras -- the per-iteration cost is independent
+//                  of the keypoint pairs.
+//
+// Why the centred form: near convergence e lies close to the null space of W,
+// so e^T W e (= sum w r^2, tiny) is a difference of terms of size |W| |e|^2.
+// Rounding W to float32 perturbs it by ~1e-7 |W| |e|^2, which can exceed the
+// value itself.  Expanding around e0 is an exact identity; b and c are sums of
+// the small, accurately computed residuals, and the only term that still sees
+// W's rounding is d^T W d with d = e - e0 small while the poses stay near the
+// ones of the last reweighting.
+#include "fm_device.cuh"
+#include "fm_internal.h"
+
+namespace fm {
+namespace {
+
+constexpr int U = kEaPairsPerLane;
+
+// one thread per lane run of U consecutive keypoint pairs (the runs of the
+// direct kernel); the run's first image pair comes from run_seg
+__global__ void k_ea_reweight(const float4* __restrict__ kp, const int* __restrict__ run_seg,
+                              const float4* __restrict__ seg_tab, int Z, int n_runs, float tau,
+                              float delta, int irls, float* __restrict__ w,
+                              unsigned long long* __restrict__ kept) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  int my_kept = 0;
+  if (q < n_runs) {
+    const int p0 = q * U;
+    const int pend = min(p0 + U, Z);
+    int s = run_seg[q];
+    float4 e0 = __ldg(seg_tab + 3 * s), e1 = __ldg(seg_tab + 3 * s + 1), e2 = __ldg(seg_tab + 3 * s + 2);
+    int end = __float_as_int(e2.y);
+    for (int p = p0; p < pend; ++p) {
+      while (p >= end) {
+        ++s;
+        e0 = __ldg(seg_tab + 3 * s);
+        e1 = __ldg(seg_tab + 3 * s + 1);
+        e2 = __ldg(seg_tab + 3 * s + 2);
+        end = __float_as_int(e2.y);
+      }
+      const float4 x = __ldg(kp + p);
+      const float ex = fmaf(e0.x, x.x, fmaf(e0.y, x.y, e0.z));
+      const float ey = fmaf(e0.w, x.x, fmaf(e1.x, x.y, e1.y));
+      const float ez = fmaf(e1.z, x.x, fmaf(e1.w, x.y, e2.x));
+      const float r = fabsf(fmaf(x.z, ex, fmaf(x.w, ey, ez)));
+      const bool keep = r < tau;
+      float wt = 0.f;
+      if (keep) wt = irls ? 1.f / fmaxf(r, delta) : 1.f;
+      w[p] = wt;
+      my_kept += keep;
+    }
+  }
+  // integer counts: the total does not depend on the order of the atomics
+  for (int d = 16; d > 0; d >>= 1) my_kept += __shfl_xor_sync(0xffffffffu, my_kept, d);
+  if ((threadIdx.x & 31) == 0 && my_kept) atomicAdd(kept, (unsigned long long)my_kept);
+}
+
+// one warp per image pair; lanes stride over its keypoint pairs, then a
+// butterfly reduction in fixed order.  Output per image pair (64 floats):
+// [0,45) W upper triangle, [45,54) b, [54] c, [55,64) e0.
+__global__ void __launch_bounds__(128) k_w_build(const float4* __restrict__ kp, const float* __restrict__ w,
+                                                 const int* __restrict__ seg_off,
+                                                 const float4* __restrict__ seg_tab, int P,
+                                                 float* __restrict__ W) {
+  const int lane = threadIdx.x & 31;
+  const int n = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (n >= P) return;
+  const float4 t0 = __ldg(seg_tab + 3 * n), t1 = __ldg(seg_tab + 3 * n + 1), t2 = __ldg(seg_tab + 3 * n + 2);
+  const float e0[9] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w, t2.x};
+  float acc[55];
+#pragma unroll
+  for (int k = 0; k < 55; ++k) acc[k] = 0.f;
+  const int b = seg_off[n], e = seg_off[n + 1];
+  for (int m = b + lane; m < e; m += 32) {
+    const float4 x = __ldg(kp + m);
+    const float wt = w ? __ldg(w + m) : 1.f;
+    // vec(x~2 x~1^T), row-major: (x2 x1, x2 y1, x2, y2 x1, y2 y1, y2, x1, y1, 1)
+    const float v[9] = {x.z * x.x, x.z * x.y, x.z, x.w * x.x, x.w * x.y, x.w, x.x, x.y, 1.f};
+    // the residual at e0, as the direct kernel forms it
+    const float ex = fmaf(e0[0], x.x, fmaf(e0[1], x.y, e0[2]));
+    const float ey = fmaf(e0[3], x.x, fmaf(e0[4], x.y, e0[5]));
+    const float ez = fmaf(e0[6], x.x, fmaf(e0[7], x.y, e0[8]));
+    const float r0 = fmaf(x.z, ex, fmaf(x.w, ey, ez));
+    int k = 0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const float wa = wt * v[a];
+#pragma unroll
+      for (int c = a; c < 9; ++c) {
+        acc[k] = fmaf(wa, v[c], acc[k]);
+        ++k;
+      }
+    }
+    const float wr = wt * r0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) acc[45 + a] = fmaf(wr, v[a], acc[45 + a]);
+    acc[54] = fmaf(wr, r0, acc[54]);
+  }
+#pragma unroll
+  for (int k = 0; k < 55; ++k) acc[k] = warp_sum(acc[k]);
+  float* out = W + (size_t)64 * n;
+  // lanes write in parallel: lane l writes entries l and l + 32
+  for (int k = lane; k < 64; k += 32) {
+    float v = 0.f;
+#pragma unroll
+    for (int j = 0; j < 55; ++j)
+      if (j == k) v = acc[j];
+    if (k >= 55) v = e0[k - 55];
+    out[k] = v;
+  }
+}
+
+__device__ __forceinline__ int tri(int a, int c) {   // index of (a, c), a <= c, in the packed upper triangle
+  return a * 9 - (a * (a - 1)) / 2 + (c - a);
+}
+
+template <bool STEP>
+__global__ void k_ea_compact(const float* __restrict__ W, const float* __restrict__ params,
+                             const int* __restrict__ pi, const int* __restrict__ pj, int P,
+                             float inv_z, float* __restrict__ seg_grad, float* __restrict__ seg_loss,
+                             int* step_counter) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (STEP && step_counter && n == 0) *step_counter += 1;
+  if (n >= P) return;
+  PairGeo g;
+  pair_geometry(params + 9 * pi[n], params + 9 * pj[n], g);
+  float e[9];
+  essential(g, e);
+  const float* Wn = W + (size_t)64 * n;
+  float d[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) d[a] = e[a] - Wn[55 + a];
+  float Wd[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) s = fmaf(Wn[a <= c ? tri(a, c) : tri(c, a)], d[c], s);
+    Wd[a] = s;
+  }
+  // e^T W e = c + 2 d.b + d^T W d ;  W e = b + W d
+  float q = 0.f, lb = 0.f;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    q = fmaf(d[a], Wd[a], q);
+    lb = fmaf(d[a], Wn[45 + a], lb);
+  }
+  seg_loss[n] = (Wn[54] + 2.f * lb + q) * inv_z;
+  float G[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) G[a] = 2.f * inv_z * (Wn[45 + a] + Wd[a]);
+  float o[kSegGradEa];
+  pair_backward(g, G, o);
+  float* out = seg_grad + (size_t)kSegGradEa * n;
+#pragma unroll
+  for (int k = 0; k < kSegGradEa; ++k) out[k] = o[k];
+}
+
+}  // namespace
+
+void launch_ea_reweight(const fm_problem* pr, float tau, float delta, int irls, float* w,
+                        unsigned long long* kept, cudaStream_t s) {
+  const int n_runs = (int)((pr->Z + U - 1) / U);
+  if (n_runs == 0) return;
+  k_ea_reweight<<<(n_runs + 255) / 256, 256, 0, s>>>(pr->kp, pr->run_seg, pr->seg_tab, (int)pr->Z,
+                                                     n_runs, tau, delta, irls, w, kept);
+}
+
+void launch_w_build(const fm_problem* pr, const float* w, float* W, cudaStream_t s) {
+  k_w_build<<<(pr->P + 3) / 4, 128, 0, s>>>(pr->kp, w, pr->seg_off, pr->seg_tab, pr->P, W);
+}
+
+void launch_ea_compact(const fm_problem* pr, const float* params, float inv_z, int* step_counter,
+                       cudaStream_t s) {
+  k_ea_compact<true><<<(pr->P + 127) / 128, 128, 0, s>>>(pr->W, params, pr->pair_i, pr->pair_j, pr->P,
+                                                         inv_z, pr->seg_grad, pr->seg_loss, step_counter);
+}
+
+}  // namespace fm

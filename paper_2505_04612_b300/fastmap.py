@@ -1,0 +1,457 @@
+"""ctypes binding of the C ABI in ``include/fastmap.h``.
+
+The functions below carry the C names and only marshal arguments: every
+computation runs in ``lib/libfastmap.so``.  Arrays may be torch tensors
+(CUDA tensors are passed as device pointers, CPU tensors and numpy arrays as
+host pointers).  If the library is missing, loading raises: there is no
+fallback implementation.
+
+``Problem`` is a small owner of one ``fm_problem`` handle built on these calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FM_OK = 0
+FM_ERR_INVALID_ARG = 1
+FM_ERR_CUDA = 2
+FM_ERR_OOM = 3
+FM_ERR_NAN = 4
+FM_ERR_TIMEOUT = 5
+FM_ERR_NOT_CONVERGED = 6
+FM_ERR_STATE = 7
+
+FM_STAGE_ROTATION = 0
+FM_STAGE_TRANSLATION = 1
+FM_STAGE_EPIPOLAR = 2
+STAGE_DIM = {FM_STAGE_ROTATION: 6, FM_STAGE_TRANSLATION: 3, FM_STAGE_EPIPOLAR: 9}
+
+FM_EA_L1 = 0
+FM_EA_L2 = 1
+FM_EA_COMPACT = 2
+
+_c_i32p = ctypes.POINTER(ctypes.c_int32)
+_c_f32p = ctypes.POINTER(ctypes.c_float)
+
+
+class fm_problem_desc(ctypes.Structure):
+    _fields_ = [
+        ("n_cams", ctypes.c_int32),
+        ("n_img_pairs", ctypes.c_int32),
+        ("n_kp_pairs", ctypes.c_int64),
+        ("pair_cam_i", ctypes.c_void_p),
+        ("pair_cam_j", ctypes.c_void_p),
+        ("kp_img_pair", ctypes.c_void_p),
+        ("kp1_px", ctypes.c_void_p),
+        ("kp2_px", ctypes.c_void_p),
+        ("kp_track", ctypes.c_void_p),
+        ("focal", ctypes.c_void_p),
+        ("cx", ctypes.c_void_p),
+        ("cy", ctypes.c_void_p),
+        ("rel_R", ctypes.c_void_p),
+        ("rel_t", ctypes.c_void_p),
+        ("inputs_on_device", ctypes.c_int32),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class fm_problem_info(ctypes.Structure):
+    _fields_ = [
+        ("n_cams", ctypes.c_int32),
+        ("n_img_pairs", ctypes.c_int32),
+        ("n_kp_pairs", ctypes.c_int64),
+        ("n_empty_img_pairs", ctypes.c_int32),
+        ("pairs_per_lane", ctypes.c_int32),
+        ("n_records", ctypes.c_int64),
+        ("device_bytes", ctypes.c_int64),
+    ]
+
+
+class fm_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+class fm_adam_opts(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
+# name -> (restype, argtypes); kept in the order of include/fastmap.h
+_SIGNATURES = {
+    "fm_problem_create": (ctypes.c_int, [ctypes.POINTER(fm_problem_desc), ctypes.POINTER(ctypes.c_void_p)]),
+    "fm_problem_destroy": (None, [ctypes.c_void_p]),
+    "fm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "fm_problem_info_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fm_problem_info)]),
+    "fm_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int32]),
+    "fm_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int32]),
+    "fm_set_rel_poses": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "fm_translation_set_runs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "fm_ea_set_loss": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "fm_ea_set_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_float]),
+    "fm_ea_reweight": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_int64)]),
+    "fm_ea_get_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_float)]),
+    "fm_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_int32]),
+    "fm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(fm_adam_opts), ctypes.c_int32,
+                               ctypes.c_void_p]),
+    "fm_timing_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "fm_timing_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fm_kernel_time), ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_int32)]),
+    "fm_track_loss": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
+    "fm_loss_history": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_int32)]),
+}
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads lib/libfastmap.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with `python -m paper_2505_04612_b300.build`")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+class FastMapError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"fastmap status {status}: {message}")
+        self.status = status
+
+
+def _check(status, handle=None):
+    if status != FM_OK:
+        msg = lib().fm_last_error(handle)
+        raise FastMapError(status, msg.decode() if msg else "")
+
+
+# ------------------------------------------------------------- marshalling
+
+def _ptr(x):
+    """(address, on_device, keepalive) of a torch tensor / numpy array / None."""
+    if x is None:
+        return None, False, None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if not x.is_contiguous():
+                x = x.contiguous()
+            return x.data_ptr(), bool(x.is_cuda), x
+    except ImportError:  # pragma: no cover
+        pass
+    a = np.ascontiguousarray(x)
+    return a.ctypes.data, False, a
+
+
+def _as(x, dtype):
+    """Convert to the given numpy dtype unless it is a tensor of the right dtype."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            want = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+            return x.to(want).contiguous()
+    except ImportError:  # pragma: no cover
+        pass
+    return np.ascontiguousarray(x, dtype=dtype)
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:  # pragma: no cover
+        pass
+    return None
+
+
+# ------------------------------------------------------------ C-named calls
+
+def fm_problem_create(desc: fm_problem_desc) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().fm_problem_create(ctypes.byref(desc), ctypes.byref(h)), None)
+    return h.value
+
+
+def fm_problem_destroy(handle):
+    lib().fm_problem_destroy(handle)
+
+
+def fm_last_error(handle=None) -> str:
+    return lib().fm_last_error(handle).decode()
+
+
+def fm_problem_info_get(handle) -> fm_problem_info:
+    info = fm_problem_info()
+    _check(lib().fm_problem_info_get(handle, ctypes.byref(info)), handle)
+    return info
+
+
+def fm_set_params(handle, stage, params):
+    p, dev, keep = _ptr(_as(params, np.float32))
+    _check(lib().fm_set_params(handle, stage, p, int(dev)), handle)
+
+
+def fm_get_params(handle, stage, out):
+    p, dev, keep = _ptr(out)
+    _check(lib().fm_get_params(handle, stage, p, int(dev)), handle)
+    return out
+
+
+def fm_set_rel_poses(handle, rel_R=None, rel_t=None):
+    rR = _as(rel_R, np.float32) if rel_R is not None else None
+    rt = _as(rel_t, np.float32) if rel_t is not None else None
+    pR, dR, kR = _ptr(rR)
+    pt, dt, kt = _ptr(rt)
+    if rR is not None and rt is not None and dR != dt:
+        raise ValueError("rel_R and rel_t must both be on the device or both on the host")
+    _check(lib().fm_set_rel_poses(handle, pR, pt, int(dR or dt)), handle)
+
+
+def fm_translation_set_runs(handle, n_runs):
+    _check(lib().fm_translation_set_runs(handle, int(n_runs)), handle)
+
+
+def fm_ea_set_loss(handle, loss):
+    _check(lib().fm_ea_set_loss(handle, int(loss)), handle)
+
+
+def fm_ea_set_weights(handle, weights, inv_z):
+    if weights is None:
+        _check(lib().fm_ea_set_weights(handle, None, 0, ctypes.c_float(0.0)), handle)
+        return
+    p, dev, keep = _ptr(_as(weights, np.float32))
+    _check(lib().fm_ea_set_weights(handle, p, int(dev), ctypes.c_float(inv_z)), handle)
+
+
+def fm_ea_reweight(handle, tau, delta, irls=True):
+    kept = ctypes.c_int64()
+    _check(lib().fm_ea_reweight(handle, ctypes.c_float(tau), ctypes.c_float(delta), int(bool(irls)),
+                                ctypes.byref(kept)), handle)
+    return kept.value
+
+
+def fm_ea_get_weights(handle, out):
+    p, dev, keep = _ptr(out)
+    inv_z = ctypes.c_float()
+    _check(lib().fm_ea_get_weights(handle, p, int(dev), ctypes.byref(inv_z)), handle)
+    return out, inv_z.value
+
+
+def fm_loss_grad(handle, stage, params, loss_out, grad_out, mem_on_device):
+    """Raw call: params / grad_out are addresses (int) or None, loss_out a
+    ctypes float array or None."""
+    _check(lib().fm_loss_grad(handle, stage, params, loss_out, grad_out, int(mem_on_device)), handle)
+
+
+def fm_step(handle, stage, opts: fm_adam_opts, n_iters, loss_out=None):
+    _check(lib().fm_step(handle, stage, ctypes.byref(opts), int(n_iters), loss_out), handle)
+
+
+def fm_timing_enable(handle, enable):
+    _check(lib().fm_timing_enable(handle, int(bool(enable))), handle)
+
+
+def fm_timing_read(handle):
+    """{kernel name: (launches, total device ms)} since timing was enabled."""
+    cap = 32
+    arr = (fm_kernel_time * cap)()
+    n = ctypes.c_int32()
+    _check(lib().fm_timing_read(handle, arr, cap, ctypes.byref(n)), handle)
+    return {arr[k].name.decode(): (int(arr[k].launches), float(arr[k].total_ms)) for k in range(min(n.value, cap))}
+
+
+def fm_track_loss(handle, every, capacity=4096):
+    _check(lib().fm_track_loss(handle, int(every), int(capacity)), handle)
+
+
+def fm_loss_history(handle, capacity=4096):
+    out = (ctypes.c_float * capacity)()
+    n = ctypes.c_int32()
+    _check(lib().fm_loss_history(handle, out, capacity, ctypes.byref(n)), handle)
+    return [out[k] for k in range(n.value)]
+
+
+# ------------------------------------------------------------ owner class
+
+class Problem:
+    """One fm_problem.  Inputs may be numpy arrays / CPU tensors (copied from
+    the host) or CUDA tensors (read on the device); all of them must be on the
+    same side."""
+
+    def __init__(self, pair_i, pair_j, kp_img_pair, kp1_px, kp2_px, focal, cx, cy,
+                 rel_R=None, rel_t=None, kp_track=None, stream=None):
+        arrs = dict(
+            pair_cam_i=_as(pair_i, np.int32), pair_cam_j=_as(pair_j, np.int32),
+            kp_img_pair=_as(kp_img_pair, np.int32),
+            kp1_px=_as(kp1_px, np.float32), kp2_px=_as(kp2_px, np.float32),
+            focal=_as(focal, np.float32), cx=_as(cx, np.float32), cy=_as(cy, np.float32),
+            rel_R=_as(rel_R, np.float32) if rel_R is not None else None,
+            rel_t=_as(rel_t, np.float32) if rel_t is not None else None,
+            kp_track=_as(kp_track, np.int32) if kp_track is not None else None,
+        )
+        d = fm_problem_desc()
+        d.n_cams = int(len(arrs["focal"]))
+        d.n_img_pairs = int(len(arrs["pair_cam_i"]))
+        d.n_kp_pairs = int(len(arrs["kp_img_pair"]))
+        self._keep = []
+        sides = set()
+        for k, v in arrs.items():
+            p, dev, keep = _ptr(v)
+            setattr(d, k, p)
+            if v is not None:
+                sides.add(dev)
+                self._keep.append(keep)
+        if len(sides) > 1:
+            raise ValueError("all inputs must be on the device or all on the host")
+        d.inputs_on_device = int(sides == {True})
+        d.cuda_stream = _stream_handle(stream)
+        self.n_cams, self.n_pairs, self.n_kp = d.n_cams, d.n_img_pairs, d.n_kp_pairs
+        self.handle = fm_problem_create(d)
+        self._keep = []
+        self.runs = 1
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fm_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def info(self):
+        return fm_problem_info_get(self.handle)
+
+    def n_params(self, stage):
+        return STAGE_DIM[stage] * self.n_cams * (self.runs if stage == FM_STAGE_TRANSLATION else 1)
+
+    def set_params(self, stage, params):
+        fm_set_params(self.handle, stage, params)
+
+    def get_params(self, stage):
+        import torch
+        out = torch.empty(self.n_params(stage), dtype=torch.float32, device="cuda")
+        fm_get_params(self.handle, stage, out)
+        return out
+
+    def set_rel_poses(self, rel_R=None, rel_t=None):
+        fm_set_rel_poses(self.handle, rel_R, rel_t)
+
+    def set_translation_runs(self, n_runs):
+        fm_translation_set_runs(self.handle, n_runs)
+        self.runs = int(n_runs)
+
+    def set_ea_loss(self, loss):
+        fm_ea_set_loss(self.handle, loss)
+
+    def set_ea_weights(self, weights, inv_z=None):
+        if weights is not None and inv_z is None:
+            inv_z = 1.0 / max(int((np.asarray(weights.cpu() if hasattr(weights, "cpu") else weights) > 0).sum()), 1)
+        fm_ea_set_weights(self.handle, weights, inv_z if inv_z is not None else 0.0)
+
+    def reweight(self, tau, delta, irls=True):
+        """IRLS weights + filtering at the current epipolar parameters; returns #kept."""
+        return fm_ea_reweight(self.handle, tau, delta, irls)
+
+    def get_weights(self):
+        import torch
+        out = torch.empty(self.n_kp, dtype=torch.float32, device="cuda")
+        return fm_ea_get_weights(self.handle, out)
+
+    def loss_grad(self, stage, params, want_loss=True, want_grad=True, grad_out=None):
+        """params: CUDA tensor (device path), or numpy array / CPU tensor (host
+        path).  Returns (loss, grad) with grad of the same kind as params, or
+        grad_out when given (same side as params)."""
+        nruns = self.runs if stage == FM_STAGE_TRANSLATION else 1
+        loss = (ctypes.c_float * nruns)() if want_loss else None
+        p = _as(params, np.float32)
+        addr, dev, keep = _ptr(p)
+        grad = None
+        gaddr = None
+        if want_grad:
+            if grad_out is not None:
+                grad = grad_out
+                gaddr, gdev, _ = _ptr(grad_out)
+                if gdev != dev:
+                    raise ValueError("grad_out must be on the same side as params")
+            elif dev:
+                import torch
+                grad = torch.empty_like(p)
+                gaddr = grad.data_ptr()
+            else:
+                grad = np.empty(np.asarray(p).shape, dtype=np.float32)
+                gaddr = grad.ctypes.data
+        fm_loss_grad(self.handle, stage, addr, loss, gaddr, int(dev))
+        lv = None
+        if want_loss:
+            lv = loss[0] if nruns == 1 else [loss[k] for k in range(nruns)]
+        return lv, grad
+
+    def timing(self, enable=True):
+        fm_timing_enable(self.handle, enable)
+
+    def timing_read(self):
+        return fm_timing_read(self.handle)
+
+    def track_loss(self, every, capacity=4096):
+        fm_track_loss(self.handle, every, capacity)
+
+    def loss_history(self, capacity=4096):
+        return fm_loss_history(self.handle, capacity)
+
+    def step(self, stage, n_iters, lr, beta1=0.9, beta2=0.999, eps=1e-8, want_loss=False):
+        opts = fm_adam_opts(lr, beta1, beta2, eps)
+        nruns = self.runs if stage == FM_STAGE_TRANSLATION else 1
+        loss = (ctypes.c_float * nruns)() if want_loss else None
+        fm_step(self.handle, stage, opts, n_iters, loss)
+        if want_loss:
+            return loss[0] if nruns == 1 else [loss[k] for k in range(nruns)]
+        return None
+
+
+def problem_from_scene(scene, rel_R=None, rel_t=None, device=True, stream=None):
+    """Builds a Problem from a ``synthetic.scenes.Scene``-like object (fields
+    pair_i, pair_j, kp_img_pair, kp1_px, kp2_px, focal, cx, cy, kp_track)."""
+    arrays = [scene.pair_i, scene.pair_j, scene.kp_img_pair, scene.kp1_px, scene.kp2_px,
+              scene.focal, scene.cx, scene.cy]
+    extra = dict(rel_R=rel_R, rel_t=rel_t, kp_track=scene.kp_track)
+    if device:
+        import torch
+
+        def dv(a, dt):
+            return None if a is None else torch.as_tensor(np.ascontiguousarray(a, dtype=dt)).cuda()
+        dts = [np.int32, np.int32, np.int32, np.float32, np.float32, np.float32, np.float32, np.float32]
+        arrays = [dv(a, dt) for a, dt in zip(arrays, dts)]
+        extra = dict(rel_R=dv(rel_R, np.float32), rel_t=dv(rel_t, np.float32),
+                     kp_track=dv(scene.kp_track, np.int32))
+    return Problem(*arrays, stream=stream, **extra)

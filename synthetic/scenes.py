@@ -229,7 +229,7 @@ def scene_c1(seed: int = 0, n_points: int = 2000, sigma_px: float = 0.5,
     u, v, z = _project(R, t, f, cx, cy, X)
     track_cams, track_uv = [], []
     for p in range(n_points):
-        k = int(rng.integers(2, 7))
+        k = min(int(rng.integers(2, 7)), N)
         cams = np.sort(rng.choice(N, size=k, replace=False))
         uv = np.stack([u[p, cams], v[p, cams]], axis=1) + rng.normal(0.0, sigma_px, size=(k, 2))
         track_cams.append(cams)

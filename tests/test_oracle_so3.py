@@ -2,7 +2,8 @@
 differences (no CUDA)."""
 import numpy as np
 
-from oracle.so3 import angle_axis, geodesic, rot_from_6d, rot_from_6d_vjp, rot_to_6d, skew
+from oracle.so3 import (angle_axis, geodesic, project_to_rotation, rot_from_6d, rot_from_6d_vjp,
+                        rot_to_6d, skew)
 
 
 def _random_rotations(rng, n):
@@ -63,3 +64,17 @@ def test_geodesic_closed_form():
         R1 = angle_axis(axis, ang) @ R0
         assert abs(geodesic(R0, R1) - ang) < 2e-8
         assert abs(geodesic(R1, R0) - ang) < 2e-8
+
+
+def test_projection_to_rotation():
+    rng = np.random.default_rng(5)
+    R = _random_rotations(rng, 20)
+    np.testing.assert_allclose(project_to_rotation(R), R, atol=1e-14)
+    # a float32 copy is brought back to an exact rotation within float32 rounding
+    Rf = R.astype(np.float32).astype(np.float64)
+    Q = project_to_rotation(Rf)
+    np.testing.assert_allclose(np.einsum("nki,nkj->nij", Q, Q), np.broadcast_to(np.eye(3), Q.shape), atol=1e-14)
+    assert np.max(np.abs(Q - R)) < 2e-7
+    # a reflection is mapped to a proper rotation
+    F = R[0] @ np.diag([1.0, 1.0, -1.0])
+    assert abs(np.linalg.det(project_to_rotation(F)) - 1.0) < 1e-12
