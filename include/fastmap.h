@@ -184,10 +184,10 @@ fm_status fm_ea_set_loss(fm_problem* problem, fm_ea_loss loss);
 /* Per-keypoint-pair weights w_m of the epipolar stage (Eq. 9: IRLS weights
  * 1/|eps^_m|; a weight of 0 removes a filtered pair), in the order of the
  * keypoint pairs given at creation, and the normaliser 1/Z of the loss.
- * weights == NULL restores unit weights and inv_z = 1/n_kp_pairs.  Rebuilds
- * the compact matrices W_n (Eq. 17), stored together with their expansion
- * around the essential matrices of the current epipolar-stage parameters, so
- * those parameters must be set first (FM_ERR_STATE otherwise). */
+ * weights == NULL restores unit weights and inv_z = 1/n_kp_pairs.  The compact
+ * matrices W_n (Eq. 17) are rebuilt by the next FM_EA_COMPACT evaluation,
+ * stored as an expansion around the essential matrices of the parameters of
+ * that evaluation. */
 fm_status fm_ea_set_weights(fm_problem* problem, const float* weights,
                             int32_t weights_on_device, float inv_z);
 
@@ -197,7 +197,8 @@ fm_status fm_ea_set_weights(fm_problem* problem, const float* weights,
  * For every keypoint pair, eps^ = x~2^T E_n x~1; the pair is kept when
  * |eps^| < tau and then weighted 1/max(|eps^|, delta) when irls != 0, or 1
  * when irls == 0; filtered pairs get weight 0.  Sets inv_z = 1/#kept,
- * rebuilds W_n, and writes #kept to *n_kept (may be NULL).  Synchronises. */
+ * rebuilds W_n around the current poses, and writes #kept to *n_kept (may be
+ * NULL).  Synchronises. */
 fm_status fm_ea_reweight(fm_problem* problem, float tau, float delta, int32_t irls,
                          int64_t* n_kept);
 

@@ -378,6 +378,24 @@ fm_status ensure_targets(fm_problem* pr) {
   return FM_OK;
 }
 
+// W_n together with its expansion around the essential matrices e0 of the
+// parameters `centre` (see fm_irls.cu); built lazily after the weights change
+fm_status rebuild_W(fm_problem* pr, const float* centre) {
+  {
+    Timed t(pr, fm::kKEaTables);
+    fm::launch_ea_tables(centre, pr->pair_i, pr->pair_j, pr->seg_off, pr->P, pr->seg_tab, nullptr,
+                         pr->stream);
+  }
+  FM_LAUNCHED(pr);
+  {
+    Timed t(pr, fm::kKWBuild);
+    fm::launch_w_build(pr, pr->ea_w, pr->W, pr->stream);
+  }
+  FM_LAUNCHED(pr);
+  pr->W_valid = true;
+  return FM_OK;
+}
+
 // One evaluation of a stage: per-image-pair pass, then the per-camera pass
 // (Adam when adam != null, else the gradient into grad_dev); the loss of every
 // run is reduced into loss_a and loss_b when they are not null.
@@ -389,7 +407,10 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
   int runs = 1;
   int* step = adam ? state->t : nullptr;
   if (st == FM_STAGE_EPIPOLAR && pr->ea_loss == FM_EA_COMPACT) {
-    if (!pr->W_valid) return fail(pr, FM_ERR_STATE, "the compact loss needs W (fm_ea_set_weights or fm_ea_reweight)");
+    if (!pr->W_valid) {
+      fm_status e = rebuild_W(pr, params);
+      if (e != FM_OK) return e;
+    }
     {
       Timed t(pr, fm::kKEaCompact);
       fm::launch_ea_compact(pr, params, pr->ea_inv_z, step, s);
@@ -614,31 +635,13 @@ fm_status fm_ea_set_loss(fm_problem* pr, fm_ea_loss loss) {
   return FM_OK;
 }
 
-// W_n together with its expansion around the essential matrices e0 of the
-// current epipolar-stage parameters (see fm_irls.cu)
-fm_status rebuild_W(fm_problem* pr) {
-  if (!pr->ea_params_set) return fail(pr, FM_ERR_STATE, "set the epipolar-stage parameters before the weights");
-  {
-    Timed t(pr, fm::kKEaTables);
-    fm::launch_ea_tables(pr->ea_params, pr->pair_i, pr->pair_j, pr->seg_off, pr->P, pr->seg_tab, nullptr,
-                         pr->stream);
-  }
-  FM_LAUNCHED(pr);
-  {
-    Timed t(pr, fm::kKWBuild);
-    fm::launch_w_build(pr, pr->ea_w, pr->W, pr->stream);
-  }
-  FM_LAUNCHED(pr);
-  pr->W_valid = true;
-  return FM_OK;
-}
-
 fm_status fm_ea_set_weights(fm_problem* pr, const float* w, int32_t on_device, float inv_z) {
   if (!pr) return FM_ERR_INVALID_ARG;
   if (!w) {
     dfree(pr->ea_w);
     pr->ea_inv_z = pr->Z > 0 ? (float)(1.0 / (double)pr->Z) : 0.f;
-    return rebuild_W(pr);
+    pr->W_valid = false;
+    return FM_OK;
   }
   if (!(std::isfinite(inv_z) && inv_z >= 0.f)) return fail(pr, FM_ERR_INVALID_ARG, "inv_z must be finite and >= 0");
   if (!pr->ea_w) FM_ALLOC(pr, pr->ea_w, (size_t)pr->Z);
@@ -651,7 +654,8 @@ fm_status fm_ea_set_weights(fm_problem* pr, const float* w, int32_t on_device, f
     if (e != FM_OK) return e;
   }
   pr->ea_inv_z = inv_z;
-  return rebuild_W(pr);
+  pr->W_valid = false;
+  return FM_OK;
 }
 
 fm_status fm_ea_reweight(fm_problem* pr, float tau, float delta, int32_t irls, int64_t* n_kept) {
@@ -672,8 +676,12 @@ fm_status fm_ea_reweight(fm_problem* pr, float tau, float delta, int32_t irls, i
     fm::launch_ea_reweight(pr, tau, delta, irls, pr->ea_w, pr->d_kept, s);
   }
   FM_LAUNCHED(pr);
-  fm_status e = rebuild_W(pr);
-  if (e != FM_OK) return e;
+  {
+    Timed t(pr, fm::kKWBuild);
+    fm::launch_w_build(pr, pr->ea_w, pr->W, s);   // centred at the reweighting pose
+  }
+  FM_LAUNCHED(pr);
+  pr->W_valid = true;
   unsigned long long kept = 0;
   FM_CUDA(pr, cudaMemcpyAsync(&kept, pr->d_kept, sizeof(kept), cudaMemcpyDeviceToHost, s));
   FM_CUDA(pr, cudaStreamSynchronize(s));

@@ -1,0 +1,222 @@
+// Rotation initialisation (Appendix "Global Rotation / Initialization",
+// Eqs. 10-14) and the multi-run translation merge (Appendix "Multiple
+// Initializations").
+//
+// Martinec-Pajdla column problems.  With x stacking one 3-vector per camera,
+// sum_{(i,j)} ||x_j - R_ij x_i||^2 = x^T A x where, per image pair,
+// A_ii += I, A_jj += I, A_ji -= R_ij, A_ij -= R_ij^T (R_ij orthogonal).  The
+// first columns are the eigenvector of A's smallest eigenvalue (Eq. 12); the
+// second columns that of B = A/|P| + (1/|I|) blockdiag(c1_i c1_i^T) (Eq. 13).
+// Both are found by power iteration on I - A/sigma (sigma >= lambda_max by
+// Gershgorin: 2 max degree), whose spectrum lies in [0, 1] with the wanted
+// eigenvector at the top; the iterate never needs rescaling.  Any vector of
+// the (near-)null space is a valid answer (x_i = R_i v for some v), so only
+// the gap to the fourth eigenvalue matters for convergence.
+#include "fm_device.cuh"
+#include "fm_internal.h"
+
+namespace fm {
+namespace {
+
+// y = x - (B x)/sigma with B = A/scaleP + (1/N) diag(c1 c1^T) (c1 may be null)
+__global__ void __launch_bounds__(128) k_mart_iter(const int* __restrict__ cam_seg_off,
+                                                   const int* __restrict__ cam_seg,
+                                                   const int* __restrict__ pi, const int* __restrict__ pj,
+                                                   const float* __restrict__ relR, const float* __restrict__ x,
+                                                   const float* __restrict__ c1, float* __restrict__ y, int N,
+                                                   float inv_sigma, float inv_scale_p, float inv_n) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (c >= N) return;
+  const float xc0 = x[3 * c], xc1 = x[3 * c + 1], xc2 = x[3 * c + 2];
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  const int b = cam_seg_off[c], e = cam_seg_off[c + 1];
+  for (int idx = b + lane; idx < e; idx += 32) {
+    const unsigned v = (unsigned)cam_seg[idx];
+    const int n = (int)(v & 0x7fffffffu);
+    const float* R = relR + 9 * n;
+    if ((v >> 31) == 0) {
+      // camera is i: row block i has -R^T x_j
+      const float* xj = x + 3 * pj[n];
+      a0 -= R[0] * xj[0] + R[3] * xj[1] + R[6] * xj[2];
+      a1 -= R[1] * xj[0] + R[4] * xj[1] + R[7] * xj[2];
+      a2 -= R[2] * xj[0] + R[5] * xj[1] + R[8] * xj[2];
+    } else {
+      // camera is j: row block j has -R x_i
+      const float* xi = x + 3 * pi[n];
+      a0 -= R[0] * xi[0] + R[1] * xi[1] + R[2] * xi[2];
+      a1 -= R[3] * xi[0] + R[4] * xi[1] + R[5] * xi[2];
+      a2 -= R[6] * xi[0] + R[7] * xi[1] + R[8] * xi[2];
+    }
+  }
+  a0 = warp_sum(a0);
+  a1 = warp_sum(a1);
+  a2 = warp_sum(a2);
+  if (lane == 0) {
+    const float deg = (float)(e - b);
+    float b0 = (a0 + deg * xc0) * inv_scale_p;
+    float b1 = (a1 + deg * xc1) * inv_scale_p;
+    float b2 = (a2 + deg * xc2) * inv_scale_p;
+    if (c1) {
+      const float* u = c1 + 3 * c;
+      const float d = (u[0] * xc0 + u[1] * xc1 + u[2] * xc2) * inv_n;
+      b0 += d * u[0];
+      b1 += d * u[1];
+      b2 += d * u[2];
+    }
+    y[3 * c] = xc0 - b0 * inv_sigma;
+    y[3 * c + 1] = xc1 - b1 * inv_sigma;
+    y[3 * c + 2] = xc2 - b2 * inv_sigma;
+  }
+}
+
+// per-camera normalisation of the first columns
+__global__ void k_normalise3(float* __restrict__ x, int N) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  float v[3] = {x[3 * c], x[3 * c + 1], x[3 * c + 2]};
+  const float n = sqrtf(dot3(v, v));
+  const float s = n > 0.f ? 1.f / n : 0.f;
+  for (int k = 0; k < 3; ++k) x[3 * c + k] = v[k] * s;
+}
+
+// second columns: normalise, Gram-Schmidt against c1 (Eq. 14 takes c3 = c1 x c2
+// implicitly through the 6D map); write the 6D parameters (c1, c2)
+__global__ void k_mart_finish(const float* __restrict__ c1, const float* __restrict__ c2, int N,
+                              float* __restrict__ params6) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  float u[3] = {c1[3 * c], c1[3 * c + 1], c1[3 * c + 2]};
+  float v[3] = {c2[3 * c], c2[3 * c + 1], c2[3 * c + 2]};
+  const float d = dot3(u, v);
+  for (int k = 0; k < 3; ++k) v[k] -= d * u[k];
+  const float n = sqrtf(dot3(v, v));
+  const float s = n > 0.f ? 1.f / n : 0.f;
+  for (int k = 0; k < 3; ++k) {
+    params6[6 * c + k] = u[k];
+    params6[6 * c + 3 + k] = v[k] * s;
+  }
+}
+
+// deterministic start vector: the index mixed by a Weyl increment and the
+// MurmurHash3 32-bit finaliser (fmix32), mapped to [-1, 1)
+__global__ void k_hash_fill(float* __restrict__ x, int n, unsigned salt) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  unsigned z = (unsigned)k * 0x9E3779B9u + salt;
+  z = (z ^ (z >> 16)) * 0x85EBCA6Bu;
+  z = (z ^ (z >> 13)) * 0xC2B2AE35u;
+  z ^= z >> 16;
+  x[k] = (float)(z >> 8) * (1.0f / 8388608.0f) - 1.0f;
+}
+
+// ---------------------------------------------------------------- merge
+// Per run: centroid and mean norm of the centres (fixed order, one CTA per run).
+__global__ void k_run_stats(const float* __restrict__ o, int N, float* __restrict__ stats) {
+  __shared__ float s[4][256];
+  const float* orun = o + (size_t)3 * N * blockIdx.x;
+  float a[3] = {0.f, 0.f, 0.f};
+  for (int c = threadIdx.x; c < N; c += 256)
+    for (int k = 0; k < 3; ++k) a[k] += orun[3 * c + k];
+  for (int k = 0; k < 3; ++k) s[k][threadIdx.x] = a[k];
+  __syncthreads();
+  for (int d = 128; d > 0; d >>= 1) {
+    if ((int)threadIdx.x < d)
+      for (int k = 0; k < 3; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + d];
+    __syncthreads();
+  }
+  const float cx = s[0][0] / N, cy = s[1][0] / N, cz = s[2][0] / N;
+  __syncthreads();
+  float m = 0.f;
+  for (int c = threadIdx.x; c < N; c += 256) {
+    const float dx = orun[3 * c] - cx, dy = orun[3 * c + 1] - cy, dz = orun[3 * c + 2] - cz;
+    m += sqrtf(dx * dx + dy * dy + dz * dz);
+  }
+  s[3][threadIdx.x] = m;
+  __syncthreads();
+  for (int d = 128; d > 0; d >>= 1) {
+    if ((int)threadIdx.x < d) s[3][threadIdx.x] += s[3][threadIdx.x + d];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    stats[4 * blockIdx.x + 0] = cx;
+    stats[4 * blockIdx.x + 1] = cy;
+    stats[4 * blockIdx.x + 2] = cz;
+    stats[4 * blockIdx.x + 3] = s[3][0] / N;
+  }
+}
+
+// Per camera (one warp): mean loss term over its image pairs in every run at
+// the normalised centres; keep the run with the lowest mean (lowest index on
+// ties) and write its normalised centre.
+__global__ void __launch_bounds__(128) k_merge(const float* __restrict__ o, const float* __restrict__ stats,
+                                               const int* __restrict__ cam_seg_off,
+                                               const int* __restrict__ cam_seg, const int* __restrict__ pi,
+                                               const int* __restrict__ pj, const float* __restrict__ tgt,
+                                               int N, int runs, float* __restrict__ out,
+                                               int* __restrict__ best_run) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (c >= N) return;
+  const int b = cam_seg_off[c], e = cam_seg_off[c + 1];
+  float best = 3.4e38f;
+  int best_r = 0;
+  for (int r = 0; r < runs; ++r) {
+    const float* orun = o + (size_t)3 * N * r;
+    const float* st = stats + 4 * r;
+    const float inv = st[3] > 0.f ? 1.f / st[3] : 0.f;
+    float acc = 0.f;
+    for (int idx = b + lane; idx < e; idx += 32) {
+      const int n = (int)((unsigned)cam_seg[idx] & 0x7fffffffu);
+      const int i = pi[n], j = pj[n];
+      float d[3];
+      for (int k = 0; k < 3; ++k) d[k] = ((orun[3 * j + k] - st[k]) - (orun[3 * i + k] - st[k])) * inv;
+      const float nn = sqrtf(dot3(d, d));
+      float l = 0.f;
+      if (nn > 1e-12f) {
+        for (int k = 0; k < 3; ++k) l += fabsf(d[k] / nn - tgt[3 * n + k]);
+      } else {
+        for (int k = 0; k < 3; ++k) l += fabsf(d[k] - tgt[3 * n + k]);
+      }
+      acc += l;
+    }
+    acc = warp_sum(acc);
+    const float mean = (e > b) ? acc / (float)(e - b) : 0.f;
+    if (mean < best) {
+      best = mean;
+      best_r = r;
+    }
+  }
+  if (lane < 3) {
+    const float* st = stats + 4 * best_r;
+    const float inv = st[3] > 0.f ? 1.f / st[3] : 0.f;
+    out[3 * c + lane] = (o[(size_t)3 * N * best_r + 3 * c + lane] - st[lane]) * inv;
+  }
+  if (lane == 0 && best_run) best_run[c] = best_r;
+}
+
+}  // namespace
+
+void launch_mart_iter(const fm_problem* pr, const float* x, const float* c1, float* y, float sigma,
+                      float scale_p, cudaStream_t s) {
+  k_mart_iter<<<(pr->N + 3) / 4, 128, 0, s>>>(pr->cam_seg_off, pr->cam_seg, pr->pair_i, pr->pair_j,
+                                              pr->rel_R, x, c1, y, pr->N, 1.f / sigma, 1.f / scale_p,
+                                              1.f / (float)pr->N);
+}
+void launch_normalise3(float* x, int N, cudaStream_t s) {
+  k_normalise3<<<(N + 127) / 128, 128, 0, s>>>(x, N);
+}
+void launch_mart_finish(const float* c1, const float* c2, int N, float* params6, cudaStream_t s) {
+  k_mart_finish<<<(N + 127) / 128, 128, 0, s>>>(c1, c2, N, params6);
+}
+void launch_hash_fill(float* x, int n, unsigned salt, cudaStream_t s) {
+  k_hash_fill<<<(n + 255) / 256, 256, 0, s>>>(x, n, salt);
+}
+void launch_merge(const fm_problem* pr, const float* o, int runs, float* stats, float* out,
+                  int* best_run, cudaStream_t s) {
+  k_run_stats<<<runs, 256, 0, s>>>(o, pr->N, stats);
+  k_merge<<<(pr->N + 3) / 4, 128, 0, s>>>(o, stats, pr->cam_seg_off, pr->cam_seg, pr->pair_i, pr->pair_j,
+                                         pr->trn_target, pr->N, runs, out, best_run);
+}
+
+}  // namespace fm

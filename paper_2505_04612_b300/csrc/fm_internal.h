@@ -30,7 +30,7 @@ enum : int {
 enum KernelId : int {
   kKCalibrate = 0, kKSegOffsets, kKRunTables, kKEaTables, kKEaDirect, kKEaSegments,
   kKRotPairs, kKTrnTargets, kKTrnPairs, kKCamUpdate, kKLossSum, kKEaReweight, kKWBuild,
-  kKEaCompact, kKCount
+  kKEaCompact, kKMartIter, kKRelTrans, kKMerge, kKTriangulate, kKCount
 };
 extern const char* const kKernelNames[kKCount];
 
@@ -67,6 +67,10 @@ struct fm_problem {
   // keypoints
   float4* kp = nullptr;          // [Z] calibrated (x1, y1, x2, y2)
   int* kp_track = nullptr;       // [Z] or null
+  int* kp_seg = nullptr;         // [Z] image pair of each keypoint pair (kept with tracks)
+  int n_tracks = 0;
+  int* track_off = nullptr;      // [T+1] keypoint pairs grouped by track
+  int* track_idx = nullptr;      // [Z]
   float* focal = nullptr;
   float* cx = nullptr;
   float* cy = nullptr;
@@ -161,6 +165,19 @@ void launch_ea_reweight(const fm_problem* pr, float tau, float delta, int irls, 
 void launch_w_build(const fm_problem* pr, const float* w, float* W, cudaStream_t s);
 void launch_ea_compact(const fm_problem* pr, const float* params, float inv_z, int* step_counter,
                        cudaStream_t s);
+
+// setup steps (fm_init.cu, fm_reltrans.cu, fm_points.cu)
+void launch_mart_iter(const fm_problem* pr, const float* x, const float* c1, float* y, float sigma,
+                      float scale_p, cudaStream_t s);
+void launch_normalise3(float* x, int N, cudaStream_t s);
+void launch_mart_finish(const float* c1, const float* c2, int N, float* params6, cudaStream_t s);
+void launch_hash_fill(float* x, int n, unsigned salt, cudaStream_t s);
+void launch_merge(const fm_problem* pr, const float* o, int runs, float* stats, float* out,
+                  int* best_run, cudaStream_t s);
+void launch_reltrans(const fm_problem* pr, const float* rot6, float* rel_t, float* err_out, cudaStream_t s);
+cudaError_t build_track_table(fm_problem* pr, int* T_out);
+void launch_triangulate(const fm_problem* pr, const float* params, float max_err_px, float min_angle_rad,
+                        float* pts, int* valid, int* ncam, cudaStream_t s);
 
 // rotation / translation (fm_pose.cu)
 void launch_rot_pairs(const float* params, const int* pi, const int* pj, const float* rel_R,

@@ -81,14 +81,18 @@ def test_compact_matches_oracle(seed):
             assert G.rel_err(gd.cpu().numpy().reshape(go.shape), go) < GRAD_TOL
 
 
-def test_compact_needs_weights_state():
+def test_compact_without_weights_is_unweighted_l2():
     from paper_2505_04612_b300 import fastmap as F
     sc = scene("c1", 3)
+    x1, x2 = G.oracle_xs(sc)
+    p = _near(sc, 3)
     with G.make_problem(sc) as pr:
         pr.set_ea_loss(F.FM_EA_COMPACT)
-        with pytest.raises(F.FastMapError) as e:
-            pr.loss_grad(F.FM_STAGE_EPIPOLAR, _near(sc, 3).reshape(-1))
-        assert e.value.status == F.FM_ERR_STATE
+        L, g = pr.loss_grad(F.FM_STAGE_EPIPOLAR, p.reshape(-1))
+    W = ep.build_W(x1, x2, sc.kp_img_pair, sc.n_pairs)
+    Lo, go, _ = ep.compact_loss_grad(G.f32(p), sc.pair_i, sc.pair_j, W, 1.0 / sc.n_kp)
+    assert abs(L - Lo) <= LOSS_TOL * Lo
+    assert G.rel_err(g.reshape(go.shape), go) < GRAD_TOL
 
 
 def test_compact_adam_steps():
