@@ -41,8 +41,8 @@
  *   - Every entry point returns an fm_status; no C++ exception crosses the
  *     ABI and the library never exits or aborts.
  *   - fm_last_error(problem) describes the last failure on that problem;
- *     fm_last_error(NULL) describes the last failure of fm_problem_create on
- *     the calling thread.
+ *     fm_last_error(NULL) describes the last failure of fm_problem_create (or
+ *     of fm_ea_loss_grad_static) on the calling thread.
  *   - Results are deterministic: no floating-point atomics are used, so the
  *     same inputs give bitwise identical outputs on the same GPU.
  */
@@ -256,6 +256,53 @@ fm_status fm_track_loss(fm_problem* problem, int32_t every, int32_t capacity);
  * first, into out and their number into *count (for the translation stage,
  * the loss of run 0).  Synchronises the stream. */
 fm_status fm_loss_history(fm_problem* problem, float* out, int32_t capacity, int32_t* count);
+
+/* ----------------------------------------------- allocation-free evaluation
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory when they evaluate -- code running under
+ * another framework's allocator or memory pool that forbids cudaMalloc,
+ * latency-critical loops where an allocation could block or fail, and
+ * deployments that must keep a fixed, known footprint.
+ *
+ * fm_ea_loss_grad_static evaluates the direct epipolar loss (Eq. 7 for
+ * FM_EA_L1, Eqs. 8-9 for FM_EA_L2) and its gradient with the same kernels as
+ * fm_loss_grad, without creating a problem and without allocating anything:
+ * its temporary tables live in one 16 MiB array of device memory that the
+ * library holds on every GPU that loads it, until the process exits.
+ *
+ * Inputs (device pointers, read only; kp_dev and weights_dev 16-byte aligned):
+ *   kp_dev       [Z] float4 (x1, y1, x2, y2): calibrated coordinates
+ *                K^-1 [u, v, 1]^T of the keypoint in image i_n and in j_n,
+ *                grouped by image pair in index order
+ *   seg_off_dev  [P+1] first keypoint pair of each image pair (seg_off[P] = Z)
+ *   pair_i_dev, pair_j_dev  [P] camera indices of each image pair
+ *   params_dev   [N*9] epipolar-stage parameters (6D rotation, t)
+ *   weights_dev  [Z] per-pair weights, or NULL for unit weights
+ * loss: FM_EA_L1 or FM_EA_L2; inv_z: the 1/Z normaliser.
+ * Outputs (device pointers, caller-owned):
+ *   loss_dev      [1] the loss
+ *   pair_grad_dev [P*24] per image pair: dL/dR_i (9, row-major), dL/dt_i
+ *                 (3), dL/dR_j (9), dL/dt_j (3) -- the caller sums them per
+ *                 camera (and applies the 6D adjoint for rotations)
+ * cuda_stream: the stream to enqueue on (NULL = default); the call returns
+ * after enqueueing.
+ *
+ * Limits and sharing: the tables need about 48 B per image pair plus 4 B per
+ * 15 keypoint pairs (plus 48 B per 480 keypoint pairs); a problem that does
+ * not fit in 16 MiB (roughly P + Z/150 beyond ~300k) is rejected with
+ * FM_ERR_INVALID_ARG and a message from fm_last_error(NULL), before any GPU
+ * work.  Every call on a device shares the one array and leaves its contents
+ * behind; nothing in it needs to start at zero.  Calls whose GPU work
+ * overlaps (two streams, or two host threads) race on the array: serialise
+ * them.  The first call on each device looks up the array's device address
+ * (and sets the kernel's shared-memory limit); make that first call before
+ * any stream capture. */
+fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev,
+                                 const int32_t* pair_i_dev, const int32_t* pair_j_dev,
+                                 const float* params_dev, const float* weights_dev,
+                                 int32_t n_cams, int32_t n_img_pairs, int64_t n_kp_pairs,
+                                 int32_t loss, float inv_z, float* loss_dev,
+                                 float* pair_grad_dev, void* cuda_stream);
 
 #ifdef __cplusplus
 }  /* extern "C" */

@@ -6,7 +6,13 @@
 
 #include "fm_internal.h"
 
+namespace {
+thread_local std::string g_create_error = "no error";
+}
+
 namespace fm {
+void set_thread_error(const std::string& msg) { g_create_error = msg; }
+
 const char* const kKernelNames[kKCount] = {
     "k_calibrate", "k_seg_offsets", "k_run_tables", "k_ea_tables", "k_ea_direct",
     "k_ea_segments", "k_rot_pairs", "k_trn_targets", "k_trn_pairs", "k_cam", "k_sum_fixed",
@@ -14,8 +20,6 @@ const char* const kKernelNames[kKCount] = {
 }
 
 namespace {
-
-thread_local std::string g_create_error = "no error";
 
 cudaEvent_t take_event(fm_problem* pr) {
   if (!pr->event_pool.empty()) {

@@ -138,6 +138,9 @@ struct fm_problem {
 
 namespace fm {
 
+// message returned by fm_last_error(NULL) on the calling thread
+void set_thread_error(const std::string& msg);
+
 // ---------------------------------------------------------------- launchers
 // setup (fm_setup.cu)
 void launch_calibrate(const float* kp1, const float* kp2, const int* kp_pair, const int* pi,

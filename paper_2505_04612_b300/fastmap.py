@@ -107,6 +107,10 @@ _SIGNATURES = {
     "fm_track_loss": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "fm_loss_history": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
                                        ctypes.POINTER(ctypes.c_int32)]),
+    "fm_ea_loss_grad_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 _LIB = None
@@ -291,6 +295,25 @@ def fm_loss_history(handle, capacity=4096):
     n = ctypes.c_int32()
     _check(lib().fm_loss_history(handle, out, capacity, ctypes.byref(n)), handle)
     return [out[k] for k in range(n.value)]
+
+
+def fm_ea_loss_grad_static(kp, seg_off, pair_i, pair_j, params, weights, n_cams, loss, inv_z,
+                           loss_out, pair_grad_out, stream=None):
+    """Allocation-free direct epipolar loss + per-image-pair gradient blocks.
+    Every array is a CUDA tensor (kp float32 [Z,4], seg_off int32 [P+1],
+    pair_i/pair_j int32 [P], params float32 [N*9], weights float32 [Z] or
+    None, loss_out float32 [1], pair_grad_out float32 [P*24])."""
+    args = [_ptr(a) for a in (kp, seg_off, pair_i, pair_j, params, weights, loss_out, pair_grad_out)]
+    for a, (addr, dev, _) in zip(("kp", "seg_off", "pair_i", "pair_j", "params", "weights", "loss_out",
+                                  "pair_grad_out"), args):
+        if addr is not None and not dev:
+            raise ValueError(f"{a} must be a CUDA tensor")
+    P = int(pair_i.numel())
+    Z = int(kp.numel() // 4)
+    st = lib().fm_ea_loss_grad_static(args[0][0], args[1][0], args[2][0], args[3][0], args[4][0], args[5][0],
+                                      int(n_cams), P, Z, int(loss), ctypes.c_float(inv_z), args[6][0],
+                                      args[7][0], _stream_handle(stream))
+    _check(st, None)
 
 
 # ------------------------------------------------------------ owner class
