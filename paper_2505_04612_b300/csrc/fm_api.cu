@@ -454,13 +454,18 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
     }
     FM_LAUNCHED(pr);
   }
-  for (float* dst : {loss_a, loss_b}) {
+  // the loss of every run: the first destination is reduced by an extra CTA
+  // of the per-camera kernel, any other by its own launch
+  float* fused = loss_a ? loss_a : loss_b;
+  float* other = (loss_a && loss_b) ? loss_b : nullptr;
+  const bool cam = adam || grad_dev;
+  for (float* dst : {cam ? other : fused, cam ? nullptr : other}) {
     if (!dst) continue;
     Timed t(pr, fm::kKLossSum);
     fm::launch_sum_fixed(pr->seg_loss, P, runs, dst, s);
   }
   FM_LAUNCHED(pr);
-  if (adam || grad_dev) {
+  if (cam) {
     fm::CamUpdate u;
     u.cam_seg_off = pr->cam_seg_off;
     u.cam_seg = pr->cam_seg;
@@ -478,6 +483,8 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
     u.N = N;
     u.P = P;
     u.runs = runs;
+    u.seg_loss = pr->seg_loss;
+    u.loss_out = fused;
     {
       Timed t(pr, fm::kKCamUpdate);
       fm::launch_cam_update((int)st, u, s);

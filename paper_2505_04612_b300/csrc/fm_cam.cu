@@ -20,13 +20,39 @@ template <> struct Layout<2> { static constexpr int PART = 12, PDIM = 9; static 
 
 constexpr int kCamWarps = 4;
 
+// fixed-order sum of the per-image-pair loss terms of one run (one CTA)
+__device__ void loss_sum_cta(const float* __restrict__ x, int n, float* out) {
+  __shared__ float part[kCamWarps * 32];
+  float s = 0.f;
+  for (int k = threadIdx.x; k < n; k += kCamWarps * 32) s += x[k];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int d = kCamWarps * 16; d > 0; d >>= 1) {
+    if ((int)threadIdx.x < d) part[threadIdx.x] += part[threadIdx.x + d];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = part[0];
+}
+
 template <int STAGE, bool ADAM>
 __global__ void __launch_bounds__(kCamWarps * 32) k_cam(CamUpdate u) {
   using L = Layout<STAGE>;
   const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * kCamWarps + (threadIdx.x >> 5);
   const int run = blockIdx.y;
-  if (c >= u.N) return;
+  pdl_trigger();
+  if (u.loss_out && blockIdx.x == gridDim.x - 1) {
+    // the extra CTA of the grid reduces the loss
+    pdl_wait();
+    loss_sum_cta(u.seg_loss + (size_t)run * u.P, u.P, u.loss_out + run);
+    return;
+  }
+  const int c = blockIdx.x * kCamWarps + (threadIdx.x >> 5);
+  if (c >= u.N) {
+    pdl_wait();
+    return;
+  }
+  const int b = u.cam_seg_off[c], e = u.cam_seg_off[c + 1];   // static: before the wait
+  pdl_wait();
   const float* prm = u.params + ((size_t)run * u.N + c) * L::PDIM;
   float p[L::PDIM];
 #pragma unroll
@@ -34,7 +60,6 @@ __global__ void __launch_bounds__(kCamWarps * 32) k_cam(CamUpdate u) {
   float acc[L::PART];
 #pragma unroll
   for (int k = 0; k < L::PART; ++k) acc[k] = 0.f;
-  const int b = u.cam_seg_off[c], e = u.cam_seg_off[c + 1];
   const float* sg = u.seg_grad + (size_t)run * u.P * 2 * L::PART;
   for (int idx = b + lane; idx < e; idx += 32) {
     const unsigned v = (unsigned)u.cam_seg[idx];
@@ -107,9 +132,9 @@ __global__ void k_sum_fixed(const float* __restrict__ x, int n, float* __restric
 
 template <int STAGE>
 void launch_stage(const CamUpdate& u, cudaStream_t s) {
-  dim3 grid((u.N + kCamWarps - 1) / kCamWarps, u.runs);
-  if (u.params_out) k_cam<STAGE, true><<<grid, kCamWarps * 32, 0, s>>>(u);
-  else k_cam<STAGE, false><<<grid, kCamWarps * 32, 0, s>>>(u);
+  dim3 grid((u.N + kCamWarps - 1) / kCamWarps + (u.loss_out ? 1 : 0), u.runs);
+  if (u.params_out) launch_pdl(k_cam<STAGE, true>, grid, dim3(kCamWarps * 32), 0, s, u);
+  else launch_pdl(k_cam<STAGE, false>, grid, dim3(kCamWarps * 32), 0, s, u);
 }
 
 }  // namespace

@@ -7,6 +7,14 @@
 
 namespace fm {
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialisation attribute may start while its predecessor in the stream
+// still runs.  pdl_wait() blocks until the predecessor grid has completed and
+// its writes are visible (a no-op without the attribute); pdl_trigger() lets
+// the successor start launching early -- it still waits in its own pdl_wait().
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ float dot3(const float* a, const float* b) {
   return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
 }

@@ -17,20 +17,20 @@
 //
 // k_ea_direct layout and schedule
 //   * keypoint pairs are sorted by image pair (CSR seg_off);
-//   * a warp run is 32 * U consecutive keypoint pairs; lane l owns the U
-//     consecutive pairs [base + l*U, base + (l+1)*U);
-//   * each warp is persistent over warp runs (grid-stride) and double-buffers
-//     its next warp run in shared memory with cp.async (coalesced 512 B per
-//     warp instruction); the image-pair table entries of the warp run
-//     (up to kEaSegCap) are staged the same way;
-//   * U is odd, so lanes reading their own contiguous pairs (stride U*16 B)
-//     hit distinct 16-B bank groups in each quarter warp: no bank conflicts;
-//   * each lane accumulates in registers along its run; a run spans at most
-//     a few image pairs, so the lane keeps a "head" part (its first image
-//     pair, which may continue from the previous lane), writes complete image
-//     pairs inside its run directly, and keeps a "tail" part; a warp-level
-//     segmented scan keyed by image pair combines heads and tails in fixed
-//     lane order.  No atomics: the result is deterministic.
+//   * a warp run is 15 rows of 32 consecutive pairs; lane l takes pair
+//     base + 32 r + l of row r, so every row is one coalesced 512-B load
+//     (LDG.128) and the warp issues all 15 rows before using them: 7.5 KB in
+//     flight per warp, no shared memory, occupancy bounded by registers;
+//   * the table entries (E and end offset) of the warp run's first 32 image
+//     pairs sit one per lane in registers and are broadcast with shuffles;
+//     entries beyond the first 32 come from global memory;
+//   * a row that lies inside the current image pair is accumulated per lane
+//     with no branches; a row that crosses one or more image-pair ends is
+//     handled warp-uniformly: each lane finds its own image pair, the current
+//     image pair is closed by a butterfly warp sum, image pairs that start and
+//     end inside the row get their own warp sums, and the last one opens.
+//     Every (warp run, image pair) gets exactly one record, summed in a fixed
+//     order: no atomics, deterministic.
 #include "fm_device.cuh"
 #include "fm_internal.h"
 
@@ -39,7 +39,6 @@ namespace {
 
 constexpr int U = kEaPairsPerLane;
 constexpr int WP = kEaWarpPairs;
-constexpr int SEGCAP = kEaSegCap;
 constexpr int WARPS = kEaWarpsPerCta;
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -47,30 +46,23 @@ __global__ void k_ea_tables(const float* __restrict__ params, const int* __restr
                             const int* __restrict__ pj, const int* __restrict__ seg_off, int P,
                             float4* __restrict__ tab, int* step_counter) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_trigger();
+  int end = 0, ci = 0, cj = 0;
+  if (n < P) {
+    end = seg_off[n + 1];   // static tables: read before waiting
+    ci = pi[n];
+    cj = pj[n];
+  }
+  pdl_wait();               // params come from the previous step's update
   if (step_counter && n == 0) *step_counter += 1;
   if (n >= P) return;
   PairGeo g;
-  pair_geometry(params + 9 * pi[n], params + 9 * pj[n], g);
+  pair_geometry(params + 9 * ci, params + 9 * cj, g);
   float E[9];
   essential(g, E);
-  int end = seg_off[n + 1];
   tab[3 * n + 0] = make_float4(E[0], E[1], E[2], E[3]);
   tab[3 * n + 1] = make_float4(E[4], E[5], E[6], E[7]);
   tab[3 * n + 2] = make_float4(E[8], __int_as_float(end), 0.f, 0.f);
-}
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async16_partial(void* smem, const void* gmem, int bytes) {
-  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
 struct DirectArgs {
@@ -84,51 +76,7 @@ struct DirectArgs {
   int n_wruns;
 };
 
-// shared memory per warp: [2][WP] float4 keypoints, [2][3*SEGCAP] float4
-// image-pair entries, and (weighted) [2][WP] float weights
-constexpr int kKpBuf = WP;
-constexpr int kSegBuf = 3 * SEGCAP;
-constexpr size_t kSmemPerWarp = 2 * (kKpBuf + kSegBuf) * sizeof(float4);
-constexpr size_t kSmemPerWarpW = kSmemPerWarp + 2 * WP * sizeof(float);
-
-template <bool WEIGHTED>
-__device__ __forceinline__ void issue(const DirectArgs& a, int w, int4 info, float4* kb, float4* sb,
-                                      float* wb, int lane) {
-  const int base = w * WP;
-#pragma unroll
-  for (int k = 0; k < U; ++k) {
-    int idx = lane + 32 * k;
-    if (base + idx < a.Z) cp_async16(kb + idx, a.kp + base + idx);
-  }
-  const int ne = 3 * min(info.y, SEGCAP);
-  for (int e = lane; e < ne; e += 32) cp_async16(sb + e, a.seg_tab + 3 * info.x + e);
-  if (WEIGHTED) {
-    for (int c = lane; c < WP / 4; c += 32) {
-      int p4 = base + 4 * c;
-      int bytes = 4 * min(4, a.Z - p4);
-      if (bytes > 0) cp_async16_partial(wb + 4 * c, a.wts + p4, bytes);
-    }
-  }
-  cp_async_commit();
-}
-
-__device__ __forceinline__ void load_entry(const float4* sb, const float4* seg_tab, int sl, int s,
-                                           float* E, int& end) {
-  float4 e0, e1, e2;
-  if (sl < SEGCAP) {
-    e0 = sb[3 * sl];
-    e1 = sb[3 * sl + 1];
-    e2 = sb[3 * sl + 2];
-  } else {
-    e0 = __ldg(seg_tab + 3 * s);
-    e1 = __ldg(seg_tab + 3 * s + 1);
-    e2 = __ldg(seg_tab + 3 * s + 2);
-  }
-  E[0] = e0.x; E[1] = e0.y; E[2] = e0.z; E[3] = e0.w;
-  E[4] = e1.x; E[5] = e1.y; E[6] = e1.z; E[7] = e1.w;
-  E[8] = e2.x;
-  end = __float_as_int(e2.y);
-}
+constexpr int ROWS = U;   // rows of 32 pairs per warp run
 
 __device__ __forceinline__ void store_record(float4* rec, int r, const float* v) {
   rec[3 * r + 0] = make_float4(v[0], v[1], v[2], v[3]);
@@ -136,49 +84,301 @@ __device__ __forceinline__ void store_record(float4* rec, int r, const float* v)
   rec[3 * r + 2] = make_float4(v[8], v[9], 0.f, 0.f);
 }
 
+// table entry t (local image-pair index of the warp run): lanes hold entries
+// 0..31 in registers; later entries are read from global memory
+struct Entry {
+  float E[9];
+  int end;
+};
+
+__device__ __forceinline__ void entry_uniform(const float* Ereg, int endreg, const float4* seg_tab,
+                                              int s_first, int t, Entry& o) {
+  if (t < 32) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) o.E[k] = __shfl_sync(FULL, Ereg[k], t);
+    o.end = __shfl_sync(FULL, endreg, t);
+  } else {
+    const float4 e0 = __ldg(seg_tab + 3 * (s_first + t)), e1 = __ldg(seg_tab + 3 * (s_first + t) + 1),
+                 e2 = __ldg(seg_tab + 3 * (s_first + t) + 2);
+    o.E[0] = e0.x; o.E[1] = e0.y; o.E[2] = e0.z; o.E[3] = e0.w;
+    o.E[4] = e1.x; o.E[5] = e1.y; o.E[6] = e1.z; o.E[7] = e1.w;
+    o.E[8] = e2.x;
+    o.end = __float_as_int(e2.y);
+  }
+}
+
+__device__ __forceinline__ int end_uniform(int endreg, const float4* seg_tab, int s_first, int t) {
+  if (t < 32) return __shfl_sync(FULL, endreg, t);
+  return __float_as_int(__ldg(seg_tab + 3 * (s_first + t) + 2).y);
+}
+
 // LOSS 0: rho = w |r|, rho' = w sign(r) (sign(0) = 0)
 // LOSS 1: rho = w r^2, rho'/2 = w r     (the factor 2 is applied per image pair)
 template <int LOSS, bool WEIGHTED>
-__device__ __forceinline__ void process(const DirectArgs& a, int w, int4 info, int s,
-                                        const float4* kb, const float4* sb, const float* wb,
-                                        int lane) {
+__device__ __forceinline__ void contrib(const float* E, float4 x, float wt, float* v) {
+  const float ex = fmaf(E[0], x.x, fmaf(E[1], x.y, E[2]));
+  const float ey = fmaf(E[3], x.x, fmaf(E[4], x.y, E[5]));
+  const float ez = fmaf(E[6], x.x, fmaf(E[7], x.y, E[8]));
+  const float r = fmaf(x.z, ex, fmaf(x.w, ey, ez));
+  float c, l;
+  if (LOSS == 0) {
+    c = (r > 0.f) ? 1.f : ((r < 0.f) ? -1.f : 0.f);
+    l = fabsf(r);
+  } else {
+    c = r;
+    l = r * r;
+  }
+  if (WEIGHTED) {
+    c *= wt;
+    l *= wt;
+  }
+  const float ca = c * x.x, cb = c * x.y;
+  v[0] = ca * x.z; v[1] = cb * x.z; v[2] = c * x.z;
+  v[3] = ca * x.w; v[4] = cb * x.w; v[5] = c * x.w;
+  v[6] = ca; v[7] = cb; v[8] = c; v[9] = l;
+}
+
+// MASKED: wt multiplies the pair even when unweighted (0 for lanes past Z)
+template <int LOSS, bool WEIGHTED, bool MASKED = false>
+__device__ __forceinline__ void accumulate(const float* E, float4 x, float wt, float* acc) {
+  const float ex = fmaf(E[0], x.x, fmaf(E[1], x.y, E[2]));
+  const float ey = fmaf(E[3], x.x, fmaf(E[4], x.y, E[5]));
+  const float ez = fmaf(E[6], x.x, fmaf(E[7], x.y, E[8]));
+  const float r = fmaf(x.z, ex, fmaf(x.w, ey, ez));
+  float c, l;
+  if (LOSS == 0) {
+    c = (r > 0.f) ? 1.f : ((r < 0.f) ? -1.f : 0.f);
+    l = fabsf(r);
+  } else {
+    c = r;
+    l = r * r;
+  }
+  if (WEIGHTED || MASKED) {
+    c *= wt;
+    l *= wt;
+  }
+  const float ca = c * x.x, cb = c * x.y;
+  acc[0] = fmaf(ca, x.z, acc[0]);
+  acc[1] = fmaf(cb, x.z, acc[1]);
+  acc[2] = fmaf(c, x.z, acc[2]);
+  acc[3] = fmaf(ca, x.w, acc[3]);
+  acc[4] = fmaf(cb, x.w, acc[4]);
+  acc[5] = fmaf(c, x.w, acc[5]);
+  acc[6] += ca;
+  acc[7] += cb;
+  acc[8] += c;
+  acc[9] += l;
+}
+
+__device__ __forceinline__ void warp_store(float4* rec, int r, const float* v, int lane) {
+  float s[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) s[k] = warp_sum(v[k]);
+  if (lane == 0) store_record(rec, r, s);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async16_partial(void* smem, const void* gmem, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes));
+}
+
+// shared memory per warp: two warp runs of keypoint pairs (double buffer),
+// row-major (row r, lane l at 32 r + l: conflict-free 512-B row reads), and
+// their weights
+constexpr size_t kSmemPerWarp = 2 * WP * sizeof(float4);
+constexpr size_t kSmemPerWarpW = kSmemPerWarp + 2 * WP * sizeof(float);
+
+// state of a warp run prefetched before its rows are processed
+struct RunHead {
+  int4 info;       // {first image pair, #image pairs, record base}
+  float Ereg[9];   // table entry of local image pair `lane`
+  int endreg;
+  int rs;          // image pair of this lane's first pair in the lane-contiguous split
+};
+
+template <bool WEIGHTED>
+__device__ __forceinline__ void issue_rows(const DirectArgs& a, int w, int lane, float4* kb, float* wb) {
   const int base = w * WP;
-  const int p0 = base + lane * U;
-  const int pend = min(p0 + U, a.Z);
-  int sl = s - info.x;
-  float E[9];
-  int end;
-  load_entry(sb, a.seg_tab, sl, s, E, end);
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    const int p = base + 32 * r + lane;
+    if (p < a.Z) cp_async16(kb + 32 * r + lane, a.kp + p);
+  }
+  if (WEIGHTED) {
+#pragma unroll
+    for (int k = 0; k < (WP / 4 + 31) / 32; ++k) {
+      const int c = lane + 32 * k;
+      if (c < WP / 4) {
+        const int p4 = base + 4 * c;
+        const int bytes = 4 * min(4, a.Z - p4);
+        if (bytes > 0) cp_async16_partial(wb + 4 * c, a.wts + p4, bytes);
+      }
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::);
+}
+
+__device__ __forceinline__ void load_static_head(const DirectArgs& a, int w, int lane, RunHead& h) {
+  h.info = __ldg(a.info + w);
+  h.rs = __ldg(a.run_seg + 32 * w + lane);
+}
+
+// the table entries are written by the preceding k_ea_tables launch
+__device__ __forceinline__ void load_table_head(const DirectArgs& a, int lane, RunHead& h) {
+  h.endreg = 0x7fffffff;
+  if (lane < h.info.y) {
+    const float4* e = a.seg_tab + 3 * (h.info.x + lane);
+    const float4 e0 = __ldg(e), e1 = __ldg(e + 1), e2 = __ldg(e + 2);
+    h.Ereg[0] = e0.x; h.Ereg[1] = e0.y; h.Ereg[2] = e0.z; h.Ereg[3] = e0.w;
+    h.Ereg[4] = e1.x; h.Ereg[5] = e1.y; h.Ereg[6] = e1.z; h.Ereg[7] = e1.w;
+    h.Ereg[8] = e2.x;
+    h.endreg = __float_as_int(e2.y);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) h.Ereg[k] = 0.f;
+  }
+}
+
+// Row-major processing: right for warp runs that touch one or two image pairs
+// (at most one image-pair end to cross with a warp reduction).
+template <int LOSS, bool WEIGHTED>
+__device__ __forceinline__ void process_rows(const DirectArgs& a, int w, int lane, const RunHead& h,
+                                             const float4* kb, const float* wb) {
+  const int base = w * WP;
+  const int4 info = h.info;
+  const int wend = min(base + WP, a.Z);    // one past the warp run's last pair
+  const int full_rows = (wend - base) >> 5; // rows with 32 valid pairs
+  int j = 0;                               // current local image pair (uniform)
+  Entry cur;
+  entry_uniform(h.Ereg, h.endreg, a.seg_tab, info.x, 0, cur);
   float acc[10];
 #pragma unroll
   for (int k = 0; k < 10; ++k) acc[k] = 0.f;
-  float head[10];
-#pragma unroll
-  for (int k = 0; k < 10; ++k) head[k] = 0.f;
-  bool has_head = false;
-  const int head_key = s;
 
+  int r = 0;
+  const int n_rows = (wend - base + 31) >> 5;
+  while (r < n_rows) {
+    // rows [r, r_in) lie inside the current image pair and are full: no checks
+    const int r_in = min(full_rows, max(r, (cur.end - base) >> 5));
+    if (r < r_in) {
+      int q = r;
+#pragma unroll 1
+      for (; q + 4 <= r_in; q += 4) {
 #pragma unroll
-  for (int k = 0; k < U; ++k) {
-    const int p = p0 + k;
-    if (p < pend) {
-      if (p >= end) {
-        do {
-          if (!has_head) {
-#pragma unroll
-            for (int c = 0; c < 10; ++c) head[c] = acc[c];
-            has_head = true;
-          } else {
-            store_record(a.rec, info.z + sl, acc);
-          }
-#pragma unroll
-          for (int c = 0; c < 10; ++c) acc[c] = 0.f;
-          ++s;
-          ++sl;
-          load_entry(sb, a.seg_tab, sl, s, E, end);
-        } while (p >= end);
+        for (int u = 0; u < 4; ++u)
+          accumulate<LOSS, WEIGHTED>(cur.E, kb[32 * (q + u) + lane], WEIGHTED ? wb[32 * (q + u) + lane] : 1.f, acc);
       }
+#pragma unroll 1
+      for (; q < r_in; ++q)
+        accumulate<LOSS, WEIGHTED>(cur.E, kb[32 * q + lane], WEIGHTED ? wb[32 * q + lane] : 1.f, acc);
+      r = r_in;
+      continue;
+    }
+    // row r crosses an image-pair end, or is the partial last row
+    const int row_lo = base + 32 * r;
+    const int row_hi = min(row_lo + 32, wend);
+    const bool valid = row_lo + lane < wend;
+    const float4 x = valid ? kb[32 * r + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float wt = valid ? (WEIGHTED ? wb[32 * r + lane] : 1.f) : 0.f;
+    if (row_hi <= cur.end) {
+      accumulate<LOSS, WEIGHTED, true>(cur.E, x, wt, acc);
+      ++r;
+      continue;
+    }
+    int jl_last = j;
+    while (end_uniform(h.endreg, a.seg_tab, info.x, jl_last) < row_hi) ++jl_last;
+    const int p = min(row_lo + lane, wend - 1);
+    int jl = j;
+    for (int t = j; t < jl_last; ++t) jl += (p >= end_uniform(h.endreg, a.seg_tab, info.x, t)) ? 1 : 0;
+    float El[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) El[k] = __shfl_sync(FULL, h.Ereg[k], jl & 31);   // all lanes take part
+    if (jl >= 32) {
+      const float4* e = a.seg_tab + 3 * (info.x + jl);
+      const float4 e0 = __ldg(e), e1 = __ldg(e + 1), e2 = __ldg(e + 2);
+      El[0] = e0.x; El[1] = e0.y; El[2] = e0.z; El[3] = e0.w;
+      El[4] = e1.x; El[5] = e1.y; El[6] = e1.z; El[7] = e1.w;
+      El[8] = e2.x;
+    }
+    float v[10];
+    contrib<LOSS, WEIGHTED>(El, x, wt, v);
+    if (!valid) {
+#pragma unroll
+      for (int k = 0; k < 10; ++k) v[k] = 0.f;
+    }
+    // close the current image pair
+    float t10[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) t10[k] = acc[k] + ((jl == j) ? v[k] : 0.f);
+    warp_store(a.rec, info.z + j, t10, lane);
+    // image pairs that start and end inside this row
+    for (int t = j + 1; t < jl_last; ++t) {
+#pragma unroll
+      for (int k = 0; k < 10; ++k) t10[k] = (jl == t) ? v[k] : 0.f;
+      warp_store(a.rec, info.z + t, t10, lane);
+    }
+    // open the last one
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] = (jl == jl_last) ? v[k] : 0.f;
+    j = jl_last;
+    entry_uniform(h.Ereg, h.endreg, a.seg_tab, info.x, j, cur);
+    ++r;
+  }
+  warp_store(a.rec, info.z + j, acc, lane);
+}
+
+// Lane-contiguous processing for warp runs that touch three or more image
+// pairs: lane l owns pairs [base + 15 l, base + 15 l + 15) (stride 15 float4 in
+// shared memory: conflict-free since 15 is odd).  A lane whose run crosses at
+// most one image-pair end splits it into a head part (its first image pair)
+// and a tail part with a branch-free two-accumulator loop; a lane crossing two
+// or more ends walks its pairs one by one and writes the image pairs that lie
+// wholly inside its run.  A segmented scan keyed by image pair then combines
+// the tails of consecutive lanes and absorbs heads, in fixed lane order.
+template <int LOSS, bool WEIGHTED>
+__device__ __forceinline__ void process_lanes(const DirectArgs& a, int w, int lane, const RunHead& h,
+                                              const float4* kb, const float* wb) {
+  const int base = w * WP;
+  const int4 info = h.info;
+  const int wend = min(base + WP, a.Z);
+  const int p0 = base + lane * U;
+  const int pend = min(p0 + U, wend);
+  const int j0 = h.rs - info.x;             // local image pair of the lane's first pair
+  float E0[9], E1[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    E0[k] = __shfl_sync(FULL, h.Ereg[k], j0 & 31);
+    E1[k] = __shfl_sync(FULL, h.Ereg[k], (j0 + 1) & 31);
+  }
+  const int end0 = __shfl_sync(FULL, h.endreg, j0 & 31);
+  const int end1 = __shfl_sync(FULL, h.endreg, (j0 + 1) & 31);
+  // split: pairs [p0, min(end0, pend)) are the head, the rest (if any) the tail
+  const bool one_part = pend <= end0;
+  const bool two_parts = !one_part && (j0 + 1 < 32) && (pend <= end1) && (end1 > end0);
+  const bool fast = (j0 < 32) && (one_part || two_parts);
+  float acc_h[10], acc_t[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    acc_h[k] = 0.f;
+    acc_t[k] = 0.f;
+  }
+  int head_key = j0, key = j0;
+  bool has_head = false;
+  if (fast) {
+    const int b = min(end0, pend) - p0;    // head pairs (>= 1)
+    const int n = pend - p0;               // valid pairs of this lane (may be < U at the end)
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
       const float4 x = kb[lane * U + k];
+      const bool in_head = k < b;
+      float E[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) E[q] = in_head ? E0[q] : E1[q];
+      const float wt = (k < n) ? (WEIGHTED ? wb[lane * U + k] : 1.f) : 0.f;
       const float ex = fmaf(E[0], x.x, fmaf(E[1], x.y, E[2]));
       const float ey = fmaf(E[3], x.x, fmaf(E[4], x.y, E[5]));
       const float ez = fmaf(E[6], x.x, fmaf(E[7], x.y, E[8]));
@@ -191,30 +391,63 @@ __device__ __forceinline__ void process(const DirectArgs& a, int w, int4 info, i
         c = r;
         l = r * r;
       }
-      if (WEIGHTED) {
-        const float wt = wb[lane * U + k];
-        c *= wt;
-        l *= wt;
-      }
-      const float ca = c * x.x, cb = c * x.y;
-      acc[0] = fmaf(ca, x.z, acc[0]);
-      acc[1] = fmaf(cb, x.z, acc[1]);
-      acc[2] = fmaf(c, x.z, acc[2]);
-      acc[3] = fmaf(ca, x.w, acc[3]);
-      acc[4] = fmaf(cb, x.w, acc[4]);
-      acc[5] = fmaf(c, x.w, acc[5]);
-      acc[6] += ca;
-      acc[7] += cb;
-      acc[8] += c;
-      acc[9] += l;
+      c *= wt;
+      l *= wt;
+      const float ch = in_head ? c : 0.f, ct = c - ch;
+      const float lh = in_head ? l : 0.f, lt = l - lh;
+      float ca = ch * x.x, cb = ch * x.y;
+      acc_h[0] = fmaf(ca, x.z, acc_h[0]); acc_h[1] = fmaf(cb, x.z, acc_h[1]); acc_h[2] = fmaf(ch, x.z, acc_h[2]);
+      acc_h[3] = fmaf(ca, x.w, acc_h[3]); acc_h[4] = fmaf(cb, x.w, acc_h[4]); acc_h[5] = fmaf(ch, x.w, acc_h[5]);
+      acc_h[6] += ca; acc_h[7] += cb; acc_h[8] += ch; acc_h[9] += lh;
+      ca = ct * x.x;
+      cb = ct * x.y;
+      acc_t[0] = fmaf(ca, x.z, acc_t[0]); acc_t[1] = fmaf(cb, x.z, acc_t[1]); acc_t[2] = fmaf(ct, x.z, acc_t[2]);
+      acc_t[3] = fmaf(ca, x.w, acc_t[3]); acc_t[4] = fmaf(cb, x.w, acc_t[4]); acc_t[5] = fmaf(ct, x.w, acc_t[5]);
+      acc_t[6] += ca; acc_t[7] += cb; acc_t[8] += ct; acc_t[9] += lt;
     }
+    if (two_parts) {
+      has_head = true;
+      key = j0 + 1;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 10; ++k) acc_t[k] = acc_h[k];
+    }
+  } else if (p0 < wend) {
+    // two or more image-pair ends inside the lane's run: one pair at a time
+    int s = info.x + j0, sl = j0;
+    const float4* e = a.seg_tab + 3 * s;
+    float4 e0 = __ldg(e), e1 = __ldg(e + 1), e2 = __ldg(e + 2);
+    int end = __float_as_int(e2.y);
+    for (int p = p0; p < pend; ++p) {
+      while (p >= end) {
+        if (!has_head) {
+#pragma unroll
+          for (int k = 0; k < 10; ++k) acc_h[k] = acc_t[k];
+          has_head = true;
+        } else {
+          store_record(a.rec, info.z + sl, acc_t);
+        }
+#pragma unroll
+        for (int k = 0; k < 10; ++k) acc_t[k] = 0.f;
+        ++s;
+        ++sl;
+        e = a.seg_tab + 3 * s;
+        e0 = __ldg(e);
+        e1 = __ldg(e + 1);
+        e2 = __ldg(e + 2);
+        end = __float_as_int(e2.y);
+      }
+      const float Es[9] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w, e2.x};
+      accumulate<LOSS, WEIGHTED>(Es, kb[lane * U + (p - p0)], WEIGHTED ? wb[lane * U + (p - p0)] : 1.f, acc_t);
+    }
+    key = sl;
   }
+  // lanes past the end of the data keep key = j0 (the last image pair) and zeros
 
-  // warp combine: segmented inclusive scan of the tails keyed by image pair
-  int key = s;
+  // segmented inclusive scan of the tails keyed by local image pair
   float sc[10];
 #pragma unroll
-  for (int c = 0; c < 10; ++c) sc[c] = acc[c];
+  for (int c = 0; c < 10; ++c) sc[c] = acc_t[c];
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const int ku = __shfl_up_sync(FULL, key, d);
@@ -232,12 +465,18 @@ __device__ __forceinline__ void process(const DirectArgs& a, int w, int4 info, i
   const bool absorb = (lane < 31) && (hk_next == key);
 #pragma unroll
   for (int c = 0; c < 10; ++c) {
-    const float hv = __shfl_down_sync(FULL, head[c], 1);
+    const float hv = __shfl_down_sync(FULL, acc_h[c], 1);
     if (absorb) sc[c] += hv;
   }
-  if (last_of_key) store_record(a.rec, info.z + (key - info.x), sc);
-  if (has_head && (lane == 0 || key_prev != head_key))
-    store_record(a.rec, info.z + (head_key - info.x), head);
+  if (last_of_key) store_record(a.rec, info.z + key, sc);
+  if (has_head && (lane == 0 || key_prev != head_key)) store_record(a.rec, info.z + head_key, acc_h);
+}
+
+template <int LOSS, bool WEIGHTED>
+__device__ __forceinline__ void process(const DirectArgs& a, int w, int lane, const RunHead& h,
+                                        const float4* kb, const float* wb) {
+  if (h.info.y <= 2) process_rows<LOSS, WEIGHTED>(a, w, lane, h, kb, wb);
+  else process_lanes<LOSS, WEIGHTED>(a, w, lane, h, kb, wb);
 }
 
 template <int LOSS, bool WEIGHTED>
@@ -245,43 +484,33 @@ __global__ void __launch_bounds__(WARPS * 32) k_ea_direct(DirectArgs a) {
   extern __shared__ float4 smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  constexpr size_t per_warp = (WEIGHTED ? kSmemPerWarpW : kSmemPerWarp) / sizeof(float4);
-  float4* my = smem + wib * per_warp;
-  // slot b: keypoints my + b*kKpBuf, image-pair entries my + 2*kKpBuf + b*kSegBuf,
-  // weights (float) wbase + b*WP
-  float* wbase = reinterpret_cast<float*>(my + 2 * (kKpBuf + kSegBuf));
+  float4* kb = smem + wib * 2 * WP;
+  float* wb = WEIGHTED ? reinterpret_cast<float*>(smem + WARPS * 2 * WP) + wib * 2 * WP : nullptr;
   const int stride = gridDim.x * WARPS;
   int w = blockIdx.x * WARPS + wib;
-  if (w >= a.n_wruns) return;   // uniform per warp
-
-  int4 info_cur = a.info[w];
-  int seg_cur = a.run_seg[w * 32 + lane];
-  int4 info_nxt = make_int4(0, 0, 0, 0);
-  if (w + stride < a.n_wruns) info_nxt = a.info[w + stride];
-  issue<WEIGHTED>(a, w, info_cur, my, my + 2 * kKpBuf, wbase, lane);
-
+  if (w >= a.n_wruns) return;              // uniform per warp
+  pdl_trigger();
+  RunHead head;
+  load_static_head(a, w, lane, head);
+  issue_rows<WEIGHTED>(a, w, lane, kb, wb);   // the keypoints do not depend on the predecessor
+  pdl_wait();
+  load_table_head(a, lane, head);
   for (int it = 0; w < a.n_wruns; ++it, w += stride) {
     const int cur = it & 1;
     const int wn = w + stride;
-    int seg_nxt = 0;
-    int4 info_nn = make_int4(0, 0, 0, 0);
+    RunHead next;
     if (wn < a.n_wruns) {
-      seg_nxt = a.run_seg[wn * 32 + lane];
-      if (wn + stride < a.n_wruns) info_nn = a.info[wn + stride];
-      const int nb = cur ^ 1;
-      issue<WEIGHTED>(a, wn, info_nxt, my + nb * kKpBuf, my + 2 * kKpBuf + nb * kSegBuf,
-                      wbase + nb * WP, lane);
-      cp_async_wait<1>();
+      load_static_head(a, wn, lane, next);
+      load_table_head(a, lane, next);
+      issue_rows<WEIGHTED>(a, wn, lane, kb + (cur ^ 1) * WP, WEIGHTED ? wb + (cur ^ 1) * WP : nullptr);
+      asm volatile("cp.async.wait_group 1;\n" ::);
     } else {
-      cp_async_wait<0>();
+      asm volatile("cp.async.wait_group 0;\n" ::);
     }
     __syncwarp();
-    process<LOSS, WEIGHTED>(a, w, info_cur, seg_cur, my + cur * kKpBuf,
-                            my + 2 * kKpBuf + cur * kSegBuf, wbase + cur * WP, lane);
-    __syncwarp();
-    info_cur = info_nxt;
-    info_nxt = info_nn;
-    seg_cur = seg_nxt;
+    process<LOSS, WEIGHTED>(a, w, lane, head, kb + cur * WP, WEIGHTED ? wb + cur * WP : nullptr);
+    __syncwarp();   // this buffer is refilled two warp runs later
+    head = next;
   }
 }
 
@@ -292,8 +521,14 @@ __global__ void k_ea_segments(const float4* __restrict__ rec, const int* __restr
                               const int* __restrict__ pj, int P, float inv_z,
                               float* __restrict__ seg_grad, float* __restrict__ seg_loss) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= P) return;
+  pdl_trigger();
+  if (n >= P) {
+    pdl_wait();
+    return;
+  }
   const int r0 = seg_rec[2 * n], cnt = seg_rec[2 * n + 1];
+  const int ci = pi[n], cj = pj[n];
+  pdl_wait();               // records come from k_ea_direct
   float* out = seg_grad + (size_t)kSegGradEa * n;
   if (cnt == 0) {
     for (int k = 0; k < kSegGradEa; ++k) out[k] = 0.f;
@@ -312,7 +547,7 @@ __global__ void k_ea_segments(const float4* __restrict__ rec, const int* __restr
   for (int k = 0; k < 9; ++k) G[k] *= gs;
   seg_loss[n] = G[9] * inv_z;
   PairGeo g;
-  pair_geometry(params + 9 * pi[n], params + 9 * pj[n], g);
+  pair_geometry(params + 9 * ci, params + 9 * cj, g);
   float o[kSegGradEa];
   pair_backward(g, G, o);
   for (int k = 0; k < kSegGradEa; ++k) out[k] = o[k];
@@ -322,7 +557,8 @@ __global__ void k_ea_segments(const float4* __restrict__ rec, const int* __restr
 
 void launch_ea_tables(const float* params, const int* pi, const int* pj, const int* seg_off,
                       int P, float4* seg_tab, int* step_counter, cudaStream_t s) {
-  k_ea_tables<<<(P + 127) / 128, 128, 0, s>>>(params, pi, pj, seg_off, P, seg_tab, step_counter);
+  launch_pdl(k_ea_tables, dim3((P + 127) / 128), dim3(128), 0, s, params, pi, pj, seg_off, P, seg_tab,
+             step_counter);
 }
 
 template <int LOSS, bool WEIGHTED>
@@ -339,16 +575,14 @@ static void launch_direct_t(const fm_problem* pr, const float* weights, cudaStre
   const size_t smem = WARPS * (WEIGHTED ? kSmemPerWarpW : kSmemPerWarp);
   static int per_sm = 0;   // resident CTAs per SM (one device per process)
   if (per_sm == 0) {
-    cudaFuncSetAttribute(k_ea_direct<LOSS, WEIGHTED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ea_direct<LOSS, WEIGHTED>,
-                                                  WARPS * 32, smem);
+    cudaFuncSetAttribute(k_ea_direct<LOSS, WEIGHTED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ea_direct<LOSS, WEIGHTED>, WARPS * 32, smem);
     if (per_sm < 1) per_sm = 1;
   }
   int ctas = (pr->n_wruns + WARPS - 1) / WARPS;
   int cap = per_sm * pr->sm_count;
   if (ctas > cap) ctas = cap;
-  k_ea_direct<LOSS, WEIGHTED><<<ctas, WARPS * 32, smem, s>>>(a);
+  launch_pdl(k_ea_direct<LOSS, WEIGHTED>, dim3(ctas), dim3(WARPS * 32), smem, s, a);
 }
 
 void launch_ea_direct(const fm_problem* pr, const float* weights, int loss, cudaStream_t s) {
@@ -366,13 +600,13 @@ void launch_ea_segments(const fm_problem* pr, const float* params, int loss, flo
                         cudaStream_t s) {
   const int P = pr->P;
   if (loss == FM_EA_L1)
-    k_ea_segments<0><<<(P + 127) / 128, 128, 0, s>>>(pr->rec, pr->seg_rec, params, pr->pair_i,
-                                                      pr->pair_j, P, inv_z, pr->seg_grad,
-                                                      pr->seg_loss);
+    launch_pdl(k_ea_segments<0>, dim3((P + 127) / 128), dim3(128), 0, s, (const float4*)pr->rec,
+               (const int*)pr->seg_rec, params, (const int*)pr->pair_i, (const int*)pr->pair_j, P, inv_z,
+               pr->seg_grad, pr->seg_loss);
   else
-    k_ea_segments<1><<<(P + 127) / 128, 128, 0, s>>>(pr->rec, pr->seg_rec, params, pr->pair_i,
-                                                      pr->pair_j, P, inv_z, pr->seg_grad,
-                                                      pr->seg_loss);
+    launch_pdl(k_ea_segments<1>, dim3((P + 127) / 128), dim3(128), 0, s, (const float4*)pr->rec,
+               (const int*)pr->seg_rec, params, (const int*)pr->pair_i, (const int*)pr->pair_j, P, inv_z,
+               pr->seg_grad, pr->seg_loss);
 }
 
 }  // namespace fm

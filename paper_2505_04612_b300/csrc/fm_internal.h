@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/fastmap.h"
@@ -13,8 +14,7 @@ namespace fm {
 // ---------------------------------------------------------------- constants
 constexpr int kEaPairsPerLane = 15;              // U: keypoint pairs per lane (odd)
 constexpr int kEaWarpPairs = 32 * kEaPairsPerLane;  // keypoint pairs per warp run
-constexpr int kEaSegCap = 32;                    // image pairs per warp run staged in smem
-constexpr int kEaWarpsPerCta = 4;
+constexpr int kEaWarpsPerCta = 2;
 constexpr int kSegGradEa = 24;                   // dR_i, dt_i, dR_j, dt_j
 constexpr int kSegGradRot = 18;                  // dR_i, dR_j
 constexpr int kSegGradTrn = 6;                   // do_i, do_j
@@ -138,6 +138,23 @@ struct fm_problem {
 
 namespace fm {
 
+// Launch with programmatic stream serialisation (see pdl_wait / pdl_trigger).
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // message returned by fm_last_error(NULL) on the calling thread
 void set_thread_error(const std::string& msg);
 
@@ -205,6 +222,8 @@ struct CamUpdate {
   const int* step;
   float lr, b1, b2, eps;
   int N, P, runs;
+  const float* seg_loss;   // [runs][P] per-image-pair loss terms, or null
+  float* loss_out;         // [runs] fixed-order sum of seg_loss, or null
 };
 void launch_cam_update(int stage, const CamUpdate& u, cudaStream_t s);
 void launch_sum_fixed(const float* x, int n, int runs, float* out, cudaStream_t s);
