@@ -228,6 +228,118 @@ fm_status fm_loss_grad(fm_problem* problem, fm_stage stage, const float* params,
 fm_status fm_step(fm_problem* problem, fm_stage stage, const fm_adam_opts* opts,
                   int32_t n_iters, float* loss);
 
+/* ------------------------------------------------------------- setup steps */
+
+/* Rotation initialisation (Appendix "Global Rotation / Initialization",
+ * Eqs. 10-14): the first columns of all world-to-camera rotations minimise
+ * sum ||c1_j - R^{i->j} c1_i||^2 (Eq. 12), the second columns the same plus
+ * the orthogonality penalty (Eq. 13); each is the eigenvector of the smallest
+ * eigenvalue of its sparse quadratic form, found here by n_iters steps of
+ * power iteration on I - A/sigma; columns are normalised per camera,
+ * Gram-Schmidt orthogonalised, and c3 = c1 x c2 (Eq. 14).  Writes the
+ * rotation-stage parameters (6D = (c1, c2)) and resets their Adam state.
+ * Needs rel_R.  The result is defined up to a global rotation (a gauge). */
+fm_status fm_rotation_init(fm_problem* problem, int32_t n_iters);
+
+/* Relative translation re-estimation (Appendix "Relative Translation"): with
+ * R^{i->j} = R_j R_i^T from the rotation-stage parameters, the unit
+ * translation of every image pair minimising the mean |x~2^T [t]_x R x~1|
+ * over a Fibonacci lattice of 4096 points on the hemisphere refined by two
+ * 1024-point lattices on spherical caps (radius twice the previous spacing),
+ * sign by cheirality (+t on ties).  Replaces rel_t.  err_out: [P] mean error
+ * of the chosen direction (host or device as flagged), or NULL. */
+fm_status fm_relative_translations(fm_problem* problem, float* err_out, int32_t err_on_device);
+
+/* Copies the current relative rotations [P*9] / translations [P*3]; either
+ * may be NULL.  Synchronises for host outputs. */
+fm_status fm_get_rel_poses(fm_problem* problem, float* rel_R, float* rel_t, int32_t out_on_device);
+
+/* Random initial centres for every translation run (Sec. 3.3: the objective
+ * is optimised from random starts): value k of the [m*N*3] array is
+ * fmix32(k * 0x9E3779B9 + seed) >> 8, scaled by 2^-23, minus 1 (uniform in
+ * [-1, 1); fmix32 is the MurmurHash3 32-bit finaliser).  Resets Adam. */
+fm_status fm_translation_random_init(fm_problem* problem, uint32_t seed);
+
+/* Merges the translation runs (Appendix "Multiple Initializations"): each run
+ * is moved to zero centroid and unit mean norm, and every camera takes the
+ * run with the lowest mean loss over its image pairs (lowest run on ties).
+ * Afterwards the problem has one run holding the merged centres (Adam reset).
+ * best_run_out: [N] host array of the chosen run per camera, or NULL.
+ * Synchronises. */
+fm_status fm_translation_merge(fm_problem* problem, int32_t* best_run_out);
+
+/* Epipolar-stage parameters from the rotation stage (6D) and the merged
+ * centres o: t_i = -R_i o_i.  Resets Adam and the compact matrices. */
+fm_status fm_epipolar_init_from_stages(fm_problem* problem);
+
+/* Sparse reconstruction (Appendix "Sparse Reconstruction") at the
+ * epipolar-stage parameters: every keypoint pair of a track is triangulated
+ * (two-ray midpoint), the points of a track are averaged, a keypoint is an
+ * inlier if its reprojection error is <= max_err_px, and a point is valid if
+ * its inlier keypoints span >= 3 cameras and its largest triangulation angle
+ * (at the point, between two inlier keypoints' camera centres) is >=
+ * min_angle_deg.  Needs kp_track at creation; tracks are the ids 0..T-1.
+ * Outputs [T*3], [T], [T] (any may be NULL; host or device as flagged) and T. */
+typedef struct {
+  float max_err_px;
+  float min_angle_deg;
+} fm_tri_opts;
+
+fm_status fm_triangulate(fm_problem* problem, const fm_tri_opts* opts, float* points,
+                         int32_t* valid, int32_t* n_inlier_cams, int32_t out_on_device,
+                         int32_t* n_tracks);
+
+/* -------------------------------------------------------- end-to-end solve
+ * The paper fixes no learning rate, iteration count or threshold; the
+ * defaults of fm_solve_opts_default are this library's choices. */
+typedef struct {
+  int32_t rot_init_iters;     /* power iterations per column (2000) */
+  int32_t rot_iters;          /* Adam steps on the rotation loss (2000) */
+  float rot_lr;               /* (1e-3) */
+  int32_t reestimate_rel_t;   /* 1: grid search; 0: keep the given rel_t (1) */
+  int32_t trn_runs;           /* translation runs from random starts (4) */
+  int32_t trn_iters;          /* Adam steps per run (2000) */
+  float trn_lr;               /* (1e-2) */
+  int32_t trn_final_iters;    /* after the merge (1000) */
+  uint32_t seed;              /* of the random starts (0) */
+  int32_t ea_rounds;          /* IRLS / filtering rounds (5) */
+  int32_t ea_iters;           /* Adam steps per round on the compact form (500) */
+  float ea_lr;                /* (1e-4) */
+  float ea_tau0;              /* first filtering threshold, calibrated units (0.05) */
+  float ea_tau_min;           /* halved each round down to this (0.005) */
+  float ea_delta;             /* IRLS weight floor (1e-5) */
+  float tri_max_err_px;       /* (4) */
+  float tri_min_angle_deg;    /* (2) */
+  float beta1, beta2, eps;    /* Adam (0.9, 0.999, 1e-8) */
+} fm_solve_opts;
+
+void fm_solve_opts_default(fm_solve_opts* opts);
+
+/* Caller-owned host buffers for the solution, and scalars filled in. */
+typedef struct {
+  float* R;                   /* [N*9] world-to-camera rotations (required) */
+  float* t;                   /* [N*3] world-to-camera translations (required) */
+  float* points;              /* [T*3] or NULL (needs kp_track) */
+  int32_t* point_valid;       /* [T] or NULL */
+  int32_t n_tracks;           /* out: T */
+  int32_t n_points_valid;     /* out */
+  float loss_rotation;        /* out: final losses of the three stages */
+  float loss_translation;
+  float loss_epipolar;
+  int64_t n_kept;             /* out: keypoint pairs kept by the last filtering */
+} fm_result;
+
+/* Runs the whole first-order pipeline: fm_rotation_init, Adam on the rotation
+ * loss, fm_relative_translations (if asked), trn_runs translation runs from
+ * fm_translation_random_init, fm_translation_merge, a final translation run,
+ * fm_epipolar_init_from_stages, ea_rounds of {fm_ea_reweight(tau_k, delta),
+ * Adam on FM_EA_COMPACT} with tau_k = max(tau0 / 2^k, tau_min), and
+ * triangulation.  Each Adam loop runs in four equal phases with the learning
+ * rate scaled by 1, 0.3, 0.1, 0.03.  Needs rel_R (and rel_t when
+ * reestimate_rel_t is 0).  The solution is defined up to a similarity of the
+ * world frame.  Synchronises. */
+fm_status fm_solve(fm_problem* problem, const fm_solve_opts* opts, fm_result* result);
+
 /* ---------------------------------------------------------- observability
  * (no counterpart in the paper, which times whole stages by wall clock) */
 

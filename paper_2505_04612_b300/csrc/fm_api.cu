@@ -16,7 +16,8 @@ void set_thread_error(const std::string& msg) { g_create_error = msg; }
 const char* const kKernelNames[kKCount] = {
     "k_calibrate", "k_seg_offsets", "k_run_tables", "k_ea_tables", "k_ea_direct",
     "k_ea_segments", "k_rot_pairs", "k_trn_targets", "k_trn_pairs", "k_cam", "k_sum_fixed",
-    "k_ea_reweight", "k_w_build", "k_ea_compact"};
+    "k_ea_reweight", "k_w_build", "k_ea_compact", "k_mart_iter", "k_reltrans", "k_merge",
+    "k_triangulate"};
 }
 
 namespace {
@@ -163,6 +164,8 @@ void release(fm_problem* pr) {
   dfree(pr->loss_hist);
   dfree(pr->W);
   dfree(pr->d_kept);
+  dfree(pr->kp_seg); dfree(pr->track_off); dfree(pr->track_idx);
+  dfree(pr->merge_buf); dfree(pr->best_run);
   drain_timing(pr, false);
   for (cudaEvent_t e : pr->event_pool) cudaEventDestroy(e);
   pr->event_pool.clear();
@@ -213,6 +216,7 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   // camera -> incident image pairs, ordered by image pair (deterministic sums)
   std::vector<int> coff(N + 1, 0), cseg(2 * (size_t)P);
   for (int n = 0; n < P; ++n) { coff[hi[n] + 1]++; coff[hj[n] + 1]++; }
+  for (int c = 0; c < N; ++c) pr->max_degree = std::max(pr->max_degree, coff[c + 1]);
   for (int c = 0; c < N; ++c) coff[c + 1] += coff[c];
   {
     std::vector<int> fill(coff.begin(), coff.end() - 1);
@@ -276,6 +280,14 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   }
   FM_LAUNCHED(pr);
   fm_status st = check_err_bits(pr);
+  if (st == FM_OK && d->kp_track && Z > 0) {
+    // triangulation needs the image pair of every keypoint pair and the tracks
+    FM_ALLOC(pr, pr->kp_seg, Z);
+    FM_CUDA(pr, cudaMemcpyAsync(pr->kp_seg, kpp, sizeof(int) * Z, cudaMemcpyDeviceToDevice, s));
+    int T = 0;
+    FM_CUDA(pr, fm::build_track_table(pr, &T));
+    st = check_err_bits(pr);
+  }
   if (tmp1) { cudaFree(tmp1); pr->device_bytes -= (int64_t)sizeof(float) * 2 * Z; }
   if (tmp2) { cudaFree(tmp2); pr->device_bytes -= (int64_t)sizeof(float) * 2 * Z; }
   if (tmpp) { cudaFree(tmpp); pr->device_bytes -= (int64_t)sizeof(int) * Z; }
@@ -336,6 +348,8 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   FM_ALLOC(pr, pr->d_loss, 1);
   FM_ALLOC(pr, pr->W, 64 * (size_t)P);
   FM_ALLOC(pr, pr->d_kept, 1);
+  FM_ALLOC(pr, pr->merge_buf, 3 * (size_t)N + 4 * 64);
+  FM_ALLOC(pr, pr->best_run, (size_t)N);
   FM_CUDA(pr, cudaMallocHost((void**)&pr->h_loss, sizeof(float)));
   pr->ea_inv_z = Z > 0 ? (float)(1.0 / (double)Z) : 0.f;
   if (d->rel_R) {
@@ -769,6 +783,265 @@ fm_status fm_step(fm_problem* pr, fm_stage st, const fm_adam_opts* opts, int32_t
     FM_CUDA(pr, cudaMemcpyAsync(pr->h_loss, pr->d_loss, sizeof(float) * runs, cudaMemcpyDeviceToHost, pr->stream));
     FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
     std::memcpy(loss, pr->h_loss, sizeof(float) * runs);
+  }
+  return FM_OK;
+}
+
+fm_status fm_rotation_init(fm_problem* pr, int32_t n_iters) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (n_iters < 1) return fail(pr, FM_ERR_INVALID_ARG, "n_iters must be >= 1");
+  if (!pr->rel_R_set) return fail(pr, FM_ERR_STATE, "rotation initialisation needs relative rotations (rel_R)");
+  cudaStream_t s = pr->stream;
+  const int N = pr->N;
+  float* x = pr->scratch_params;           // [3N]
+  float* y = pr->scratch_params + 3 * N;   // [3N]
+  float* c1 = pr->scratch_grad;            // [3N]
+  // lambda_max(A) <= 2 max degree (Gershgorin); B = A/|P| + diag(c1 c1^T)/|I|
+  const float sigma1 = 2.f * (float)std::max(pr->max_degree, 1);
+  const float sigma2 = sigma1 / (float)pr->P + 1.f / (float)N;
+  for (int col = 0; col < 2; ++col) {
+    fm::launch_hash_fill(x, 3 * N, col == 0 ? 0x1234567u : 0x89ABCDEu, s);
+    fm::launch_scale_to_unit(x, 3 * N, s);
+    for (int it = 0; it < n_iters; ++it) {
+      {
+        Timed t(pr, fm::kKMartIter);
+        if (col == 0) fm::launch_mart_iter(pr, x, nullptr, y, sigma1, 1.f, s);
+        else fm::launch_mart_iter(pr, x, c1, y, sigma2, (float)pr->P, s);
+      }
+      std::swap(x, y);
+      if ((it & 31) == 31) fm::launch_scale_to_unit(x, 3 * N, s);
+    }
+    FM_LAUNCHED(pr);
+    if (col == 0) {
+      fm::launch_normalise3(x, N, s);
+      FM_CUDA(pr, cudaMemcpyAsync(c1, x, sizeof(float) * 3 * N, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  fm::launch_mart_finish(c1, x, N, pr->rot_params, s);
+  FM_LAUNCHED(pr);
+  fm_status e = reset_adam(pr, pr->rot_adam, 6 * (size_t)N);
+  if (e != FM_OK) return e;
+  pr->rot_params_set = true;
+  pr->trn_target_valid = false;
+  return FM_OK;
+}
+
+fm_status fm_relative_translations(fm_problem* pr, float* err_out, int32_t err_on_device) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!pr->rot_params_set) return fail(pr, FM_ERR_STATE, "the grid search needs rotation-stage parameters");
+  float* err = nullptr;
+  if (err_out) err = err_on_device ? err_out : pr->seg_loss;
+  {
+    Timed t(pr, fm::kKRelTrans);
+    fm::launch_reltrans(pr, pr->rot_params, pr->rel_t, err, pr->stream);
+  }
+  FM_LAUNCHED(pr);
+  pr->rel_t_set = true;
+  pr->trn_target_valid = false;
+  if (err_out && !err_on_device) {
+    FM_CUDA(pr, cudaMemcpyAsync(err_out, err, sizeof(float) * pr->P, cudaMemcpyDeviceToHost, pr->stream));
+    FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+  }
+  return FM_OK;
+}
+
+fm_status fm_get_rel_poses(fm_problem* pr, float* rel_R, float* rel_t, int32_t out_on_device) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  const cudaMemcpyKind k = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (rel_R) {
+    if (!pr->rel_R_set) return fail(pr, FM_ERR_STATE, "no relative rotations are set");
+    FM_CUDA(pr, cudaMemcpyAsync(rel_R, pr->rel_R, sizeof(float) * 9 * pr->P, k, pr->stream));
+  }
+  if (rel_t) {
+    if (!pr->rel_t_set) return fail(pr, FM_ERR_STATE, "no relative translations are set");
+    FM_CUDA(pr, cudaMemcpyAsync(rel_t, pr->rel_t, sizeof(float) * 3 * pr->P, k, pr->stream));
+  }
+  if (!out_on_device) FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+  return FM_OK;
+}
+
+fm_status fm_translation_random_init(fm_problem* pr, uint32_t seed) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  const size_t n = 3 * (size_t)pr->N * pr->trn_runs;
+  fm::launch_hash_fill(pr->trn_params, (int)n, seed, pr->stream);
+  FM_LAUNCHED(pr);
+  fm_status e = reset_adam(pr, pr->trn_adam, n);
+  if (e != FM_OK) return e;
+  pr->trn_params_set = true;
+  return FM_OK;
+}
+
+fm_status fm_translation_merge(fm_problem* pr, int32_t* best_run_out) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!pr->trn_params_set) return fail(pr, FM_ERR_STATE, "the translation-stage parameters have not been set");
+  fm_status e = ensure_targets(pr);
+  if (e != FM_OK) return e;
+  cudaStream_t s = pr->stream;
+  const int N = pr->N, runs = pr->trn_runs;
+  float* merged = pr->merge_buf;
+  float* stats = pr->merge_buf + 3 * N;
+  {
+    Timed t(pr, fm::kKMerge);
+    fm::launch_merge(pr, pr->trn_params, runs, stats, merged, pr->best_run, s);
+  }
+  FM_LAUNCHED(pr);
+  if (best_run_out) {
+    FM_CUDA(pr, cudaMemcpyAsync(best_run_out, pr->best_run, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
+  }
+  FM_CUDA(pr, cudaStreamSynchronize(s));
+  if (runs != 1) {
+    e = resize_runs(pr, 1);
+    if (e != FM_OK) return e;
+  }
+  FM_CUDA(pr, cudaMemcpyAsync(pr->trn_params, merged, sizeof(float) * 3 * N, cudaMemcpyDeviceToDevice, s));
+  e = reset_adam(pr, pr->trn_adam, 3 * (size_t)N);
+  if (e != FM_OK) return e;
+  pr->trn_params_set = true;
+  FM_CUDA(pr, cudaStreamSynchronize(s));
+  return FM_OK;
+}
+
+fm_status fm_epipolar_init_from_stages(fm_problem* pr) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!pr->rot_params_set || !pr->trn_params_set)
+    return fail(pr, FM_ERR_STATE, "needs rotation- and translation-stage parameters");
+  if (pr->trn_runs != 1) return fail(pr, FM_ERR_STATE, "merge the translation runs first");
+  fm::launch_ea_from_stages(pr->rot_params, pr->trn_params, pr->N, pr->ea_params, pr->stream);
+  FM_LAUNCHED(pr);
+  fm_status e = reset_adam(pr, pr->ea_adam, 9 * (size_t)pr->N);
+  if (e != FM_OK) return e;
+  pr->ea_params_set = true;
+  pr->W_valid = false;
+  return FM_OK;
+}
+
+fm_status fm_triangulate(fm_problem* pr, const fm_tri_opts* opts, float* points, int32_t* valid,
+                         int32_t* n_inlier_cams, int32_t out_on_device, int32_t* n_tracks) {
+  if (!pr || !opts) return FM_ERR_INVALID_ARG;
+  if (!pr->track_idx) return fail(pr, FM_ERR_STATE, "triangulation needs kp_track at creation");
+  if (!pr->ea_params_set) return fail(pr, FM_ERR_STATE, "the epipolar-stage parameters have not been set");
+  const int T = pr->n_tracks;
+  if (n_tracks) *n_tracks = T;
+  if (T <= 0) return FM_OK;
+  cudaStream_t s = pr->stream;
+  float* d_pts = nullptr;
+  int* d_valid = nullptr;
+  int* d_ncam = nullptr;
+  FM_ALLOC(pr, d_pts, 3 * (size_t)T);
+  FM_ALLOC(pr, d_valid, (size_t)T);
+  FM_ALLOC(pr, d_ncam, (size_t)T);
+  {
+    Timed t(pr, fm::kKTriangulate);
+    fm::launch_triangulate(pr, pr->ea_params, opts->max_err_px, opts->min_angle_deg * 3.14159265358979f / 180.f,
+                           d_pts, d_valid, d_ncam, s);
+  }
+  cudaError_t le = cudaGetLastError();
+  const cudaMemcpyKind k = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (le == cudaSuccess && points) le = cudaMemcpyAsync(points, d_pts, sizeof(float) * 3 * T, k, s);
+  if (le == cudaSuccess && valid) le = cudaMemcpyAsync(valid, d_valid, sizeof(int) * T, k, s);
+  if (le == cudaSuccess && n_inlier_cams) le = cudaMemcpyAsync(n_inlier_cams, d_ncam, sizeof(int) * T, k, s);
+  if (le == cudaSuccess) le = cudaStreamSynchronize(s);
+  cudaFree(d_pts);
+  cudaFree(d_valid);
+  cudaFree(d_ncam);
+  pr->device_bytes -= (int64_t)(sizeof(float) * 3 + 2 * sizeof(int)) * T;
+  if (le != cudaSuccess) return fail(pr, FM_ERR_CUDA, std::string("triangulation: ") + cudaGetErrorString(le));
+  return FM_OK;
+}
+
+void fm_solve_opts_default(fm_solve_opts* o) {
+  if (!o) return;
+  o->rot_init_iters = 2000;
+  o->rot_iters = 2000;
+  o->rot_lr = 1e-3f;
+  o->reestimate_rel_t = 1;
+  o->trn_runs = 4;
+  o->trn_iters = 2000;
+  o->trn_lr = 1e-2f;
+  o->trn_final_iters = 1000;
+  o->seed = 0;
+  o->ea_rounds = 5;
+  o->ea_iters = 500;
+  o->ea_lr = 1e-4f;
+  o->ea_tau0 = 0.05f;
+  o->ea_tau_min = 0.005f;
+  o->ea_delta = 1e-5f;
+  o->tri_max_err_px = 4.f;
+  o->tri_min_angle_deg = 2.f;
+  o->beta1 = 0.9f;
+  o->beta2 = 0.999f;
+  o->eps = 1e-8f;
+}
+
+// Adam steps in four equal phases with the learning rate scaled by
+// 1, 0.3, 0.1, 0.03 (the moments carry over between phases)
+static fm_status stepped(fm_problem* pr, fm_stage st, const fm_solve_opts* o, float lr, int iters, float* loss) {
+  static const float kPhase[4] = {1.f, 0.3f, 0.1f, 0.03f};
+  const int per = iters / 4;
+  for (int ph = 0; ph < 4; ++ph) {
+    const int n = (ph < 3) ? per : iters - 3 * per;
+    fm_adam_opts a{lr * kPhase[ph], o->beta1, o->beta2, o->eps};
+    fm_status e = fm_step(pr, st, &a, n, (ph == 3) ? loss : nullptr);
+    if (e != FM_OK) return e;
+  }
+  return FM_OK;
+}
+
+fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
+  if (!pr || !o || !res) return FM_ERR_INVALID_ARG;
+  if (!res->R || !res->t) return fail(pr, FM_ERR_INVALID_ARG, "result R and t buffers are required");
+  if (o->trn_runs < 1 || o->trn_runs > 64 || o->ea_rounds < 0 || o->rot_init_iters < 1)
+    return fail(pr, FM_ERR_INVALID_ARG, "invalid solve options");
+  fm_status e;
+  float L = 0.f;
+  // 1-2. rotations
+  if ((e = fm_rotation_init(pr, o->rot_init_iters)) != FM_OK) return e;
+  if ((e = stepped(pr, FM_STAGE_ROTATION, o, o->rot_lr, o->rot_iters, &L)) != FM_OK) return e;
+  res->loss_rotation = L;
+  // 3. relative translations
+  if (o->reestimate_rel_t) {
+    if ((e = fm_relative_translations(pr, nullptr, 0)) != FM_OK) return e;
+  } else if (!pr->rel_t_set) {
+    return fail(pr, FM_ERR_STATE, "rel_t is needed when reestimate_rel_t is 0");
+  }
+  // 4. translation runs, merge, final run
+  if ((e = fm_translation_set_runs(pr, o->trn_runs)) != FM_OK) return e;
+  if ((e = fm_translation_random_init(pr, o->seed)) != FM_OK) return e;
+  std::vector<float> run_loss(o->trn_runs);
+  if ((e = stepped(pr, FM_STAGE_TRANSLATION, o, o->trn_lr, o->trn_iters, run_loss.data())) != FM_OK) return e;
+  if ((e = fm_translation_merge(pr, nullptr)) != FM_OK) return e;
+  if ((e = stepped(pr, FM_STAGE_TRANSLATION, o, o->trn_lr, o->trn_final_iters, &L)) != FM_OK) return e;
+  res->loss_translation = L;
+  // 5. epipolar adjustment: IRLS / filtering rounds on the compact form
+  if ((e = fm_epipolar_init_from_stages(pr)) != FM_OK) return e;
+  if ((e = fm_ea_set_loss(pr, FM_EA_COMPACT)) != FM_OK) return e;
+  res->loss_epipolar = 0.f;
+  res->n_kept = pr->Z;
+  for (int k = 0; k < o->ea_rounds; ++k) {
+    const float tau = std::max(o->ea_tau0 * std::pow(0.5f, (float)k), o->ea_tau_min);
+    int64_t kept = 0;
+    if ((e = fm_ea_reweight(pr, tau, o->ea_delta, 1, &kept)) != FM_OK) return e;
+    res->n_kept = kept;
+    if ((e = stepped(pr, FM_STAGE_EPIPOLAR, o, o->ea_lr, o->ea_iters, &L)) != FM_OK) return e;
+    res->loss_epipolar = L;
+  }
+  // outputs
+  float* dR = pr->scratch_params;     // [9N]
+  float* dt = pr->scratch_grad;       // [3N]
+  fm::launch_ea_to_Rt(pr->ea_params, pr->N, dR, dt, pr->stream);
+  FM_LAUNCHED(pr);
+  FM_CUDA(pr, cudaMemcpyAsync(res->R, dR, sizeof(float) * 9 * pr->N, cudaMemcpyDeviceToHost, pr->stream));
+  FM_CUDA(pr, cudaMemcpyAsync(res->t, dt, sizeof(float) * 3 * pr->N, cudaMemcpyDeviceToHost, pr->stream));
+  FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+  res->n_tracks = 0;
+  res->n_points_valid = 0;
+  if (pr->track_idx && (res->points || res->point_valid)) {
+    fm_tri_opts to{o->tri_max_err_px, o->tri_min_angle_deg};
+    int32_t T = 0;
+    if ((e = fm_triangulate(pr, &to, res->points, res->point_valid, nullptr, 0, &T)) != FM_OK) return e;
+    res->n_tracks = T;
+    if (res->point_valid)
+      for (int k = 0; k < T; ++k) res->n_points_valid += res->point_valid[k] != 0;
   }
   return FM_OK;
 }

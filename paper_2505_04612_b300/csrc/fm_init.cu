@@ -110,6 +110,23 @@ __global__ void k_hash_fill(float* __restrict__ x, int n, unsigned salt) {
   x[k] = (float)(z >> 8) * (1.0f / 8388608.0f) - 1.0f;
 }
 
+// x <- x / |x| over the whole vector (one CTA, fixed-order sum), so that the
+// power iteration neither underflows nor overflows
+__global__ void k_scale_to_unit(float* __restrict__ x, int n) {
+  __shared__ float part[256];
+  float s = 0.f;
+  for (int k = threadIdx.x; k < n; k += 256) s += x[k] * x[k];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int d = 128; d > 0; d >>= 1) {
+    if ((int)threadIdx.x < d) part[threadIdx.x] += part[threadIdx.x + d];
+    __syncthreads();
+  }
+  const float tot = part[0];
+  const float inv = tot > 0.f ? rsqrtf(tot) : 0.f;
+  for (int k = threadIdx.x; k < n; k += 256) x[k] *= inv;
+}
+
 // ---------------------------------------------------------------- merge
 // Per run: centroid and mean norm of the centres (fixed order, one CTA per run).
 __global__ void k_run_stats(const float* __restrict__ o, int N, float* __restrict__ stats) {
@@ -203,6 +220,7 @@ void launch_mart_iter(const fm_problem* pr, const float* x, const float* c1, flo
                                               pr->rel_R, x, c1, y, pr->N, 1.f / sigma, 1.f / scale_p,
                                               1.f / (float)pr->N);
 }
+void launch_scale_to_unit(float* x, int n, cudaStream_t s) { k_scale_to_unit<<<1, 256, 0, s>>>(x, n); }
 void launch_normalise3(float* x, int N, cudaStream_t s) {
   k_normalise3<<<(N + 127) / 128, 128, 0, s>>>(x, N);
 }

@@ -63,6 +63,9 @@ struct fm_problem {
   int* cam_seg_off = nullptr;    // [N+1]
   int* cam_seg = nullptr;        // [2P] image pair | role << 31 (role 1: camera is j)
   int n_empty = 0;
+  int max_degree = 0;            // largest number of image pairs of one camera
+  float* merge_buf = nullptr;    // [3N + 4*64] merged centres and per-run statistics
+  int* best_run = nullptr;       // [N]
 
   // keypoints
   float4* kp = nullptr;          // [Z] calibrated (x1, y1, x2, y2)
@@ -198,6 +201,9 @@ void launch_reltrans(const fm_problem* pr, const float* rot6, float* rel_t, floa
 cudaError_t build_track_table(fm_problem* pr, int* T_out);
 void launch_triangulate(const fm_problem* pr, const float* params, float max_err_px, float min_angle_rad,
                         float* pts, int* valid, int* ncam, cudaStream_t s);
+void launch_scale_to_unit(float* x, int n, cudaStream_t s);
+void launch_ea_from_stages(const float* rot6, const float* o, int N, float* ea, cudaStream_t s);
+void launch_ea_to_Rt(const float* ea, int N, float* R, float* t, cudaStream_t s);
 
 // rotation / translation (fm_pose.cu)
 void launch_rot_pairs(const float* params, const int* pi, const int* pj, const float* rel_R,

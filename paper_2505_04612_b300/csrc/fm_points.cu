@@ -200,10 +200,16 @@ cudaError_t build_track_table(fm_problem* pr, int* T_out) {
   int init = -1;
   cudaMemcpyAsync(d_max, &init, sizeof(int), cudaMemcpyHostToDevice, s);
   if (Z > 0) k_track_max<<<(Z + 255) / 256, 256, 0, s>>>(pr->kp_track, Z, d_max, pr->d_err);
-  int mx = -1;
+  int mx = -1, bits = 0;
   cudaMemcpyAsync(&mx, d_max, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&bits, pr->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { cudaFree(d_max); return e; }
+  if (bits & kErrKpRange) {   // a negative track id: reported by the caller, nothing indexed with it
+    cudaFree(d_max);
+    *T_out = 0;
+    return cudaSuccess;
+  }
   const int T = mx + 1;
   *T_out = T;
   pr->n_tracks = T;

@@ -76,6 +76,31 @@ class fm_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
+class fm_tri_opts(ctypes.Structure):
+    _fields_ = [("max_err_px", ctypes.c_float), ("min_angle_deg", ctypes.c_float)]
+
+
+class fm_solve_opts(ctypes.Structure):
+    _fields_ = [
+        ("rot_init_iters", ctypes.c_int32), ("rot_iters", ctypes.c_int32), ("rot_lr", ctypes.c_float),
+        ("reestimate_rel_t", ctypes.c_int32), ("trn_runs", ctypes.c_int32), ("trn_iters", ctypes.c_int32),
+        ("trn_lr", ctypes.c_float), ("trn_final_iters", ctypes.c_int32), ("seed", ctypes.c_uint32),
+        ("ea_rounds", ctypes.c_int32), ("ea_iters", ctypes.c_int32), ("ea_lr", ctypes.c_float),
+        ("ea_tau0", ctypes.c_float), ("ea_tau_min", ctypes.c_float), ("ea_delta", ctypes.c_float),
+        ("tri_max_err_px", ctypes.c_float), ("tri_min_angle_deg", ctypes.c_float),
+        ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+    ]
+
+
+class fm_result(ctypes.Structure):
+    _fields_ = [
+        ("R", ctypes.c_void_p), ("t", ctypes.c_void_p), ("points", ctypes.c_void_p),
+        ("point_valid", ctypes.c_void_p), ("n_tracks", ctypes.c_int32), ("n_points_valid", ctypes.c_int32),
+        ("loss_rotation", ctypes.c_float), ("loss_translation", ctypes.c_float),
+        ("loss_epipolar", ctypes.c_float), ("n_kept", ctypes.c_int64),
+    ]
+
+
 class fm_adam_opts(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
@@ -107,6 +132,16 @@ _SIGNATURES = {
     "fm_track_loss": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "fm_loss_history": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
                                        ctypes.POINTER(ctypes.c_int32)]),
+    "fm_rotation_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "fm_relative_translations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "fm_get_rel_poses": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "fm_translation_random_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "fm_translation_merge": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "fm_epipolar_init_from_stages": (ctypes.c_int, [ctypes.c_void_p]),
+    "fm_triangulate": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fm_tri_opts), ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "fm_solve_opts_default": (None, [ctypes.POINTER(fm_solve_opts)]),
+    "fm_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fm_solve_opts), ctypes.POINTER(fm_result)]),
     "fm_ea_loss_grad_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_void_p,
@@ -316,6 +351,14 @@ def fm_ea_loss_grad_static(kp, seg_off, pair_i, pair_j, params, weights, n_cams,
     _check(st, None)
 
 
+def solve_opts(**overrides) -> fm_solve_opts:
+    o = fm_solve_opts()
+    lib().fm_solve_opts_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
 # ------------------------------------------------------------ owner class
 
 class Problem:
@@ -451,6 +494,69 @@ class Problem:
 
     def loss_history(self, capacity=4096):
         return fm_loss_history(self.handle, capacity)
+
+    def rotation_init(self, n_iters=2000):
+        _check(lib().fm_rotation_init(self.handle, int(n_iters)), self.handle)
+
+    def relative_translations(self):
+        err = np.empty(self.n_pairs, np.float32)
+        _check(lib().fm_relative_translations(self.handle, err.ctypes.data, 0), self.handle)
+        return err
+
+    def get_rel_poses(self, want_R=True, want_t=True):
+        R = np.empty((self.n_pairs, 3, 3), np.float32) if want_R else None
+        t = np.empty((self.n_pairs, 3), np.float32) if want_t else None
+        _check(lib().fm_get_rel_poses(self.handle, R.ctypes.data if want_R else None,
+                                      t.ctypes.data if want_t else None, 0), self.handle)
+        return R, t
+
+    def translation_random_init(self, seed=0):
+        _check(lib().fm_translation_random_init(self.handle, ctypes.c_uint32(seed)), self.handle)
+
+    def translation_merge(self):
+        best = np.empty(self.n_cams, np.int32)
+        _check(lib().fm_translation_merge(self.handle, best.ctypes.data), self.handle)
+        self.runs = 1
+        return best
+
+    def epipolar_init_from_stages(self):
+        _check(lib().fm_epipolar_init_from_stages(self.handle), self.handle)
+
+    def triangulate(self, max_err_px=4.0, min_angle_deg=2.0):
+        T = ctypes.c_int32()
+        opts = fm_tri_opts(max_err_px, min_angle_deg)
+        _check(lib().fm_triangulate(self.handle, ctypes.byref(opts), None, None, None, 0, ctypes.byref(T)),
+               self.handle)
+        n = T.value
+        pts = np.empty((n, 3), np.float32)
+        valid = np.empty(n, np.int32)
+        ncam = np.empty(n, np.int32)
+        _check(lib().fm_triangulate(self.handle, ctypes.byref(opts), pts.ctypes.data, valid.ctypes.data,
+                                    ncam.ctypes.data, 0, ctypes.byref(T)), self.handle)
+        return pts, valid.astype(bool), ncam
+
+    def solve(self, n_tracks=None, **overrides):
+        """fm_solve; returns a dict with R [N,3,3], t [N,3], points/valid (if
+        the problem has tracks) and the final losses."""
+        opts = solve_opts(**overrides)
+        R = np.empty((self.n_cams, 3, 3), np.float32)
+        t = np.empty((self.n_cams, 3), np.float32)
+        res = fm_result()
+        res.R = R.ctypes.data
+        res.t = t.ctypes.data
+        pts = valid = None
+        if n_tracks:
+            pts = np.empty((n_tracks, 3), np.float32)
+            valid = np.empty(n_tracks, np.int32)
+            res.points = pts.ctypes.data
+            res.point_valid = valid.ctypes.data
+        _check(lib().fm_solve(self.handle, ctypes.byref(opts), ctypes.byref(res)), self.handle)
+        self.runs = 1
+        out = dict(R=R, t=t, loss_rotation=res.loss_rotation, loss_translation=res.loss_translation,
+                   loss_epipolar=res.loss_epipolar, n_kept=res.n_kept, n_points_valid=res.n_points_valid)
+        if n_tracks:
+            out.update(points=pts[:res.n_tracks], point_valid=valid[:res.n_tracks].astype(bool))
+        return out
 
     def step(self, stage, n_iters, lr, beta1=0.9, beta2=0.999, eps=1e-8, want_loss=False):
         opts = fm_adam_opts(lr, beta1, beta2, eps)

@@ -49,8 +49,10 @@ def test_struct_layout_matches_c():
 #include <stddef.h>
 #include "fastmap.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(fm_problem_desc), offsetof(fm_problem_desc, inputs_on_device),
-         offsetof(fm_problem_desc, cuda_stream), sizeof(fm_problem_info), sizeof(fm_adam_opts));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(fm_problem_desc),
+         offsetof(fm_problem_desc, inputs_on_device), offsetof(fm_problem_desc, cuda_stream),
+         sizeof(fm_problem_info), sizeof(fm_adam_opts), sizeof(fm_solve_opts), offsetof(fm_solve_opts, eps),
+         sizeof(fm_result), offsetof(fm_result, n_kept), sizeof(fm_kernel_time));
   return 0;
 }
 """
@@ -62,7 +64,8 @@ int main(void) {
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     assert vals == [ctypes.sizeof(F.fm_problem_desc), F.fm_problem_desc.inputs_on_device.offset,
                     F.fm_problem_desc.cuda_stream.offset, ctypes.sizeof(F.fm_problem_info),
-                    ctypes.sizeof(F.fm_adam_opts)]
+                    ctypes.sizeof(F.fm_adam_opts), ctypes.sizeof(F.fm_solve_opts), F.fm_solve_opts.eps.offset,
+                    ctypes.sizeof(F.fm_result), F.fm_result.n_kept.offset, ctypes.sizeof(F.fm_kernel_time)]
 
 
 def test_errors_without_problem_are_reported(lib):

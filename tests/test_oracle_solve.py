@@ -1,0 +1,35 @@
+"""Pins of the oracle's end-to-end solve (no CUDA): exact recovery of a
+noise-free scene up to a similarity, and the counter-based generator of the
+random translation starts."""
+import numpy as np
+
+from oracle import epipolar as ep
+from oracle import solve as S
+from synthetic.scenes import gt_relative_poses
+from tests._util import clean_scene
+
+
+def test_hash_uniform_properties():
+    v = S.hash_uniform(200_000, 7)
+    assert v.min() >= -1.0 and v.max() < 1.0
+    assert abs(v.mean()) < 0.01 and abs(np.var(v) - 1.0 / 3.0) < 0.01
+    assert len(np.unique(v)) > 0.99 * len(v)
+    # different salts give different streams; the same salt the same one
+    assert not np.allclose(S.hash_uniform(100, 1), S.hash_uniform(100, 2))
+    np.testing.assert_array_equal(S.hash_uniform(100, 3), S.hash_uniform(100, 3))
+    # the Weyl step makes neighbouring counters unrelated
+    assert abs(np.corrcoef(v[:-1], v[1:])[0, 1]) < 0.01
+
+
+def test_oracle_solve_recovers_noise_free_scene():
+    sc = clean_scene(6)
+    x1, x2 = ep.calibrated_pairs(sc.kp1_px, sc.kp2_px, sc.kp_img_pair, sc.pair_i, sc.pair_j,
+                                 sc.focal, sc.cx, sc.cy)
+    Rij, _ = gt_relative_poses(sc)
+    out = S.solve(sc.n_cams, sc.pair_i, sc.pair_j, x1, x2, sc.kp_img_pair, Rij, None, sc.focal,
+                  sc.kp_track, S.SolveOpts())
+    assert S.rotation_errors_deg(out["R"], sc.R_gt).max() < 0.02
+    scale = np.mean(np.linalg.norm(sc.centers_gt - sc.centers_gt.mean(0), axis=1))
+    assert S.centre_errors(out["centres"], sc.centers_gt).max() < 5e-3 * scale
+    assert out["n_kept"] == sc.n_kp
+    assert out["point_valid"].sum() > 0.3 * len(out["point_valid"])
