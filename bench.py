@@ -57,6 +57,8 @@ def args_():
     ap.add_argument("--config", default="c2_5m")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autograd-modes", action="store_true",
+                    help="skip the autograd forward/backward comparison (after the timed step)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -237,6 +239,45 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def autograd_modes(pr, p_dev, flush, steps, warmup, Z):
+    """Forward + backward of the epipolar loss through the autograd adjoint in
+    each mode (L2 flushed before every forward; with the keypoints left in L2
+    between forward and backward, and with L2 flushed there too, as when the
+    pairs do not fit in L2).  Device time of the library's kernels per
+    forward + backward, the per-pair passes alone, and their algorithmic bytes
+    per pair: fused 16 (one pass), recompute 16 + 16, stored 16 + 4 (write)
+    + 16 + 4 (read).  A ~0.5 ms device sleep ahead of each iteration keeps
+    the launches queued, so that the per-kernel events do not absorb the
+    autograd engine's host time."""
+    import torch
+    from paper_2505_04612_b300 import autograd as A
+    p = p_dev.clone().requires_grad_(True)
+    out = {}
+    for mode, bpp in (("fused", 16), ("recompute", 32), ("stored", 40)):
+        for between in ("kept", "flushed"):
+            def once():
+                flush.zero_()
+                torch.cuda._sleep(1_000_000)
+                p.grad = None
+                L = A.epipolar_loss(p, pr, mode)
+                if between == "flushed":
+                    flush.zero_()
+                L.backward()
+            for _ in range(warmup):
+                once()
+            torch.cuda.synchronize()
+            pr.timing(True)
+            for _ in range(steps):
+                once()
+            kt = pr.timing_read()
+            pr.timing(False)
+            total = sum(v[1] for v in kt.values()) * 1e3 / steps
+            pairs = sum(v[1] for k, v in kt.items() if k.startswith("k_ea_direct")) * 1e3 / steps
+            out[f"{mode}/{between}"] = {"kernels_us": total, "pair_passes_us": pairs, "bytes_per_pair": bpp,
+                                        "pair_passes_GBps": bpp * Z / (pairs * 1e-6) / 1e9 if pairs > 0 else None}
+    return out
+
+
 def workload_config(sc, a):
     return {"workload": f"{a.config}: epipolar adjustment step (L1, Eq. 7, + Adam), {sc.n_cams} cameras, "
                         f"{sc.n_pairs} image pairs, {sc.n_kp} keypoint pairs, seed {a.seed}",
@@ -321,6 +362,8 @@ def main():
     pr.timing(False)
     losses = pr.loss_history(8)
 
+    modes = None if a.no_autograd_modes else autograd_modes(pr, p_dev, flush, a.steps, a.warmup, Z)
+
     # end to end through the C ABI with pinned host buffers (params in, loss + grad out)
     host_p = torch.from_numpy(params.reshape(-1).copy()).pin_memory()
     host_g = torch.empty_like(host_p).pin_memory()
@@ -360,6 +403,7 @@ def main():
             "kernels_us_per_launch": {k: 1e3 * v[1] / max(v[0], 1) for k, v in kt.items()},
             "clocks": clk.summary(),
             "last_losses": losses[-3:],
+            "autograd_modes": modes,
         }
         if not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(sc, params, a.cpu_seconds)

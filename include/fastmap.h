@@ -219,6 +219,46 @@ fm_status fm_ea_get_weights(fm_problem* problem, float* weights_out, int32_t out
 fm_status fm_loss_grad(fm_problem* problem, fm_stage stage, const float* params,
                        float* loss, float* grad, int32_t mem_on_device);
 
+/* ------------------------------------------- epipolar forward / backward */
+
+/* What fm_ea_forward keeps for fm_ea_backward.  The paper evaluates loss and
+ * gradient together (Sec. 3.3); these calls split the direct epipolar
+ * objective (Eq. 7, or Eqs. 8-9 with per-pair weights: losses FM_EA_L1 and
+ * FM_EA_L2) into a forward pass and its adjoint, for reverse-mode use (e.g.
+ * behind torch.autograd.Function).
+ *   FM_EA_SAVE_NONE  nothing: the backward pass re-reads every keypoint pair
+ *                    and recomputes its residual (16 B per pair);
+ *   FM_EA_SAVE_COEF  per keypoint pair the coefficient c_m = w_m rho'(r_m)
+ *                    (sign(r) for L1, 2r for L2), Z floats in the library's
+ *                    internal pair order (sorted by image pair, stable);
+ *                    the backward pass reads c_m and the pair's keypoints
+ *                    (4 + 16 B per pair) and recomputes no residual;
+ *   FM_EA_SAVE_DLDE  per image pair dL/dE_n = (1/Z) sum_m c_m x~2 x~1^T
+ *                    (row-major 3x3), P*9 floats; the forward pass does all
+ *                    the per-pair work and the backward pass only the chain
+ *                    rule through E_n and the per-camera sums. */
+typedef enum {
+  FM_EA_SAVE_NONE = 0,
+  FM_EA_SAVE_COEF = 1,
+  FM_EA_SAVE_DLDE = 2
+} fm_ea_save;
+
+/* Forward pass: the epipolar loss (current loss and weights of the problem;
+ * FM_ERR_STATE for FM_EA_COMPACT) at params_dev [N*9] into loss_dev (one
+ * device float), and the intermediates selected by `save` into saved_dev
+ * (device, 16-byte aligned: Z floats for FM_EA_SAVE_COEF, P*9 for
+ * FM_EA_SAVE_DLDE, ignored for FM_EA_SAVE_NONE).  All pointers are device
+ * memory owned by the caller.  Asynchronous on the problem's stream. */
+fm_status fm_ea_forward(fm_problem* problem, const float* params_dev, float* loss_dev,
+                        int32_t save, float* saved_dev);
+
+/* Backward pass: grad_dev [N*9] = g * dL/dparams at params_dev, where g is the
+ * device scalar *grad_loss_dev (1 when grad_loss_dev is NULL).  `save` and
+ * saved_dev must be those of the forward call at the same params_dev, and the
+ * loss and weights must be unchanged since.  Asynchronous. */
+fm_status fm_ea_backward(fm_problem* problem, const float* params_dev, int32_t save,
+                         const float* saved_dev, const float* grad_loss_dev, float* grad_dev);
+
 /* n_iters Adam steps on the stage's parameters, each one a full evaluation of
  * the loss and gradient (over all keypoint pairs for the epipolar stage)
  * followed by the update (Sec. 3.2-3.4).  loss (host, or NULL; [m] for the

@@ -1,0 +1,78 @@
+"""The direct epipolar objective as a ``torch.autograd.Function``.
+
+Forward evaluates L = (1/Z) sum_m w_m rho(x~2_m^T E_n x~1_m) (Sec. 3.3, Eq. 7
+for rho = |r|; Eqs. 8-9 for rho = r^2 with IRLS weights) at the epipolar-stage
+parameters [N, 9] (6D rotation, translation per camera); backward is the
+library's hand-written adjoint: dL/dE_n per image pair, the chain rule
+through E_n = [t^_ij]_x R_j R_i^T to both cameras, the fixed-order
+per-camera sum and the 6D map's adjoint.  Both passes run in the C ABI
+(``fm_ea_forward`` / ``fm_ea_backward``); this module only allocates the
+outputs and passes pointers.
+
+Modes (what forward keeps for backward):
+  ``"recompute"``  nothing; backward re-reads every keypoint pair and
+                   recomputes its residual (16 B per pair again);
+  ``"stored"``     the per-pair coefficient w rho'(r) (4 B per pair written,
+                   then 4 + 16 B per pair read by backward);
+  ``"fused"``      dL/dE_n per image pair (9 floats): forward does all the
+                   per-pair work, backward only the per-image-pair and
+                   per-camera parts.
+
+The problem's loss (L1 or L2) and weights are the ones set on it; they must
+not change between a forward call and its backward call.  The problem is
+bound to the CUDA stream it was created on, which should be the stream torch
+runs the surrounding graph on.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import fastmap as F
+
+MODES = {"recompute": F.FM_EA_SAVE_NONE, "stored": F.FM_EA_SAVE_COEF, "fused": F.FM_EA_SAVE_DLDE}
+
+
+def _saved_buffer(problem, save, device):
+    if save == F.FM_EA_SAVE_COEF:
+        return torch.empty(max(problem.n_kp, 1), dtype=torch.float32, device=device)
+    if save == F.FM_EA_SAVE_DLDE:
+        return torch.empty(max(problem.n_pairs, 1) * 9, dtype=torch.float32, device=device)
+    return None
+
+
+class EpipolarLoss(torch.autograd.Function):
+    """loss = EpipolarLoss.apply(params [N, 9] CUDA float32, problem, mode)."""
+
+    @staticmethod
+    def forward(ctx, params, problem, mode="recompute"):
+        if mode not in MODES:
+            raise ValueError(f"mode must be one of {sorted(MODES)}")
+        if not (params.is_cuda and params.dtype == torch.float32 and params.is_contiguous()):
+            raise ValueError("params must be a contiguous float32 CUDA tensor")
+        if params.numel() != 9 * problem.n_cams:
+            raise ValueError(f"params must hold {9 * problem.n_cams} values")
+        save = MODES[mode]
+        loss = torch.empty((), dtype=torch.float32, device=params.device)
+        saved = _saved_buffer(problem, save, params.device)
+        F.fm_ea_forward(problem.handle, params.data_ptr(), loss.data_ptr(), save,
+                        saved.data_ptr() if saved is not None else None)
+        ctx.problem = problem
+        ctx.save = save
+        ctx.save_for_backward(params, saved)
+        return loss
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        params, saved = ctx.saved_tensors
+        g = grad_loss.detach()
+        if g.dtype != torch.float32:
+            g = g.float()
+        grad = torch.empty_like(params)
+        F.fm_ea_backward(ctx.problem.handle, params.data_ptr(), ctx.save,
+                         saved.data_ptr() if saved is not None else None, g.data_ptr(), grad.data_ptr())
+        return grad, None, None
+
+
+def epipolar_loss(params, problem, mode="recompute"):
+    """The epipolar loss of `problem` at `params` with the hand-written adjoint."""
+    return EpipolarLoss.apply(params, problem, mode)

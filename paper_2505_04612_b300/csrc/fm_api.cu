@@ -17,7 +17,7 @@ const char* const kKernelNames[kKCount] = {
     "k_calibrate", "k_seg_offsets", "k_run_tables", "k_ea_tables", "k_ea_direct",
     "k_ea_segments", "k_rot_pairs", "k_trn_targets", "k_trn_pairs", "k_cam", "k_sum_fixed",
     "k_ea_reweight", "k_w_build", "k_ea_compact", "k_mart_iter", "k_reltrans", "k_merge",
-    "k_triangulate"};
+    "k_triangulate", "k_ea_direct_loss", "k_ea_direct_coef"};
 }
 
 namespace {
@@ -750,6 +750,116 @@ fm_status fm_loss_grad(fm_problem* pr, fm_stage st, const float* params, float* 
     FM_CUDA(pr, cudaStreamSynchronize(s));
     if (loss) std::memcpy(loss, pr->h_loss, sizeof(float) * runs);
   }
+  return FM_OK;
+}
+
+static fm_status ea_split_check(fm_problem* pr, const float* params, int32_t save, const void* saved) {
+  if (!params) return fail(pr, FM_ERR_INVALID_ARG, "params_dev is NULL");
+  if (save < FM_EA_SAVE_NONE || save > FM_EA_SAVE_DLDE) return fail(pr, FM_ERR_INVALID_ARG, "unknown save mode");
+  if (save != FM_EA_SAVE_NONE && !saved) return fail(pr, FM_ERR_INVALID_ARG, "saved_dev is NULL");
+  if (save != FM_EA_SAVE_NONE && (reinterpret_cast<uintptr_t>(saved) & 15u))
+    return fail(pr, FM_ERR_INVALID_ARG, "saved_dev must be 16-byte aligned");
+  if (pr->ea_loss == FM_EA_COMPACT)
+    return fail(pr, FM_ERR_STATE,
+                "the forward/backward split evaluates the direct forms (FM_EA_L1, FM_EA_L2); "
+                "the compact form goes through fm_loss_grad");
+  return FM_OK;
+}
+
+fm_status fm_ea_forward(fm_problem* pr, const float* params, float* loss_dev, int32_t save, float* saved) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  fm_status e = ea_split_check(pr, params, save, saved);
+  if (e != FM_OK) return e;
+  if (!loss_dev) return fail(pr, FM_ERR_INVALID_ARG, "loss_dev is NULL");
+  cudaStream_t s = pr->stream;
+  {
+    Timed t(pr, fm::kKEaTables);
+    fm::launch_ea_tables(params, pr->pair_i, pr->pair_j, pr->seg_off, pr->P, pr->seg_tab, nullptr, s);
+  }
+  FM_LAUNCHED(pr);
+  fm::SegArgs a = fm::seg_args(pr, params);
+  a.seg_grad = nullptr;
+  a.l_scale = pr->ea_inv_z;
+  if (save == FM_EA_SAVE_DLDE) {
+    if (pr->n_wruns > 0) {
+      Timed t(pr, fm::kKEaDirect);
+      fm::launch_ea_direct(pr, pr->ea_w, pr->ea_loss, s);
+    }
+    a.g_scale = (pr->ea_loss == FM_EA_L1) ? pr->ea_inv_z : 2.f * pr->ea_inv_z;
+    a.dlde_out = saved;
+  } else if (pr->n_wruns > 0) {
+    Timed t(pr, fm::kKEaDirectLoss);
+    fm::launch_ea_direct_loss(pr, pr->ea_w, pr->ea_loss, save == FM_EA_SAVE_COEF ? saved : nullptr, s);
+  }
+  FM_LAUNCHED(pr);
+  {
+    Timed t(pr, fm::kKEaSegments);
+    fm::launch_ea_segments(a, s);
+  }
+  FM_LAUNCHED(pr);
+  {
+    Timed t(pr, fm::kKLossSum);
+    fm::launch_sum_fixed(pr->seg_loss, pr->P, 1, loss_dev, s);
+  }
+  FM_LAUNCHED(pr);
+  return FM_OK;
+}
+
+fm_status fm_ea_backward(fm_problem* pr, const float* params, int32_t save, const float* saved,
+                         const float* grad_loss, float* grad) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  fm_status e = ea_split_check(pr, params, save, saved);
+  if (e != FM_OK) return e;
+  if (!grad) return fail(pr, FM_ERR_INVALID_ARG, "grad_dev is NULL");
+  cudaStream_t s = pr->stream;
+  fm::SegArgs a = fm::seg_args(pr, params);
+  a.seg_loss = nullptr;
+  a.grad_loss = grad_loss;
+  if (save == FM_EA_SAVE_DLDE) {
+    a.dlde_in = saved;
+  } else {
+    {
+      Timed t(pr, fm::kKEaTables);
+      fm::launch_ea_tables(params, pr->pair_i, pr->pair_j, pr->seg_off, pr->P, pr->seg_tab, nullptr, s);
+    }
+    FM_LAUNCHED(pr);
+    if (save == FM_EA_SAVE_COEF) {
+      if (pr->n_wruns > 0) {
+        Timed t(pr, fm::kKEaDirectCoef);
+        fm::launch_ea_direct_from_coef(pr, saved, s);
+      }
+      a.g_scale = pr->ea_inv_z;   // the stored coefficients carry rho' in full
+    } else {
+      if (pr->n_wruns > 0) {
+        Timed t(pr, fm::kKEaDirect);
+        fm::launch_ea_direct(pr, pr->ea_w, pr->ea_loss, s);
+      }
+      a.g_scale = (pr->ea_loss == FM_EA_L1) ? pr->ea_inv_z : 2.f * pr->ea_inv_z;
+    }
+    FM_LAUNCHED(pr);
+  }
+  {
+    Timed t(pr, fm::kKEaSegments);
+    fm::launch_ea_segments(a, s);
+  }
+  FM_LAUNCHED(pr);
+  fm::CamUpdate u{};
+  u.cam_seg_off = pr->cam_seg_off;
+  u.cam_seg = pr->cam_seg;
+  u.seg_grad = pr->seg_grad;
+  u.params = params;
+  u.params_out = nullptr;
+  u.grad_out = grad;
+  u.N = pr->N;
+  u.P = pr->P;
+  u.runs = 1;
+  u.seg_loss = pr->seg_loss;
+  u.loss_out = nullptr;
+  {
+    Timed t(pr, fm::kKCamUpdate);
+    fm::launch_cam_update(FM_STAGE_EPIPOLAR, u, s);
+  }
+  FM_LAUNCHED(pr);
   return FM_OK;
 }
 

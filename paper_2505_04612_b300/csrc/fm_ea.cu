@@ -31,6 +31,14 @@
 //     end inside the row get their own warp sums, and the last one opens.
 //     Every (warp run, image pair) gets exactly one record, summed in a fixed
 //     order: no atomics, deterministic.
+//
+// Modes of k_ea_direct (the split of one evaluation into a forward and a
+// backward pass, for the autograd adjoint):
+//   kFull      loss and dL/dE together (one pass, 16 B per pair);
+//   kLossOnly  the loss alone; optionally writes each pair's coefficient
+//              c = w drho/dr (4 B per pair) for a later kFromCoef pass;
+//   kFromCoef  dL/dE from stored coefficients: no residual is recomputed, but
+//              the pair's x~2 x~1^T still needs the keypoints (16 + 4 B).
 #include "fm_device.cuh"
 #include "fm_internal.h"
 
@@ -65,13 +73,16 @@ __global__ void k_ea_tables(const float* __restrict__ params, const int* __restr
   tab[3 * n + 2] = make_float4(E[8], __int_as_float(end), 0.f, 0.f);
 }
 
+enum DirectMode { kFull = 0, kLossOnly = 1, kFromCoef = 2 };
+
 struct DirectArgs {
   const float4* kp;
-  const float* wts;
+  const float* wts;      // per-pair weights; the stored coefficients in kFromCoef
   const int* run_seg;
   const int4* info;
   const float4* seg_tab;
   float4* rec;
+  float* coef_out;       // kLossOnly: per-pair coefficients when not null
   int Z;
   int n_wruns;
 };
@@ -112,62 +123,63 @@ __device__ __forceinline__ int end_uniform(int endreg, const float4* seg_tab, in
   return __float_as_int(__ldg(seg_tab + 3 * (s_first + t) + 2).y);
 }
 
-// LOSS 0: rho = w |r|, rho' = w sign(r) (sign(0) = 0)
-// LOSS 1: rho = w r^2, rho'/2 = w r     (the factor 2 is applied per image pair)
-template <int LOSS, bool WEIGHTED>
-__device__ __forceinline__ void contrib(const float* E, float4 x, float wt, float* v) {
+// c = w drho/dr and l = w rho of one pair.
+// LOSS 0: rho = |r|, rho' = sign(r) (sign(0) = 0)
+// LOSS 1: rho = r^2; c = w r in kFull (the factor 2 is applied per image pair)
+//         and the full 2 w r when stored (kLossOnly), so that stored
+//         coefficients need no per-loss factor.
+// kFromCoef: c is the stored coefficient (passed in wt), l is not computed.
+// MASKED: wt multiplies the pair even when unweighted (0 for lanes past Z).
+template <int LOSS, bool WEIGHTED, int MODE, bool MASKED = false>
+__device__ __forceinline__ void pair_terms(const float* E, float4 x, float wt, float& c, float& l) {
+  if (MODE == kFromCoef) {
+    c = wt;
+    l = 0.f;
+    return;
+  }
   const float ex = fmaf(E[0], x.x, fmaf(E[1], x.y, E[2]));
   const float ey = fmaf(E[3], x.x, fmaf(E[4], x.y, E[5]));
   const float ez = fmaf(E[6], x.x, fmaf(E[7], x.y, E[8]));
   const float r = fmaf(x.z, ex, fmaf(x.w, ey, ez));
-  float c, l;
   if (LOSS == 0) {
     c = (r > 0.f) ? 1.f : ((r < 0.f) ? -1.f : 0.f);
     l = fabsf(r);
   } else {
-    c = r;
-    l = r * r;
-  }
-  if (WEIGHTED) {
-    c *= wt;
-    l *= wt;
-  }
-  const float ca = c * x.x, cb = c * x.y;
-  v[0] = ca * x.z; v[1] = cb * x.z; v[2] = c * x.z;
-  v[3] = ca * x.w; v[4] = cb * x.w; v[5] = c * x.w;
-  v[6] = ca; v[7] = cb; v[8] = c; v[9] = l;
-}
-
-// MASKED: wt multiplies the pair even when unweighted (0 for lanes past Z)
-template <int LOSS, bool WEIGHTED, bool MASKED = false>
-__device__ __forceinline__ void accumulate(const float* E, float4 x, float wt, float* acc) {
-  const float ex = fmaf(E[0], x.x, fmaf(E[1], x.y, E[2]));
-  const float ey = fmaf(E[3], x.x, fmaf(E[4], x.y, E[5]));
-  const float ez = fmaf(E[6], x.x, fmaf(E[7], x.y, E[8]));
-  const float r = fmaf(x.z, ex, fmaf(x.w, ey, ez));
-  float c, l;
-  if (LOSS == 0) {
-    c = (r > 0.f) ? 1.f : ((r < 0.f) ? -1.f : 0.f);
-    l = fabsf(r);
-  } else {
-    c = r;
+    c = (MODE == kLossOnly) ? 2.f * r : r;
     l = r * r;
   }
   if (WEIGHTED || MASKED) {
     c *= wt;
     l *= wt;
   }
-  const float ca = c * x.x, cb = c * x.y;
-  acc[0] = fmaf(ca, x.z, acc[0]);
-  acc[1] = fmaf(cb, x.z, acc[1]);
-  acc[2] = fmaf(c, x.z, acc[2]);
-  acc[3] = fmaf(ca, x.w, acc[3]);
-  acc[4] = fmaf(cb, x.w, acc[4]);
-  acc[5] = fmaf(c, x.w, acc[5]);
-  acc[6] += ca;
-  acc[7] += cb;
-  acc[8] += c;
-  acc[9] += l;
+}
+
+// v += the pair's record terms: c x~2 x~1^T (9, unless kLossOnly) and l
+// (unless kFromCoef)
+template <int MODE>
+__device__ __forceinline__ void add_terms(float c, float l, float4 x, float* v) {
+  if (MODE != kLossOnly) {
+    const float ca = c * x.x, cb = c * x.y;
+    v[0] = fmaf(ca, x.z, v[0]);
+    v[1] = fmaf(cb, x.z, v[1]);
+    v[2] = fmaf(c, x.z, v[2]);
+    v[3] = fmaf(ca, x.w, v[3]);
+    v[4] = fmaf(cb, x.w, v[4]);
+    v[5] = fmaf(c, x.w, v[5]);
+    v[6] += ca;
+    v[7] += cb;
+    v[8] += c;
+  }
+  if (MODE != kFromCoef) v[9] += l;
+}
+
+// accumulate one pair; returns its coefficient (for kLossOnly's store)
+template <int LOSS, bool WEIGHTED, int MODE, bool MASKED = false>
+__device__ __forceinline__ float accumulate(const float* E, float4 x, float wt, float* acc) {
+  float c, l;
+  pair_terms<LOSS, WEIGHTED, MODE, MASKED>(E, x, wt, c, l);
+  add_terms<MODE>(c, l, x, acc);
+  return c;
 }
 
 __device__ __forceinline__ void warp_store(float4* rec, int r, const float* v, int lane) {
@@ -203,10 +215,13 @@ struct RunHead {
 template <bool WEIGHTED>
 __device__ __forceinline__ void issue_rows(const DirectArgs& a, int w, int lane, float4* kb, float* wb) {
   const int base = w * WP;
+  // slots past Z are zero-filled (src-size 0), so that no lane ever reads
+  // stale shared memory
 #pragma unroll
   for (int r = 0; r < ROWS; ++r) {
     const int p = base + 32 * r + lane;
     if (p < a.Z) cp_async16(kb + 32 * r + lane, a.kp + p);
+    else cp_async16_partial(kb + 32 * r + lane, a.kp, 0);
   }
   if (WEIGHTED) {
 #pragma unroll
@@ -214,8 +229,8 @@ __device__ __forceinline__ void issue_rows(const DirectArgs& a, int w, int lane,
       const int c = lane + 32 * k;
       if (c < WP / 4) {
         const int p4 = base + 4 * c;
-        const int bytes = 4 * min(4, a.Z - p4);
-        if (bytes > 0) cp_async16_partial(wb + 4 * c, a.wts + p4, bytes);
+        const int bytes = 4 * max(0, min(4, a.Z - p4));
+        cp_async16_partial(wb + 4 * c, bytes > 0 ? a.wts + p4 : a.wts, bytes);
       }
     }
   }
@@ -243,11 +258,18 @@ __device__ __forceinline__ void load_table_head(const DirectArgs& a, int lane, R
   }
 }
 
+// The coefficient of pair base + i goes into the x component of its own
+// shared-memory slot (read only by the lane that stores it); the warp copies
+// them out with coalesced stores after the warp run (coef_store).
+__device__ __forceinline__ void stash_coef(float4* kb, int i, float c) {
+  reinterpret_cast<float*>(kb + i)[0] = c;
+}
+
 // Row-major processing: right for warp runs that touch one or two image pairs
 // (at most one image-pair end to cross with a warp reduction).
-template <int LOSS, bool WEIGHTED>
+template <int LOSS, bool WEIGHTED, int MODE>
 __device__ __forceinline__ void process_rows(const DirectArgs& a, int w, int lane, const RunHead& h,
-                                             const float4* kb, const float* wb) {
+                                             float4* kb, const float* wb, bool store) {
   const int base = w * WP;
   const int4 info = h.info;
   const int wend = min(base + WP, a.Z);    // one past the warp run's last pair
@@ -269,12 +291,18 @@ __device__ __forceinline__ void process_rows(const DirectArgs& a, int w, int lan
 #pragma unroll 1
       for (; q + 4 <= r_in; q += 4) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          accumulate<LOSS, WEIGHTED>(cur.E, kb[32 * (q + u) + lane], WEIGHTED ? wb[32 * (q + u) + lane] : 1.f, acc);
+        for (int u = 0; u < 4; ++u) {
+          const int i = 32 * (q + u) + lane;
+          const float c = accumulate<LOSS, WEIGHTED, MODE>(cur.E, kb[i], WEIGHTED ? wb[i] : 1.f, acc);
+          if (MODE == kLossOnly && store) stash_coef(kb, i, c);
+        }
       }
 #pragma unroll 1
-      for (; q < r_in; ++q)
-        accumulate<LOSS, WEIGHTED>(cur.E, kb[32 * q + lane], WEIGHTED ? wb[32 * q + lane] : 1.f, acc);
+      for (; q < r_in; ++q) {
+        const int i = 32 * q + lane;
+        const float c = accumulate<LOSS, WEIGHTED, MODE>(cur.E, kb[i], WEIGHTED ? wb[i] : 1.f, acc);
+        if (MODE == kLossOnly && store) stash_coef(kb, i, c);
+      }
       r = r_in;
       continue;
     }
@@ -285,7 +313,8 @@ __device__ __forceinline__ void process_rows(const DirectArgs& a, int w, int lan
     const float4 x = valid ? kb[32 * r + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float wt = valid ? (WEIGHTED ? wb[32 * r + lane] : 1.f) : 0.f;
     if (row_hi <= cur.end) {
-      accumulate<LOSS, WEIGHTED, true>(cur.E, x, wt, acc);
+      const float c = accumulate<LOSS, WEIGHTED, MODE, true>(cur.E, x, wt, acc);
+      if (MODE == kLossOnly && store && valid) stash_coef(kb, 32 * r + lane, c);
       ++r;
       continue;
     }
@@ -305,10 +334,11 @@ __device__ __forceinline__ void process_rows(const DirectArgs& a, int w, int lan
       El[8] = e2.x;
     }
     float v[10];
-    contrib<LOSS, WEIGHTED>(El, x, wt, v);
-    if (!valid) {
 #pragma unroll
-      for (int k = 0; k < 10; ++k) v[k] = 0.f;
+    for (int k = 0; k < 10; ++k) v[k] = 0.f;
+    if (valid) {
+      const float c = accumulate<LOSS, WEIGHTED, MODE, true>(El, x, wt, v);
+      if (MODE == kLossOnly && store) stash_coef(kb, 32 * r + lane, c);
     }
     // close the current image pair
     float t10[10];
@@ -339,9 +369,9 @@ __device__ __forceinline__ void process_rows(const DirectArgs& a, int w, int lan
 // or more ends walks its pairs one by one and writes the image pairs that lie
 // wholly inside its run.  A segmented scan keyed by image pair then combines
 // the tails of consecutive lanes and absorbs heads, in fixed lane order.
-template <int LOSS, bool WEIGHTED>
+template <int LOSS, bool WEIGHTED, int MODE>
 __device__ __forceinline__ void process_lanes(const DirectArgs& a, int w, int lane, const RunHead& h,
-                                              const float4* kb, const float* wb) {
+                                              float4* kb, const float* wb, bool store) {
   const int base = w * WP;
   const int4 info = h.info;
   const int wend = min(base + WP, a.Z);
@@ -379,31 +409,13 @@ __device__ __forceinline__ void process_lanes(const DirectArgs& a, int w, int la
 #pragma unroll
       for (int q = 0; q < 9; ++q) E[q] = in_head ? E0[q] : E1[q];
       const float wt = (k < n) ? (WEIGHTED ? wb[lane * U + k] : 1.f) : 0.f;
-      const float ex = fmaf(E[0], x.x, fmaf(E[1], x.y, E[2]));
-      const float ey = fmaf(E[3], x.x, fmaf(E[4], x.y, E[5]));
-      const float ez = fmaf(E[6], x.x, fmaf(E[7], x.y, E[8]));
-      const float r = fmaf(x.z, ex, fmaf(x.w, ey, ez));
       float c, l;
-      if (LOSS == 0) {
-        c = (r > 0.f) ? 1.f : ((r < 0.f) ? -1.f : 0.f);
-        l = fabsf(r);
-      } else {
-        c = r;
-        l = r * r;
-      }
-      c *= wt;
-      l *= wt;
+      pair_terms<LOSS, WEIGHTED, MODE, true>(E, x, wt, c, l);
+      if (MODE == kLossOnly && store && k < n) stash_coef(kb, lane * U + k, c);
       const float ch = in_head ? c : 0.f, ct = c - ch;
       const float lh = in_head ? l : 0.f, lt = l - lh;
-      float ca = ch * x.x, cb = ch * x.y;
-      acc_h[0] = fmaf(ca, x.z, acc_h[0]); acc_h[1] = fmaf(cb, x.z, acc_h[1]); acc_h[2] = fmaf(ch, x.z, acc_h[2]);
-      acc_h[3] = fmaf(ca, x.w, acc_h[3]); acc_h[4] = fmaf(cb, x.w, acc_h[4]); acc_h[5] = fmaf(ch, x.w, acc_h[5]);
-      acc_h[6] += ca; acc_h[7] += cb; acc_h[8] += ch; acc_h[9] += lh;
-      ca = ct * x.x;
-      cb = ct * x.y;
-      acc_t[0] = fmaf(ca, x.z, acc_t[0]); acc_t[1] = fmaf(cb, x.z, acc_t[1]); acc_t[2] = fmaf(ct, x.z, acc_t[2]);
-      acc_t[3] = fmaf(ca, x.w, acc_t[3]); acc_t[4] = fmaf(cb, x.w, acc_t[4]); acc_t[5] = fmaf(ct, x.w, acc_t[5]);
-      acc_t[6] += ca; acc_t[7] += cb; acc_t[8] += ct; acc_t[9] += lt;
+      add_terms<MODE>(ch, lh, x, acc_h);
+      add_terms<MODE>(ct, lt, x, acc_t);
     }
     if (two_parts) {
       has_head = true;
@@ -438,7 +450,9 @@ __device__ __forceinline__ void process_lanes(const DirectArgs& a, int w, int la
         end = __float_as_int(e2.y);
       }
       const float Es[9] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w, e2.x};
-      accumulate<LOSS, WEIGHTED>(Es, kb[lane * U + (p - p0)], WEIGHTED ? wb[lane * U + (p - p0)] : 1.f, acc_t);
+      const int i = lane * U + (p - p0);
+      const float c = accumulate<LOSS, WEIGHTED, MODE>(Es, kb[i], WEIGHTED ? wb[i] : 1.f, acc_t);
+      if (MODE == kLossOnly && store) stash_coef(kb, i, c);
     }
     key = sl;
   }
@@ -472,14 +486,25 @@ __device__ __forceinline__ void process_lanes(const DirectArgs& a, int w, int la
   if (has_head && (lane == 0 || key_prev != head_key)) store_record(a.rec, info.z + head_key, acc_h);
 }
 
-template <int LOSS, bool WEIGHTED>
+template <int LOSS, bool WEIGHTED, int MODE>
 __device__ __forceinline__ void process(const DirectArgs& a, int w, int lane, const RunHead& h,
-                                        const float4* kb, const float* wb) {
-  if (h.info.y <= 2) process_rows<LOSS, WEIGHTED>(a, w, lane, h, kb, wb);
-  else process_lanes<LOSS, WEIGHTED>(a, w, lane, h, kb, wb);
+                                        float4* kb, const float* wb) {
+  const bool store = (MODE == kLossOnly) && a.coef_out != nullptr;
+  if (h.info.y <= 2) process_rows<LOSS, WEIGHTED, MODE>(a, w, lane, h, kb, wb, store);
+  else process_lanes<LOSS, WEIGHTED, MODE>(a, w, lane, h, kb, wb, store);
+  if (store) {
+    // coalesced copy-out of the stashed coefficients
+    __syncwarp();
+    const int base = w * WP;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      const int i = 32 * r + lane;
+      if (base + i < a.Z) a.coef_out[base + i] = reinterpret_cast<const float*>(kb + i)[0];
+    }
+  }
 }
 
-template <int LOSS, bool WEIGHTED>
+template <int LOSS, bool WEIGHTED, int MODE>
 __global__ void __launch_bounds__(WARPS * 32) k_ea_direct(DirectArgs a) {
   extern __shared__ float4 smem[];
   const int lane = threadIdx.x & 31;
@@ -508,46 +533,52 @@ __global__ void __launch_bounds__(WARPS * 32) k_ea_direct(DirectArgs a) {
       asm volatile("cp.async.wait_group 0;\n" ::);
     }
     __syncwarp();
-    process<LOSS, WEIGHTED>(a, w, lane, head, kb + cur * WP, WEIGHTED ? wb + cur * WP : nullptr);
+    process<LOSS, WEIGHTED, MODE>(a, w, lane, head, kb + cur * WP, WEIGHTED ? wb + cur * WP : nullptr);
     __syncwarp();   // this buffer is refilled two warp runs later
     head = next;
   }
 }
 
-// per image pair: sum its records (fixed order), scale, chain rule
-template <int LOSS>
-__global__ void k_ea_segments(const float4* __restrict__ rec, const int* __restrict__ seg_rec,
-                              const float* __restrict__ params, const int* __restrict__ pi,
-                              const int* __restrict__ pj, int P, float inv_z,
-                              float* __restrict__ seg_grad, float* __restrict__ seg_loss) {
+// per image pair: sum its records (fixed order) -- or take dL/dE_n from a
+// saved copy -- scale, and apply the chain rule
+__global__ void k_ea_segments(SegArgs a) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   pdl_trigger();
-  if (n >= P) {
+  if (n >= a.P) {
     pdl_wait();
     return;
   }
-  const int r0 = seg_rec[2 * n], cnt = seg_rec[2 * n + 1];
-  const int ci = pi[n], cj = pj[n];
+  const int r0 = a.seg_rec[2 * n], cnt = a.seg_rec[2 * n + 1];
+  const int ci = a.pi[n], cj = a.pj[n];
   pdl_wait();               // records come from k_ea_direct
-  float* out = seg_grad + (size_t)kSegGradEa * n;
-  if (cnt == 0) {
-    for (int k = 0; k < kSegGradEa; ++k) out[k] = 0.f;
-    seg_loss[n] = 0.f;
-    return;
-  }
   float G[10];
   for (int k = 0; k < 10; ++k) G[k] = 0.f;
-  for (int r = r0; r < r0 + cnt; ++r) {
-    float4 v0 = rec[3 * r], v1 = rec[3 * r + 1], v2 = rec[3 * r + 2];
-    G[0] += v0.x; G[1] += v0.y; G[2] += v0.z; G[3] += v0.w;
-    G[4] += v1.x; G[5] += v1.y; G[6] += v1.z; G[7] += v1.w;
-    G[8] += v2.x; G[9] += v2.y;
+  if (a.dlde_in) {
+    for (int k = 0; k < 9; ++k) G[k] = a.dlde_in[9 * (size_t)n + k];
+  } else {
+    for (int r = r0; r < r0 + cnt; ++r) {
+      float4 v0 = a.rec[3 * r], v1 = a.rec[3 * r + 1], v2 = a.rec[3 * r + 2];
+      G[0] += v0.x; G[1] += v0.y; G[2] += v0.z; G[3] += v0.w;
+      G[4] += v1.x; G[5] += v1.y; G[6] += v1.z; G[7] += v1.w;
+      G[8] += v2.x; G[9] += v2.y;
+    }
+    for (int k = 0; k < 9; ++k) G[k] *= a.g_scale;
   }
-  const float gs = (LOSS == 1) ? 2.f * inv_z : inv_z;
-  for (int k = 0; k < 9; ++k) G[k] *= gs;
-  seg_loss[n] = G[9] * inv_z;
+  if (a.seg_loss) a.seg_loss[n] = G[9] * a.l_scale;
+  if (a.dlde_out)
+    for (int k = 0; k < 9; ++k) a.dlde_out[9 * (size_t)n + k] = G[k];
+  if (!a.seg_grad) return;
+  float* out = a.seg_grad + (size_t)kSegGradEa * n;
+  if (cnt == 0) {   // an image pair without keypoint pairs (its geometry may be degenerate)
+    for (int k = 0; k < kSegGradEa; ++k) out[k] = 0.f;
+    return;
+  }
+  if (a.grad_loss) {
+    const float gl = *a.grad_loss;
+    for (int k = 0; k < 9; ++k) G[k] *= gl;
+  }
   PairGeo g;
-  pair_geometry(params + 9 * ci, params + 9 * cj, g);
+  pair_geometry(a.params + 9 * ci, a.params + 9 * cj, g);
   float o[kSegGradEa];
   pair_backward(g, G, o);
   for (int k = 0; k < kSegGradEa; ++k) out[k] = o[k];
@@ -561,8 +592,8 @@ void launch_ea_tables(const float* params, const int* pi, const int* pj, const i
              step_counter);
 }
 
-template <int LOSS, bool WEIGHTED>
-static void launch_direct_t(const fm_problem* pr, const float* weights, cudaStream_t s) {
+template <int LOSS, bool WEIGHTED, int MODE>
+static void launch_direct_t(const fm_problem* pr, const float* weights, float* coef_out, cudaStream_t s) {
   DirectArgs a;
   a.kp = pr->kp;
   a.wts = weights;
@@ -570,43 +601,78 @@ static void launch_direct_t(const fm_problem* pr, const float* weights, cudaStre
   a.info = pr->wrun_info;
   a.seg_tab = pr->seg_tab;
   a.rec = pr->rec;
+  a.coef_out = coef_out;
   a.Z = (int)pr->Z;
   a.n_wruns = pr->n_wruns;
   const size_t smem = WARPS * (WEIGHTED ? kSmemPerWarpW : kSmemPerWarp);
   static int per_sm = 0;   // resident CTAs per SM (one device per process)
   if (per_sm == 0) {
-    cudaFuncSetAttribute(k_ea_direct<LOSS, WEIGHTED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ea_direct<LOSS, WEIGHTED>, WARPS * 32, smem);
+    cudaFuncSetAttribute(k_ea_direct<LOSS, WEIGHTED, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ea_direct<LOSS, WEIGHTED, MODE>, WARPS * 32, smem);
     if (per_sm < 1) per_sm = 1;
   }
   int ctas = (pr->n_wruns + WARPS - 1) / WARPS;
   int cap = per_sm * pr->sm_count;
   if (ctas > cap) ctas = cap;
-  launch_pdl(k_ea_direct<LOSS, WEIGHTED>, dim3(ctas), dim3(WARPS * 32), smem, s, a);
+  launch_pdl(k_ea_direct<LOSS, WEIGHTED, MODE>, dim3(ctas), dim3(WARPS * 32), smem, s, a);
+}
+
+template <int MODE>
+static void launch_direct_m(const fm_problem* pr, const float* weights, int loss, float* coef_out,
+                            cudaStream_t s) {
+  if (loss == FM_EA_L1) {
+    if (weights) launch_direct_t<0, true, MODE>(pr, weights, coef_out, s);
+    else launch_direct_t<0, false, MODE>(pr, nullptr, coef_out, s);
+  } else {
+    if (weights) launch_direct_t<1, true, MODE>(pr, weights, coef_out, s);
+    else launch_direct_t<1, false, MODE>(pr, nullptr, coef_out, s);
+  }
 }
 
 void launch_ea_direct(const fm_problem* pr, const float* weights, int loss, cudaStream_t s) {
   if (pr->n_wruns == 0) return;
-  if (loss == FM_EA_L1) {
-    if (weights) launch_direct_t<0, true>(pr, weights, s);
-    else launch_direct_t<0, false>(pr, nullptr, s);
-  } else {
-    if (weights) launch_direct_t<1, true>(pr, weights, s);
-    else launch_direct_t<1, false>(pr, nullptr, s);
-  }
+  launch_direct_m<kFull>(pr, weights, loss, nullptr, s);
+}
+
+void launch_ea_direct_loss(const fm_problem* pr, const float* weights, int loss, float* coef_out,
+                           cudaStream_t s) {
+  if (pr->n_wruns == 0) return;
+  launch_direct_m<kLossOnly>(pr, weights, loss, coef_out, s);
+}
+
+void launch_ea_direct_from_coef(const fm_problem* pr, const float* coef, cudaStream_t s) {
+  if (pr->n_wruns == 0) return;
+  launch_direct_t<0, true, kFromCoef>(pr, coef, nullptr, s);
+}
+
+SegArgs seg_args(const fm_problem* pr, const float* params) {
+  SegArgs a;
+  a.rec = pr->rec;
+  a.seg_rec = pr->seg_rec;
+  a.dlde_in = nullptr;
+  a.params = params;
+  a.pi = pr->pair_i;
+  a.pj = pr->pair_j;
+  a.P = pr->P;
+  a.g_scale = 0.f;
+  a.l_scale = 0.f;
+  a.grad_loss = nullptr;
+  a.seg_grad = pr->seg_grad;
+  a.seg_loss = pr->seg_loss;
+  a.dlde_out = nullptr;
+  return a;
+}
+
+void launch_ea_segments(const SegArgs& a, cudaStream_t s) {
+  launch_pdl(k_ea_segments, dim3((a.P + 127) / 128), dim3(128), 0, s, a);
 }
 
 void launch_ea_segments(const fm_problem* pr, const float* params, int loss, float inv_z,
                         cudaStream_t s) {
-  const int P = pr->P;
-  if (loss == FM_EA_L1)
-    launch_pdl(k_ea_segments<0>, dim3((P + 127) / 128), dim3(128), 0, s, (const float4*)pr->rec,
-               (const int*)pr->seg_rec, params, (const int*)pr->pair_i, (const int*)pr->pair_j, P, inv_z,
-               pr->seg_grad, pr->seg_loss);
-  else
-    launch_pdl(k_ea_segments<1>, dim3((P + 127) / 128), dim3(128), 0, s, (const float4*)pr->rec,
-               (const int*)pr->seg_rec, params, (const int*)pr->pair_i, (const int*)pr->pair_j, P, inv_z,
-               pr->seg_grad, pr->seg_loss);
+  SegArgs a = seg_args(pr, params);
+  a.g_scale = (loss == FM_EA_L1) ? inv_z : 2.f * inv_z;
+  a.l_scale = inv_z;
+  launch_ea_segments(a, s);
 }
 
 }  // namespace fm

@@ -30,7 +30,7 @@ enum : int {
 enum KernelId : int {
   kKCalibrate = 0, kKSegOffsets, kKRunTables, kKEaTables, kKEaDirect, kKEaSegments,
   kKRotPairs, kKTrnTargets, kKTrnPairs, kKCamUpdate, kKLossSum, kKEaReweight, kKWBuild,
-  kKEaCompact, kKMartIter, kKRelTrans, kKMerge, kKTriangulate, kKCount
+  kKEaCompact, kKMartIter, kKRelTrans, kKMerge, kKTriangulate, kKEaDirectLoss, kKEaDirectCoef, kKCount
 };
 extern const char* const kKernelNames[kKCount];
 
@@ -179,6 +179,30 @@ void launch_exclusive_scan_info(int4* wrun_info, int n, int64_t* total_out_dev, 
 void launch_ea_tables(const float* params, const int* pi, const int* pj, const int* seg_off,
                       int P, float4* seg_tab, int* step_counter, cudaStream_t s);
 void launch_ea_direct(const fm_problem* pr, const float* weights, int loss, cudaStream_t s);
+// the loss alone; coef_out (optional, Z floats) receives w drho/dr per pair
+void launch_ea_direct_loss(const fm_problem* pr, const float* weights, int loss, float* coef_out,
+                           cudaStream_t s);
+// dL/dE records from stored per-pair coefficients (no residual recompute)
+void launch_ea_direct_from_coef(const fm_problem* pr, const float* coef, cudaStream_t s);
+
+// per-image-pair pass after k_ea_direct
+struct SegArgs {
+  const float4* rec;       // records of k_ea_direct
+  const int* seg_rec;      // [P][2] first record, count
+  const float* dlde_in;    // [P][9] saved dL/dE_n: used instead of the records when not null
+  const float* params;     // [N][9]
+  const int* pi;
+  const int* pj;
+  int P;
+  float g_scale;           // factor on the summed coefficient terms
+  float l_scale;           // factor on the summed loss terms
+  const float* grad_loss;  // device scalar multiplying the gradient (null: 1)
+  float* seg_grad;         // [P][24] chain rule (null: skipped)
+  float* seg_loss;         // [P] (null: skipped)
+  float* dlde_out;         // [P][9] scaled dL/dE_n (null: skipped)
+};
+SegArgs seg_args(const fm_problem* pr, const float* params);
+void launch_ea_segments(const SegArgs& a, cudaStream_t s);
 void launch_ea_segments(const fm_problem* pr, const float* params, int loss, float inv_z,
                         cudaStream_t s);
 

@@ -35,6 +35,10 @@ FM_EA_L1 = 0
 FM_EA_L2 = 1
 FM_EA_COMPACT = 2
 
+FM_EA_SAVE_NONE = 0
+FM_EA_SAVE_COEF = 1
+FM_EA_SAVE_DLDE = 2
+
 _c_i32p = ctypes.POINTER(ctypes.c_int32)
 _c_f32p = ctypes.POINTER(ctypes.c_float)
 
@@ -124,6 +128,10 @@ _SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_float)]),
     "fm_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_int32]),
+    "fm_ea_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                     ctypes.c_void_p]),
+    "fm_ea_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
     "fm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(fm_adam_opts), ctypes.c_int32,
                                ctypes.c_void_p]),
     "fm_timing_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
@@ -302,6 +310,16 @@ def fm_loss_grad(handle, stage, params, loss_out, grad_out, mem_on_device):
     """Raw call: params / grad_out are addresses (int) or None, loss_out a
     ctypes float array or None."""
     _check(lib().fm_loss_grad(handle, stage, params, loss_out, grad_out, int(mem_on_device)), handle)
+
+
+def fm_ea_forward(handle, params_dev, loss_dev, save, saved_dev):
+    """Raw call: device addresses (int) or None."""
+    _check(lib().fm_ea_forward(handle, params_dev, loss_dev, int(save), saved_dev), handle)
+
+
+def fm_ea_backward(handle, params_dev, save, saved_dev, grad_loss_dev, grad_dev):
+    """Raw call: device addresses (int) or None."""
+    _check(lib().fm_ea_backward(handle, params_dev, int(save), saved_dev, grad_loss_dev, grad_dev), handle)
 
 
 def fm_step(handle, stage, opts: fm_adam_opts, n_iters, loss_out=None):
