@@ -2,8 +2,9 @@
 // over the image pairs it belongs to (camera CSR, fixed order), of the
 // per-image-pair gradients; rotations then go through the adjoint of the 6D
 // map (Sec. 3.3), and Adam updates the camera's parameters in place.
-// One warp per camera; lanes stride over the incident image pairs and a
-// butterfly reduction combines them, so the order of additions is fixed.
+// One CTA per camera; threads stride over the incident image pairs, a
+// butterfly inside each warp and a fixed-order sum over the warps combine
+// them, so the order of additions is fixed.
 #include "fm_device.cuh"
 #include "fm_internal.h"
 
@@ -18,16 +19,25 @@ template <> struct Layout<0> { static constexpr int PART = 9, PDIM = 6; static c
 template <> struct Layout<1> { static constexpr int PART = 3, PDIM = 3; static constexpr bool ROT = false; };
 template <> struct Layout<2> { static constexpr int PART = 12, PDIM = 9; static constexpr bool ROT = true; };
 
-constexpr int kCamWarps = 4;
+constexpr int kCamThreads = 128;
+constexpr int kCamWarps = kCamThreads / 32;
 
-// fixed-order sum of the per-image-pair loss terms of one run (one CTA)
+// fixed-order sum of the per-image-pair loss terms of one run (one CTA; four
+// independent accumulators per thread keep four loads in flight)
 __device__ void loss_sum_cta(const float* __restrict__ x, int n, float* out) {
-  __shared__ float part[kCamWarps * 32];
-  float s = 0.f;
-  for (int k = threadIdx.x; k < n; k += kCamWarps * 32) s += x[k];
-  part[threadIdx.x] = s;
+  __shared__ float part[kCamThreads];
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  int k = threadIdx.x;
+  for (; k + 3 * kCamThreads < n; k += 4 * kCamThreads) {
+    s0 += x[k];
+    s1 += x[k + kCamThreads];
+    s2 += x[k + 2 * kCamThreads];
+    s3 += x[k + 3 * kCamThreads];
+  }
+  for (; k < n; k += kCamThreads) s0 += x[k];
+  part[threadIdx.x] = (s0 + s1) + (s2 + s3);
   __syncthreads();
-  for (int d = kCamWarps * 16; d > 0; d >>= 1) {
+  for (int d = kCamThreads / 2; d > 0; d >>= 1) {
     if ((int)threadIdx.x < d) part[threadIdx.x] += part[threadIdx.x + d];
     __syncthreads();
   }
@@ -35,9 +45,10 @@ __device__ void loss_sum_cta(const float* __restrict__ x, int n, float* out) {
 }
 
 template <int STAGE, bool ADAM>
-__global__ void __launch_bounds__(kCamWarps * 32) k_cam(CamUpdate u) {
+__global__ void __launch_bounds__(kCamThreads) k_cam(CamUpdate u) {
   using L = Layout<STAGE>;
   const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   const int run = blockIdx.y;
   pdl_trigger();
   if (u.loss_out && blockIdx.x == gridDim.x - 1) {
@@ -46,31 +57,51 @@ __global__ void __launch_bounds__(kCamWarps * 32) k_cam(CamUpdate u) {
     loss_sum_cta(u.seg_loss + (size_t)run * u.P, u.P, u.loss_out + run);
     return;
   }
-  const int c = blockIdx.x * kCamWarps + (threadIdx.x >> 5);
-  if (c >= u.N) {
-    pdl_wait();
-    return;
-  }
+  const int c = blockIdx.x;                                    // one CTA per camera
   const int b = u.cam_seg_off[c], e = u.cam_seg_off[c + 1];   // static: before the wait
   pdl_wait();
-  const float* prm = u.params + ((size_t)run * u.N + c) * L::PDIM;
-  float p[L::PDIM];
-#pragma unroll
-  for (int k = 0; k < L::PDIM; ++k) p[k] = prm[k];
   float acc[L::PART];
 #pragma unroll
   for (int k = 0; k < L::PART; ++k) acc[k] = 0.f;
   const float* sg = u.seg_grad + (size_t)run * u.P * 2 * L::PART;
-  for (int idx = b + lane; idx < e; idx += 32) {
+  for (int idx = b + (int)threadIdx.x; idx < e; idx += kCamThreads) {
     const unsigned v = (unsigned)u.cam_seg[idx];
     const int n = (int)(v & 0x7fffffffu);
     const int role = (int)(v >> 31);
     const float* g = sg + ((size_t)n * 2 + role) * L::PART;
+    if (L::PART % 4 == 0) {
+      // 48-B parts of a cudaMalloc'd buffer: 16-B aligned
 #pragma unroll
-    for (int k = 0; k < L::PART; ++k) acc[k] += g[k];
+      for (int q = 0; q < L::PART / 4; ++q) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(g) + q);
+        acc[4 * q] += t.x;
+        acc[4 * q + 1] += t.y;
+        acc[4 * q + 2] += t.z;
+        acc[4 * q + 3] += t.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < L::PART; ++k) acc[k] += __ldg(g + k);
+    }
   }
+  __shared__ float red[kCamWarps][L::PART];
 #pragma unroll
   for (int k = 0; k < L::PART; ++k) acc[k] = warp_sum(acc[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < L::PART; ++k) red[warp][k] = acc[k];
+  __syncthreads();
+  if (warp != 0) return;
+#pragma unroll
+  for (int k = 0; k < L::PART; ++k) {
+    float t = red[0][k];
+    for (int w = 1; w < kCamWarps; ++w) t += red[w][k];
+    acc[k] = t;
+  }
+  const float* prm = u.params + ((size_t)run * u.N + c) * L::PDIM;
+  float p[L::PDIM];
+#pragma unroll
+  for (int k = 0; k < L::PDIM; ++k) p[k] = prm[k];
   float g[L::PDIM];
   if (L::ROT) {
     Rot6 s;
@@ -132,9 +163,9 @@ __global__ void k_sum_fixed(const float* __restrict__ x, int n, float* __restric
 
 template <int STAGE>
 void launch_stage(const CamUpdate& u, cudaStream_t s) {
-  dim3 grid((u.N + kCamWarps - 1) / kCamWarps + (u.loss_out ? 1 : 0), u.runs);
-  if (u.params_out) launch_pdl(k_cam<STAGE, true>, grid, dim3(kCamWarps * 32), 0, s, u);
-  else launch_pdl(k_cam<STAGE, false>, grid, dim3(kCamWarps * 32), 0, s, u);
+  dim3 grid(u.N + (u.loss_out ? 1 : 0), u.runs);
+  if (u.params_out) launch_pdl(k_cam<STAGE, true>, grid, dim3(kCamThreads), 0, s, u);
+  else launch_pdl(k_cam<STAGE, false>, grid, dim3(kCamThreads), 0, s, u);
 }
 
 }  // namespace

@@ -505,7 +505,7 @@ __device__ __forceinline__ void process(const DirectArgs& a, int w, int lane, co
 }
 
 template <int LOSS, bool WEIGHTED, int MODE>
-__global__ void __launch_bounds__(WARPS * 32) k_ea_direct(DirectArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, kEaMinCtas) k_ea_direct(DirectArgs a) {
   extern __shared__ float4 smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -539,29 +539,46 @@ __global__ void __launch_bounds__(WARPS * 32) k_ea_direct(DirectArgs a) {
   }
 }
 
-// per image pair: sum its records (fixed order) -- or take dL/dE_n from a
-// saved copy -- scale, and apply the chain rule
+// per image pair: sum its records -- or take dL/dE_n from a saved copy --
+// scale, and apply the chain rule.  kSegLanes lanes share an image pair: they
+// sum its records with a stride of kSegLanes and combine them with a
+// butterfly inside the group (a fixed order), so that image pairs spanning
+// many warp runs are not summed by one thread; the group's first lane then
+// applies the chain rule.
+constexpr int kSegLanes = 8;
+
 __global__ void k_ea_segments(SegArgs a) {
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = gid / kSegLanes;
+  const int sub = gid % kSegLanes;
   pdl_trigger();
-  if (n >= a.P) {
-    pdl_wait();
-    return;
+  const bool valid = n < a.P;
+  int r0 = 0, cnt = 0, ci = 0, cj = 0;
+  if (valid) {
+    r0 = a.seg_rec[2 * n];
+    cnt = a.seg_rec[2 * n + 1];
+    ci = a.pi[n];
+    cj = a.pj[n];
   }
-  const int r0 = a.seg_rec[2 * n], cnt = a.seg_rec[2 * n + 1];
-  const int ci = a.pi[n], cj = a.pj[n];
   pdl_wait();               // records come from k_ea_direct
   float G[10];
   for (int k = 0; k < 10; ++k) G[k] = 0.f;
-  if (a.dlde_in) {
-    for (int k = 0; k < 9; ++k) G[k] = a.dlde_in[9 * (size_t)n + k];
-  } else {
-    for (int r = r0; r < r0 + cnt; ++r) {
-      float4 v0 = a.rec[3 * r], v1 = a.rec[3 * r + 1], v2 = a.rec[3 * r + 2];
+  if (valid && !a.dlde_in) {
+    for (int r = r0 + sub; r < r0 + cnt; r += kSegLanes) {
+      const float4 v0 = a.rec[3 * r], v1 = a.rec[3 * r + 1], v2 = a.rec[3 * r + 2];
       G[0] += v0.x; G[1] += v0.y; G[2] += v0.z; G[3] += v0.w;
       G[4] += v1.x; G[5] += v1.y; G[6] += v1.z; G[7] += v1.w;
       G[8] += v2.x; G[9] += v2.y;
     }
+  }
+#pragma unroll
+  for (int d = kSegLanes / 2; d > 0; d >>= 1)
+#pragma unroll
+    for (int k = 0; k < 10; ++k) G[k] += __shfl_xor_sync(0xffffffffu, G[k], d);
+  if (!valid || sub != 0) return;
+  if (a.dlde_in) {
+    for (int k = 0; k < 9; ++k) G[k] = a.dlde_in[9 * (size_t)n + k];
+  } else {
     for (int k = 0; k < 9; ++k) G[k] *= a.g_scale;
   }
   if (a.seg_loss) a.seg_loss[n] = G[9] * a.l_scale;
@@ -581,7 +598,13 @@ __global__ void k_ea_segments(SegArgs a) {
   pair_geometry(a.params + 9 * ci, a.params + 9 * cj, g);
   float o[kSegGradEa];
   pair_backward(g, G, o);
-  for (int k = 0; k < kSegGradEa; ++k) out[k] = o[k];
+  if ((reinterpret_cast<uintptr_t>(out) & 15u) == 0) {   // library buffers: 96-B rows, 16-B aligned
+    float4* o4 = reinterpret_cast<float4*>(out);
+#pragma unroll
+    for (int k = 0; k < kSegGradEa / 4; ++k) o4[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+  } else {
+    for (int k = 0; k < kSegGradEa; ++k) out[k] = o[k];
+  }
 }
 
 }  // namespace
@@ -664,7 +687,8 @@ SegArgs seg_args(const fm_problem* pr, const float* params) {
 }
 
 void launch_ea_segments(const SegArgs& a, cudaStream_t s) {
-  launch_pdl(k_ea_segments, dim3((a.P + 127) / 128), dim3(128), 0, s, a);
+  const long long threads = (long long)a.P * kSegLanes;
+  launch_pdl(k_ea_segments, dim3((unsigned)((threads + 127) / 128)), dim3(128), 0, s, a);
 }
 
 void launch_ea_segments(const fm_problem* pr, const float* params, int loss, float inv_z,

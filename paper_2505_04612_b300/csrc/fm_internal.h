@@ -12,9 +12,24 @@
 namespace fm {
 
 // ---------------------------------------------------------------- constants
-constexpr int kEaPairsPerLane = 15;              // U: keypoint pairs per lane (odd)
-constexpr int kEaWarpPairs = 32 * kEaPairsPerLane;  // keypoint pairs per warp run
-constexpr int kEaWarpsPerCta = 2;
+// tile of the direct epipolar kernel (overridable at build time for tuning)
+#ifndef FM_EA_PAIRS_PER_LANE
+#define FM_EA_PAIRS_PER_LANE 15
+#endif
+#ifndef FM_EA_WARPS_PER_CTA
+#define FM_EA_WARPS_PER_CTA 2
+#endif
+constexpr int kEaPairsPerLane = FM_EA_PAIRS_PER_LANE;  // U: keypoint pairs per lane (odd)
+constexpr int kEaWarpPairs = 32 * kEaPairsPerLane;     // keypoint pairs per warp run
+constexpr int kEaWarpsPerCta = FM_EA_WARPS_PER_CTA;
+// register budget of k_ea_direct: at least this many CTAs per SM (shared
+// memory allows 7 at two warps per CTA, so 8 costs no occupancy and leaves
+// the compiler 128 registers to interleave a lane's pairs)
+#ifndef FM_EA_MIN_CTAS
+#define FM_EA_MIN_CTAS 8
+#endif
+constexpr int kEaMinCtas = FM_EA_MIN_CTAS;
+static_assert(kEaPairsPerLane % 2 == 1, "lane-contiguous shared-memory reads need an odd stride");
 constexpr int kSegGradEa = 24;                   // dR_i, dt_i, dR_j, dt_j
 constexpr int kSegGradRot = 18;                  // dR_i, dR_j
 constexpr int kSegGradTrn = 6;                   // do_i, do_j
