@@ -37,6 +37,15 @@
  *     returns after the work is enqueued, unless it writes a host buffer, in
  *     which case it synchronises that stream first.
  *
+ * Scenes (batches)
+ *   - One problem may hold S independent scenes (fm_problem_desc.n_scenes):
+ *     their cameras, image pairs and keypoint pairs are concatenated, scene
+ *     by scene.  Every kernel runs once over all of them; every loss is the
+ *     scene's own (normalised by the scene's own |P| or Z), so that a scene
+ *     gets the same losses, gradients and Adam steps as when solved alone.
+ *   - Loss outputs hold one value per scene: [S] for the rotation and
+ *     epipolar stages, [m][S] (run-major) for m translation runs.
+ *
  * Errors
  *   - Every entry point returns an fm_status; no C++ exception crosses the
  *     ABI and the library never exits or aborts.
@@ -104,8 +113,8 @@ typedef struct {
                                   image pair, image pairs in index order) */
   const float* kp1_px;         /* [Z*2] (u, v) of the keypoint in image i_n */
   const float* kp2_px;         /* [Z*2] (u, v) of the keypoint in image j_n */
-  const int32_t* kp_track;     /* [Z] track id, or NULL (used by no entry
-                                  point yet; copied if given) */
+  const int32_t* kp_track;     /* [Z] track id (>= 0), or NULL; needed by
+                                  fm_triangulate only */
   const float* focal;          /* [N] > 0 */
   const float* cx;             /* [N] */
   const float* cy;             /* [N] */
@@ -113,6 +122,13 @@ typedef struct {
   const float* rel_t;          /* [P*3] unit t^{i->j}, or NULL */
   int32_t inputs_on_device;    /* 1: every pointer above is device memory */
   void* cuda_stream;           /* cudaStream_t to run on; NULL = default */
+  int32_t n_scenes;            /* S: independent scenes held by the problem;
+                                  0 or 1 = one scene (scene_cam_off unused) */
+  const int32_t* scene_cam_off; /* [S+1] host memory: cameras of scene s are
+                                  [off[s], off[s+1]), off[0] = 0, off[S] = N,
+                                  >= 2 cameras each; every image pair joins two
+                                  cameras of one scene, image pairs are grouped
+                                  by scene in scene order, >= 1 per scene */
 } fm_problem_desc;
 
 typedef struct {
@@ -123,6 +139,7 @@ typedef struct {
   int32_t pairs_per_lane;      /* keypoint pairs per thread in the direct kernel */
   int64_t n_records;           /* per-(warp run, image pair) partial sums */
   int64_t device_bytes;        /* device memory held by the problem */
+  int32_t n_scenes;            /* S */
 } fm_problem_info;
 
 /* Adam (the paper's cited adaptive first-order method, Sec. 1, Sec. 3.2; no
@@ -183,8 +200,10 @@ fm_status fm_ea_set_loss(fm_problem* problem, fm_ea_loss loss);
 
 /* Per-keypoint-pair weights w_m of the epipolar stage (Eq. 9: IRLS weights
  * 1/|eps^_m|; a weight of 0 removes a filtered pair), in the order of the
- * keypoint pairs given at creation, and the normaliser 1/Z of the loss.
- * weights == NULL restores unit weights and inv_z = 1/n_kp_pairs.  The compact
+ * keypoint pairs given at creation, and the normaliser 1/Z of the loss:
+ * inv_z > 0 is used for every scene; inv_z == 0 gives each scene
+ * 1/(number of its pairs with a positive weight).  weights == NULL restores
+ * unit weights and 1/(the scene's keypoint pairs).  The compact
  * matrices W_n (Eq. 17) are rebuilt by the next FM_EA_COMPACT evaluation,
  * stored as an expansion around the essential matrices of the parameters of
  * that evaluation. */
@@ -196,14 +215,15 @@ fm_status fm_ea_set_weights(fm_problem* problem, const float* weights,
  * previous round, Eq. 9; periodic filtering of pairs with a large error).
  * For every keypoint pair, eps^ = x~2^T E_n x~1; the pair is kept when
  * |eps^| < tau and then weighted 1/max(|eps^|, delta) when irls != 0, or 1
- * when irls == 0; filtered pairs get weight 0.  Sets inv_z = 1/#kept,
- * rebuilds W_n around the current poses, and writes #kept to *n_kept (may be
- * NULL).  Synchronises. */
+ * when irls == 0; filtered pairs get weight 0.  Sets each scene's inv_z to
+ * 1/(its kept pairs), rebuilds W_n around the current poses, and writes the
+ * total #kept over all scenes to *n_kept (may be NULL).  Synchronises. */
 fm_status fm_ea_reweight(fm_problem* problem, float tau, float delta, int32_t irls,
                          int64_t* n_kept);
 
 /* Copies the current per-pair weights (host or device as flagged) and the
- * loss normaliser.  FM_ERR_STATE when no weights are set.  Synchronises. */
+ * loss normaliser (of scene 0).  FM_ERR_STATE when no weights are set.
+ * Synchronises. */
 fm_status fm_ea_get_weights(fm_problem* problem, float* weights_out, int32_t out_on_device,
                             float* inv_z);
 
@@ -212,8 +232,8 @@ fm_status fm_ea_get_weights(fm_problem* problem, float* weights_out, int32_t out
  * o^{i->j} = -R_j^T t^{i->j} from the rotation-stage parameters; Eq. 7 or
  * Eqs. 8-9 for the epipolar stage, with the loss chosen by fm_ea_set_loss).
  * params: [N*dim] (layout above; [m*N*3] for m translation runs); grad: same
- * layout, or NULL; loss: host array of one value ([m] for the translation
- * stage), or NULL.  mem_on_device: 1 if params and grad are device pointers.
+ * layout, or NULL; loss: host array of one value per scene ([m][S] for the
+ * translation stage), or NULL.  mem_on_device: 1 if params and grad are device pointers.
  * The stage's own parameters and Adam state are not touched.  Synchronises
  * when loss or a host grad is requested. */
 fm_status fm_loss_grad(fm_problem* problem, fm_stage stage, const float* params,
@@ -245,24 +265,25 @@ typedef enum {
 
 /* Forward pass: the epipolar loss (current loss and weights of the problem;
  * FM_ERR_STATE for FM_EA_COMPACT) at params_dev [N*9] into loss_dev (one
- * device float), and the intermediates selected by `save` into saved_dev
+ * device float per scene), and the intermediates selected by `save` into saved_dev
  * (device, 16-byte aligned: Z floats for FM_EA_SAVE_COEF, P*9 for
  * FM_EA_SAVE_DLDE, ignored for FM_EA_SAVE_NONE).  All pointers are device
  * memory owned by the caller.  Asynchronous on the problem's stream. */
 fm_status fm_ea_forward(fm_problem* problem, const float* params_dev, float* loss_dev,
                         int32_t save, float* saved_dev);
 
-/* Backward pass: grad_dev [N*9] = g * dL/dparams at params_dev, where g is the
- * device scalar *grad_loss_dev (1 when grad_loss_dev is NULL).  `save` and
- * saved_dev must be those of the forward call at the same params_dev, and the
- * loss and weights must be unchanged since.  Asynchronous. */
+/* Backward pass: grad_dev [N*9] = sum_s g_s dL_s/dparams at params_dev, where
+ * g_s is grad_loss_dev[s], one device float per scene (all 1 when
+ * grad_loss_dev is NULL).  `save` and saved_dev must be those of the forward
+ * call at the same params_dev, and the loss and weights must be unchanged
+ * since.  Asynchronous. */
 fm_status fm_ea_backward(fm_problem* problem, const float* params_dev, int32_t save,
                          const float* saved_dev, const float* grad_loss_dev, float* grad_dev);
 
 /* n_iters Adam steps on the stage's parameters, each one a full evaluation of
  * the loss and gradient (over all keypoint pairs for the epipolar stage)
- * followed by the update (Sec. 3.2-3.4).  loss (host, or NULL; [m] for the
- * translation stage) receives the loss of the last evaluation, i.e. at the
+ * followed by the update (Sec. 3.2-3.4).  loss (host, or NULL; [S], or
+ * [m][S] for the translation stage) receives the loss of the last evaluation, i.e. at the
  * parameters before the last update; passing NULL keeps the call
  * asynchronous. */
 fm_status fm_step(fm_problem* problem, fm_stage stage, const fm_adam_opts* opts,
@@ -363,10 +384,12 @@ typedef struct {
   int32_t* point_valid;       /* [T] or NULL */
   int32_t n_tracks;           /* out: T */
   int32_t n_points_valid;     /* out */
-  float loss_rotation;        /* out: final losses of the three stages */
+  float loss_rotation;        /* out: final losses of the three stages
+                                 (summed over the scenes of a batch) */
   float loss_translation;
   float loss_epipolar;
-  int64_t n_kept;             /* out: keypoint pairs kept by the last filtering */
+  int64_t n_kept;             /* out: keypoint pairs kept by the last filtering
+                                 (all scenes) */
 } fm_result;
 
 /* Runs the whole first-order pipeline: fm_rotation_init, Adam on the rotation

@@ -52,7 +52,9 @@ class EpipolarLoss(torch.autograd.Function):
         if params.numel() != 9 * problem.n_cams:
             raise ValueError(f"params must hold {9 * problem.n_cams} values")
         save = MODES[mode]
-        loss = torch.empty((), dtype=torch.float32, device=params.device)
+        # one loss per scene of a batched problem; a scalar for one scene
+        S = getattr(problem, "S", 1)
+        loss = torch.empty(() if S == 1 else (S,), dtype=torch.float32, device=params.device)
         saved = _saved_buffer(problem, save, params.device)
         F.fm_ea_forward(problem.handle, params.data_ptr(), loss.data_ptr(), save,
                         saved.data_ptr() if saved is not None else None)
@@ -67,6 +69,7 @@ class EpipolarLoss(torch.autograd.Function):
         g = grad_loss.detach()
         if g.dtype != torch.float32:
             g = g.float()
+        g = g.contiguous()
         grad = torch.empty_like(params)
         F.fm_ea_backward(ctx.problem.handle, params.data_ptr(), ctx.save,
                          saved.data_ptr() if saved is not None else None, g.data_ptr(), grad.data_ptr())

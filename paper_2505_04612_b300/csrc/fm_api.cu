@@ -166,6 +166,8 @@ void release(fm_problem* pr) {
   dfree(pr->d_kept);
   dfree(pr->kp_seg); dfree(pr->track_off); dfree(pr->track_idx);
   dfree(pr->merge_buf); dfree(pr->best_run);
+  dfree(pr->sc_cam_off); dfree(pr->sc_pair_off); dfree(pr->sc_kp_off); dfree(pr->cam_scene);
+  dfree(pr->pair_scene); dfree(pr->pair_inv_p); dfree(pr->pair_inv_z); dfree(pr->mart_coef);
   drain_timing(pr, false);
   for (cudaEvent_t e : pr->event_pool) cudaEventDestroy(e);
   pr->event_pool.clear();
@@ -213,10 +215,52 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
     if (!(std::isfinite(hcx[c]) && std::isfinite(hcy[c])))
       return fail(pr, FM_ERR_INVALID_ARG, "principal point of camera " + std::to_string(c) + " is not finite");
   }
+  // ---- scenes: camera ranges, image pairs grouped by scene
+  const int S = d->n_scenes > 1 ? d->n_scenes : 1;
+  pr->S = S;
+  pr->h_sc_cam_off.assign(S + 1, 0);
+  if (S > 1) {
+    if (!d->scene_cam_off) return fail(pr, FM_ERR_INVALID_ARG, "scene_cam_off is required when n_scenes > 1");
+    for (int q = 0; q <= S; ++q) pr->h_sc_cam_off[q] = d->scene_cam_off[q];
+    if (pr->h_sc_cam_off[0] != 0 || pr->h_sc_cam_off[S] != N)
+      return fail(pr, FM_ERR_INVALID_ARG, "scene_cam_off must start at 0 and end at n_cams");
+    for (int q = 0; q < S; ++q)
+      if (pr->h_sc_cam_off[q + 1] - pr->h_sc_cam_off[q] < 2)
+        return fail(pr, FM_ERR_INVALID_ARG, "scene " + std::to_string(q) + " has fewer than 2 cameras");
+  } else {
+    pr->h_sc_cam_off[1] = N;
+  }
+  std::vector<int> cam_scene(N), pair_scene(P);
+  for (int q = 0; q < S; ++q)
+    for (int c = pr->h_sc_cam_off[q]; c < pr->h_sc_cam_off[q + 1]; ++c) cam_scene[c] = q;
+  pr->h_sc_pair_off.assign(S + 1, 0);
+  for (int n = 0; n < P; ++n) {
+    const int q = cam_scene[hi[n]];
+    if (cam_scene[hj[n]] != q)
+      return fail(pr, FM_ERR_INVALID_ARG, "image pair " + std::to_string(n) + " joins cameras of two scenes");
+    if (n > 0 && q < pair_scene[n - 1])
+      return fail(pr, FM_ERR_INVALID_ARG, "image pairs are not grouped by scene in scene order");
+    pair_scene[n] = q;
+    pr->h_sc_pair_off[q + 1]++;
+  }
+  for (int q = 0; q < S; ++q) {
+    if (pr->h_sc_pair_off[q + 1] == 0)
+      return fail(pr, FM_ERR_INVALID_ARG, "scene " + std::to_string(q) + " has no image pair");
+    pr->h_sc_pair_off[q + 1] += pr->h_sc_pair_off[q];
+  }
+  std::vector<float> inv_p(P);
+  for (int n = 0; n < P; ++n) {
+    const int q = pair_scene[n];
+    inv_p[n] = 1.f / (float)(pr->h_sc_pair_off[q + 1] - pr->h_sc_pair_off[q]);
+  }
+
   // camera -> incident image pairs, ordered by image pair (deterministic sums)
   std::vector<int> coff(N + 1, 0), cseg(2 * (size_t)P);
   for (int n = 0; n < P; ++n) { coff[hi[n] + 1]++; coff[hj[n] + 1]++; }
   for (int c = 0; c < N; ++c) pr->max_degree = std::max(pr->max_degree, coff[c + 1]);
+  pr->h_sc_max_degree.assign(S, 0);
+  for (int c = 0; c < N; ++c)
+    pr->h_sc_max_degree[cam_scene[c]] = std::max(pr->h_sc_max_degree[cam_scene[c]], coff[c + 1]);
   for (int c = 0; c < N; ++c) coff[c + 1] += coff[c];
   {
     std::vector<int> fill(coff.begin(), coff.end() - 1);
@@ -243,6 +287,20 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   FM_CUDA(pr, cudaMemcpyAsync(pr->cam_seg_off, coff.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->cam_seg, cseg.data(), sizeof(int) * 2 * (size_t)P, cudaMemcpyHostToDevice, s));
   FM_CUDA(pr, cudaMemsetAsync(pr->d_err, 0, sizeof(int), s));
+  FM_ALLOC(pr, pr->sc_cam_off, S + 1);
+  FM_ALLOC(pr, pr->sc_pair_off, S + 1);
+  FM_ALLOC(pr, pr->sc_kp_off, S + 1);
+  FM_ALLOC(pr, pr->cam_scene, N);
+  FM_ALLOC(pr, pr->pair_scene, P);
+  FM_ALLOC(pr, pr->pair_inv_p, P);
+  FM_ALLOC(pr, pr->pair_inv_z, P);
+  FM_ALLOC(pr, pr->mart_coef, 3 * (size_t)S);
+  FM_CUDA(pr, cudaMemcpyAsync(pr->sc_cam_off, pr->h_sc_cam_off.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice, s));
+  FM_CUDA(pr, cudaMemcpyAsync(pr->sc_pair_off, pr->h_sc_pair_off.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice, s));
+  FM_CUDA(pr, cudaMemcpyAsync(pr->cam_scene, cam_scene.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  FM_CUDA(pr, cudaMemcpyAsync(pr->pair_scene, pair_scene.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
+  FM_CUDA(pr, cudaMemcpyAsync(pr->pair_inv_p, inv_p.data(), sizeof(float) * P, cudaMemcpyHostToDevice, s));
+  FM_CUDA(pr, cudaStreamSynchronize(s));   // the host vectors above are locals
 
   // ---- keypoints: stage host inputs on the device, calibrate, offsets
   FM_ALLOC(pr, pr->kp, Z);
@@ -299,6 +357,17 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
     int e = 0;
     for (int n = 0; n < P; ++n) e += (so[n] == so[n + 1]);
     pr->n_empty = e;
+    // keypoint range of each scene, and the unit-weight normaliser 1/Z_s
+    pr->h_sc_kp_off.assign(S + 1, 0);
+    for (int q = 0; q <= S; ++q) pr->h_sc_kp_off[q] = so[pr->h_sc_pair_off[q]];
+    std::vector<float> inv_z(P);
+    for (int n = 0; n < P; ++n) {
+      const int q = pair_scene[n];
+      const int64_t zq = pr->h_sc_kp_off[q + 1] - pr->h_sc_kp_off[q];
+      inv_z[n] = zq > 0 ? (float)(1.0 / (double)zq) : 0.f;
+    }
+    FM_CUDA(pr, cudaMemcpy(pr->sc_kp_off, pr->h_sc_kp_off.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice));
+    FM_CUDA(pr, cudaMemcpy(pr->pair_inv_z, inv_z.data(), sizeof(float) * P, cudaMemcpyHostToDevice));
   }
 
   // ---- tables of the direct epipolar kernel
@@ -345,13 +414,16 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   if ((a = alloc_adam(pr, pr->trn_adam, 3 * (size_t)N)) != FM_OK) return a;
   FM_ALLOC(pr, pr->scratch_params, 9 * (size_t)N);
   FM_ALLOC(pr, pr->scratch_grad, 9 * (size_t)N);
-  FM_ALLOC(pr, pr->d_loss, 1);
+  FM_ALLOC(pr, pr->d_loss, (size_t)S);
   FM_ALLOC(pr, pr->W, 64 * (size_t)P);
-  FM_ALLOC(pr, pr->d_kept, 1);
-  FM_ALLOC(pr, pr->merge_buf, 3 * (size_t)N + 4 * 64);
+  FM_ALLOC(pr, pr->d_kept, (size_t)S);
+  FM_ALLOC(pr, pr->merge_buf, 3 * (size_t)N + 4 * 64 * (size_t)S);
   FM_ALLOC(pr, pr->best_run, (size_t)N);
-  FM_CUDA(pr, cudaMallocHost((void**)&pr->h_loss, sizeof(float)));
-  pr->ea_inv_z = Z > 0 ? (float)(1.0 / (double)Z) : 0.f;
+  FM_CUDA(pr, cudaMallocHost((void**)&pr->h_loss, sizeof(float) * S));
+  {
+    const int64_t z0 = pr->h_sc_kp_off[1] - pr->h_sc_kp_off[0];
+    pr->ea_inv_z = z0 > 0 ? (float)(1.0 / (double)z0) : 0.f;
+  }
   if (d->rel_R) {
     FM_CUDA(pr, cudaMemcpyAsync(pr->rel_R, d->rel_R, sizeof(float) * 9 * P,
                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
@@ -431,7 +503,7 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
     }
     {
       Timed t(pr, fm::kKEaCompact);
-      fm::launch_ea_compact(pr, params, pr->ea_inv_z, step, s);
+      fm::launch_ea_compact(pr, params, step, s);
     }
     FM_LAUNCHED(pr);
   } else if (st == FM_STAGE_EPIPOLAR) {
@@ -447,14 +519,15 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
     FM_LAUNCHED(pr);
     {
       Timed t(pr, fm::kKEaSegments);
-      fm::launch_ea_segments(pr, params, pr->ea_loss, pr->ea_inv_z, s);
+      fm::launch_ea_segments(pr, params, pr->ea_loss, s);
     }
     FM_LAUNCHED(pr);
   } else if (st == FM_STAGE_ROTATION) {
     if (!pr->rel_R_set) return fail(pr, FM_ERR_STATE, "rotation stage needs relative rotations (rel_R)");
     {
       Timed t(pr, fm::kKRotPairs);
-      fm::launch_rot_pairs(params, pr->pair_i, pr->pair_j, pr->rel_R, P, pr->seg_grad, pr->seg_loss, step, s);
+      fm::launch_rot_pairs(params, pr->pair_i, pr->pair_j, pr->rel_R, P, pr->pair_inv_p, pr->seg_grad,
+                           pr->seg_loss, step, s);
     }
     FM_LAUNCHED(pr);
   } else {
@@ -463,8 +536,8 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
     runs = pr->trn_runs;
     {
       Timed t(pr, fm::kKTrnPairs);
-      fm::launch_trn_pairs(params, pr->pair_i, pr->pair_j, pr->trn_target, N, P, runs, pr->seg_grad,
-                           pr->seg_loss, step, s);
+      fm::launch_trn_pairs(params, pr->pair_i, pr->pair_j, pr->trn_target, N, P, runs, pr->pair_inv_p,
+                           pr->seg_grad, pr->seg_loss, step, s);
     }
     FM_LAUNCHED(pr);
   }
@@ -476,7 +549,7 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
   for (float* dst : {cam ? other : fused, cam ? nullptr : other}) {
     if (!dst) continue;
     Timed t(pr, fm::kKLossSum);
-    fm::launch_sum_fixed(pr->seg_loss, P, runs, dst, s);
+    fm::launch_sum_fixed(pr->seg_loss, P, runs, pr->sc_pair_off, pr->S, dst, s);
   }
   FM_LAUNCHED(pr);
   if (cam) {
@@ -499,6 +572,8 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
     u.runs = runs;
     u.seg_loss = pr->seg_loss;
     u.loss_out = fused;
+    u.sc_pair_off = pr->sc_pair_off;
+    u.S = pr->S;
     {
       Timed t(pr, fm::kKCamUpdate);
       fm::launch_cam_update((int)st, u, s);
@@ -530,8 +605,8 @@ fm_status resize_runs(fm_problem* pr, int runs) {
   const size_t sp = std::max((size_t)9 * pr->N, n);
   FM_ALLOC(pr, pr->scratch_params, sp);
   FM_ALLOC(pr, pr->scratch_grad, sp);
-  FM_ALLOC(pr, pr->d_loss, runs);
-  FM_CUDA(pr, cudaMallocHost((void**)&pr->h_loss, sizeof(float) * runs));
+  FM_ALLOC(pr, pr->d_loss, (size_t)runs * pr->S);
+  FM_CUDA(pr, cudaMallocHost((void**)&pr->h_loss, sizeof(float) * runs * pr->S));
   pr->trn_runs = runs;
   pr->trn_params_set = false;
   return FM_OK;
@@ -596,6 +671,7 @@ fm_status fm_problem_info_get(const fm_problem* pr, fm_problem_info* out) {
   out->pairs_per_lane = fm::kEaPairsPerLane;
   out->n_records = pr->n_rec;
   out->device_bytes = pr->device_bytes;
+  out->n_scenes = pr->S;
   return FM_OK;
 }
 
@@ -660,13 +736,43 @@ fm_status fm_ea_set_loss(fm_problem* pr, fm_ea_loss loss) {
   return FM_OK;
 }
 
+// pair_inv_z = 1/Z_s (unit weights) for every image pair of scene s
+static fm_status set_unit_normalisers(fm_problem* pr) {
+  std::vector<float> inv_z(pr->P);
+  for (int q = 0; q < pr->S; ++q) {
+    const int64_t zq = pr->h_sc_kp_off[q + 1] - pr->h_sc_kp_off[q];
+    const float v = zq > 0 ? (float)(1.0 / (double)zq) : 0.f;
+    for (int n = pr->h_sc_pair_off[q]; n < pr->h_sc_pair_off[q + 1]; ++n) inv_z[n] = v;
+  }
+  FM_CUDA(pr, cudaMemcpyAsync(pr->pair_inv_z, inv_z.data(), sizeof(float) * pr->P, cudaMemcpyHostToDevice,
+                              pr->stream));
+  FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+  const int64_t z0 = pr->h_sc_kp_off[1] - pr->h_sc_kp_off[0];
+  pr->ea_inv_z = z0 > 0 ? (float)(1.0 / (double)z0) : 0.f;
+  return FM_OK;
+}
+
+// pair_inv_z from the per-scene counts in d_kept; returns the total on the host
+static fm_status normalisers_from_counts(fm_problem* pr, int64_t* total) {
+  fm::launch_pair_inv_from_counts(pr, pr->d_kept, pr->stream);
+  FM_LAUNCHED(pr);
+  std::vector<unsigned long long> kept(pr->S);
+  FM_CUDA(pr, cudaMemcpyAsync(kept.data(), pr->d_kept, sizeof(unsigned long long) * pr->S,
+                              cudaMemcpyDeviceToHost, pr->stream));
+  FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+  int64_t t = 0;
+  for (int q = 0; q < pr->S; ++q) t += (int64_t)kept[q];
+  if (total) *total = t;
+  pr->ea_inv_z = kept[0] > 0 ? (float)(1.0 / (double)kept[0]) : 0.f;
+  return FM_OK;
+}
+
 fm_status fm_ea_set_weights(fm_problem* pr, const float* w, int32_t on_device, float inv_z) {
   if (!pr) return FM_ERR_INVALID_ARG;
   if (!w) {
     dfree(pr->ea_w);
-    pr->ea_inv_z = pr->Z > 0 ? (float)(1.0 / (double)pr->Z) : 0.f;
     pr->W_valid = false;
-    return FM_OK;
+    return set_unit_normalisers(pr);
   }
   if (!(std::isfinite(inv_z) && inv_z >= 0.f)) return fail(pr, FM_ERR_INVALID_ARG, "inv_z must be finite and >= 0");
   if (!pr->ea_w) FM_ALLOC(pr, pr->ea_w, (size_t)pr->Z);
@@ -678,9 +784,20 @@ fm_status fm_ea_set_weights(fm_problem* pr, const float* w, int32_t on_device, f
     fm_status e = check_err_bits(pr);
     if (e != FM_OK) return e;
   }
-  pr->ea_inv_z = inv_z;
   pr->W_valid = false;
-  return FM_OK;
+  if (inv_z > 0.f) {
+    std::vector<float> v(pr->P, inv_z);
+    FM_CUDA(pr, cudaMemcpyAsync(pr->pair_inv_z, v.data(), sizeof(float) * pr->P, cudaMemcpyHostToDevice,
+                                pr->stream));
+    FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+    pr->ea_inv_z = inv_z;
+    return FM_OK;
+  }
+  // inv_z == 0: each scene's 1/(number of its pairs with a positive weight)
+  FM_CUDA(pr, cudaMemsetAsync(pr->d_kept, 0, sizeof(unsigned long long) * pr->S, pr->stream));
+  fm::launch_count_positive(pr, pr->ea_w, pr->d_kept, pr->stream);
+  FM_LAUNCHED(pr);
+  return normalisers_from_counts(pr, nullptr);
 }
 
 fm_status fm_ea_reweight(fm_problem* pr, float tau, float delta, int32_t irls, int64_t* n_kept) {
@@ -695,7 +812,7 @@ fm_status fm_ea_reweight(fm_problem* pr, float tau, float delta, int32_t irls, i
     fm::launch_ea_tables(pr->ea_params, pr->pair_i, pr->pair_j, pr->seg_off, pr->P, pr->seg_tab, nullptr, s);
   }
   FM_LAUNCHED(pr);
-  FM_CUDA(pr, cudaMemsetAsync(pr->d_kept, 0, sizeof(unsigned long long), s));
+  FM_CUDA(pr, cudaMemsetAsync(pr->d_kept, 0, sizeof(unsigned long long) * pr->S, s));
   {
     Timed t(pr, fm::kKEaReweight);
     fm::launch_ea_reweight(pr, tau, delta, irls, pr->ea_w, pr->d_kept, s);
@@ -707,11 +824,10 @@ fm_status fm_ea_reweight(fm_problem* pr, float tau, float delta, int32_t irls, i
   }
   FM_LAUNCHED(pr);
   pr->W_valid = true;
-  unsigned long long kept = 0;
-  FM_CUDA(pr, cudaMemcpyAsync(&kept, pr->d_kept, sizeof(kept), cudaMemcpyDeviceToHost, s));
-  FM_CUDA(pr, cudaStreamSynchronize(s));
-  pr->ea_inv_z = kept > 0 ? (float)(1.0 / (double)kept) : 0.f;
-  if (n_kept) *n_kept = (int64_t)kept;
+  int64_t total = 0;
+  fm_status e = normalisers_from_counts(pr, &total);
+  if (e != FM_OK) return e;
+  if (n_kept) *n_kept = total;
   return FM_OK;
 }
 
@@ -745,10 +861,11 @@ fm_status fm_loss_grad(fm_problem* pr, fm_stage st, const float* params, float* 
   const int runs = (st == FM_STAGE_TRANSLATION) ? pr->trn_runs : 1;
   if (grad && !mem_on_device)
     FM_CUDA(pr, cudaMemcpyAsync(grad, g, sizeof(float) * count, cudaMemcpyDeviceToHost, s));
-  if (loss) FM_CUDA(pr, cudaMemcpyAsync(pr->h_loss, pr->d_loss, sizeof(float) * runs, cudaMemcpyDeviceToHost, s));
+  const size_t nl = (size_t)runs * pr->S;
+  if (loss) FM_CUDA(pr, cudaMemcpyAsync(pr->h_loss, pr->d_loss, sizeof(float) * nl, cudaMemcpyDeviceToHost, s));
   if (loss || (grad && !mem_on_device)) {
     FM_CUDA(pr, cudaStreamSynchronize(s));
-    if (loss) std::memcpy(loss, pr->h_loss, sizeof(float) * runs);
+    if (loss) std::memcpy(loss, pr->h_loss, sizeof(float) * nl);
   }
   return FM_OK;
 }
@@ -777,15 +894,14 @@ fm_status fm_ea_forward(fm_problem* pr, const float* params, float* loss_dev, in
     fm::launch_ea_tables(params, pr->pair_i, pr->pair_j, pr->seg_off, pr->P, pr->seg_tab, nullptr, s);
   }
   FM_LAUNCHED(pr);
-  fm::SegArgs a = fm::seg_args(pr, params);
+  fm::SegArgs a = fm::seg_args(pr, params);   // per-pair (per-scene) normalisers
   a.seg_grad = nullptr;
-  a.l_scale = pr->ea_inv_z;
   if (save == FM_EA_SAVE_DLDE) {
     if (pr->n_wruns > 0) {
       Timed t(pr, fm::kKEaDirect);
       fm::launch_ea_direct(pr, pr->ea_w, pr->ea_loss, s);
     }
-    a.g_scale = (pr->ea_loss == FM_EA_L1) ? pr->ea_inv_z : 2.f * pr->ea_inv_z;
+    a.g_scale = (pr->ea_loss == FM_EA_L1) ? 1.f : 2.f;
     a.dlde_out = saved;
   } else if (pr->n_wruns > 0) {
     Timed t(pr, fm::kKEaDirectLoss);
@@ -799,7 +915,7 @@ fm_status fm_ea_forward(fm_problem* pr, const float* params, float* loss_dev, in
   FM_LAUNCHED(pr);
   {
     Timed t(pr, fm::kKLossSum);
-    fm::launch_sum_fixed(pr->seg_loss, pr->P, 1, loss_dev, s);
+    fm::launch_sum_fixed(pr->seg_loss, pr->P, 1, pr->sc_pair_off, pr->S, loss_dev, s);
   }
   FM_LAUNCHED(pr);
   return FM_OK;
@@ -828,13 +944,13 @@ fm_status fm_ea_backward(fm_problem* pr, const float* params, int32_t save, cons
         Timed t(pr, fm::kKEaDirectCoef);
         fm::launch_ea_direct_from_coef(pr, saved, s);
       }
-      a.g_scale = pr->ea_inv_z;   // the stored coefficients carry rho' in full
+      a.g_scale = 1.f;   // the stored coefficients carry rho' in full
     } else {
       if (pr->n_wruns > 0) {
         Timed t(pr, fm::kKEaDirect);
         fm::launch_ea_direct(pr, pr->ea_w, pr->ea_loss, s);
       }
-      a.g_scale = (pr->ea_loss == FM_EA_L1) ? pr->ea_inv_z : 2.f * pr->ea_inv_z;
+      a.g_scale = (pr->ea_loss == FM_EA_L1) ? 1.f : 2.f;
     }
     FM_LAUNCHED(pr);
   }
@@ -879,7 +995,7 @@ fm_status fm_step(fm_problem* pr, fm_stage st, const fm_adam_opts* opts, int32_t
     float* trace = nullptr;
     if (pr->loss_every > 0) {
       if (pr->iter_count % pr->loss_every == 0) {
-        trace = pr->loss_hist + (size_t)(pr->loss_count % pr->loss_cap) * 64;
+        trace = pr->loss_hist + (size_t)(pr->loss_count % pr->loss_cap) * 64 * pr->S;
         pr->loss_count += 1;
       }
       pr->iter_count += 1;
@@ -890,9 +1006,10 @@ fm_status fm_step(fm_problem* pr, fm_stage st, const fm_adam_opts* opts, int32_t
   }
   if (st == FM_STAGE_ROTATION && n_iters > 0) pr->trn_target_valid = false;
   if (loss && n_iters > 0) {
-    FM_CUDA(pr, cudaMemcpyAsync(pr->h_loss, pr->d_loss, sizeof(float) * runs, cudaMemcpyDeviceToHost, pr->stream));
+    const size_t nl = (size_t)runs * pr->S;
+    FM_CUDA(pr, cudaMemcpyAsync(pr->h_loss, pr->d_loss, sizeof(float) * nl, cudaMemcpyDeviceToHost, pr->stream));
     FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
-    std::memcpy(loss, pr->h_loss, sizeof(float) * runs);
+    std::memcpy(loss, pr->h_loss, sizeof(float) * nl);
   }
   return FM_OK;
 }
@@ -906,20 +1023,30 @@ fm_status fm_rotation_init(fm_problem* pr, int32_t n_iters) {
   float* x = pr->scratch_params;           // [3N]
   float* y = pr->scratch_params + 3 * N;   // [3N]
   float* c1 = pr->scratch_grad;            // [3N]
-  // lambda_max(A) <= 2 max degree (Gershgorin); B = A/|P| + diag(c1 c1^T)/|I|
-  const float sigma1 = 2.f * (float)std::max(pr->max_degree, 1);
-  const float sigma2 = sigma1 / (float)pr->P + 1.f / (float)N;
+  // per scene: lambda_max(A) <= 2 max degree (Gershgorin); B = A/|P| + diag(c1 c1^T)/|I|
+  const int S = pr->S;
+  std::vector<float> coef1(3 * (size_t)S), coef2(3 * (size_t)S);
+  for (int q = 0; q < S; ++q) {
+    const float Pq = (float)(pr->h_sc_pair_off[q + 1] - pr->h_sc_pair_off[q]);
+    const float Nq = (float)(pr->h_sc_cam_off[q + 1] - pr->h_sc_cam_off[q]);
+    const float sigma1 = 2.f * (float)std::max(pr->h_sc_max_degree[q], 1);
+    const float sigma2 = sigma1 / Pq + 1.f / Nq;
+    coef1[3 * q] = 1.f / sigma1; coef1[3 * q + 1] = 1.f;      coef1[3 * q + 2] = 1.f / Nq;
+    coef2[3 * q] = 1.f / sigma2; coef2[3 * q + 1] = 1.f / Pq; coef2[3 * q + 2] = 1.f / Nq;
+  }
   for (int col = 0; col < 2; ++col) {
-    fm::launch_hash_fill(x, 3 * N, col == 0 ? 0x1234567u : 0x89ABCDEu, s);
-    fm::launch_scale_to_unit(x, 3 * N, s);
+    FM_CUDA(pr, cudaMemcpyAsync(pr->mart_coef, (col == 0 ? coef1 : coef2).data(), sizeof(float) * 3 * S,
+                                cudaMemcpyHostToDevice, s));
+    FM_CUDA(pr, cudaStreamSynchronize(s));   // the host vector is reused
+    fm::launch_hash_fill(pr, x, 1, col == 0 ? 0x1234567u : 0x89ABCDEu, s);
+    fm::launch_scale_to_unit(pr, x, s);
     for (int it = 0; it < n_iters; ++it) {
       {
         Timed t(pr, fm::kKMartIter);
-        if (col == 0) fm::launch_mart_iter(pr, x, nullptr, y, sigma1, 1.f, s);
-        else fm::launch_mart_iter(pr, x, c1, y, sigma2, (float)pr->P, s);
+        fm::launch_mart_iter(pr, x, col == 0 ? nullptr : c1, y, s);
       }
       std::swap(x, y);
-      if ((it & 31) == 31) fm::launch_scale_to_unit(x, 3 * N, s);
+      if ((it & 31) == 31) fm::launch_scale_to_unit(pr, x, s);
     }
     FM_LAUNCHED(pr);
     if (col == 0) {
@@ -973,7 +1100,7 @@ fm_status fm_get_rel_poses(fm_problem* pr, float* rel_R, float* rel_t, int32_t o
 fm_status fm_translation_random_init(fm_problem* pr, uint32_t seed) {
   if (!pr) return FM_ERR_INVALID_ARG;
   const size_t n = 3 * (size_t)pr->N * pr->trn_runs;
-  fm::launch_hash_fill(pr->trn_params, (int)n, seed, pr->stream);
+  fm::launch_hash_fill(pr, pr->trn_params, pr->trn_runs, seed, pr->stream);
   FM_LAUNCHED(pr);
   fm_status e = reset_adam(pr, pr->trn_adam, n);
   if (e != FM_OK) return e;
@@ -1103,11 +1230,17 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
   if (o->trn_runs < 1 || o->trn_runs > 64 || o->ea_rounds < 0 || o->rot_init_iters < 1)
     return fail(pr, FM_ERR_INVALID_ARG, "invalid solve options");
   fm_status e;
-  float L = 0.f;
+  // per-scene losses; the result reports their sum
+  std::vector<float> Lv(pr->S);
+  auto total = [&]() {
+    float t = 0.f;
+    for (float v : Lv) t += v;
+    return t;
+  };
   // 1-2. rotations
   if ((e = fm_rotation_init(pr, o->rot_init_iters)) != FM_OK) return e;
-  if ((e = stepped(pr, FM_STAGE_ROTATION, o, o->rot_lr, o->rot_iters, &L)) != FM_OK) return e;
-  res->loss_rotation = L;
+  if ((e = stepped(pr, FM_STAGE_ROTATION, o, o->rot_lr, o->rot_iters, Lv.data())) != FM_OK) return e;
+  res->loss_rotation = total();
   // 3. relative translations
   if (o->reestimate_rel_t) {
     if ((e = fm_relative_translations(pr, nullptr, 0)) != FM_OK) return e;
@@ -1117,11 +1250,11 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
   // 4. translation runs, merge, final run
   if ((e = fm_translation_set_runs(pr, o->trn_runs)) != FM_OK) return e;
   if ((e = fm_translation_random_init(pr, o->seed)) != FM_OK) return e;
-  std::vector<float> run_loss(o->trn_runs);
+  std::vector<float> run_loss((size_t)o->trn_runs * pr->S);
   if ((e = stepped(pr, FM_STAGE_TRANSLATION, o, o->trn_lr, o->trn_iters, run_loss.data())) != FM_OK) return e;
   if ((e = fm_translation_merge(pr, nullptr)) != FM_OK) return e;
-  if ((e = stepped(pr, FM_STAGE_TRANSLATION, o, o->trn_lr, o->trn_final_iters, &L)) != FM_OK) return e;
-  res->loss_translation = L;
+  if ((e = stepped(pr, FM_STAGE_TRANSLATION, o, o->trn_lr, o->trn_final_iters, Lv.data())) != FM_OK) return e;
+  res->loss_translation = total();
   // 5. epipolar adjustment: IRLS / filtering rounds on the compact form
   if ((e = fm_epipolar_init_from_stages(pr)) != FM_OK) return e;
   if ((e = fm_ea_set_loss(pr, FM_EA_COMPACT)) != FM_OK) return e;
@@ -1132,8 +1265,8 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
     int64_t kept = 0;
     if ((e = fm_ea_reweight(pr, tau, o->ea_delta, 1, &kept)) != FM_OK) return e;
     res->n_kept = kept;
-    if ((e = stepped(pr, FM_STAGE_EPIPOLAR, o, o->ea_lr, o->ea_iters, &L)) != FM_OK) return e;
-    res->loss_epipolar = L;
+    if ((e = stepped(pr, FM_STAGE_EPIPOLAR, o, o->ea_lr, o->ea_iters, Lv.data())) != FM_OK) return e;
+    res->loss_epipolar = total();
   }
   // outputs
   float* dR = pr->scratch_params;     // [9N]
@@ -1196,7 +1329,7 @@ fm_status fm_track_loss(fm_problem* pr, int32_t every, int32_t capacity) {
   pr->loss_count = 0;
   pr->iter_count = 0;
   if (every == 0) return FM_OK;
-  FM_ALLOC(pr, pr->loss_hist, (size_t)capacity * 64);
+  FM_ALLOC(pr, pr->loss_hist, (size_t)capacity * 64 * pr->S);
   pr->loss_every = every;
   pr->loss_cap = capacity;
   return FM_OK;
@@ -1210,13 +1343,13 @@ fm_status fm_loss_history(fm_problem* pr, float* out, int32_t capacity, int32_t*
   }
   const int64_t have = std::min<int64_t>(pr->loss_count, pr->loss_cap);
   const int64_t n = std::min<int64_t>(have, capacity);
-  std::vector<float> ring((size_t)pr->loss_cap * 64);
+  std::vector<float> ring((size_t)pr->loss_cap * 64 * pr->S);
   FM_CUDA(pr, cudaMemcpyAsync(ring.data(), pr->loss_hist, sizeof(float) * ring.size(),
                               cudaMemcpyDeviceToHost, pr->stream));
   FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
   for (int64_t k = 0; k < n; ++k) {
     const int64_t idx = pr->loss_count - n + k;
-    out[k] = ring[(size_t)(idx % pr->loss_cap) * 64];   // run 0 of the translation stage
+    out[k] = ring[(size_t)(idx % pr->loss_cap) * 64 * pr->S];   // scene 0 (run 0 of the translation stage)
   }
   *count = (int32_t)n;
   return FM_OK;

@@ -51,10 +51,12 @@ __global__ void __launch_bounds__(kCamThreads) k_cam(CamUpdate u) {
   const int warp = threadIdx.x >> 5;
   const int run = blockIdx.y;
   pdl_trigger();
-  if (u.loss_out && blockIdx.x == gridDim.x - 1) {
-    // the extra CTA of the grid reduces the loss
+  if (u.loss_out && (int)blockIdx.x >= u.N) {
+    // the S extra CTAs of the grid reduce the loss of each scene
+    const int sc = blockIdx.x - u.N;
+    const int b = u.sc_pair_off[sc], e = u.sc_pair_off[sc + 1];
     pdl_wait();
-    loss_sum_cta(u.seg_loss + (size_t)run * u.P, u.P, u.loss_out + run);
+    loss_sum_cta(u.seg_loss + (size_t)run * u.P + b, e - b, u.loss_out + (size_t)run * u.S + sc);
     return;
   }
   const int c = blockIdx.x;                                    // one CTA per camera
@@ -146,10 +148,15 @@ __global__ void __launch_bounds__(kCamThreads) k_cam(CamUpdate u) {
   }
 }
 
-// fixed-order sum of n values per run (one CTA per run)
-__global__ void k_sum_fixed(const float* __restrict__ x, int n, float* __restrict__ out) {
+// fixed-order sum of each scene's range of values per run (one CTA per
+// (scene, run))
+__global__ void k_sum_fixed(const float* __restrict__ x, int P, const int* __restrict__ sc_pair_off,
+                            float* __restrict__ out) {
   __shared__ float part[1024];
-  const float* xr = x + (size_t)blockIdx.x * n;
+  const int sc = blockIdx.x, run = blockIdx.y;
+  const int b = sc_pair_off ? sc_pair_off[sc] : 0, e = sc_pair_off ? sc_pair_off[sc + 1] : P;
+  const float* xr = x + (size_t)run * P + b;
+  const int n = e - b;
   float s = 0.f;
   for (int k = threadIdx.x; k < n; k += 1024) s += xr[k];
   part[threadIdx.x] = s;
@@ -158,12 +165,12 @@ __global__ void k_sum_fixed(const float* __restrict__ x, int n, float* __restric
     if ((int)threadIdx.x < d) part[threadIdx.x] += part[threadIdx.x + d];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[blockIdx.x] = part[0];
+  if (threadIdx.x == 0) out[(size_t)run * gridDim.x + sc] = part[0];
 }
 
 template <int STAGE>
 void launch_stage(const CamUpdate& u, cudaStream_t s) {
-  dim3 grid(u.N + (u.loss_out ? 1 : 0), u.runs);
+  dim3 grid(u.N + (u.loss_out ? u.S : 0), u.runs);
   if (u.params_out) launch_pdl(k_cam<STAGE, true>, grid, dim3(kCamThreads), 0, s, u);
   else launch_pdl(k_cam<STAGE, false>, grid, dim3(kCamThreads), 0, s, u);
 }
@@ -176,8 +183,9 @@ void launch_cam_update(int stage, const CamUpdate& u, cudaStream_t s) {
   else launch_stage<2>(u, s);
 }
 
-void launch_sum_fixed(const float* x, int n, int runs, float* out, cudaStream_t s) {
-  k_sum_fixed<<<runs, 1024, 0, s>>>(x, n, out);
+void launch_sum_fixed(const float* x, int P, int runs, const int* sc_pair_off, int S, float* out,
+                      cudaStream_t s) {
+  k_sum_fixed<<<dim3(S, runs), 1024, 0, s>>>(x, P, sc_pair_off, out);
 }
 
 }  // namespace fm

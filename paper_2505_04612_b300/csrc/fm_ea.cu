@@ -576,12 +576,14 @@ __global__ void k_ea_segments(SegArgs a) {
 #pragma unroll
     for (int k = 0; k < 10; ++k) G[k] += __shfl_xor_sync(0xffffffffu, G[k], d);
   if (!valid || sub != 0) return;
+  const float ps = a.pair_scale ? a.pair_scale[n] : 1.f;
   if (a.dlde_in) {
     for (int k = 0; k < 9; ++k) G[k] = a.dlde_in[9 * (size_t)n + k];
   } else {
-    for (int k = 0; k < 9; ++k) G[k] *= a.g_scale;
+    const float gs = a.g_scale * ps;
+    for (int k = 0; k < 9; ++k) G[k] *= gs;
   }
-  if (a.seg_loss) a.seg_loss[n] = G[9] * a.l_scale;
+  if (a.seg_loss) a.seg_loss[n] = G[9] * (a.l_scale * ps);
   if (a.dlde_out)
     for (int k = 0; k < 9; ++k) a.dlde_out[9 * (size_t)n + k] = G[k];
   if (!a.seg_grad) return;
@@ -591,7 +593,7 @@ __global__ void k_ea_segments(SegArgs a) {
     return;
   }
   if (a.grad_loss) {
-    const float gl = *a.grad_loss;
+    const float gl = a.grad_loss[a.pair_scene ? a.pair_scene[n] : 0];
     for (int k = 0; k < 9; ++k) G[k] *= gl;
   }
   PairGeo g;
@@ -678,8 +680,10 @@ SegArgs seg_args(const fm_problem* pr, const float* params) {
   a.pj = pr->pair_j;
   a.P = pr->P;
   a.g_scale = 0.f;
-  a.l_scale = 0.f;
+  a.l_scale = 1.f;
+  a.pair_scale = pr->pair_inv_z;
   a.grad_loss = nullptr;
+  a.pair_scene = pr->pair_scene;
   a.seg_grad = pr->seg_grad;
   a.seg_loss = pr->seg_loss;
   a.dlde_out = nullptr;
@@ -691,11 +695,9 @@ void launch_ea_segments(const SegArgs& a, cudaStream_t s) {
   launch_pdl(k_ea_segments, dim3((unsigned)((threads + 127) / 128)), dim3(128), 0, s, a);
 }
 
-void launch_ea_segments(const fm_problem* pr, const float* params, int loss, float inv_z,
-                        cudaStream_t s) {
+void launch_ea_segments(const fm_problem* pr, const float* params, int loss, cudaStream_t s) {
   SegArgs a = seg_args(pr, params);
-  a.g_scale = (loss == FM_EA_L1) ? inv_z : 2.f * inv_z;
-  a.l_scale = inv_z;
+  a.g_scale = (loss == FM_EA_L1) ? 1.f : 2.f;
   launch_ea_segments(a, s);
 }
 

@@ -9,7 +9,9 @@
 // second columns that of B = A/|P| + (1/|I|) blockdiag(c1_i c1_i^T) (Eq. 13).
 // Both are found by power iteration on I - A/sigma (sigma >= lambda_max by
 // Gershgorin: 2 max degree), whose spectrum lies in [0, 1] with the wanted
-// eigenvector at the top; the iterate never needs rescaling.  Any vector of
+// eigenvector at the top.  A problem holding several scenes is block
+// diagonal: every scene gets its own sigma, |P|, |I| and normalisation, so
+// each one converges as it would alone.  Any vector of
 // the (near-)null space is a valid answer (x_i = R_i v for some v), so only
 // the gap to the fourth eigenvalue matters for convergence.
 #include "fm_device.cuh"
@@ -18,16 +20,20 @@
 namespace fm {
 namespace {
 
-// y = x - (B x)/sigma with B = A/scaleP + (1/N) diag(c1 c1^T) (c1 may be null)
+// y = x - (B x)/sigma with B = A/scaleP + (1/N) diag(c1 c1^T) (c1 may be
+// null); coef[3 s + {0,1,2}] = (1/sigma, 1/scaleP, 1/N) of scene s
 __global__ void __launch_bounds__(128) k_mart_iter(const int* __restrict__ cam_seg_off,
                                                    const int* __restrict__ cam_seg,
                                                    const int* __restrict__ pi, const int* __restrict__ pj,
                                                    const float* __restrict__ relR, const float* __restrict__ x,
                                                    const float* __restrict__ c1, float* __restrict__ y, int N,
-                                                   float inv_sigma, float inv_scale_p, float inv_n) {
+                                                   const int* __restrict__ cam_scene,
+                                                   const float* __restrict__ coef) {
   const int lane = threadIdx.x & 31;
   const int c = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (c >= N) return;
+  const int sc = cam_scene[c];
+  const float inv_sigma = coef[3 * sc], inv_scale_p = coef[3 * sc + 1], inv_n = coef[3 * sc + 2];
   const float xc0 = x[3 * c], xc1 = x[3 * c + 1], xc2 = x[3 * c + 2];
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   const int b = cam_seg_off[c], e = cam_seg_off[c + 1];
@@ -99,21 +105,33 @@ __global__ void k_mart_finish(const float* __restrict__ c1, const float* __restr
 }
 
 // deterministic start vector: the index mixed by a Weyl increment and the
-// MurmurHash3 32-bit finaliser (fmix32), mapped to [-1, 1)
-__global__ void k_hash_fill(float* __restrict__ x, int n, unsigned salt) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  unsigned z = (unsigned)k * 0x9E3779B9u + salt;
+// MurmurHash3 32-bit finaliser (fmix32), mapped to [-1, 1).  x is
+// [runs][N][3]; the index of an entry is the one it has within its camera's
+// scene, (r N_s + c - c0_s) 3 + a, so that a scene draws the same values
+// whether it is solved alone or with others.
+__global__ void k_hash_fill(float* __restrict__ x, int runs, int N, const int* __restrict__ cam_scene,
+                            const int* __restrict__ sc_cam_off, unsigned salt) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (long long)runs * N * 3) return;
+  const int r = (int)(k / (3LL * N));
+  const int rem = (int)(k - (long long)r * 3 * N);
+  const int c = rem / 3, a = rem - 3 * c;
+  const int sc = cam_scene[c];
+  const int c0 = sc_cam_off[sc], ns = sc_cam_off[sc + 1] - c0;
+  const unsigned idx = (unsigned)(((long long)r * ns + (c - c0)) * 3 + a);
+  unsigned z = idx * 0x9E3779B9u + salt;
   z = (z ^ (z >> 16)) * 0x85EBCA6Bu;
   z = (z ^ (z >> 13)) * 0xC2B2AE35u;
   z ^= z >> 16;
   x[k] = (float)(z >> 8) * (1.0f / 8388608.0f) - 1.0f;
 }
 
-// x <- x / |x| over the whole vector (one CTA, fixed-order sum), so that the
-// power iteration neither underflows nor overflows
-__global__ void k_scale_to_unit(float* __restrict__ x, int n) {
+// x <- x / |x| over each scene's cameras (one CTA per scene, fixed-order
+// sum), so that the power iteration neither underflows nor overflows
+__global__ void k_scale_to_unit(float* __restrict__ x_all, const int* __restrict__ sc_cam_off) {
   __shared__ float part[256];
+  float* x = x_all + 3 * (size_t)sc_cam_off[blockIdx.x];
+  const int n = 3 * (sc_cam_off[blockIdx.x + 1] - sc_cam_off[blockIdx.x]);
   float s = 0.f;
   for (int k = threadIdx.x; k < n; k += 256) s += x[k] * x[k];
   part[threadIdx.x] = s;
@@ -128,10 +146,15 @@ __global__ void k_scale_to_unit(float* __restrict__ x, int n) {
 }
 
 // ---------------------------------------------------------------- merge
-// Per run: centroid and mean norm of the centres (fixed order, one CTA per run).
-__global__ void k_run_stats(const float* __restrict__ o, int N, float* __restrict__ stats) {
+// Per (scene, run): centroid and mean norm of the scene's centres (fixed
+// order, one CTA each); stats[4 (run S + scene) + {0..3}].
+__global__ void k_run_stats(const float* __restrict__ o, int N_all, const int* __restrict__ sc_cam_off,
+                            float* __restrict__ stats) {
   __shared__ float s[4][256];
-  const float* orun = o + (size_t)3 * N * blockIdx.x;
+  const int sc = blockIdx.x, run = blockIdx.y;
+  const int c0 = sc_cam_off[sc], N = sc_cam_off[sc + 1] - c0;
+  const float* orun = o + (size_t)3 * N_all * run + 3 * (size_t)c0;
+  const int out = run * gridDim.x + sc;
   float a[3] = {0.f, 0.f, 0.f};
   for (int c = threadIdx.x; c < N; c += 256)
     for (int k = 0; k < 3; ++k) a[k] += orun[3 * c + k];
@@ -156,10 +179,10 @@ __global__ void k_run_stats(const float* __restrict__ o, int N, float* __restric
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    stats[4 * blockIdx.x + 0] = cx;
-    stats[4 * blockIdx.x + 1] = cy;
-    stats[4 * blockIdx.x + 2] = cz;
-    stats[4 * blockIdx.x + 3] = s[3][0] / N;
+    stats[4 * out + 0] = cx;
+    stats[4 * out + 1] = cy;
+    stats[4 * out + 2] = cz;
+    stats[4 * out + 3] = s[3][0] / N;
   }
 }
 
@@ -170,17 +193,18 @@ __global__ void __launch_bounds__(128) k_merge(const float* __restrict__ o, cons
                                                const int* __restrict__ cam_seg_off,
                                                const int* __restrict__ cam_seg, const int* __restrict__ pi,
                                                const int* __restrict__ pj, const float* __restrict__ tgt,
-                                               int N, int runs, float* __restrict__ out,
-                                               int* __restrict__ best_run) {
+                                               int N, int runs, const int* __restrict__ cam_scene, int S,
+                                               float* __restrict__ out, int* __restrict__ best_run) {
   const int lane = threadIdx.x & 31;
   const int c = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (c >= N) return;
+  const int sc = cam_scene[c];
   const int b = cam_seg_off[c], e = cam_seg_off[c + 1];
   float best = 3.4e38f;
   int best_r = 0;
   for (int r = 0; r < runs; ++r) {
     const float* orun = o + (size_t)3 * N * r;
-    const float* st = stats + 4 * r;
+    const float* st = stats + 4 * (r * S + sc);
     const float inv = st[3] > 0.f ? 1.f / st[3] : 0.f;
     float acc = 0.f;
     for (int idx = b + lane; idx < e; idx += 32) {
@@ -205,7 +229,7 @@ __global__ void __launch_bounds__(128) k_merge(const float* __restrict__ o, cons
     }
   }
   if (lane < 3) {
-    const float* st = stats + 4 * best_r;
+    const float* st = stats + 4 * (best_r * S + sc);
     const float inv = st[3] > 0.f ? 1.f / st[3] : 0.f;
     out[3 * c + lane] = (o[(size_t)3 * N * best_r + 3 * c + lane] - st[lane]) * inv;
   }
@@ -214,27 +238,28 @@ __global__ void __launch_bounds__(128) k_merge(const float* __restrict__ o, cons
 
 }  // namespace
 
-void launch_mart_iter(const fm_problem* pr, const float* x, const float* c1, float* y, float sigma,
-                      float scale_p, cudaStream_t s) {
+void launch_mart_iter(const fm_problem* pr, const float* x, const float* c1, float* y, cudaStream_t s) {
   k_mart_iter<<<(pr->N + 3) / 4, 128, 0, s>>>(pr->cam_seg_off, pr->cam_seg, pr->pair_i, pr->pair_j,
-                                              pr->rel_R, x, c1, y, pr->N, 1.f / sigma, 1.f / scale_p,
-                                              1.f / (float)pr->N);
+                                              pr->rel_R, x, c1, y, pr->N, pr->cam_scene, pr->mart_coef);
 }
-void launch_scale_to_unit(float* x, int n, cudaStream_t s) { k_scale_to_unit<<<1, 256, 0, s>>>(x, n); }
+void launch_scale_to_unit(const fm_problem* pr, float* x, cudaStream_t s) {
+  k_scale_to_unit<<<pr->S, 256, 0, s>>>(x, pr->sc_cam_off);
+}
 void launch_normalise3(float* x, int N, cudaStream_t s) {
   k_normalise3<<<(N + 127) / 128, 128, 0, s>>>(x, N);
 }
 void launch_mart_finish(const float* c1, const float* c2, int N, float* params6, cudaStream_t s) {
   k_mart_finish<<<(N + 127) / 128, 128, 0, s>>>(c1, c2, N, params6);
 }
-void launch_hash_fill(float* x, int n, unsigned salt, cudaStream_t s) {
-  k_hash_fill<<<(n + 255) / 256, 256, 0, s>>>(x, n, salt);
+void launch_hash_fill(const fm_problem* pr, float* x, int runs, unsigned salt, cudaStream_t s) {
+  const long long n = (long long)runs * pr->N * 3;
+  k_hash_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, runs, pr->N, pr->cam_scene, pr->sc_cam_off, salt);
 }
 void launch_merge(const fm_problem* pr, const float* o, int runs, float* stats, float* out,
                   int* best_run, cudaStream_t s) {
-  k_run_stats<<<runs, 256, 0, s>>>(o, pr->N, stats);
+  k_run_stats<<<dim3(pr->S, runs), 256, 0, s>>>(o, pr->N, pr->sc_cam_off, stats);
   k_merge<<<(pr->N + 3) / 4, 128, 0, s>>>(o, stats, pr->cam_seg_off, pr->cam_seg, pr->pair_i, pr->pair_j,
-                                         pr->trn_target, pr->N, runs, out, best_run);
+                                         pr->trn_target, pr->N, runs, pr->cam_scene, pr->S, out, best_run);
 }
 
 }  // namespace fm

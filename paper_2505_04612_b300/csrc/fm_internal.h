@@ -71,6 +71,22 @@ struct fm_problem {
   std::string last_error;
   int64_t device_bytes = 0;
 
+  // scenes: a problem may hold S independent scenes, cameras and image pairs
+  // grouped by scene; every loss is per scene (normalised within its scene)
+  int S = 1;
+  std::vector<int> h_sc_cam_off;   // [S+1]
+  std::vector<int> h_sc_pair_off;  // [S+1]
+  std::vector<int64_t> h_sc_kp_off;  // [S+1]
+  std::vector<int> h_sc_max_degree;  // [S]
+  int* sc_cam_off = nullptr;     // [S+1]
+  int* sc_pair_off = nullptr;    // [S+1]
+  int64_t* sc_kp_off = nullptr;  // [S+1] keypoint-pair range of each scene
+  int* cam_scene = nullptr;      // [N]
+  int* pair_scene = nullptr;     // [P]
+  float* pair_inv_p = nullptr;   // [P] 1/P_s: normaliser of the rotation and translation losses
+  float* pair_inv_z = nullptr;   // [P] normaliser of the epipolar loss of the pair's scene
+  float* mart_coef = nullptr;    // [3S] per-scene constants of the rotation initialisation
+
   // image-pair graph
   int* pair_i = nullptr;         // [P]
   int* pair_j = nullptr;         // [P]
@@ -79,7 +95,7 @@ struct fm_problem {
   int* cam_seg = nullptr;        // [2P] image pair | role << 31 (role 1: camera is j)
   int n_empty = 0;
   int max_degree = 0;            // largest number of image pairs of one camera
-  float* merge_buf = nullptr;    // [3N + 4*64] merged centres and per-run statistics
+  float* merge_buf = nullptr;    // [3N + 4*64*S] merged centres and per-(run, scene) statistics
   int* best_run = nullptr;       // [N]
 
   // keypoints
@@ -112,7 +128,7 @@ struct fm_problem {
   float ea_inv_z = 0.f;
   float* W = nullptr;            // [P*45] packed upper triangle of W_n (Eq. 17)
   bool W_valid = false;
-  unsigned long long* d_kept = nullptr;
+  unsigned long long* d_kept = nullptr;  // [S] kept keypoint pairs per scene
   float* ea_params = nullptr;    // [N*9]
   fm::AdamState ea_adam;
   bool ea_params_set = false;
@@ -144,13 +160,13 @@ struct fm_problem {
   int loss_cap = 0;
   int64_t loss_count = 0;     // traced values written so far
   int64_t iter_count = 0;     // fm_step iterations while tracing
-  float* loss_hist = nullptr; // [loss_cap * max(m,1)]
+  float* loss_hist = nullptr; // [loss_cap * 64 * S]: one row of [m][S] losses per traced iteration
 
   // scratch
   float* scratch_params = nullptr;  // [max(m,1)*N*9] parameters of fm_loss_grad
   float* scratch_grad = nullptr;    // [max(m,1)*N*9]
-  float* d_loss = nullptr;          // [max(m,1)]
-  float* h_loss = nullptr;          // pinned [max(m,1)]
+  float* d_loss = nullptr;          // [max(m,1)*S]
+  float* h_loss = nullptr;          // pinned [max(m,1)*S]
   int* d_err = nullptr;             // device error bits
 };
 
@@ -211,48 +227,57 @@ struct SegArgs {
   int P;
   float g_scale;           // factor on the summed coefficient terms
   float l_scale;           // factor on the summed loss terms
-  const float* grad_loss;  // device scalar multiplying the gradient (null: 1)
+  const float* pair_scale; // [P] per-image-pair normaliser (null: 1), applied with g_scale / l_scale
+  const float* grad_loss;  // [S] per-scene factor on the gradient (null: 1)
+  const int* pair_scene;   // [P] scene of each image pair (null: scene 0)
   float* seg_grad;         // [P][24] chain rule (null: skipped)
   float* seg_loss;         // [P] (null: skipped)
   float* dlde_out;         // [P][9] scaled dL/dE_n (null: skipped)
 };
 SegArgs seg_args(const fm_problem* pr, const float* params);
 void launch_ea_segments(const SegArgs& a, cudaStream_t s);
-void launch_ea_segments(const fm_problem* pr, const float* params, int loss, float inv_z,
-                        cudaStream_t s);
+// the problem's own normalisers (per image pair, i.e. per scene)
+void launch_ea_segments(const fm_problem* pr, const float* params, int loss, cudaStream_t s);
 
 // IRLS / compact form (fm_irls.cu)
 void launch_ea_reweight(const fm_problem* pr, float tau, float delta, int irls, float* w,
                         unsigned long long* kept, cudaStream_t s);
 void launch_w_build(const fm_problem* pr, const float* w, float* W, cudaStream_t s);
-void launch_ea_compact(const fm_problem* pr, const float* params, float inv_z, int* step_counter,
-                       cudaStream_t s);
+void launch_ea_compact(const fm_problem* pr, const float* params, int* step_counter, cudaStream_t s);
+// pair_inv_z from per-scene counts: 1/count[scene] (0 when the count is 0)
+void launch_pair_inv_from_counts(const fm_problem* pr, const unsigned long long* count, cudaStream_t s);
+// count[s] = number of keypoint pairs of scene s with a weight > 0
+void launch_count_positive(const fm_problem* pr, const float* w, unsigned long long* count, cudaStream_t s);
 
 // setup steps (fm_init.cu, fm_reltrans.cu, fm_points.cu)
-void launch_mart_iter(const fm_problem* pr, const float* x, const float* c1, float* y, float sigma,
-                      float scale_p, cudaStream_t s);
+// y = x - (B x)/sigma_s per camera, with the constants of the camera's scene
+// in pr->mart_coef (see fm_rotation_init); c1 null for the first column
+void launch_mart_iter(const fm_problem* pr, const float* x, const float* c1, float* y, cudaStream_t s);
 void launch_normalise3(float* x, int N, cudaStream_t s);
 void launch_mart_finish(const float* c1, const float* c2, int N, float* params6, cudaStream_t s);
-void launch_hash_fill(float* x, int n, unsigned salt, cudaStream_t s);
+// x[r][c][a] (runs x N x 3) from the counter-based generator at the index the
+// value would have in the camera's own scene: (r N_s + c - c0_s) 3 + a
+void launch_hash_fill(const fm_problem* pr, float* x, int runs, unsigned salt, cudaStream_t s);
 void launch_merge(const fm_problem* pr, const float* o, int runs, float* stats, float* out,
                   int* best_run, cudaStream_t s);
 void launch_reltrans(const fm_problem* pr, const float* rot6, float* rel_t, float* err_out, cudaStream_t s);
 cudaError_t build_track_table(fm_problem* pr, int* T_out);
 void launch_triangulate(const fm_problem* pr, const float* params, float max_err_px, float min_angle_rad,
                         float* pts, int* valid, int* ncam, cudaStream_t s);
-void launch_scale_to_unit(float* x, int n, cudaStream_t s);
+// x <- x/|x| over each scene's cameras ([N][3])
+void launch_scale_to_unit(const fm_problem* pr, float* x, cudaStream_t s);
 void launch_ea_from_stages(const float* rot6, const float* o, int N, float* ea, cudaStream_t s);
 void launch_ea_to_Rt(const float* ea, int N, float* R, float* t, cudaStream_t s);
 
 // rotation / translation (fm_pose.cu)
 void launch_rot_pairs(const float* params, const int* pi, const int* pj, const float* rel_R,
-                      int P, float* seg_grad, float* seg_loss, int* step_counter,
+                      int P, const float* pair_inv_p, float* seg_grad, float* seg_loss, int* step_counter,
                       cudaStream_t s);
 void launch_trn_targets(const float* rot_params, const int* pj, const float* rel_t, int P,
                         float* target, cudaStream_t s);
 void launch_trn_pairs(const float* o, const int* pi, const int* pj, const float* target, int N,
-                      int P, int runs, float* seg_grad, float* seg_loss, int* step_counter,
-                      cudaStream_t s);
+                      int P, int runs, const float* pair_inv_p, float* seg_grad, float* seg_loss,
+                      int* step_counter, cudaStream_t s);
 
 // per-camera reduction, 6D adjoint and Adam (fm_cam.cu)
 struct CamUpdate {
@@ -268,9 +293,14 @@ struct CamUpdate {
   float lr, b1, b2, eps;
   int N, P, runs;
   const float* seg_loss;   // [runs][P] per-image-pair loss terms, or null
-  float* loss_out;         // [runs] fixed-order sum of seg_loss, or null
+  float* loss_out;         // [runs][S] fixed-order sums of seg_loss per scene, or null
+  const int* sc_pair_off;  // [S+1] image-pair range of each scene
+  int S;
 };
 void launch_cam_update(int stage, const CamUpdate& u, cudaStream_t s);
-void launch_sum_fixed(const float* x, int n, int runs, float* out, cudaStream_t s);
+// out[r*S + s] = fixed-order sum of x[r*P + sc_pair_off[s] .. sc_pair_off[s+1]);
+// sc_pair_off null: one range [0, P) (S = 1)
+void launch_sum_fixed(const float* x, int P, int runs, const int* sc_pair_off, int S, float* out,
+                      cudaStream_t s);
 
 }  // namespace fm

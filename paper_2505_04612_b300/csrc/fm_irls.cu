@@ -25,6 +25,8 @@
 // the small, accurately computed residuals, and the only term that still sees
 // W's rounding is d^T W d with d = e - e0 small while the poses stay near the
 // ones of the last reweighting.
+#include <algorithm>
+
 #include "fm_device.cuh"
 #include "fm_internal.h"
 
@@ -36,11 +38,12 @@ constexpr int U = kEaPairsPerLane;
 // one thread per lane run of U consecutive keypoint pairs (the runs of the
 // direct kernel); the run's first image pair comes from run_seg
 __global__ void k_ea_reweight(const float4* __restrict__ kp, const int* __restrict__ run_seg,
-                              const float4* __restrict__ seg_tab, int Z, int n_runs, float tau,
-                              float delta, int irls, float* __restrict__ w,
+                              const float4* __restrict__ seg_tab, const int* __restrict__ pair_scene,
+                              int Z, int n_runs, float tau, float delta, int irls, float* __restrict__ w,
                               unsigned long long* __restrict__ kept) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   int my_kept = 0;
+  int scene = -1;     // scene of the pairs counted in my_kept
   if (q < n_runs) {
     const int p0 = q * U;
     const int pend = min(p0 + U, Z);
@@ -55,6 +58,12 @@ __global__ void k_ea_reweight(const float4* __restrict__ kp, const int* __restri
         e2 = __ldg(seg_tab + 3 * s + 2);
         end = __float_as_int(e2.y);
       }
+      const int sc = __ldg(pair_scene + s);
+      if (sc != scene) {   // a run crossing a scene boundary (rare): flush the count
+        if (my_kept) atomicAdd(kept + scene, (unsigned long long)my_kept);
+        my_kept = 0;
+        scene = sc;
+      }
       const float4 x = __ldg(kp + p);
       const float ex = fmaf(e0.x, x.x, fmaf(e0.y, x.y, e0.z));
       const float ey = fmaf(e0.w, x.x, fmaf(e1.x, x.y, e1.y));
@@ -67,9 +76,38 @@ __global__ void k_ea_reweight(const float4* __restrict__ kp, const int* __restri
       my_kept += keep;
     }
   }
-  // integer counts: the total does not depend on the order of the atomics
-  for (int d = 16; d > 0; d >>= 1) my_kept += __shfl_xor_sync(0xffffffffu, my_kept, d);
-  if ((threadIdx.x & 31) == 0 && my_kept) atomicAdd(kept, (unsigned long long)my_kept);
+  // integer counts: the totals do not depend on the order of the atomics.
+  // Lanes of one scene are summed with a warp reduction (the usual case);
+  // otherwise every lane adds its own count.
+  const unsigned FULL = 0xffffffffu;
+  const int s0 = __shfl_sync(FULL, scene, 0);
+  if (__all_sync(FULL, scene == s0 || my_kept == 0)) {
+    for (int d = 16; d > 0; d >>= 1) my_kept += __shfl_xor_sync(FULL, my_kept, d);
+    if ((threadIdx.x & 31) == 0 && my_kept) atomicAdd(kept + s0, (unsigned long long)my_kept);
+  } else if (my_kept) {
+    atomicAdd(kept + scene, (unsigned long long)my_kept);
+  }
+}
+
+// count[s] += number of keypoint pairs with w > 0 in scene s (integer
+// atomics: order-independent)
+__global__ void k_count_positive(const float* __restrict__ w, const long long* __restrict__ sc_kp_off,
+                                 unsigned long long* __restrict__ count) {
+  // one CTA per (scene, chunk of 8192 pairs)
+  const int s = blockIdx.y;
+  const long long b = sc_kp_off[s] + (long long)blockIdx.x * 8192, e = min(b + 8192, sc_kp_off[s + 1]);
+  int c = 0;
+  for (long long m = b + threadIdx.x; m < e; m += blockDim.x) c += (w[m] > 0.f);
+  for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count + s, (unsigned long long)c);
+}
+
+__global__ void k_pair_inv_from_counts(const unsigned long long* __restrict__ count,
+                                       const int* __restrict__ pair_scene, int P, float* __restrict__ inv) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= P) return;
+  const unsigned long long c = count[pair_scene[n]];
+  inv[n] = c > 0 ? (float)(1.0 / (double)c) : 0.f;
 }
 
 // one warp per image pair; lanes stride over its keypoint pairs, then a
@@ -134,11 +172,12 @@ __device__ __forceinline__ int tri(int a, int c) {   // index of (a, c), a <= c,
 template <bool STEP>
 __global__ void k_ea_compact(const float* __restrict__ W, const float* __restrict__ params,
                              const int* __restrict__ pi, const int* __restrict__ pj, int P,
-                             float inv_z, float* __restrict__ seg_grad, float* __restrict__ seg_loss,
-                             int* step_counter) {
+                             const float* __restrict__ pair_inv_z, float* __restrict__ seg_grad,
+                             float* __restrict__ seg_loss, int* step_counter) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (STEP && step_counter && n == 0) *step_counter += 1;
   if (n >= P) return;
+  const float inv_z = pair_inv_z[n];   // normaliser of the image pair's scene
   PairGeo g;
   pair_geometry(params + 9 * pi[n], params + 9 * pj[n], g);
   float e[9];
@@ -179,18 +218,30 @@ void launch_ea_reweight(const fm_problem* pr, float tau, float delta, int irls, 
                         unsigned long long* kept, cudaStream_t s) {
   const int n_runs = (int)((pr->Z + U - 1) / U);
   if (n_runs == 0) return;
-  k_ea_reweight<<<(n_runs + 255) / 256, 256, 0, s>>>(pr->kp, pr->run_seg, pr->seg_tab, (int)pr->Z,
-                                                     n_runs, tau, delta, irls, w, kept);
+  k_ea_reweight<<<(n_runs + 255) / 256, 256, 0, s>>>(pr->kp, pr->run_seg, pr->seg_tab, pr->pair_scene,
+                                                     (int)pr->Z, n_runs, tau, delta, irls, w, kept);
 }
 
 void launch_w_build(const fm_problem* pr, const float* w, float* W, cudaStream_t s) {
   k_w_build<<<(pr->P + 3) / 4, 128, 0, s>>>(pr->kp, w, pr->seg_off, pr->seg_tab, pr->P, W);
 }
 
-void launch_ea_compact(const fm_problem* pr, const float* params, float inv_z, int* step_counter,
-                       cudaStream_t s) {
+void launch_ea_compact(const fm_problem* pr, const float* params, int* step_counter, cudaStream_t s) {
   k_ea_compact<true><<<(pr->P + 127) / 128, 128, 0, s>>>(pr->W, params, pr->pair_i, pr->pair_j, pr->P,
-                                                         inv_z, pr->seg_grad, pr->seg_loss, step_counter);
+                                                         pr->pair_inv_z, pr->seg_grad, pr->seg_loss,
+                                                         step_counter);
+}
+
+void launch_count_positive(const fm_problem* pr, const float* w, unsigned long long* count, cudaStream_t s) {
+  int64_t most = 0;
+  for (int q = 0; q < pr->S; ++q) most = std::max<int64_t>(most, pr->h_sc_kp_off[q + 1] - pr->h_sc_kp_off[q]);
+  if (most == 0) return;
+  dim3 grid((unsigned)((most + 8191) / 8192), pr->S);
+  k_count_positive<<<grid, 256, 0, s>>>(w, reinterpret_cast<const long long*>(pr->sc_kp_off), count);
+}
+
+void launch_pair_inv_from_counts(const fm_problem* pr, const unsigned long long* count, cudaStream_t s) {
+  k_pair_inv_from_counts<<<(pr->P + 127) / 128, 128, 0, s>>>(count, pr->pair_scene, pr->P, pr->pair_inv_z);
 }
 
 }  // namespace fm

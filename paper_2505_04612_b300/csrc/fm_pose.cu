@@ -14,11 +14,12 @@ namespace {
 // dtheta/dM = (c [w]_x / (2|w|) - |w| I / 2) / (|w|^2 + c^2); 0 at |w| = 0.
 __global__ void k_rot_pairs(const float* __restrict__ params, const int* __restrict__ pi,
                             const int* __restrict__ pj, const float* __restrict__ relR, int P,
-                            float inv_p, float* __restrict__ seg_grad,
+                            const float* __restrict__ pair_inv_p, float* __restrict__ seg_grad,
                             float* __restrict__ seg_loss, int* step_counter) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (step_counter && n == 0) *step_counter += 1;
   if (n >= P) return;
+  const float inv_p = pair_inv_p[n];   // 1/|P| of the image pair's scene
   Rot6 si, sj;
   rot6_forward(params + 6 * pi[n], si);
   rot6_forward(params + 6 * pj[n], sj);
@@ -86,12 +87,13 @@ __global__ void k_trn_targets(const float* __restrict__ rot, const int* __restri
 // sign(0) = 0; |o_j - o_i| <= 1e-12 gives a zero gradient.
 __global__ void k_trn_pairs(const float* __restrict__ o, const int* __restrict__ pi,
                             const int* __restrict__ pj, const float* __restrict__ tgt, int N,
-                            int P, int runs, float inv_p, float* __restrict__ seg_grad,
-                            float* __restrict__ seg_loss, int* step_counter) {
+                            int P, int runs, const float* __restrict__ pair_inv_p,
+                            float* __restrict__ seg_grad, float* __restrict__ seg_loss, int* step_counter) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (step_counter && idx == 0) *step_counter += 1;
   if (idx >= P * runs) return;
   const int run = idx / P, n = idx - run * P;
+  const float inv_p = pair_inv_p[n];
   const float* orun = o + (size_t)3 * N * run;
   const int i = pi[n], j = pj[n];
   float d[3], u[3], gu[3];
@@ -125,9 +127,9 @@ __global__ void k_trn_pairs(const float* __restrict__ o, const int* __restrict__
 }  // namespace
 
 void launch_rot_pairs(const float* params, const int* pi, const int* pj, const float* rel_R,
-                      int P, float* seg_grad, float* seg_loss, int* step_counter,
+                      int P, const float* pair_inv_p, float* seg_grad, float* seg_loss, int* step_counter,
                       cudaStream_t s) {
-  k_rot_pairs<<<(P + 127) / 128, 128, 0, s>>>(params, pi, pj, rel_R, P, 1.f / (float)P, seg_grad,
+  k_rot_pairs<<<(P + 127) / 128, 128, 0, s>>>(params, pi, pj, rel_R, P, pair_inv_p, seg_grad,
                                               seg_loss, step_counter);
 }
 
@@ -137,10 +139,10 @@ void launch_trn_targets(const float* rot_params, const int* pj, const float* rel
 }
 
 void launch_trn_pairs(const float* o, const int* pi, const int* pj, const float* target, int N,
-                      int P, int runs, float* seg_grad, float* seg_loss, int* step_counter,
-                      cudaStream_t s) {
+                      int P, int runs, const float* pair_inv_p, float* seg_grad, float* seg_loss,
+                      int* step_counter, cudaStream_t s) {
   const int n = P * runs;
-  k_trn_pairs<<<(n + 127) / 128, 128, 0, s>>>(o, pi, pj, target, N, P, runs, 1.f / (float)P,
+  k_trn_pairs<<<(n + 127) / 128, 128, 0, s>>>(o, pi, pj, target, N, P, runs, pair_inv_p,
                                               seg_grad, seg_loss, step_counter);
 }
 

@@ -128,8 +128,12 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
   }
   fm::launch_seg_records(v.seg_off, v.run_seg, v.wrun_info, P, v.seg_rec, s);
   if (n_wruns > 0) fm::launch_ea_direct(&v, weights_dev, loss, s);
-  fm::launch_ea_segments(&v, params_dev, loss, inv_z, s);
-  fm::launch_sum_fixed(v.seg_loss, P, 1, loss_dev, s);
+  fm::SegArgs sa = fm::seg_args(&v, params_dev);
+  sa.pair_scale = nullptr;   // one scene: the scalar normaliser
+  sa.g_scale = (loss == FM_EA_L1) ? inv_z : 2.f * inv_z;
+  sa.l_scale = inv_z;
+  fm::launch_ea_segments(sa, s);
+  fm::launch_sum_fixed(v.seg_loss, P, 1, nullptr, 1, loss_dev, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) return static_fail(FM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   return FM_OK;

@@ -61,6 +61,8 @@ class fm_problem_desc(ctypes.Structure):
         ("rel_t", ctypes.c_void_p),
         ("inputs_on_device", ctypes.c_int32),
         ("cuda_stream", ctypes.c_void_p),
+        ("n_scenes", ctypes.c_int32),
+        ("scene_cam_off", ctypes.c_void_p),
     ]
 
 
@@ -73,6 +75,7 @@ class fm_problem_info(ctypes.Structure):
         ("pairs_per_lane", ctypes.c_int32),
         ("n_records", ctypes.c_int64),
         ("device_bytes", ctypes.c_int64),
+        ("n_scenes", ctypes.c_int32),
     ]
 
 
@@ -382,10 +385,11 @@ def solve_opts(**overrides) -> fm_solve_opts:
 class Problem:
     """One fm_problem.  Inputs may be numpy arrays / CPU tensors (copied from
     the host) or CUDA tensors (read on the device); all of them must be on the
-    same side."""
+    same side.  scene_cam_off ([S+1] camera offsets, host) makes a problem of
+    S independent scenes whose losses come back per scene."""
 
     def __init__(self, pair_i, pair_j, kp_img_pair, kp1_px, kp2_px, focal, cx, cy,
-                 rel_R=None, rel_t=None, kp_track=None, stream=None):
+                 rel_R=None, rel_t=None, kp_track=None, stream=None, scene_cam_off=None):
         arrs = dict(
             pair_cam_i=_as(pair_i, np.int32), pair_cam_j=_as(pair_j, np.int32),
             kp_img_pair=_as(kp_img_pair, np.int32),
@@ -411,6 +415,13 @@ class Problem:
             raise ValueError("all inputs must be on the device or all on the host")
         d.inputs_on_device = int(sides == {True})
         d.cuda_stream = _stream_handle(stream)
+        self.S = 1
+        if scene_cam_off is not None:
+            off = np.ascontiguousarray(np.asarray(scene_cam_off), dtype=np.int32)
+            self._keep.append(off)
+            d.n_scenes = int(len(off) - 1)
+            d.scene_cam_off = off.ctypes.data
+            self.S = max(int(len(off) - 1), 1)
         self.n_cams, self.n_pairs, self.n_kp = d.n_cams, d.n_img_pairs, d.n_kp_pairs
         self.handle = fm_problem_create(d)
         self._keep = []
@@ -459,8 +470,8 @@ class Problem:
         fm_ea_set_loss(self.handle, loss)
 
     def set_ea_weights(self, weights, inv_z=None):
-        if weights is not None and inv_z is None:
-            inv_z = 1.0 / max(int((np.asarray(weights.cpu() if hasattr(weights, "cpu") else weights) > 0).sum()), 1)
+        """inv_z None: each scene's 1/(number of its positive weights),
+        computed by the library."""
         fm_ea_set_weights(self.handle, weights, inv_z if inv_z is not None else 0.0)
 
     def reweight(self, tau, delta, irls=True):
@@ -477,7 +488,7 @@ class Problem:
         path).  Returns (loss, grad) with grad of the same kind as params, or
         grad_out when given (same side as params)."""
         nruns = self.runs if stage == FM_STAGE_TRANSLATION else 1
-        loss = (ctypes.c_float * nruns)() if want_loss else None
+        loss = (ctypes.c_float * (nruns * self.S))() if want_loss else None
         p = _as(params, np.float32)
         addr, dev, keep = _ptr(p)
         grad = None
@@ -496,10 +507,18 @@ class Problem:
                 grad = np.empty(np.asarray(p).shape, dtype=np.float32)
                 gaddr = grad.ctypes.data
         fm_loss_grad(self.handle, stage, addr, loss, gaddr, int(dev))
-        lv = None
-        if want_loss:
-            lv = loss[0] if nruns == 1 else [loss[k] for k in range(nruns)]
+        lv = self._losses(loss, nruns) if want_loss else None
         return lv, grad
+
+    def _losses(self, loss, nruns):
+        """One scene: a float ([m] for m translation runs); S scenes: [S]
+        (or [m][S])."""
+        vals = [loss[k] for k in range(nruns * self.S)]
+        if self.S == 1:
+            return vals[0] if nruns == 1 else vals
+        if nruns == 1:
+            return vals
+        return [vals[r * self.S:(r + 1) * self.S] for r in range(nruns)]
 
     def timing(self, enable=True):
         fm_timing_enable(self.handle, enable)
@@ -579,16 +598,17 @@ class Problem:
     def step(self, stage, n_iters, lr, beta1=0.9, beta2=0.999, eps=1e-8, want_loss=False):
         opts = fm_adam_opts(lr, beta1, beta2, eps)
         nruns = self.runs if stage == FM_STAGE_TRANSLATION else 1
-        loss = (ctypes.c_float * nruns)() if want_loss else None
+        loss = (ctypes.c_float * (nruns * self.S))() if want_loss else None
         fm_step(self.handle, stage, opts, n_iters, loss)
         if want_loss:
-            return loss[0] if nruns == 1 else [loss[k] for k in range(nruns)]
+            return self._losses(loss, nruns)
         return None
 
 
 def problem_from_scene(scene, rel_R=None, rel_t=None, device=True, stream=None):
     """Builds a Problem from a ``synthetic.scenes.Scene``-like object (fields
-    pair_i, pair_j, kp_img_pair, kp1_px, kp2_px, focal, cx, cy, kp_track)."""
+    pair_i, pair_j, kp_img_pair, kp1_px, kp2_px, focal, cx, cy, kp_track, and
+    scene_cam_off for a batch of scenes)."""
     arrays = [scene.pair_i, scene.pair_j, scene.kp_img_pair, scene.kp1_px, scene.kp2_px,
               scene.focal, scene.cx, scene.cy]
     extra = dict(rel_R=rel_R, rel_t=rel_t, kp_track=scene.kp_track)
@@ -601,4 +621,4 @@ def problem_from_scene(scene, rel_R=None, rel_t=None, device=True, stream=None):
         arrays = [dv(a, dt) for a, dt in zip(arrays, dts)]
         extra = dict(rel_R=dv(rel_R, np.float32), rel_t=dv(rel_t, np.float32),
                      kp_track=dv(scene.kp_track, np.int32))
-    return Problem(*arrays, stream=stream, **extra)
+    return Problem(*arrays, stream=stream, scene_cam_off=getattr(scene, "scene_cam_off", None), **extra)

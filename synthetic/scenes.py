@@ -26,7 +26,7 @@ from itertools import combinations
 import numpy as np
 
 __all__ = ["Scene", "make_scene", "scene_c1", "scene_c2", "perturb_params",
-           "gt_relative_poses", "CONFIGS"]
+           "gt_relative_poses", "CONFIGS", "concat_scenes", "batch_c4"]
 
 
 @dataclass
@@ -49,6 +49,7 @@ class Scene:
     kp_track: np.ndarray     # [Z] int32
     kp_inlier: np.ndarray    # [Z] bool, False where the pair was replaced by an outlier
     meta: dict = field(default_factory=dict)
+    scene_cam_off: np.ndarray | None = None   # [S+1] camera offsets of a batch of scenes
 
     @property
     def n_cams(self) -> int:
@@ -339,6 +340,52 @@ CONFIGS = {
     # keypoint pairs is about 5M, the pair count the workload is quoted at
     "c2_5m": dict(fn=scene_c2, kwargs=dict(n_points=605_000)),
 }
+
+
+def concat_scenes(scenes, name="batch") -> Scene:
+    """One Scene holding several independent scenes: cameras, image pairs,
+    keypoint pairs and tracks concatenated scene by scene, with the camera
+    offsets in ``scene_cam_off``.  Image-pair and track indices are shifted."""
+    cam_off = np.zeros(len(scenes) + 1, dtype=np.int64)
+    pair_off = np.zeros(len(scenes) + 1, dtype=np.int64)
+    trk_off = np.zeros(len(scenes) + 1, dtype=np.int64)
+    for k, sc in enumerate(scenes):
+        cam_off[k + 1] = cam_off[k] + sc.n_cams
+        pair_off[k + 1] = pair_off[k] + sc.n_pairs
+        trk_off[k + 1] = trk_off[k] + (int(sc.kp_track.max()) + 1 if sc.n_kp else 0)
+    cat = np.concatenate
+    return Scene(
+        name=name, seed=scenes[0].seed, width=scenes[0].width, height=scenes[0].height,
+        focal=cat([sc.focal for sc in scenes]), cx=cat([sc.cx for sc in scenes]),
+        cy=cat([sc.cy for sc in scenes]), R_gt=cat([sc.R_gt for sc in scenes]),
+        t_gt=cat([sc.t_gt for sc in scenes]), points=cat([sc.points for sc in scenes]),
+        pair_i=cat([sc.pair_i + cam_off[k] for k, sc in enumerate(scenes)]).astype(np.int32),
+        pair_j=cat([sc.pair_j + cam_off[k] for k, sc in enumerate(scenes)]).astype(np.int32),
+        kp_img_pair=cat([sc.kp_img_pair + pair_off[k] for k, sc in enumerate(scenes)]).astype(np.int32),
+        kp1_px=cat([sc.kp1_px for sc in scenes]), kp2_px=cat([sc.kp2_px for sc in scenes]),
+        kp_track=cat([sc.kp_track + trk_off[k] for k, sc in enumerate(scenes)]).astype(np.int32),
+        kp_inlier=cat([sc.kp_inlier for sc in scenes]),
+        meta=dict(pair_off=pair_off, track_off=trk_off,
+                  kp_off=np.concatenate([[0], np.cumsum([sc.n_kp for sc in scenes])])),
+        scene_cam_off=cam_off.astype(np.int32))
+
+
+def batch_c4(seed: int = 0, n_scenes: int = 64, cams=(20, 500), points=(2_000, 150_000),
+             outliers=(0.05, 0.20)):
+    """Scenes of uneven size for batched solving: per scene (seed-indexed)
+    N ~ logU(cams), point count ~ logU(points), outlier fraction ~ U(outliers),
+    sigma = 1 px, the geometry of ``scene_c2`` (trajectory through a
+    50x50x10 box).  Returns the list of scenes."""
+    rng = np.random.default_rng(10_000 + seed)
+    out = []
+    for k in range(n_scenes):
+        n = int(round(np.exp(rng.uniform(np.log(cams[0]), np.log(cams[1])))))
+        m = int(round(np.exp(rng.uniform(np.log(points[0]), np.log(points[1])))))
+        of = float(rng.uniform(*outliers))
+        sc = scene_c2(seed=1000 * (seed + 1) + k, n_cams=n, n_points=m, outlier_frac=of)
+        sc.name = f"c4[{k}]"
+        out.append(sc)
+    return out
 
 
 def make_scene(config: str = "c1", seed: int = 0, **overrides) -> Scene:

@@ -49,10 +49,11 @@ def test_struct_layout_matches_c():
 #include <stddef.h>
 #include "fastmap.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(fm_problem_desc),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(fm_problem_desc),
          offsetof(fm_problem_desc, inputs_on_device), offsetof(fm_problem_desc, cuda_stream),
          sizeof(fm_problem_info), sizeof(fm_adam_opts), sizeof(fm_solve_opts), offsetof(fm_solve_opts, eps),
-         sizeof(fm_result), offsetof(fm_result, n_kept), sizeof(fm_kernel_time));
+         sizeof(fm_result), offsetof(fm_result, n_kept), sizeof(fm_kernel_time),
+         offsetof(fm_problem_desc, scene_cam_off), offsetof(fm_problem_info, n_scenes));
   return 0;
 }
 """
@@ -65,7 +66,8 @@ int main(void) {
     assert vals == [ctypes.sizeof(F.fm_problem_desc), F.fm_problem_desc.inputs_on_device.offset,
                     F.fm_problem_desc.cuda_stream.offset, ctypes.sizeof(F.fm_problem_info),
                     ctypes.sizeof(F.fm_adam_opts), ctypes.sizeof(F.fm_solve_opts), F.fm_solve_opts.eps.offset,
-                    ctypes.sizeof(F.fm_result), F.fm_result.n_kept.offset, ctypes.sizeof(F.fm_kernel_time)]
+                    ctypes.sizeof(F.fm_result), F.fm_result.n_kept.offset, ctypes.sizeof(F.fm_kernel_time),
+                    F.fm_problem_desc.scene_cam_off.offset, F.fm_problem_info.n_scenes.offset]
 
 
 def test_errors_without_problem_are_reported(lib):

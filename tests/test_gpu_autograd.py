@@ -251,3 +251,30 @@ def test_errors():
         assert e.value.status == F.FM_ERR_STATE
         with pytest.raises(ValueError):
             A.epipolar_loss(p, pr, "bogus")
+
+
+def test_batch_of_scenes_per_scene_losses():
+    """A problem holding several scenes returns one loss per scene; backward
+    with upstream gradients g_s gives sum_s g_s dL_s/dparams (each scene's
+    cameras get g_s times their own gradient)."""
+    torch, A, F = _mods()
+    from synthetic.scenes import concat_scenes
+    scenes = [scene("c1", 0), scene("c1", 2), scene("c1", 4)]
+    b = concat_scenes(scenes)
+    ps = [np.asarray(perturbed_params_ea(sc, 5 + k), np.float32) for k, sc in enumerate(scenes)]
+    gs = torch.tensor([1.0, -0.5, 2.0], device="cuda")
+    with G.make_problem(b) as pb:
+        _set_loss(pb, "l2")
+        for mode in MODES:
+            p = torch.from_numpy(np.concatenate([q.reshape(-1) for q in ps])).cuda().requires_grad_(True)
+            L = A.epipolar_loss(p, pb, mode)
+            assert L.shape == (3,)
+            (L * gs).sum().backward()
+            g = p.grad.cpu().numpy()
+            o = 0
+            for k, sc in enumerate(scenes):
+                Lo, go = G.ea_oracle(sc, ps[k], "l2")
+                assert abs(float(L.detach()[k]) - Lo) <= LOSS_TOL * abs(Lo)
+                gk = g[o:o + 9 * sc.n_cams].astype(np.float64)
+                assert G.rel_err(gk, float(gs[k]) * go.reshape(-1)) < GRAD_TOL, (mode, k)
+                o += 9 * sc.n_cams

@@ -1,0 +1,184 @@
+"""Several independent scenes in one problem (scene_cam_off): every loss is
+the scene's own and every kernel touches a scene's cameras and image pairs
+only, so a batch must give each scene what solving it alone gives.  The
+rotation and translation stages, the IRLS/compact epipolar path and the whole
+fm_solve do the same float32 operations per element in the same order
+whether batched or not (checked bit for bit); the direct epipolar kernel
+splits a batch into warp runs at other places than a scene alone, so its
+sums are compared within the parity tolerance, and against the oracle."""
+import numpy as np
+import pytest
+
+from synthetic.scenes import concat_scenes, gt_relative_poses, make_scene
+from tests import _gpu as G
+from tests._util import gt_params6, perturbed_params_ea
+
+pytestmark = pytest.mark.gpu
+
+LOSS_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+def _F():
+    from paper_2505_04612_b300 import fastmap as F
+    return F
+
+
+def _scenes():
+    # uneven sizes: two c1 scenes, a small and a larger c2-geometry scene
+    return [make_scene("c1", 0), make_scene("c1", 3, n_points=900),
+            make_scene("c2", 1, n_cams=24, n_points=4000), make_scene("c2", 2, n_cams=60, n_points=12000)]
+
+
+def _rel(scenes, noise=1.0):
+    R, t = [], []
+    for k, sc in enumerate(scenes):
+        a, b = gt_relative_poses(sc, rot_noise_deg=noise, dir_noise_deg=noise, seed=k)
+        R.append(a.astype(np.float32))
+        t.append(b.astype(np.float32))
+    return R, t
+
+
+def _cat_params(per_scene):
+    return np.concatenate([np.asarray(p, np.float32).reshape(-1) for p in per_scene])
+
+
+def _split(x, scenes, dim):
+    out, o = [], 0
+    for sc in scenes:
+        out.append(x[o:o + dim * sc.n_cams])
+        o += dim * sc.n_cams
+    return out
+
+
+def test_invalid_batches_are_rejected():
+    F = _F()
+    scenes = _scenes()[:2]
+    b = concat_scenes(scenes)
+    bad = b.scene_cam_off.copy()
+    bad[1] += 1                                   # the first scene's last pair now crosses scenes
+    b.scene_cam_off = bad
+    with pytest.raises(F.FastMapError) as e:
+        G.make_problem(b)
+    assert e.value.status == F.FM_ERR_INVALID_ARG
+    b = concat_scenes(scenes)
+    b.scene_cam_off = np.array([0, 2, b.n_cams], np.int32)   # image pairs of cameras 0-1 with others cross
+    with pytest.raises(F.FastMapError):
+        G.make_problem(b)
+    b = concat_scenes(scenes)
+    b.scene_cam_off = np.array([0, 5, b.n_cams - 1], np.int32)   # does not end at n_cams
+    with pytest.raises(F.FastMapError):
+        G.make_problem(b)
+
+
+def test_rotation_and_translation_stages_bitwise():
+    """Loss per scene and gradient of the rotation and translation stages,
+    and ten Adam steps of each, equal the per-scene results bit for bit."""
+    import torch
+    F = _F()
+    scenes = _scenes()
+    b = concat_scenes(scenes)
+    R, t = _rel(scenes)
+    rng = np.random.default_rng(0)
+    p6 = [gt_params6(sc) + rng.normal(0, 0.05, size=(sc.n_cams, 6)) for sc in scenes]
+    o = [sc.centers_gt + rng.normal(0, 0.3, size=(sc.n_cams, 3)) for sc in scenes]
+    with G.make_problem(b, rel_R=np.concatenate(R), rel_t=np.concatenate(t)) as pb:
+        assert pb.info().n_scenes == len(scenes)
+        Lb, gb = pb.loss_grad(F.FM_STAGE_ROTATION, torch.from_numpy(_cat_params(p6)).cuda())
+        pb.set_params(F.FM_STAGE_ROTATION, torch.from_numpy(_cat_params(p6)).cuda())
+        pb.step(F.FM_STAGE_ROTATION, 10, lr=1e-3)
+        rb = pb.get_params(F.FM_STAGE_ROTATION).cpu().numpy()
+        Ltb, gtb = pb.loss_grad(F.FM_STAGE_TRANSLATION, torch.from_numpy(_cat_params(o)).cuda())
+        gb, gtb = gb.cpu().numpy(), gtb.cpu().numpy()
+    for k, sc in enumerate(scenes):
+        with G.make_problem(sc, rel_R=R[k], rel_t=t[k]) as ps:
+            L, g = ps.loss_grad(F.FM_STAGE_ROTATION, torch.from_numpy(_cat_params([p6[k]])).cuda())
+            assert L == Lb[k]
+            np.testing.assert_array_equal(g.cpu().numpy(), _split(gb, scenes, 6)[k])
+            ps.set_params(F.FM_STAGE_ROTATION, torch.from_numpy(_cat_params([p6[k]])).cuda())
+            ps.step(F.FM_STAGE_ROTATION, 10, lr=1e-3)
+            np.testing.assert_array_equal(ps.get_params(F.FM_STAGE_ROTATION).cpu().numpy(),
+                                          _split(rb, scenes, 6)[k])
+            Lt, gt = ps.loss_grad(F.FM_STAGE_TRANSLATION, torch.from_numpy(_cat_params([o[k]])).cuda())
+            assert Lt == Ltb[k]
+            np.testing.assert_array_equal(gt.cpu().numpy(), _split(gtb, scenes, 3)[k])
+
+
+@pytest.mark.parametrize("loss", ["l1", "l2"])
+def test_direct_epipolar_per_scene(loss):
+    """Direct epipolar loss and gradient of a batch: each scene's loss and
+    gradient match the scene alone and the oracle (L1 up to sign-ambiguous
+    pairs, as in the single-scene parity tests)."""
+    import torch
+    F = _F()
+    scenes = _scenes()
+    b = concat_scenes(scenes)
+    ps = [perturbed_params_ea(sc, 3 + k) for k, sc in enumerate(scenes)]
+    with G.make_problem(b) as pb:
+        pb.set_ea_loss(F.FM_EA_L1 if loss == "l1" else F.FM_EA_L2)
+        Lb, gb = pb.loss_grad(F.FM_STAGE_EPIPOLAR, torch.from_numpy(_cat_params(ps)).cuda())
+        gb = gb.cpu().numpy().astype(np.float64)
+    for k, sc in enumerate(scenes):
+        g = _split(gb, scenes, 9)[k]
+        Lo, go = G.ea_oracle(sc, ps[k], loss)
+        assert abs(Lb[k] - Lo) <= LOSS_TOL * abs(Lo)
+        if loss == "l2":
+            assert G.rel_err(g.reshape(go.shape), go) < GRAD_TOL
+        else:
+            res = G.l1_grad_matches(sc, ps[k], g, GRAD_TOL)
+            if res is not None:
+                assert res[0], res
+        with G.make_problem(sc) as p1:
+            p1.set_ea_loss(F.FM_EA_L1 if loss == "l1" else F.FM_EA_L2)
+            L1, g1 = p1.loss_grad(F.FM_STAGE_EPIPOLAR, torch.from_numpy(_cat_params([ps[k]])).cuda())
+        assert abs(Lb[k] - L1) <= 1e-6 * abs(L1)
+        assert G.rel_err(g, g1.cpu().numpy()) < 1e-5
+
+
+def test_reweight_and_compact_bitwise():
+    """IRLS reweighting counts kept pairs per scene; the compact steps that
+    follow equal the per-scene ones bit for bit."""
+    import torch
+    F = _F()
+    scenes = _scenes()
+    b = concat_scenes(scenes)
+    ps = [perturbed_params_ea(sc, k, sigma_rot=0.002, sigma_t=0.002) for k, sc in enumerate(scenes)]
+    with G.make_problem(b) as pb:
+        pb.set_params(F.FM_STAGE_EPIPOLAR, torch.from_numpy(_cat_params(ps)).cuda())
+        kept_b = pb.reweight(0.02, 1e-5)
+        pb.set_ea_loss(F.FM_EA_COMPACT)
+        Lb = pb.step(F.FM_STAGE_EPIPOLAR, 20, lr=1e-4, want_loss=True)
+        eb = pb.get_params(F.FM_STAGE_EPIPOLAR).cpu().numpy()
+    kept = 0
+    for k, sc in enumerate(scenes):
+        with G.make_problem(sc) as p1:
+            p1.set_params(F.FM_STAGE_EPIPOLAR, torch.from_numpy(_cat_params([ps[k]])).cuda())
+            kept += p1.reweight(0.02, 1e-5)
+            p1.set_ea_loss(F.FM_EA_COMPACT)
+            L1 = p1.step(F.FM_STAGE_EPIPOLAR, 20, lr=1e-4, want_loss=True)
+            assert L1 == Lb[k]
+            np.testing.assert_array_equal(p1.get_params(F.FM_STAGE_EPIPOLAR).cpu().numpy(),
+                                          _split(eb, scenes, 9)[k])
+    assert kept == kept_b
+
+
+def test_solve_batch_equals_solves_one_at_a_time():
+    """fm_solve on a batch returns, per scene, the poses and points of
+    fm_solve on the scene alone, bit for bit (fewer iterations than the
+    defaults, to keep the test short)."""
+    scenes = _scenes()
+    b = concat_scenes(scenes)
+    R, _ = _rel(scenes)
+    opts = dict(rot_iters=200, trn_iters=200, trn_final_iters=100, ea_rounds=2, ea_iters=100)
+    T = int(b.kp_track.max()) + 1
+    with G.make_problem(b, rel_R=np.concatenate(R)) as pb:
+        ob = pb.solve(n_tracks=T, **opts)
+    toff = b.meta["track_off"]
+    for k, sc in enumerate(scenes):
+        c0, c1 = b.scene_cam_off[k], b.scene_cam_off[k + 1]
+        with G.make_problem(sc, rel_R=R[k]) as p1:
+            o1 = p1.solve(n_tracks=int(sc.kp_track.max()) + 1, **opts)
+        np.testing.assert_array_equal(o1["R"], ob["R"][c0:c1])
+        np.testing.assert_array_equal(o1["t"], ob["t"][c0:c1])
+        np.testing.assert_array_equal(o1["points"], ob["points"][toff[k]:toff[k + 1]])
+        np.testing.assert_array_equal(o1["point_valid"], ob["point_valid"][toff[k]:toff[k + 1]])
