@@ -54,7 +54,7 @@ def args_():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2_5m")
+    ap.add_argument("--config", default="c2_5m", help="c2_5m (default) or batch_c4")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autograd-modes", action="store_true",
@@ -278,6 +278,110 @@ def autograd_modes(pr, p_dev, flush, steps, warmup, Z):
     return out
 
 
+def run_batch(a):
+    """Batched solving (many scenes of uneven size in one problem) against
+    solving the same scenes one problem at a time, on one GPU.
+
+    Workload: ``batch_c4`` -- 64 scenes, N ~ logU(20, 500) cameras, point
+    counts ~ logU(2k, 150k) scaled by 2.3 so that the batch holds ~20M
+    keypoint pairs, 5-20% outliers, sigma 1 px, relative rotations from
+    ground truth with 1 deg noise.  Two measurements:
+      * the epipolar step (direct L1 + Adam, one fm_step iteration, L2 flushed
+        before each): one step over the whole batch vs one step of every
+        scene's own problem in turn; value = keypoint-pair evals/s of the
+        batched step;
+      * the whole fm_solve (default options) of the batch vs the 64 solves.
+    """
+    import torch
+    from paper_2505_04612_b300 import build as B
+    B.build()
+    from paper_2505_04612_b300 import fastmap as F
+    from synthetic.scenes import batch_c4, concat_scenes, gt_relative_poses
+    t0 = time.time()
+    scenes = batch_c4(a.seed, point_scale=2.3)
+    gen_s = time.time() - t0
+    rels = [gt_relative_poses(sc, rot_noise_deg=1.0, seed=k) for k, sc in enumerate(scenes)]
+    b = concat_scenes(scenes)
+    Z = b.n_kp
+    dev = torch.device("cuda", 0)
+    flush_w = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush_r = torch.zeros(64 << 20, dtype=torch.float32, device=dev)
+
+    def flush():
+        flush_w.zero_()
+        flush_r.sum()
+
+    def ea_params(sc, k):
+        rng = np.random.default_rng(500 + k)
+        p = np.concatenate([sc.R_gt[:, :, 0], sc.R_gt[:, :, 1], sc.t_gt], axis=1)
+        return (p + rng.normal(0.0, 0.01, size=p.shape)).astype(np.float32)
+
+    params = [ea_params(sc, k) for k, sc in enumerate(scenes)]
+    rel_R = [r[0].astype(np.float32) for r in rels]
+
+    def step_time(pr, p, steps):
+        pr.set_params(F.FM_STAGE_EPIPOLAR, torch.from_numpy(p.reshape(-1)).to(dev))
+        pr.set_ea_loss(F.FM_EA_L1)
+        for _ in range(a.warmup):
+            flush()
+            pr.step(F.FM_STAGE_EPIPOLAR, 1, lr=1e-4)
+        st = torch.cuda.current_stream()
+        ms = 0.0
+        for _ in range(steps):
+            flush()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            pr.step(F.FM_STAGE_EPIPOLAR, 1, lr=1e-4)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        return ms / steps
+
+    def solve_time(pr):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = pr.solve()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, out
+
+    # batched
+    pb = F.problem_from_scene(b, rel_R=np.concatenate(rel_R))
+    step_b = step_time(pb, np.concatenate(params), a.steps)
+    solve_b, out_b = solve_time(pb)
+    kt = pb.timing_read()
+    pb.close()
+    # one scene at a time
+    step_s = 0.0
+    solve_s = 0.0
+    for k, sc in enumerate(scenes):
+        ps = F.problem_from_scene(sc, rel_R=rel_R[k])
+        step_s += step_time(ps, params[k], max(a.steps // 4, 3))
+        ts, _ = solve_time(ps)
+        solve_s += ts
+        ps.close()
+    from oracle.solve import rotation_errors_deg
+    rot_err = [float(rotation_errors_deg(out_b["R"][b.scene_cam_off[k]:b.scene_cam_off[k + 1]].astype(np.float64),
+                                         sc.R_gt).mean()) for k, sc in enumerate(scenes)]
+    line = {
+        "metric": METRIC, "value": Z / (step_b * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": step_b, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch_c4: {len(scenes)} scenes in one problem, {b.n_cams} cameras, "
+                               f"{b.n_pairs} image pairs, {Z} keypoint pairs, seed {a.seed}",
+                   "l2": "flushed before every timed step (256 MB write + 256 MB read); flush not timed"},
+        "batched_vs_one_at_a_time": {
+            "epipolar_step_ms": {"batched": step_b, "one_at_a_time": step_s, "speedup": step_s / step_b},
+            "fm_solve_s": {"batched": solve_b, "one_at_a_time": solve_s, "speedup": solve_s / solve_b},
+            "mean_rotation_error_deg": {"median_over_scenes": float(np.median(rot_err)),
+                                        "max_over_scenes": float(np.max(rot_err))},
+            "generation_s": gen_s,
+        },
+        "gpu_launches_batched_solve": int(sum(v[0] for v in kt.values())),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def workload_config(sc, a):
     return {"workload": f"{a.config}: epipolar adjustment step (L1, Eq. 7, + Adam), {sc.n_cams} cameras, "
                         f"{sc.n_pairs} image pairs, {sc.n_kp} keypoint pairs, seed {a.seed}",
@@ -292,6 +396,8 @@ def main():
         return cpu_worker(a.cpu_worker)
     if a.impl == "reference":
         return run_reference(a)
+    if a.config == "batch_c4":
+        return run_batch(a)
     import torch
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))

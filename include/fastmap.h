@@ -403,6 +403,12 @@ typedef struct {
  * world frame.  Synchronises. */
 fm_status fm_solve(fm_problem* problem, const fm_solve_opts* opts, fm_result* result);
 
+/* fm_step replays captured CUDA graphs of 16 iterations (one graph launch
+ * instead of every kernel launch of the 16 iterations) whenever per-kernel
+ * timing and the loss trace are off; the results are identical either way.
+ * enable = 0 launches every kernel from the host.  Default on. */
+fm_status fm_graphs_enable(fm_problem* problem, int32_t enable);
+
 /* ---------------------------------------------------------- observability
  * (no counterpart in the paper, which times whole stages by wall clock) */
 

@@ -11,6 +11,8 @@ thread_local std::string g_create_error = "no error";
 }
 
 namespace fm {
+thread_local bool g_capturing = false;
+thread_local bool g_plain_once = false;
 void set_thread_error(const std::string& msg) { g_create_error = msg; }
 
 const char* const kKernelNames[kKCount] = {
@@ -168,6 +170,14 @@ void release(fm_problem* pr) {
   dfree(pr->merge_buf); dfree(pr->best_run);
   dfree(pr->sc_cam_off); dfree(pr->sc_pair_off); dfree(pr->sc_kp_off); dfree(pr->cam_scene);
   dfree(pr->pair_scene); dfree(pr->pair_inv_p); dfree(pr->pair_inv_z); dfree(pr->mart_coef);
+  for (auto& g : pr->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  pr->graphs.clear();
+  if (pr->cap_stream) cudaStreamDestroy(pr->cap_stream);
+  pr->cap_stream = nullptr;
+  if (pr->graph_in) cudaEventDestroy(pr->graph_in);
+  if (pr->graph_out) cudaEventDestroy(pr->graph_out);
+  pr->graph_in = pr->graph_out = nullptr;
   drain_timing(pr, false);
   for (cudaEvent_t e : pr->event_pool) cudaEventDestroy(e);
   pr->event_pool.clear();
@@ -496,6 +506,7 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
   const int P = pr->P, N = pr->N;
   int runs = 1;
   int* step = adam ? state->t : nullptr;
+
   if (st == FM_STAGE_EPIPOLAR && pr->ea_loss == FM_EA_COMPACT) {
     if (!pr->W_valid) {
       fm_status e = rebuild_W(pr, params);
@@ -585,6 +596,7 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
 
 fm_status resize_runs(fm_problem* pr, int runs) {
   if (runs == pr->trn_runs) return FM_OK;
+  pr->graph_epoch += 1;   // buffers are reallocated
   const size_t n = 3 * (size_t)pr->N * runs;
   dfree(pr->trn_params);
   dfree(pr->trn_adam.m);
@@ -733,6 +745,7 @@ fm_status fm_ea_set_loss(fm_problem* pr, fm_ea_loss loss) {
   if (loss != FM_EA_L1 && loss != FM_EA_L2 && loss != FM_EA_COMPACT)
     return fail(pr, FM_ERR_INVALID_ARG, "unknown epipolar loss");
   pr->ea_loss = loss;
+  pr->graph_epoch += 1;
   return FM_OK;
 }
 
@@ -769,6 +782,7 @@ static fm_status normalisers_from_counts(fm_problem* pr, int64_t* total) {
 
 fm_status fm_ea_set_weights(fm_problem* pr, const float* w, int32_t on_device, float inv_z) {
   if (!pr) return FM_ERR_INVALID_ARG;
+  pr->graph_epoch += 1;   // the weight pointer of the captured launches may change
   if (!w) {
     dfree(pr->ea_w);
     pr->W_valid = false;
@@ -801,11 +815,13 @@ fm_status fm_ea_set_weights(fm_problem* pr, const float* w, int32_t on_device, f
 }
 
 fm_status fm_ea_reweight(fm_problem* pr, float tau, float delta, int32_t irls, int64_t* n_kept) {
+  fm::g_plain_once = true;
   if (!pr) return FM_ERR_INVALID_ARG;
   if (!(tau > 0.f) || !(delta > 0.f) || !std::isfinite(delta))
     return fail(pr, FM_ERR_INVALID_ARG, "tau > 0 and finite delta > 0 required");
   if (!pr->ea_params_set) return fail(pr, FM_ERR_STATE, "the epipolar-stage parameters have not been set");
   cudaStream_t s = pr->stream;
+  pr->graph_epoch += 1;
   if (!pr->ea_w) FM_ALLOC(pr, pr->ea_w, (size_t)pr->Z);
   {
     Timed t(pr, fm::kKEaTables);
@@ -844,6 +860,7 @@ fm_status fm_ea_get_weights(fm_problem* pr, float* out, int32_t on_device, float
 
 fm_status fm_loss_grad(fm_problem* pr, fm_stage st, const float* params, float* loss, float* grad,
                        int32_t mem_on_device) {
+  fm::g_plain_once = true;
   if (!pr) return FM_ERR_INVALID_ARG;
   if (!valid_stage(st)) return fail(pr, FM_ERR_INVALID_ARG, "unknown stage");
   if (!params) return fail(pr, FM_ERR_INVALID_ARG, "params is NULL");
@@ -884,6 +901,7 @@ static fm_status ea_split_check(fm_problem* pr, const float* params, int32_t sav
 }
 
 fm_status fm_ea_forward(fm_problem* pr, const float* params, float* loss_dev, int32_t save, float* saved) {
+  fm::g_plain_once = true;
   if (!pr) return FM_ERR_INVALID_ARG;
   fm_status e = ea_split_check(pr, params, save, saved);
   if (e != FM_OK) return e;
@@ -923,6 +941,7 @@ fm_status fm_ea_forward(fm_problem* pr, const float* params, float* loss_dev, in
 
 fm_status fm_ea_backward(fm_problem* pr, const float* params, int32_t save, const float* saved,
                          const float* grad_loss, float* grad) {
+  fm::g_plain_once = true;
   if (!pr) return FM_ERR_INVALID_ARG;
   fm_status e = ea_split_check(pr, params, save, saved);
   if (e != FM_OK) return e;
@@ -979,7 +998,108 @@ fm_status fm_ea_backward(fm_problem* pr, const float* params, int32_t save, cons
   return FM_OK;
 }
 
+// ---- captured iterations
+// fm_step replays a CUDA graph of kGraphIters iterations (each one the
+// stage's launches of `evaluate` with Adam) instead of launching every kernel
+// from the host.  Captured arguments are device pointers and the Adam
+// constants; the graphs are keyed by stage, constants and an epoch that every
+// call able to change a captured pointer or branch bumps.  Capture runs on a
+// private stream (the legacy default stream cannot be captured); replays go
+// to the problem's stream.
+//
+// A replay is ordered by events on both sides: the kernels of this library
+// signal their successors early (programmatic dependent launch), and a graph
+// launched right behind such a kernel was seen to start before that kernel's
+// writes were done.  An event records the completion of everything before
+// it, so the graph runs on the private stream behind one event, and the
+// problem's stream waits for a second one.
+constexpr int kGraphIters = 16;
+
+static fm_status replay(fm_problem* pr, cudaGraphExec_t exec) {
+  if (!pr->graph_in) FM_CUDA(pr, cudaEventCreateWithFlags(&pr->graph_in, cudaEventDisableTiming));
+  if (!pr->graph_out) FM_CUDA(pr, cudaEventCreateWithFlags(&pr->graph_out, cudaEventDisableTiming));
+  FM_CUDA(pr, cudaEventRecord(pr->graph_in, pr->stream));
+  FM_CUDA(pr, cudaStreamWaitEvent(pr->cap_stream, pr->graph_in, 0));
+  FM_CUDA(pr, cudaGraphLaunch(exec, pr->cap_stream));
+  FM_CUDA(pr, cudaEventRecord(pr->graph_out, pr->cap_stream));
+  FM_CUDA(pr, cudaStreamWaitEvent(pr->stream, pr->graph_out, 0));
+  fm::g_plain_once = true;
+  return FM_OK;
+}
+
+static fm_status capture_graph(fm_problem* pr, fm_stage st, const fm_adam_opts* opts, float* params,
+                               fm::AdamState* adam, fm_problem::GraphEntry* out) {
+  if (!pr->cap_stream) FM_CUDA(pr, cudaStreamCreateWithFlags(&pr->cap_stream, cudaStreamNonBlocking));
+  int64_t before[fm::kKCount];
+  std::memcpy(before, pr->k_launches, sizeof(before));
+  cudaStream_t orig = pr->stream;
+  pr->stream = pr->cap_stream;
+  cudaError_t ce = cudaStreamBeginCapture(pr->cap_stream, cudaStreamCaptureModeThreadLocal);
+  fm_status e = FM_OK;
+  const bool was = fm::g_capturing;
+  fm::g_capturing = true;
+  if (ce == cudaSuccess)
+    for (int k = 0; k < kGraphIters && e == FM_OK; ++k) e = evaluate(pr, st, params, nullptr, opts, adam, nullptr);
+  fm::g_capturing = was;
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce2 = (ce == cudaSuccess) ? cudaStreamEndCapture(pr->cap_stream, &graph) : ce;
+  pr->stream = orig;
+  for (int k = 0; k < fm::kKCount; ++k) {
+    out->counts[k] = pr->k_launches[k] - before[k];
+    pr->k_launches[k] = before[k];
+  }
+  if (e != FM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return e;
+  }
+  if (ce != cudaSuccess || ce2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return fail(pr, FM_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
+  }
+  cudaError_t ci = cudaGraphInstantiate(&out->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ci != cudaSuccess) {
+    out->exec = nullptr;
+    return fail(pr, FM_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ci));
+  }
+  return FM_OK;
+}
+
+static fm_status graph_for(fm_problem* pr, fm_stage st, const fm_adam_opts* opts, float* params,
+                           fm::AdamState* adam, fm_problem::GraphEntry** g) {
+  for (auto& e : pr->graphs)
+    if (e.stage == (int)st && e.lr == opts->lr && e.b1 == opts->beta1 && e.b2 == opts->beta2 &&
+        e.eps == opts->eps && e.epoch == pr->graph_epoch && e.exec) {
+      e.last_use = ++pr->graph_clock;
+      *g = &e;
+      return FM_OK;
+    }
+  constexpr size_t kMaxGraphs = 16;
+  if (pr->graphs.size() >= kMaxGraphs) {   // evict the least recently used
+    size_t lru = 0;
+    for (size_t k = 1; k < pr->graphs.size(); ++k)
+      if (pr->graphs[k].last_use < pr->graphs[lru].last_use) lru = k;
+    if (pr->graphs[lru].exec) cudaGraphExecDestroy(pr->graphs[lru].exec);
+    pr->graphs.erase(pr->graphs.begin() + lru);
+  }
+  fm_problem::GraphEntry e;
+  e.stage = (int)st;
+  e.lr = opts->lr;
+  e.b1 = opts->beta1;
+  e.b2 = opts->beta2;
+  e.eps = opts->eps;
+  e.epoch = pr->graph_epoch;
+  fm_status r = capture_graph(pr, st, opts, params, adam, &e);
+  if (r != FM_OK) return r;
+  e.last_use = ++pr->graph_clock;
+  pr->graphs.push_back(e);
+  *g = &pr->graphs.back();
+  return FM_OK;
+}
+
 fm_status fm_step(fm_problem* pr, fm_stage st, const fm_adam_opts* opts, int32_t n_iters, float* loss) {
+  fm::g_plain_once = true;
   if (!pr) return FM_ERR_INVALID_ARG;
   if (!valid_stage(st)) return fail(pr, FM_ERR_INVALID_ARG, "unknown stage");
   if (!opts) return fail(pr, FM_ERR_INVALID_ARG, "opts is NULL");
@@ -990,8 +1110,24 @@ fm_status fm_step(fm_problem* pr, fm_stage st, const fm_adam_opts* opts, int32_t
   StageBuf b = stage_buf(pr, st);
   if (!*b.set) return fail(pr, FM_ERR_STATE, "the stage's parameters have not been set");
   const int runs = (st == FM_STAGE_TRANSLATION) ? pr->trn_runs : 1;
-  for (int it = 0; it < n_iters; ++it) {
+  // graphs need no per-iteration host decisions: no per-kernel timing, no
+  // loss trace; the first iteration runs directly (it settles the lazily
+  // built state: W of the compact form, the translation targets)
+  const bool graphs = pr->use_graphs && !pr->timing && pr->loss_every == 0;
+  for (int it = 0; it < n_iters;) {
     const bool last = (it == n_iters - 1);
+    const int left_for_graph = n_iters - it - (loss ? 1 : 0);
+    if (graphs && it > 0 && left_for_graph >= kGraphIters) {
+      fm_problem::GraphEntry* g = nullptr;
+      fm_status e = graph_for(pr, st, opts, b.params, b.adam, &g);
+      if (e != FM_OK) return e;
+      e = replay(pr, g->exec);
+      if (e != FM_OK) return e;
+      for (int k = 0; k < fm::kKCount; ++k) pr->k_launches[k] += g->counts[k];
+      pr->graph_replays += 1;
+      it += kGraphIters;
+      continue;
+    }
     float* trace = nullptr;
     if (pr->loss_every > 0) {
       if (pr->iter_count % pr->loss_every == 0) {
@@ -1003,6 +1139,7 @@ fm_status fm_step(fm_problem* pr, fm_stage st, const fm_adam_opts* opts, int32_t
     fm_status e = evaluate(pr, st, b.params, nullptr, opts, b.adam, (last && loss) ? pr->d_loss : nullptr,
                            trace);
     if (e != FM_OK) return e;
+    ++it;
   }
   if (st == FM_STAGE_ROTATION && n_iters > 0) pr->trn_target_valid = false;
   if (loss && n_iters > 0) {
@@ -1011,6 +1148,12 @@ fm_status fm_step(fm_problem* pr, fm_stage st, const fm_adam_opts* opts, int32_t
     FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
     std::memcpy(loss, pr->h_loss, sizeof(float) * nl);
   }
+  return FM_OK;
+}
+
+fm_status fm_graphs_enable(fm_problem* pr, int32_t enable) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  pr->use_graphs = enable != 0;
   return FM_OK;
 }
 
@@ -1040,7 +1183,43 @@ fm_status fm_rotation_init(fm_problem* pr, int32_t n_iters) {
     FM_CUDA(pr, cudaStreamSynchronize(s));   // the host vector is reused
     fm::launch_hash_fill(pr, x, 1, col == 0 ? 0x1234567u : 0x89ABCDEu, s);
     fm::launch_scale_to_unit(pr, x, s);
-    for (int it = 0; it < n_iters; ++it) {
+    int it = 0;
+    // blocks of 32 iterations (an even count: x and y swap back) followed by
+    // the rescaling, replayed from one captured graph
+    if (pr->use_graphs && !pr->timing && n_iters >= 64) {
+      if (!pr->cap_stream) FM_CUDA(pr, cudaStreamCreateWithFlags(&pr->cap_stream, cudaStreamNonBlocking));
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      FM_CUDA(pr, cudaStreamBeginCapture(pr->cap_stream, cudaStreamCaptureModeThreadLocal));
+      const bool was = fm::g_capturing;
+      fm::g_capturing = true;   // (these launches are plain ones anyway)
+      float* gx = x;
+      float* gy = y;
+      for (int k = 0; k < 32; ++k) {
+        fm::launch_mart_iter(pr, gx, col == 0 ? nullptr : c1, gy, pr->cap_stream);
+        std::swap(gx, gy);
+      }
+      fm::launch_scale_to_unit(pr, gx, pr->cap_stream);
+      fm::g_capturing = was;
+      cudaError_t ce = cudaStreamEndCapture(pr->cap_stream, &graph);
+      if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return fail(pr, FM_ERR_CUDA, std::string("rotation-init graph: ") + cudaGetErrorString(ce));
+      }
+      for (; it + 32 <= n_iters; it += 32) {
+        cudaError_t le = cudaGraphLaunch(exec, s);
+        if (le != cudaSuccess) {
+          cudaGraphExecDestroy(exec);
+          return fail(pr, FM_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(le));
+        }
+        pr->k_launches[fm::kKMartIter] += 32;
+      }
+      FM_CUDA(pr, cudaStreamSynchronize(s));
+      cudaGraphExecDestroy(exec);
+    }
+    for (; it < n_iters; ++it) {
       {
         Timed t(pr, fm::kKMartIter);
         fm::launch_mart_iter(pr, x, col == 0 ? nullptr : c1, y, s);

@@ -24,7 +24,7 @@ constexpr int kCamWarps = kCamThreads / 32;
 
 // fixed-order sum of the per-image-pair loss terms of one run (one CTA; four
 // independent accumulators per thread keep four loads in flight)
-__device__ void loss_sum_cta(const float* __restrict__ x, int n, float* out) {
+__device__ void loss_sum_cta(const float* x, int n, float* out) {
   __shared__ float part[kCamThreads];
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
   int k = threadIdx.x;
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kCamThreads) k_cam(CamUpdate u) {
       // 48-B parts of a cudaMalloc'd buffer: 16-B aligned
 #pragma unroll
       for (int q = 0; q < L::PART / 4; ++q) {
-        const float4 t = __ldg(reinterpret_cast<const float4*>(g) + q);
+        const float4 t = reinterpret_cast<const float4*>(g)[q];
         acc[4 * q] += t.x;
         acc[4 * q + 1] += t.y;
         acc[4 * q + 2] += t.z;
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kCamThreads) k_cam(CamUpdate u) {
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < L::PART; ++k) acc[k] += __ldg(g + k);
+      for (int k = 0; k < L::PART; ++k) acc[k] += g[k];
     }
   }
   __shared__ float red[kCamWarps][L::PART];
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kCamThreads) k_cam(CamUpdate u) {
     for (int k = 1; k < L::PDIM; ++k)
       if (lane == k) { gv = g[k]; pv = p[k]; }
     if (u.grad_out) u.grad_out[off + lane] = gv;
-    const float t = (float)(*u.step);
+    const float t = (float)*u.step;
     const float bc1 = 1.f - powf(u.b1, t);
     const float bc2 = 1.f - powf(u.b2, t);
     float m = u.m[off + lane], v = u.v[off + lane];

@@ -15,6 +15,18 @@ namespace fm {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// A kernel launched this way is resident while its predecessor still writes,
+// so nothing the predecessor (or an earlier kernel of the chain) produces may
+// be read through the non-coherent read-only path (__ldg, or const
+// __restrict__ pointers the compiler may turn into it): that path assumes the
+// data is constant for the kernel's lifetime, and its lines were seen stale.
+// Such data is read with ordinary loads after pdl_wait(), which makes the
+// predecessors' writes visible to them.  Inputs that no kernel writes may
+// still use __ldg.
+__device__ __forceinline__ void load_plain(const float* p, float* out, int n) {
+  for (int k = 0; k < n; ++k) out[k] = p[k];
+}
+
 __device__ __forceinline__ float dot3(const float* a, const float* b) {
   return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
 }

@@ -50,7 +50,7 @@ constexpr int WP = kEaWarpPairs;
 constexpr int WARPS = kEaWarpsPerCta;
 constexpr unsigned FULL = 0xffffffffu;
 
-__global__ void k_ea_tables(const float* __restrict__ params, const int* __restrict__ pi,
+__global__ void k_ea_tables(const float* params, const int* __restrict__ pi,
                             const int* __restrict__ pj, const int* __restrict__ seg_off, int P,
                             float4* __restrict__ tab, int* step_counter) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -62,10 +62,13 @@ __global__ void k_ea_tables(const float* __restrict__ params, const int* __restr
     cj = pj[n];
   }
   pdl_wait();               // params come from the previous step's update
-  if (step_counter && n == 0) *step_counter += 1;
+  if (step_counter && n == 0) atomicAdd(step_counter, 1);
   if (n >= P) return;
+  float qi[9], qj[9];
+  load_plain(params + 9 * ci, qi, 9);
+  load_plain(params + 9 * cj, qj, 9);
   PairGeo g;
-  pair_geometry(params + 9 * ci, params + 9 * cj, g);
+  pair_geometry(qi, qj, g);
   float E[9];
   essential(g, E);
   tab[3 * n + 0] = make_float4(E[0], E[1], E[2], E[3]);
@@ -109,8 +112,8 @@ __device__ __forceinline__ void entry_uniform(const float* Ereg, int endreg, con
     for (int k = 0; k < 9; ++k) o.E[k] = __shfl_sync(FULL, Ereg[k], t);
     o.end = __shfl_sync(FULL, endreg, t);
   } else {
-    const float4 e0 = __ldg(seg_tab + 3 * (s_first + t)), e1 = __ldg(seg_tab + 3 * (s_first + t) + 1),
-                 e2 = __ldg(seg_tab + 3 * (s_first + t) + 2);
+    const float4* e = seg_tab + 3 * (s_first + t);
+    const float4 e0 = e[0], e1 = e[1], e2 = e[2];
     o.E[0] = e0.x; o.E[1] = e0.y; o.E[2] = e0.z; o.E[3] = e0.w;
     o.E[4] = e1.x; o.E[5] = e1.y; o.E[6] = e1.z; o.E[7] = e1.w;
     o.E[8] = e2.x;
@@ -120,7 +123,7 @@ __device__ __forceinline__ void entry_uniform(const float* Ereg, int endreg, con
 
 __device__ __forceinline__ int end_uniform(int endreg, const float4* seg_tab, int s_first, int t) {
   if (t < 32) return __shfl_sync(FULL, endreg, t);
-  return __float_as_int(__ldg(seg_tab + 3 * (s_first + t) + 2).y);
+  return __float_as_int(seg_tab[3 * (s_first + t) + 2].y);
 }
 
 // c = w drho/dr and l = w rho of one pair.
@@ -247,7 +250,7 @@ __device__ __forceinline__ void load_table_head(const DirectArgs& a, int lane, R
   h.endreg = 0x7fffffff;
   if (lane < h.info.y) {
     const float4* e = a.seg_tab + 3 * (h.info.x + lane);
-    const float4 e0 = __ldg(e), e1 = __ldg(e + 1), e2 = __ldg(e + 2);
+    const float4 e0 = e[0], e1 = e[1], e2 = e[2];
     h.Ereg[0] = e0.x; h.Ereg[1] = e0.y; h.Ereg[2] = e0.z; h.Ereg[3] = e0.w;
     h.Ereg[4] = e1.x; h.Ereg[5] = e1.y; h.Ereg[6] = e1.z; h.Ereg[7] = e1.w;
     h.Ereg[8] = e2.x;
@@ -328,7 +331,7 @@ __device__ __forceinline__ void process_rows(const DirectArgs& a, int w, int lan
     for (int k = 0; k < 9; ++k) El[k] = __shfl_sync(FULL, h.Ereg[k], jl & 31);   // all lanes take part
     if (jl >= 32) {
       const float4* e = a.seg_tab + 3 * (info.x + jl);
-      const float4 e0 = __ldg(e), e1 = __ldg(e + 1), e2 = __ldg(e + 2);
+      const float4 e0 = e[0], e1 = e[1], e2 = e[2];
       El[0] = e0.x; El[1] = e0.y; El[2] = e0.z; El[3] = e0.w;
       El[4] = e1.x; El[5] = e1.y; El[6] = e1.z; El[7] = e1.w;
       El[8] = e2.x;
@@ -428,7 +431,7 @@ __device__ __forceinline__ void process_lanes(const DirectArgs& a, int w, int la
     // two or more image-pair ends inside the lane's run: one pair at a time
     int s = info.x + j0, sl = j0;
     const float4* e = a.seg_tab + 3 * s;
-    float4 e0 = __ldg(e), e1 = __ldg(e + 1), e2 = __ldg(e + 2);
+    float4 e0 = e[0], e1 = e[1], e2 = e[2];
     int end = __float_as_int(e2.y);
     for (int p = p0; p < pend; ++p) {
       while (p >= end) {
@@ -444,9 +447,9 @@ __device__ __forceinline__ void process_lanes(const DirectArgs& a, int w, int la
         ++s;
         ++sl;
         e = a.seg_tab + 3 * s;
-        e0 = __ldg(e);
-        e1 = __ldg(e + 1);
-        e2 = __ldg(e + 2);
+        e0 = e[0];
+        e1 = e[1];
+        e2 = e[2];
         end = __float_as_int(e2.y);
       }
       const float Es[9] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w, e2.x};
@@ -596,8 +599,11 @@ __global__ void k_ea_segments(SegArgs a) {
     const float gl = a.grad_loss[a.pair_scene ? a.pair_scene[n] : 0];
     for (int k = 0; k < 9; ++k) G[k] *= gl;
   }
+  float qi[9], qj[9];
+  load_plain(a.params + 9 * ci, qi, 9);
+  load_plain(a.params + 9 * cj, qj, 9);
   PairGeo g;
-  pair_geometry(a.params + 9 * ci, a.params + 9 * cj, g);
+  pair_geometry(qi, qj, g);
   float o[kSegGradEa];
   pair_backward(g, G, o);
   if ((reinterpret_cast<uintptr_t>(out) & 15u) == 0) {   // library buffers: 96-B rows, 16-B aligned

@@ -162,6 +162,23 @@ struct fm_problem {
   int64_t iter_count = 0;     // fm_step iterations while tracing
   float* loss_hist = nullptr; // [loss_cap * 64 * S]: one row of [m][S] losses per traced iteration
 
+  // captured iteration graphs of fm_step (see fm_api.cu)
+  struct GraphEntry {
+    int stage = 0;
+    float lr = 0.f, b1 = 0.f, b2 = 0.f, eps = 0.f;
+    uint64_t epoch = 0;
+    cudaGraphExec_t exec = nullptr;
+    int64_t counts[fm::kKCount] = {};   // kernel launches of one replay
+    uint64_t last_use = 0;
+  };
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_epoch = 1;      // bumped whenever captured launch arguments may change
+  uint64_t graph_clock = 0;
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t graph_in = nullptr, graph_out = nullptr;   // orders replays by completion
+  int64_t graph_replays = 0;
+
   // scratch
   float* scratch_params = nullptr;  // [max(m,1)*N*9] parameters of fm_loss_grad
   float* scratch_grad = nullptr;    // [max(m,1)*N*9]
@@ -172,7 +189,20 @@ struct fm_problem {
 
 namespace fm {
 
-// Launch with programmatic stream serialisation (see pdl_wait / pdl_trigger).
+// Set while this thread captures a graph.  Captured programmatic edges do not
+// order a kernel's reads after its predecessor's writes the way stream
+// launches do (measured: replays were not even repeatable), so launches made
+// during a capture are plain, fully ordered ones.
+extern thread_local bool g_capturing;
+// The next launch_pdl on this thread is a plain launch.  Every entry point of
+// the library sets it, so that its first kernel is ordered after whatever the
+// stream ran before (a caller's graph, copies, other libraries' kernels), and
+// fm_step sets it after each graph replay; launches that follow one of this
+// library's own kernels overlap with it.
+extern thread_local bool g_plain_once;
+
+// Launch with programmatic stream serialisation (see pdl_wait / pdl_trigger);
+// a plain launch while capturing.
 template <typename... KArgs, typename... Args>
 inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                        Args&&... args) {
@@ -185,7 +215,8 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = (g_capturing || g_plain_once) ? 0 : 1;
+  g_plain_once = false;
   cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 

@@ -121,6 +121,16 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
   v.n_wruns = n_wruns;
   cudaStream_t s = v.stream;
 
+  // inside a caller's stream capture the launches must be plain ones (see
+  // launch_pdl); the query is on the caller's own stream
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (s != nullptr && cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    cap = cudaStreamCaptureStatusNone;
+  }
+  const bool was = fm::g_capturing;
+  fm::g_capturing = was || cap == cudaStreamCaptureStatusActive;
+  fm::g_plain_once = true;
   fm::launch_ea_tables(params_dev, v.pair_i, v.pair_j, v.seg_off, P, v.seg_tab, nullptr, s);
   if (n_wruns > 0) {
     fm::launch_run_tables(v.seg_off, P, Z, n_wruns, v.run_seg, v.wrun_info, nullptr, s);
@@ -134,6 +144,7 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
   sa.l_scale = inv_z;
   fm::launch_ea_segments(sa, s);
   fm::launch_sum_fixed(v.seg_loss, P, 1, nullptr, 1, loss_dev, s);
+  fm::g_capturing = was;
   e = cudaGetLastError();
   if (e != cudaSuccess) return static_fail(FM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   return FM_OK;

@@ -137,6 +137,7 @@ _SIGNATURES = {
                                       ctypes.c_void_p, ctypes.c_void_p]),
     "fm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(fm_adam_opts), ctypes.c_int32,
                                ctypes.c_void_p]),
+    "fm_graphs_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fm_timing_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fm_timing_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fm_kernel_time), ctypes.c_int32,
                                       ctypes.POINTER(ctypes.c_int32)]),
@@ -519,6 +520,9 @@ class Problem:
         if nruns == 1:
             return vals
         return [vals[r * self.S:(r + 1) * self.S] for r in range(nruns)]
+
+    def graphs(self, enable=True):
+        _check(lib().fm_graphs_enable(self.handle, int(bool(enable))), self.handle)
 
     def timing(self, enable=True):
         fm_timing_enable(self.handle, enable)

@@ -371,16 +371,16 @@ def concat_scenes(scenes, name="batch") -> Scene:
 
 
 def batch_c4(seed: int = 0, n_scenes: int = 64, cams=(20, 500), points=(2_000, 150_000),
-             outliers=(0.05, 0.20)):
+             outliers=(0.05, 0.20), point_scale: float = 1.0):
     """Scenes of uneven size for batched solving: per scene (seed-indexed)
-    N ~ logU(cams), point count ~ logU(points), outlier fraction ~ U(outliers),
-    sigma = 1 px, the geometry of ``scene_c2`` (trajectory through a
-    50x50x10 box).  Returns the list of scenes."""
+    N ~ logU(cams), point count ~ logU(points) times point_scale, outlier
+    fraction ~ U(outliers), sigma = 1 px, the geometry of ``scene_c2``
+    (trajectory through a 50x50x10 box).  Returns the list of scenes."""
     rng = np.random.default_rng(10_000 + seed)
     out = []
     for k in range(n_scenes):
         n = int(round(np.exp(rng.uniform(np.log(cams[0]), np.log(cams[1])))))
-        m = int(round(np.exp(rng.uniform(np.log(points[0]), np.log(points[1])))))
+        m = int(round(point_scale * np.exp(rng.uniform(np.log(points[0]), np.log(points[1])))))
         of = float(rng.uniform(*outliers))
         sc = scene_c2(seed=1000 * (seed + 1) + k, n_cams=n, n_points=m, outlier_frac=of)
         sc.name = f"c4[{k}]"
