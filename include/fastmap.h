@@ -140,6 +140,8 @@ typedef struct {
   int64_t n_records;           /* per-(warp run, image pair) partial sums */
   int64_t device_bytes;        /* device memory held by the problem */
   int32_t n_scenes;            /* S */
+  int32_t n_cams_connected;    /* cameras in the largest connected component of
+                                  their scene's view graph */
 } fm_problem_info;
 
 /* Adam (the paper's cited adaptive first-order method, Sec. 1, Sec. 3.2; no
@@ -390,6 +392,11 @@ typedef struct {
   float loss_epipolar;
   int64_t n_kept;             /* out: keypoint pairs kept by the last filtering
                                  (all scenes) */
+  int32_t* cam_valid;         /* [N] or NULL: 1 for the cameras of the largest
+                                 connected component of their scene's view
+                                 graph (the connectivity filter, Appendix
+                                 "Global Rotation"), 0 for the others, whose
+                                 poses nothing constrains */
 } fm_result;
 
 /* Runs the whole first-order pipeline: fm_rotation_init, Adam on the rotation

@@ -264,6 +264,30 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
     inv_p[n] = 1.f / (float)(pr->h_sc_pair_off[q + 1] - pr->h_sc_pair_off[q]);
   }
 
+  // connectivity filter: the largest connected component of each scene's view
+  // graph (union-find; lowest camera index wins ties between components)
+  {
+    std::vector<int> parent(N);
+    for (int c = 0; c < N; ++c) parent[c] = c;
+    auto find = [&](int c) {
+      while (parent[c] != c) c = parent[c] = parent[parent[c]];
+      return c;
+    };
+    for (int n = 0; n < P; ++n) {
+      const int a = find(hi[n]), b = find(hj[n]);
+      if (a != b) parent[std::max(a, b)] = std::min(a, b);
+    }
+    std::vector<int> size(N, 0);
+    for (int c = 0; c < N; ++c) size[find(c)]++;
+    pr->h_cam_valid.assign(N, 0);
+    for (int q = 0; q < S; ++q) {
+      int best = -1;
+      for (int c = pr->h_sc_cam_off[q]; c < pr->h_sc_cam_off[q + 1]; ++c)
+        if (best < 0 || size[find(c)] > size[best]) best = find(c);
+      for (int c = pr->h_sc_cam_off[q]; c < pr->h_sc_cam_off[q + 1]; ++c) pr->h_cam_valid[c] = find(c) == best;
+    }
+  }
+
   // camera -> incident image pairs, ordered by image pair (deterministic sums)
   std::vector<int> coff(N + 1, 0), cseg(2 * (size_t)P);
   for (int n = 0; n < P; ++n) { coff[hi[n] + 1]++; coff[hj[n] + 1]++; }
@@ -684,6 +708,9 @@ fm_status fm_problem_info_get(const fm_problem* pr, fm_problem_info* out) {
   out->n_records = pr->n_rec;
   out->device_bytes = pr->device_bytes;
   out->n_scenes = pr->S;
+  int nv = 0;
+  for (int v : pr->h_cam_valid) nv += v;
+  out->n_cams_connected = nv;
   return FM_OK;
 }
 
@@ -1455,6 +1482,8 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
   FM_CUDA(pr, cudaMemcpyAsync(res->R, dR, sizeof(float) * 9 * pr->N, cudaMemcpyDeviceToHost, pr->stream));
   FM_CUDA(pr, cudaMemcpyAsync(res->t, dt, sizeof(float) * 3 * pr->N, cudaMemcpyDeviceToHost, pr->stream));
   FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+  if (res->cam_valid)
+    for (int c = 0; c < pr->N; ++c) res->cam_valid[c] = pr->h_cam_valid[c];
   res->n_tracks = 0;
   res->n_points_valid = 0;
   if (pr->track_idx && (res->points || res->point_valid)) {

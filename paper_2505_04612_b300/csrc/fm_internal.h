@@ -78,6 +78,7 @@ struct fm_problem {
   std::vector<int> h_sc_pair_off;  // [S+1]
   std::vector<int64_t> h_sc_kp_off;  // [S+1]
   std::vector<int> h_sc_max_degree;  // [S]
+  std::vector<int> h_cam_valid;      // [N] 1: in the largest connected component of its scene
   int* sc_cam_off = nullptr;     // [S+1]
   int* sc_pair_off = nullptr;    // [S+1]
   int64_t* sc_kp_off = nullptr;  // [S+1] keypoint-pair range of each scene

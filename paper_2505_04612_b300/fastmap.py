@@ -76,6 +76,7 @@ class fm_problem_info(ctypes.Structure):
         ("n_records", ctypes.c_int64),
         ("device_bytes", ctypes.c_int64),
         ("n_scenes", ctypes.c_int32),
+        ("n_cams_connected", ctypes.c_int32),
     ]
 
 
@@ -105,6 +106,7 @@ class fm_result(ctypes.Structure):
         ("point_valid", ctypes.c_void_p), ("n_tracks", ctypes.c_int32), ("n_points_valid", ctypes.c_int32),
         ("loss_rotation", ctypes.c_float), ("loss_translation", ctypes.c_float),
         ("loss_epipolar", ctypes.c_float), ("n_kept", ctypes.c_int64),
+        ("cam_valid", ctypes.c_void_p),
     ]
 
 
@@ -585,6 +587,8 @@ class Problem:
         res = fm_result()
         res.R = R.ctypes.data
         res.t = t.ctypes.data
+        cam_valid = np.empty(self.n_cams, np.int32)
+        res.cam_valid = cam_valid.ctypes.data
         pts = valid = None
         if n_tracks:
             pts = np.empty((n_tracks, 3), np.float32)
@@ -594,7 +598,8 @@ class Problem:
         _check(lib().fm_solve(self.handle, ctypes.byref(opts), ctypes.byref(res)), self.handle)
         self.runs = 1
         out = dict(R=R, t=t, loss_rotation=res.loss_rotation, loss_translation=res.loss_translation,
-                   loss_epipolar=res.loss_epipolar, n_kept=res.n_kept, n_points_valid=res.n_points_valid)
+                   loss_epipolar=res.loss_epipolar, n_kept=res.n_kept, n_points_valid=res.n_points_valid,
+                   cam_valid=cam_valid.astype(bool))
         if n_tracks:
             out.update(points=pts[:res.n_tracks], point_valid=valid[:res.n_tracks].astype(bool))
         return out

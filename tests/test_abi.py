@@ -49,11 +49,12 @@ def test_struct_layout_matches_c():
 #include <stddef.h>
 #include "fastmap.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(fm_problem_desc),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(fm_problem_desc),
          offsetof(fm_problem_desc, inputs_on_device), offsetof(fm_problem_desc, cuda_stream),
          sizeof(fm_problem_info), sizeof(fm_adam_opts), sizeof(fm_solve_opts), offsetof(fm_solve_opts, eps),
          sizeof(fm_result), offsetof(fm_result, n_kept), sizeof(fm_kernel_time),
-         offsetof(fm_problem_desc, scene_cam_off), offsetof(fm_problem_info, n_scenes));
+         offsetof(fm_problem_desc, scene_cam_off), offsetof(fm_problem_info, n_scenes),
+         offsetof(fm_result, cam_valid), offsetof(fm_problem_info, n_cams_connected));
   return 0;
 }
 """
@@ -67,7 +68,8 @@ int main(void) {
                     F.fm_problem_desc.cuda_stream.offset, ctypes.sizeof(F.fm_problem_info),
                     ctypes.sizeof(F.fm_adam_opts), ctypes.sizeof(F.fm_solve_opts), F.fm_solve_opts.eps.offset,
                     ctypes.sizeof(F.fm_result), F.fm_result.n_kept.offset, ctypes.sizeof(F.fm_kernel_time),
-                    F.fm_problem_desc.scene_cam_off.offset, F.fm_problem_info.n_scenes.offset]
+                    F.fm_problem_desc.scene_cam_off.offset, F.fm_problem_info.n_scenes.offset,
+                    F.fm_result.cam_valid.offset, F.fm_problem_info.n_cams_connected.offset]
 
 
 def test_errors_without_problem_are_reported(lib):

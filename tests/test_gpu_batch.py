@@ -178,7 +178,41 @@ def test_solve_batch_equals_solves_one_at_a_time():
         c0, c1 = b.scene_cam_off[k], b.scene_cam_off[k + 1]
         with G.make_problem(sc, rel_R=R[k]) as p1:
             o1 = p1.solve(n_tracks=int(sc.kp_track.max()) + 1, **opts)
+        np.testing.assert_array_equal(o1["cam_valid"], ob["cam_valid"][c0:c1])
         np.testing.assert_array_equal(o1["R"], ob["R"][c0:c1])
         np.testing.assert_array_equal(o1["t"], ob["t"][c0:c1])
         np.testing.assert_array_equal(o1["points"], ob["points"][toff[k]:toff[k + 1]])
         np.testing.assert_array_equal(o1["point_valid"], ob["point_valid"][toff[k]:toff[k + 1]])
+
+
+def test_connectivity_filter_marks_the_largest_component():
+    """A camera without image pairs and a two-camera island beside the main
+    view graph: only the main component's cameras are valid (per scene in a
+    batch)."""
+    from synthetic.scenes import Scene
+    sc = make_scene("c1", 0)
+    N = sc.n_cams
+    m = np.nonzero(sc.kp_img_pair == 0)[0]                 # reuse the first image pair's keypoints
+    extra = Scene(name="x", seed=0, width=sc.width, height=sc.height,
+                  focal=np.concatenate([sc.focal, sc.focal[:3]]), cx=np.concatenate([sc.cx, sc.cx[:3]]),
+                  cy=np.concatenate([sc.cy, sc.cy[:3]]), R_gt=np.concatenate([sc.R_gt, sc.R_gt[:3]]),
+                  t_gt=np.concatenate([sc.t_gt, sc.t_gt[:3]]), points=sc.points,
+                  pair_i=np.concatenate([sc.pair_i, [N]]).astype(np.int32),
+                  pair_j=np.concatenate([sc.pair_j, [N + 1]]).astype(np.int32),
+                  kp_img_pair=np.concatenate([sc.kp_img_pair, np.full(len(m), sc.n_pairs)]).astype(np.int32),
+                  kp1_px=np.concatenate([sc.kp1_px, sc.kp1_px[m]]), kp2_px=np.concatenate([sc.kp2_px, sc.kp2_px[m]]),
+                  kp_track=np.concatenate([sc.kp_track, sc.kp_track[m]]).astype(np.int32),
+                  kp_inlier=np.concatenate([sc.kp_inlier, sc.kp_inlier[m]]))
+    Rij, _ = gt_relative_poses(sc, rot_noise_deg=0.5, seed=1)
+    rel_R = np.concatenate([Rij, np.eye(3)[None]]).astype(np.float32)
+    want = np.r_[np.ones(N, bool), np.zeros(3, bool)]
+    opts = dict(rot_iters=100, trn_iters=100, trn_final_iters=50, ea_rounds=1, ea_iters=50)
+    with G.make_problem(extra, rel_R=rel_R) as pr:
+        assert pr.info().n_cams_connected == N
+        out = pr.solve(**opts)
+    np.testing.assert_array_equal(out["cam_valid"], want)
+    b = concat_scenes([extra, make_scene("c1", 2)])
+    with G.make_problem(b, rel_R=np.concatenate([rel_R, gt_relative_poses(make_scene("c1", 2))[0].astype(np.float32)])) as pr:
+        assert pr.info().n_cams_connected == N + 20
+        out = pr.solve(**opts)
+    np.testing.assert_array_equal(out["cam_valid"], np.r_[want, np.ones(20, bool)])
