@@ -410,6 +410,31 @@ typedef struct {
  * world frame.  Synchronises. */
 fm_status fm_solve(fm_problem* problem, const fm_solve_opts* opts, fm_result* result);
 
+/* Launch configuration of the direct epipolar kernel (k_ea_direct). */
+typedef struct {
+  int32_t pairs_per_lane;      /* keypoint pairs per thread: 11 or 15 (a warp
+                                  run is 32 x this many consecutive pairs) */
+  int32_t ctas_per_sm;         /* persistent CTAs per SM; 0 = as many as fit */
+  int32_t rows_max_img_pairs;  /* warp runs touching at most this many image
+                                  pairs are processed row by row (one
+                                  coalesced row of 32 pairs at a time), the
+                                  others lane by lane (>= 1) */
+  float us_per_eval;           /* fm_autotune: median time of the chosen one */
+} fm_tuning;
+
+/* Sets / reads the configuration (changing pairs_per_lane rebuilds the
+ * kernel's tables; synchronises).  Defaults: 15, 0, 2. */
+fm_status fm_set_tuning(fm_problem* problem, const fm_tuning* tuning);
+fm_status fm_get_tuning(const fm_problem* problem, fm_tuning* tuning);
+
+/* Autotuner: times the direct kernel (L1, the problem's current weights and
+ * epipolar parameters, or generated parameters when none are set) for both
+ * tiles, every CTA count per SM that fits and thresholds 1..4, `repeats`
+ * times each with L2 flushed before every launch, and keeps the fastest
+ * (median).  The choice changes no result beyond the order of additions
+ * inside an image pair's records.  Synchronises. */
+fm_status fm_autotune(fm_problem* problem, int32_t repeats, fm_tuning* best);
+
 /* fm_step replays captured CUDA graphs of 16 iterations (one graph launch
  * instead of every kernel launch of the 16 iterations) whenever per-kernel
  * timing and the loss trace are off; the results are identical either way.

@@ -1,4 +1,5 @@
 // Host runtime of the C ABI declared in include/fastmap.h.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -196,6 +197,56 @@ fm_status reset_adam(fm_problem* pr, fm::AdamState& a, size_t n) {
   FM_CUDA(pr, cudaMemsetAsync(a.m, 0, sizeof(float) * n, pr->stream));
   FM_CUDA(pr, cudaMemsetAsync(a.v, 0, sizeof(float) * n, pr->stream));
   FM_CUDA(pr, cudaMemsetAsync(a.t, 0, sizeof(int), pr->stream));
+  return FM_OK;
+}
+
+// Tables of the direct epipolar kernel for a tile of U keypoint pairs per
+// lane: warp runs of 32 U pairs, each lane's first image pair, per warp run
+// its image pairs and record base, per image pair its records.  Rebuilt when
+// the tile changes (fm_autotune, fm_set_tuning).
+fm_status build_direct_tables(fm_problem* pr, int U) {
+  cudaStream_t s = pr->stream;
+  const int P = pr->P;
+  const int64_t Z = pr->Z;
+  FM_CUDA(pr, cudaStreamSynchronize(s));
+  if (pr->run_seg) {   // tables of a previous tile
+    pr->device_bytes -= (int64_t)sizeof(int) * 32 * std::max(pr->n_wruns, 1) +
+                        (int64_t)sizeof(int4) * std::max(pr->n_wruns, 1) + (int64_t)sizeof(int) * 2 * P +
+                        (int64_t)sizeof(float4) * 3 * std::max<int64_t>(pr->n_rec, 1);
+  }
+  dfree(pr->run_seg);
+  dfree(pr->wrun_info);
+  dfree(pr->seg_rec);
+  dfree(pr->rec);
+  pr->ea_U = U;
+  pr->n_wruns = (int)((Z + 32 * (int64_t)U - 1) / (32 * (int64_t)U));
+  FM_ALLOC(pr, pr->run_seg, (size_t)pr->n_wruns * 32);
+  FM_ALLOC(pr, pr->wrun_info, pr->n_wruns);
+  FM_ALLOC(pr, pr->seg_rec, 2 * (size_t)P);
+  if (pr->n_wruns > 0) {
+    int64_t* d_total = nullptr;
+    FM_ALLOC(pr, d_total, 1);
+    {
+      Timed t(pr, fm::kKRunTables);
+      fm::launch_run_tables(pr->seg_off, P, Z, pr->n_wruns, U, pr->run_seg, pr->wrun_info, s);
+    }
+    FM_LAUNCHED(pr);
+    fm::launch_exclusive_scan_info(pr->wrun_info, pr->n_wruns, d_total, s);
+    FM_LAUNCHED(pr);
+    int64_t total = 0;
+    FM_CUDA(pr, cudaMemcpyAsync(&total, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    FM_CUDA(pr, cudaStreamSynchronize(s));
+    cudaFree(d_total);
+    pr->device_bytes -= (int64_t)sizeof(int64_t);
+    pr->n_rec = total;
+  } else {
+    pr->n_rec = 0;
+  }
+  FM_ALLOC(pr, pr->rec, 3 * (size_t)(pr->n_rec > 0 ? pr->n_rec : 1));
+  fm::launch_seg_records(pr->seg_off, pr->run_seg, pr->wrun_info, P, U, pr->seg_rec, s);
+  FM_LAUNCHED(pr);
+  FM_CUDA(pr, cudaStreamSynchronize(s));
+  pr->graph_epoch += 1;   // captured launches hold the table pointers
   return FM_OK;
 }
 
@@ -405,32 +456,10 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   }
 
   // ---- tables of the direct epipolar kernel
-  pr->n_wruns = (int)((Z + fm::kEaWarpPairs - 1) / fm::kEaWarpPairs);
-  FM_ALLOC(pr, pr->run_seg, (size_t)pr->n_wruns * 32);
-  FM_ALLOC(pr, pr->wrun_info, pr->n_wruns);
-  FM_ALLOC(pr, pr->seg_rec, 2 * (size_t)P);
-  if (pr->n_wruns > 0) {
-    int64_t* d_total = nullptr;
-    FM_ALLOC(pr, d_total, 1);
-    {
-      Timed t(pr, fm::kKRunTables);
-      fm::launch_run_tables(pr->seg_off, P, Z, pr->n_wruns, pr->run_seg, pr->wrun_info, nullptr, s);
-    }
-    FM_LAUNCHED(pr);
-    fm::launch_exclusive_scan_info(pr->wrun_info, pr->n_wruns, d_total, s);
-    FM_LAUNCHED(pr);
-    int64_t total = 0;
-    FM_CUDA(pr, cudaMemcpyAsync(&total, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    FM_CUDA(pr, cudaStreamSynchronize(s));
-    cudaFree(d_total);
-    pr->device_bytes -= (int64_t)sizeof(int64_t);
-    pr->n_rec = total;
-  } else {
-    pr->n_rec = 0;
+  {
+    fm_status st2 = build_direct_tables(pr, pr->ea_U);
+    if (st2 != FM_OK) return st2;
   }
-  FM_ALLOC(pr, pr->rec, 3 * (size_t)(pr->n_rec > 0 ? pr->n_rec : 1));
-  fm::launch_seg_records(pr->seg_off, pr->run_seg, pr->wrun_info, P, pr->seg_rec, s);
-  FM_LAUNCHED(pr);
 
   // ---- per-stage state
   FM_ALLOC(pr, pr->seg_tab, 3 * (size_t)P);
@@ -704,7 +733,7 @@ fm_status fm_problem_info_get(const fm_problem* pr, fm_problem_info* out) {
   out->n_img_pairs = pr->P;
   out->n_kp_pairs = pr->Z;
   out->n_empty_img_pairs = pr->n_empty;
-  out->pairs_per_lane = fm::kEaPairsPerLane;
+  out->pairs_per_lane = pr->ea_U;
   out->n_records = pr->n_rec;
   out->device_bytes = pr->device_bytes;
   out->n_scenes = pr->S;
@@ -1175,6 +1204,110 @@ fm_status fm_step(fm_problem* pr, fm_stage st, const fm_adam_opts* opts, int32_t
     FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
     std::memcpy(loss, pr->h_loss, sizeof(float) * nl);
   }
+  return FM_OK;
+}
+
+fm_status fm_get_tuning(const fm_problem* pr, fm_tuning* out) {
+  if (!pr || !out) return FM_ERR_INVALID_ARG;
+  out->pairs_per_lane = pr->ea_U;
+  out->ctas_per_sm = pr->ea_ctas_per_sm;
+  out->rows_max_img_pairs = pr->ea_rows_max;
+  out->us_per_eval = 0.f;
+  return FM_OK;
+}
+
+fm_status fm_set_tuning(fm_problem* pr, const fm_tuning* t) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!t) return fail(pr, FM_ERR_INVALID_ARG, "tuning is NULL");
+  if (t->pairs_per_lane != 11 && t->pairs_per_lane != 15)
+    return fail(pr, FM_ERR_INVALID_ARG, "pairs_per_lane must be 11 or 15 (the tiles built into the library)");
+  if (t->ctas_per_sm < 0 || t->rows_max_img_pairs < 1)
+    return fail(pr, FM_ERR_INVALID_ARG, "ctas_per_sm >= 0 and rows_max_img_pairs >= 1 required");
+  if (t->pairs_per_lane != pr->ea_U) {
+    fm_status e = build_direct_tables(pr, t->pairs_per_lane);
+    if (e != FM_OK) return e;
+  }
+  pr->ea_ctas_per_sm = t->ctas_per_sm;
+  pr->ea_rows_max = t->rows_max_img_pairs;
+  pr->graph_epoch += 1;
+  return FM_OK;
+}
+
+// Times k_ea_direct (L1, the problem's weights) for every tile built into
+// the library, every CTA count per SM and row/lane threshold 1..4, each launch
+// after a flush of L2, and keeps the fastest (median of `repeats`).
+fm_status fm_autotune(fm_problem* pr, int32_t repeats, fm_tuning* best_out) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (repeats < 1) return fail(pr, FM_ERR_INVALID_ARG, "repeats must be >= 1");
+  cudaStream_t s = pr->stream;
+  FM_CUDA(pr, cudaStreamSynchronize(s));
+  // table entries E_n: the epipolar parameters if set, else generated ones
+  const float* params = pr->ea_params;
+  if (!pr->ea_params_set) {
+    fm::launch_hash_fill(pr, pr->scratch_params, 3, 0x5EED5u, s);   // [N][9] values in [-1, 1)
+    params = pr->scratch_params;
+  }
+  {
+    fm::g_plain_once = true;
+    Timed t(pr, fm::kKEaTables);
+    fm::launch_ea_tables(params, pr->pair_i, pr->pair_j, pr->seg_off, pr->P, pr->seg_tab, nullptr, s);
+  }
+  FM_LAUNCHED(pr);
+  // an L2-sized flush between timed launches (skipped if it cannot be allocated)
+  void* flush = nullptr;
+  const size_t flush_bytes = (size_t)256 << 20;
+  if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    flush = nullptr;
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int old_u = pr->ea_U, old_c = pr->ea_ctas_per_sm, old_r = pr->ea_rows_max;
+  fm_tuning best{old_u, old_c, old_r, 3.4e38f};
+  fm_status st = FM_OK;
+  for (int U : {15, 11}) {
+    if (pr->Z == 0) break;
+    if (U != pr->ea_U && (st = build_direct_tables(pr, U)) != FM_OK) break;
+    const int max_c = fm::direct_max_ctas_per_sm(pr);
+    for (int c = 1; c <= max_c && st == FM_OK; ++c)
+      for (int r = 1; r <= 4 && st == FM_OK; ++r) {
+        pr->ea_ctas_per_sm = c;
+        pr->ea_rows_max = r;
+        std::vector<float> ms;
+        for (int k = 0; k < repeats; ++k) {
+          if (flush) cudaMemsetAsync(flush, k & 0xff, flush_bytes, s);
+          cudaEventRecord(a, s);
+          fm::g_plain_once = true;
+          fm::launch_ea_direct(pr, pr->ea_w, FM_EA_L1, s);
+          cudaEventRecord(b, s);
+          cudaError_t ce = cudaEventSynchronize(b);
+          float t = 0.f;
+          if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, a, b);
+          if (ce != cudaSuccess) {
+            st = fail(pr, FM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+            break;
+          }
+          ms.push_back(t);
+        }
+        if (st != FM_OK) break;
+        std::sort(ms.begin(), ms.end());
+        const float med = 1000.f * ms[ms.size() / 2];
+        if (med < best.us_per_eval) best = fm_tuning{U, c, r, med};
+        pr->k_launches[fm::kKEaDirect] += repeats;
+      }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (flush) cudaFree(flush);
+  if (st == FM_OK && pr->Z > 0) st = fm_set_tuning(pr, &best);
+  if (st != FM_OK) {   // leave the previous tile in place
+    if (pr->ea_U != old_u) build_direct_tables(pr, old_u);
+    pr->ea_ctas_per_sm = old_c;
+    pr->ea_rows_max = old_r;
+    return st;
+  }
+  if (best_out) *best_out = best;
   return FM_OK;
 }
 

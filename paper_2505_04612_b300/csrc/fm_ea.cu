@@ -39,14 +39,14 @@
 //              c = w drho/dr (4 B per pair) for a later kFromCoef pass;
 //   kFromCoef  dL/dE from stored coefficients: no residual is recomputed, but
 //              the pair's x~2 x~1^T still needs the keypoints (16 + 4 B).
+#include <algorithm>
+
 #include "fm_device.cuh"
 #include "fm_internal.h"
 
 namespace fm {
 namespace {
 
-constexpr int U = kEaPairsPerLane;
-constexpr int WP = kEaWarpPairs;
 constexpr int WARPS = kEaWarpsPerCta;
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -81,6 +81,7 @@ enum DirectMode { kFull = 0, kLossOnly = 1, kFromCoef = 2 };
 struct DirectArgs {
   const float4* kp;
   const float* wts;      // per-pair weights; the stored coefficients in kFromCoef
+  int rows_max;          // warp runs touching at most this many image pairs go row by row
   const int* run_seg;
   const int4* info;
   const float4* seg_tab;
@@ -90,7 +91,6 @@ struct DirectArgs {
   int n_wruns;
 };
 
-constexpr int ROWS = U;   // rows of 32 pairs per warp run
 
 __device__ __forceinline__ void store_record(float4* rec, int r, const float* v) {
   rec[3 * r + 0] = make_float4(v[0], v[1], v[2], v[3]);
@@ -204,8 +204,10 @@ __device__ __forceinline__ void cp_async16_partial(void* smem, const void* gmem,
 // shared memory per warp: two warp runs of keypoint pairs (double buffer),
 // row-major (row r, lane l at 32 r + l: conflict-free 512-B row reads), and
 // their weights
-constexpr size_t kSmemPerWarp = 2 * WP * sizeof(float4);
-constexpr size_t kSmemPerWarpW = kSmemPerWarp + 2 * WP * sizeof(float);
+template <int U>
+constexpr size_t smem_per_warp(bool weighted) {
+  return 2 * 32 * U * (sizeof(float4) + (weighted ? sizeof(float) : 0));
+}
 
 // state of a warp run prefetched before its rows are processed
 struct RunHead {
@@ -215,8 +217,9 @@ struct RunHead {
   int rs;          // image pair of this lane's first pair in the lane-contiguous split
 };
 
-template <bool WEIGHTED>
+template <int U, bool WEIGHTED>
 __device__ __forceinline__ void issue_rows(const DirectArgs& a, int w, int lane, float4* kb, float* wb) {
+  constexpr int WP = 32 * U, ROWS = U;
   const int base = w * WP;
   // slots past Z are zero-filled (src-size 0), so that no lane ever reads
   // stale shared memory
@@ -270,9 +273,10 @@ __device__ __forceinline__ void stash_coef(float4* kb, int i, float c) {
 
 // Row-major processing: right for warp runs that touch one or two image pairs
 // (at most one image-pair end to cross with a warp reduction).
-template <int LOSS, bool WEIGHTED, int MODE>
+template <int U, int LOSS, bool WEIGHTED, int MODE>
 __device__ __forceinline__ void process_rows(const DirectArgs& a, int w, int lane, const RunHead& h,
                                              float4* kb, const float* wb, bool store) {
+  constexpr int WP = 32 * U;
   const int base = w * WP;
   const int4 info = h.info;
   const int wend = min(base + WP, a.Z);    // one past the warp run's last pair
@@ -372,9 +376,10 @@ __device__ __forceinline__ void process_rows(const DirectArgs& a, int w, int lan
 // or more ends walks its pairs one by one and writes the image pairs that lie
 // wholly inside its run.  A segmented scan keyed by image pair then combines
 // the tails of consecutive lanes and absorbs heads, in fixed lane order.
-template <int LOSS, bool WEIGHTED, int MODE>
+template <int U, int LOSS, bool WEIGHTED, int MODE>
 __device__ __forceinline__ void process_lanes(const DirectArgs& a, int w, int lane, const RunHead& h,
                                               float4* kb, const float* wb, bool store) {
+  constexpr int WP = 32 * U;
   const int base = w * WP;
   const int4 info = h.info;
   const int wend = min(base + WP, a.Z);
@@ -489,12 +494,13 @@ __device__ __forceinline__ void process_lanes(const DirectArgs& a, int w, int la
   if (has_head && (lane == 0 || key_prev != head_key)) store_record(a.rec, info.z + head_key, acc_h);
 }
 
-template <int LOSS, bool WEIGHTED, int MODE>
+template <int U, int LOSS, bool WEIGHTED, int MODE>
 __device__ __forceinline__ void process(const DirectArgs& a, int w, int lane, const RunHead& h,
                                         float4* kb, const float* wb) {
+  constexpr int WP = 32 * U, ROWS = U;
   const bool store = (MODE == kLossOnly) && a.coef_out != nullptr;
-  if (h.info.y <= 2) process_rows<LOSS, WEIGHTED, MODE>(a, w, lane, h, kb, wb, store);
-  else process_lanes<LOSS, WEIGHTED, MODE>(a, w, lane, h, kb, wb, store);
+  if (h.info.y <= a.rows_max) process_rows<U, LOSS, WEIGHTED, MODE>(a, w, lane, h, kb, wb, store);
+  else process_lanes<U, LOSS, WEIGHTED, MODE>(a, w, lane, h, kb, wb, store);
   if (store) {
     // coalesced copy-out of the stashed coefficients
     __syncwarp();
@@ -507,8 +513,9 @@ __device__ __forceinline__ void process(const DirectArgs& a, int w, int lane, co
   }
 }
 
-template <int LOSS, bool WEIGHTED, int MODE>
+template <int U, int LOSS, bool WEIGHTED, int MODE>
 __global__ void __launch_bounds__(WARPS * 32, kEaMinCtas) k_ea_direct(DirectArgs a) {
+  constexpr int WP = 32 * U;
   extern __shared__ float4 smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -520,7 +527,7 @@ __global__ void __launch_bounds__(WARPS * 32, kEaMinCtas) k_ea_direct(DirectArgs
   pdl_trigger();
   RunHead head;
   load_static_head(a, w, lane, head);
-  issue_rows<WEIGHTED>(a, w, lane, kb, wb);   // the keypoints do not depend on the predecessor
+  issue_rows<U, WEIGHTED>(a, w, lane, kb, wb);   // the keypoints do not depend on the predecessor
   pdl_wait();
   load_table_head(a, lane, head);
   for (int it = 0; w < a.n_wruns; ++it, w += stride) {
@@ -530,13 +537,13 @@ __global__ void __launch_bounds__(WARPS * 32, kEaMinCtas) k_ea_direct(DirectArgs
     if (wn < a.n_wruns) {
       load_static_head(a, wn, lane, next);
       load_table_head(a, lane, next);
-      issue_rows<WEIGHTED>(a, wn, lane, kb + (cur ^ 1) * WP, WEIGHTED ? wb + (cur ^ 1) * WP : nullptr);
+      issue_rows<U, WEIGHTED>(a, wn, lane, kb + (cur ^ 1) * WP, WEIGHTED ? wb + (cur ^ 1) * WP : nullptr);
       asm volatile("cp.async.wait_group 1;\n" ::);
     } else {
       asm volatile("cp.async.wait_group 0;\n" ::);
     }
     __syncwarp();
-    process<LOSS, WEIGHTED, MODE>(a, w, lane, head, kb + cur * WP, WEIGHTED ? wb + cur * WP : nullptr);
+    process<U, LOSS, WEIGHTED, MODE>(a, w, lane, head, kb + cur * WP, WEIGHTED ? wb + cur * WP : nullptr);
     __syncwarp();   // this buffer is refilled two warp runs later
     head = next;
   }
@@ -623,11 +630,12 @@ void launch_ea_tables(const float* params, const int* pi, const int* pj, const i
              step_counter);
 }
 
-template <int LOSS, bool WEIGHTED, int MODE>
-static void launch_direct_t(const fm_problem* pr, const float* weights, float* coef_out, cudaStream_t s) {
+template <int U, int LOSS, bool WEIGHTED, int MODE>
+static void launch_direct_u(const fm_problem* pr, const float* weights, float* coef_out, cudaStream_t s) {
   DirectArgs a;
   a.kp = pr->kp;
   a.wts = weights;
+  a.rows_max = pr->ea_rows_max;
   a.run_seg = pr->run_seg;
   a.info = pr->wrun_info;
   a.seg_tab = pr->seg_tab;
@@ -635,17 +643,35 @@ static void launch_direct_t(const fm_problem* pr, const float* weights, float* c
   a.coef_out = coef_out;
   a.Z = (int)pr->Z;
   a.n_wruns = pr->n_wruns;
-  const size_t smem = WARPS * (WEIGHTED ? kSmemPerWarpW : kSmemPerWarp);
+  const size_t smem = WARPS * smem_per_warp<U>(WEIGHTED);
   static int per_sm = 0;   // resident CTAs per SM (one device per process)
   if (per_sm == 0) {
-    cudaFuncSetAttribute(k_ea_direct<LOSS, WEIGHTED, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ea_direct<LOSS, WEIGHTED, MODE>, WARPS * 32, smem);
+    cudaFuncSetAttribute(k_ea_direct<U, LOSS, WEIGHTED, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ea_direct<U, LOSS, WEIGHTED, MODE>, WARPS * 32, smem);
     if (per_sm < 1) per_sm = 1;
   }
+  const int want = pr->ea_ctas_per_sm > 0 ? std::min(pr->ea_ctas_per_sm, per_sm) : per_sm;
   int ctas = (pr->n_wruns + WARPS - 1) / WARPS;
-  int cap = per_sm * pr->sm_count;
+  int cap = want * pr->sm_count;
   if (ctas > cap) ctas = cap;
-  launch_pdl(k_ea_direct<LOSS, WEIGHTED, MODE>, dim3(ctas), dim3(WARPS * 32), smem, s, a);
+  launch_pdl(k_ea_direct<U, LOSS, WEIGHTED, MODE>, dim3(ctas), dim3(WARPS * 32), smem, s, a);
+}
+
+// the tile sizes the library is built with (pairs per lane, odd)
+template <int LOSS, bool WEIGHTED, int MODE>
+static void launch_direct_t(const fm_problem* pr, const float* weights, float* coef_out, cudaStream_t s) {
+  if (pr->ea_U == 11) launch_direct_u<11, LOSS, WEIGHTED, MODE>(pr, weights, coef_out, s);
+  else launch_direct_u<15, LOSS, WEIGHTED, MODE>(pr, weights, coef_out, s);
+}
+
+int direct_max_ctas_per_sm(const fm_problem* pr) {
+  const size_t smem = WARPS * (pr->ea_U == 11 ? smem_per_warp<11>(false) : smem_per_warp<15>(false));
+  int per_sm = 0;
+  if (pr->ea_U == 11)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ea_direct<11, 0, false, kFull>, WARPS * 32, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ea_direct<15, 0, false, kFull>, WARPS * 32, smem);
+  return per_sm > 0 ? per_sm : 1;
 }
 
 template <int MODE>

@@ -110,8 +110,11 @@ struct fm_problem {
   float* cx = nullptr;
   float* cy = nullptr;
 
-  // direct epipolar kernel tables
-  int n_wruns = 0;               // warp runs of kEaWarpPairs keypoint pairs
+  // direct epipolar kernel: tile (chosen by fm_autotune or fm_set_tuning) and tables
+  int ea_U = fm::kEaPairsPerLane;  // keypoint pairs per lane (11 or 15); a warp run is 32 U pairs
+  int ea_rows_max = 2;           // warp runs touching <= this many image pairs go row by row
+  int ea_ctas_per_sm = 0;        // persistent CTAs per SM (0: as many as fit)
+  int n_wruns = 0;               // warp runs of 32 ea_U keypoint pairs
   int* run_seg = nullptr;        // [n_wruns*32] image pair of each lane's first pair
   int4* wrun_info = nullptr;     // [n_wruns] {first image pair, #image pairs, record base, 0}
   int* seg_rec = nullptr;        // [2P] {first record, #records} per image pair
@@ -231,9 +234,9 @@ void launch_calibrate(const float* kp1, const float* kp2, const int* kp_pair, co
                       int64_t Z, int P, float4* out, int* err, cudaStream_t s);
 void launch_seg_offsets(const int* kp_pair, int64_t Z, int P, int* seg_off, int* err,
                         cudaStream_t s);
-void launch_run_tables(const int* seg_off, int P, int64_t Z, int n_wruns, int* run_seg,
-                       int4* wrun_info, int* counts_scratch, cudaStream_t s);
-void launch_seg_records(const int* seg_off, const int* run_seg, const int4* wrun_info, int P,
+void launch_run_tables(const int* seg_off, int P, int64_t Z, int n_wruns, int U, int* run_seg,
+                       int4* wrun_info, cudaStream_t s);
+void launch_seg_records(const int* seg_off, const int* run_seg, const int4* wrun_info, int P, int U,
                         int* seg_rec, cudaStream_t s);
 void launch_check_finite(const float* x, int64_t n, int* err, int bit, cudaStream_t s);
 void launch_exclusive_scan_info(int4* wrun_info, int n, int64_t* total_out_dev, cudaStream_t s);
@@ -247,6 +250,8 @@ void launch_ea_direct_loss(const fm_problem* pr, const float* weights, int loss,
                            cudaStream_t s);
 // dL/dE records from stored per-pair coefficients (no residual recompute)
 void launch_ea_direct_from_coef(const fm_problem* pr, const float* coef, cudaStream_t s);
+// CTAs of k_ea_direct that fit on one SM at the problem's tile
+int direct_max_ctas_per_sm(const fm_problem* pr);
 
 // per-image-pair pass after k_ea_direct
 struct SegArgs {

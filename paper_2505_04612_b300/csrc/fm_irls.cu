@@ -33,13 +33,11 @@
 namespace fm {
 namespace {
 
-constexpr int U = kEaPairsPerLane;
-
 // one thread per lane run of U consecutive keypoint pairs (the runs of the
 // direct kernel); the run's first image pair comes from run_seg
 __global__ void k_ea_reweight(const float4* __restrict__ kp, const int* __restrict__ run_seg,
                               const float4* __restrict__ seg_tab, const int* __restrict__ pair_scene,
-                              int Z, int n_runs, float tau, float delta, int irls, float* __restrict__ w,
+                              int Z, int n_runs, int U, float tau, float delta, int irls, float* __restrict__ w,
                               unsigned long long* __restrict__ kept) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   int my_kept = 0;
@@ -216,10 +214,11 @@ __global__ void k_ea_compact(const float* __restrict__ W, const float* __restric
 
 void launch_ea_reweight(const fm_problem* pr, float tau, float delta, int irls, float* w,
                         unsigned long long* kept, cudaStream_t s) {
+  const int U = pr->ea_U;   // lane runs of the direct kernel's tables
   const int n_runs = (int)((pr->Z + U - 1) / U);
   if (n_runs == 0) return;
   k_ea_reweight<<<(n_runs + 255) / 256, 256, 0, s>>>(pr->kp, pr->run_seg, pr->seg_tab, pr->pair_scene,
-                                                     (int)pr->Z, n_runs, tau, delta, irls, w, kept);
+                                                     (int)pr->Z, n_runs, U, tau, delta, irls, w, kept);
 }
 
 void launch_w_build(const fm_problem* pr, const float* w, float* W, cudaStream_t s) {

@@ -56,16 +56,16 @@ __device__ __forceinline__ int segment_of(const int* __restrict__ seg_off, int P
   return lo;
 }
 
-__global__ void k_run_tables(const int* __restrict__ seg_off, int P, int Z, int n_wruns,
+__global__ void k_run_tables(const int* __restrict__ seg_off, int P, int Z, int n_wruns, int U,
                              int* __restrict__ run_seg, int4* __restrict__ info) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n_wruns * 32) return;
-  int p0 = min(q * kEaPairsPerLane, Z - 1);
+  int p0 = min(q * U, Z - 1);
   int s = segment_of(seg_off, P, p0);
   run_seg[q] = s;
   if ((q & 31) == 0) {
     int w = q >> 5;
-    int last = min((w + 1) * kEaWarpPairs, Z) - 1;
+    int last = min((w + 1) * 32 * U, Z) - 1;
     int sl = segment_of(seg_off, P, last);
     info[w] = make_int4(s, sl - s + 1, 0, 0);
   }
@@ -98,7 +98,7 @@ __global__ void k_scan_info(int4* info, int n, long long* total) {
 }
 
 __global__ void k_seg_records(const int* __restrict__ seg_off, const int* __restrict__ run_seg,
-                              const int4* __restrict__ info, int P, int* __restrict__ seg_rec) {
+                              const int4* __restrict__ info, int P, int WP, int* __restrict__ seg_rec) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= P) return;
   int b = seg_off[n], e = seg_off[n + 1];
@@ -107,7 +107,7 @@ __global__ void k_seg_records(const int* __restrict__ seg_off, const int* __rest
     seg_rec[2 * n + 1] = 0;
     return;
   }
-  int w0 = b / kEaWarpPairs, w1 = (e - 1) / kEaWarpPairs;
+  int w0 = b / WP, w1 = (e - 1) / WP;
   int4 i0 = info[w0];
   seg_rec[2 * n] = i0.z + (n - i0.x);
   seg_rec[2 * n + 1] = w1 - w0 + 1;
@@ -145,20 +145,20 @@ void launch_seg_offsets(const int* kp_pair, int64_t Z, int P, int* seg_off, int*
   k_seg_offsets<<<grid_for(Z, 256), 256, 0, s>>>(kp_pair, Z, P, seg_off, err);
 }
 
-void launch_run_tables(const int* seg_off, int P, int64_t Z, int n_wruns, int* run_seg,
-                       int4* wrun_info, int*, cudaStream_t s) {
+void launch_run_tables(const int* seg_off, int P, int64_t Z, int n_wruns, int U, int* run_seg,
+                       int4* wrun_info, cudaStream_t s) {
   if (n_wruns == 0) return;
   int n = n_wruns * 32;
-  k_run_tables<<<(n + 255) / 256, 256, 0, s>>>(seg_off, P, (int)Z, n_wruns, run_seg, wrun_info);
+  k_run_tables<<<(n + 255) / 256, 256, 0, s>>>(seg_off, P, (int)Z, n_wruns, U, run_seg, wrun_info);
 }
 
 void launch_exclusive_scan_info(int4* wrun_info, int n, int64_t* total_out_dev, cudaStream_t s) {
   k_scan_info<<<1, 1024, 0, s>>>(wrun_info, n, (long long*)total_out_dev);
 }
 
-void launch_seg_records(const int* seg_off, const int* run_seg, const int4* wrun_info, int P,
+void launch_seg_records(const int* seg_off, const int* run_seg, const int4* wrun_info, int P, int U,
                         int* seg_rec, cudaStream_t s) {
-  k_seg_records<<<(P + 255) / 256, 256, 0, s>>>(seg_off, run_seg, wrun_info, P, seg_rec);
+  k_seg_records<<<(P + 255) / 256, 256, 0, s>>>(seg_off, run_seg, wrun_info, P, 32 * U, seg_rec);
 }
 
 void launch_check_finite(const float* x, int64_t n, int* err, int bit, cudaStream_t s) {

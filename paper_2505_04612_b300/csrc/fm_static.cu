@@ -133,10 +133,10 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
   fm::g_plain_once = true;
   fm::launch_ea_tables(params_dev, v.pair_i, v.pair_j, v.seg_off, P, v.seg_tab, nullptr, s);
   if (n_wruns > 0) {
-    fm::launch_run_tables(v.seg_off, P, Z, n_wruns, v.run_seg, v.wrun_info, nullptr, s);
+    fm::launch_run_tables(v.seg_off, P, Z, n_wruns, fm::kEaPairsPerLane, v.run_seg, v.wrun_info, s);
     fm::launch_exclusive_scan_info(v.wrun_info, n_wruns, reinterpret_cast<int64_t*>(total), s);
   }
-  fm::launch_seg_records(v.seg_off, v.run_seg, v.wrun_info, P, v.seg_rec, s);
+  fm::launch_seg_records(v.seg_off, v.run_seg, v.wrun_info, P, fm::kEaPairsPerLane, v.seg_rec, s);
   if (n_wruns > 0) fm::launch_ea_direct(&v, weights_dev, loss, s);
   fm::SegArgs sa = fm::seg_args(&v, params_dev);
   sa.pair_scale = nullptr;   // one scene: the scalar normaliser

@@ -110,6 +110,11 @@ class fm_result(ctypes.Structure):
     ]
 
 
+class fm_tuning(ctypes.Structure):
+    _fields_ = [("pairs_per_lane", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("rows_max_img_pairs", ctypes.c_int32), ("us_per_eval", ctypes.c_float)]
+
+
 class fm_adam_opts(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
@@ -139,6 +144,9 @@ _SIGNATURES = {
                                       ctypes.c_void_p, ctypes.c_void_p]),
     "fm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(fm_adam_opts), ctypes.c_int32,
                                ctypes.c_void_p]),
+    "fm_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fm_tuning)]),
+    "fm_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fm_tuning)]),
+    "fm_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(fm_tuning)]),
     "fm_graphs_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fm_timing_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fm_timing_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fm_kernel_time), ctypes.c_int32,
@@ -522,6 +530,23 @@ class Problem:
         if nruns == 1:
             return vals
         return [vals[r * self.S:(r + 1) * self.S] for r in range(nruns)]
+
+    def autotune(self, repeats=5):
+        """fm_autotune; returns the chosen fm_tuning as a dict."""
+        t = fm_tuning()
+        _check(lib().fm_autotune(self.handle, int(repeats), ctypes.byref(t)), self.handle)
+        return dict(pairs_per_lane=t.pairs_per_lane, ctas_per_sm=t.ctas_per_sm,
+                    rows_max_img_pairs=t.rows_max_img_pairs, us_per_eval=t.us_per_eval)
+
+    def set_tuning(self, pairs_per_lane=15, ctas_per_sm=0, rows_max_img_pairs=2):
+        t = fm_tuning(pairs_per_lane, ctas_per_sm, rows_max_img_pairs, 0.0)
+        _check(lib().fm_set_tuning(self.handle, ctypes.byref(t)), self.handle)
+
+    def get_tuning(self):
+        t = fm_tuning()
+        _check(lib().fm_get_tuning(self.handle, ctypes.byref(t)), self.handle)
+        return dict(pairs_per_lane=t.pairs_per_lane, ctas_per_sm=t.ctas_per_sm,
+                    rows_max_img_pairs=t.rows_max_img_pairs)
 
     def graphs(self, enable=True):
         _check(lib().fm_graphs_enable(self.handle, int(bool(enable))), self.handle)
