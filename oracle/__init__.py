@@ -32,4 +32,11 @@ Modules and what pins them (pins live in ``tests/test_oracle_*.py``):
   adam         Adam (Kingma & Ba), the paper's cited first-order optimiser
                                                -- pinned by a hand-computed
                two-step example.
+  mlp          learned per-pair inlier weights (the learned extension; the
+               paper has none): features, the 8-64-64-1 GELU network, its
+               binary cross-entropy and hand-derived gradient, bfloat16
+               emulation            -- pinned by torch's bfloat16 conversion
+               and float64 autograd, central finite differences, closed forms
+               with zero weights, a per-pair feature loop, invariances and the
+               generator's track lengths.
 """
