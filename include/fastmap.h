@@ -410,6 +410,78 @@ typedef struct {
  * world frame.  Synchronises. */
 fm_status fm_solve(fm_problem* problem, const fm_solve_opts* opts, fm_result* result);
 
+/* ------------------------------------------------- learned inlier weights
+ *
+ * The paper handles outlier keypoint pairs with IRLS weights and a periodic
+ * filter whose threshold decreases (Sec. 3.3, Eq. 9).  These calls add a
+ * learned filter: a network predicts, per keypoint pair, the probability that
+ * it is an inlier.  The paper has no learned component; the definitions
+ * below are this library's.
+ *
+ * Features of keypoint pair m of image pair n = (i, j) at epipolar-stage
+ * parameters (r_m = x~2^T E_n x~1, the residual of Eq. 7):
+ *   f0 |r_m| / (mean over the pairs of n of |r| + 1e-12)
+ *   f1 log1p(d_m), d_m the epipolar (Sampson) distance in pixels:
+ *      ((f_i + f_j)/2) |r_m| / sqrt(a0^2 + a1^2 + b0^2 + b1^2), a = E x~1,
+ *      b = E^T x~2
+ *   f2 log(k_m), k_m = (1 + sqrt(1 + 8 c_m))/2 the track length from the
+ *      number c_m of keypoint pairs of the track (0 without kp_track)
+ *   f3 the angle (radians) between the viewing rays R_i^T x~1, R_j^T x~2
+ *   f4 (|x~1[0:2]| + |x~2[0:2]|)/2, the keypoint radius (calibrated units)
+ *   f5 the iteration fraction (given)
+ *   f6 log(Z_n)
+ *   f7 log1p(w_m)/log1p(1/delta), w_m the current weight (1 without weights)
+ * Network: h1 = GELU(x W1 + b1) [64], h2 = GELU(h1 W2 + b2) [64],
+ * o = h2 . w3 + b3, p = sigmoid(o), GELU exact (erf).  Parameters, float32,
+ * flat: W1 [8][64] (feature-major), b1 [64], W2 [64][64] (input-major),
+ * b2 [64], w3 [64], b3 [1].  The products run on the tensor cores with
+ * bfloat16 operands (x, W1, h1, W2; in training also dz2 and dz1) and
+ * float32 accumulation. */
+#define FM_MLP_N_PARAMS 4801
+#define FM_MLP_N_FEATURES 8
+
+/* Sets the problem's network parameters (NULL clears them). */
+fm_status fm_mlp_set_params(fm_problem* problem, const float* theta, int32_t on_device);
+
+/* At epipolar-stage parameters params_dev [N*9] (NULL: the stage's own) and
+ * the problem's current weights: features into feat_dev [Z*8], the signed
+ * residuals r_m into resid_dev [Z], and the inlier probabilities p_m into
+ * prob_dev [Z] (needs the network parameters); any output may be NULL.
+ * Device pointers, in the order of the keypoint pairs given at creation.
+ * delta: the IRLS floor of f7 (> 0).  Asynchronous. */
+fm_status fm_mlp_eval(fm_problem* problem, const float* params_dev, float iter_frac, float delta,
+                      float* feat_dev, float* resid_dev, float* prob_dev);
+
+/* The learned counterpart of fm_ea_reweight: at the current epipolar-stage
+ * parameters, keeps a pair when its predicted inlier probability is >= p_min
+ * (instead of |eps^| < tau) and weights it 1/max(|eps^|, delta) when
+ * irls != 0, else 1; normalisers, W_n and *n_kept as fm_ea_reweight.
+ * Synchronises. */
+fm_status fm_mlp_reweight(fm_problem* problem, float iter_frac, float delta, float p_min, int32_t irls,
+                          int64_t* n_kept);
+
+/* Trainer: the network's parameters and Adam state on the device, trained
+ * on feature rows x [B][8] and labels y [B] in {0, 1} (device pointers) with
+ * the mean binary cross-entropy mean(softplus(o) - y o).  Errors are
+ * reported by fm_last_error(NULL).  Gradients are deterministic (fixed-order
+ * sums, no atomics). */
+typedef struct fm_mlp_trainer fm_mlp_trainer;
+fm_status fm_mlp_trainer_create(int64_t max_batch, void* cuda_stream, fm_mlp_trainer** out);
+void fm_mlp_trainer_destroy(fm_mlp_trainer* trainer);
+/* Sets the parameters (host or device) and resets Adam. */
+fm_status fm_mlp_trainer_set_params(fm_mlp_trainer* trainer, const float* theta, int32_t on_device);
+fm_status fm_mlp_trainer_get_params(fm_mlp_trainer* trainer, float* theta, int32_t on_device);
+/* Loss into loss_dev [1] and gradient into grad_dev [4801] (either may be
+ * NULL) at the current parameters.  Asynchronous. */
+fm_status fm_mlp_trainer_loss_grad(fm_mlp_trainer* trainer, const float* x_dev, const float* y_dev, int64_t B,
+                                   float* loss_dev, float* grad_dev);
+/* One Adam step on the batch; loss_dev [1] (or NULL) receives the loss before
+ * the step.  Asynchronous. */
+fm_status fm_mlp_trainer_step(fm_mlp_trainer* trainer, const float* x_dev, const float* y_dev, int64_t B,
+                              const fm_adam_opts* opts, float* loss_dev);
+/* Logits o of feature rows x [B][8] into logit_dev [B].  Asynchronous. */
+fm_status fm_mlp_trainer_forward(fm_mlp_trainer* trainer, const float* x_dev, int64_t B, float* logit_dev);
+
 /* Launch configuration of the direct epipolar kernel (k_ea_direct). */
 typedef struct {
   int32_t pairs_per_lane;      /* keypoint pairs per thread: 11 or 15 (a warp

@@ -20,7 +20,7 @@ const char* const kKernelNames[kKCount] = {
     "k_calibrate", "k_seg_offsets", "k_run_tables", "k_ea_tables", "k_ea_direct",
     "k_ea_segments", "k_rot_pairs", "k_trn_targets", "k_trn_pairs", "k_cam", "k_sum_fixed",
     "k_ea_reweight", "k_w_build", "k_ea_compact", "k_mart_iter", "k_reltrans", "k_merge",
-    "k_triangulate", "k_ea_direct_loss", "k_ea_direct_coef"};
+    "k_triangulate", "k_ea_direct_loss", "k_ea_direct_coef", "k_mlp_pair_tables", "k_mlp_infer"};
 }
 
 namespace {
@@ -169,6 +169,7 @@ void release(fm_problem* pr) {
   dfree(pr->d_kept);
   dfree(pr->kp_seg); dfree(pr->track_off); dfree(pr->track_idx);
   dfree(pr->merge_buf); dfree(pr->best_run);
+  dfree(pr->mlp_theta); dfree(pr->mlp_tab); dfree(pr->mlp_prob);
   dfree(pr->sc_cam_off); dfree(pr->sc_pair_off); dfree(pr->sc_kp_off); dfree(pr->cam_scene);
   dfree(pr->pair_scene); dfree(pr->pair_inv_p); dfree(pr->pair_inv_z); dfree(pr->mart_coef);
   for (auto& g : pr->graphs)
@@ -423,10 +424,12 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   }
   FM_LAUNCHED(pr);
   fm_status st = check_err_bits(pr);
-  if (st == FM_OK && d->kp_track && Z > 0) {
-    // triangulation needs the image pair of every keypoint pair and the tracks
+  if (st == FM_OK && Z > 0) {
+    // the image pair of every keypoint pair (triangulation, learned-weight features)
     FM_ALLOC(pr, pr->kp_seg, Z);
     FM_CUDA(pr, cudaMemcpyAsync(pr->kp_seg, kpp, sizeof(int) * Z, cudaMemcpyDeviceToDevice, s));
+  }
+  if (st == FM_OK && d->kp_track && Z > 0) {
     int T = 0;
     FM_CUDA(pr, fm::build_track_table(pr, &T));
     st = check_err_bits(pr);
@@ -1207,6 +1210,91 @@ fm_status fm_step(fm_problem* pr, fm_stage st, const fm_adam_opts* opts, int32_t
   return FM_OK;
 }
 
+// ---- learned per-pair weights
+
+fm_status fm_mlp_set_params(fm_problem* pr, const float* theta, int32_t on_device) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!theta) {
+    dfree(pr->mlp_theta);
+    return FM_OK;
+  }
+  if (!pr->mlp_theta) FM_ALLOC(pr, pr->mlp_theta, (size_t)fm::kMlpParams);
+  FM_CUDA(pr, cudaMemcpyAsync(pr->mlp_theta, theta, sizeof(float) * fm::kMlpParams,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, pr->stream));
+  fm::launch_check_finite(pr->mlp_theta, fm::kMlpParams, pr->d_err, fm::kErrParamNonFinite, pr->stream);
+  FM_LAUNCHED(pr);
+  return check_err_bits(pr);
+}
+
+static fm_status mlp_eval(fm_problem* pr, const float* params, float iter_frac, float delta, float* feat,
+                          float* resid, float* prob, const float* w) {
+  if (!params) {
+    if (!pr->ea_params_set) return fail(pr, FM_ERR_STATE, "the epipolar-stage parameters have not been set");
+    params = pr->ea_params;
+  }
+  if (prob && !pr->mlp_theta) return fail(pr, FM_ERR_STATE, "no network parameters (fm_mlp_set_params)");
+  if (!(delta > 0.f) || !std::isfinite(delta)) return fail(pr, FM_ERR_INVALID_ARG, "delta must be finite and > 0");
+  if (!(iter_frac >= 0.f && iter_frac <= 1.f)) return fail(pr, FM_ERR_INVALID_ARG, "iter_frac must lie in [0, 1]");
+  if (!pr->mlp_tab) FM_ALLOC(pr, pr->mlp_tab, (size_t)32 * pr->P);
+  cudaStream_t s = pr->stream;
+  {
+    Timed t(pr, fm::kKMlpTables);
+    fm::launch_mlp_pair_tables(pr, params, pr->mlp_tab, s);
+  }
+  FM_LAUNCHED(pr);
+  {
+    Timed t(pr, fm::kKMlpInfer);
+    fm::launch_mlp_infer(pr, pr->mlp_tab, prob ? pr->mlp_theta : nullptr, w, iter_frac, delta, prob, nullptr,
+                         feat, resid, s);
+  }
+  FM_LAUNCHED(pr);
+  return FM_OK;
+}
+
+fm_status fm_mlp_eval(fm_problem* pr, const float* params_dev, float iter_frac, float delta, float* feat_dev,
+                      float* resid_dev, float* prob_dev) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  fm::g_plain_once = true;
+  return mlp_eval(pr, params_dev, iter_frac, delta, feat_dev, resid_dev, prob_dev, pr->ea_w);
+}
+
+fm_status fm_mlp_reweight(fm_problem* pr, float iter_frac, float delta, float p_min, int32_t irls,
+                          int64_t* n_kept) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  fm::g_plain_once = true;
+  if (!(p_min >= 0.f && p_min <= 1.f)) return fail(pr, FM_ERR_INVALID_ARG, "p_min must lie in [0, 1]");
+  if (!pr->ea_params_set) return fail(pr, FM_ERR_STATE, "the epipolar-stage parameters have not been set");
+  cudaStream_t s = pr->stream;
+  pr->graph_epoch += 1;
+  if (!pr->mlp_prob) FM_ALLOC(pr, pr->mlp_prob, (size_t)pr->Z);
+  // probabilities from the features at the current poses and weights
+  fm_status e = mlp_eval(pr, pr->ea_params, iter_frac, delta, nullptr, nullptr, pr->mlp_prob, pr->ea_w);
+  if (e != FM_OK) return e;
+  if (!pr->ea_w) FM_ALLOC(pr, pr->ea_w, (size_t)pr->Z);
+  {
+    Timed t(pr, fm::kKEaTables);
+    fm::launch_ea_tables(pr->ea_params, pr->pair_i, pr->pair_j, pr->seg_off, pr->P, pr->seg_tab, nullptr, s);
+  }
+  FM_LAUNCHED(pr);
+  FM_CUDA(pr, cudaMemsetAsync(pr->d_kept, 0, sizeof(unsigned long long) * pr->S, s));
+  {
+    Timed t(pr, fm::kKEaReweight);
+    fm::launch_ea_reweight(pr, 0.f, delta, irls, pr->ea_w, pr->d_kept, s, pr->mlp_prob, p_min);
+  }
+  FM_LAUNCHED(pr);
+  {
+    Timed t(pr, fm::kKWBuild);
+    fm::launch_w_build(pr, pr->ea_w, pr->W, s);
+  }
+  FM_LAUNCHED(pr);
+  pr->W_valid = true;
+  int64_t total = 0;
+  e = normalisers_from_counts(pr, &total);
+  if (e != FM_OK) return e;
+  if (n_kept) *n_kept = total;
+  return FM_OK;
+}
+
 fm_status fm_get_tuning(const fm_problem* pr, fm_tuning* out) {
   if (!pr || !out) return FM_ERR_INVALID_ARG;
   out->pairs_per_lane = pr->ea_U;
@@ -1693,6 +1781,135 @@ fm_status fm_loss_history(fm_problem* pr, float* out, int32_t capacity, int32_t*
     out[k] = ring[(size_t)(idx % pr->loss_cap) * 64 * pr->S];   // scene 0 (run 0 of the translation stage)
   }
   *count = (int32_t)n;
+  return FM_OK;
+}
+
+
+// ---- network trainer (no problem needed)
+
+struct fm_mlp_trainer {
+  cudaStream_t stream = nullptr;
+  int64_t max_batch = 0;
+  int step = 0;
+  float* theta = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  float* grad = nullptr;
+  float* loss = nullptr;
+  float* partial = nullptr;
+};
+
+static fm_status trainer_fail(fm_status st, const std::string& msg) {
+  fm::set_thread_error(msg);
+  return st;
+}
+
+static void trainer_free(fm_mlp_trainer* t) {
+  if (!t) return;
+  for (float* p : {t->theta, t->m, t->v, t->grad, t->loss, t->partial})
+    if (p) cudaFree(p);
+}
+
+fm_status fm_mlp_trainer_create(int64_t max_batch, void* cuda_stream, fm_mlp_trainer** out) {
+  if (!out) return trainer_fail(FM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (max_batch < 1 || max_batch > (int64_t(1) << 31))
+    return trainer_fail(FM_ERR_INVALID_ARG, "max_batch must be in [1, 2^31]");
+  fm_mlp_trainer* t = new (std::nothrow) fm_mlp_trainer();
+  if (!t) return trainer_fail(FM_ERR_OOM, "host allocation failed");
+  t->stream = (cudaStream_t)cuda_stream;
+  t->max_batch = max_batch;
+  const size_t n = fm::kMlpParams;
+  const size_t parts = (size_t)fm::mlp_grad_parts(max_batch) * fm::mlp_part_stride();
+  cudaError_t e = cudaSuccess;
+  for (auto pp : {&t->theta, &t->m, &t->v, &t->grad})
+    if (e == cudaSuccess) e = cudaMalloc((void**)pp, sizeof(float) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&t->loss, sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&t->partial, sizeof(float) * parts);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->theta, 0, sizeof(float) * n, t->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->m, 0, sizeof(float) * n, t->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->v, 0, sizeof(float) * n, t->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(t->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    trainer_free(t);
+    delete t;
+    return trainer_fail(e == cudaErrorMemoryAllocation ? FM_ERR_OOM : FM_ERR_CUDA,
+                        std::string("trainer: ") + cudaGetErrorString(e));
+  }
+  *out = t;
+  return FM_OK;
+}
+
+void fm_mlp_trainer_destroy(fm_mlp_trainer* t) {
+  if (!t) return;
+  cudaStreamSynchronize(t->stream);
+  trainer_free(t);
+  delete t;
+}
+
+fm_status fm_mlp_trainer_set_params(fm_mlp_trainer* t, const float* theta, int32_t on_device) {
+  if (!t || !theta) return trainer_fail(FM_ERR_INVALID_ARG, "trainer and theta are required");
+  const size_t n = sizeof(float) * fm::kMlpParams;
+  cudaError_t e = cudaMemcpyAsync(t->theta, theta, n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  t->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->m, 0, n, t->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->v, 0, n, t->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(t->stream);
+  if (e != cudaSuccess) return trainer_fail(FM_ERR_CUDA, std::string("trainer: ") + cudaGetErrorString(e));
+  t->step = 0;
+  return FM_OK;
+}
+
+fm_status fm_mlp_trainer_get_params(fm_mlp_trainer* t, float* theta, int32_t on_device) {
+  if (!t || !theta) return trainer_fail(FM_ERR_INVALID_ARG, "trainer and theta are required");
+  cudaError_t e = cudaMemcpyAsync(theta, t->theta, sizeof(float) * fm::kMlpParams,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, t->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(t->stream);
+  if (e != cudaSuccess) return trainer_fail(FM_ERR_CUDA, std::string("trainer: ") + cudaGetErrorString(e));
+  return FM_OK;
+}
+
+static fm_status trainer_check_batch(fm_mlp_trainer* t, const float* x, int64_t B) {
+  if (!t) return trainer_fail(FM_ERR_INVALID_ARG, "trainer is NULL");
+  if (B < 0 || B > t->max_batch) return trainer_fail(FM_ERR_INVALID_ARG, "batch size outside [0, max_batch]");
+  if (B > 0 && !x) return trainer_fail(FM_ERR_INVALID_ARG, "x_dev is NULL");
+  return FM_OK;
+}
+
+fm_status fm_mlp_trainer_loss_grad(fm_mlp_trainer* t, const float* x, const float* y, int64_t B, float* loss_dev,
+                                   float* grad_dev) {
+  fm_status st = trainer_check_batch(t, x, B);
+  if (st != FM_OK) return st;
+  if (B > 0 && !y) return trainer_fail(FM_ERR_INVALID_ARG, "y_dev is NULL");
+  fm::launch_mlp_grad(t->theta, x, y, B, t->partial, grad_dev, loss_dev, t->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return trainer_fail(FM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return FM_OK;
+}
+
+fm_status fm_mlp_trainer_step(fm_mlp_trainer* t, const float* x, const float* y, int64_t B, const fm_adam_opts* o,
+                              float* loss_dev) {
+  fm_status st = trainer_check_batch(t, x, B);
+  if (st != FM_OK) return st;
+  if (B > 0 && !y) return trainer_fail(FM_ERR_INVALID_ARG, "y_dev is NULL");
+  if (!o || !(o->lr > 0.f && o->beta1 >= 0.f && o->beta1 < 1.f && o->beta2 >= 0.f && o->beta2 < 1.f && o->eps >= 0.f))
+    return trainer_fail(FM_ERR_INVALID_ARG, "invalid Adam options");
+  fm::launch_mlp_grad(t->theta, x, y, B, t->partial, t->grad, loss_dev ? loss_dev : t->loss, t->stream);
+  t->step += 1;
+  fm::launch_mlp_adam(t->theta, t->grad, t->m, t->v, t->step, o->lr, o->beta1, o->beta2, o->eps, t->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return trainer_fail(FM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return FM_OK;
+}
+
+fm_status fm_mlp_trainer_forward(fm_mlp_trainer* t, const float* x, int64_t B, float* logit_dev) {
+  fm_status st = trainer_check_batch(t, x, B);
+  if (st != FM_OK) return st;
+  if (B > 0 && !logit_dev) return trainer_fail(FM_ERR_INVALID_ARG, "logit_dev is NULL");
+  fm::launch_mlp_forward_x(t->theta, x, B, logit_dev, t->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return trainer_fail(FM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   return FM_OK;
 }
 

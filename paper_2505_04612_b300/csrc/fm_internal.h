@@ -29,6 +29,10 @@ constexpr int kEaWarpsPerCta = FM_EA_WARPS_PER_CTA;
 #define FM_EA_MIN_CTAS 8
 #endif
 constexpr int kEaMinCtas = FM_EA_MIN_CTAS;
+
+// learned per-pair inlier weights (fm_mlp.cu)
+constexpr int kMlpParams = 4801;   // W1 [8][64], b1, W2 [64][64], b2, w3, b3
+constexpr int kMlpFeatures = 8;
 static_assert(kEaPairsPerLane % 2 == 1, "lane-contiguous shared-memory reads need an odd stride");
 constexpr int kSegGradEa = 24;                   // dR_i, dt_i, dR_j, dt_j
 constexpr int kSegGradRot = 18;                  // dR_i, dR_j
@@ -45,7 +49,7 @@ enum : int {
 enum KernelId : int {
   kKCalibrate = 0, kKSegOffsets, kKRunTables, kKEaTables, kKEaDirect, kKEaSegments,
   kKRotPairs, kKTrnTargets, kKTrnPairs, kKCamUpdate, kKLossSum, kKEaReweight, kKWBuild,
-  kKEaCompact, kKMartIter, kKRelTrans, kKMerge, kKTriangulate, kKEaDirectLoss, kKEaDirectCoef, kKCount
+  kKEaCompact, kKMartIter, kKRelTrans, kKMerge, kKTriangulate, kKEaDirectLoss, kKEaDirectCoef, kKMlpTables, kKMlpInfer, kKCount
 };
 extern const char* const kKernelNames[kKCount];
 
@@ -153,6 +157,11 @@ struct fm_problem {
   float* trn_params = nullptr;   // [m*N*3]
   fm::AdamState trn_adam;
   bool trn_params_set = false;
+
+  // learned weights
+  float* mlp_theta = nullptr;    // [kMlpParams] network parameters, or null
+  float* mlp_tab = nullptr;      // [P][32] per-image-pair feature table
+  float* mlp_prob = nullptr;     // [Z] inlier probabilities of the last evaluation
 
   // observability
   bool timing = false;
@@ -277,14 +286,29 @@ void launch_ea_segments(const SegArgs& a, cudaStream_t s);
 void launch_ea_segments(const fm_problem* pr, const float* params, int loss, cudaStream_t s);
 
 // IRLS / compact form (fm_irls.cu)
+// prob (optional): keep a pair when prob >= p_min instead of |eps^| < tau
 void launch_ea_reweight(const fm_problem* pr, float tau, float delta, int irls, float* w,
-                        unsigned long long* kept, cudaStream_t s);
+                        unsigned long long* kept, cudaStream_t s, const float* prob = nullptr,
+                        float p_min = 0.5f);
 void launch_w_build(const fm_problem* pr, const float* w, float* W, cudaStream_t s);
 void launch_ea_compact(const fm_problem* pr, const float* params, int* step_counter, cudaStream_t s);
 // pair_inv_z from per-scene counts: 1/count[scene] (0 when the count is 0)
 void launch_pair_inv_from_counts(const fm_problem* pr, const unsigned long long* count, cudaStream_t s);
 // count[s] = number of keypoint pairs of scene s with a weight > 0
 void launch_count_positive(const fm_problem* pr, const float* w, unsigned long long* count, cudaStream_t s);
+
+// learned weights (fm_mlp.cu)
+size_t mlp_grad_smem();
+int mlp_grad_parts(int64_t B);
+int mlp_part_stride();
+void launch_mlp_pair_tables(const fm_problem* pr, const float* params, float* tab, cudaStream_t s);
+void launch_mlp_infer(const fm_problem* pr, const float* tab, const float* theta, const float* w, float iter_frac,
+                      float delta, float* prob, float* logit, float* feat, float* resid, cudaStream_t s);
+void launch_mlp_forward_x(const float* theta, const float* x, int64_t B, float* logit, cudaStream_t s);
+void launch_mlp_grad(const float* theta, const float* x, const float* y, int64_t B, float* partial, float* grad,
+                     float* loss, cudaStream_t s);
+void launch_mlp_adam(float* theta, const float* grad, float* m, float* v, int step, float lr, float b1, float b2,
+                     float eps, cudaStream_t s);
 
 // setup steps (fm_init.cu, fm_reltrans.cu, fm_points.cu)
 // y = x - (B x)/sigma_s per camera, with the constants of the camera's scene

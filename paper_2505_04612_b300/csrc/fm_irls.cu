@@ -38,7 +38,7 @@ namespace {
 __global__ void k_ea_reweight(const float4* __restrict__ kp, const int* __restrict__ run_seg,
                               const float4* __restrict__ seg_tab, const int* __restrict__ pair_scene,
                               int Z, int n_runs, int U, float tau, float delta, int irls, float* __restrict__ w,
-                              unsigned long long* __restrict__ kept) {
+                              unsigned long long* __restrict__ kept, const float* __restrict__ prob, float p_min) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   int my_kept = 0;
   int scene = -1;     // scene of the pairs counted in my_kept
@@ -67,7 +67,7 @@ __global__ void k_ea_reweight(const float4* __restrict__ kp, const int* __restri
       const float ey = fmaf(e0.w, x.x, fmaf(e1.x, x.y, e1.y));
       const float ez = fmaf(e1.z, x.x, fmaf(e1.w, x.y, e2.x));
       const float r = fabsf(fmaf(x.z, ex, fmaf(x.w, ey, ez)));
-      const bool keep = r < tau;
+      const bool keep = prob ? (prob[p] >= p_min) : (r < tau);
       float wt = 0.f;
       if (keep) wt = irls ? 1.f / fmaxf(r, delta) : 1.f;
       w[p] = wt;
@@ -213,12 +213,13 @@ __global__ void k_ea_compact(const float* __restrict__ W, const float* __restric
 }  // namespace
 
 void launch_ea_reweight(const fm_problem* pr, float tau, float delta, int irls, float* w,
-                        unsigned long long* kept, cudaStream_t s) {
+                        unsigned long long* kept, cudaStream_t s, const float* prob, float p_min) {
   const int U = pr->ea_U;   // lane runs of the direct kernel's tables
   const int n_runs = (int)((pr->Z + U - 1) / U);
   if (n_runs == 0) return;
   k_ea_reweight<<<(n_runs + 255) / 256, 256, 0, s>>>(pr->kp, pr->run_seg, pr->seg_tab, pr->pair_scene,
-                                                     (int)pr->Z, n_runs, U, tau, delta, irls, w, kept);
+                                                     (int)pr->Z, n_runs, U, tau, delta, irls, w, kept, prob,
+                                                     p_min);
 }
 
 void launch_w_build(const fm_problem* pr, const float* w, float* W, cudaStream_t s) {

@@ -144,6 +144,20 @@ _SIGNATURES = {
                                       ctypes.c_void_p, ctypes.c_void_p]),
     "fm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(fm_adam_opts), ctypes.c_int32,
                                ctypes.c_void_p]),
+    "fm_mlp_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "fm_mlp_eval": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "fm_mlp_reweight": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
+    "fm_mlp_trainer_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "fm_mlp_trainer_destroy": (None, [ctypes.c_void_p]),
+    "fm_mlp_trainer_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "fm_mlp_trainer_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "fm_mlp_trainer_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                ctypes.c_void_p, ctypes.c_void_p]),
+    "fm_mlp_trainer_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                           ctypes.POINTER(fm_adam_opts), ctypes.c_void_p]),
+    "fm_mlp_trainer_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "fm_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fm_tuning)]),
     "fm_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fm_tuning)]),
     "fm_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(fm_tuning)]),
@@ -383,6 +397,62 @@ def fm_ea_loss_grad_static(kp, seg_off, pair_i, pair_j, params, weights, n_cams,
     _check(st, None)
 
 
+def fm_mlp_set_params(handle, theta):
+    p, dev, keep = _ptr(None if theta is None else _as(theta, np.float32))
+    _check(lib().fm_mlp_set_params(handle, p, int(dev)), handle)
+
+
+class MlpTrainer:
+    """Owner of an fm_mlp_trainer (device parameters + Adam state)."""
+
+    def __init__(self, max_batch, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().fm_mlp_trainer_create(int(max_batch), _stream_handle(stream), ctypes.byref(h)), None)
+        self.handle = h.value
+        self.max_batch = int(max_batch)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fm_mlp_trainer_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        p, dev, keep = _ptr(_as(theta, np.float32))
+        _check(lib().fm_mlp_trainer_set_params(self.handle, p, int(dev)), None)
+
+    def get_params(self):
+        out = np.empty(4801, np.float32)
+        _check(lib().fm_mlp_trainer_get_params(self.handle, out.ctypes.data, 0), None)
+        return out
+
+    def loss_grad(self, x, y):
+        """x [B,8], y [B] CUDA float32 tensors -> (loss, grad [4801]) tensors."""
+        import torch
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        grad = torch.empty(4801, dtype=torch.float32, device=x.device)
+        _check(lib().fm_mlp_trainer_loss_grad(self.handle, x.data_ptr(), y.data_ptr(), int(y.numel()),
+                                              loss.data_ptr(), grad.data_ptr()), None)
+        return loss, grad
+
+    def step(self, x, y, lr, beta1=0.9, beta2=0.999, eps=1e-8, loss_out=None):
+        opts = fm_adam_opts(lr, beta1, beta2, eps)
+        _check(lib().fm_mlp_trainer_step(self.handle, x.data_ptr(), y.data_ptr(), int(y.numel()),
+                                         ctypes.byref(opts), None if loss_out is None else loss_out.data_ptr()),
+               None)
+
+    def forward(self, x):
+        import torch
+        out = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        _check(lib().fm_mlp_trainer_forward(self.handle, x.data_ptr(), int(x.shape[0]), out.data_ptr()), None)
+        return out
+
+
 def solve_opts(**overrides) -> fm_solve_opts:
     o = fm_solve_opts()
     lib().fm_solve_opts_default(ctypes.byref(o))
@@ -530,6 +600,29 @@ class Problem:
         if nruns == 1:
             return vals
         return [vals[r * self.S:(r + 1) * self.S] for r in range(nruns)]
+
+    def mlp_set_params(self, theta):
+        fm_mlp_set_params(self.handle, theta)
+
+    def mlp_eval(self, params=None, iter_frac=0.0, delta=1e-5, want_feat=True, want_resid=True, want_prob=False):
+        """fm_mlp_eval on the device; returns (feat [Z,8], resid [Z], prob [Z])
+        (None for outputs not asked for)."""
+        import torch
+        feat = torch.empty((self.n_kp, 8), dtype=torch.float32, device="cuda") if want_feat else None
+        resid = torch.empty(self.n_kp, dtype=torch.float32, device="cuda") if want_resid else None
+        prob = torch.empty(self.n_kp, dtype=torch.float32, device="cuda") if want_prob else None
+        pp = None if params is None else _ptr(_as(params, np.float32))[0]
+        _check(lib().fm_mlp_eval(self.handle, pp, ctypes.c_float(iter_frac), ctypes.c_float(delta),
+                                 None if feat is None else feat.data_ptr(),
+                                 None if resid is None else resid.data_ptr(),
+                                 None if prob is None else prob.data_ptr()), self.handle)
+        return feat, resid, prob
+
+    def mlp_reweight(self, iter_frac, delta=1e-5, p_min=0.5, irls=True):
+        kept = ctypes.c_int64()
+        _check(lib().fm_mlp_reweight(self.handle, ctypes.c_float(iter_frac), ctypes.c_float(delta),
+                                     ctypes.c_float(p_min), int(bool(irls)), ctypes.byref(kept)), self.handle)
+        return kept.value
 
     def autotune(self, repeats=5):
         """fm_autotune; returns the chosen fm_tuning as a dict."""
