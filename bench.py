@@ -54,7 +54,11 @@ def args_():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2_5m", help="c2_5m (default) or batch_c4")
+    ap.add_argument("--config", default="c2_5m", help="c2_5m (default), batch_c4 or learned_c5")
+    ap.add_argument("--train-scenes", type=int, default=200)
+    ap.add_argument("--eval-cams", type=int, default=3000)
+    ap.add_argument("--eval-points", type=int, default=1_000_000)
+    ap.add_argument("--eval-track", type=float, default=10.0)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autograd-modes", action="store_true",
@@ -390,6 +394,96 @@ def run_batch(a):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(a):
+    """Time to accuracy, learned filter against the plain one (one GPU).
+
+    Training: `--train-scenes` seeded scenes with the geometry of scene_c2
+    (N ~ U(60, 150) cameras, U(8k, 30k) points, 5-40% outliers, seeds from
+    1000), solved with the plain method in batches; features captured where
+    the learned solve evaluates the network, labels from the converged
+    residuals; the network trained with the library's trainer.
+    Evaluation: one scene with N = `--eval-cams` cameras, `--eval-points`
+    points, track length 2 + Geometric (mean `--eval-track`), 30% outliers,
+    relative rotations with 1 deg noise.  The plain fm_solve (5 filtering
+    rounds) and the learned one (2 pruning passes, 1 round) are timed end to
+    end (wall clock around the call, after a warm-up solve); accuracy is the
+    mean rotation error and the mean camera-centre error (relative to the
+    scene's size, after a similarity alignment) over the connected cameras.
+    value = plain time / learned time when the learned solve is at least as
+    accurate on both, else null."""
+    import torch
+    from paper_2505_04612_b300 import build as B
+    B.build()
+    from paper_2505_04612_b300 import fastmap as F
+    from paper_2505_04612_b300 import learned as Lm
+    from synthetic.scenes import concat_scenes, gt_relative_poses, scene_c2
+    from oracle.solve import centre_errors, rotation_errors_deg
+    t0 = time.time()
+    rng = np.random.default_rng(1000)
+    train = [scene_c2(seed=1000 + k, n_cams=int(rng.integers(60, 151)), n_points=int(rng.integers(8000, 30001)),
+                      outlier_frac=float(rng.uniform(0.05, 0.4))) for k in range(a.train_scenes)]
+    gen_train = time.time() - t0
+    t0 = time.time()
+    Xs, ys = [], []
+    for b in range(0, len(train), 25):
+        grp = train[b:b + 25]
+        R = np.concatenate([gt_relative_poses(s, rot_noise_deg=1.0, seed=b + k)[0] for k, s in enumerate(grp)])
+        with F.problem_from_scene(concat_scenes(grp), rel_R=R.astype(np.float32)) as pr:
+            X, y = Lm.training_rows(pr, keep_frac=0.1, seed=b)
+        Xs.append(X)
+        ys.append(y)
+    X, y = torch.cat(Xs), torch.cat(ys)
+    torch.cuda.synchronize()
+    data_s = time.time() - t0
+    t0 = time.time()
+    theta, losses = Lm.train(X, y, steps=3000)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    acc = float(((Lm.logits(theta, X) >= 0).float() == y).float().mean())
+    del X, y, Xs, ys
+    t0 = time.time()
+    ev = scene_c2(seed=5000 + a.seed, n_cams=a.eval_cams, n_points=a.eval_points, outlier_frac=0.3,
+                  track_mean=a.eval_track)
+    gen_eval = time.time() - t0
+    R = gt_relative_poses(ev, rot_noise_deg=1.0, seed=a.seed)[0].astype(np.float32)
+
+    def solve(learned, rounds):
+        with F.problem_from_scene(ev, rel_R=R) as pr:
+            if learned:
+                pr.mlp_set_params(theta)
+            pr.solve(learned=int(learned), ea_rounds=rounds)          # warm-up
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            out = pr.solve(learned=int(learned), ea_rounds=rounds)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+        ok = out["cam_valid"]
+        Rr = out["R"].astype(np.float64)
+        c = -np.einsum("nba,nb->na", Rr, out["t"].astype(np.float64))
+        scale = np.mean(np.linalg.norm(ev.centers_gt[ok] - ev.centers_gt[ok].mean(0), axis=1))
+        return {"wall_s": dt, "rotation_error_deg": float(rotation_errors_deg(Rr[ok], ev.R_gt[ok]).mean()),
+                "centre_error_rel": float(centre_errors(c[ok], ev.centers_gt[ok]).mean() / scale),
+                "ea_rounds": rounds}
+
+    plain = solve(False, 5)
+    learned = solve(True, 1)
+    ok = (learned["rotation_error_deg"] <= plain["rotation_error_deg"] and
+          learned["centre_error_rel"] <= plain["centre_error_rel"])
+    line = {
+        "metric": METRIC, "value": plain["wall_s"] / learned["wall_s"] if ok else None,
+        "unit": "x (plain fm_solve wall time / learned fm_solve wall time, learned at least as accurate)",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "f32 (network: bf16 tensor cores, f32 accumulate)",
+        "data": "synthetic",
+        "config": {"workload": f"learned_c5: eval scene {ev.n_cams} cameras, {ev.n_pairs} image pairs, "
+                               f"{ev.n_kp} keypoint pairs, 30% outliers; trained on {len(train)} scenes",
+                   "train_scenes": len(train), "train_rows": None},
+        "plain": plain, "learned": learned,
+        "training": {"rows_accuracy": acc, "bce_first_last": [losses[0], losses[-1]], "train_s": train_s,
+                     "data_s": data_s, "generation_s": gen_train + gen_eval},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def workload_config(sc, a):
     return {"workload": f"{a.config}: epipolar adjustment step (L1, Eq. 7, + Adam), {sc.n_cams} cameras, "
                         f"{sc.n_pairs} image pairs, {sc.n_kp} keypoint pairs, seed {a.seed}",
@@ -406,6 +500,8 @@ def main():
         return run_reference(a)
     if a.config == "batch_c4":
         return run_batch(a)
+    if a.config == "learned_c5":
+        return run_learned(a)
     import torch
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -310,7 +310,9 @@ fm_status fm_rotation_init(fm_problem* problem, int32_t n_iters);
  * over a Fibonacci lattice of 4096 points on the hemisphere refined by two
  * 1024-point lattices on spherical caps (radius twice the previous spacing),
  * sign by cheirality (+t on ties).  Replaces rel_t.  err_out: [P] mean error
- * of the chosen direction (host or device as flagged), or NULL. */
+ * of the chosen direction (host or device as flagged), or NULL.  When
+ * per-pair weights are set, pairs with weight 0 are left out of the score
+ * and the sign (unless an image pair has no other pair). */
 fm_status fm_relative_translations(fm_problem* problem, float* err_out, int32_t err_on_device);
 
 /* Copies the current relative rotations [P*9] / translations [P*3]; either
@@ -374,6 +376,18 @@ typedef struct {
   float tri_max_err_px;       /* (4) */
   float tri_min_angle_deg;    /* (2) */
   float beta1, beta2, eps;    /* Adam (0.9, 0.999, 1e-8) */
+  int32_t learned;            /* 1: the network prunes pairs after the first
+                                 grid search (fm_mlp_prune, iteration
+                                 fraction 0), the relative translations are
+                                 re-estimated from the kept pairs, and every
+                                 round filters with the network
+                                 (fm_mlp_reweight, fraction (k+1)/(rounds+1))
+                                 instead of the threshold tau_k; needs
+                                 fm_mlp_set_params (0) */
+  float learned_p_min;        /* inlier probability to keep a pair (0.5) */
+  int32_t learned_prune_passes; /* prune + re-estimate passes before the
+                                 translation stage (2): each pass sees the
+                                 relative translations of the previous one */
 } fm_solve_opts;
 
 void fm_solve_opts_default(fm_solve_opts* opts);
@@ -399,7 +413,8 @@ typedef struct {
                                  poses nothing constrains */
 } fm_result;
 
-/* Runs the whole first-order pipeline: fm_rotation_init, Adam on the rotation
+/* Runs the whole first-order pipeline (from unit weights: weights left by an
+ * earlier call are cleared): fm_rotation_init, Adam on the rotation
  * loss, fm_relative_translations (if asked), trn_runs translation runs from
  * fm_translation_random_init, fm_translation_merge, a final translation run,
  * fm_epipolar_init_from_stages, ea_rounds of {fm_ea_reweight(tau_k, delta),
@@ -451,6 +466,19 @@ fm_status fm_mlp_set_params(fm_problem* problem, const float* theta, int32_t on_
  * delta: the IRLS floor of f7 (> 0).  Asynchronous. */
 fm_status fm_mlp_eval(fm_problem* problem, const float* params_dev, float iter_frac, float delta,
                       float* feat_dev, float* resid_dev, float* prob_dev);
+
+/* The same at the rotation stage's global rotations and the current relative
+ * translations (E_n = [t^{i->j}]_x R_j R_i^T), before any camera centre is
+ * known. */
+fm_status fm_mlp_eval_relative(fm_problem* problem, float iter_frac, float delta, float* feat_dev,
+                               float* resid_dev, float* prob_dev);
+
+/* Early pruning: the pairs whose inlier probability at the global rotations
+ * and current relative translations is below p_min get weight 0, the others
+ * weight 1 (per-scene normalisers 1/kept); the relative translations can then
+ * be re-estimated from the kept pairs (fm_relative_translations).
+ * Synchronises. */
+fm_status fm_mlp_prune(fm_problem* problem, float iter_frac, float delta, float p_min, int64_t* n_kept);
 
 /* The learned counterpart of fm_ea_reweight: at the current epipolar-stage
  * parameters, keeps a pair when its predicted inlier probability is >= p_min

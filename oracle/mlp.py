@@ -150,10 +150,30 @@ def loss_grad(theta, x, y, quantise=False):
 def features(params, pair_i, pair_j, x1, x2, kp_img_pair, focal, iter_frac, kp_track=None,
              weights=None, delta=1e-5):
     """[Z, 8] features of every keypoint pair (definitions in the module
-    docstring).  x1, x2: [Z, 3] calibrated; params: [N, 9]."""
+    docstring) at epipolar-stage parameters [N, 9].  x1, x2: [Z, 3]
+    calibrated.  Returns (features, residuals)."""
     params = np.asarray(params, np.float64)
     geo = pair_geometry(params, pair_i, pair_j)
-    E = geo["E"][kp_img_pair]
+    return _features(geo["E"], geo["R"], pair_i, pair_j, x1, x2, kp_img_pair, focal, iter_frac, kp_track,
+                     weights, delta)
+
+
+def features_relative(params6, rel_t, pair_i, pair_j, x1, x2, kp_img_pair, focal, iter_frac, kp_track=None,
+                      weights=None, delta=1e-5):
+    """The same before any camera centre is known: E_n = [t^{i->j}]_x R_j R_i^T
+    from rotation-stage parameters [N, 6] and unit relative translations
+    [P, 3]."""
+    from .so3 import skew
+    R = rot_from_6d(np.asarray(params6, np.float64))
+    t = np.asarray(rel_t, np.float64)
+    t = t / np.linalg.norm(t, axis=1, keepdims=True)
+    Rij = R[pair_j] @ np.transpose(R[pair_i], (0, 2, 1))
+    E = skew(t) @ Rij
+    return _features(E, R, pair_i, pair_j, x1, x2, kp_img_pair, focal, iter_frac, kp_track, weights, delta)
+
+
+def _features(E_pairs, R, pair_i, pair_j, x1, x2, kp_img_pair, focal, iter_frac, kp_track, weights, delta):
+    E = E_pairs[kp_img_pair]
     a = np.einsum("mab,mb->ma", E, x1)
     b = np.einsum("mba,mb->ma", E, x2)
     r = np.einsum("ma,ma->m", x2, a)
@@ -169,7 +189,6 @@ def features(params, pair_i, pair_j, x1, x2, kp_img_pair, focal, iter_frac, kp_t
     if kp_track is not None:
         c = np.bincount(kp_track).astype(np.float64)[kp_track]
         f[:, 2] = np.log(0.5 * (1.0 + np.sqrt(1.0 + 8.0 * c)))
-    R = rot_from_6d(params[:, :6])
     d1 = np.einsum("mba,mb->ma", R[np.asarray(pair_i)[kp_img_pair]], x1)   # R_i^T x1
     d2 = np.einsum("mba,mb->ma", R[np.asarray(pair_j)[kp_img_pair]], x2)
     cosang = np.einsum("ma,ma->m", d1, d2) / (np.linalg.norm(d1, axis=1) * np.linalg.norm(d2, axis=1))

@@ -1226,9 +1226,14 @@ fm_status fm_mlp_set_params(fm_problem* pr, const float* theta, int32_t on_devic
   return check_err_bits(pr);
 }
 
+// relative: E from the rotation stage and rel_t (params ignored)
 static fm_status mlp_eval(fm_problem* pr, const float* params, float iter_frac, float delta, float* feat,
-                          float* resid, float* prob, const float* w) {
-  if (!params) {
+                          float* resid, float* prob, const float* w, bool relative = false) {
+  if (relative) {
+    if (!pr->rot_params_set) return fail(pr, FM_ERR_STATE, "the rotation-stage parameters have not been set");
+    if (!pr->rel_t_set) return fail(pr, FM_ERR_STATE, "no relative translations (rel_t)");
+    params = pr->rot_params;
+  } else if (!params) {
     if (!pr->ea_params_set) return fail(pr, FM_ERR_STATE, "the epipolar-stage parameters have not been set");
     params = pr->ea_params;
   }
@@ -1239,7 +1244,7 @@ static fm_status mlp_eval(fm_problem* pr, const float* params, float iter_frac, 
   cudaStream_t s = pr->stream;
   {
     Timed t(pr, fm::kKMlpTables);
-    fm::launch_mlp_pair_tables(pr, params, pr->mlp_tab, s);
+    fm::launch_mlp_pair_tables(pr, params, relative ? pr->rel_t : nullptr, pr->mlp_tab, s);
   }
   FM_LAUNCHED(pr);
   {
@@ -1256,6 +1261,36 @@ fm_status fm_mlp_eval(fm_problem* pr, const float* params_dev, float iter_frac, 
   if (!pr) return FM_ERR_INVALID_ARG;
   fm::g_plain_once = true;
   return mlp_eval(pr, params_dev, iter_frac, delta, feat_dev, resid_dev, prob_dev, pr->ea_w);
+}
+
+fm_status fm_mlp_eval_relative(fm_problem* pr, float iter_frac, float delta, float* feat_dev, float* resid_dev,
+                               float* prob_dev) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  fm::g_plain_once = true;
+  return mlp_eval(pr, nullptr, iter_frac, delta, feat_dev, resid_dev, prob_dev, pr->ea_w, true);
+}
+
+fm_status fm_mlp_prune(fm_problem* pr, float iter_frac, float delta, float p_min, int64_t* n_kept) {
+  if (!pr) return FM_ERR_INVALID_ARG;
+  fm::g_plain_once = true;
+  if (!(p_min >= 0.f && p_min <= 1.f)) return fail(pr, FM_ERR_INVALID_ARG, "p_min must lie in [0, 1]");
+  cudaStream_t s = pr->stream;
+  pr->graph_epoch += 1;
+  if (!pr->mlp_prob) FM_ALLOC(pr, pr->mlp_prob, (size_t)pr->Z);
+  fm_status e = mlp_eval(pr, nullptr, iter_frac, delta, nullptr, nullptr, pr->mlp_prob, pr->ea_w, true);
+  if (e != FM_OK) return e;
+  if (!pr->ea_w) FM_ALLOC(pr, pr->ea_w, (size_t)pr->Z);
+  fm::launch_mask_from_prob(pr->mlp_prob, pr->Z, p_min, pr->ea_w, s);
+  FM_LAUNCHED(pr);
+  pr->W_valid = false;
+  FM_CUDA(pr, cudaMemsetAsync(pr->d_kept, 0, sizeof(unsigned long long) * pr->S, s));
+  fm::launch_count_positive(pr, pr->ea_w, pr->d_kept, s);
+  FM_LAUNCHED(pr);
+  int64_t total = 0;
+  e = normalisers_from_counts(pr, &total);
+  if (e != FM_OK) return e;
+  if (n_kept) *n_kept = total;
+  return FM_OK;
 }
 
 fm_status fm_mlp_reweight(fm_problem* pr, float iter_frac, float delta, float p_min, int32_t irls,
@@ -1635,6 +1670,9 @@ void fm_solve_opts_default(fm_solve_opts* o) {
   o->beta1 = 0.9f;
   o->beta2 = 0.999f;
   o->eps = 1e-8f;
+  o->learned = 0;
+  o->learned_p_min = 0.5f;
+  o->learned_prune_passes = 2;
 }
 
 // Adam steps in four equal phases with the learning rate scaled by
@@ -1656,7 +1694,11 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
   if (!res->R || !res->t) return fail(pr, FM_ERR_INVALID_ARG, "result R and t buffers are required");
   if (o->trn_runs < 1 || o->trn_runs > 64 || o->ea_rounds < 0 || o->rot_init_iters < 1)
     return fail(pr, FM_ERR_INVALID_ARG, "invalid solve options");
+  if (o->learned && !pr->mlp_theta)
+    return fail(pr, FM_ERR_STATE, "learned filtering needs the network parameters (fm_mlp_set_params)");
   fm_status e;
+  // every solve starts from unit weights (a previous solve leaves its own)
+  if ((e = fm_ea_set_weights(pr, nullptr, 0, 0.f)) != FM_OK) return e;
   // per-scene losses; the result reports their sum
   std::vector<float> Lv(pr->S);
   auto total = [&]() {
@@ -1674,6 +1716,12 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
   } else if (!pr->rel_t_set) {
     return fail(pr, FM_ERR_STATE, "rel_t is needed when reestimate_rel_t is 0");
   }
+  if (o->learned) {   // early pruning, then the relative translations of the kept pairs
+    for (int pass = 0; pass < std::max(o->learned_prune_passes, 1); ++pass) {
+      if ((e = fm_mlp_prune(pr, 0.f, o->ea_delta, o->learned_p_min, nullptr)) != FM_OK) return e;
+      if (o->reestimate_rel_t && (e = fm_relative_translations(pr, nullptr, 0)) != FM_OK) return e;
+    }
+  }
   // 4. translation runs, merge, final run
   if ((e = fm_translation_set_runs(pr, o->trn_runs)) != FM_OK) return e;
   if ((e = fm_translation_random_init(pr, o->seed)) != FM_OK) return e;
@@ -1690,7 +1738,12 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
   for (int k = 0; k < o->ea_rounds; ++k) {
     const float tau = std::max(o->ea_tau0 * std::pow(0.5f, (float)k), o->ea_tau_min);
     int64_t kept = 0;
-    if ((e = fm_ea_reweight(pr, tau, o->ea_delta, 1, &kept)) != FM_OK) return e;
+    if (o->learned)
+      e = fm_mlp_reweight(pr, (float)(k + 1) / (float)(o->ea_rounds + 1), o->ea_delta, o->learned_p_min, 1,
+                          &kept);
+    else
+      e = fm_ea_reweight(pr, tau, o->ea_delta, 1, &kept);
+    if (e != FM_OK) return e;
     res->n_kept = kept;
     if ((e = stepped(pr, FM_STAGE_EPIPOLAR, o, o->ea_lr, o->ea_iters, Lv.data())) != FM_OK) return e;
     res->loss_epipolar = total();

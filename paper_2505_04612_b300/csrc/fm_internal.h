@@ -301,7 +301,9 @@ void launch_count_positive(const fm_problem* pr, const float* w, unsigned long l
 size_t mlp_grad_smem();
 int mlp_grad_parts(int64_t B);
 int mlp_part_stride();
-void launch_mlp_pair_tables(const fm_problem* pr, const float* params, float* tab, cudaStream_t s);
+void launch_mlp_pair_tables(const fm_problem* pr, const float* params, const float* rel_t, float* tab,
+                            cudaStream_t s);
+void launch_mask_from_prob(const float* prob, int64_t Z, float p_min, float* w, cudaStream_t s);
 void launch_mlp_infer(const fm_problem* pr, const float* tab, const float* theta, const float* w, float iter_frac,
                       float delta, float* prob, float* logit, float* feat, float* resid, cudaStream_t s);
 void launch_mlp_forward_x(const float* theta, const float* x, int64_t B, float* logit, cudaStream_t s);

@@ -152,8 +152,10 @@ __device__ __forceinline__ void mlp_forward(const MlpWeights& s, const uint32_t 
 // per image pair: E (9), R_i (9), R_j (9), mean |r|, log Z_n, fbar, 0
 constexpr int kTab = 32;
 
-__global__ void __launch_bounds__(128) k_mlp_pair_tables(const float* params, const int* __restrict__ pi,
-                                                         const int* __restrict__ pj,
+// params: epipolar-stage [N][9]; or, with rel_t, rotation-stage [N][6] and
+// E_n = [t^{i->j}]_x R_j R_i^T from the relative translation of the pair
+__global__ void __launch_bounds__(128) k_mlp_pair_tables(const float* params, const float* rel_t,
+                                                         const int* __restrict__ pi, const int* __restrict__ pj,
                                                          const int* __restrict__ seg_off,
                                                          const float4* __restrict__ kp,
                                                          const float* __restrict__ focal, int P,
@@ -162,13 +164,33 @@ __global__ void __launch_bounds__(128) k_mlp_pair_tables(const float* params, co
   const int n = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (n >= P) return;
   const int ci = pi[n], cj = pj[n];
-  float qi[9], qj[9];
-  load_plain(params + 9 * ci, qi, 9);
-  load_plain(params + 9 * cj, qj, 9);
   PairGeo g;
-  pair_geometry(qi, qj, g);
   float E[9];
-  essential(g, E);
+  if (rel_t) {
+    float qi[6], qj[6];
+    load_plain(params + 6 * ci, qi, 6);
+    load_plain(params + 6 * cj, qj, 6);
+    Rot6 si, sj;
+    rot6_forward(qi, si);
+    rot6_forward(qj, sj);
+    rot6_matrix(si, g.Ri);
+    rot6_matrix(sj, g.Rj);
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c)
+        g.Rij[r * 3 + c] = fmaf(g.Rj[r * 3 + 0], g.Ri[c * 3 + 0],
+                           fmaf(g.Rj[r * 3 + 1], g.Ri[c * 3 + 1], g.Rj[r * 3 + 2] * g.Ri[c * 3 + 2]));
+    float t[3];
+    load_plain(rel_t + 3 * n, t, 3);
+    const float inv = rsqrtf(fmaxf(dot3(t, t), 1e-30f));
+    for (int k = 0; k < 3; ++k) g.that[k] = t[k] * inv;
+    essential(g, E);
+  } else {
+    float qi[9], qj[9];
+    load_plain(params + 9 * ci, qi, 9);
+    load_plain(params + 9 * cj, qj, 9);
+    pair_geometry(qi, qj, g);
+    essential(g, E);
+  }
   const int b = seg_off[n], e = seg_off[n + 1];
   float s = 0.f;
   for (int m = b + lane; m < e; m += 32) {
@@ -303,6 +325,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_mlp_infer(InferArgs a) {
     }
     __syncwarp();
   }
+}
+
+// w = 1 for pairs with p >= p_min, else 0
+__global__ void k_mask_from_prob(const float* __restrict__ prob, int64_t Z, float p_min, float* __restrict__ w) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < Z) w[m] = prob[m] >= p_min ? 1.f : 0.f;
 }
 
 // the network on feature rows x [B][8] (inference on stored features)
@@ -601,9 +629,15 @@ size_t mlp_grad_smem() { return sizeof(GradSmem); }
 int mlp_grad_parts(int64_t B) { return grid_for_pairs(B, kChunk); }
 int mlp_part_stride() { return kPartStride; }
 
-void launch_mlp_pair_tables(const fm_problem* pr, const float* params, float* tab, cudaStream_t s) {
-  k_mlp_pair_tables<<<(pr->P + 3) / 4, 128, 0, s>>>(params, pr->pair_i, pr->pair_j, pr->seg_off, pr->kp, pr->focal,
-                                                   pr->P, tab);
+void launch_mlp_pair_tables(const fm_problem* pr, const float* params, const float* rel_t, float* tab,
+                            cudaStream_t s) {
+  k_mlp_pair_tables<<<(pr->P + 3) / 4, 128, 0, s>>>(params, rel_t, pr->pair_i, pr->pair_j, pr->seg_off, pr->kp,
+                                                   pr->focal, pr->P, tab);
+}
+
+void launch_mask_from_prob(const float* prob, int64_t Z, float p_min, float* w, cudaStream_t s) {
+  if (Z == 0) return;
+  k_mask_from_prob<<<(unsigned)((Z + 255) / 256), 256, 0, s>>>(prob, Z, p_min, w);
 }
 
 void launch_mlp_infer(const fm_problem* pr, const float* tab, const float* theta, const float* w, float iter_frac,

@@ -7,7 +7,8 @@
 // points on the hemisphere, then two Fibonacci lattices of 1024 points on
 // spherical caps of radius twice the previous spacing around the best point.
 // The error is even in t, so the sign is chosen by cheirality (more pairs
-// with both depths positive; +t on ties).
+// with both depths positive; +t on ties).  Keypoint pairs whose weight is 0
+// (filtered) are left out of both, unless the image pair has no other.
 //
 // One CTA per image pair.  The a_m of a tile of keypoint pairs are formed in
 // shared memory; each thread scores its own candidates over the tile.  An ALU
@@ -72,8 +73,8 @@ __device__ __forceinline__ Best better(Best a, Best b) {
 }
 
 template <int PER>
-__device__ Best score_level(const float4* __restrict__ kp, int b, int e, const float* Rij, int K, float H,
-                            const float* Q, float (*a_s)[kTile]) {
+__device__ Best score_level(const float4* __restrict__ kp, const float* __restrict__ w, int b, int e,
+                            const float* Rij, int K, float H, const float* Q, float (*a_s)[kTile]) {
   float t[PER][3];
   float acc[PER];
 #pragma unroll
@@ -89,10 +90,11 @@ __device__ Best score_level(const float4* __restrict__ kp, int b, int e, const f
       const float r0 = Rij[0] * x.x + Rij[1] * x.y + Rij[2];
       const float r1 = Rij[3] * x.x + Rij[4] * x.y + Rij[5];
       const float r2 = Rij[6] * x.x + Rij[7] * x.y + Rij[8];
-      // (R x1) x x2 with x2 = (x.z, x.w, 1)
-      a_s[0][m] = r1 * 1.f - r2 * x.w;
-      a_s[1][m] = r2 * x.z - r0 * 1.f;
-      a_s[2][m] = r0 * x.w - r1 * x.z;
+      // (R x1) x x2 with x2 = (x.z, x.w, 1); a left-out pair adds |t . 0| = 0
+      const float keep = (w == nullptr || w[base + m] > 0.f) ? 1.f : 0.f;
+      a_s[0][m] = keep * (r1 * 1.f - r2 * x.w);
+      a_s[1][m] = keep * (r2 * x.z - r0 * 1.f);
+      a_s[2][m] = keep * (r0 * x.w - r1 * x.z);
     }
     __syncthreads();
     for (int m = 0; m < n; ++m) {
@@ -141,14 +143,24 @@ __device__ __forceinline__ int positive_depths(const float4 x, const float* R, c
 
 __global__ void __launch_bounds__(kThreads) k_reltrans(const float4* __restrict__ kp, const int* __restrict__ seg_off,
                                                       const int* __restrict__ pi, const int* __restrict__ pj,
-                                                      const float* __restrict__ rot6, float* __restrict__ rel_t,
-                                                      float* __restrict__ err_out) {
+                                                      const float* __restrict__ rot6, const float* __restrict__ w_in,
+                                                      float* __restrict__ rel_t, float* __restrict__ err_out) {
   __shared__ float a_s[3][kTile];
   __shared__ Best red[kThreads / 32];
   __shared__ float Rij_s[9];
   __shared__ int cnt_s[2][kThreads / 32];
+  __shared__ int kept_s;
   const int n = blockIdx.x;
   const int b = seg_off[n], e = seg_off[n + 1];
+  // pairs that count: those with a positive weight, or all of them when the
+  // image pair has none (or no weights are set)
+  int kc = 0;
+  if (w_in)
+    for (int m = b + threadIdx.x; m < e; m += kThreads) kc += (w_in[m] > 0.f);
+  for (int d = 16; d > 0; d >>= 1) kc += __shfl_xor_sync(0xffffffffu, kc, d);
+  if (threadIdx.x == 0) kept_s = 0;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0 && kc) atomicAdd(&kept_s, kc);   // integer: order-free
   if (threadIdx.x == 0) {
     Rot6 si, sj;
     rot6_forward(rot6 + 6 * pi[n], si);
@@ -161,6 +173,9 @@ __global__ void __launch_bounds__(kThreads) k_reltrans(const float4* __restrict_
         Rij_s[3 * r + c] = Rj[3 * r] * Ri[3 * c] + Rj[3 * r + 1] * Ri[3 * c + 1] + Rj[3 * r + 2] * Ri[3 * c + 2];
   }
   __syncthreads();
+  const int kept = kept_s;
+  const float* w = (w_in && kept > 0) ? w_in : nullptr;
+  const int count = w ? kept : e - b;
   float Rij[9];
   for (int k = 0; k < 9; ++k) Rij[k] = Rij_s[k];
   if (e == b) {
@@ -170,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_reltrans(const float4* __restrict_
   }
   const float I3[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
   // level 0: hemisphere
-  Best bst = block_best(score_level<kK0 / kThreads>(kp, b, e, Rij, kK0, 1.f, I3, a_s), red);
+  Best bst = block_best(score_level<kK0 / kThreads>(kp, w, b, e, Rij, kK0, 1.f, I3, a_s), red);
   float t[3];
   lattice_point(bst.k, kK0, 1.f, I3, t);
   float best_e = bst.e;
@@ -181,7 +196,7 @@ __global__ void __launch_bounds__(kThreads) k_reltrans(const float4* __restrict_
     const float H = 2.f * sh * sh;   // 1 - cos(radius)
     float Q[9];
     rotation_to(t, Q);
-    Best c = block_best(score_level<kK1 / kThreads>(kp, b, e, Rij, kK1, H, Q, a_s), red);
+    Best c = block_best(score_level<kK1 / kThreads>(kp, w, b, e, Rij, kK1, H, Q, a_s), red);
     if (c.e < best_e) {
       best_e = c.e;
       lattice_point(c.k, kK1, H, Q, t);
@@ -192,6 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_reltrans(const float4* __restrict_
   int cp = 0, cm = 0;
   const float tm[3] = {-t[0], -t[1], -t[2]};
   for (int m = b + threadIdx.x; m < e; m += kThreads) {
+    if (w && !(w[m] > 0.f)) continue;
     const float4 x = kp[m];
     cp += positive_depths(x, Rij, t);
     cm += positive_depths(x, Rij, tm);
@@ -215,14 +231,15 @@ __global__ void __launch_bounds__(kThreads) k_reltrans(const float4* __restrict_
     const float sg = (M > P) ? -1.f : 1.f;
     const float nn = sqrtf(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
     for (int k = 0; k < 3; ++k) rel_t[3 * n + k] = sg * t[k] / nn;
-    if (err_out) err_out[n] = best_e / (float)(e - b);
+    if (err_out) err_out[n] = best_e / (float)count;
   }
 }
 
 }  // namespace
 
 void launch_reltrans(const fm_problem* pr, const float* rot6, float* rel_t, float* err_out, cudaStream_t s) {
-  k_reltrans<<<pr->P, kThreads, 0, s>>>(pr->kp, pr->seg_off, pr->pair_i, pr->pair_j, rot6, rel_t, err_out);
+  k_reltrans<<<pr->P, kThreads, 0, s>>>(pr->kp, pr->seg_off, pr->pair_i, pr->pair_j, rot6, pr->ea_w, rel_t,
+                                        err_out);
 }
 
 }  // namespace fm

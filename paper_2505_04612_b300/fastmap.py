@@ -97,6 +97,7 @@ class fm_solve_opts(ctypes.Structure):
         ("ea_tau0", ctypes.c_float), ("ea_tau_min", ctypes.c_float), ("ea_delta", ctypes.c_float),
         ("tri_max_err_px", ctypes.c_float), ("tri_min_angle_deg", ctypes.c_float),
         ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+        ("learned", ctypes.c_int32), ("learned_p_min", ctypes.c_float), ("learned_prune_passes", ctypes.c_int32),
     ]
 
 
@@ -147,6 +148,10 @@ _SIGNATURES = {
     "fm_mlp_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "fm_mlp_eval": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "fm_mlp_eval_relative": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p]),
+    "fm_mlp_prune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.POINTER(ctypes.c_int64)]),
     "fm_mlp_reweight": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
     "fm_mlp_trainer_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
@@ -617,6 +622,24 @@ class Problem:
                                  None if resid is None else resid.data_ptr(),
                                  None if prob is None else prob.data_ptr()), self.handle)
         return feat, resid, prob
+
+    def mlp_eval_relative(self, iter_frac=0.0, delta=1e-5, want_feat=True, want_resid=True, want_prob=False):
+        """fm_mlp_eval_relative (rotation stage + relative translations)."""
+        import torch
+        feat = torch.empty((self.n_kp, 8), dtype=torch.float32, device="cuda") if want_feat else None
+        resid = torch.empty(self.n_kp, dtype=torch.float32, device="cuda") if want_resid else None
+        prob = torch.empty(self.n_kp, dtype=torch.float32, device="cuda") if want_prob else None
+        _check(lib().fm_mlp_eval_relative(self.handle, ctypes.c_float(iter_frac), ctypes.c_float(delta),
+                                          None if feat is None else feat.data_ptr(),
+                                          None if resid is None else resid.data_ptr(),
+                                          None if prob is None else prob.data_ptr()), self.handle)
+        return feat, resid, prob
+
+    def mlp_prune(self, iter_frac=0.0, delta=1e-5, p_min=0.5):
+        kept = ctypes.c_int64()
+        _check(lib().fm_mlp_prune(self.handle, ctypes.c_float(iter_frac), ctypes.c_float(delta),
+                                  ctypes.c_float(p_min), ctypes.byref(kept)), self.handle)
+        return kept.value
 
     def mlp_reweight(self, iter_frac, delta=1e-5, p_min=0.5, irls=True):
         kept = ctypes.c_int64()

@@ -192,3 +192,35 @@ def test_errors():
         tr.loss_grad(_dev(x), _dev(y))
     assert e.value.status == F.FM_ERR_INVALID_ARG
     tr.close()
+
+
+def test_relative_features_and_early_pruning():
+    """Features from the global rotations and relative translations (before
+    any centre is known) against the oracle; pruning keeps exactly the pairs
+    whose probability reaches p_min, with weight 1."""
+    torch, F = _mods()
+    from tests._util import gt_params6
+    from synthetic.scenes import gt_relative_poses
+    sc = make_scene("c1", 6)
+    x1, x2 = G.oracle_xs(sc)
+    Rij, tij = gt_relative_poses(sc, rot_noise_deg=0.5, dir_noise_deg=2.0, seed=4)
+    p6 = (gt_params6(sc) + np.random.default_rng(1).normal(0, 0.01, (sc.n_cams, 6))).astype(np.float32)
+    th = _theta(41)
+    with G.make_problem(sc, rel_R=Rij.astype(np.float32), rel_t=tij.astype(np.float32)) as pr:
+        pr.set_params(F.FM_STAGE_ROTATION, p6.reshape(-1))
+        pr.mlp_set_params(th)
+        feat, resid, prob = pr.mlp_eval_relative(iter_frac=0.0, delta=1e-5, want_prob=True)
+        p_min = float(prob.median().item())    # about half the pairs on each side
+        kept = pr.mlp_prune(0.0, delta=1e-5, p_min=p_min)
+        w, inv_z = pr.get_weights()
+        feat, resid, prob, w = feat.cpu().numpy(), resid.cpu().numpy(), prob.cpu().numpy(), w.cpu().numpy()
+    fo, ro = M.features_relative(G.f32(p6), G.f32(tij), sc.pair_i, sc.pair_j, x1, x2, sc.kp_img_pair,
+                                 G.f32(sc.focal), 0.0, kp_track=sc.kp_track, delta=1e-5)
+    np.testing.assert_allclose(resid, ro, rtol=1e-4, atol=2e-7)
+    np.testing.assert_allclose(feat[:, 0], fo[:, 0], rtol=1e-3, atol=2e-4)
+    np.testing.assert_allclose(feat[:, 1], fo[:, 1], rtol=1e-3, atol=1e-4)
+    np.testing.assert_allclose(feat[:, 2:], fo[:, 2:], rtol=1e-5, atol=2e-6)
+    keep = prob >= p_min
+    assert 0 < kept == int(keep.sum()) < len(keep)
+    np.testing.assert_array_equal(w, keep.astype(np.float32))
+    assert abs(inv_z - 1.0 / kept) < 1e-9

@@ -150,3 +150,33 @@ def test_solve_matches_oracle_accuracy():
     e_g = S.rotation_errors_deg(out["R"].astype(np.float64), sc.R_gt).mean()
     e_o = S.rotation_errors_deg(o["R"], sc.R_gt).mean()
     assert abs(e_g - e_o) < 0.05, (e_g, e_o)
+
+
+def test_relative_translations_leave_out_zero_weight_pairs():
+    """With per-pair weights set, the grid search scores and signs each image
+    pair on its pairs of positive weight only (all of them when none has one):
+    every choice attains the oracle's minimum over the kept pairs."""
+    from paper_2505_04612_b300 import fastmap as F
+    sc = scene("c1", 2)
+    x1, x2 = G.oracle_xs(sc)
+    p6 = gt_params6(sc).astype(np.float32)
+    R = _rot6_to_R(p6)
+    rng = np.random.default_rng(3)
+    w = (rng.random(sc.n_kp) < 0.6).astype(np.float32)
+    off = sc.seg_off()
+    w[off[5]:off[6]] = 0.0                     # an image pair with nothing kept: all its pairs count
+    with G.make_problem(sc) as pr:
+        pr.set_params(F.FM_STAGE_ROTATION, p6.reshape(-1))
+        pr.set_ea_weights(w)
+        err_g = pr.relative_translations()
+        _, t_g = pr.get_rel_poses(want_R=False)
+    for n in range(sc.n_pairs):
+        idx = np.arange(off[n], off[n + 1])
+        kept = idx[w[idx] > 0] if np.any(w[idx] > 0) else idx
+        Rij = R[sc.pair_j[n]] @ R[sc.pair_i[n]].T
+        t_o, e_o = rp.relative_translation(Rij, x1[kept], x2[kept])
+        tg = G.f32(t_g[n])
+        e_g = rp.mean_epipolar_error(tg[None], Rij, x1[kept], x2[kept])[0]
+        assert e_g <= e_o * (1 + 1e-3) + 1e-7, (n, e_g, e_o)
+        assert abs(err_g[n] - e_g) <= 1e-4 * e_g + 1e-7
+        assert rp.cheirality_count(Rij, tg, x1[kept], x2[kept]) >= rp.cheirality_count(Rij, -tg, x1[kept], x2[kept])

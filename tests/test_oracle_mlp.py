@@ -148,3 +148,18 @@ def test_feature_invariances_and_known_values():
     p2 = similarity_transform_ea(p, Q, rng.normal(size=3), 2.5)
     f1, _ = M.features(p2, sc2.pair_i, sc2.pair_j, x1, x2, sc2.kp_img_pair, sc2.focal, 0.5)
     np.testing.assert_allclose(f1[:, [0, 1, 3]], f0[:, [0, 1, 3]], rtol=1e-7, atol=1e-9)
+
+
+def test_relative_features_equal_the_camera_features_when_consistent():
+    """With the relative translations of the epipolar-stage parameters
+    themselves, E_n is the same either way, and so are the features."""
+    from oracle.epipolar import pair_geometry
+    sc = make_scene("c1", 5)
+    x1, x2 = G.oracle_xs(sc)
+    p = perturbed_params_ea(sc, 3)
+    geo = pair_geometry(p, sc.pair_i, sc.pair_j)
+    f_a, r_a = M.features(p, sc.pair_i, sc.pair_j, x1, x2, sc.kp_img_pair, sc.focal, 0.0, kp_track=sc.kp_track)
+    f_b, r_b = M.features_relative(p[:, :6], 3.0 * geo["that"], sc.pair_i, sc.pair_j, x1, x2, sc.kp_img_pair,
+                                   sc.focal, 0.0, kp_track=sc.kp_track)
+    np.testing.assert_allclose(r_b, r_a, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(f_b, f_a, rtol=1e-10, atol=1e-12)
