@@ -59,6 +59,7 @@ def args_():
     ap.add_argument("--eval-cams", type=int, default=3000)
     ap.add_argument("--eval-points", type=int, default=1_000_000)
     ap.add_argument("--eval-track", type=float, default=10.0)
+    ap.add_argument("--eval-outliers", type=float, default=0.3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autograd-modes", action="store_true",
@@ -403,8 +404,9 @@ def run_learned(a):
     the learned solve evaluates the network, labels from the converged
     residuals; the network trained with the library's trainer.
     Evaluation: one scene with N = `--eval-cams` cameras, `--eval-points`
-    points, track length 2 + Geometric (mean `--eval-track`), 30% outliers,
-    relative rotations with 1 deg noise.  The plain fm_solve (5 filtering
+    points, track length 2 + Geometric (mean `--eval-track`), an outlier
+    fraction of `--eval-outliers` (default 0.3), relative rotations with 1 deg
+    noise.  The plain fm_solve (5 filtering
     rounds) and the learned one (2 pruning passes, 1 round) are timed end to
     end (wall clock around the call, after a warm-up solve); accuracy is the
     mean rotation error and the mean camera-centre error (relative to the
@@ -442,7 +444,7 @@ def run_learned(a):
     acc = float(((Lm.logits(theta, X) >= 0).float() == y).float().mean())
     del X, y, Xs, ys
     t0 = time.time()
-    ev = scene_c2(seed=5000 + a.seed, n_cams=a.eval_cams, n_points=a.eval_points, outlier_frac=0.3,
+    ev = scene_c2(seed=5000 + a.seed, n_cams=a.eval_cams, n_points=a.eval_points, outlier_frac=a.eval_outliers,
                   track_mean=a.eval_track)
     gen_eval = time.time() - t0
     R = gt_relative_poses(ev, rot_noise_deg=1.0, seed=a.seed)[0].astype(np.float32)
@@ -475,7 +477,8 @@ def run_learned(a):
         "n_gpus": 1, "higher_is_better": True, "dtype": "f32 (network: bf16 tensor cores, f32 accumulate)",
         "data": "synthetic",
         "config": {"workload": f"learned_c5: eval scene {ev.n_cams} cameras, {ev.n_pairs} image pairs, "
-                               f"{ev.n_kp} keypoint pairs, 30% outliers; trained on {len(train)} scenes",
+                               f"{ev.n_kp} keypoint pairs, {100 * a.eval_outliers:.0f}% outliers; "
+                               f"trained on {len(train)} scenes",
                    "train_scenes": len(train), "train_rows": None},
         "plain": plain, "learned": learned,
         "training": {"rows_accuracy": acc, "bce_first_last": [losses[0], losses[-1]], "train_s": train_s,
