@@ -58,6 +58,8 @@ def args_():
     ap.add_argument("--train-scenes", type=int, default=200)
     ap.add_argument("--eval-cams", type=int, default=3000)
     ap.add_argument("--eval-points", type=int, default=1_000_000)
+    ap.add_argument("--tuning", default=None,
+                    help="pairs_per_lane,ctas_per_sm,rows_max for the direct kernel instead of autotuning")
     ap.add_argument("--eval-track", type=float, default=10.0)
     ap.add_argument("--eval-outliers", type=float, default=0.3)
     ap.add_argument("--seed", type=int, default=0)
@@ -525,7 +527,12 @@ def main():
     p_dev = torch.from_numpy(params.reshape(-1)).to(dev)
     pr.set_params(F.FM_STAGE_EPIPOLAR, p_dev)
     pr.set_ea_loss(F.FM_EA_L1)
-    tuning = pr.autotune(repeats=5)       # the project's autotuner picks the direct kernel's launch
+    if a.tuning:                          # a given launch configuration (profiling runs)
+        u, c, r = (int(v) for v in a.tuning.split(","))
+        pr.set_tuning(u, c, r)
+        tuning = dict(pr.get_tuning(), source="--tuning")
+    else:                                 # the project's autotuner picks the direct kernel's launch
+        tuning = pr.autotune(repeats=5)
     pr.track_loss(1, 4096)
     flush_w = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     flush_r = torch.zeros(64 << 20, dtype=torch.float32, device=dev)
