@@ -451,7 +451,8 @@ fm_status fm_solve(fm_problem* problem, const fm_solve_opts* opts, fm_result* re
  * flat: W1 [8][64] (feature-major), b1 [64], W2 [64][64] (input-major),
  * b2 [64], w3 [64], b3 [1].  The products run on the tensor cores with
  * bfloat16 operands (x, W1, h1, W2; in training also dz2 and dz1) and
- * float32 accumulation. */
+ * float32 accumulation: inference on tcgen05 (accumulators in tensor
+ * memory), training on mma.sync. */
 #define FM_MLP_N_PARAMS 4801
 #define FM_MLP_N_FEATURES 8
 
@@ -463,7 +464,9 @@ fm_status fm_mlp_set_params(fm_problem* problem, const float* theta, int32_t on_
  * residuals r_m into resid_dev [Z], and the inlier probabilities p_m into
  * prob_dev [Z] (needs the network parameters); any output may be NULL.
  * Device pointers, in the order of the keypoint pairs given at creation.
- * delta: the IRLS floor of f7 (> 0).  Asynchronous. */
+ * delta: the IRLS floor of f7 (> 0).  Asynchronous without prob_dev; with
+ * it, synchronises and returns FM_ERR_TIMEOUT if a bounded wait of the
+ * tensor-core kernel ran out. */
 fm_status fm_mlp_eval(fm_problem* problem, const float* params_dev, float iter_frac, float delta,
                       float* feat_dev, float* resid_dev, float* prob_dev);
 
@@ -507,7 +510,9 @@ fm_status fm_mlp_trainer_loss_grad(fm_mlp_trainer* trainer, const float* x_dev, 
  * the step.  Asynchronous. */
 fm_status fm_mlp_trainer_step(fm_mlp_trainer* trainer, const float* x_dev, const float* y_dev, int64_t B,
                               const fm_adam_opts* opts, float* loss_dev);
-/* Logits o of feature rows x [B][8] into logit_dev [B].  Asynchronous. */
+/* Logits o of feature rows x [B][8] into logit_dev [B], on the tcgen05
+ * tensor cores (bf16 operands in shared memory, fp32 accumulators in tensor
+ * memory).  Synchronises; FM_ERR_TIMEOUT if a bounded wait ran out. */
 fm_status fm_mlp_trainer_forward(fm_mlp_trainer* trainer, const float* x_dev, int64_t B, float* logit_dev);
 
 /* Launch configuration of the direct epipolar kernel (k_ea_direct). */

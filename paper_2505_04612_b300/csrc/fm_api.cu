@@ -142,6 +142,10 @@ fm_status check_err_bits(fm_problem* pr) {
   if (bits & fm::kErrKpOrder) msg += "kp_img_pair is not non-decreasing; ";
   if (bits & fm::kErrKpNonFinite) msg += "a keypoint coordinate is not finite; ";
   if (bits & fm::kErrParamNonFinite) msg += "a parameter is not finite; ";
+  if (bits & fm::kErrMlpTimeout) {
+    msg += "a bounded wait of the tensor-core network kernel ran out; ";
+    return fail(pr, FM_ERR_TIMEOUT, msg);
+  }
   fm_status st = (bits & (fm::kErrKpNonFinite | fm::kErrParamNonFinite)) &&
                          !(bits & (fm::kErrKpRange | fm::kErrKpOrder))
                      ? FM_ERR_NAN
@@ -1253,7 +1257,7 @@ static fm_status mlp_eval(fm_problem* pr, const float* params, float iter_frac, 
                          feat, resid, s);
   }
   FM_LAUNCHED(pr);
-  return FM_OK;
+  return prob ? check_err_bits(pr) : FM_OK;
 }
 
 fm_status fm_mlp_eval(fm_problem* pr, const float* params_dev, float iter_frac, float delta, float* feat_dev,
@@ -1844,6 +1848,8 @@ struct fm_mlp_trainer {
   cudaStream_t stream = nullptr;
   int64_t max_batch = 0;
   int step = 0;
+  int sm_count = 0;
+  int* err = nullptr;   // device error bits of the tensor-core kernels
   float* theta = nullptr;
   float* m = nullptr;
   float* v = nullptr;
@@ -1861,6 +1867,7 @@ static void trainer_free(fm_mlp_trainer* t) {
   if (!t) return;
   for (float* p : {t->theta, t->m, t->v, t->grad, t->loss, t->partial})
     if (p) cudaFree(p);
+  if (t->err) cudaFree(t->err);
 }
 
 fm_status fm_mlp_trainer_create(int64_t max_batch, void* cuda_stream, fm_mlp_trainer** out) {
@@ -1879,6 +1886,11 @@ fm_status fm_mlp_trainer_create(int64_t max_batch, void* cuda_stream, fm_mlp_tra
     if (e == cudaSuccess) e = cudaMalloc((void**)pp, sizeof(float) * n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&t->loss, sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&t->partial, sizeof(float) * parts);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&t->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->err, 0, sizeof(int), t->stream);
+  int dev = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->theta, 0, sizeof(float) * n, t->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->m, 0, sizeof(float) * n, t->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->v, 0, sizeof(float) * n, t->stream);
@@ -1960,9 +1972,17 @@ fm_status fm_mlp_trainer_forward(fm_mlp_trainer* t, const float* x, int64_t B, f
   fm_status st = trainer_check_batch(t, x, B);
   if (st != FM_OK) return st;
   if (B > 0 && !logit_dev) return trainer_fail(FM_ERR_INVALID_ARG, "logit_dev is NULL");
-  fm::launch_mlp_forward_x(t->theta, x, B, logit_dev, t->stream);
+  fm::launch_mlp_forward_tc(t->theta, x, B, logit_dev, t->err, t->sm_count, t->stream);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return trainer_fail(FM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  int bits = 0;
+  e = cudaMemcpyAsync(&bits, t->err, sizeof(int), cudaMemcpyDeviceToHost, t->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(t->stream);
+  if (e != cudaSuccess) return trainer_fail(FM_ERR_CUDA, std::string("trainer: ") + cudaGetErrorString(e));
+  if (bits & fm::kErrMlpTimeout) {
+    cudaMemsetAsync(t->err, 0, sizeof(int), t->stream);
+    return trainer_fail(FM_ERR_TIMEOUT, "a bounded wait of the tensor-core network kernel ran out");
+  }
   return FM_OK;
 }
 

@@ -44,6 +44,7 @@ enum : int {
   kErrKpRange = 2,       // kp_img_pair outside [0, P)
   kErrKpNonFinite = 4,   // keypoint not finite
   kErrParamNonFinite = 8,
+  kErrMlpTimeout = 16,   // a bounded wait of the tensor-core network kernel ran out
 };
 
 enum KernelId : int {
@@ -306,7 +307,13 @@ void launch_mlp_pair_tables(const fm_problem* pr, const float* params, const flo
 void launch_mask_from_prob(const float* prob, int64_t Z, float p_min, float* w, cudaStream_t s);
 void launch_mlp_infer(const fm_problem* pr, const float* tab, const float* theta, const float* w, float iter_frac,
                       float delta, float* prob, float* logit, float* feat, float* resid, cudaStream_t s);
-void launch_mlp_forward_x(const float* theta, const float* x, int64_t B, float* logit, cudaStream_t s);
+// tcgen05 forward pass (fm_mlp_tc.cu); err: device error bits
+struct InferArgs;
+// the network on the tcgen05 tensor cores over the pairs of a (features
+// computed in the kernel); err gets kErrMlpTimeout if a bounded wait ran out
+void launch_mlp_infer_tc(const InferArgs& a, int* err, int sm_count, cudaStream_t s);
+void launch_mlp_forward_tc(const float* theta, const float* x, int64_t B, float* logit, int* err, int sm_count,
+                           cudaStream_t s);
 void launch_mlp_grad(const float* theta, const float* x, const float* y, int64_t B, float* partial, float* grad,
                      float* loss, cudaStream_t s);
 void launch_mlp_adam(float* theta, const float* grad, float* m, float* v, int step, float lr, float b1, float b2,

@@ -1,7 +1,8 @@
-// Learned per-pair inlier weights: the features of a keypoint pair, the
-// 8-64-64-1 GELU network on the tensor cores (bfloat16 operands, float32
-// accumulation, mma.sync m16n8k16), its binary cross-entropy gradient and
-// Adam.  The paper down-weights outliers with IRLS and a periodic filter
+// Learned per-pair inlier weights: the per-image-pair feature tables, the
+// features alone, and the training of the 8-64-64-1 GELU network on the
+// tensor cores (bfloat16 operands, float32 accumulation, mma.sync m16n8k16):
+// its binary cross-entropy gradient and Adam.  Inference runs on tcgen05
+// (fm_mlp_tc.cu).  The paper down-weights outliers with IRLS and a periodic filter
 // (Sec. 3.3, Eq. 9); the network replaces the filter by a predicted inlier
 // probability.  Feature and network definitions (readings) are those of the
 // problem-level documentation in include/fastmap.h.
@@ -25,6 +26,7 @@
 
 #include "fm_device.cuh"
 #include "fm_internal.h"
+#include "fm_mlp.cuh"
 
 namespace fm {
 namespace {
@@ -150,7 +152,7 @@ __device__ __forceinline__ void mlp_forward(const MlpWeights& s, const uint32_t 
 // ------------------------------------------------------------ features
 
 // per image pair: E (9), R_i (9), R_j (9), mean |r|, log Z_n, fbar, 0
-constexpr int kTab = 32;
+constexpr int kTab = kMlpTab;
 
 // params: epipolar-stage [N][9]; or, with rel_t, rotation-stage [N][6] and
 // E_n = [t^{i->j}]_x R_j R_i^T from the relative translation of the pair
@@ -221,109 +223,16 @@ __global__ void __launch_bounds__(128) k_mlp_pair_tables(const float* params, co
   }
 }
 
-struct InferArgs {
-  const float4* kp;
-  const int* kp_seg;
-  const float* tab;
-  const int* kp_track;     // or null
-  const int* track_off;    // or null
-  const float* w;          // current per-pair weights, or null (1)
-  float iter_frac;
-  float inv_log_delta;     // 1 / log1p(1/delta)
-  const float* theta;      // or null: features only
-  int64_t Z;
-  float* prob;             // [Z] or null
-  float* logit;            // [Z] or null
-  float* feat;             // [Z][8] or null
-  float* resid;            // [Z] or null
-};
-
-__device__ __forceinline__ void pair_features(const InferArgs& a, int64_t m, float* f, float& r) {
-  const int n = a.kp_seg[m];
-  const float* T = a.tab + (size_t)kTab * n;
-  const float4 x = __ldg(a.kp + m);
-  const float a0 = fmaf(T[0], x.x, fmaf(T[1], x.y, T[2]));
-  const float a1 = fmaf(T[3], x.x, fmaf(T[4], x.y, T[5]));
-  const float a2 = fmaf(T[6], x.x, fmaf(T[7], x.y, T[8]));
-  r = fmaf(x.z, a0, fmaf(x.w, a1, a2));
-  const float b0 = fmaf(T[0], x.z, fmaf(T[3], x.w, T[6]));
-  const float b1 = fmaf(T[1], x.z, fmaf(T[4], x.w, T[7]));
-  const float ar = fabsf(r);
-  f[0] = ar / (T[27] + 1e-12f);
-  f[1] = log1pf(T[29] * ar / sqrtf(a0 * a0 + a1 * a1 + b0 * b0 + b1 * b1));
-  f[2] = 0.f;
-  if (a.kp_track) {
-    const int tr = a.kp_track[m];
-    const float c = (float)(a.track_off[tr + 1] - a.track_off[tr]);
-    f[2] = logf(0.5f * (1.f + sqrtf(1.f + 8.f * c)));
-  }
-  // viewing rays R^T x~ of both keypoints; their angle via atan2 (accurate
-  // for small angles)
-  const float* Ri = T + 9;
-  const float* Rj = T + 18;
-  float d1[3], d2[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    d1[k] = fmaf(Ri[k], x.x, fmaf(Ri[3 + k], x.y, Ri[6 + k]));
-    d2[k] = fmaf(Rj[k], x.z, fmaf(Rj[3 + k], x.w, Rj[6 + k]));
-  }
-  float cr[3];
-  cross3(d1, d2, cr);
-  f[3] = atan2f(sqrtf(dot3(cr, cr)), dot3(d1, d2));
-  f[4] = 0.5f * (sqrtf(x.x * x.x + x.y * x.y) + sqrtf(x.z * x.z + x.w * x.w));
-  f[5] = a.iter_frac;
-  f[6] = T[28];
-  f[7] = log1pf(a.w ? a.w[m] : 1.f) * a.inv_log_delta;
-}
-
+// features (and residuals) only; the network runs in k_mlp_forward_tc
 __global__ void __launch_bounds__(kWarps * 32) k_mlp_infer(InferArgs a) {
-  __shared__ MlpWeights s;
-  __shared__ float xs[kWarps][32][kIn];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  if (a.theta) stage_weights(a.theta, s, false);
-  __syncthreads();
-  for (int64_t base = ((int64_t)blockIdx.x * kWarps + wib) * 32; base < a.Z;
-       base += (int64_t)gridDim.x * kWarps * 32) {
-    const int64_t m = base + lane;
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < a.Z; m += (int64_t)gridDim.x * blockDim.x) {
     float f[kIn];
     float r = 0.f;
-    if (m < a.Z) {
-      pair_features(a, m, f, r);
-      if (a.feat)
+    pair_features(a, m, f, r);
+    if (a.feat)
 #pragma unroll
-        for (int k = 0; k < kIn; ++k) a.feat[m * kIn + k] = f[k];
-      if (a.resid) a.resid[m] = r;
-    } else {
-#pragma unroll
-      for (int k = 0; k < kIn; ++k) f[k] = 0.f;
-    }
-    if (!a.theta) continue;
-#pragma unroll
-    for (int k = 0; k < kIn; ++k) xs[wib][lane][k] = f[k];
-    __syncwarp();
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      const float* xg = xs[wib][16 * mt + g];
-      const float* xg8 = xs[wib][16 * mt + g + 8];
-      const uint32_t ax[4] = {pack_bf16(xg[2 * t], xg[2 * t + 1]), pack_bf16(xg8[2 * t], xg8[2 * t + 1]), 0u, 0u};
-      float z1[8][4], z2[8][4];
-      uint32_t a1[4][4];
-      float o_g, o_g8;
-      mlp_forward(s, ax, lane, z1, a1, z2, o_g, o_g8);
-      if (t == 0) {
-        const int64_t m0 = base + 16 * mt + g, m1 = m0 + 8;
-        if (m0 < a.Z) {
-          if (a.prob) a.prob[m0] = sigmoid_f(o_g);
-          if (a.logit) a.logit[m0] = o_g;
-        }
-        if (m1 < a.Z) {
-          if (a.prob) a.prob[m1] = sigmoid_f(o_g8);
-          if (a.logit) a.logit[m1] = o_g8;
-        }
-      }
-    }
-    __syncwarp();
+      for (int k = 0; k < kIn; ++k) a.feat[m * kIn + k] = f[k];
+    if (a.resid) a.resid[m] = r;
   }
 }
 
@@ -331,32 +240,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_mlp_infer(InferArgs a) {
 __global__ void k_mask_from_prob(const float* __restrict__ prob, int64_t Z, float p_min, float* __restrict__ w) {
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m < Z) w[m] = prob[m] >= p_min ? 1.f : 0.f;
-}
-
-// the network on feature rows x [B][8] (inference on stored features)
-__global__ void __launch_bounds__(kWarps * 32) k_mlp_forward_x(const float* theta, const float* __restrict__ x,
-                                                               int64_t B, float* __restrict__ logit) {
-  __shared__ MlpWeights s;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  stage_weights(theta, s, false);
-  __syncthreads();
-  for (int64_t base = ((int64_t)blockIdx.x * kWarps + wib) * 16; base < B;
-       base += (int64_t)gridDim.x * kWarps * 16) {
-    const int64_t r0 = base + g, r1 = base + g + 8;
-    float x0 = 0.f, x1 = 0.f, y0 = 0.f, y1 = 0.f;
-    if (r0 < B) { x0 = x[r0 * kIn + 2 * t]; x1 = x[r0 * kIn + 2 * t + 1]; }
-    if (r1 < B) { y0 = x[r1 * kIn + 2 * t]; y1 = x[r1 * kIn + 2 * t + 1]; }
-    const uint32_t ax[4] = {pack_bf16(x0, x1), pack_bf16(y0, y1), 0u, 0u};
-    float z1[8][4], z2[8][4];
-    uint32_t a1[4][4];
-    float o_g, o_g8;
-    mlp_forward(s, ax, lane, z1, a1, z2, o_g, o_g8);
-    if (t == 0) {
-      if (r0 < B) logit[r0] = o_g;
-      if (r1 < B) logit[r1] = o_g8;
-    }
-  }
 }
 
 // ------------------------------------------------------------ training
@@ -653,17 +536,16 @@ void launch_mlp_infer(const fm_problem* pr, const float* tab, const float* theta
   a.iter_frac = iter_frac;
   a.inv_log_delta = 1.f / log1pf(1.f / delta);
   a.theta = theta;
+  a.x = nullptr;
   a.Z = pr->Z;
   a.prob = prob;
   a.logit = logit;
   a.feat = feat;
   a.resid = resid;
-  k_mlp_infer<<<grid_for_pairs(pr->Z, kWarps * 32), kWarps * 32, 0, s>>>(a);
-}
-
-void launch_mlp_forward_x(const float* theta, const float* x, int64_t B, float* logit, cudaStream_t s) {
-  if (B == 0) return;
-  k_mlp_forward_x<<<grid_for_pairs(B, kWarps * 16), kWarps * 32, 0, s>>>(theta, x, B, logit);
+  if (theta)
+    launch_mlp_infer_tc(a, pr->d_err, pr->sm_count, s);
+  else
+    k_mlp_infer<<<grid_for_pairs(pr->Z, kWarps * 32), kWarps * 32, 0, s>>>(a);
 }
 
 void launch_mlp_grad(const float* theta, const float* x, const float* y, int64_t B, float* partial, float* grad,

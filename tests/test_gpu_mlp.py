@@ -72,10 +72,12 @@ def test_loss_and_gradient_match_the_oracle(B):
     tr.close()
 
 
-def test_forward_logits_match_the_oracle():
+@pytest.mark.parametrize("B", [1, 127, 128, 5000, 200003])
+def test_forward_logits_match_the_oracle(B):
+    """The tcgen05 forward pass: single rows, one ragged tile, one full tile,
+    many tiles, and more tiles than resident CTAs (persistent loop)."""
     torch, F = _mods()
     G.lib_ready()
-    B = 5000
     x, _ = _batch(B, 7)
     th = _theta(11)
     tr = F.MlpTrainer(B)
