@@ -517,24 +517,22 @@ fm_status fm_mlp_trainer_forward(fm_mlp_trainer* trainer, const float* x_dev, in
 
 /* Launch configuration of the direct epipolar kernel (k_ea_direct). */
 typedef struct {
-  int32_t pairs_per_lane;      /* keypoint pairs per thread: 11 or 15 (a warp
-                                  run is 32 x this many consecutive pairs) */
+  int32_t pairs_per_lane;      /* keypoint pairs per thread at most: 11, 15
+                                  or 21
+                                  (a thread's pairs never cross an image-pair
+                                  end; a warp run is 32 threads' pairs) */
   int32_t ctas_per_sm;         /* persistent CTAs per SM; 0 = as many as fit */
-  int32_t rows_max_img_pairs;  /* warp runs touching at most this many image
-                                  pairs are processed row by row (one
-                                  coalesced row of 32 pairs at a time), the
-                                  others lane by lane (>= 1) */
   float us_per_eval;           /* fm_autotune: median time of the chosen one */
 } fm_tuning;
 
 /* Sets / reads the configuration (changing pairs_per_lane rebuilds the
- * kernel's tables; synchronises).  Defaults: 15, 0, 2. */
+ * kernel's tables; synchronises).  Defaults: 15, 0. */
 fm_status fm_set_tuning(fm_problem* problem, const fm_tuning* tuning);
 fm_status fm_get_tuning(const fm_problem* problem, fm_tuning* tuning);
 
 /* Autotuner: times the direct kernel (L1, the problem's current weights and
  * epipolar parameters, or generated parameters when none are set) for both
- * tiles, every CTA count per SM that fits and thresholds 1..4, `repeats`
+ * tiles and every CTA count per SM that fits, `repeats`
  * times each with L2 flushed before every launch, and keeps the fastest
  * (median).  The choice changes no result beyond the order of additions
  * inside an image pair's records.  Synchronises. */
@@ -551,7 +549,10 @@ fm_status fm_graphs_enable(fm_problem* problem, int32_t enable);
 
 /* Per-kernel device time: with timing on, the library records a CUDA event
  * pair around every kernel it launches (on its stream) and accumulates the
- * elapsed time per kernel name.  Enabling or disabling resets the counters. */
+ * elapsed time per kernel name; timed kernels are launched without
+ * programmatic dependent launch, so that each pair brackets exactly one
+ * kernel (results are identical).  Enabling or disabling resets the
+ * counters. */
 typedef struct {
   char name[32];
   int64_t launches;
@@ -605,9 +606,9 @@ fm_status fm_loss_history(fm_problem* problem, float* out, int32_t capacity, int
  * cuda_stream: the stream to enqueue on (NULL = default); the call returns
  * after enqueueing.
  *
- * Limits and sharing: the tables need about 48 B per image pair plus 4 B per
- * 15 keypoint pairs (plus 48 B per 480 keypoint pairs); a problem that does
- * not fit in 16 MiB (roughly P + Z/150 beyond ~300k) is rejected with
+ * Limits and sharing: the tables need about 118 B per image pair plus 0.4 B
+ * per keypoint pair; a problem that does not fit in 16 MiB (118 P + 0.4 Z
+ * beyond 16.7M) is rejected with
  * FM_ERR_INVALID_ARG and a message from fm_last_error(NULL), before any GPU
  * work.  Every call on a device shares the one array and leaves its contents
  * behind; nothing in it needs to start at zero.  Calls whose GPU work

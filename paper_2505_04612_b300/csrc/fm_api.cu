@@ -47,6 +47,10 @@ struct Timed {
       a = take_event(pr);
       b = take_event(pr);
       cudaEventRecord(a, pr->stream);
+      // a timed kernel starts after the event, not overlapped with its
+      // predecessor by programmatic dependent launch: the pair brackets
+      // exactly this kernel
+      fm::g_plain_once = true;
     }
   }
   ~Timed() {
@@ -159,7 +163,7 @@ void release(fm_problem* pr) {
   dfree(pr->pair_i); dfree(pr->pair_j); dfree(pr->seg_off);
   dfree(pr->cam_seg_off); dfree(pr->cam_seg);
   dfree(pr->kp); dfree(pr->kp_track); dfree(pr->focal); dfree(pr->cx); dfree(pr->cy);
-  dfree(pr->run_seg); dfree(pr->wrun_info); dfree(pr->seg_rec); dfree(pr->rec);
+  dfree(pr->lane_desc); dfree(pr->wrun_info); dfree(pr->seg_rec); dfree(pr->rec);
   dfree(pr->seg_tab); dfree(pr->seg_grad); dfree(pr->seg_loss);
   dfree(pr->ea_w); dfree(pr->ea_params);
   dfree(pr->ea_adam.m); dfree(pr->ea_adam.v); dfree(pr->ea_adam.t);
@@ -214,43 +218,65 @@ fm_status build_direct_tables(fm_problem* pr, int U) {
   const int P = pr->P;
   const int64_t Z = pr->Z;
   FM_CUDA(pr, cudaStreamSynchronize(s));
-  if (pr->run_seg) {   // tables of a previous tile
+  if (pr->lane_desc) {   // tables of a previous tile
     pr->device_bytes -= (int64_t)sizeof(int) * 32 * std::max(pr->n_wruns, 1) +
                         (int64_t)sizeof(int4) * std::max(pr->n_wruns, 1) + (int64_t)sizeof(int) * 2 * P +
                         (int64_t)sizeof(float4) * 3 * std::max<int64_t>(pr->n_rec, 1);
   }
-  dfree(pr->run_seg);
+  dfree(pr->lane_desc);
   dfree(pr->wrun_info);
   dfree(pr->seg_rec);
   dfree(pr->rec);
   pr->ea_U = U;
-  pr->n_wruns = (int)((Z + 32 * (int64_t)U - 1) / (32 * (int64_t)U));
-  FM_ALLOC(pr, pr->run_seg, (size_t)pr->n_wruns * 32);
-  FM_ALLOC(pr, pr->wrun_info, pr->n_wruns);
-  FM_ALLOC(pr, pr->seg_rec, 2 * (size_t)P);
-  if (pr->n_wruns > 0) {
-    int64_t* d_total = nullptr;
-    FM_ALLOC(pr, d_total, 1);
+  // lanes per image pair and their scan G (temporary)
+  int* G = nullptr;
+  int* d_T = nullptr;
+  int64_t* d_total = nullptr;
+  FM_ALLOC(pr, G, (size_t)P + 1);
+  FM_ALLOC(pr, d_T, 1);
+  FM_ALLOC(pr, d_total, 1);
+  auto release_tmp = [&]() {
+    cudaFree(G);
+    cudaFree(d_T);
+    cudaFree(d_total);
+    pr->device_bytes -= (int64_t)sizeof(int) * (P + 2) + (int64_t)sizeof(int64_t);
+  };
+  int T = 0;
+  if (Z > 0 && P > 0) {
     {
       Timed t(pr, fm::kKRunTables);
-      fm::launch_run_tables(pr->seg_off, P, Z, pr->n_wruns, U, pr->run_seg, pr->wrun_info, s);
+      fm::launch_lane_scan(pr->seg_off, P, U, G, d_T, s);
     }
+    FM_LAUNCHED(pr);
+    FM_CUDA(pr, cudaMemcpyAsync(&T, d_T, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FM_CUDA(pr, cudaStreamSynchronize(s));
+  }
+  pr->n_wruns = (T + 31) / 32;
+  fm_status st = FM_OK;
+  if ((st = dalloc(pr, &pr->lane_desc, (size_t)pr->n_wruns * 32)) != FM_OK ||
+      (st = dalloc(pr, &pr->wrun_info, (size_t)pr->n_wruns)) != FM_OK ||
+      (st = dalloc(pr, &pr->seg_rec, 2 * (size_t)P)) != FM_OK) {
+    release_tmp();
+    return st;
+  }
+  int64_t total = 0;
+  if (pr->n_wruns > 0) {
+    fm::launch_lane_desc(pr->seg_off, G, d_T, P, U, pr->n_wruns, pr->lane_desc, pr->wrun_info, s);
     FM_LAUNCHED(pr);
     fm::launch_exclusive_scan_info(pr->wrun_info, pr->n_wruns, d_total, s);
     FM_LAUNCHED(pr);
-    int64_t total = 0;
     FM_CUDA(pr, cudaMemcpyAsync(&total, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     FM_CUDA(pr, cudaStreamSynchronize(s));
-    cudaFree(d_total);
-    pr->device_bytes -= (int64_t)sizeof(int64_t);
-    pr->n_rec = total;
-  } else {
-    pr->n_rec = 0;
   }
-  FM_ALLOC(pr, pr->rec, 3 * (size_t)(pr->n_rec > 0 ? pr->n_rec : 1));
-  fm::launch_seg_records(pr->seg_off, pr->run_seg, pr->wrun_info, P, U, pr->seg_rec, s);
+  pr->n_rec = total;
+  if ((st = dalloc(pr, &pr->rec, 3 * (size_t)(pr->n_rec > 0 ? pr->n_rec : 1))) != FM_OK) {
+    release_tmp();
+    return st;
+  }
+  fm::launch_seg_records(pr->seg_off, G, pr->wrun_info, P, pr->seg_rec, s);
   FM_LAUNCHED(pr);
   FM_CUDA(pr, cudaStreamSynchronize(s));
+  release_tmp();
   pr->graph_epoch += 1;   // captured launches hold the table pointers
   return FM_OK;
 }
@@ -1338,7 +1364,6 @@ fm_status fm_get_tuning(const fm_problem* pr, fm_tuning* out) {
   if (!pr || !out) return FM_ERR_INVALID_ARG;
   out->pairs_per_lane = pr->ea_U;
   out->ctas_per_sm = pr->ea_ctas_per_sm;
-  out->rows_max_img_pairs = pr->ea_rows_max;
   out->us_per_eval = 0.f;
   return FM_OK;
 }
@@ -1346,23 +1371,21 @@ fm_status fm_get_tuning(const fm_problem* pr, fm_tuning* out) {
 fm_status fm_set_tuning(fm_problem* pr, const fm_tuning* t) {
   if (!pr) return FM_ERR_INVALID_ARG;
   if (!t) return fail(pr, FM_ERR_INVALID_ARG, "tuning is NULL");
-  if (t->pairs_per_lane != 11 && t->pairs_per_lane != 15)
-    return fail(pr, FM_ERR_INVALID_ARG, "pairs_per_lane must be 11 or 15 (the tiles built into the library)");
-  if (t->ctas_per_sm < 0 || t->rows_max_img_pairs < 1)
-    return fail(pr, FM_ERR_INVALID_ARG, "ctas_per_sm >= 0 and rows_max_img_pairs >= 1 required");
+  if (!fm::ea_tile_built(t->pairs_per_lane))
+    return fail(pr, FM_ERR_INVALID_ARG, "pairs_per_lane must be 11, 15 or 21 (the tiles built into the library)");
+  if (t->ctas_per_sm < 0) return fail(pr, FM_ERR_INVALID_ARG, "ctas_per_sm >= 0 required");
   if (t->pairs_per_lane != pr->ea_U) {
     fm_status e = build_direct_tables(pr, t->pairs_per_lane);
     if (e != FM_OK) return e;
   }
   pr->ea_ctas_per_sm = t->ctas_per_sm;
-  pr->ea_rows_max = t->rows_max_img_pairs;
   pr->graph_epoch += 1;
   return FM_OK;
 }
 
 // Times k_ea_direct (L1, the problem's weights) for every tile built into
-// the library, every CTA count per SM and row/lane threshold 1..4, each launch
-// after a flush of L2, and keeps the fastest (median of `repeats`).
+// the library and every CTA count per SM, each launch after a flush of L2,
+// and keeps the fastest (median of `repeats`).
 fm_status fm_autotune(fm_problem* pr, int32_t repeats, fm_tuning* best_out) {
   if (!pr) return FM_ERR_INVALID_ARG;
   if (repeats < 1) return fail(pr, FM_ERR_INVALID_ARG, "repeats must be >= 1");
@@ -1390,39 +1413,40 @@ fm_status fm_autotune(fm_problem* pr, int32_t repeats, fm_tuning* best_out) {
   cudaEvent_t a = nullptr, b = nullptr;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  const int old_u = pr->ea_U, old_c = pr->ea_ctas_per_sm, old_r = pr->ea_rows_max;
-  fm_tuning best{old_u, old_c, old_r, 3.4e38f};
+  const int old_u = pr->ea_U, old_c = pr->ea_ctas_per_sm;
+  fm_tuning best{old_u, old_c, 3.4e38f};
   fm_status st = FM_OK;
-  for (int U : {15, 11}) {
+  for (int U : {15, 11, 21}) {
     if (pr->Z == 0) break;
     if (U != pr->ea_U && (st = build_direct_tables(pr, U)) != FM_OK) break;
     const int max_c = fm::direct_max_ctas_per_sm(pr);
-    for (int c = 1; c <= max_c && st == FM_OK; ++c)
-      for (int r = 1; r <= 4 && st == FM_OK; ++r) {
+    // round robin over the CTA counts, so that a slow drift of the device
+    // (clocks, power) does not favour the first ones
+    std::vector<std::vector<float>> ms(max_c + 1);
+    for (int k = 0; k < repeats && st == FM_OK; ++k)
+      for (int c = 1; c <= max_c; ++c) {
         pr->ea_ctas_per_sm = c;
-        pr->ea_rows_max = r;
-        std::vector<float> ms;
-        for (int k = 0; k < repeats; ++k) {
-          if (flush) cudaMemsetAsync(flush, k & 0xff, flush_bytes, s);
-          cudaEventRecord(a, s);
-          fm::g_plain_once = true;
-          fm::launch_ea_direct(pr, pr->ea_w, FM_EA_L1, s);
-          cudaEventRecord(b, s);
-          cudaError_t ce = cudaEventSynchronize(b);
-          float t = 0.f;
-          if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, a, b);
-          if (ce != cudaSuccess) {
-            st = fail(pr, FM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
-            break;
-          }
-          ms.push_back(t);
+        if (flush) fm::launch_l2_flush(flush, flush_bytes, k & 0xff, s);
+        cudaEventRecord(a, s);
+        fm::g_plain_once = true;
+        fm::launch_ea_direct(pr, pr->ea_w, FM_EA_L1, s);
+        cudaEventRecord(b, s);
+        cudaError_t ce = cudaEventSynchronize(b);
+        float t = 0.f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, a, b);
+        if (ce != cudaSuccess) {
+          st = fail(pr, FM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+          break;
         }
-        if (st != FM_OK) break;
-        std::sort(ms.begin(), ms.end());
-        const float med = 1000.f * ms[ms.size() / 2];
-        if (med < best.us_per_eval) best = fm_tuning{U, c, r, med};
-        pr->k_launches[fm::kKEaDirect] += repeats;
+        ms[c].push_back(t);
+        pr->k_launches[fm::kKEaDirect] += 1;
       }
+    if (st != FM_OK) break;
+    for (int c = 1; c <= max_c; ++c) {
+      std::sort(ms[c].begin(), ms[c].end());
+      const float med = 1000.f * ms[c][ms[c].size() / 2];
+      if (med < best.us_per_eval) best = fm_tuning{U, c, med};
+    }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -1431,7 +1455,6 @@ fm_status fm_autotune(fm_problem* pr, int32_t repeats, fm_tuning* best_out) {
   if (st != FM_OK) {   // leave the previous tile in place
     if (pr->ea_U != old_u) build_direct_tables(pr, old_u);
     pr->ea_ctas_per_sm = old_c;
-    pr->ea_rows_max = old_r;
     return st;
   }
   if (best_out) *best_out = best;

@@ -17,20 +17,19 @@
 //
 // k_ea_direct layout and schedule
 //   * keypoint pairs are sorted by image pair (CSR seg_off);
-//   * a warp run is 15 rows of 32 consecutive pairs; lane l takes pair
-//     base + 32 r + l of row r, so every row is one coalesced 512-B load
-//     (LDG.128) and the warp issues all 15 rows before using them: 7.5 KB in
-//     flight per warp, no shared memory, occupancy bounded by registers;
-//   * the table entries (E and end offset) of the warp run's first 32 image
-//     pairs sit one per lane in registers and are broadcast with shuffles;
-//     entries beyond the first 32 come from global memory;
-//   * a row that lies inside the current image pair is accumulated per lane
-//     with no branches; a row that crosses one or more image-pair ends is
-//     handled warp-uniformly: each lane finds its own image pair, the current
-//     image pair is closed by a butterfly warp sum, image pairs that start and
-//     end inside the row get their own warp sums, and the last one opens.
-//     Every (warp run, image pair) gets exactly one record, summed in a fixed
-//     order: no atomics, deterministic.
+//   * lanes: image pair n gets max(1, ceil(m_n / U)) lanes of at most U
+//     consecutive pairs, so a lane never crosses an image-pair end; a warp
+//     run is 32 consecutive lanes (at most 32 U pairs, at most 32 image
+//     pairs), described by per-lane descriptors built once per problem;
+//   * persistent warps: each warp stages its next warp run into shared memory
+//     with cp.async (coalesced 512-B rows) while it processes the current one
+//     (double buffer);
+//   * the E entries of the run's image pairs sit one per lane in registers;
+//     a lane takes its own once per run and accumulates its pairs with no
+//     per-pair selection;
+//   * a segmented scan over the lanes (a butterfly when the run lies inside
+//     one image pair) gives one record per (warp run, image pair), summed in
+//     a fixed order: no atomics, deterministic.
 //
 // Modes of k_ea_direct (the split of one evaluation into a forward and a
 // backward pass, for the autograd adjoint):
@@ -81,49 +80,18 @@ enum DirectMode { kFull = 0, kLossOnly = 1, kFromCoef = 2 };
 struct DirectArgs {
   const float4* kp;
   const float* wts;      // per-pair weights; the stored coefficients in kFromCoef
-  int rows_max;          // warp runs touching at most this many image pairs go row by row
-  const int* run_seg;
-  const int4* info;
+  const int* lane_desc;  // [32 n_wruns] offset | count << 10 | key << 15 per lane
+  const int4* info;      // [n_wruns] {first image pair, n_img | len << 8, record base, first pair}
   const float4* seg_tab;
   float4* rec;
   float* coef_out;       // kLossOnly: per-pair coefficients when not null
-  int Z;
   int n_wruns;
 };
-
 
 __device__ __forceinline__ void store_record(float4* rec, int r, const float* v) {
   rec[3 * r + 0] = make_float4(v[0], v[1], v[2], v[3]);
   rec[3 * r + 1] = make_float4(v[4], v[5], v[6], v[7]);
   rec[3 * r + 2] = make_float4(v[8], v[9], 0.f, 0.f);
-}
-
-// table entry t (local image-pair index of the warp run): lanes hold entries
-// 0..31 in registers; later entries are read from global memory
-struct Entry {
-  float E[9];
-  int end;
-};
-
-__device__ __forceinline__ void entry_uniform(const float* Ereg, int endreg, const float4* seg_tab,
-                                              int s_first, int t, Entry& o) {
-  if (t < 32) {
-#pragma unroll
-    for (int k = 0; k < 9; ++k) o.E[k] = __shfl_sync(FULL, Ereg[k], t);
-    o.end = __shfl_sync(FULL, endreg, t);
-  } else {
-    const float4* e = seg_tab + 3 * (s_first + t);
-    const float4 e0 = e[0], e1 = e[1], e2 = e[2];
-    o.E[0] = e0.x; o.E[1] = e0.y; o.E[2] = e0.z; o.E[3] = e0.w;
-    o.E[4] = e1.x; o.E[5] = e1.y; o.E[6] = e1.z; o.E[7] = e1.w;
-    o.E[8] = e2.x;
-    o.end = __float_as_int(e2.y);
-  }
-}
-
-__device__ __forceinline__ int end_uniform(int endreg, const float4* seg_tab, int s_first, int t) {
-  if (t < 32) return __shfl_sync(FULL, endreg, t);
-  return __float_as_int(seg_tab[3 * (s_first + t) + 2].y);
 }
 
 // c = w drho/dr and l = w rho of one pair.
@@ -196,356 +164,192 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
 }
-__device__ __forceinline__ void cp_async16_partial(void* smem, const void* gmem, int bytes) {
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
 }
 
-// shared memory per warp: two warp runs of keypoint pairs (double buffer),
-// row-major (row r, lane l at 32 r + l: conflict-free 512-B row reads), and
-// their weights
+// shared memory per warp: kStages warp runs of keypoint pairs and their
+// weights; slot 32 r + l is filled by lane l (coalesced 512-B rows)
 template <int U>
 constexpr size_t smem_per_warp(bool weighted) {
-  return 2 * 32 * U * (sizeof(float4) + (weighted ? sizeof(float) : 0));
+  return kEaStages * 32 * U * (sizeof(float4) + (weighted ? sizeof(float) : 0));
 }
 
-// state of a warp run prefetched before its rows are processed
+// state of a warp run, loaded before its pairs are processed
 struct RunHead {
-  int4 info;       // {first image pair, #image pairs, record base}
-  float Ereg[9];   // table entry of local image pair `lane`
-  int endreg;
-  int rs;          // image pair of this lane's first pair in the lane-contiguous split
+  int4 info;       // {first image pair, n_img | len << 8, record base, first pair}
+  int desc;        // this lane's descriptor
+  float Ereg[9];   // E of local image pair `lane` (lanes < n_img)
 };
-
-template <int U, bool WEIGHTED>
-__device__ __forceinline__ void issue_rows(const DirectArgs& a, int w, int lane, float4* kb, float* wb) {
-  constexpr int WP = 32 * U, ROWS = U;
-  const int base = w * WP;
-  // slots past Z are zero-filled (src-size 0), so that no lane ever reads
-  // stale shared memory
-#pragma unroll
-  for (int r = 0; r < ROWS; ++r) {
-    const int p = base + 32 * r + lane;
-    if (p < a.Z) cp_async16(kb + 32 * r + lane, a.kp + p);
-    else cp_async16_partial(kb + 32 * r + lane, a.kp, 0);
-  }
-  if (WEIGHTED) {
-#pragma unroll
-    for (int k = 0; k < (WP / 4 + 31) / 32; ++k) {
-      const int c = lane + 32 * k;
-      if (c < WP / 4) {
-        const int p4 = base + 4 * c;
-        const int bytes = 4 * max(0, min(4, a.Z - p4));
-        cp_async16_partial(wb + 4 * c, bytes > 0 ? a.wts + p4 : a.wts, bytes);
-      }
-    }
-  }
-  asm volatile("cp.async.commit_group;\n" ::);
-}
 
 __device__ __forceinline__ void load_static_head(const DirectArgs& a, int w, int lane, RunHead& h) {
   h.info = __ldg(a.info + w);
-  h.rs = __ldg(a.run_seg + 32 * w + lane);
+  h.desc = __ldg(a.lane_desc + 32 * w + lane);
 }
 
-// the table entries are written by the preceding k_ea_tables launch
+// the table entries are written by the preceding k_ea_tables launch: plain
+// loads after the dependency wait
 __device__ __forceinline__ void load_table_head(const DirectArgs& a, int lane, RunHead& h) {
-  h.endreg = 0x7fffffff;
-  if (lane < h.info.y) {
+  if (lane < (h.info.y & 0xff)) {
     const float4* e = a.seg_tab + 3 * (h.info.x + lane);
     const float4 e0 = e[0], e1 = e[1], e2 = e[2];
     h.Ereg[0] = e0.x; h.Ereg[1] = e0.y; h.Ereg[2] = e0.z; h.Ereg[3] = e0.w;
     h.Ereg[4] = e1.x; h.Ereg[5] = e1.y; h.Ereg[6] = e1.z; h.Ereg[7] = e1.w;
     h.Ereg[8] = e2.x;
-    h.endreg = __float_as_int(e2.y);
   } else {
 #pragma unroll
     for (int k = 0; k < 9; ++k) h.Ereg[k] = 0.f;
   }
 }
 
+// both buffers start at zero, so that a lane reading past its own pairs
+// (masked by a zero weight) only ever sees finite values: afterwards those
+// slots hold earlier keypoints (finite, checked at creation) or stashed
+// coefficients.  Slot 32 r + l is zeroed and later filled by lane l.
+template <int ROWS, bool WEIGHTED>
+__device__ __forceinline__ void zero_buffers(int lane, float4* kb, float* wb) {
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) kb[32 * r + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (WEIGHTED)
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) wb[32 * r + lane] = 0.f;
+}
+
+template <int U, bool WEIGHTED>
+__device__ __forceinline__ void issue_run(const DirectArgs& a, const int4 info, int lane, float4* kb, float* wb) {
+  const int base = info.w, len = info.y >> 8;
+#pragma unroll
+  for (int r = 0; r < U; ++r) {
+    const int i = 32 * r + lane;
+    if (i < len) cp_async16(kb + i, a.kp + base + i);
+  }
+  if (WEIGHTED) {
+#pragma unroll
+    for (int r = 0; r < U; ++r) {
+      const int i = 32 * r + lane;
+      if (i < len) cp_async4(wb + i, a.wts + base + i);
+    }
+  }
+}
+
 // The coefficient of pair base + i goes into the x component of its own
-// shared-memory slot (read only by the lane that stores it); the warp copies
-// them out with coalesced stores after the warp run (coef_store).
+// shared-memory slot (written only by the lane that owns the pair); the warp
+// copies them out with coalesced stores after the warp run.
 __device__ __forceinline__ void stash_coef(float4* kb, int i, float c) {
   reinterpret_cast<float*>(kb + i)[0] = c;
 }
 
-// Row-major processing: right for warp runs that touch one or two image pairs
-// (at most one image-pair end to cross with a warp reduction).
+// Lane l owns pairs [off, off + cnt) of the warp run (cnt <= U), all of one
+// image pair (local key): it takes E once, runs a branch-free U-step loop with
+// a zero weight past cnt (stride-U float4 reads: conflict-free for odd U) and
+// one accumulator.  A warp run inside one image pair ends with a butterfly
+// sum; otherwise a segmented inclusive scan keyed by image pair (keys do not
+// decrease with the lane) leaves each image pair's sum in its last lane.  Every
+// (warp run, image pair) gets one record, summed in a fixed order.
 template <int U, int LOSS, bool WEIGHTED, int MODE>
-__device__ __forceinline__ void process_rows(const DirectArgs& a, int w, int lane, const RunHead& h,
-                                             float4* kb, const float* wb, bool store) {
-  constexpr int WP = 32 * U;
-  const int base = w * WP;
-  const int4 info = h.info;
-  const int wend = min(base + WP, a.Z);    // one past the warp run's last pair
-  const int full_rows = (wend - base) >> 5; // rows with 32 valid pairs
-  int j = 0;                               // current local image pair (uniform)
-  Entry cur;
-  entry_uniform(h.Ereg, h.endreg, a.seg_tab, info.x, 0, cur);
+__device__ __forceinline__ void process(const DirectArgs& a, int lane, const RunHead& h, float4* kb,
+                                        const float* wb) {
+  const bool store = (MODE == kLossOnly) && a.coef_out != nullptr;
+  const int n_img = h.info.y & 0xff;
+  const int off = h.desc & ((1 << kDescCntShift) - 1);
+  const int cnt = (h.desc >> kDescCntShift) & 31, key = h.desc >> kDescKeyShift;
+  float E[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) E[q] = __shfl_sync(FULL, h.Ereg[q], key);
   float acc[10];
 #pragma unroll
   for (int k = 0; k < 10; ++k) acc[k] = 0.f;
-
-  int r = 0;
-  const int n_rows = (wend - base + 31) >> 5;
-  while (r < n_rows) {
-    // rows [r, r_in) lie inside the current image pair and are full: no checks
-    const int r_in = min(full_rows, max(r, (cur.end - base) >> 5));
-    if (r < r_in) {
-      int q = r;
-#pragma unroll 1
-      for (; q + 4 <= r_in; q += 4) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = 32 * (q + u) + lane;
-          const float c = accumulate<LOSS, WEIGHTED, MODE>(cur.E, kb[i], WEIGHTED ? wb[i] : 1.f, acc);
-          if (MODE == kLossOnly && store) stash_coef(kb, i, c);
-        }
+  for (int k = 0; k < U; ++k) {
+    const float4 x = kb[off + k];
+    const float m = (k < cnt) ? 1.f : 0.f;
+    const float wt = WEIGHTED ? wb[off + k] * m : m;
+    float c, l;
+    pair_terms<LOSS, WEIGHTED, MODE, true>(E, x, wt, c, l);
+    if (MODE == kLossOnly && store && k < cnt) stash_coef(kb, off + k, c);
+    add_terms<MODE>(c, l, x, acc);
+  }
+  if (n_img == 1) {
+    warp_store(a.rec, h.info.z, acc, lane);
+  } else {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int ku = __shfl_up_sync(FULL, key, d);
+      const bool take = (lane >= d) && (ku == key);
+#pragma unroll
+      for (int c = 0; c < 10; ++c) {
+        const float v = __shfl_up_sync(FULL, acc[c], d);
+        if (take) acc[c] += v;
       }
-#pragma unroll 1
-      for (; q < r_in; ++q) {
-        const int i = 32 * q + lane;
-        const float c = accumulate<LOSS, WEIGHTED, MODE>(cur.E, kb[i], WEIGHTED ? wb[i] : 1.f, acc);
-        if (MODE == kLossOnly && store) stash_coef(kb, i, c);
-      }
-      r = r_in;
-      continue;
     }
-    // row r crosses an image-pair end, or is the partial last row
-    const int row_lo = base + 32 * r;
-    const int row_hi = min(row_lo + 32, wend);
-    const bool valid = row_lo + lane < wend;
-    const float4 x = valid ? kb[32 * r + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float wt = valid ? (WEIGHTED ? wb[32 * r + lane] : 1.f) : 0.f;
-    if (row_hi <= cur.end) {
-      const float c = accumulate<LOSS, WEIGHTED, MODE, true>(cur.E, x, wt, acc);
-      if (MODE == kLossOnly && store && valid) stash_coef(kb, 32 * r + lane, c);
-      ++r;
-      continue;
-    }
-    int jl_last = j;
-    while (end_uniform(h.endreg, a.seg_tab, info.x, jl_last) < row_hi) ++jl_last;
-    const int p = min(row_lo + lane, wend - 1);
-    int jl = j;
-    for (int t = j; t < jl_last; ++t) jl += (p >= end_uniform(h.endreg, a.seg_tab, info.x, t)) ? 1 : 0;
-    float El[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) El[k] = __shfl_sync(FULL, h.Ereg[k], jl & 31);   // all lanes take part
-    if (jl >= 32) {
-      const float4* e = a.seg_tab + 3 * (info.x + jl);
-      const float4 e0 = e[0], e1 = e[1], e2 = e[2];
-      El[0] = e0.x; El[1] = e0.y; El[2] = e0.z; El[3] = e0.w;
-      El[4] = e1.x; El[5] = e1.y; El[6] = e1.z; El[7] = e1.w;
-      El[8] = e2.x;
-    }
-    float v[10];
-#pragma unroll
-    for (int k = 0; k < 10; ++k) v[k] = 0.f;
-    if (valid) {
-      const float c = accumulate<LOSS, WEIGHTED, MODE, true>(El, x, wt, v);
-      if (MODE == kLossOnly && store) stash_coef(kb, 32 * r + lane, c);
-    }
-    // close the current image pair
-    float t10[10];
-#pragma unroll
-    for (int k = 0; k < 10; ++k) t10[k] = acc[k] + ((jl == j) ? v[k] : 0.f);
-    warp_store(a.rec, info.z + j, t10, lane);
-    // image pairs that start and end inside this row
-    for (int t = j + 1; t < jl_last; ++t) {
-#pragma unroll
-      for (int k = 0; k < 10; ++k) t10[k] = (jl == t) ? v[k] : 0.f;
-      warp_store(a.rec, info.z + t, t10, lane);
-    }
-    // open the last one
-#pragma unroll
-    for (int k = 0; k < 10; ++k) acc[k] = (jl == jl_last) ? v[k] : 0.f;
-    j = jl_last;
-    entry_uniform(h.Ereg, h.endreg, a.seg_tab, info.x, j, cur);
-    ++r;
+    const int key_next = __shfl_down_sync(FULL, key, 1);
+    if (lane == 31 || key_next != key) store_record(a.rec, h.info.z + key, acc);
   }
-  warp_store(a.rec, info.z + j, acc, lane);
-}
-
-// Lane-contiguous processing for warp runs that touch three or more image
-// pairs: lane l owns pairs [base + 15 l, base + 15 l + 15) (stride 15 float4 in
-// shared memory: conflict-free since 15 is odd).  A lane whose run crosses at
-// most one image-pair end splits it into a head part (its first image pair)
-// and a tail part with a branch-free two-accumulator loop; a lane crossing two
-// or more ends walks its pairs one by one and writes the image pairs that lie
-// wholly inside its run.  A segmented scan keyed by image pair then combines
-// the tails of consecutive lanes and absorbs heads, in fixed lane order.
-template <int U, int LOSS, bool WEIGHTED, int MODE>
-__device__ __forceinline__ void process_lanes(const DirectArgs& a, int w, int lane, const RunHead& h,
-                                              float4* kb, const float* wb, bool store) {
-  constexpr int WP = 32 * U;
-  const int base = w * WP;
-  const int4 info = h.info;
-  const int wend = min(base + WP, a.Z);
-  const int p0 = base + lane * U;
-  const int pend = min(p0 + U, wend);
-  const int j0 = h.rs - info.x;             // local image pair of the lane's first pair
-  float E0[9], E1[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    E0[k] = __shfl_sync(FULL, h.Ereg[k], j0 & 31);
-    E1[k] = __shfl_sync(FULL, h.Ereg[k], (j0 + 1) & 31);
-  }
-  const int end0 = __shfl_sync(FULL, h.endreg, j0 & 31);
-  const int end1 = __shfl_sync(FULL, h.endreg, (j0 + 1) & 31);
-  // split: pairs [p0, min(end0, pend)) are the head, the rest (if any) the tail
-  const bool one_part = pend <= end0;
-  const bool two_parts = !one_part && (j0 + 1 < 32) && (pend <= end1) && (end1 > end0);
-  const bool fast = (j0 < 32) && (one_part || two_parts);
-  float acc_h[10], acc_t[10];
-#pragma unroll
-  for (int k = 0; k < 10; ++k) {
-    acc_h[k] = 0.f;
-    acc_t[k] = 0.f;
-  }
-  int head_key = j0, key = j0;
-  bool has_head = false;
-  if (fast) {
-    const int b = min(end0, pend) - p0;    // head pairs (>= 1)
-    const int n = pend - p0;               // valid pairs of this lane (may be < U at the end)
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      const float4 x = kb[lane * U + k];
-      const bool in_head = k < b;
-      float E[9];
-#pragma unroll
-      for (int q = 0; q < 9; ++q) E[q] = in_head ? E0[q] : E1[q];
-      const float wt = (k < n) ? (WEIGHTED ? wb[lane * U + k] : 1.f) : 0.f;
-      float c, l;
-      pair_terms<LOSS, WEIGHTED, MODE, true>(E, x, wt, c, l);
-      if (MODE == kLossOnly && store && k < n) stash_coef(kb, lane * U + k, c);
-      const float ch = in_head ? c : 0.f, ct = c - ch;
-      const float lh = in_head ? l : 0.f, lt = l - lh;
-      add_terms<MODE>(ch, lh, x, acc_h);
-      add_terms<MODE>(ct, lt, x, acc_t);
-    }
-    if (two_parts) {
-      has_head = true;
-      key = j0 + 1;
-    } else {
-#pragma unroll
-      for (int k = 0; k < 10; ++k) acc_t[k] = acc_h[k];
-    }
-  } else if (p0 < wend) {
-    // two or more image-pair ends inside the lane's run: one pair at a time
-    int s = info.x + j0, sl = j0;
-    const float4* e = a.seg_tab + 3 * s;
-    float4 e0 = e[0], e1 = e[1], e2 = e[2];
-    int end = __float_as_int(e2.y);
-    for (int p = p0; p < pend; ++p) {
-      while (p >= end) {
-        if (!has_head) {
-#pragma unroll
-          for (int k = 0; k < 10; ++k) acc_h[k] = acc_t[k];
-          has_head = true;
-        } else {
-          store_record(a.rec, info.z + sl, acc_t);
-        }
-#pragma unroll
-        for (int k = 0; k < 10; ++k) acc_t[k] = 0.f;
-        ++s;
-        ++sl;
-        e = a.seg_tab + 3 * s;
-        e0 = e[0];
-        e1 = e[1];
-        e2 = e[2];
-        end = __float_as_int(e2.y);
-      }
-      const float Es[9] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w, e2.x};
-      const int i = lane * U + (p - p0);
-      const float c = accumulate<LOSS, WEIGHTED, MODE>(Es, kb[i], WEIGHTED ? wb[i] : 1.f, acc_t);
-      if (MODE == kLossOnly && store) stash_coef(kb, i, c);
-    }
-    key = sl;
-  }
-  // lanes past the end of the data keep key = j0 (the last image pair) and zeros
-
-  // segmented inclusive scan of the tails keyed by local image pair
-  float sc[10];
-#pragma unroll
-  for (int c = 0; c < 10; ++c) sc[c] = acc_t[c];
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int ku = __shfl_up_sync(FULL, key, d);
-    const bool take = (lane >= d) && (ku == key);
-#pragma unroll
-    for (int c = 0; c < 10; ++c) {
-      const float v = __shfl_up_sync(FULL, sc[c], d);
-      if (take) sc[c] += v;
-    }
-  }
-  const int key_next = __shfl_down_sync(FULL, key, 1);
-  const int hk_next = __shfl_down_sync(FULL, has_head ? head_key : -1, 1);
-  const int key_prev = __shfl_up_sync(FULL, key, 1);
-  const bool last_of_key = (lane == 31) || (key_next != key);
-  const bool absorb = (lane < 31) && (hk_next == key);
-#pragma unroll
-  for (int c = 0; c < 10; ++c) {
-    const float hv = __shfl_down_sync(FULL, acc_h[c], 1);
-    if (absorb) sc[c] += hv;
-  }
-  if (last_of_key) store_record(a.rec, info.z + key, sc);
-  if (has_head && (lane == 0 || key_prev != head_key)) store_record(a.rec, info.z + head_key, acc_h);
-}
-
-template <int U, int LOSS, bool WEIGHTED, int MODE>
-__device__ __forceinline__ void process(const DirectArgs& a, int w, int lane, const RunHead& h,
-                                        float4* kb, const float* wb) {
-  constexpr int WP = 32 * U, ROWS = U;
-  const bool store = (MODE == kLossOnly) && a.coef_out != nullptr;
-  if (h.info.y <= a.rows_max) process_rows<U, LOSS, WEIGHTED, MODE>(a, w, lane, h, kb, wb, store);
-  else process_lanes<U, LOSS, WEIGHTED, MODE>(a, w, lane, h, kb, wb, store);
   if (store) {
     // coalesced copy-out of the stashed coefficients
     __syncwarp();
-    const int base = w * WP;
+    const int len = h.info.y >> 8;
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) {
+    for (int r = 0; r < U; ++r) {
       const int i = 32 * r + lane;
-      if (base + i < a.Z) a.coef_out[base + i] = reinterpret_cast<const float*>(kb + i)[0];
+      if (i < len) a.coef_out[h.info.w + i] = reinterpret_cast<const float*>(kb + i)[0];
     }
   }
 }
 
+// Schedule of a warp (persistent, runs w, w + stride, ...): kStages shared-
+// memory buffers; while run k is processed, runs k + 1 .. k + kStages - 1 are
+// in flight, the E entries of run k + 1 and the header of run k + kStages are
+// being loaded, so that staging a run never waits on its header.  One
+// cp.async group is committed per iteration (empty past the last run), so
+// "at most kStages - 1 groups pending" always means run k has landed.
 template <int U, int LOSS, bool WEIGHTED, int MODE>
 __global__ void __launch_bounds__(WARPS * 32, kEaMinCtas) k_ea_direct(DirectArgs a) {
   constexpr int WP = 32 * U;
+  constexpr int S = kEaStages;
   extern __shared__ float4 smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  float4* kb = smem + wib * 2 * WP;
-  float* wb = WEIGHTED ? reinterpret_cast<float*>(smem + WARPS * 2 * WP) + wib * 2 * WP : nullptr;
+  float4* kb = smem + wib * S * WP;
+  float* wb = WEIGHTED ? reinterpret_cast<float*>(smem + WARPS * S * WP) + wib * S * WP : nullptr;
   const int stride = gridDim.x * WARPS;
   int w = blockIdx.x * WARPS + wib;
   if (w >= a.n_wruns) return;              // uniform per warp
   pdl_trigger();
-  RunHead head;
-  load_static_head(a, w, lane, head);
-  issue_rows<U, WEIGHTED>(a, w, lane, kb, wb);   // the keypoints do not depend on the predecessor
+  zero_buffers<U * S, WEIGHTED>(lane, kb, wb);
+  // q[0] = run w (current), q[k] = run w + k stride
+  RunHead q[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k)
+    if (w + k * stride < a.n_wruns) load_static_head(a, w + k * stride, lane, q[k]);
+#pragma unroll
+  for (int k = 0; k < S - 1; ++k) {        // the keypoints do not depend on the predecessor
+    if (w + k * stride < a.n_wruns) issue_run<U, WEIGHTED>(a, q[k].info, lane, kb + k * WP, WEIGHTED ? wb + k * WP : nullptr);
+    asm volatile("cp.async.commit_group;\n" ::);
+  }
   pdl_wait();
-  load_table_head(a, lane, head);
-  for (int it = 0; w < a.n_wruns; ++it, w += stride) {
-    const int cur = it & 1;
-    const int wn = w + stride;
-    RunHead next;
-    if (wn < a.n_wruns) {
-      load_static_head(a, wn, lane, next);
-      load_table_head(a, lane, next);
-      issue_rows<U, WEIGHTED>(a, wn, lane, kb + (cur ^ 1) * WP, WEIGHTED ? wb + (cur ^ 1) * WP : nullptr);
-      asm volatile("cp.async.wait_group 1;\n" ::);
-    } else {
-      asm volatile("cp.async.wait_group 0;\n" ::);
-    }
+  load_table_head(a, lane, q[0]);
+  int buf = 0;                             // buffer of run w
+  for (; w < a.n_wruns; w += stride) {
+    const int wl = w + (S - 1) * stride;   // the run to stage now
+    int bl = buf + (S - 1);
+    if (bl >= S) bl -= S;
+    if (wl < a.n_wruns)
+      issue_run<U, WEIGHTED>(a, q[S - 1].info, lane, kb + bl * WP, WEIGHTED ? wb + bl * WP : nullptr);
+    asm volatile("cp.async.commit_group;\n" ::);
+    RunHead fresh;                         // header of run w + S stride, loaded a run ahead
+    if (w + S * stride < a.n_wruns) load_static_head(a, w + S * stride, lane, fresh);
+    if (w + stride < a.n_wruns) load_table_head(a, lane, q[1]);
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(S - 1));
     __syncwarp();
-    process<U, LOSS, WEIGHTED, MODE>(a, w, lane, head, kb + cur * WP, WEIGHTED ? wb + cur * WP : nullptr);
-    __syncwarp();   // this buffer is refilled two warp runs later
-    head = next;
+    if ((q[0].info.y & 0xff) != 0)         // runs past the lanes in use are empty
+      process<U, LOSS, WEIGHTED, MODE>(a, lane, q[0], kb + buf * WP, WEIGHTED ? wb + buf * WP : nullptr);
+    __syncwarp();                          // this buffer is refilled S - 1 runs later
+#pragma unroll
+    for (int k = 0; k < S - 1; ++k) q[k] = q[k + 1];
+    q[S - 1] = fresh;
+    if (++buf == S) buf = 0;
   }
 }
 
@@ -635,13 +439,11 @@ static void launch_direct_u(const fm_problem* pr, const float* weights, float* c
   DirectArgs a;
   a.kp = pr->kp;
   a.wts = weights;
-  a.rows_max = pr->ea_rows_max;
-  a.run_seg = pr->run_seg;
+  a.lane_desc = pr->lane_desc;
   a.info = pr->wrun_info;
   a.seg_tab = pr->seg_tab;
   a.rec = pr->rec;
   a.coef_out = coef_out;
-  a.Z = (int)pr->Z;
   a.n_wruns = pr->n_wruns;
   const size_t smem = WARPS * smem_per_warp<U>(WEIGHTED);
   static int per_sm = 0;   // resident CTAs per SM (one device per process)
@@ -657,21 +459,30 @@ static void launch_direct_u(const fm_problem* pr, const float* weights, float* c
   launch_pdl(k_ea_direct<U, LOSS, WEIGHTED, MODE>, dim3(ctas), dim3(WARPS * 32), smem, s, a);
 }
 
-// the tile sizes the library is built with (pairs per lane, odd)
+// the tiles built into the library (pairs per lane, odd)
 template <int LOSS, bool WEIGHTED, int MODE>
 static void launch_direct_t(const fm_problem* pr, const float* weights, float* coef_out, cudaStream_t s) {
-  if (pr->ea_U == 11) launch_direct_u<11, LOSS, WEIGHTED, MODE>(pr, weights, coef_out, s);
-  else launch_direct_u<15, LOSS, WEIGHTED, MODE>(pr, weights, coef_out, s);
+  switch (pr->ea_U) {
+    case 11: launch_direct_u<11, LOSS, WEIGHTED, MODE>(pr, weights, coef_out, s); break;
+    case 21: launch_direct_u<21, LOSS, WEIGHTED, MODE>(pr, weights, coef_out, s); break;
+    default: launch_direct_u<15, LOSS, WEIGHTED, MODE>(pr, weights, coef_out, s); break;
+  }
+}
+
+template <int U>
+static int max_ctas_u() {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ea_direct<U, 0, false, kFull>, WARPS * 32,
+                                                WARPS * smem_per_warp<U>(false));
+  return per_sm > 0 ? per_sm : 1;
 }
 
 int direct_max_ctas_per_sm(const fm_problem* pr) {
-  const size_t smem = WARPS * (pr->ea_U == 11 ? smem_per_warp<11>(false) : smem_per_warp<15>(false));
-  int per_sm = 0;
-  if (pr->ea_U == 11)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ea_direct<11, 0, false, kFull>, WARPS * 32, smem);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ea_direct<15, 0, false, kFull>, WARPS * 32, smem);
-  return per_sm > 0 ? per_sm : 1;
+  switch (pr->ea_U) {
+    case 11: return max_ctas_u<11>();
+    case 21: return max_ctas_u<21>();
+    default: return max_ctas_u<15>();
+  }
 }
 
 template <int MODE>

@@ -19,9 +19,18 @@ namespace fm {
 #ifndef FM_EA_WARPS_PER_CTA
 #define FM_EA_WARPS_PER_CTA 2
 #endif
-constexpr int kEaPairsPerLane = FM_EA_PAIRS_PER_LANE;  // U: keypoint pairs per lane (odd)
-constexpr int kEaWarpPairs = 32 * kEaPairsPerLane;     // keypoint pairs per warp run
+constexpr int kEaPairsPerLane = FM_EA_PAIRS_PER_LANE;  // U: keypoint pairs per lane at most (odd)
+// the tiles U built into k_ea_direct (odd: stride-U float4 reads from shared
+// memory are free of bank conflicts)
+inline bool ea_tile_built(int U) { return U == 11 || U == 15 || U == 21; }
+// lane descriptor of k_ea_direct: offset | count << 10 | key << 15
+constexpr int kDescCntShift = 10, kDescKeyShift = 15;
 constexpr int kEaWarpsPerCta = FM_EA_WARPS_PER_CTA;
+// shared-memory stages of k_ea_direct per warp (warp runs in flight + 1)
+#ifndef FM_EA_STAGES
+#define FM_EA_STAGES 2
+#endif
+constexpr int kEaStages = FM_EA_STAGES;
 // register budget of k_ea_direct: at least this many CTAs per SM (shared
 // memory allows 7 at two warps per CTA, so 8 costs no occupancy and leaves
 // the compiler 128 registers to interleave a lane's pairs)
@@ -116,12 +125,11 @@ struct fm_problem {
   float* cy = nullptr;
 
   // direct epipolar kernel: tile (chosen by fm_autotune or fm_set_tuning) and tables
-  int ea_U = fm::kEaPairsPerLane;  // keypoint pairs per lane (11 or 15); a warp run is 32 U pairs
-  int ea_rows_max = 2;           // warp runs touching <= this many image pairs go row by row
+  int ea_U = fm::kEaPairsPerLane;  // keypoint pairs per lane at most (a tile built into the library)
   int ea_ctas_per_sm = 0;        // persistent CTAs per SM (0: as many as fit)
-  int n_wruns = 0;               // warp runs of 32 ea_U keypoint pairs
-  int* run_seg = nullptr;        // [n_wruns*32] image pair of each lane's first pair
-  int4* wrun_info = nullptr;     // [n_wruns] {first image pair, #image pairs, record base, 0}
+  int n_wruns = 0;               // warp runs of 32 lanes
+  int* lane_desc = nullptr;      // [n_wruns*32] offset | count << 10 | key << 15 of each lane
+  int4* wrun_info = nullptr;     // [n_wruns] {first image pair, n_img | len << 8, record base, first pair}
   int* seg_rec = nullptr;        // [2P] {first record, #records} per image pair
   int64_t n_rec = 0;
   float4* rec = nullptr;         // [n_rec*3] per-(warp run, image pair) partial sums
@@ -244,11 +252,18 @@ void launch_calibrate(const float* kp1, const float* kp2, const int* kp_pair, co
                       int64_t Z, int P, float4* out, int* err, cudaStream_t s);
 void launch_seg_offsets(const int* kp_pair, int64_t Z, int P, int* seg_off, int* err,
                         cudaStream_t s);
-void launch_run_tables(const int* seg_off, int P, int64_t Z, int n_wruns, int U, int* run_seg,
-                       int4* wrun_info, cudaStream_t s);
-void launch_seg_records(const int* seg_off, const int* run_seg, const int4* wrun_info, int P, int U,
-                        int* seg_rec, cudaStream_t s);
+// lane tables of the direct kernel: G [P+1] = exclusive scan of the lanes per
+// image pair, *T = lanes in use; then the lane descriptors and run headers of
+// n_runs warp runs (n_runs >= ceil(T / 32); runs past the lanes in use are
+// empty), the record bases, and seg_rec
+void launch_lane_scan(const int* seg_off, int P, int U, int* G, int* T, cudaStream_t s);
+void launch_lane_desc(const int* seg_off, const int* G, const int* T, int P, int U, int n_runs, int* desc,
+                      int4* wrun_info, cudaStream_t s);
+void launch_seg_records(const int* seg_off, const int* G, const int4* wrun_info, int P, int* seg_rec,
+                        cudaStream_t s);
 void launch_check_finite(const float* x, int64_t n, int* err, int bit, cudaStream_t s);
+// fills buf and reads it back, leaving L2 full of clean lines of buf
+void launch_l2_flush(void* buf, size_t bytes, int fill, cudaStream_t s);
 void launch_exclusive_scan_info(int4* wrun_info, int n, int64_t* total_out_dev, cudaStream_t s);
 
 // epipolar (fm_ea.cu)

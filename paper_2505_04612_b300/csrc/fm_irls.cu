@@ -33,28 +33,29 @@
 namespace fm {
 namespace {
 
-// one thread per lane run of U consecutive keypoint pairs (the runs of the
-// direct kernel); the run's first image pair comes from run_seg
-__global__ void k_ea_reweight(const float4* __restrict__ kp, const int* __restrict__ run_seg,
+// one thread per run of kReweightRun consecutive keypoint pairs; the image
+// pair of each pair comes from kp_seg (E reloaded when it changes)
+constexpr int kReweightRun = 8;
+
+__global__ void k_ea_reweight(const float4* __restrict__ kp, const int* __restrict__ kp_seg,
                               const float4* __restrict__ seg_tab, const int* __restrict__ pair_scene,
-                              int Z, int n_runs, int U, float tau, float delta, int irls, float* __restrict__ w,
+                              int Z, int n_runs, float tau, float delta, int irls, float* __restrict__ w,
                               unsigned long long* __restrict__ kept, const float* __restrict__ prob, float p_min) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   int my_kept = 0;
   int scene = -1;     // scene of the pairs counted in my_kept
   if (q < n_runs) {
-    const int p0 = q * U;
-    const int pend = min(p0 + U, Z);
-    int s = run_seg[q];
-    float4 e0 = __ldg(seg_tab + 3 * s), e1 = __ldg(seg_tab + 3 * s + 1), e2 = __ldg(seg_tab + 3 * s + 2);
-    int end = __float_as_int(e2.y);
+    const int p0 = q * kReweightRun;
+    const int pend = min(p0 + kReweightRun, Z);
+    int s = -1;
+    float4 e0 = make_float4(0.f, 0.f, 0.f, 0.f), e1 = e0, e2 = e0;
     for (int p = p0; p < pend; ++p) {
-      while (p >= end) {
-        ++s;
-        e0 = __ldg(seg_tab + 3 * s);
-        e1 = __ldg(seg_tab + 3 * s + 1);
-        e2 = __ldg(seg_tab + 3 * s + 2);
-        end = __float_as_int(e2.y);
+      const int sp = __ldg(kp_seg + p);
+      if (sp != s) {
+        s = sp;
+        e0 = seg_tab[3 * s];
+        e1 = seg_tab[3 * s + 1];
+        e2 = seg_tab[3 * s + 2];
       }
       const int sc = __ldg(pair_scene + s);
       if (sc != scene) {   // a run crossing a scene boundary (rare): flush the count
@@ -214,12 +215,10 @@ __global__ void k_ea_compact(const float* __restrict__ W, const float* __restric
 
 void launch_ea_reweight(const fm_problem* pr, float tau, float delta, int irls, float* w,
                         unsigned long long* kept, cudaStream_t s, const float* prob, float p_min) {
-  const int U = pr->ea_U;   // lane runs of the direct kernel's tables
-  const int n_runs = (int)((pr->Z + U - 1) / U);
+  const int n_runs = (int)((pr->Z + kReweightRun - 1) / kReweightRun);
   if (n_runs == 0) return;
-  k_ea_reweight<<<(n_runs + 255) / 256, 256, 0, s>>>(pr->kp, pr->run_seg, pr->seg_tab, pr->pair_scene,
-                                                     (int)pr->Z, n_runs, U, tau, delta, irls, w, kept, prob,
-                                                     p_min);
+  k_ea_reweight<<<(n_runs + 255) / 256, 256, 0, s>>>(pr->kp, pr->kp_seg, pr->seg_tab, pr->pair_scene, (int)pr->Z,
+                                                     n_runs, tau, delta, irls, w, kept, prob, p_min);
 }
 
 void launch_w_build(const fm_problem* pr, const float* w, float* W, cudaStream_t s) {

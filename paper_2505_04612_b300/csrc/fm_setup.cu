@@ -46,39 +46,91 @@ __global__ void k_seg_offsets(const int* __restrict__ kp_pair, int64_t Z, int P,
   }
 }
 
-// largest s in [0, P) with seg_off[s] <= p (the image pair holding pair p)
-__device__ __forceinline__ int segment_of(const int* __restrict__ seg_off, int P, int p) {
-  int lo = 0, hi = P - 1;
+// ---- lane tables of the direct kernel
+// Image pair n (m_n keypoint pairs) gets L_n = max(1, ceil(m_n / U)) lanes;
+// lane j of n holds pairs [seg_off[n] + j U, min(seg_off[n] + (j + 1) U,
+// seg_off[n + 1])).  G = exclusive scan of L orders all lanes; warp run w is
+// lanes [32 w, 32 w + 32).  A lane never crosses an image-pair end, so the
+// direct kernel needs no per-pair selection of E; an empty image pair keeps
+// one lane (with no pairs) so that a warp run spans at most 32 image pairs.
+
+__device__ __forceinline__ int lanes_of(const int* __restrict__ seg_off, int n, int U) {
+  const int m = seg_off[n + 1] - seg_off[n];
+  return m > 0 ? (m + U - 1) / U : 1;
+}
+
+// G[n] = sum_{n' < n} L_n' for n in [0, P]; *T = G[P].  One CTA, fixed order.
+__global__ void __launch_bounds__(1024) k_scan_lanes(const int* __restrict__ seg_off, int P, int U,
+                                                     int* __restrict__ G, int* __restrict__ T) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x;
+  const int per = (P + 1023) / 1024;
+  const int b = min(t * per, P), e = min(b + per, P);
+  int s = 0;
+  for (int n = b; n < e; ++n) s += lanes_of(seg_off, n, U);
+  part[t] = s;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {
+    const int v = (t >= d) ? part[t - d] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int run = (t == 0) ? 0 : part[t - 1];
+  for (int n = b; n < e; ++n) {
+    G[n] = run;
+    run += lanes_of(seg_off, n, U);
+  }
+  if (t == 1023) {
+    G[P] = part[1023];
+    *T = part[1023];
+  }
+}
+
+// one thread per lane slot g of n_slots = 32 n_runs (a warp is a warp run):
+// desc[g] = offset | count << 10 | key << 15 with offset the lane's first
+// pair relative to the run's first pair, count <= U its pairs, key its image
+// pair relative to the run's first one; info[w] = {first image pair,
+// n_img | len << 8, record base (filled by k_scan_info), first pair}.  Slots
+// at or past T (the lanes in use) copy the last lane in use with count 0;
+// a run with no lane in use gets n_img = 0.
+__global__ void k_lane_desc(const int* __restrict__ seg_off, const int* __restrict__ G,
+                            const int* __restrict__ T_dev, int P, int U, int n_slots, int* __restrict__ desc,
+                            int4* __restrict__ info) {
+  const unsigned FULL = 0xffffffffu;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;   // blockDim and n_slots are multiples of 32
+  const int lane = threadIdx.x & 31;
+  if (g - lane >= n_slots) return;                     // whole warp out of range
+  const int T = *T_dev;
+  const bool used = g < T;
+  const int gg = used ? g : T - 1;
+  int lo = 0, hi = P - 1;                                // largest n with G[n] <= gg
   while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (seg_off[mid] <= p) lo = mid; else hi = mid - 1;
+    const int mid = (lo + hi + 1) >> 1;
+    if (G[mid] <= gg) lo = mid; else hi = mid - 1;
   }
-  return lo;
+  const int n = lo;
+  const int start = seg_off[n] + (gg - G[n]) * U;
+  const int cnt = used ? min(U, seg_off[n + 1] - start) : 0;
+  const int base = __shfl_sync(FULL, start, 0);
+  const int s0 = __shfl_sync(FULL, n, 0);
+  const int key = n - s0;
+  desc[g] = (start - base) | (cnt << kDescCntShift) | (key << kDescKeyShift);
+  int end = used ? start + cnt - base : 0;
+  for (int d = 16; d > 0; d >>= 1) end = max(end, __shfl_xor_sync(FULL, end, d));
+  const int n_img = __any_sync(FULL, used) ? __shfl_sync(FULL, key, 31) + 1 : 0;
+  if (lane == 0) info[g >> 5] = make_int4(s0, n_img | (end << 8), 0, base);
 }
 
-__global__ void k_run_tables(const int* __restrict__ seg_off, int P, int Z, int n_wruns, int U,
-                             int* __restrict__ run_seg, int4* __restrict__ info) {
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n_wruns * 32) return;
-  int p0 = min(q * U, Z - 1);
-  int s = segment_of(seg_off, P, p0);
-  run_seg[q] = s;
-  if ((q & 31) == 0) {
-    int w = q >> 5;
-    int last = min((w + 1) * 32 * U, Z) - 1;
-    int sl = segment_of(seg_off, P, last);
-    info[w] = make_int4(s, sl - s + 1, 0, 0);
-  }
-}
-
-// exclusive scan of info[].y into info[].z, one CTA, fixed order
+// exclusive scan of the runs' image-pair counts (info[].y & 0xff) into
+// info[].z, one CTA, fixed order; *total = the number of records
 __global__ void k_scan_info(int4* info, int n, long long* total) {
   __shared__ long long part[1024];
   const int t = threadIdx.x;
   const int per = (n + 1023) / 1024;
-  const int b = t * per, e = min(b + per, n);
+  const int b = min(t * per, n), e = min(b + per, n);
   long long s = 0;
-  for (int k = b; k < e; ++k) s += info[k].y;
+  for (int k = b; k < e; ++k) s += info[k].y & 0xff;
   part[t] = s;
   __syncthreads();
   for (int d = 1; d < 1024; d <<= 1) {
@@ -91,26 +143,38 @@ __global__ void k_scan_info(int4* info, int n, long long* total) {
   for (int k = b; k < e; ++k) {
     int4 v = info[k];
     v.z = (int)run;
-    run += v.y;
+    run += v.y & 0xff;
     info[k] = v;
   }
   if (t == 1023) *total = part[1023];
 }
 
-__global__ void k_seg_records(const int* __restrict__ seg_off, const int* __restrict__ run_seg,
-                              const int4* __restrict__ info, int P, int WP, int* __restrict__ seg_rec) {
+// seg_rec[n] = {first record of image pair n, number of records}: one per
+// warp run its lanes fall in, consecutive in record order
+__global__ void k_seg_records(const int* __restrict__ seg_off, const int* __restrict__ G,
+                              const int4* __restrict__ info, int P, int* __restrict__ seg_rec) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= P) return;
-  int b = seg_off[n], e = seg_off[n + 1];
-  if (b == e) {
+  if (seg_off[n] == seg_off[n + 1]) {
     seg_rec[2 * n] = 0;
     seg_rec[2 * n + 1] = 0;
     return;
   }
-  int w0 = b / WP, w1 = (e - 1) / WP;
-  int4 i0 = info[w0];
+  const int w0 = G[n] >> 5, w1 = (G[n + 1] - 1) >> 5;
+  const int4 i0 = info[w0];
   seg_rec[2 * n] = i0.z + (n - i0.x);
   seg_rec[2 * n + 1] = w1 - w0 + 1;
+}
+
+// reads n16 16-byte words (an L2 sweep after a memset, so that the cache
+// holds clean lines); the store never happens for a buffer set by memset
+__global__ void k_l2_sweep(const uint4* __restrict__ p, int64_t n16, unsigned marker) {
+  unsigned acc = 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n16; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 v = p[k];
+    acc ^= v.x ^ v.y ^ v.z ^ v.w;
+  }
+  if (acc == marker) const_cast<uint4*>(p)[0].x = acc;
 }
 
 __global__ void k_check_finite(const float* __restrict__ x, int64_t n, int* err, int bit) {
@@ -145,20 +209,31 @@ void launch_seg_offsets(const int* kp_pair, int64_t Z, int P, int* seg_off, int*
   k_seg_offsets<<<grid_for(Z, 256), 256, 0, s>>>(kp_pair, Z, P, seg_off, err);
 }
 
-void launch_run_tables(const int* seg_off, int P, int64_t Z, int n_wruns, int U, int* run_seg,
-                       int4* wrun_info, cudaStream_t s) {
-  if (n_wruns == 0) return;
-  int n = n_wruns * 32;
-  k_run_tables<<<(n + 255) / 256, 256, 0, s>>>(seg_off, P, (int)Z, n_wruns, U, run_seg, wrun_info);
+void launch_lane_scan(const int* seg_off, int P, int U, int* G, int* T, cudaStream_t s) {
+  k_scan_lanes<<<1, 1024, 0, s>>>(seg_off, P, U, G, T);
+}
+
+void launch_lane_desc(const int* seg_off, const int* G, const int* T, int P, int U, int n_runs, int* desc,
+                      int4* wrun_info, cudaStream_t s) {
+  if (n_runs == 0) return;
+  const int n = 32 * n_runs;
+  k_lane_desc<<<(n + 255) / 256, 256, 0, s>>>(seg_off, G, T, P, U, n, desc, wrun_info);
 }
 
 void launch_exclusive_scan_info(int4* wrun_info, int n, int64_t* total_out_dev, cudaStream_t s) {
   k_scan_info<<<1, 1024, 0, s>>>(wrun_info, n, (long long*)total_out_dev);
 }
 
-void launch_seg_records(const int* seg_off, const int* run_seg, const int4* wrun_info, int P, int U,
-                        int* seg_rec, cudaStream_t s) {
-  k_seg_records<<<(P + 255) / 256, 256, 0, s>>>(seg_off, run_seg, wrun_info, P, 32 * U, seg_rec);
+void launch_seg_records(const int* seg_off, const int* G, const int4* wrun_info, int P, int* seg_rec,
+                        cudaStream_t s) {
+  if (P == 0) return;
+  k_seg_records<<<(P + 255) / 256, 256, 0, s>>>(seg_off, G, wrun_info, P, seg_rec);
+}
+
+void launch_l2_flush(void* buf, size_t bytes, int fill, cudaStream_t s) {
+  cudaMemsetAsync(buf, fill, bytes, s);
+  // every byte equals fill: an even number of equal words xors to 0, never to 1
+  k_l2_sweep<<<148 * 8, 256, 0, s>>>(static_cast<const uint4*>(buf), (int64_t)(bytes / 16) & ~int64_t(1), 1u);
 }
 
 void launch_check_finite(const float* x, int64_t n, int* err, int bit, cudaStream_t s) {

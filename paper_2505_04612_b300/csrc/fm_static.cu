@@ -71,16 +71,21 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
     return static_fail(FM_ERR_INVALID_ARG, "kp_dev and weights_dev must be 16-byte aligned");
   const int P = n_img_pairs;
   const int64_t Z = n_kp_pairs;
-  const int n_wruns = (int)((Z + fm::kEaWarpPairs - 1) / fm::kEaWarpPairs);
-  // records: at most one per (warp run, image pair it touches) <= P - 1 + n_wruns
+  // lanes in use <= sum_n max(1, ceil(m_n / U)) <= ceil(Z / U) + P; the warp
+  // runs past the lanes in use are empty.  Records: at most one per (warp
+  // run, image pair it touches) <= P - 1 + n_wruns
+  constexpr int U = fm::kEaPairsPerLane;
+  const int64_t lanes_max = (Z + U - 1) / U + P;
+  const int n_wruns = Z > 0 ? (int)((lanes_max + 31) / 32) : 0;
   const size_t b_tab = align256(sizeof(float4) * 3 * (size_t)P);
   const size_t b_run = align256(sizeof(int) * 32 * (size_t)n_wruns);
   const size_t b_info = align256(sizeof(int4) * (size_t)n_wruns);
   const size_t b_srec = align256(sizeof(int) * 2 * (size_t)P);
   const size_t b_rec = align256(sizeof(float4) * 3 * ((size_t)P + (size_t)n_wruns));
   const size_t b_loss = align256(sizeof(float) * (size_t)P);
+  const size_t b_g = align256(sizeof(int) * ((size_t)P + 2));
   const size_t b_total = align256(sizeof(long long));
-  const size_t need = b_tab + b_run + b_info + b_srec + b_rec + b_loss + b_total;
+  const size_t need = b_tab + b_run + b_info + b_srec + b_rec + b_loss + b_g + b_total;
   if (need > kStaticScratchBytes)
     return static_fail(FM_ERR_INVALID_ARG,
                        "problem needs " + std::to_string(need) + " bytes of scratch; the static array holds " +
@@ -106,7 +111,7 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
   v.pair_j = const_cast<int*>(pair_j_dev);
   v.seg_tab = reinterpret_cast<float4*>(p);
   p += b_tab;
-  v.run_seg = reinterpret_cast<int*>(p);
+  v.lane_desc = reinterpret_cast<int*>(p);
   p += b_run;
   v.wrun_info = reinterpret_cast<int4*>(p);
   p += b_info;
@@ -116,6 +121,9 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
   p += b_rec;
   v.seg_loss = reinterpret_cast<float*>(p);
   p += b_loss;
+  int* G = reinterpret_cast<int*>(p);   // [P+1] lane scan, then the lanes in use
+  int* T = G + P + 1;
+  p += b_g;
   long long* total = reinterpret_cast<long long*>(p);
   v.seg_grad = pair_grad_dev;
   v.n_wruns = n_wruns;
@@ -133,10 +141,11 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
   fm::g_plain_once = true;
   fm::launch_ea_tables(params_dev, v.pair_i, v.pair_j, v.seg_off, P, v.seg_tab, nullptr, s);
   if (n_wruns > 0) {
-    fm::launch_run_tables(v.seg_off, P, Z, n_wruns, fm::kEaPairsPerLane, v.run_seg, v.wrun_info, s);
+    fm::launch_lane_scan(v.seg_off, P, U, G, T, s);
+    fm::launch_lane_desc(v.seg_off, G, T, P, U, n_wruns, v.lane_desc, v.wrun_info, s);
     fm::launch_exclusive_scan_info(v.wrun_info, n_wruns, reinterpret_cast<int64_t*>(total), s);
   }
-  fm::launch_seg_records(v.seg_off, v.run_seg, v.wrun_info, P, fm::kEaPairsPerLane, v.seg_rec, s);
+  fm::launch_seg_records(v.seg_off, G, v.wrun_info, P, v.seg_rec, s);
   if (n_wruns > 0) fm::launch_ea_direct(&v, weights_dev, loss, s);
   fm::SegArgs sa = fm::seg_args(&v, params_dev);
   sa.pair_scale = nullptr;   // one scene: the scalar normaliser

@@ -113,7 +113,7 @@ class fm_result(ctypes.Structure):
 
 class fm_tuning(ctypes.Structure):
     _fields_ = [("pairs_per_lane", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("rows_max_img_pairs", ctypes.c_int32), ("us_per_eval", ctypes.c_float)]
+                ("us_per_eval", ctypes.c_float)]
 
 
 class fm_adam_opts(ctypes.Structure):
@@ -651,18 +651,16 @@ class Problem:
         """fm_autotune; returns the chosen fm_tuning as a dict."""
         t = fm_tuning()
         _check(lib().fm_autotune(self.handle, int(repeats), ctypes.byref(t)), self.handle)
-        return dict(pairs_per_lane=t.pairs_per_lane, ctas_per_sm=t.ctas_per_sm,
-                    rows_max_img_pairs=t.rows_max_img_pairs, us_per_eval=t.us_per_eval)
+        return dict(pairs_per_lane=t.pairs_per_lane, ctas_per_sm=t.ctas_per_sm, us_per_eval=t.us_per_eval)
 
-    def set_tuning(self, pairs_per_lane=15, ctas_per_sm=0, rows_max_img_pairs=2):
-        t = fm_tuning(pairs_per_lane, ctas_per_sm, rows_max_img_pairs, 0.0)
+    def set_tuning(self, pairs_per_lane=15, ctas_per_sm=0):
+        t = fm_tuning(pairs_per_lane, ctas_per_sm, 0.0)
         _check(lib().fm_set_tuning(self.handle, ctypes.byref(t)), self.handle)
 
     def get_tuning(self):
         t = fm_tuning()
         _check(lib().fm_get_tuning(self.handle, ctypes.byref(t)), self.handle)
-        return dict(pairs_per_lane=t.pairs_per_lane, ctas_per_sm=t.ctas_per_sm,
-                    rows_max_img_pairs=t.rows_max_img_pairs)
+        return dict(pairs_per_lane=t.pairs_per_lane, ctas_per_sm=t.ctas_per_sm)
 
     def graphs(self, enable=True):
         _check(lib().fm_graphs_enable(self.handle, int(bool(enable))), self.handle)

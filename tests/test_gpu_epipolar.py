@@ -140,8 +140,8 @@ def test_empty_image_pairs_first_middle_last():
 
 
 def test_many_tiny_image_pairs_per_warp_run():
-    """Image pairs of 1-3 keypoint pairs: a warp run of 480 pairs then holds
-    more than the 32 image pairs staged in shared memory (global fallback)."""
+    """Image pairs of 1-3 keypoint pairs: each takes a lane of its own, so a
+    warp run holds 32 image pairs and most lanes are partly empty."""
     sc = scene("c1", 7)
     rng = np.random.default_rng(7)
     pi, pj, kp_pair = [], [], np.zeros(sc.n_kp, np.int64)
