@@ -146,8 +146,9 @@ fm_status check_err_bits(fm_problem* pr) {
   if (bits & fm::kErrKpOrder) msg += "kp_img_pair is not non-decreasing; ";
   if (bits & fm::kErrKpNonFinite) msg += "a keypoint coordinate is not finite; ";
   if (bits & fm::kErrParamNonFinite) msg += "a parameter is not finite; ";
-  if (bits & fm::kErrMlpTimeout) {
-    msg += "a bounded wait of the tensor-core network kernel ran out; ";
+  if (bits & (fm::kErrMlpTimeout | fm::kErrEaTimeout)) {
+    if (bits & fm::kErrMlpTimeout) msg += "a bounded wait of the tensor-core network kernel ran out; ";
+    if (bits & fm::kErrEaTimeout) msg += "a bounded wait of the direct epipolar kernel ran out; ";
     return fail(pr, FM_ERR_TIMEOUT, msg);
   }
   fm_status st = (bits & (fm::kErrKpNonFinite | fm::kErrParamNonFinite)) &&
@@ -193,6 +194,8 @@ void release(fm_problem* pr) {
   pr->event_pool.clear();
   if (pr->h_loss) cudaFreeHost(pr->h_loss);
   pr->h_loss = nullptr;
+  if (pr->h_err) cudaFreeHost(pr->h_err);
+  pr->h_err = nullptr;
 }
 
 fm_status alloc_adam(fm_problem* pr, fm::AdamState& a, size_t n) {
@@ -516,6 +519,7 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   FM_ALLOC(pr, pr->merge_buf, 3 * (size_t)N + 4 * 64 * (size_t)S);
   FM_ALLOC(pr, pr->best_run, (size_t)N);
   FM_CUDA(pr, cudaMallocHost((void**)&pr->h_loss, sizeof(float) * S));
+  FM_CUDA(pr, cudaMallocHost((void**)&pr->h_err, sizeof(int)));
   {
     const int64_t z0 = pr->h_sc_kp_off[1] - pr->h_sc_kp_off[0];
     pr->ea_inv_z = z0 > 0 ? (float)(1.0 / (double)z0) : 0.f;
@@ -970,7 +974,10 @@ fm_status fm_loss_grad(fm_problem* pr, fm_stage st, const float* params, float* 
   const size_t nl = (size_t)runs * pr->S;
   if (loss) FM_CUDA(pr, cudaMemcpyAsync(pr->h_loss, pr->d_loss, sizeof(float) * nl, cudaMemcpyDeviceToHost, s));
   if (loss || (grad && !mem_on_device)) {
+    // the error bits travel with the results (no extra synchronisation)
+    FM_CUDA(pr, cudaMemcpyAsync(pr->h_err, pr->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     FM_CUDA(pr, cudaStreamSynchronize(s));
+    if (*pr->h_err) return check_err_bits(pr);
     if (loss) std::memcpy(loss, pr->h_loss, sizeof(float) * nl);
   }
   return FM_OK;
@@ -1782,7 +1789,9 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
   FM_LAUNCHED(pr);
   FM_CUDA(pr, cudaMemcpyAsync(res->R, dR, sizeof(float) * 9 * pr->N, cudaMemcpyDeviceToHost, pr->stream));
   FM_CUDA(pr, cudaMemcpyAsync(res->t, dt, sizeof(float) * 3 * pr->N, cudaMemcpyDeviceToHost, pr->stream));
+  FM_CUDA(pr, cudaMemcpyAsync(pr->h_err, pr->d_err, sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
   FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+  if (*pr->h_err) return check_err_bits(pr);
   if (res->cam_valid)
     for (int c = 0; c < pr->N; ++c) res->cam_valid[c] = pr->h_cam_valid[c];
   res->n_tracks = 0;

@@ -22,8 +22,8 @@
 //     run is 32 consecutive lanes (at most 32 U pairs, at most 32 image
 //     pairs), described by per-lane descriptors built once per problem;
 //   * persistent warps: each warp stages its next warp run into shared memory
-//     with cp.async (coalesced 512-B rows) while it processes the current one
-//     (double buffer);
+//     with one bulk copy (TMA) while it processes the current one (double
+//     buffer, mbarrier completion);
 //   * the E entries of the run's image pairs sit one per lane in registers;
 //     a lane takes its own once per run and accumulates its pairs with no
 //     per-pair selection;
@@ -85,6 +85,7 @@ struct DirectArgs {
   const float4* seg_tab;
   float4* rec;
   float* coef_out;       // kLossOnly: per-pair coefficients when not null
+  int* err;              // error bits (kErrEaTimeout)
   int n_wruns;
 };
 
@@ -169,11 +170,12 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
 }
 
-// shared memory per warp: kStages warp runs of keypoint pairs and their
-// weights; slot 32 r + l is filled by lane l (coalesced 512-B rows)
+// shared memory per warp: kStages warp runs of keypoint pairs (each filled by
+// one bulk copy), their weights (slot i filled by lane i % 32) and one
+// mbarrier per stage
 template <int U>
 constexpr size_t smem_per_warp(bool weighted) {
-  return kEaStages * 32 * U * (sizeof(float4) + (weighted ? sizeof(float) : 0));
+  return kEaStages * 32 * U * (sizeof(float4) + (weighted ? sizeof(float) : 0)) + kEaStages * sizeof(uint64_t);
 }
 
 // state of a warp run, loaded before its pairs are processed
@@ -203,10 +205,11 @@ __device__ __forceinline__ void load_table_head(const DirectArgs& a, int lane, R
   }
 }
 
-// both buffers start at zero, so that a lane reading past its own pairs
+// the buffers start at zero, so that a lane reading past its own pairs
 // (masked by a zero weight) only ever sees finite values: afterwards those
 // slots hold earlier keypoints (finite, checked at creation) or stashed
-// coefficients.  Slot 32 r + l is zeroed and later filled by lane l.
+// coefficients.  A weight slot is zeroed by the lane that later fills it; the
+// keypoint slots are ordered before the bulk copies by a proxy fence.
 template <int ROWS, bool WEIGHTED>
 __device__ __forceinline__ void zero_buffers(int lane, float4* kb, float* wb) {
 #pragma unroll
@@ -214,23 +217,6 @@ __device__ __forceinline__ void zero_buffers(int lane, float4* kb, float* wb) {
   if (WEIGHTED)
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) wb[32 * r + lane] = 0.f;
-}
-
-template <int U, bool WEIGHTED>
-__device__ __forceinline__ void issue_run(const DirectArgs& a, const int4 info, int lane, float4* kb, float* wb) {
-  const int base = info.w, len = info.y >> 8;
-#pragma unroll
-  for (int r = 0; r < U; ++r) {
-    const int i = 32 * r + lane;
-    if (i < len) cp_async16(kb + i, a.kp + base + i);
-  }
-  if (WEIGHTED) {
-#pragma unroll
-    for (int r = 0; r < U; ++r) {
-      const int i = 32 * r + lane;
-      if (i < len) cp_async4(wb + i, a.wts + base + i);
-    }
-  }
 }
 
 // The coefficient of pair base + i goes into the x component of its own
@@ -298,12 +284,56 @@ __device__ __forceinline__ void process(const DirectArgs& a, int lane, const Run
   }
 }
 
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void bar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
+  uint32_t d;
+  asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(d) : "r"(bar), "r"(parity) : "memory");
+  return d != 0;
+}
+constexpr int kBarPolls = 1 << 20;
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+  for (int i = 0; i < kBarPolls; ++i)
+    if (bar_try(bar, parity)) return true;
+  return false;
+}
+
+// lane 0 stages run `info`'s keypoint pairs with one bulk copy completing on bar
+__device__ __forceinline__ void issue_bulk(const DirectArgs& a, int4 info, int lane, float4* kb, uint32_t bar) {
+  if (lane == 0) {
+    const int base = info.w, len = info.y >> 8;
+    bar_expect_tx(bar, 16u * (uint32_t)len);   // len == 0: the arrive alone completes the phase
+    if (len > 0)
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                   ::"r"(smem_u32(kb)), "l"(a.kp + base), "r"(16u * (uint32_t)len), "r"(bar) : "memory");
+  }
+}
+
+template <int U>
+__device__ __forceinline__ void issue_weights(const DirectArgs& a, int4 info, int lane, float* wb) {
+  const int base = info.w, len = info.y >> 8;
+#pragma unroll
+  for (int r = 0; r < U; ++r) {
+    const int i = 32 * r + lane;
+    if (i < len) cp_async4(wb + i, a.wts + base + i);
+  }
+}
+
 // Schedule of a warp (persistent, runs w, w + stride, ...): kStages shared-
-// memory buffers; while run k is processed, runs k + 1 .. k + kStages - 1 are
-// in flight, the E entries of run k + 1 and the header of run k + kStages are
-// being loaded, so that staging a run never waits on its header.  One
-// cp.async group is committed per iteration (empty past the last run), so
-// "at most kStages - 1 groups pending" always means run k has landed.
+// memory buffers, each with an mbarrier.  One lane stages a run with a single
+// bulk copy (TMA, cp.async.bulk) that completes on the buffer's mbarrier;
+// while run k is processed, runs k + 1 .. k + kStages - 1 are in flight and
+// the E entries of run k + 1 and the header of run k + kStages are being
+// loaded, so that staging never waits on a header.  Weights (4 B per pair,
+// not 16-B aligned per run) come with per-lane cp.async.  Every mbarrier wait
+// is bounded: past the bound the warp sets kErrEaTimeout, waits (bounded) for
+// its copies in flight and leaves.
 template <int U, int LOSS, bool WEIGHTED, int MODE>
 __global__ void __launch_bounds__(WARPS * 32, kEaMinCtas) k_ea_direct(DirectArgs a) {
   constexpr int WP = 32 * U;
@@ -313,44 +343,78 @@ __global__ void __launch_bounds__(WARPS * 32, kEaMinCtas) k_ea_direct(DirectArgs
   const int wib = threadIdx.x >> 5;
   float4* kb = smem + wib * S * WP;
   float* wb = WEIGHTED ? reinterpret_cast<float*>(smem + WARPS * S * WP) + wib * S * WP : nullptr;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<float*>(smem + WARPS * S * WP) +
+                                               (WEIGHTED ? WARPS * S * WP : 0)) + wib * S;
   const int stride = gridDim.x * WARPS;
   int w = blockIdx.x * WARPS + wib;
   if (w >= a.n_wruns) return;              // uniform per warp
   pdl_trigger();
+  if (lane == 0) {
+#pragma unroll
+    for (int b = 0; b < S; ++b) bar_init(smem_u32(bars + b));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
   zero_buffers<U * S, WEIGHTED>(lane, kb, wb);
-  // q[0] = run w (current), q[k] = run w + k stride
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  __syncwarp();
   RunHead q[S];
 #pragma unroll
   for (int k = 0; k < S; ++k)
     if (w + k * stride < a.n_wruns) load_static_head(a, w + k * stride, lane, q[k]);
+  unsigned pending = 0;                    // buffers with a bulk copy not yet waited for
 #pragma unroll
-  for (int k = 0; k < S - 1; ++k) {        // the keypoints do not depend on the predecessor
-    if (w + k * stride < a.n_wruns) issue_run<U, WEIGHTED>(a, q[k].info, lane, kb + k * WP, WEIGHTED ? wb + k * WP : nullptr);
-    asm volatile("cp.async.commit_group;\n" ::);
+  for (int k = 0; k < S - 1; ++k) {
+    if (w + k * stride < a.n_wruns) {
+      issue_bulk(a, q[k].info, lane, kb + k * WP, smem_u32(bars + k));
+      pending |= 1u << k;
+      if (WEIGHTED) issue_weights<U>(a, q[k].info, lane, wb + k * WP);
+    }
+    if (WEIGHTED) asm volatile("cp.async.commit_group;\n" ::);
   }
   pdl_wait();
   load_table_head(a, lane, q[0]);
-  int buf = 0;                             // buffer of run w
+  int buf = 0;
+  unsigned phase = 0;                      // parity bit per buffer
+  bool ok = true;
   for (; w < a.n_wruns; w += stride) {
-    const int wl = w + (S - 1) * stride;   // the run to stage now
+    const int wl = w + (S - 1) * stride;
     int bl = buf + (S - 1);
     if (bl >= S) bl -= S;
-    if (wl < a.n_wruns)
-      issue_run<U, WEIGHTED>(a, q[S - 1].info, lane, kb + bl * WP, WEIGHTED ? wb + bl * WP : nullptr);
-    asm volatile("cp.async.commit_group;\n" ::);
-    RunHead fresh;                         // header of run w + S stride, loaded a run ahead
+    if (wl < a.n_wruns) {
+      issue_bulk(a, q[S - 1].info, lane, kb + bl * WP, smem_u32(bars + bl));
+      pending |= 1u << bl;
+      if (WEIGHTED) issue_weights<U>(a, q[S - 1].info, lane, wb + bl * WP);
+    }
+    if (WEIGHTED) asm volatile("cp.async.commit_group;\n" ::);
+    RunHead fresh;
     if (w + S * stride < a.n_wruns) load_static_head(a, w + S * stride, lane, fresh);
     if (w + stride < a.n_wruns) load_table_head(a, lane, q[1]);
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(S - 1));
+    ok = bar_wait(smem_u32(bars + buf), (phase >> buf) & 1u);
+    if (!__all_sync(FULL, ok)) { ok = false; break; }
+    phase ^= 1u << buf;
+    pending &= ~(1u << buf);
+    if (WEIGHTED) asm volatile("cp.async.wait_group %0;\n" ::"n"(S - 1));
     __syncwarp();
     if ((q[0].info.y & 0xff) != 0)         // runs past the lanes in use are empty
       process<U, LOSS, WEIGHTED, MODE>(a, lane, q[0], kb + buf * WP, WEIGHTED ? wb + buf * WP : nullptr);
-    __syncwarp();                          // this buffer is refilled S - 1 runs later
+    // the buffer's generic reads and stash writes come before the next bulk
+    // copy into it (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncwarp();
 #pragma unroll
     for (int k = 0; k < S - 1; ++k) q[k] = q[k + 1];
     q[S - 1] = fresh;
     if (++buf == S) buf = 0;
   }
+  if (!ok) {
+    // a wait ran out: record it, then give every copy still in flight one
+    // more bounded wait before the warp leaves its shared memory
+    if (lane == 0) atomicOr(a.err, kErrEaTimeout);
+#pragma unroll
+    for (int b = 0; b < S; ++b)
+      if (pending & (1u << b)) bar_wait(smem_u32(bars + b), (phase >> b) & 1u);
+  }
+  if (WEIGHTED) asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
 // per image pair: sum its records -- or take dL/dE_n from a saved copy --
@@ -444,6 +508,7 @@ static void launch_direct_u(const fm_problem* pr, const float* weights, float* c
   a.seg_tab = pr->seg_tab;
   a.rec = pr->rec;
   a.coef_out = coef_out;
+  a.err = pr->d_err;
   a.n_wruns = pr->n_wruns;
   const size_t smem = WARPS * smem_per_warp<U>(WEIGHTED);
   static int per_sm = 0;   // resident CTAs per SM (one device per process)

@@ -54,6 +54,7 @@ enum : int {
   kErrKpNonFinite = 4,   // keypoint not finite
   kErrParamNonFinite = 8,
   kErrMlpTimeout = 16,   // a bounded wait of the tensor-core network kernel ran out
+  kErrEaTimeout = 32,    // a bounded wait of the direct epipolar kernel ran out
 };
 
 enum KernelId : int {
@@ -206,6 +207,7 @@ struct fm_problem {
   float* scratch_grad = nullptr;    // [max(m,1)*N*9]
   float* d_loss = nullptr;          // [max(m,1)*S]
   float* h_loss = nullptr;          // pinned [max(m,1)*S]
+  int* h_err = nullptr;             // pinned copy of d_err
   int* d_err = nullptr;             // device error bits
 };
 

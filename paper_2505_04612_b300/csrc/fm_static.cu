@@ -125,6 +125,7 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
   int* T = G + P + 1;
   p += b_g;
   long long* total = reinterpret_cast<long long*>(p);
+  v.d_err = reinterpret_cast<int*>(total + 1);   // error bits of bounded waits (not reported: the call is asynchronous)
   v.seg_grad = pair_grad_dev;
   v.n_wruns = n_wruns;
   cudaStream_t s = v.stream;
