@@ -1,5 +1,6 @@
 // Host runtime of the C ABI declared in include/fastmap.h.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -196,6 +197,9 @@ void release(fm_problem* pr) {
   pr->h_loss = nullptr;
   if (pr->h_err) cudaFreeHost(pr->h_err);
   pr->h_err = nullptr;
+  if (pr->h_lg_in) cudaFreeHost(pr->h_lg_in);
+  if (pr->h_lg_grad) cudaFreeHost(pr->h_lg_grad);
+  pr->h_lg_in = pr->h_lg_grad = nullptr;
 }
 
 fm_status alloc_adam(fm_problem* pr, fm::AdamState& a, size_t n) {
@@ -951,6 +955,87 @@ fm_status fm_ea_get_weights(fm_problem* pr, float* out, int32_t on_device, float
   return FM_OK;
 }
 
+static fm_status replay(fm_problem* pr, cudaGraphExec_t exec);
+static void evict_lru(fm_problem* pr);
+
+// waits for the problem's stream: polls for up to 5 ms (a synchronous call
+// that returns results to the host is latency-bound; a blocking wait adds the
+// host's wake-up latency), then blocks
+static fm_status wait_stream(fm_problem* pr) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t q = cudaStreamQuery(pr->stream);
+    if (q == cudaSuccess) return FM_OK;
+    if (q != cudaErrorNotReady) return fail(pr, FM_ERR_CUDA, std::string("cudaStreamQuery: ") + cudaGetErrorString(q));
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(5)) break;
+  }
+  FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+  return FM_OK;
+}
+static fm_status capture_loss_grad(fm_problem* pr, fm_stage st, size_t count, size_t nl, bool want_loss,
+                                   bool want_grad, fm_problem::GraphEntry* out);
+
+// fm_loss_grad with host buffers through a captured graph (from the second
+// call at an epoch on); *done = false leaves the call to the direct path
+static fm_status loss_grad_graph(fm_problem* pr, fm_stage st, const float* params, float* loss, float* grad,
+                                 size_t count, size_t nl, bool* done) {
+  *done = false;
+  // lazily built state is settled by a direct evaluation first
+  if (st == FM_STAGE_TRANSLATION && !pr->trn_target_valid) return FM_OK;
+  if (st == FM_STAGE_EPIPOLAR && pr->ea_loss == FM_EA_COMPACT && !pr->W_valid) return FM_OK;
+  const int flags = (loss ? 1 : 0) | (grad ? 2 : 0);
+  fm_problem::GraphEntry* g = nullptr;
+  for (auto& e : pr->graphs)
+    if (e.kind == 1 && e.stage == (int)st && e.flags == flags && e.epoch == pr->graph_epoch && e.exec) g = &e;
+  if (!g) {
+    // the first call at an epoch runs directly: it settles lazily built state
+    // (the compact form's W, the translation targets) outside any graph
+    if (pr->lg_seen[st] != pr->graph_epoch) {
+      pr->lg_seen[st] = pr->graph_epoch;
+      return FM_OK;
+    }
+    if (pr->h_lg_cap < count) {
+      if (pr->h_lg_in) cudaFreeHost(pr->h_lg_in);
+      if (pr->h_lg_grad) cudaFreeHost(pr->h_lg_grad);
+      pr->h_lg_in = pr->h_lg_grad = nullptr;
+      pr->h_lg_cap = 0;
+      FM_CUDA(pr, cudaMallocHost((void**)&pr->h_lg_in, sizeof(float) * count));
+      FM_CUDA(pr, cudaMallocHost((void**)&pr->h_lg_grad, sizeof(float) * count));
+      pr->h_lg_cap = count;
+      for (auto& e : pr->graphs)   // graphs of the old buffers
+        if (e.kind == 1 && e.exec) {
+          cudaGraphExecDestroy(e.exec);
+          e.exec = nullptr;
+        }
+    }
+    evict_lru(pr);
+    fm_problem::GraphEntry e;
+    e.stage = (int)st;
+    e.kind = 1;
+    e.flags = flags;
+    e.epoch = pr->graph_epoch;
+    fm_status r = capture_loss_grad(pr, st, count, nl, loss != nullptr, grad != nullptr, &e);
+    if (r != FM_OK) return r;
+    pr->graphs.push_back(e);
+    g = &pr->graphs.back();
+  }
+  g->last_use = ++pr->graph_clock;
+  std::memcpy(pr->h_lg_in, params, sizeof(float) * count);
+  // one launch on the problem's stream (stream order covers the copies in and
+  // out); the wait spins first, which avoids the blocking wake-up latency
+  FM_CUDA(pr, cudaGraphLaunch(g->exec, pr->stream));
+  fm::g_plain_once = true;
+  for (int k = 0; k < fm::kKCount; ++k) pr->k_launches[k] += g->counts[k];
+  pr->graph_replays += 1;
+  fm_status r = wait_stream(pr);
+  if (r != FM_OK) return r;
+  if (*pr->h_err) return check_err_bits(pr);
+  if (grad) std::memcpy(grad, pr->h_lg_grad, sizeof(float) * count);
+  if (loss) std::memcpy(loss, pr->h_loss, sizeof(float) * nl);
+  *done = true;
+  return FM_OK;
+}
+
 fm_status fm_loss_grad(fm_problem* pr, fm_stage st, const float* params, float* loss, float* grad,
                        int32_t mem_on_device) {
   fm::g_plain_once = true;
@@ -959,6 +1044,12 @@ fm_status fm_loss_grad(fm_problem* pr, fm_stage st, const float* params, float* 
   if (!params) return fail(pr, FM_ERR_INVALID_ARG, "params is NULL");
   cudaStream_t s = pr->stream;
   const size_t count = (size_t)stage_dim(st) * pr->N * (st == FM_STAGE_TRANSLATION ? pr->trn_runs : 1);
+  if (!mem_on_device && (loss || grad) && pr->use_graphs && !pr->timing) {
+    bool done = false;
+    const size_t nl = (size_t)((st == FM_STAGE_TRANSLATION) ? pr->trn_runs : 1) * pr->S;
+    fm_status e = loss_grad_graph(pr, st, params, loss, grad, count, nl, &done);
+    if (e != FM_OK || done) return e;
+  }
   const float* p = params;
   if (!mem_on_device) {
     FM_CUDA(pr, cudaMemcpyAsync(pr->scratch_params, params, sizeof(float) * count, cudaMemcpyHostToDevice, s));
@@ -976,7 +1067,8 @@ fm_status fm_loss_grad(fm_problem* pr, fm_stage st, const float* params, float* 
   if (loss || (grad && !mem_on_device)) {
     // the error bits travel with the results (no extra synchronisation)
     FM_CUDA(pr, cudaMemcpyAsync(pr->h_err, pr->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    FM_CUDA(pr, cudaStreamSynchronize(s));
+    fm_status w = wait_stream(pr);
+    if (w != FM_OK) return w;
     if (*pr->h_err) return check_err_bits(pr);
     if (loss) std::memcpy(loss, pr->h_loss, sizeof(float) * nl);
   }
@@ -1162,23 +1254,75 @@ static fm_status capture_graph(fm_problem* pr, fm_stage st, const fm_adam_opts* 
   return FM_OK;
 }
 
+static void evict_lru(fm_problem* pr) {
+  constexpr size_t kMaxGraphs = 16;
+  if (pr->graphs.size() < kMaxGraphs) return;
+  size_t lru = 0;
+  for (size_t k = 1; k < pr->graphs.size(); ++k)
+    if (pr->graphs[k].last_use < pr->graphs[lru].last_use) lru = k;
+  if (pr->graphs[lru].exec) cudaGraphExecDestroy(pr->graphs[lru].exec);
+  pr->graphs.erase(pr->graphs.begin() + lru);
+}
+
+// fm_loss_grad with host buffers as one graph: parameters in from the pinned
+// staging buffer, the evaluation, gradient / loss / error word out to pinned
+// buffers.  Replaying it costs one launch instead of one per copy and kernel.
+static fm_status capture_loss_grad(fm_problem* pr, fm_stage st, size_t count, size_t nl, bool want_loss,
+                                   bool want_grad, fm_problem::GraphEntry* out) {
+  if (!pr->cap_stream) FM_CUDA(pr, cudaStreamCreateWithFlags(&pr->cap_stream, cudaStreamNonBlocking));
+  int64_t before[fm::kKCount];
+  std::memcpy(before, pr->k_launches, sizeof(before));
+  cudaStream_t orig = pr->stream;
+  pr->stream = pr->cap_stream;
+  cudaStream_t s = pr->cap_stream;
+  cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  fm_status e = FM_OK;
+  const bool was = fm::g_capturing;
+  fm::g_capturing = true;
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(pr->scratch_params, pr->h_lg_in, sizeof(float) * count,
+                                              cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess)
+    e = evaluate(pr, st, pr->scratch_params, want_grad ? pr->scratch_grad : nullptr, nullptr, nullptr,
+                 want_loss ? pr->d_loss : nullptr);
+  if (ce == cudaSuccess && e == FM_OK && want_grad)
+    ce = cudaMemcpyAsync(pr->h_lg_grad, pr->scratch_grad, sizeof(float) * count, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess && e == FM_OK && want_loss)
+    ce = cudaMemcpyAsync(pr->h_loss, pr->d_loss, sizeof(float) * nl, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess && e == FM_OK)
+    ce = cudaMemcpyAsync(pr->h_err, pr->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  fm::g_capturing = was;
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce2 = cudaStreamEndCapture(s, &graph);
+  pr->stream = orig;
+  for (int k = 0; k < fm::kKCount; ++k) {
+    out->counts[k] = pr->k_launches[k] - before[k];
+    pr->k_launches[k] = before[k];
+  }
+  if (e != FM_OK || ce != cudaSuccess || ce2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (e != FM_OK) return e;
+    return fail(pr, FM_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
+  }
+  cudaError_t ci = cudaGraphInstantiate(&out->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ci != cudaSuccess) {
+    out->exec = nullptr;
+    return fail(pr, FM_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ci));
+  }
+  return FM_OK;
+}
+
 static fm_status graph_for(fm_problem* pr, fm_stage st, const fm_adam_opts* opts, float* params,
                            fm::AdamState* adam, fm_problem::GraphEntry** g) {
   for (auto& e : pr->graphs)
-    if (e.stage == (int)st && e.lr == opts->lr && e.b1 == opts->beta1 && e.b2 == opts->beta2 &&
+    if (e.kind == 0 && e.stage == (int)st && e.lr == opts->lr && e.b1 == opts->beta1 && e.b2 == opts->beta2 &&
         e.eps == opts->eps && e.epoch == pr->graph_epoch && e.exec) {
       e.last_use = ++pr->graph_clock;
       *g = &e;
       return FM_OK;
     }
-  constexpr size_t kMaxGraphs = 16;
-  if (pr->graphs.size() >= kMaxGraphs) {   // evict the least recently used
-    size_t lru = 0;
-    for (size_t k = 1; k < pr->graphs.size(); ++k)
-      if (pr->graphs[k].last_use < pr->graphs[lru].last_use) lru = k;
-    if (pr->graphs[lru].exec) cudaGraphExecDestroy(pr->graphs[lru].exec);
-    pr->graphs.erase(pr->graphs.begin() + lru);
-  }
+  evict_lru(pr);
   fm_problem::GraphEntry e;
   e.stage = (int)st;
   e.lr = opts->lr;

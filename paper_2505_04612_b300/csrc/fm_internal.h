@@ -188,6 +188,8 @@ struct fm_problem {
   // captured iteration graphs of fm_step (see fm_api.cu)
   struct GraphEntry {
     int stage = 0;
+    int kind = 0;                 // 0: 16 Adam iterations (fm_step); 1: fm_loss_grad with host buffers
+    int flags = 0;                // kind 1: 1 loss, 2 gradient
     float lr = 0.f, b1 = 0.f, b2 = 0.f, eps = 0.f;
     uint64_t epoch = 0;
     cudaGraphExec_t exec = nullptr;
@@ -201,6 +203,13 @@ struct fm_problem {
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t graph_in = nullptr, graph_out = nullptr;   // orders replays by completion
   int64_t graph_replays = 0;
+  // fm_loss_grad with host buffers: pinned staging of the parameters and the
+  // gradient (captured by its graphs), and the epoch each stage was last
+  // evaluated at without a graph (a graph is captured on the second call)
+  float* h_lg_in = nullptr;
+  float* h_lg_grad = nullptr;
+  size_t h_lg_cap = 0;               // floats in each
+  uint64_t lg_seen[3] = {0, 0, 0};
 
   // scratch
   float* scratch_params = nullptr;  // [max(m,1)*N*9] parameters of fm_loss_grad

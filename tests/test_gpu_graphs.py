@@ -93,3 +93,48 @@ def test_weighted_direct_steps_repeatable(loss):
             outs.append(pr.get_params(F.FM_STAGE_EPIPOLAR).cpu().numpy())
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
+
+
+def test_host_loss_grad_graph_is_bitwise_identical():
+    """fm_loss_grad with host buffers runs directly on the first call at an
+    epoch and through a captured graph afterwards: every call, for every
+    stage and after every change of captured state (loss form, weights,
+    translation runs), returns the bits of the device-buffer path."""
+    import torch
+    from paper_2505_04612_b300 import fastmap as F
+    sc = make_scene("c1", 3)
+    rel_R, rel_t = gt_relative_poses(sc, rot_noise_deg=0.5, dir_noise_deg=0.5, seed=5)
+    rng = np.random.default_rng(2)
+    p6 = (gt_params6(sc) + rng.normal(0, 0.05, size=(sc.n_cams, 6))).astype(np.float32).reshape(-1)
+    pe = perturbed_params_ea(sc, 4).astype(np.float32).reshape(-1)
+
+    def same(pr, stage, host):
+        dev = torch.from_numpy(host).cuda()
+        Ld, gd = pr.loss_grad(stage, dev)
+        for _ in range(4):   # direct, capture + replay, replays
+            Lh, gh = pr.loss_grad(stage, host)
+            np.testing.assert_array_equal(np.asarray(Lh), np.asarray(Ld))
+            np.testing.assert_array_equal(gh, gd.cpu().numpy())
+        Lg, _ = pr.loss_grad(stage, host, want_grad=False)   # loss only: another graph
+        np.testing.assert_array_equal(np.asarray(Lg), np.asarray(Ld))
+
+    with G.make_problem(sc, rel_R=rel_R.astype(np.float32), rel_t=rel_t.astype(np.float32)) as pr:
+        same(pr, F.FM_STAGE_ROTATION, p6)
+        same(pr, F.FM_STAGE_ROTATION, (p6 * 1.01).astype(np.float32))   # other parameters, same graph
+        pr.set_params(F.FM_STAGE_ROTATION, torch.from_numpy(p6).cuda())
+        pr.set_translation_runs(2)
+        pr.translation_random_init(3)
+        t = pr.get_params(F.FM_STAGE_TRANSLATION).cpu().numpy().reshape(-1)
+        same(pr, F.FM_STAGE_TRANSLATION, t)
+        pr.set_translation_runs(3)
+        pr.translation_random_init(4)
+        same(pr, F.FM_STAGE_TRANSLATION, pr.get_params(F.FM_STAGE_TRANSLATION).cpu().numpy().reshape(-1))
+        for loss in (F.FM_EA_L1, F.FM_EA_L2):
+            pr.set_ea_loss(loss)
+            same(pr, F.FM_STAGE_EPIPOLAR, pe)
+        pr.set_ea_weights(rng.uniform(0.0, 2.0, sc.n_kp).astype(np.float32))
+        same(pr, F.FM_STAGE_EPIPOLAR, pe)
+        pr.set_params(F.FM_STAGE_EPIPOLAR, torch.from_numpy(pe).cuda())
+        pr.reweight(0.05, 1e-5)
+        pr.set_ea_loss(F.FM_EA_COMPACT)
+        same(pr, F.FM_STAGE_EPIPOLAR, pe)
