@@ -54,7 +54,7 @@ def args_():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2_5m", help="c2_5m (default), batch_c4 or learned_c5")
+    ap.add_argument("--config", default="c2_5m", help="c2_5m (default), batch_c4, learned_c5 or mlp_c2_5m")
     ap.add_argument("--train-scenes", type=int, default=200)
     ap.add_argument("--eval-cams", type=int, default=3000)
     ap.add_argument("--eval-points", type=int, default=1_000_000)
@@ -397,6 +397,71 @@ def run_batch(a):
     print(json.dumps(line), flush=True)
 
 
+def run_mlp(a):
+    """--config mlp_c2_5m: the learned inlier network's inference over every
+    keypoint pair of the c2_5m scene (fm_mlp_eval with probabilities: the
+    per-image-pair feature tables, then one tcgen05 kernel computing each
+    pair's 8 features and the 8-64-64-1 GELU network), random-init weights.
+    Reports keypoint-pair evaluations/s and the tensor-core roofline of the
+    network kernel (bf16 products: 2 (16*64 + 64*64) flop per pair with the
+    features padded to K = 16), which is far from the bound: the kernel is
+    limited by the 128 exact-erf GELUs per pair on the FP32 pipe."""
+    import torch
+    from paper_2505_04612_b300 import build as B
+    B.build()
+    from paper_2505_04612_b300 import fastmap as F
+    from oracle import mlp as M   # random initial weights only (the oracle's initialiser)
+    sc, params = make_workload("c2_5m", a.seed)
+    Z = sc.n_kp
+    dev = torch.device("cuda", 0)
+    flush_w = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush_r = torch.zeros(64 << 20, dtype=torch.float32, device=dev)
+
+    def flush():
+        flush_w.zero_()
+        flush_r.sum()
+        torch.cuda._sleep(1_000_000)
+
+    with F.problem_from_scene(sc) as pr:
+        pr.set_params(F.FM_STAGE_EPIPOLAR, torch.from_numpy(params.reshape(-1)).to(dev))
+        pr.mlp_set_params(M.init_params(3).astype(np.float32))
+        prob = torch.empty(Z, dtype=torch.float32, device=dev)
+        for _ in range(a.warmup):
+            flush()
+            pr.mlp_eval(want_feat=False, want_resid=False, want_prob=True)
+        torch.cuda.synchronize()
+        pr.timing(True)
+        with Clocks(0) as clk:
+            for _ in range(a.steps):
+                flush()
+                _, _, prob = pr.mlp_eval(want_feat=False, want_resid=False, want_prob=True)
+            kt = pr.timing_read()
+        pr.timing(False)
+        pmean = float(prob.mean().item())
+    n_t, ms_t = kt.get("k_mlp_pair_tables", (0, 0.0))
+    n_i, ms_i = kt.get("k_mlp_infer", (0, 0.0))
+    step_ms = (ms_t + ms_i) / max(a.steps, 1)
+    infer_us = 1e3 * ms_i / max(n_i, 1)
+    flop_per_pair = 2 * (16 * 64 + 64 * 64)
+    achieved = flop_per_pair * Z / (infer_us * 1e-6) / 1e12
+    pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1800.0
+    line = {"metric": "learned inlier network: keypoint-pair evaluations/s (features + 8-64-64-1 GELU network + p)",
+            "value": Z / (step_ms * 1e-3), "unit": "keypoint-pair evals/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 products, f32 accumulation and activations", "data": "synthetic",
+            "config": {"workload": f"mlp_c2_5m: fm_mlp_eval with probabilities over {Z} keypoint pairs "
+                                   f"({sc.n_pairs} image pairs), random-init network",
+                       "l2": "flushed before every timed evaluation, then a 0.5 ms device sleep; neither timed"},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                         "frac": achieved / pk, "traffic": None, "kernel": "k_mlp_forward_tc<PAIRS>",
+                         "flop_per_pair": flop_per_pair, "avg_launch_us": infer_us,
+                         "note": "limited by the exact-erf GELUs on the FP32 pipe, not by the tensor cores"},
+            "kernels_us_per_launch": {k: 1e3 * v[1] / max(v[0], 1) for k, v in kt.items()},
+            "gpu_launches": int(n_t + n_i), "clocks": clk.summary(), "mean_probability": pmean}
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(a):
     """Time to accuracy, learned filter against the plain one (one GPU).
 
@@ -507,6 +572,8 @@ def main():
         return run_batch(a)
     if a.config == "learned_c5":
         return run_learned(a)
+    if a.config == "mlp_c2_5m":
+        return run_mlp(a)
     import torch
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))

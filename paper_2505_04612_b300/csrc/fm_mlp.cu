@@ -166,6 +166,16 @@ __global__ void __launch_bounds__(128) k_mlp_pair_tables(const float* params, co
   const int n = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (n >= P) return;
   const int ci = pi[n], cj = pj[n];
+  // the keypoints do not depend on the geometry: the first loads go out now,
+  // four per lane in flight (pairs b + lane + 32 u; the sum keeps that order)
+  const int b = seg_off[n], e = seg_off[n + 1];
+  constexpr int kAhead = 4;
+  float4 xs[kAhead];
+#pragma unroll
+  for (int u = 0; u < kAhead; ++u) {
+    const int m = b + lane + 32 * u;
+    xs[u] = m < e ? __ldg(kp + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   PairGeo g;
   float E[9];
   if (rel_t) {
@@ -193,14 +203,24 @@ __global__ void __launch_bounds__(128) k_mlp_pair_tables(const float* params, co
     pair_geometry(qi, qj, g);
     essential(g, E);
   }
-  const int b = seg_off[n], e = seg_off[n + 1];
   float s = 0.f;
-  for (int m = b + lane; m < e; m += 32) {
-    const float4 x = __ldg(kp + m);
-    const float a0 = fmaf(E[0], x.x, fmaf(E[1], x.y, E[2]));
-    const float a1 = fmaf(E[3], x.x, fmaf(E[4], x.y, E[5]));
-    const float a2 = fmaf(E[6], x.x, fmaf(E[7], x.y, E[8]));
-    s += fabsf(fmaf(x.z, a0, fmaf(x.w, a1, a2)));
+  for (int m0 = b; m0 < e; m0 += 32 * kAhead) {
+    float4 cur[kAhead];
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) {
+      cur[u] = xs[u];
+      const int m = m0 + 32 * kAhead + lane + 32 * u;
+      xs[u] = m < e ? __ldg(kp + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) {
+      if (m0 + lane + 32 * u >= e) break;
+      const float4 x = cur[u];
+      const float a0 = fmaf(E[0], x.x, fmaf(E[1], x.y, E[2]));
+      const float a1 = fmaf(E[3], x.x, fmaf(E[4], x.y, E[5]));
+      const float a2 = fmaf(E[6], x.x, fmaf(E[7], x.y, E[8]));
+      s += fabsf(fmaf(x.z, a0, fmaf(x.w, a1, a2)));
+    }
   }
   s = warp_sum(s);
   float* o = tab + (size_t)kTab * n;

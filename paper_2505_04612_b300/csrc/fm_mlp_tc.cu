@@ -14,9 +14,10 @@
 // 8-row x 16-byte core matrices, LBO = stride between core matrices along K,
 // SBO = stride between 8-row groups.  W1^T, W2^T are staged once per CTA.
 //
-// TMEM: 128 columns per CTA (D1 in columns 0..63, D2 in 64..127); the CTA's
-// dynamic shared memory is sized so that at most four CTAs share an SM
-// (4 x 128 = 512 columns), so an allocation never waits for another CTA.
+// TMEM: 64 columns per CTA; D2 reuses D1's columns (every thread has read
+// its row of D1 before the layer-2 MMA is issued).  The CTA's dynamic shared
+// memory is sized so that at most seven CTAs share an SM (7 x 64 = 448 of the
+// 512 columns), so an allocation never waits for another CTA.
 // Waits on the mbarrier are bounded: past the bound the kernel records
 // kErrMlpTimeout, skips the rest of its work, and still frees its TMEM.
 #include <cuda_bf16.h>
@@ -32,8 +33,8 @@ namespace {
 
 constexpr int kRows = 128;   // M
 constexpr int kN = 64;       // N of both layers
-constexpr int kTmemCols = 128;
-constexpr int kCtasPerSm = 4;
+constexpr int kTmemCols = 64;
+constexpr int kCtasPerSm = 7;
 constexpr long kWaitBound = 1L << 22;   // polls of the mbarrier before giving up
 
 // shared-memory layout (bytes), K-major no-swizzle core-matrix tiles
@@ -44,8 +45,11 @@ constexpr int kB2 = kA2 + 16384;               // W2^T 64 x 64: SBO 1024, LBO 12
 constexpr int kPar = kB2 + 8192;               // b1, b2, w3 (fp32), b3            772 B
 constexpr int kBar = kPar + 1024;              // mbarrier (8 B) + TMEM address (4 B)
 constexpr int kSmemUsed = kBar + 64;
-// padded so that shared memory admits at most kCtasPerSm CTAs per SM
-constexpr int kSmemDyn = 232448 / kCtasPerSm - 2048;
+// padded so that shared memory (227 KB per SM for CTAs, 1 KB reserved per
+// CTA) admits at most kCtasPerSm CTAs per SM; registers (64 x 128 threads)
+// admit at most 8 in any case, and 8 x 64 columns fit the 512 of TMEM
+constexpr int kSmemDyn = 232448 / kCtasPerSm - 1024;
+static_assert(8 * kTmemCols <= 512, "TMEM columns of the resident CTAs");
 
 // byte offset of element (row r, k) in a K-major no-swizzle tile
 __device__ __forceinline__ int core_off(int r, int k, int sbo) {
@@ -212,7 +216,7 @@ __global__ void __launch_bounds__(kRows, 1) k_mlp_forward_tc(InferArgs a, int* e
     if (__syncthreads_or(!ok)) break;   // a wait ran out: stop, free TMEM below
     fence_after();
     // ---- row tid of D1 -> bias, GELU -> bf16 row of H1
-#pragma unroll
+#pragma unroll 1
     for (int c = 0; c < kN; c += 16) {
       float v[16];
       tmem_ld16(tmem + lane_base + (uint32_t)c, v);
@@ -228,7 +232,7 @@ __global__ void __launch_bounds__(kRows, 1) k_mlp_forward_tc(InferArgs a, int* e
     if (tid == 0 && ok) {
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        umma(tmem + kN, smem_desc(a2 + 256 * kk, 128, 1024), smem_desc(b2s + 256 * kk, 128, 1024),
+        umma(tmem, smem_desc(a2 + 256 * kk, 128, 1024), smem_desc(b2s + 256 * kk, 128, 1024),
              kk > 0 ? 1u : 0u);
       umma_commit(bar_a);
     }
@@ -238,10 +242,10 @@ __global__ void __launch_bounds__(kRows, 1) k_mlp_forward_tc(InferArgs a, int* e
     fence_after();
     // ---- row tid of D2 -> bias, GELU, . w3 + b3
     float o = 0.f;
-#pragma unroll
+#pragma unroll 1
     for (int c = 0; c < kN; c += 16) {
       float v[16];
-      tmem_ld16(tmem + lane_base + (uint32_t)(kN + c), v);
+      tmem_ld16(tmem + lane_base + (uint32_t)c, v);
 #pragma unroll
       for (int k = 0; k < 16; ++k) o = fmaf(gelu_tc(v[k] + par[kN + c + k]), par[2 * kN + c + k], o);
     }
@@ -270,14 +274,18 @@ __global__ void __launch_bounds__(kRows, 1) k_mlp_forward_tc(InferArgs a, int* e
 template <bool PAIRS>
 void launch_tc(const InferArgs& a, int* err, int sm_count, cudaStream_t s) {
   if (a.Z == 0) return;
-  static bool attr = false;
-  if (!attr) {
+  static int per_sm = 0;   // resident CTAs per SM, bound by shared memory (one device per process)
+  if (per_sm == 0) {
     cudaFuncSetAttribute(k_mlp_forward_tc<PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn);
-    attr = true;
+    int dev = 0, smem_sm = 0, reserved = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    per_sm = std::max(1, std::min(kCtasPerSm, smem_sm / (kSmemDyn + reserved)));
   }
   static_assert(kSmemUsed <= kSmemDyn, "shared memory layout");
   const int64_t tiles = (a.Z + kRows - 1) / kRows;
-  const int64_t grid = std::min<int64_t>(tiles, (int64_t)sm_count * kCtasPerSm);
+  const int64_t grid = std::min<int64_t>(tiles, (int64_t)sm_count * per_sm);
   k_mlp_forward_tc<PAIRS><<<(unsigned)grid, kRows, kSmemDyn, s>>>(a, err);
 }
 
