@@ -54,7 +54,7 @@ def args_():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2_5m", help="c2_5m (default), batch_c4, learned_c5 or mlp_c2_5m")
+    ap.add_argument("--config", default="c2_5m", help="c2_5m (default), batch_c4, learned_c5, mlp_c2_5m or stages_c2_5m")
     ap.add_argument("--train-scenes", type=int, default=200)
     ap.add_argument("--eval-cams", type=int, default=3000)
     ap.add_argument("--eval-points", type=int, default=1_000_000)
@@ -397,6 +397,62 @@ def run_batch(a):
     print(json.dumps(line), flush=True)
 
 
+def run_stages(a):
+    """--config stages_c2_5m: microseconds per optimiser iteration of each
+    stage on the c2_5m scene under captured-graph replay (fm_step of 16 x k
+    iterations, CUDA events around the call): rotation (loss + gradient over
+    the image pairs, per-camera assembly, 6D adjoint, Adam), translation with
+    4 batched initialisations, the direct epipolar step (L1) and the compact
+    epipolar step (the paper's form, cost independent of the keypoint pairs).
+    Iterations run back to back, so the 80 MB of keypoints of the direct step
+    are largely L2-resident here (the main line flushes L2 before every step)."""
+    import torch
+    from paper_2505_04612_b300 import build as B
+    B.build()
+    from paper_2505_04612_b300 import fastmap as F
+    from synthetic.scenes import gt_relative_poses
+    sc, params = make_workload("c2_5m", a.seed)
+    dev = torch.device("cuda", 0)
+    Rij, tij = gt_relative_poses(sc, rot_noise_deg=1.0, dir_noise_deg=2.0, seed=a.seed)
+    rng = np.random.default_rng(7)
+    R = sc.R_gt
+    p6 = np.concatenate([R[:, :, 0], R[:, :, 1]], axis=1) + rng.normal(0, 0.02, (sc.n_cams, 6))
+    iters = 16 * max(1, a.steps)
+    out = {}
+    with F.problem_from_scene(sc, rel_R=Rij.astype(np.float32), rel_t=tij.astype(np.float32)) as pr:
+        pr.autotune(repeats=5)
+
+        def timed(stage, lr):
+            pr.step(stage, 16 * 3 + 1, lr=lr)        # captures the graphs
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pr.step(stage, iters + 1, lr=lr)
+            e1.record()
+            torch.cuda.synchronize()
+            return 1e3 * e0.elapsed_time(e1) / (iters + 1)
+
+        pr.set_params(F.FM_STAGE_ROTATION, torch.from_numpy(p6.astype(np.float32).reshape(-1)).to(dev))
+        out["rotation_a3_a9"] = timed(F.FM_STAGE_ROTATION, 1e-2)
+        pr.set_translation_runs(4)
+        pr.translation_random_init(a.seed)
+        out["translation_m4_a5_a9"] = timed(F.FM_STAGE_TRANSLATION, 1e-2)
+        pr.set_params(F.FM_STAGE_EPIPOLAR, torch.from_numpy(params.reshape(-1)).to(dev))
+        pr.set_ea_loss(F.FM_EA_L1)
+        out["epipolar_direct_l1_a6_a9"] = timed(F.FM_STAGE_EPIPOLAR, 1e-4)
+        pr.reweight(0.05, 1e-5)
+        pr.set_ea_loss(F.FM_EA_COMPACT)
+        out["epipolar_compact_a7_a8_a9"] = timed(F.FM_STAGE_EPIPOLAR, 1e-4)
+    line = {"metric": "microseconds per optimiser iteration per stage (captured-graph replay)",
+            "value": out["epipolar_direct_l1_a6_a9"], "unit": "us/iteration (direct epipolar step)",
+            "n_gpus": 1, "steps": iters, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"stages_c2_5m: {sc.n_cams} cameras, {sc.n_pairs} image pairs, {sc.n_kp} "
+                                   "keypoint pairs; relative poses from ground truth with 1 deg / 2 deg noise",
+                       "l2": "not flushed between iterations (back-to-back graph replay)"},
+            "us_per_iteration": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_mlp(a):
     """--config mlp_c2_5m: the learned inlier network's inference over every
     keypoint pair of the c2_5m scene (fm_mlp_eval with probabilities: the
@@ -574,6 +630,8 @@ def main():
         return run_learned(a)
     if a.config == "mlp_c2_5m":
         return run_mlp(a)
+    if a.config == "stages_c2_5m":
+        return run_stages(a)
     import torch
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))
