@@ -403,7 +403,8 @@ def run_stages(a):
     iterations, CUDA events around the call): rotation (loss + gradient over
     the image pairs, per-camera assembly, 6D adjoint, Adam), translation with
     4 batched initialisations, the direct epipolar step (L1) and the compact
-    epipolar step (the paper's form, cost independent of the keypoint pairs).
+    epipolar step (the paper's form, cost independent of the keypoint pairs);
+    and the wall time of one fm_relative_poses call (a1, every image pair).
     Iterations run back to back, so the 80 MB of keypoints of the direct step
     are largely L2-resident here (the main line flushes L2 before every step)."""
     import torch
@@ -421,6 +422,14 @@ def run_stages(a):
     out = {}
     with F.problem_from_scene(sc, rel_R=Rij.astype(np.float32), rel_t=tij.astype(np.float32)) as pr:
         pr.autotune(repeats=5)
+        # a1: relative poses of all image pairs from their keypoints (one call,
+        # wall time of the synchronous call after a warm-up call)
+        pr.relative_poses()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_est = pr.relative_poses()
+        out["relative_poses_a1_call"] = 1e6 * (time.perf_counter() - t0)
+        pr.set_rel_poses(Rij.astype(np.float32), tij.astype(np.float32))
 
         def timed(stage, lr):
             pr.step(stage, 16 * 3 + 1, lr=lr)        # captures the graphs

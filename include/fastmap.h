@@ -315,6 +315,21 @@ fm_status fm_rotation_init(fm_problem* problem, int32_t n_iters);
  * and the sign (unless an image pair has no other pair). */
 fm_status fm_relative_translations(fm_problem* problem, float* err_out, int32_t err_on_device);
 
+/* Relative poses of every image pair from its keypoint pairs (the setup step
+ * standing in for the upstream two-view estimate the paper decomposes, Sec.
+ * 3.3 "Global Rotation"): the eigenvector of W_n = sum_m w_m vec(x~2 x~1^T)
+ * vec(x~2 x~1^T)^T with the smallest eigenvalue (the linear eight-point
+ * estimate of E in calibrated coordinates; Eq. 17's W_n), irls_iters re-solves
+ * with weights w_m = 1/max(|x~2^T E x~1|, delta) (0 <= irls_iters <= 16,
+ * delta > 0), the projection onto the essential matrices (singular values
+ * (1, 1, 0)), and of its four decompositions the one with the most keypoint
+ * pairs in front of both cameras (the first on ties).  Writes the problem's
+ * rel_R and unit rel_t (as fm_set_rel_poses would); image pairs with fewer
+ * than 8 keypoint pairs get R = I, t = 0.  n_valid (or NULL) receives the
+ * number of image pairs estimated.  Not robust to outliers by itself (a
+ * linear least-squares estimate); synchronises. */
+fm_status fm_relative_poses(fm_problem* problem, int32_t irls_iters, float delta, int32_t* n_valid);
+
 /* Copies the current relative rotations [P*9] / translations [P*3]; either
  * may be NULL.  Synchronises for host outputs. */
 fm_status fm_get_rel_poses(fm_problem* problem, float* rel_R, float* rel_t, int32_t out_on_device);
@@ -414,14 +429,15 @@ typedef struct {
 } fm_result;
 
 /* Runs the whole first-order pipeline (from unit weights: weights left by an
- * earlier call are cleared): fm_rotation_init, Adam on the rotation
+ * earlier call are cleared): fm_relative_poses (irls_iters 0, ea_delta) when
+ * no relative rotations were given, fm_rotation_init, Adam on the rotation
  * loss, fm_relative_translations (if asked), trn_runs translation runs from
  * fm_translation_random_init, fm_translation_merge, a final translation run,
  * fm_epipolar_init_from_stages, ea_rounds of {fm_ea_reweight(tau_k, delta),
  * Adam on FM_EA_COMPACT} with tau_k = max(tau0 / 2^k, tau_min), and
  * triangulation.  Each Adam loop runs in four equal phases with the learning
- * rate scaled by 1, 0.3, 0.1, 0.03.  Needs rel_R (and rel_t when
- * reestimate_rel_t is 0).  The solution is defined up to a similarity of the
+ * rate scaled by 1, 0.3, 0.1, 0.03.  Needs rel_t when reestimate_rel_t is 0
+ * and rel_R was given.  The solution is defined up to a similarity of the
  * world frame.  Synchronises. */
 fm_status fm_solve(fm_problem* problem, const fm_solve_opts* opts, fm_result* result);
 

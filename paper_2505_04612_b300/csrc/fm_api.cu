@@ -830,6 +830,33 @@ fm_status fm_set_rel_poses(fm_problem* pr, const float* rel_R, const float* rel_
   return FM_OK;
 }
 
+fm_status fm_relative_poses(fm_problem* pr, int32_t irls_iters, float delta, int32_t* n_valid) {
+  fm::g_plain_once = true;
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (irls_iters < 0 || irls_iters > 16) return fail(pr, FM_ERR_INVALID_ARG, "irls_iters must be in [0, 16]");
+  if (!(delta > 0.f) || !std::isfinite(delta)) return fail(pr, FM_ERR_INVALID_ARG, "delta must be finite and > 0");
+  cudaStream_t s = pr->stream;
+  int* d_valid = nullptr;
+  FM_ALLOC(pr, d_valid, (size_t)pr->P);
+  fm::launch_relpose(pr, irls_iters, delta, pr->rel_R, pr->rel_t, d_valid, s);
+  cudaError_t le = cudaGetLastError();
+  std::vector<int> h(pr->P);
+  cudaError_t ce = le;
+  if (ce == cudaSuccess && pr->P > 0)
+    ce = cudaMemcpyAsync(h.data(), d_valid, sizeof(int) * pr->P, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  cudaFree(d_valid);
+  pr->device_bytes -= (int64_t)sizeof(int) * std::max(pr->P, 1);
+  if (ce != cudaSuccess) return fail(pr, FM_ERR_CUDA, std::string("relative poses: ") + cudaGetErrorString(ce));
+  int cnt = 0;
+  for (int v : h) cnt += v;
+  if (n_valid) *n_valid = cnt;
+  pr->rel_R_set = true;
+  pr->rel_t_set = true;
+  pr->trn_target_valid = false;
+  return FM_OK;
+}
+
 fm_status fm_translation_set_runs(fm_problem* pr, int32_t n_runs) {
   if (!pr) return FM_ERR_INVALID_ARG;
   if (n_runs < 1 || n_runs > 64) return fail(pr, FM_ERR_INVALID_ARG, "n_runs must be in [1, 64]");
@@ -1884,6 +1911,8 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
     for (float v : Lv) t += v;
     return t;
   };
+  // 0. relative poses from the keypoints when none were given
+  if (!pr->rel_R_set && (e = fm_relative_poses(pr, 0, o->ea_delta, nullptr)) != FM_OK) return e;
   // 1-2. rotations
   if ((e = fm_rotation_init(pr, o->rot_init_iters)) != FM_OK) return e;
   if ((e = stepped(pr, FM_STAGE_ROTATION, o, o->rot_lr, o->rot_iters, Lv.data())) != FM_OK) return e;

@@ -324,6 +324,10 @@ void launch_pair_inv_from_counts(const fm_problem* pr, const unsigned long long*
 // count[s] = number of keypoint pairs of scene s with a weight > 0
 void launch_count_positive(const fm_problem* pr, const float* w, unsigned long long* count, cudaStream_t s);
 
+// relative poses from keypoints (fm_relpose.cu)
+void launch_relpose(const fm_problem* pr, int irls_iters, float delta, float* rel_R, float* rel_t, int* valid,
+                    cudaStream_t s);
+
 // learned weights (fm_mlp.cu)
 size_t mlp_grad_smem();
 int mlp_grad_parts(int64_t B);

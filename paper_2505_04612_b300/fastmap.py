@@ -175,6 +175,8 @@ _SIGNATURES = {
                                        ctypes.POINTER(ctypes.c_int32)]),
     "fm_rotation_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "fm_relative_translations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "fm_relative_poses": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_float,
+                                         ctypes.POINTER(ctypes.c_int32)]),
     "fm_get_rel_poses": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "fm_translation_random_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "fm_translation_merge": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -684,6 +686,14 @@ class Problem:
         err = np.empty(self.n_pairs, np.float32)
         _check(lib().fm_relative_translations(self.handle, err.ctypes.data, 0), self.handle)
         return err
+
+    def relative_poses(self, irls_iters=0, delta=1e-5):
+        """fm_relative_poses: estimates rel_R / rel_t from the keypoints; returns
+        the number of image pairs estimated."""
+        n = ctypes.c_int32()
+        _check(lib().fm_relative_poses(self.handle, int(irls_iters), ctypes.c_float(delta), ctypes.byref(n)),
+               self.handle)
+        return n.value
 
     def get_rel_poses(self, want_R=True, want_t=True):
         R = np.empty((self.n_pairs, 3, 3), np.float32) if want_R else None
