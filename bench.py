@@ -404,7 +404,8 @@ def run_stages(a):
     the image pairs, per-camera assembly, 6D adjoint, Adam), translation with
     4 batched initialisations, the direct epipolar step (L1) and the compact
     epipolar step (the paper's form, cost independent of the keypoint pairs);
-    and the wall time of one fm_relative_poses call (a1, every image pair).
+    and the wall time of one fm_relative_poses call (a1, every image pair) and
+    of one fm_focal_search call (one focal length, 1024 candidates).
     Iterations run back to back, so the 80 MB of keypoints of the direct step
     are largely L2-resident here (the main line flushes L2 before every step)."""
     import torch
@@ -429,6 +430,13 @@ def run_stages(a):
         t0 = time.perf_counter()
         n_est = pr.relative_poses()
         out["relative_poses_a1_call"] = 1e6 * (time.perf_counter() - t0)
+        # focal interval search, one focal length for all images, 1024
+        # candidates (eight-point E0 of every image pair + the vote)
+        pr.focal_search(n_cand=1024)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pr.focal_search(n_cand=1024)
+        out["focal_search_shared_call"] = 1e6 * (time.perf_counter() - t0)
         pr.set_rel_poses(Rij.astype(np.float32), tij.astype(np.float32))
 
         def timed(stage, lr):

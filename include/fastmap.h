@@ -330,6 +330,35 @@ fm_status fm_relative_translations(fm_problem* problem, float* err_out, int32_t 
  * linear least-squares estimate); synchronises. */
 fm_status fm_relative_poses(fm_problem* problem, int32_t irls_iters, float delta, int32_t* n_valid);
 
+/* Focal length interval search (Sec. 3.1 "Focal Length Estimation", Eq.
+ * focal-vote; Appendix "Focal Length Estimation").  For every image pair, E0
+ * = the eight-point estimate (as fm_relative_poses, irls_iters re-solves) in
+ * the problem's current calibration (focal f0 per image, principal point
+ * fixed); at focal ratios rho_i, rho_j (f = rho f0) its candidate essential
+ * matrix is D_j E0 D_i, D = diag(rho, rho, 1), scored by
+ * exp((1 - lambda1/lambda2)/tau) with lambda1 >= lambda2 its two largest
+ * singular values.  Images form n_groups groups sharing intrinsics (group
+ * [N] ids in [0, n_groups), or NULL with n_groups = 1: one focal length for
+ * all).  Groups are estimated one at a time, the one with the most "ready"
+ * image pairs first (both images in it, or one in it and the other's group
+ * already estimated; the lowest id on ties), each by the candidate with the
+ * highest summed score over its ready pairs (the first on ties), the other
+ * side's ratio fixed where it is known.  Candidates: n_cand (2..65536) ratios
+ * spaced evenly in log between rho_min and rho_max.  focal_out [N] (host)
+ * receives f0 rho of each image's group, f0 where a group never became ready;
+ * n_estimated (or NULL) the number of groups estimated.  Image pairs with
+ * fewer than 8 keypoint pairs take no part.  Synchronises. */
+fm_status fm_focal_search(fm_problem* problem, const int32_t* group, int32_t n_groups, float rho_min,
+                          float rho_max, int32_t n_cand, float tau, int32_t irls_iters, float* focal_out,
+                          int32_t* n_estimated);
+
+/* Recalibrates the problem at new focal lengths focal [N] (host or device as
+ * flagged; finite, > 0; principal points unchanged): every stored keypoint's
+ * calibrated coordinates are rescaled by f_old / f_new of its image.  The
+ * relative poses and every stage's parameters are kept (re-estimate them as
+ * needed).  Synchronises. */
+fm_status fm_set_focal(fm_problem* problem, const float* focal, int32_t on_device);
+
 /* Copies the current relative rotations [P*9] / translations [P*3]; either
  * may be NULL.  Synchronises for host outputs. */
 fm_status fm_get_rel_poses(fm_problem* problem, float* rel_R, float* rel_t, int32_t out_on_device);

@@ -857,6 +857,155 @@ fm_status fm_relative_poses(fm_problem* pr, int32_t irls_iters, float delta, int
   return FM_OK;
 }
 
+fm_status fm_focal_search(fm_problem* pr, const int32_t* group, int32_t n_groups, float rho_min, float rho_max,
+                          int32_t n_cand, float tau, int32_t irls_iters, float* focal_out, int32_t* n_estimated) {
+  fm::g_plain_once = true;
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!focal_out) return fail(pr, FM_ERR_INVALID_ARG, "focal_out is NULL");
+  if (n_groups < 1 || (!group && n_groups != 1)) return fail(pr, FM_ERR_INVALID_ARG, "n_groups >= 1 (1 without group)");
+  if (!(rho_min > 0.f && rho_max > rho_min) || !std::isfinite(rho_max))
+    return fail(pr, FM_ERR_INVALID_ARG, "0 < rho_min < rho_max required");
+  if (n_cand < 2 || n_cand > 65536) return fail(pr, FM_ERR_INVALID_ARG, "n_cand must be in [2, 65536]");
+  if (!(tau > 0.f) || !std::isfinite(tau)) return fail(pr, FM_ERR_INVALID_ARG, "tau must be finite and > 0");
+  if (irls_iters < 0 || irls_iters > 16) return fail(pr, FM_ERR_INVALID_ARG, "irls_iters must be in [0, 16]");
+  const int N = pr->N, P = pr->P;
+  std::vector<int> g(N, 0);
+  if (group)
+    for (int c = 0; c < N; ++c) {
+      g[c] = group[c];
+      if (g[c] < 0 || g[c] >= n_groups) return fail(pr, FM_ERR_INVALID_ARG, "group id outside [0, n_groups)");
+    }
+  cudaStream_t s = pr->stream;
+  std::vector<int> hi, hj;
+  std::vector<float> f0;
+  FM_CUDA(pr, fetch(hi, pr->pair_i, P, true));
+  FM_CUDA(pr, fetch(hj, pr->pair_j, P, true));
+  FM_CUDA(pr, fetch(f0, pr->focal, N, true));
+  // candidates rho_k = exp(log rho_min + k (log rho_max - log rho_min) / (n - 1))
+  std::vector<float> rhos(n_cand);
+  for (int k = 0; k < n_cand; ++k)
+    rhos[k] = (float)std::exp(std::log((double)rho_min) +
+                              k * (std::log((double)rho_max) - std::log((double)rho_min)) / (n_cand - 1));
+  float *e0 = nullptr, *d_rhos = nullptr, *votes = nullptr, *fix = nullptr;
+  int *valid = nullptr, *idx = nullptr;
+  auto release_all = [&]() {
+    for (void* q : {(void*)e0, (void*)d_rhos, (void*)votes, (void*)fix, (void*)valid, (void*)idx})
+      if (q) cudaFree(q);
+  };
+  cudaError_t ce = cudaSuccess;
+  auto dmalloc = [&](void** q, size_t bytes) {
+    if (ce == cudaSuccess) ce = cudaMalloc(q, std::max<size_t>(bytes, 16));
+  };
+  dmalloc((void**)&e0, sizeof(float) * 9 * P);
+  dmalloc((void**)&valid, sizeof(int) * P);
+  dmalloc((void**)&d_rhos, sizeof(float) * n_cand);
+  dmalloc((void**)&votes, sizeof(float) * n_cand);
+  dmalloc((void**)&idx, sizeof(int) * P);
+  dmalloc((void**)&fix, sizeof(float) * 2 * P);
+  if (ce != cudaSuccess) {
+    release_all();
+    cudaGetLastError();
+    return fail(pr, ce == cudaErrorMemoryAllocation ? FM_ERR_OOM : FM_ERR_CUDA, "focal search: allocation");
+  }
+  fm::launch_relpose(pr, irls_iters, 1e-5f, nullptr, nullptr, valid, s, e0);
+  ce = cudaGetLastError();
+  std::vector<int> hv(P);
+  if (ce == cudaSuccess && P > 0) ce = cudaMemcpyAsync(hv.data(), valid, sizeof(int) * P, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_rhos, rhos.data(), sizeof(float) * n_cand, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  // greedy order of the groups by ready image pairs (incremental counts)
+  std::vector<std::vector<int>> inc(n_groups);   // valid image pairs touching each group
+  std::vector<int64_t> ready(n_groups, 0);
+  for (int n = 0; n < P && ce == cudaSuccess; ++n) {
+    if (!hv[n]) continue;
+    const int a = g[hi[n]], b = g[hj[n]];
+    inc[a].push_back(n);
+    if (b != a) inc[b].push_back(n);
+    else ready[a] += 1;
+  }
+  std::vector<char> done(n_groups, 0);
+  std::vector<float> rho_g(n_groups, 1.f);
+  int n_done = 0;
+  std::vector<int> list;
+  std::vector<float> fixes;
+  std::vector<float> hvotes(n_cand);
+  while (ce == cudaSuccess) {
+    int best = -1;
+    int64_t bn = 0;
+    for (int q = 0; q < n_groups; ++q)
+      if (!done[q] && ready[q] > bn) {
+        best = q;
+        bn = ready[q];
+      }
+    if (best < 0) break;
+    list.clear();
+    fixes.assign(2 * P, -1.f);
+    int M = 0;
+    for (int n : inc[best]) {
+      const int a = g[hi[n]], b = g[hj[n]];
+      const bool ok = (a == best && b == best) || (a == best && done[b]) || (b == best && done[a]);
+      if (!ok) continue;
+      list.push_back(n);
+      fixes[M] = (a == best) ? -1.f : rho_g[a];
+      fixes[P + M] = (b == best) ? -1.f : rho_g[b];
+      ++M;
+    }
+    ce = cudaMemcpyAsync(idx, list.data(), sizeof(int) * M, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(fix, fixes.data(), sizeof(float) * 2 * P, cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) break;
+    fm::launch_focal_vote(e0, idx, fix, fix + P, M, d_rhos, n_cand, tau, votes, s);
+    ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(hvotes.data(), votes, sizeof(float) * n_cand, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) break;
+    int k = 0;
+    for (int q = 1; q < n_cand; ++q)
+      if (hvotes[q] > hvotes[k]) k = q;   // the first maximum
+    rho_g[best] = rhos[k];
+    done[best] = 1;
+    ++n_done;
+    // image pairs between `best` and a group still open become ready for it
+    for (int n : inc[best]) {
+      const int a = g[hi[n]], b = g[hj[n]];
+      if (a == b) continue;
+      const int other = (a == best) ? b : a;
+      if (!done[other]) ready[other] += 1;
+    }
+  }
+  release_all();
+  if (ce != cudaSuccess) return fail(pr, FM_ERR_CUDA, std::string("focal search: ") + cudaGetErrorString(ce));
+  for (int c = 0; c < N; ++c) focal_out[c] = done[g[c]] ? f0[c] * rho_g[g[c]] : f0[c];
+  if (n_estimated) *n_estimated = n_done;
+  return FM_OK;
+}
+
+fm_status fm_set_focal(fm_problem* pr, const float* focal, int32_t on_device) {
+  fm::g_plain_once = true;
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!focal) return fail(pr, FM_ERR_INVALID_ARG, "focal is NULL");
+  std::vector<float> f;
+  FM_CUDA(pr, fetch(f, focal, pr->N, on_device != 0));
+  for (int c = 0; c < pr->N; ++c)
+    if (!(std::isfinite(f[c]) && f[c] > 0.f))
+      return fail(pr, FM_ERR_INVALID_ARG, "focal[" + std::to_string(c) + "] must be finite and > 0");
+  float* f_new = nullptr;
+  FM_ALLOC(pr, f_new, (size_t)pr->N);
+  cudaStream_t s = pr->stream;
+  cudaError_t ce = cudaMemcpyAsync(f_new, f.data(), sizeof(float) * pr->N, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) {
+    fm::launch_recalibrate(pr, pr->focal, f_new, s);
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(pr->focal, f_new, sizeof(float) * pr->N, cudaMemcpyDeviceToDevice, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  cudaFree(f_new);
+  pr->device_bytes -= (int64_t)sizeof(float) * std::max(pr->N, 1);
+  if (ce != cudaSuccess) return fail(pr, FM_ERR_CUDA, std::string("set focal: ") + cudaGetErrorString(ce));
+  pr->W_valid = false;
+  pr->graph_epoch += 1;
+  return FM_OK;
+}
+
 fm_status fm_translation_set_runs(fm_problem* pr, int32_t n_runs) {
   if (!pr) return FM_ERR_INVALID_ARG;
   if (n_runs < 1 || n_runs > 64) return fail(pr, FM_ERR_INVALID_ARG, "n_runs must be in [1, 64]");

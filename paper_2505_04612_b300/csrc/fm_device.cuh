@@ -177,6 +177,44 @@ __device__ __forceinline__ void pair_backward(const PairGeo& g, const float* G, 
     }
 }
 
+// eigen-decomposition of a symmetric 3 x 3 matrix S (row-major), cyclic
+// Jacobi; on return S's diagonal holds the eigenvalues, Q's columns the
+// eigenvectors
+__device__ __forceinline__ void jacobi3(float* S, float* Q) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Q[k] = (k % 4 == 0) ? 1.f : 0.f;
+#pragma unroll 1
+  for (int sweep = 0; sweep < 10; ++sweep) {
+#pragma unroll
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+      const float apq = S[p * 3 + q];
+      if (apq == 0.f) continue;
+      const float tau = (S[q * 3 + q] - S[p * 3 + p]) / (2.f * apq);
+      const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+      const float c = rsqrtf(fmaf(t, t, 1.f)), s = t * c;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float akp = S[k * 3 + p], akq = S[k * 3 + q];
+        S[k * 3 + p] = c * akp - s * akq;
+        S[k * 3 + q] = s * akp + c * akq;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float apk = S[p * 3 + k], aqk = S[q * 3 + k];
+        S[p * 3 + k] = c * apk - s * aqk;
+        S[q * 3 + k] = s * apk + c * aqk;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float vkp = Q[k * 3 + p], vkq = Q[k * 3 + q];
+        Q[k * 3 + p] = c * vkp - s * vkq;
+        Q[k * 3 + q] = s * vkp + c * vkq;
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);

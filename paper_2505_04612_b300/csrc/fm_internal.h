@@ -325,8 +325,16 @@ void launch_pair_inv_from_counts(const fm_problem* pr, const unsigned long long*
 void launch_count_positive(const fm_problem* pr, const float* w, unsigned long long* count, cudaStream_t s);
 
 // relative poses from keypoints (fm_relpose.cu)
+// rel_R == nullptr: only the eight-point estimates E0 into e0_out [P*9]
 void launch_relpose(const fm_problem* pr, int irls_iters, float delta, float* rel_R, float* rel_t, int* valid,
-                    cudaStream_t s);
+                    cudaStream_t s, float* e0_out = nullptr);
+// focal interval search (fm_focal.cu): votes[k] = sum over the listed image
+// pairs of exp((1 - lambda1/lambda2)/tau) of D_j E0 D_i at candidate rho_k
+// (fix_i / fix_j >= 0: that side's rho is fixed), fixed order
+void launch_focal_vote(const float* e0, const int* idx, const float* fix_i, const float* fix_j, int M,
+                       const float* rhos, int K, float tau, float* votes, cudaStream_t s);
+// kp (x1, y1) *= f_old[i]/f_new[i], (x2, y2) *= f_old[j]/f_new[j] per keypoint pair
+void launch_recalibrate(const fm_problem* pr, const float* f_old, const float* f_new, cudaStream_t s);
 
 // learned weights (fm_mlp.cu)
 size_t mlp_grad_smem();

@@ -116,44 +116,6 @@ __device__ void eight_point(const float4* __restrict__ kp, const float* E_w, flo
   __syncwarp();   // the scratch is reused by the next call
 }
 
-// eigen-decomposition of a symmetric 3 x 3 matrix S (row-major), cyclic
-// Jacobi; on return S's diagonal holds the eigenvalues, Q's columns the
-// eigenvectors
-__device__ __forceinline__ void jacobi3(float* S, float* Q) {
-#pragma unroll
-  for (int k = 0; k < 9; ++k) Q[k] = (k % 4 == 0) ? 1.f : 0.f;
-#pragma unroll 1
-  for (int sweep = 0; sweep < 10; ++sweep) {
-#pragma unroll
-    for (int pq = 0; pq < 3; ++pq) {
-      const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
-      const float apq = S[p * 3 + q];
-      if (apq == 0.f) continue;
-      const float tau = (S[q * 3 + q] - S[p * 3 + p]) / (2.f * apq);
-      const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
-      const float c = rsqrtf(fmaf(t, t, 1.f)), s = t * c;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float akp = S[k * 3 + p], akq = S[k * 3 + q];
-        S[k * 3 + p] = c * akp - s * akq;
-        S[k * 3 + q] = s * akp + c * akq;
-      }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float apk = S[p * 3 + k], aqk = S[q * 3 + k];
-        S[p * 3 + k] = c * apk - s * aqk;
-        S[q * 3 + k] = s * apk + c * aqk;
-      }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float vkp = Q[k * 3 + p], vkq = Q[k * 3 + q];
-        Q[k * 3 + p] = c * vkp - s * vkq;
-        Q[k * 3 + q] = s * vkp + c * vkq;
-      }
-    }
-  }
-}
-
 // U, V (columns u_k, v_k; det +1) of the projection of E onto the essential
 // matrices: E = U diag(s1, s2, s3) V^T with s1 >= s2 >= s3
 __device__ void essential_frames(const float* E, float* U, float* V) {
@@ -231,10 +193,12 @@ __device__ __forceinline__ int in_front(const float* R, const float* t, float4 x
   return (l1 > 0.f && l2 > 0.f) ? 1 : 0;
 }
 
+// rel_R == nullptr: only the (IRLS) eight-point estimates E0 [P*9] and valid
 __global__ void __launch_bounds__(kRelposeWarps * 32) k_relpose(const float4* __restrict__ kp,
                                                                 const int* __restrict__ seg_off, int P,
                                                                 int irls_iters, float delta, float* __restrict__ rel_R,
-                                                                float* __restrict__ rel_t, int* __restrict__ valid) {
+                                                                float* __restrict__ rel_t, int* __restrict__ valid,
+                                                                float* __restrict__ e0_out) {
   __shared__ float scratch[kRelposeWarps][2][81];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int n = blockIdx.x * kRelposeWarps + wib;
@@ -243,8 +207,11 @@ __global__ void __launch_bounds__(kRelposeWarps * 32) k_relpose(const float4* __
   float* A = scratch[wib][0];
   float* V = scratch[wib][1];
   if (e - b < 8) {
-    if (lane < 9) rel_R[9 * (size_t)n + lane] = (lane % 4 == 0) ? 1.f : 0.f;
-    if (lane < 3) rel_t[3 * (size_t)n + lane] = 0.f;
+    if (rel_R) {
+      if (lane < 9) rel_R[9 * (size_t)n + lane] = (lane % 4 == 0) ? 1.f : 0.f;
+      if (lane < 3) rel_t[3 * (size_t)n + lane] = 0.f;
+    }
+    if (e0_out && lane < 9) e0_out[9 * (size_t)n + lane] = 0.f;
     if (lane == 0) valid[n] = 0;
     return;
   }
@@ -255,6 +222,17 @@ __global__ void __launch_bounds__(kRelposeWarps * 32) k_relpose(const float4* __
     eight_point(kp, E, delta, b, e, lane, A, V, En);
 #pragma unroll
     for (int k = 0; k < 9; ++k) E[k] = En[k];
+  }
+  if (e0_out && lane < 9) {
+    float v = E[0];
+#pragma unroll
+    for (int k = 1; k < 9; ++k)
+      if (lane == k) v = E[k];
+    e0_out[9 * (size_t)n + lane] = v;
+  }
+  if (!rel_R) {
+    if (lane == 0) valid[n] = 1;
+    return;
   }
   float U[9], Vf[9];
   essential_frames(E, U, Vf);
@@ -302,10 +280,10 @@ __global__ void __launch_bounds__(kRelposeWarps * 32) k_relpose(const float4* __
 }  // namespace
 
 void launch_relpose(const fm_problem* pr, int irls_iters, float delta, float* rel_R, float* rel_t, int* valid,
-                    cudaStream_t s) {
+                    cudaStream_t s, float* e0_out) {
   if (pr->P == 0) return;
   k_relpose<<<(pr->P + kRelposeWarps - 1) / kRelposeWarps, kRelposeWarps * 32, 0, s>>>(
-      pr->kp, pr->seg_off, pr->P, irls_iters, delta, rel_R, rel_t, valid);
+      pr->kp, pr->seg_off, pr->P, irls_iters, delta, rel_R, rel_t, valid, e0_out);
 }
 
 }  // namespace fm

@@ -177,6 +177,10 @@ _SIGNATURES = {
     "fm_relative_translations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "fm_relative_poses": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_float,
                                          ctypes.POINTER(ctypes.c_int32)]),
+    "fm_focal_search": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_float,
+                                       ctypes.c_float, ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
+    "fm_set_focal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "fm_get_rel_poses": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "fm_translation_random_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "fm_translation_merge": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -694,6 +698,22 @@ class Problem:
         _check(lib().fm_relative_poses(self.handle, int(irls_iters), ctypes.c_float(delta), ctypes.byref(n)),
                self.handle)
         return n.value
+
+    def focal_search(self, group=None, n_groups=1, rho_min=1.0 / 3.0, rho_max=3.0, n_cand=1024, tau=0.01,
+                     irls_iters=0):
+        """fm_focal_search; returns (focal [N] float32, number of groups estimated)."""
+        out = np.empty(self.n_cams, np.float32)
+        g = None if group is None else np.ascontiguousarray(group, dtype=np.int32)
+        n = ctypes.c_int32()
+        _check(lib().fm_focal_search(self.handle, None if g is None else g.ctypes.data, int(n_groups),
+                                     ctypes.c_float(rho_min), ctypes.c_float(rho_max), int(n_cand),
+                                     ctypes.c_float(tau), int(irls_iters), out.ctypes.data, ctypes.byref(n)),
+               self.handle)
+        return out, n.value
+
+    def set_focal(self, focal):
+        f = np.ascontiguousarray(focal, dtype=np.float32)
+        _check(lib().fm_set_focal(self.handle, f.ctypes.data, 0), self.handle)
 
     def get_rel_poses(self, want_R=True, want_t=True):
         R = np.empty((self.n_pairs, 3, 3), np.float32) if want_R else None

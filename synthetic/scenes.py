@@ -266,12 +266,14 @@ def scene_c2(seed: int = 0, n_cams: int = 300, n_points: int = 100_000,
              sigma_px: float = 1.0, outlier_frac: float = 0.10,
              box=(50.0, 50.0, 10.0), max_depth: float = 30.0,
              track_mean: float = 4.0, jitter_deg: float = 15.0,
-             focal_range=(400.0, 900.0), chunk: int = 8192) -> Scene:
+             focal_range=(400.0, 900.0), chunk: int = 8192, focal_groups: int = 0) -> Scene:
     """Scene at scale: cameras on a smooth random trajectory (cubic B-spline
     through 8 random control points inside a 50x50x10 box) looking along the
     tangent with +-15deg jitter, f ~ U(400, 900) px, points uniform in the box,
     track length 2 + Geometric (mean ``track_mean``) capped by visibility (in
-    front, inside the image, depth <= 30)."""
+    front, inside the image, depth <= 30).  focal_groups = g > 0: the images
+    form g contiguous blocks along the trajectory, each sharing one focal
+    length (``meta["focal_group"]``); 0: one focal length per image."""
     rng = np.random.default_rng(seed)
     W, H = 640, 480
     N = n_cams
@@ -293,6 +295,10 @@ def scene_c2(seed: int = 0, n_cams: int = 300, n_points: int = 100_000,
         R[k] = Rk
         t[k] = -Rk @ pos[k]
     f = rng.uniform(focal_range[0], focal_range[1], size=N)
+    group = np.arange(N, dtype=np.int32)
+    if focal_groups > 0:
+        group = (np.arange(N) * focal_groups // N).astype(np.int32)
+        f = f[np.searchsorted(group, np.arange(focal_groups))][group]
     cx = np.full(N, W / 2.0)
     cy = np.full(N, H / 2.0)
     X = rng.uniform(0.0, 1.0, size=(n_points, 3)) * bx
@@ -328,7 +334,7 @@ def scene_c2(seed: int = 0, n_cams: int = 300, n_points: int = 100_000,
     return Scene(name="c2", seed=seed, width=W, height=H, focal=f, cx=cx, cy=cy,
                  R_gt=R, t_gt=t, points=X[track_pts],
                  meta=dict(sigma_px=sigma_px, outlier_frac=outlier_frac,
-                           n_points_sampled=n_points), **g)
+                           n_points_sampled=n_points, focal_group=group), **g)
 
 
 CONFIGS = {
