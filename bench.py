@@ -54,7 +54,7 @@ def args_():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2_5m", help="c2_5m (default), batch_c4, learned_c5, mlp_c2_5m or stages_c2_5m")
+    ap.add_argument("--config", default="c2_5m", help="c2_5m (default), batch_c4, learned_c5, mlp_c2_5m, stages_c2_5m or distortion_c2_5m")
     ap.add_argument("--train-scenes", type=int, default=200)
     ap.add_argument("--eval-cams", type=int, default=3000)
     ap.add_argument("--eval-points", type=int, default=1_000_000)
@@ -405,7 +405,9 @@ def run_stages(a):
     4 batched initialisations, the direct epipolar step (L1) and the compact
     epipolar step (the paper's form, cost independent of the keypoint pairs);
     and the wall time of one fm_relative_poses call (a1, every image pair) and
-    of one fm_focal_search call (one focal length, 1024 candidates).
+    of one fm_focal_search call (one focal length, 1024 candidates), one
+    distortion level (fm_distortion_pair_errors, 32 candidates) and one
+    fm_distortion_search call (32 candidates x 3 levels).
     Iterations run back to back, so the 80 MB of keypoints of the direct step
     are largely L2-resident here (the main line flushes L2 before every step)."""
     import torch
@@ -437,6 +439,16 @@ def run_stages(a):
         t0 = time.perf_counter()
         pr.focal_search(n_cand=1024)
         out["focal_search_shared_call"] = 1e6 * (time.perf_counter() - t0)
+        # distortion: one level (32 candidates on every image pair, the
+        # per-pair scores copied to the host) and a whole search (3 levels)
+        cands = np.linspace(-0.5, 0.5, 32).astype(np.float32)
+        pr.distortion_pair_errors(cands)
+        t0 = time.perf_counter()
+        pr.distortion_pair_errors(cands)
+        out["distortion_level_32cand_call"] = 1e6 * (time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        pr.distortion_search(n_cand=32, n_levels=3)
+        out["distortion_search_shared_call"] = 1e6 * (time.perf_counter() - t0)
         pr.set_rel_poses(Rij.astype(np.float32), tij.astype(np.float32))
 
         def timed(stage, lr):
@@ -533,6 +545,111 @@ def run_mlp(a):
             "kernels_us_per_launch": {k: 1e3 * v[1] / max(v[0], 1) for k, v in kt.items()},
             "gpu_launches": int(n_t + n_i), "clocks": clk.summary(), "mean_probability": pmean}
     print(json.dumps(line), flush=True)
+
+
+DIST_OPS_PER_EVAL = 123   # FP32 operations per (candidate, keypoint pair) of k_dist_errors' three passes
+# (8 + 8 + 8) + (8 + 8 + 4 + 4 + 45) + (8 + 8 + 4 + 10) = 123
+
+
+def run_distortion(a):
+    """--config distortion_c2_5m: the distortion interval search's scoring
+    kernel on the c2_5m scene observed through a division-model lens
+    (alpha = -0.2), with verified matches (no gross outliers): one level of 32 candidates over all 15,631 image pairs
+    (fm_distortion_pair_errors: per candidate and image pair, Hartley
+    normalisation, moments, Cholesky + inverse iteration, rank-2 F, error
+    sum), and one whole search (3 levels).  value = candidate x keypoint-pair evaluations/s of
+    the kernel (event time).  Roofline: FP32 issue -- each evaluation costs
+    DIST_OPS_PER_EVAL operations in the three passes over the keypoints
+    (undistortion 2 x 8, centroid sums 8; normalisation 4, products 4,
+    moments 45; normalisation 4, line and residual 10), the per-(candidate,
+    image pair) eigenvector not counted; the peak is 148 SMs x 128 FP32 lanes x the measured
+    SM clock."""
+    import torch
+    from paper_2505_04612_b300 import build as B
+    B.build()
+    from paper_2505_04612_b300 import fastmap as F
+    from synthetic.scenes import scene_c2
+    # verified matches (the step runs after two-view verification): no gross
+    # outliers, 1 px noise
+    sc = scene_c2(seed=a.seed, n_points=605_000, alpha=-0.2, outlier_frac=0.0)
+    Z = sc.n_kp
+    K = 32
+    dev = torch.device("cuda", 0)
+    flush_w = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush_r = torch.zeros(64 << 20, dtype=torch.float32, device=dev)
+
+    def flush():
+        flush_w.zero_()
+        flush_r.sum()
+        torch.cuda._sleep(1_000_000)
+
+    cands = torch.linspace(-0.5, 0.5, K, device=dev)
+    with F.problem_from_scene(sc) as pr:
+        for _ in range(a.warmup):
+            flush()
+            pr.distortion_pair_errors(cands)
+        torch.cuda.synchronize()
+        pr.timing(True)
+        with Clocks(0) as clk:
+            for _ in range(a.steps):
+                flush()
+                pr.distortion_pair_errors(cands)
+            kt = pr.timing_read()
+            pr.timing(False)
+            t0 = time.perf_counter()
+            alpha, _ = pr.distortion_search(n_cand=K, n_levels=3)
+            search_ms = 1e3 * (time.perf_counter() - t0)
+    n_k, ms_k = kt.get("k_dist_errors", (0, 0.0))
+    # one event pair brackets a level's launches (warp-per-pair and
+    # CTA-per-pair kernels, back to back on the stream)
+    level_us = 1e3 * ms_k / max(a.steps, 1)
+    evals = K * Z
+    cs = clk.summary()
+    sm_mhz = cs.get("sm_mhz") or 2032.0
+    peak = 148 * 128 * sm_mhz * 1e6 / 1e12           # T FP32 lane-ops/s
+    achieved = DIST_OPS_PER_EVAL * evals / (level_us * 1e-6) / 1e12
+    line = {"metric": "distortion search: candidate x keypoint-pair evaluations/s",
+            "value": evals / (level_us * 1e-6), "unit": "candidate-pair evals/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": level_us * 1e-3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"distortion_c2_5m: one level of 32 candidates over {sc.n_pairs} image pairs, "
+                                   f"{Z} keypoint pairs (c2_5m scene, division-model distortion alpha = -0.2)",
+                       "l2": "flushed before every timed level, then a 0.5 ms device sleep; neither timed"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32 ops/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_dist_errors",
+                         "ops_per_eval": DIST_OPS_PER_EVAL, "avg_level_us": level_us,
+                         "launches_per_level": n_k / max(a.steps, 1),
+                         "peak_kind": "148 SMs x 128 FP32 lanes x median SM clock (one op per lane per cycle)"},
+            "search_3_levels_ms": search_ms, "alpha_estimate": float(alpha[0]), "alpha_true": -0.2,
+            "gpu_launches": int(n_k), "clocks": cs}
+    if not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_distortion_baseline(sc, a.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def cpu_distortion_baseline(sc, seconds):
+    """The oracle's error sum (float64 normalised eight-point and error pass)
+    over image pairs in order, 32 candidates each, until `seconds` pass."""
+    from oracle import distortion as D
+    ci = sc.pair_i[sc.kp_img_pair]
+    cj = sc.pair_j[sc.kp_img_pair]
+    off = D.pair_offsets(sc.kp_img_pair, sc.n_pairs)
+    cands = np.linspace(-0.5, 0.5, 32)
+    done = 0
+    n = 0
+    t0 = time.perf_counter()
+    while n < sc.n_pairs and time.perf_counter() - t0 < seconds:
+        s = slice(off[n], off[n + 1])
+        if off[n + 1] - off[n] >= 8:
+            xd1 = D.normalised(sc.kp1_px[s], sc.cx[ci[s]], sc.cy[ci[s]])
+            xd2 = D.normalised(sc.kp2_px[s], sc.cx[cj[s]], sc.cy[cj[s]])
+            for al in cands:
+                D.error_sum(D.homogeneous(D.undistort(xd1, al)), D.homogeneous(D.undistort(xd2, al)))
+            done += len(cands) * (off[n + 1] - off[n])
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "candidate-pair evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} image pairs x 32 candidates ({done} evaluations) in {dt:.1f} s"}
 
 
 def run_learned(a):
@@ -647,6 +764,8 @@ def main():
         return run_learned(a)
     if a.config == "mlp_c2_5m":
         return run_mlp(a)
+    if a.config == "distortion_c2_5m":
+        return run_distortion(a)
     if a.config == "stages_c2_5m":
         return run_stages(a)
     import torch

@@ -359,6 +359,49 @@ fm_status fm_focal_search(fm_problem* problem, const int32_t* group, int32_t n_g
  * needed).  Synchronises. */
 fm_status fm_set_focal(fm_problem* problem, const float* focal, int32_t on_device);
 
+/* Distortion interval search (Sec. 3.1 "Distortion Estimation", Eq. 1;
+ * Appendix "Distortion Estimation").  One-parameter division model about the
+ * image centre (cx, cy): x_u = x_d / (1 + alpha r_d^2), x_d the observed
+ * offset from the centre in units of the half diagonal h = |(cx, cy)|.  A
+ * candidate alpha is scored on a set of image pairs by undistorting their
+ * keypoints (homogeneous (x_u, y_u, 1)), re-estimating each pair's
+ * fundamental matrix (Hartley-normalised linear eight-point: per image
+ * y = T x_u with the centroid at the origin and RMS distance sqrt(2); F^
+ * projected to rank 2, unit Frobenius norm) and averaging the epipolar error
+ * |y_2^T F^ y_1| (scale-free) over all their keypoint pairs; the lowest
+ * average wins (the first on ties).  The scores assume verified matches:
+ * the eight-point fit is least squares, so gross outliers (more than a few
+ * percent) bias the estimate.  Hierarchical: n_levels levels of
+ * n_cand (2..32) candidates spaced evenly over the interval, [alpha_min,
+ * alpha_max] at the first level and the winner's two neighbours (the end
+ * candidate at an end) at the next.  Groups (cameras) as in fm_focal_search:
+ * one at a time in the ready-pair order, an image of an estimated group
+ * undistorted with its alpha.  Works on the stored keypoints as they are
+ * (alpha of residual distortion once fm_set_distortion has been applied).
+ * alpha_out [N] (host): each image's group's alpha, 0 where the group never
+ * became ready; n_estimated (or NULL): groups estimated.  Image pairs with
+ * fewer than 8 keypoint pairs take no part.  Synchronises. */
+fm_status fm_distortion_search(fm_problem* problem, const int32_t* group, int32_t n_groups, float alpha_min,
+                               float alpha_max, int32_t n_cand, int32_t n_levels, float* alpha_out,
+                               int32_t* n_estimated);
+
+/* The scores behind fm_distortion_search, per image pair: err_out [P*n_cand]
+ * (pair-major; host or device as flagged) receives, for every image pair and
+ * candidate alpha_cand[k] (n_cand in 1..32; host or device as flagged)
+ * applied to both of its images, the sum of |y_2^T F^ y_1| over its keypoint
+ * pairs with F^ its own normalised rank-2 eight-point estimate; 0 for image
+ * pairs with fewer than 8 keypoint pairs.  Synchronises. */
+fm_status fm_distortion_pair_errors(fm_problem* problem, const float* alpha_cand, int32_t n_cand,
+                                    float* err_out, int32_t on_device);
+
+/* Undistorts the stored keypoints in place with alpha [N] per image (host
+ * or device as flagged; finite): x_c <- x_c / (1 + alpha r_d^2) in the
+ * calibrated coordinates.  A keypoint with 1 + alpha r_d^2 <= 0 has no
+ * undistorted point: its keypoint pair is left as it was and the call returns
+ * FM_ERR_INVALID_ARG after undistorting all others.  Relative poses and stage
+ * parameters are kept.  Synchronises. */
+fm_status fm_set_distortion(fm_problem* problem, const float* alpha, int32_t on_device);
+
 /* Copies the current relative rotations [P*9] / translations [P*3]; either
  * may be NULL.  Synchronises for host outputs. */
 fm_status fm_get_rel_poses(fm_problem* problem, float* rel_R, float* rel_t, int32_t out_on_device);

@@ -21,7 +21,8 @@ const char* const kKernelNames[kKCount] = {
     "k_calibrate", "k_seg_offsets", "k_run_tables", "k_ea_tables", "k_ea_direct",
     "k_ea_segments", "k_rot_pairs", "k_trn_targets", "k_trn_pairs", "k_cam", "k_sum_fixed",
     "k_ea_reweight", "k_w_build", "k_ea_compact", "k_mart_iter", "k_reltrans", "k_merge",
-    "k_triangulate", "k_ea_direct_loss", "k_ea_direct_coef", "k_mlp_pair_tables", "k_mlp_infer"};
+    "k_triangulate", "k_ea_direct_loss", "k_ea_direct_coef", "k_mlp_pair_tables", "k_mlp_infer",
+    "k_relpose", "k_focal_vote", "k_dist_errors", "k_dist_reduce"};
 }
 
 namespace {
@@ -187,6 +188,11 @@ void release(fm_problem* pr) {
   pr->graphs.clear();
   if (pr->cap_stream) cudaStreamDestroy(pr->cap_stream);
   pr->cap_stream = nullptr;
+  if (pr->aux_stream) cudaStreamDestroy(pr->aux_stream);
+  if (pr->aux_fork) cudaEventDestroy(pr->aux_fork);
+  if (pr->aux_join) cudaEventDestroy(pr->aux_join);
+  pr->aux_stream = nullptr;
+  pr->aux_fork = pr->aux_join = nullptr;
   if (pr->graph_in) cudaEventDestroy(pr->graph_in);
   if (pr->graph_out) cudaEventDestroy(pr->graph_out);
   pr->graph_in = pr->graph_out = nullptr;
@@ -718,6 +724,160 @@ fm_status resize_runs(fm_problem* pr, int runs) {
   return FM_OK;
 }
 
+
+// Greedy order of the cameras (groups of images sharing intrinsics) of the
+// focal and distortion searches: an image pair is ready for a group when both
+// images are in it, or one is and the other's group is done; the group with
+// the most ready image pairs goes next (the lowest id on ties), never one
+// with none.  Counts are kept incrementally.
+struct ReadyOrder {
+  const std::vector<int>& g;
+  const std::vector<int>& hi;
+  const std::vector<int>& hj;
+  std::vector<std::vector<int>> inc;   // usable image pairs touching each group
+  std::vector<int64_t> ready;
+  std::vector<char> done;
+
+  ReadyOrder(const std::vector<int>& g_, const std::vector<int>& hi_, const std::vector<int>& hj_,
+             const std::vector<int>& usable, int n_groups)
+      : g(g_), hi(hi_), hj(hj_), inc(n_groups), ready(n_groups, 0), done(n_groups, 0) {
+    for (size_t n = 0; n < hi.size(); ++n) {
+      if (!usable[n]) continue;
+      const int a = g[hi[n]], b = g[hj[n]];
+      inc[a].push_back((int)n);
+      if (b != a) inc[b].push_back((int)n);
+      else ready[a] += 1;
+    }
+  }
+  int next() const {
+    int best = -1;
+    int64_t bn = 0;
+    for (size_t q = 0; q < ready.size(); ++q)
+      if (!done[q] && ready[q] > bn) {
+        best = (int)q;
+        bn = ready[q];
+      }
+    return best;
+  }
+  // ready pairs of `best` in increasing order, with the group of each side
+  // (-1 where the side belongs to `best`)
+  void list(int best, std::vector<int>& pairs, std::vector<int>& gi_fixed, std::vector<int>& gj_fixed) const {
+    pairs.clear();
+    gi_fixed.clear();
+    gj_fixed.clear();
+    for (int n : inc[best]) {
+      const int a = g[hi[n]], b = g[hj[n]];
+      if (!((a == best && b == best) || (a == best && done[b]) || (b == best && done[a]))) continue;
+      pairs.push_back(n);
+      gi_fixed.push_back(a == best ? -1 : a);
+      gj_fixed.push_back(b == best ? -1 : b);
+    }
+  }
+  void finish(int best) {
+    done[best] = 1;
+    for (int n : inc[best]) {
+      const int a = g[hi[n]], b = g[hj[n]];
+      if (a == b) continue;
+      const int other = (a == best) ? b : a;
+      if (!done[other]) ready[other] += 1;
+    }
+  }
+};
+
+fm_status check_groups(fm_problem* pr, const int32_t* group, int32_t n_groups, std::vector<int>& g) {
+  if (n_groups < 1 || (!group && n_groups != 1)) return fail(pr, FM_ERR_INVALID_ARG, "n_groups >= 1 (1 without group)");
+  g.assign(pr->N, 0);
+  if (group)
+    for (int c = 0; c < pr->N; ++c) {
+      g[c] = group[c];
+      if (g[c] < 0 || g[c] >= n_groups) return fail(pr, FM_ERR_INVALID_ARG, "group id outside [0, n_groups)");
+    }
+  return FM_OK;
+}
+
+// device scratch of one search call, freed on every return path
+struct Scratch {
+  std::vector<void*> ptrs;
+  cudaError_t ce = cudaSuccess;
+  template <typename T>
+  T* get(size_t n) {
+    void* q = nullptr;
+    if (ce == cudaSuccess) ce = cudaMalloc(&q, std::max<size_t>(n * sizeof(T), 16));
+    if (ce == cudaSuccess) ptrs.push_back(q);
+    return (T*)q;
+  }
+  ~Scratch() {
+    for (void* q : ptrs) cudaFree(q);
+  }
+};
+
+// work items of k_dist_errors: image pairs and their output rows, those of at
+// most kDistSplit keypoint pairs (one warp each) first, then the larger ones
+// (one CTA each); returns the number of small ones
+int split_by_size(const std::vector<int>& pairs, const std::vector<int>& off, std::vector<int>& idx,
+                  std::vector<int>& row) {
+  idx.clear();
+  row.clear();
+  for (int big = 0; big < 2; ++big)
+    for (size_t q = 0; q < pairs.size(); ++q) {
+      const int n = pairs[q];
+      if ((off[n + 1] - off[n] > fm::kDistSplit) == (big == 1)) {
+        idx.push_back(n);
+        row.push_back((int)q);
+      }
+    }
+  int n_small = 0;
+  for (int n : idx)
+    if (off[n + 1] - off[n] <= fm::kDistSplit) ++n_small;
+  return n_small;
+}
+
+// One level of distortion scores: the items of more than kDistSplit keypoint
+// pairs (one CTA each) on the auxiliary stream, forked from and joined back
+// to the problem's stream, the others (one warp each) on the problem's
+// stream, so that the two launches overlap.  items/rows: n_small small items
+// first, then M - n_small large ones.
+cudaError_t dist_level(fm_problem* pr, const float* scale, const int* items, const int* rows, const float* fix_i,
+                       const float* fix_j, int M, int n_small, const float* cand, int K, float* err) {
+  cudaStream_t s = pr->stream;
+  const int n_big = M - n_small;
+  if (n_big > 0 && !pr->aux_stream) {
+    cudaError_t ce = cudaStreamCreateWithFlags(&pr->aux_stream, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pr->aux_fork, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pr->aux_join, cudaEventDisableTiming);
+    if (ce != cudaSuccess) return ce;
+  }
+  Timed t(pr, fm::kKDistErrors);
+  if (n_big > 0) {
+    cudaError_t ce = cudaEventRecord(pr->aux_fork, s);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(pr->aux_stream, pr->aux_fork, 0);
+    if (ce != cudaSuccess) return ce;
+    fm::launch_dist_errors(pr, scale, items + n_small, rows + n_small, fix_i, fix_j, n_big, true, cand, K, err,
+                           pr->aux_stream);
+  }
+  fm::launch_dist_errors(pr, scale, items, rows, fix_i, fix_j, n_small, false, cand, K, err, s);
+  if (n_big > 0) {
+    if (n_small > 0) pr->k_launches[fm::kKDistErrors] += 1;   // two launches in one bracket
+    cudaError_t ce = cudaEventRecord(pr->aux_join, pr->aux_stream);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, pr->aux_join, 0);
+    if (ce != cudaSuccess) return ce;
+  }
+  return cudaGetLastError();
+}
+
+// f0 / half diagonal of every image (x_d = s x_c for keypoints calibrated at f0)
+cudaError_t image_scales(const fm_problem* pr, std::vector<float>& scale) {
+  std::vector<float> f, cx, cy;
+  cudaError_t ce = fetch(f, pr->focal, pr->N, true);
+  if (ce == cudaSuccess) ce = fetch(cx, pr->cx, pr->N, true);
+  if (ce == cudaSuccess) ce = fetch(cy, pr->cy, pr->N, true);
+  if (ce != cudaSuccess) return ce;
+  scale.resize(pr->N);
+  for (int c = 0; c < pr->N; ++c)
+    scale[c] = (float)((double)f[c] / std::sqrt((double)cx[c] * cx[c] + (double)cy[c] * cy[c]));
+  return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -838,7 +998,10 @@ fm_status fm_relative_poses(fm_problem* pr, int32_t irls_iters, float delta, int
   cudaStream_t s = pr->stream;
   int* d_valid = nullptr;
   FM_ALLOC(pr, d_valid, (size_t)pr->P);
-  fm::launch_relpose(pr, irls_iters, delta, pr->rel_R, pr->rel_t, d_valid, s);
+  {
+    Timed t(pr, fm::kKRelpose);
+    fm::launch_relpose(pr, irls_iters, delta, pr->rel_R, pr->rel_t, d_valid, s);
+  }
   cudaError_t le = cudaGetLastError();
   std::vector<int> h(pr->P);
   cudaError_t ce = le;
@@ -862,19 +1025,17 @@ fm_status fm_focal_search(fm_problem* pr, const int32_t* group, int32_t n_groups
   fm::g_plain_once = true;
   if (!pr) return FM_ERR_INVALID_ARG;
   if (!focal_out) return fail(pr, FM_ERR_INVALID_ARG, "focal_out is NULL");
-  if (n_groups < 1 || (!group && n_groups != 1)) return fail(pr, FM_ERR_INVALID_ARG, "n_groups >= 1 (1 without group)");
   if (!(rho_min > 0.f && rho_max > rho_min) || !std::isfinite(rho_max))
     return fail(pr, FM_ERR_INVALID_ARG, "0 < rho_min < rho_max required");
   if (n_cand < 2 || n_cand > 65536) return fail(pr, FM_ERR_INVALID_ARG, "n_cand must be in [2, 65536]");
   if (!(tau > 0.f) || !std::isfinite(tau)) return fail(pr, FM_ERR_INVALID_ARG, "tau must be finite and > 0");
   if (irls_iters < 0 || irls_iters > 16) return fail(pr, FM_ERR_INVALID_ARG, "irls_iters must be in [0, 16]");
+  std::vector<int> g;
+  {
+    fm_status st = check_groups(pr, group, n_groups, g);
+    if (st != FM_OK) return st;
+  }
   const int N = pr->N, P = pr->P;
-  std::vector<int> g(N, 0);
-  if (group)
-    for (int c = 0; c < N; ++c) {
-      g[c] = group[c];
-      if (g[c] < 0 || g[c] >= n_groups) return fail(pr, FM_ERR_INVALID_ARG, "group id outside [0, n_groups)");
-    }
   cudaStream_t s = pr->stream;
   std::vector<int> hi, hj;
   std::vector<float> f0;
@@ -886,74 +1047,48 @@ fm_status fm_focal_search(fm_problem* pr, const int32_t* group, int32_t n_groups
   for (int k = 0; k < n_cand; ++k)
     rhos[k] = (float)std::exp(std::log((double)rho_min) +
                               k * (std::log((double)rho_max) - std::log((double)rho_min)) / (n_cand - 1));
-  float *e0 = nullptr, *d_rhos = nullptr, *votes = nullptr, *fix = nullptr;
-  int *valid = nullptr, *idx = nullptr;
-  auto release_all = [&]() {
-    for (void* q : {(void*)e0, (void*)d_rhos, (void*)votes, (void*)fix, (void*)valid, (void*)idx})
-      if (q) cudaFree(q);
-  };
-  cudaError_t ce = cudaSuccess;
-  auto dmalloc = [&](void** q, size_t bytes) {
-    if (ce == cudaSuccess) ce = cudaMalloc(q, std::max<size_t>(bytes, 16));
-  };
-  dmalloc((void**)&e0, sizeof(float) * 9 * P);
-  dmalloc((void**)&valid, sizeof(int) * P);
-  dmalloc((void**)&d_rhos, sizeof(float) * n_cand);
-  dmalloc((void**)&votes, sizeof(float) * n_cand);
-  dmalloc((void**)&idx, sizeof(int) * P);
-  dmalloc((void**)&fix, sizeof(float) * 2 * P);
+  Scratch sc;
+  float* e0 = sc.get<float>((size_t)9 * P);
+  int* valid = sc.get<int>(P);
+  float* d_rhos = sc.get<float>(n_cand);
+  float* votes = sc.get<float>(n_cand);
+  int* idx = sc.get<int>(P);
+  float* fix = sc.get<float>((size_t)2 * P);
+  cudaError_t ce = sc.ce;
   if (ce != cudaSuccess) {
-    release_all();
     cudaGetLastError();
     return fail(pr, ce == cudaErrorMemoryAllocation ? FM_ERR_OOM : FM_ERR_CUDA, "focal search: allocation");
   }
-  fm::launch_relpose(pr, irls_iters, 1e-5f, nullptr, nullptr, valid, s, e0);
+  {
+    Timed t(pr, fm::kKRelpose);
+    fm::launch_relpose(pr, irls_iters, 1e-5f, nullptr, nullptr, valid, s, e0);
+  }
   ce = cudaGetLastError();
   std::vector<int> hv(P);
   if (ce == cudaSuccess && P > 0) ce = cudaMemcpyAsync(hv.data(), valid, sizeof(int) * P, cudaMemcpyDeviceToHost, s);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_rhos, rhos.data(), sizeof(float) * n_cand, cudaMemcpyHostToDevice, s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-  // greedy order of the groups by ready image pairs (incremental counts)
-  std::vector<std::vector<int>> inc(n_groups);   // valid image pairs touching each group
-  std::vector<int64_t> ready(n_groups, 0);
-  for (int n = 0; n < P && ce == cudaSuccess; ++n) {
-    if (!hv[n]) continue;
-    const int a = g[hi[n]], b = g[hj[n]];
-    inc[a].push_back(n);
-    if (b != a) inc[b].push_back(n);
-    else ready[a] += 1;
-  }
-  std::vector<char> done(n_groups, 0);
+  if (ce != cudaSuccess) return fail(pr, FM_ERR_CUDA, std::string("focal search: ") + cudaGetErrorString(ce));
+  ReadyOrder order(g, hi, hj, hv, n_groups);
   std::vector<float> rho_g(n_groups, 1.f);
-  int n_done = 0;
-  std::vector<int> list;
-  std::vector<float> fixes;
+  std::vector<int> list, fi, fj;
+  std::vector<float> fixes(2 * (size_t)std::max(P, 1));
   std::vector<float> hvotes(n_cand);
-  while (ce == cudaSuccess) {
-    int best = -1;
-    int64_t bn = 0;
-    for (int q = 0; q < n_groups; ++q)
-      if (!done[q] && ready[q] > bn) {
-        best = q;
-        bn = ready[q];
-      }
-    if (best < 0) break;
-    list.clear();
-    fixes.assign(2 * P, -1.f);
-    int M = 0;
-    for (int n : inc[best]) {
-      const int a = g[hi[n]], b = g[hj[n]];
-      const bool ok = (a == best && b == best) || (a == best && done[b]) || (b == best && done[a]);
-      if (!ok) continue;
-      list.push_back(n);
-      fixes[M] = (a == best) ? -1.f : rho_g[a];
-      fixes[P + M] = (b == best) ? -1.f : rho_g[b];
-      ++M;
+  int n_done = 0;
+  for (int best = order.next(); best >= 0 && ce == cudaSuccess; best = order.next()) {
+    order.list(best, list, fi, fj);
+    const int M = (int)list.size();
+    for (int q = 0; q < M; ++q) {
+      fixes[q] = fi[q] < 0 ? -1.f : rho_g[fi[q]];
+      fixes[P + q] = fj[q] < 0 ? -1.f : rho_g[fj[q]];
     }
     ce = cudaMemcpyAsync(idx, list.data(), sizeof(int) * M, cudaMemcpyHostToDevice, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(fix, fixes.data(), sizeof(float) * 2 * P, cudaMemcpyHostToDevice, s);
     if (ce != cudaSuccess) break;
-    fm::launch_focal_vote(e0, idx, fix, fix + P, M, d_rhos, n_cand, tau, votes, s);
+    {
+      Timed t(pr, fm::kKFocalVote);
+      fm::launch_focal_vote(e0, idx, fix, fix + P, M, d_rhos, n_cand, tau, votes, s);
+    }
     ce = cudaGetLastError();
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(hvotes.data(), votes, sizeof(float) * n_cand, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
@@ -962,20 +1097,180 @@ fm_status fm_focal_search(fm_problem* pr, const int32_t* group, int32_t n_groups
     for (int q = 1; q < n_cand; ++q)
       if (hvotes[q] > hvotes[k]) k = q;   // the first maximum
     rho_g[best] = rhos[k];
-    done[best] = 1;
+    order.finish(best);
     ++n_done;
-    // image pairs between `best` and a group still open become ready for it
-    for (int n : inc[best]) {
-      const int a = g[hi[n]], b = g[hj[n]];
-      if (a == b) continue;
-      const int other = (a == best) ? b : a;
-      if (!done[other]) ready[other] += 1;
-    }
   }
-  release_all();
   if (ce != cudaSuccess) return fail(pr, FM_ERR_CUDA, std::string("focal search: ") + cudaGetErrorString(ce));
-  for (int c = 0; c < N; ++c) focal_out[c] = done[g[c]] ? f0[c] * rho_g[g[c]] : f0[c];
+  for (int c = 0; c < N; ++c) focal_out[c] = order.done[g[c]] ? f0[c] * rho_g[g[c]] : f0[c];
   if (n_estimated) *n_estimated = n_done;
+  return FM_OK;
+}
+
+fm_status fm_distortion_search(fm_problem* pr, const int32_t* group, int32_t n_groups, float alpha_min,
+                               float alpha_max, int32_t n_cand, int32_t n_levels, float* alpha_out,
+                               int32_t* n_estimated) {
+  fm::g_plain_once = true;
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!alpha_out) return fail(pr, FM_ERR_INVALID_ARG, "alpha_out is NULL");
+  if (!(alpha_max > alpha_min) || !std::isfinite(alpha_min) || !std::isfinite(alpha_max))
+    return fail(pr, FM_ERR_INVALID_ARG, "finite alpha_min < alpha_max required");
+  if (n_cand < 2 || n_cand > 32) return fail(pr, FM_ERR_INVALID_ARG, "n_cand must be in [2, 32]");
+  if (n_levels < 1 || n_levels > 16) return fail(pr, FM_ERR_INVALID_ARG, "n_levels must be in [1, 16]");
+  std::vector<int> g;
+  {
+    fm_status st = check_groups(pr, group, n_groups, g);
+    if (st != FM_OK) return st;
+  }
+  const int N = pr->N, P = pr->P;
+  cudaStream_t s = pr->stream;
+  std::vector<int> hi, hj, off;
+  std::vector<float> scale;
+  FM_CUDA(pr, fetch(hi, pr->pair_i, P, true));
+  FM_CUDA(pr, fetch(hj, pr->pair_j, P, true));
+  FM_CUDA(pr, fetch(off, pr->seg_off, (size_t)P + 1, true));
+  FM_CUDA(pr, image_scales(pr, scale));
+  std::vector<int> usable(P);
+  for (int n = 0; n < P; ++n) usable[n] = off[n + 1] - off[n] >= 8;
+  Scratch sc;
+  float* d_scale = sc.get<float>(N);
+  int* idx = sc.get<int>((size_t)2 * P);   // pairs, then rows
+  float* fix = sc.get<float>((size_t)2 * P);
+  float* d_cand = sc.get<float>(32);
+  float* err = sc.get<float>((size_t)32 * P);
+  float* sums = sc.get<float>(32);
+  cudaError_t ce = sc.ce;
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    return fail(pr, ce == cudaErrorMemoryAllocation ? FM_ERR_OOM : FM_ERR_CUDA, "distortion search: allocation");
+  }
+  ce = cudaMemcpyAsync(d_scale, scale.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s);
+  ReadyOrder order(g, hi, hj, usable, n_groups);
+  std::vector<float> alpha_g(n_groups, 0.f);
+  std::vector<int> list, fi, fj, items, rows;
+  std::vector<float> fixes(2 * (size_t)std::max(P, 1));
+  std::vector<float> cand(n_cand), hs(n_cand);
+  int n_done = 0;
+  for (int best = ce == cudaSuccess ? order.next() : -1; best >= 0 && ce == cudaSuccess; best = order.next()) {
+    order.list(best, list, fi, fj);
+    const int M = (int)list.size();
+    for (int q = 0; q < M; ++q) {
+      fixes[q] = fi[q] < 0 ? NAN : alpha_g[fi[q]];
+      fixes[P + q] = fj[q] < 0 ? NAN : alpha_g[fj[q]];
+    }
+    const int n_small = split_by_size(list, off, items, rows);
+    ce = cudaMemcpyAsync(idx, items.data(), sizeof(int) * M, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(idx + P, rows.data(), sizeof(int) * M, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(fix, fixes.data(), sizeof(float) * 2 * P, cudaMemcpyHostToDevice, s);
+    // hierarchical levels: candidates evenly over [lo, hi]; the winner's
+    // neighbours (the end candidate at an end) bound the next level
+    double lo = alpha_min, hi_a = alpha_max, est = alpha_min;
+    for (int level = 0; level < n_levels && ce == cudaSuccess; ++level) {
+      for (int k = 0; k < n_cand; ++k) cand[k] = (float)(lo + (hi_a - lo) * k / (n_cand - 1));
+      ce = cudaMemcpyAsync(d_cand, cand.data(), sizeof(float) * n_cand, cudaMemcpyHostToDevice, s);
+      if (ce != cudaSuccess) break;
+      ce = dist_level(pr, d_scale, idx, idx + P, fix, fix + P, M, n_small, d_cand, n_cand, err);
+      if (ce != cudaSuccess) break;
+      {
+        Timed t(pr, fm::kKDistReduce);
+        fm::launch_dist_reduce(err, M, n_cand, sums, s);
+      }
+      ce = cudaGetLastError();
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(hs.data(), sums, sizeof(float) * n_cand, cudaMemcpyDeviceToHost, s);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+      if (ce != cudaSuccess) break;
+      // every candidate's average divides by the same keypoint-pair count, so
+      // the sums rank them alike
+      int k = -1;
+      for (int q = 0; q < n_cand; ++q)   // the first minimum; NaN never wins
+        if (!std::isnan(hs[q]) && (k < 0 || hs[q] < hs[k])) k = q;
+      if (k < 0) k = 0;
+      est = cand[k];
+      lo = cand[std::max(k - 1, 0)];
+      hi_a = cand[std::min(k + 1, n_cand - 1)];
+    }
+    alpha_g[best] = (float)est;
+    order.finish(best);
+    ++n_done;
+  }
+  if (ce != cudaSuccess) return fail(pr, FM_ERR_CUDA, std::string("distortion search: ") + cudaGetErrorString(ce));
+  for (int c = 0; c < N; ++c) alpha_out[c] = order.done[g[c]] ? alpha_g[g[c]] : 0.f;
+  if (n_estimated) *n_estimated = n_done;
+  return FM_OK;
+}
+
+fm_status fm_distortion_pair_errors(fm_problem* pr, const float* alpha_cand, int32_t n_cand, float* err_out,
+                                    int32_t on_device) {
+  fm::g_plain_once = true;
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!alpha_cand || !err_out) return fail(pr, FM_ERR_INVALID_ARG, "alpha_cand and err_out are required");
+  if (n_cand < 1 || n_cand > 32) return fail(pr, FM_ERR_INVALID_ARG, "n_cand must be in [1, 32]");
+  const int N = pr->N, P = pr->P;
+  cudaStream_t s = pr->stream;
+  std::vector<float> cand, scale;
+  std::vector<int> off, all(P), items, rows;
+  FM_CUDA(pr, fetch(cand, alpha_cand, n_cand, on_device != 0));
+  FM_CUDA(pr, image_scales(pr, scale));
+  FM_CUDA(pr, fetch(off, pr->seg_off, (size_t)P + 1, true));
+  for (int n = 0; n < P; ++n) all[n] = n;
+  const int n_small = split_by_size(all, off, items, rows);
+  Scratch sc;
+  float* d_scale = sc.get<float>(N);
+  float* d_cand = sc.get<float>(32);
+  int* d_idx = sc.get<int>((size_t)2 * P);
+  float* err = on_device ? err_out : sc.get<float>((size_t)n_cand * P);
+  cudaError_t ce = sc.ce;
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    return fail(pr, ce == cudaErrorMemoryAllocation ? FM_ERR_OOM : FM_ERR_CUDA, "distortion errors: allocation");
+  }
+  ce = cudaMemcpyAsync(d_scale, scale.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_cand, cand.data(), sizeof(float) * n_cand, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess && P > 0) ce = cudaMemcpyAsync(d_idx, items.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess && P > 0)
+    ce = cudaMemcpyAsync(d_idx + P, rows.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = dist_level(pr, d_scale, d_idx, d_idx + P, nullptr, nullptr, P, n_small, d_cand, n_cand, err);
+  if (ce == cudaSuccess && !on_device && P > 0)
+    ce = cudaMemcpyAsync(err_out, err, sizeof(float) * n_cand * P, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return fail(pr, FM_ERR_CUDA, std::string("distortion errors: ") + cudaGetErrorString(ce));
+  return FM_OK;
+}
+
+fm_status fm_set_distortion(fm_problem* pr, const float* alpha, int32_t on_device) {
+  fm::g_plain_once = true;
+  if (!pr) return FM_ERR_INVALID_ARG;
+  if (!alpha) return fail(pr, FM_ERR_INVALID_ARG, "alpha is NULL");
+  std::vector<float> a, scale;
+  FM_CUDA(pr, fetch(a, alpha, pr->N, on_device != 0));
+  for (int c = 0; c < pr->N; ++c)
+    if (!std::isfinite(a[c])) return fail(pr, FM_ERR_INVALID_ARG, "alpha[" + std::to_string(c) + "] must be finite");
+  FM_CUDA(pr, image_scales(pr, scale));
+  Scratch sc;
+  float* d_scale = sc.get<float>(pr->N);
+  float* d_alpha = sc.get<float>(pr->N);
+  int* bad = sc.get<int>(1);
+  cudaError_t ce = sc.ce;
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    return fail(pr, ce == cudaErrorMemoryAllocation ? FM_ERR_OOM : FM_ERR_CUDA, "set distortion: allocation");
+  }
+  cudaStream_t s = pr->stream;
+  int h_bad = 0;
+  ce = cudaMemcpyAsync(d_scale, scale.data(), sizeof(float) * pr->N, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_alpha, a.data(), sizeof(float) * pr->N, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(bad, 0, sizeof(int), s);
+  if (ce == cudaSuccess) {
+    fm::launch_undistort(pr, d_scale, d_alpha, bad, s);
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return fail(pr, FM_ERR_CUDA, std::string("set distortion: ") + cudaGetErrorString(ce));
+  pr->W_valid = false;
+  pr->graph_epoch += 1;
+  if (h_bad)
+    return fail(pr, FM_ERR_INVALID_ARG,
+                "1 + alpha r^2 <= 0 at some keypoint: those keypoint pairs were left as they were");
   return FM_OK;
 }
 

@@ -60,7 +60,8 @@ enum : int {
 enum KernelId : int {
   kKCalibrate = 0, kKSegOffsets, kKRunTables, kKEaTables, kKEaDirect, kKEaSegments,
   kKRotPairs, kKTrnTargets, kKTrnPairs, kKCamUpdate, kKLossSum, kKEaReweight, kKWBuild,
-  kKEaCompact, kKMartIter, kKRelTrans, kKMerge, kKTriangulate, kKEaDirectLoss, kKEaDirectCoef, kKMlpTables, kKMlpInfer, kKCount
+  kKEaCompact, kKMartIter, kKRelTrans, kKMerge, kKTriangulate, kKEaDirectLoss, kKEaDirectCoef, kKMlpTables, kKMlpInfer,
+  kKRelpose, kKFocalVote, kKDistErrors, kKDistReduce, kKCount
 };
 extern const char* const kKernelNames[kKCount];
 
@@ -201,6 +202,8 @@ struct fm_problem {
   uint64_t graph_clock = 0;
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t aux_stream = nullptr;   // second stream of the distortion scoring (created on first use)
+  cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
   cudaEvent_t graph_in = nullptr, graph_out = nullptr;   // orders replays by completion
   int64_t graph_replays = 0;
   // fm_loss_grad with host buffers: pinned staging of the parameters and the
@@ -335,6 +338,19 @@ void launch_focal_vote(const float* e0, const int* idx, const float* fix_i, cons
                        const float* rhos, int K, float tau, float* votes, cudaStream_t s);
 // kp (x1, y1) *= f_old[i]/f_new[i], (x2, y2) *= f_old[j]/f_new[j] per keypoint pair
 void launch_recalibrate(const fm_problem* pr, const float* f_old, const float* f_new, cudaStream_t s);
+
+// distortion interval search (fm_distortion.cu): err[row[q]*K + k] = sum over
+// the keypoint pairs of work item q's image pair idx[q] of |y_2^T F^ y_1| at
+// candidate k (idx/row null: identity; fix_i/fix_j: known alpha per row or
+// NaN, may be null).  big: the items have more than kDistSplit keypoint pairs
+// (a CTA each), else at most kDistSplit (a warp each).
+constexpr int kDistSplit = 1024;
+void launch_dist_errors(const fm_problem* pr, const float* scale, const int* idx, const int* row,
+                        const float* fix_i, const float* fix_j, int M, bool big, const float* cand, int K,
+                        float* err, cudaStream_t s);
+void launch_dist_reduce(const float* err, int M, int K, float* out, cudaStream_t s);
+// kp <- undistorted at alpha [N] (scale [N] = f0 / half diagonal); *bad |= 1 where 1 + alpha r^2 <= 0
+void launch_undistort(const fm_problem* pr, const float* scale, const float* alpha, int* bad, cudaStream_t s);
 
 // learned weights (fm_mlp.cu)
 size_t mlp_grad_smem();

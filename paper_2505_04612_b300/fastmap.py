@@ -181,6 +181,12 @@ _SIGNATURES = {
                                        ctypes.c_float, ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
     "fm_set_focal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "fm_distortion_search": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_float,
+                                            ctypes.c_float, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_int32)]),
+    "fm_distortion_pair_errors": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                                 ctypes.c_int32]),
+    "fm_set_distortion": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "fm_get_rel_poses": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "fm_translation_random_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "fm_translation_merge": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -714,6 +720,36 @@ class Problem:
     def set_focal(self, focal):
         f = np.ascontiguousarray(focal, dtype=np.float32)
         _check(lib().fm_set_focal(self.handle, f.ctypes.data, 0), self.handle)
+
+    def distortion_search(self, group=None, n_groups=1, alpha_min=-0.5, alpha_max=0.5, n_cand=32, n_levels=3):
+        """fm_distortion_search; returns (alpha [N] float32, number of groups estimated)."""
+        out = np.empty(self.n_cams, np.float32)
+        g = None if group is None else np.ascontiguousarray(group, dtype=np.int32)
+        n = ctypes.c_int32()
+        _check(lib().fm_distortion_search(self.handle, None if g is None else g.ctypes.data, int(n_groups),
+                                          ctypes.c_float(alpha_min), ctypes.c_float(alpha_max), int(n_cand),
+                                          int(n_levels), out.ctypes.data, ctypes.byref(n)), self.handle)
+        return out, n.value
+
+    def distortion_pair_errors(self, alpha_cand):
+        """fm_distortion_pair_errors; returns [P, n_cand] float32 on the side
+        of alpha_cand (numpy array or CUDA tensor)."""
+        if hasattr(alpha_cand, "is_cuda") and alpha_cand.is_cuda:
+            import torch
+            c = alpha_cand.to(torch.float32).contiguous().reshape(-1)
+            out = torch.empty((self.n_pairs, c.numel()), dtype=torch.float32, device=c.device)
+            _check(lib().fm_distortion_pair_errors(self.handle, c.data_ptr(), c.numel(), out.data_ptr(), 1),
+                   self.handle)
+            return out
+        c = np.ascontiguousarray(alpha_cand, dtype=np.float32).reshape(-1)
+        out = np.empty((self.n_pairs, len(c)), np.float32)
+        _check(lib().fm_distortion_pair_errors(self.handle, c.ctypes.data, len(c), out.ctypes.data, 0),
+               self.handle)
+        return out
+
+    def set_distortion(self, alpha):
+        a = np.ascontiguousarray(alpha, dtype=np.float32)
+        _check(lib().fm_set_distortion(self.handle, a.ctypes.data, 0), self.handle)
 
     def get_rel_poses(self, want_R=True, want_t=True):
         R = np.empty((self.n_pairs, 3, 3), np.float32) if want_R else None

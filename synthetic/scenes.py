@@ -262,18 +262,39 @@ def _bspline(ctrl: np.ndarray, s: np.ndarray):
     return pos, tan
 
 
+def _distort(uv, alpha, cx, cy):
+    """Observed pixels of ideal pixels uv [...,2] under the division model
+    x_u = x_d / (1 + alpha r_d^2) (x about the centre, in half-diagonal
+    units): the radius solving that equation closest to r_u,
+    r_d = 2 r_u / (1 + sqrt(1 - 4 alpha r_u^2))."""
+    c = np.stack([cx, cy], axis=-1)
+    h = np.linalg.norm(c, axis=-1, keepdims=True)
+    x = (uv - c) / h
+    r2 = np.sum(x * x, axis=-1, keepdims=True)
+    disc = 1.0 - 4.0 * alpha[..., None] * r2
+    if np.any(disc < 0.0):
+        raise ValueError("alpha too large for the image: no distorted radius")
+    return c + h * x * (2.0 / (1.0 + np.sqrt(disc)))
+
+
 def scene_c2(seed: int = 0, n_cams: int = 300, n_points: int = 100_000,
              sigma_px: float = 1.0, outlier_frac: float = 0.10,
              box=(50.0, 50.0, 10.0), max_depth: float = 30.0,
              track_mean: float = 4.0, jitter_deg: float = 15.0,
-             focal_range=(400.0, 900.0), chunk: int = 8192, focal_groups: int = 0) -> Scene:
+             focal_range=(400.0, 900.0), chunk: int = 8192, focal_groups: int = 0,
+             alpha=0.0) -> Scene:
     """Scene at scale: cameras on a smooth random trajectory (cubic B-spline
     through 8 random control points inside a 50x50x10 box) looking along the
     tangent with +-15deg jitter, f ~ U(400, 900) px, points uniform in the box,
     track length 2 + Geometric (mean ``track_mean``) capped by visibility (in
     front, inside the image, depth <= 30).  focal_groups = g > 0: the images
     form g contiguous blocks along the trajectory, each sharing one focal
-    length (``meta["focal_group"]``); 0: one focal length per image."""
+    length (``meta["focal_group"]``); 0: one focal length per image.
+    alpha: radial distortion of the observed pixels (one-parameter division
+    model about the image centre, radii in units of the half diagonal), a
+    scalar for every image or one value per focal group; the visibility test
+    uses the undistorted projection, the pixel noise is added after the
+    distortion (``meta["alpha"]`` per image)."""
     rng = np.random.default_rng(seed)
     W, H = 640, 480
     N = n_cams
@@ -301,6 +322,8 @@ def scene_c2(seed: int = 0, n_cams: int = 300, n_points: int = 100_000,
         f = f[np.searchsorted(group, np.arange(focal_groups))][group]
     cx = np.full(N, W / 2.0)
     cy = np.full(N, H / 2.0)
+    a = np.asarray(alpha, np.float64)
+    alpha_cam = np.full(N, float(a)) if a.ndim == 0 else a[group]
     X = rng.uniform(0.0, 1.0, size=(n_points, 3)) * bx
     p_geom = 1.0 / (track_mean - 1.0)   # k = 2 + (Geometric(p) - 1), mean track_mean
     groups = {}                          # k -> list of (cams [n,k], uv [n,k,2], point ids [n])
@@ -324,6 +347,8 @@ def scene_c2(seed: int = 0, n_cams: int = 300, n_points: int = 100_000,
         cams = np.concatenate([g[0] for g in groups[kk]])
         uv = np.concatenate([g[1] for g in groups[kk]])
         pts = np.concatenate([g[2] for g in groups[kk]])
+        if np.any(alpha_cam != 0.0):
+            uv = _distort(uv, alpha_cam[cams], cx[cams], cy[cams])
         # per-observation noise (shared by every pair that uses the observation)
         uv = uv + rng.normal(0.0, sigma_px, size=uv.shape)
         track_cams.append(cams)
@@ -334,7 +359,7 @@ def scene_c2(seed: int = 0, n_cams: int = 300, n_points: int = 100_000,
     return Scene(name="c2", seed=seed, width=W, height=H, focal=f, cx=cx, cy=cy,
                  R_gt=R, t_gt=t, points=X[track_pts],
                  meta=dict(sigma_px=sigma_px, outlier_frac=outlier_frac,
-                           n_points_sampled=n_points, focal_group=group), **g)
+                           n_points_sampled=n_points, focal_group=group, alpha=alpha_cam), **g)
 
 
 CONFIGS = {
