@@ -277,24 +277,15 @@ def _distort(uv, alpha, cx, cy):
     return c + h * x * (2.0 / (1.0 + np.sqrt(disc)))
 
 
-def scene_c2(seed: int = 0, n_cams: int = 300, n_points: int = 100_000,
+def _observe_c2(seed: int = 0, n_cams: int = 300, n_points: int = 100_000,
              sigma_px: float = 1.0, outlier_frac: float = 0.10,
              box=(50.0, 50.0, 10.0), max_depth: float = 30.0,
              track_mean: float = 4.0, jitter_deg: float = 15.0,
              focal_range=(400.0, 900.0), chunk: int = 8192, focal_groups: int = 0,
-             alpha=0.0) -> Scene:
-    """Scene at scale: cameras on a smooth random trajectory (cubic B-spline
-    through 8 random control points inside a 50x50x10 box) looking along the
-    tangent with +-15deg jitter, f ~ U(400, 900) px, points uniform in the box,
-    track length 2 + Geometric (mean ``track_mean``) capped by visibility (in
-    front, inside the image, depth <= 30).  focal_groups = g > 0: the images
-    form g contiguous blocks along the trajectory, each sharing one focal
-    length (``meta["focal_group"]``); 0: one focal length per image.
-    alpha: radial distortion of the observed pixels (one-parameter division
-    model about the image centre, radii in units of the half diagonal), a
-    scalar for every image or one value per focal group; the visibility test
-    uses the undistorted projection, the pixel noise is added after the
-    distortion (``meta["alpha"]`` per image)."""
+             alpha=0.0):
+    """Cameras, points and noisy track observations of ``scene_c2`` (same
+    arguments; ``outlier_frac`` is not used here).  Returns the generator and
+    a dict of the scene's parts."""
     rng = np.random.default_rng(seed)
     W, H = 640, 480
     N = n_cams
@@ -354,12 +345,143 @@ def scene_c2(seed: int = 0, n_cams: int = 300, n_points: int = 100_000,
         track_cams.append(cams)
         track_uv.append(uv)
         track_pts.append(pts)
+    return rng, dict(W=W, H=H, R=R, t=t, f=f, cx=cx, cy=cy, X=X, group=group, alpha_cam=alpha_cam,
+                     track_cams=track_cams, track_uv=track_uv, track_pts=track_pts)
+
+
+def scene_c2(seed: int = 0, n_cams: int = 300, n_points: int = 100_000,
+             sigma_px: float = 1.0, outlier_frac: float = 0.10,
+             box=(50.0, 50.0, 10.0), max_depth: float = 30.0,
+             track_mean: float = 4.0, jitter_deg: float = 15.0,
+             focal_range=(400.0, 900.0), chunk: int = 8192, focal_groups: int = 0,
+             alpha=0.0) -> Scene:
+    """Scene at scale: cameras on a smooth random trajectory (cubic B-spline
+    through 8 random control points inside a 50x50x10 box) looking along the
+    tangent with +-15deg jitter, f ~ U(400, 900) px, points uniform in the box,
+    track length 2 + Geometric (mean ``track_mean``) capped by visibility (in
+    front, inside the image, depth <= 30).  focal_groups = g > 0: the images
+    form g contiguous blocks along the trajectory, each sharing one focal
+    length (``meta["focal_group"]``); 0: one focal length per image.
+    alpha: radial distortion of the observed pixels (one-parameter division
+    model about the image centre, radii in units of the half diagonal), a
+    scalar for every image or one value per focal group; the visibility test
+    uses the undistorted projection, the pixel noise is added after the
+    distortion (``meta["alpha"]`` per image)."""
+    rng, o = _observe_c2(seed, n_cams, n_points, sigma_px, outlier_frac, box, max_depth, track_mean,
+                         jitter_deg, focal_range, chunk, focal_groups, alpha)
+    W, H = o["W"], o["H"]
+    track_cams, track_uv, track_pts = o["track_cams"], o["track_uv"], o["track_pts"]
+    R, t, f, cx, cy, X = o["R"], o["t"], o["f"], o["cx"], o["cy"], o["X"]
+    group, alpha_cam = o["group"], o["alpha_cam"]
     g = _grouped_tracks_to_pairs(rng, track_cams, track_uv, W, H, outlier_frac, 8)
     track_pts = np.concatenate(track_pts)
     return Scene(name="c2", seed=seed, width=W, height=H, focal=f, cx=cx, cy=cy,
                  R_gt=R, t_gt=t, points=X[track_pts],
                  meta=dict(sigma_px=sigma_px, outlier_frac=outlier_frac,
                            n_points_sampled=n_points, focal_group=group, alpha=alpha_cam), **g)
+
+
+@dataclass
+class RawMatches:
+    """Keypoints per image and raw pairwise matches (before track completion).
+
+    Keypoints are grouped by image: those of image c are kp_off[c] ..
+    kp_off[c+1]-1, in a random order (a detector's order carries no meaning).
+    matches [M,2] holds keypoint ids (the first in the lower image), grouped by
+    image pair.  true_track [K] is the generator's track of each keypoint (-1
+    for distractors that observe no point)."""
+    kp_off: np.ndarray       # [N+1] int32
+    kp_px: np.ndarray        # [K,2] float32
+    matches: np.ndarray      # [M,2] int32
+    true_track: np.ndarray   # [K] int32
+    n_spurious: int
+    focal: np.ndarray
+    cx: np.ndarray
+    cy: np.ndarray
+    R_gt: np.ndarray
+    t_gt: np.ndarray
+    width: int
+    height: int
+
+    @property
+    def n_cams(self) -> int:
+        return int(self.kp_off.shape[0] - 1)
+
+    @property
+    def n_kp(self) -> int:
+        return int(self.kp_off[-1])
+
+
+def raw_matches_c2(seed: int = 0, n_cams: int = 300, n_points: int = 100_000, recall: float = 0.5,
+                   spurious_frac: float = 0.0, distractors: int = 0, sigma_px: float = 1.0,
+                   **scene_kw) -> RawMatches:
+    """Raw matches of the ``scene_c2`` geometry with low matching recall:
+    every observation of a track is one keypoint of its image; each pair of
+    observations of a track is matched independently with probability
+    ``recall`` (a track may fall apart into several components); a fraction
+    ``spurious_frac`` of extra matches join a random keypoint of the lower
+    image of a matched image pair to a random keypoint of the other (these
+    merge unrelated tracks); ``distractors`` unmatched keypoints per image."""
+    _, o = _observe_c2(seed, n_cams, n_points, sigma_px, 0.0, **scene_kw)
+    rng = np.random.default_rng(1_000_003 + seed)   # the matching draws, apart from the scene's
+    N = n_cams
+    cams = [c.reshape(-1) for c in o["track_cams"]]
+    uvs = [u.reshape(-1, 2) for u in o["track_uv"]]
+    tids, base = [], 0
+    for c in o["track_cams"]:
+        n, k = c.shape
+        tids.append(np.repeat(np.arange(base, base + n), k))
+        base += n
+    obs_cam = np.concatenate(cams).astype(np.int64)
+    obs_uv = np.concatenate(uvs)
+    obs_track = np.concatenate(tids).astype(np.int64)
+    n_obs = len(obs_cam)
+    # distractors
+    d_cam = np.repeat(np.arange(N), distractors)
+    d_uv = rng.uniform([0.0, 0.0], [o["W"], o["H"]], size=(len(d_cam), 2))
+    all_cam = np.concatenate([obs_cam, d_cam])
+    all_uv = np.concatenate([obs_uv, d_uv])
+    all_track = np.concatenate([obs_track, np.full(len(d_cam), -1)])
+    # keypoint ids: grouped by image, random order inside an image
+    order = np.lexsort((rng.random(len(all_cam)), all_cam))
+    node_of = np.empty(len(all_cam), np.int64)
+    node_of[order] = np.arange(len(all_cam))
+    kp_off = np.concatenate([[0], np.cumsum(np.bincount(all_cam, minlength=N))]).astype(np.int32)
+    kp_px = all_uv[order].astype(np.float32)
+    true_track = all_track[order].astype(np.int32)
+    # matches inside tracks: observations of a track are contiguous (cameras
+    # increasing); each pair of them is matched with probability `recall`
+    o1, o2, off = [], [], 0
+    for c in o["track_cams"]:
+        n, k = c.shape
+        first = off + np.arange(n) * k
+        for a in range(k):
+            for b in range(a + 1, k):
+                keep = rng.random(n) < recall
+                o1.append(first[keep] + a)
+                o2.append(first[keep] + b)
+        off += n * k
+    o1 = np.concatenate(o1) if o1 else np.zeros(0, np.int64)
+    o2 = np.concatenate(o2) if o2 else np.zeros(0, np.int64)
+    u, v = node_of[o1], node_of[o2]
+    # spurious matches between images already matched
+    n_sp = int(round(spurious_frac * len(u)))
+    if n_sp > 0 and len(u) > 0:
+        pick = rng.integers(0, len(u), n_sp)
+        ci, cj = all_cam[o1[pick]], all_cam[o2[pick]]
+        su = kp_off[ci] + (rng.random(n_sp) * (kp_off[ci + 1] - kp_off[ci])).astype(np.int64)
+        sv = kp_off[cj] + (rng.random(n_sp) * (kp_off[cj + 1] - kp_off[cj])).astype(np.int64)
+        u = np.concatenate([u, su])
+        v = np.concatenate([v, sv])
+    # group by image pair (lower image first), then by keypoint ids
+    ci, cj = np.searchsorted(kp_off, u, side="right") - 1, np.searchsorted(kp_off, v, side="right") - 1
+    swap = ci > cj
+    u, v = np.where(swap, v, u), np.where(swap, u, v)
+    ci, cj = np.where(swap, cj, ci), np.where(swap, ci, cj)
+    order = np.lexsort((v, u, cj, ci))
+    matches = np.stack([u[order], v[order]], axis=1).astype(np.int32)
+    return RawMatches(kp_off=kp_off, kp_px=kp_px, matches=matches, true_track=true_track, n_spurious=n_sp,
+                      focal=o["f"], cx=o["cx"], cy=o["cy"], R_gt=o["R"], t_gt=o["t"], width=o["W"], height=o["H"])
 
 
 CONFIGS = {
