@@ -54,7 +54,8 @@ def args_():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2_5m", help="c2_5m (default), batch_c4, learned_c5, mlp_c2_5m, stages_c2_5m or distortion_c2_5m")
+    ap.add_argument("--config", default="c2_5m", help="c2_5m (default), batch_c4, learned_c5, mlp_c2_5m, stages_c2_5m, distortion_c2_5m or "
+                         "tracks_c2_5m")
     ap.add_argument("--train-scenes", type=int, default=200)
     ap.add_argument("--eval-cams", type=int, default=3000)
     ap.add_argument("--eval-points", type=int, default=1_000_000)
@@ -627,6 +628,87 @@ def run_distortion(a):
     print(json.dumps(line), flush=True)
 
 
+def run_tracks(a):
+    """--config tracks_c2_5m: track completion (fm_tracks_complete) of raw
+    matches with the c2_5m geometry (300 images, 605,000 points, track
+    length 2 + Geometric(mean 4)): each pair of a track's observations matched
+    with probability 0.5, 1 % spurious matches (which make some components
+    inconsistent), 20 distractor keypoints per image; inputs resident on the
+    device.  value = completed keypoint pairs per second of the whole call
+    (union-find, two stable radix sorts, emission, grouping, gathers, the
+    library's own allocations and host synchronisation), wall clock around
+    the synchronous call.  Roofline: the call's algorithmic bytes (matches
+    read, keypoint pixels gathered, the six output arrays written) over its
+    time, against the measured copy bandwidth; the sorts' passes and the
+    union-find's random accesses are the gap."""
+    import torch
+    from paper_2505_04612_b300 import build as B
+    B.build()
+    from paper_2505_04612_b300 import fastmap as F
+    from synthetic.scenes import raw_matches_c2
+    rm = raw_matches_c2(seed=a.seed, n_points=605_000, recall=0.5, spurious_frac=0.01, distractors=20)
+    dev = torch.device("cuda", 0)
+    off = torch.as_tensor(rm.kp_off).to(dev)
+    mt = torch.as_tensor(rm.matches).to(dev)
+    px = torch.as_tensor(rm.kp_px).to(dev)
+    flush_w = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush_r = torch.zeros(64 << 20, dtype=torch.float32, device=dev)
+    out = None
+    for _ in range(a.warmup):
+        out = F.complete_tracks(off, mt, px)
+    torch.cuda.synchronize()
+    times = []
+    with Clocks(0) as clk:
+        for _ in range(a.steps):
+            flush_w.zero_()
+            flush_r.sum()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = F.complete_tracks(off, mt, px)
+            times.append(time.perf_counter() - t0)
+    Z, P, M, K = int(out["node1"].numel()), int(out["pair_i"].numel()), len(rm.matches), rm.n_kp
+    t_med = float(np.median(times))
+    algo_bytes = 8 * M + 4 * (rm.n_cams + 1) + 8 * K + Z * (4 * 4 + 2 * 8) + 8 * P
+    peak, kind = peaks()
+    achieved = algo_bytes / t_med / 1e9
+    line = {"metric": "track completion: completed keypoint pairs/s (whole call)",
+            "value": Z / t_med, "unit": "keypoint pairs/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * t_med, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"tracks_c2_5m: {rm.n_cams} images, {K} keypoints, {M} raw matches "
+                                   f"(recall 0.5, {rm.n_spurious} spurious, 20 distractors per image)",
+                       "l2": "flushed before every timed call (256 MB write + 256 MB read); inputs on the device"},
+            "outputs": {"n_img_pairs": P, "n_kp_pairs": Z, "n_tracks": int(out["n_tracks"]),
+                        "n_inconsistent": int(out["n_inconsistent"])},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "fm_tracks_complete (whole call)",
+                         "bytes_per_call": algo_bytes, "peak_kind": f"{kind} copy bandwidth"},
+            "ms_min": 1e3 * min(times), "ms_max": 1e3 * max(times), "clocks": clk.summary()}
+    if not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_tracks_baseline(rm, a.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def cpu_tracks_baseline(rm, seconds):
+    """The oracle (plain Python union-find and emission) on the keypoints of
+    the first n images and the matches among them, n grown until one call
+    takes about `seconds` / 4; rate = completed pairs / s."""
+    from oracle import tracks as T
+    n, rate, sample = 8, None, ""
+    while n <= rm.n_cams:
+        K = int(rm.kp_off[n])
+        m = rm.matches[(rm.matches[:, 0] < K) & (rm.matches[:, 1] < K)]
+        t0 = time.perf_counter()
+        out = T.complete_tracks(rm.kp_off[:n + 1], m)
+        dt = time.perf_counter() - t0
+        rate = len(out["node1"]) / dt
+        sample = f"first {n} images: {K} keypoints, {len(m)} matches, {len(out['node1'])} pairs in {dt:.1f} s"
+        if dt > seconds / 4:
+            break
+        n *= 2
+    return {"value": rate, "unit": "keypoint pairs/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+
 def cpu_distortion_baseline(sc, seconds):
     """The oracle's error sum (float64 normalised eight-point and error pass)
     over image pairs in order, 32 candidates each, until `seconds` pass."""
@@ -766,6 +848,8 @@ def main():
         return run_mlp(a)
     if a.config == "distortion_c2_5m":
         return run_distortion(a)
+    if a.config == "tracks_c2_5m":
+        return run_tracks(a)
     if a.config == "stages_c2_5m":
         return run_stages(a)
     import torch

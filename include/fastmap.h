@@ -402,6 +402,64 @@ fm_status fm_distortion_pair_errors(fm_problem* problem, const float* alpha_cand
  * parameters are kept.  Synchronises. */
 fm_status fm_set_distortion(fm_problem* problem, const float* alpha, int32_t on_device);
 
+/* ------------------------------------------------ tracks and image pairs
+ * Preprocessing of raw matches before a problem is built (Appendix "Tracks"
+ * and "Filtering"). */
+
+typedef struct fm_tracks fm_tracks;   /* opaque; results held on the device */
+
+/* Track completion.  Keypoints are grouped by image: those of image c are
+ * kp_off[c] .. kp_off[c+1]-1 (kp_off [n_images + 1], kp_off[0] = 0,
+ * non-decreasing; n_images in 2..65535).  matches [n_matches * 2] holds
+ * keypoint ids (u, v) of raw matches between two different images, in any
+ * order and orientation.  A track is a connected component of the keypoint
+ * graph with at least two keypoints; tracks are numbered by their smallest
+ * keypoint id.  A consistent track (no two keypoints in one image) yields
+ * every pair of its keypoints; an inconsistent one yields its raw matches as
+ * given (duplicates included).  The keypoint pairs are oriented from the lower
+ * to the higher image and grouped by image pair (i < j) in increasing (i, j);
+ * inside an image pair the consistent tracks' pairs come first, by track,
+ * then the raw matches of inconsistent tracks in input order.  Image pairs
+ * with fewer than min_pairs (>= 1) keypoint pairs are dropped with their
+ * pairs.  kp_px [K * 2] (or NULL): pixel coordinates, gathered into the
+ * output pairs.  on_device: kp_off, matches and kp_px are device pointers,
+ * complete when the call starts.  The labels, order and outputs are
+ * deterministic.  Errors: FM_ERR_INVALID_ARG for a match outside [0, K) or
+ * inside one image (checked on the device), FM_ERR_TIMEOUT if a union-find
+ * step bound is reached.  *out is released with fm_tracks_destroy.  Device
+ * memory (scratch and results) comes from a stream-ordered pool that the
+ * library creates on first use and keeps for the process, so that later calls
+ * reuse it without mapping memory.  Synchronises. */
+fm_status fm_tracks_complete(int32_t n_images, const int32_t* kp_off, int64_t n_matches, const int32_t* matches,
+                             const float* kp_px, int32_t min_pairs, int32_t on_device, fm_tracks** out);
+
+/* Sizes of a completion: tracks, image pairs P, keypoint pairs Z and
+ * inconsistent tracks; any pointer may be NULL. */
+fm_status fm_tracks_info(const fm_tracks* tracks, int64_t* n_tracks, int64_t* n_img_pairs, int64_t* n_kp_pairs,
+                         int64_t* n_inconsistent);
+
+/* Copies the results (host or device buffers as flagged; any may be NULL):
+ * pair_i, pair_j [P]; kp_img_pair, node1 (keypoint in image pair_i), node2,
+ * kp_track [Z]; kp1_px, kp2_px [Z * 2] when kp_px was given.  The arrays feed
+ * fm_problem_desc directly (kp_track as the track ids). */
+fm_status fm_tracks_copy(const fm_tracks* tracks, int32_t* pair_i, int32_t* pair_j, int32_t* kp_img_pair,
+                         int32_t* node1, int32_t* node2, int32_t* kp_track, float* kp1_px, float* kp2_px,
+                         int32_t on_device);
+
+void fm_tracks_destroy(fm_tracks* tracks);
+
+/* Adaptive image-pair filtering (host).  An image pair is kept while its
+ * count (e.g. its number of keypoint pairs) is above the threshold t; t
+ * starts at t_start and becomes max(t / 2, t_min) while the kept pairs leave
+ * the n_images images in more than one connected component and t > t_min.
+ * At the final t, images outside the largest component (the one holding the
+ * smallest image id on ties) are outliers: image_valid[c] = 0 (or NULL) and
+ * every image pair touching one is dropped.  keep [n_pairs] receives 1 for
+ * the kept pairs, *t_used (or NULL) the final threshold. */
+fm_status fm_filter_image_pairs(int32_t n_images, int32_t n_pairs, const int32_t* pair_i, const int32_t* pair_j,
+                                const int32_t* counts, double t_start, double t_min, int32_t* keep,
+                                int32_t* image_valid, double* t_used);
+
 /* Copies the current relative rotations [P*9] / translations [P*3]; either
  * may be NULL.  Synchronises for host outputs. */
 fm_status fm_get_rel_poses(fm_problem* problem, float* rel_R, float* rel_t, int32_t out_on_device);

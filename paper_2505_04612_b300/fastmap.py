@@ -187,6 +187,16 @@ _SIGNATURES = {
     "fm_distortion_pair_errors": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                                  ctypes.c_int32]),
     "fm_set_distortion": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "fm_tracks_complete": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "fm_tracks_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "fm_tracks_copy": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 8 + [ctypes.c_int32]),
+    "fm_tracks_destroy": (None, [ctypes.c_void_p]),
+    "fm_filter_image_pairs": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "fm_get_rel_poses": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "fm_translation_random_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "fm_translation_merge": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -412,6 +422,71 @@ def fm_ea_loss_grad_static(kp, seg_off, pair_i, pair_j, params, weights, n_cams,
                                       int(n_cams), P, Z, int(loss), ctypes.c_float(inv_z), args[6][0],
                                       args[7][0], _stream_handle(stream))
     _check(st, None)
+
+
+def complete_tracks(kp_off, matches, kp_px=None, min_pairs=1):
+    """fm_tracks_complete + fm_tracks_copy.  Inputs as numpy arrays (host) or
+    CUDA tensors (device; outputs then stay on the device as tensors).
+    Returns a dict: pair_i, pair_j [P]; kp_img_pair, node1, node2, kp_track
+    [Z]; kp1_px, kp2_px [Z,2] when kp_px is given; n_tracks, n_inconsistent."""
+    dev = hasattr(matches, "is_cuda") and matches.is_cuda
+    if dev:
+        import torch
+        off = kp_off.to(torch.int32).contiguous()
+        m = matches.to(torch.int32).contiguous().reshape(-1, 2)
+        px = None if kp_px is None else kp_px.to(torch.float32).contiguous()
+        torch.cuda.current_stream().synchronize()   # the library reads them on its own stream
+        a_off, a_m, a_px = off.data_ptr(), m.data_ptr(), (None if px is None else px.data_ptr())
+        n_img, n_m = off.numel() - 1, m.shape[0]
+    else:
+        off = np.ascontiguousarray(kp_off, dtype=np.int32)
+        m = np.ascontiguousarray(matches, dtype=np.int32).reshape(-1, 2)
+        px = None if kp_px is None else np.ascontiguousarray(kp_px, dtype=np.float32)
+        a_off, a_m, a_px = off.ctypes.data, m.ctypes.data, (None if px is None else px.ctypes.data)
+        n_img, n_m = len(off) - 1, len(m)
+    h = ctypes.c_void_p()
+    _check(lib().fm_tracks_complete(int(n_img), a_off, int(n_m), a_m if n_m else None, a_px, int(min_pairs),
+                                    int(dev), ctypes.byref(h)))
+    try:
+        nt, P, Z, ni = (ctypes.c_int64() for _ in range(4))
+        _check(lib().fm_tracks_info(h, ctypes.byref(nt), ctypes.byref(P), ctypes.byref(Z), ctypes.byref(ni)))
+        P, Z = P.value, Z.value
+        if dev:
+            import torch
+            mk = lambda *shape, dt=torch.int32: torch.empty(shape, dtype=dt, device=m.device)  # noqa: E731
+            ptr = lambda a: a.data_ptr()  # noqa: E731
+        else:
+            mk = lambda *shape, dt=np.int32: np.empty(shape, dtype=dt)  # noqa: E731
+            ptr = lambda a: a.ctypes.data  # noqa: E731
+        f32 = (torch.float32 if dev else np.float32)
+        out = dict(pair_i=mk(P), pair_j=mk(P), kp_img_pair=mk(Z), node1=mk(Z), node2=mk(Z), kp_track=mk(Z))
+        if px is not None:
+            out["kp1_px"] = mk(Z, 2, dt=f32)
+            out["kp2_px"] = mk(Z, 2, dt=f32)
+        _check(lib().fm_tracks_copy(h, *(ptr(out[k]) for k in ["pair_i", "pair_j", "kp_img_pair", "node1", "node2",
+                                                              "kp_track"]),
+                                    ptr(out["kp1_px"]) if px is not None else None,
+                                    ptr(out["kp2_px"]) if px is not None else None, int(dev)))
+        out["n_tracks"] = nt.value
+        out["n_inconsistent"] = ni.value
+        return out
+    finally:
+        lib().fm_tracks_destroy(h)
+
+
+def filter_image_pairs(n_images, pair_i, pair_j, counts, t_start, t_min):
+    """fm_filter_image_pairs (host): returns (keep [P] bool, image_valid [N]
+    bool, threshold used)."""
+    pi = np.ascontiguousarray(pair_i, dtype=np.int32)
+    pj = np.ascontiguousarray(pair_j, dtype=np.int32)
+    c = np.ascontiguousarray(counts, dtype=np.int32)
+    keep = np.empty(len(pi), np.int32)
+    valid = np.empty(int(n_images), np.int32)
+    t = ctypes.c_double()
+    _check(lib().fm_filter_image_pairs(int(n_images), len(pi), pi.ctypes.data, pj.ctypes.data, c.ctypes.data,
+                                       ctypes.c_double(t_start), ctypes.c_double(t_min), keep.ctypes.data,
+                                       valid.ctypes.data, ctypes.byref(t)))
+    return keep.astype(bool), valid.astype(bool), t.value
 
 
 def fm_mlp_set_params(handle, theta):
