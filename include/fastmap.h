@@ -668,7 +668,7 @@ typedef struct {
                                   (a thread's pairs never cross an image-pair
                                   end; a warp run is 32 threads' pairs) */
   int32_t ctas_per_sm;         /* persistent CTAs per SM; 0 = as many as fit */
-  float us_per_eval;           /* fm_autotune: median time of the chosen one */
+  float us_per_eval;           /* fm_autotune: fastest time of the chosen one */
 } fm_tuning;
 
 /* Sets / reads the configuration (changing pairs_per_lane rebuilds the
@@ -677,11 +677,12 @@ fm_status fm_set_tuning(fm_problem* problem, const fm_tuning* tuning);
 fm_status fm_get_tuning(const fm_problem* problem, fm_tuning* tuning);
 
 /* Autotuner: times the direct kernel (L1, the problem's current weights and
- * epipolar parameters, or generated parameters when none are set) for both
- * tiles and every CTA count per SM that fits, `repeats`
- * times each with L2 flushed before every launch, and keeps the fastest
- * (median).  The choice changes no result beyond the order of additions
- * inside an image pair's records.  Synchronises. */
+ * epipolar parameters, or generated parameters when none are set) for the
+ * three tiles and every CTA count per SM that fits, `repeats` times each
+ * (CTA counts in round robin), every launch after an L2 flush and a 0.2 ms
+ * device idle, and keeps the configuration with the fastest single launch
+ * (noise only adds time).  The choice changes no result beyond the order of
+ * additions inside an image pair's records.  Synchronises. */
 fm_status fm_autotune(fm_problem* problem, int32_t repeats, fm_tuning* best);
 
 /* fm_step replays captured CUDA graphs of 16 iterations (one graph launch

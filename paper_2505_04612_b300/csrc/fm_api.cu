@@ -2032,46 +2032,58 @@ fm_status fm_autotune(fm_problem* pr, int32_t repeats, fm_tuning* best_out) {
     cudaGetLastError();
     flush = nullptr;
   }
-  cudaEvent_t a = nullptr, b = nullptr;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
   const int old_u = pr->ea_U, old_c = pr->ea_ctas_per_sm;
   fm_tuning best{old_u, old_c, 3.4e38f};
   fm_status st = FM_OK;
+  std::vector<cudaEvent_t> ev;
   for (int U : {15, 11, 21}) {
     if (pr->Z == 0) break;
     if (U != pr->ea_U && (st = build_direct_tables(pr, U)) != FM_OK) break;
     const int max_c = fm::direct_max_ctas_per_sm(pr);
     // round robin over the CTA counts, so that a slow drift of the device
-    // (clocks, power) does not favour the first ones
-    std::vector<std::vector<float>> ms(max_c + 1);
-    for (int k = 0; k < repeats && st == FM_OK; ++k)
-      for (int c = 1; c <= max_c; ++c) {
+    // (clocks, power) does not favour the first ones; every sample after an
+    // L2 flush and a 0.2 ms device idle, no host synchronisation in between
+    const size_t n_ev = 2 * (size_t)repeats * max_c;
+    while (ev.size() < n_ev) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) break;
+      ev.push_back(e);
+    }
+    if (ev.size() < n_ev) {
+      cudaGetLastError();
+      st = fail(pr, FM_ERR_CUDA, "autotune: events");
+      break;
+    }
+    size_t q = 0;
+    for (int k = 0; k < repeats; ++k)
+      for (int c = 1; c <= max_c; ++c, q += 2) {
         pr->ea_ctas_per_sm = c;
         if (flush) fm::launch_l2_flush(flush, flush_bytes, k & 0xff, s);
-        cudaEventRecord(a, s);
+        fm::launch_idle(200000u, s);
+        cudaEventRecord(ev[q], s);
         fm::g_plain_once = true;
         fm::launch_ea_direct(pr, pr->ea_w, FM_EA_L1, s);
-        cudaEventRecord(b, s);
-        cudaError_t ce = cudaEventSynchronize(b);
-        float t = 0.f;
-        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, a, b);
-        if (ce != cudaSuccess) {
-          st = fail(pr, FM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
-          break;
-        }
-        ms[c].push_back(t);
+        cudaEventRecord(ev[q + 1], s);
         pr->k_launches[fm::kKEaDirect] += 1;
       }
-    if (st != FM_OK) break;
-    for (int c = 1; c <= max_c; ++c) {
-      std::sort(ms[c].begin(), ms[c].end());
-      const float med = 1000.f * ms[c][ms[c].size() / 2];
-      if (med < best.us_per_eval) best = fm_tuning{U, c, med};
+    cudaError_t ce = cudaStreamSynchronize(s);
+    // the fastest sample of each CTA count: noise only adds time
+    std::vector<float> fastest(max_c + 1, 3.4e38f);
+    q = 0;
+    for (int k = 0; k < repeats && ce == cudaSuccess; ++k)
+      for (int c = 1; c <= max_c && ce == cudaSuccess; ++c, q += 2) {
+        float t = 0.f;
+        ce = cudaEventElapsedTime(&t, ev[q], ev[q + 1]);
+        fastest[c] = std::min(fastest[c], 1000.f * t);
+      }
+    if (ce != cudaSuccess) {
+      st = fail(pr, FM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+      break;
     }
+    for (int c = 1; c <= max_c; ++c)
+      if (fastest[c] < best.us_per_eval) best = fm_tuning{U, c, fastest[c]};
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
+  for (cudaEvent_t e : ev) cudaEventDestroy(e);
   if (flush) cudaFree(flush);
   if (st == FM_OK && pr->Z > 0) st = fm_set_tuning(pr, &best);
   if (st != FM_OK) {   // leave the previous tile in place

@@ -277,6 +277,8 @@ void launch_seg_records(const int* seg_off, const int* G, const int4* wrun_info,
                         cudaStream_t s);
 void launch_check_finite(const float* x, int64_t n, int* err, int bit, cudaStream_t s);
 // fills buf and reads it back, leaving L2 full of clean lines of buf
+// the stream idles on the device for about ns nanoseconds (one thread)
+void launch_idle(unsigned ns, cudaStream_t s);
 void launch_l2_flush(void* buf, size_t bytes, int fill, cudaStream_t s);
 void launch_exclusive_scan_info(int4* wrun_info, int n, int64_t* total_out_dev, cudaStream_t s);
 

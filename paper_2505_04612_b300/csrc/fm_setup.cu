@@ -230,6 +230,14 @@ void launch_seg_records(const int* seg_off, const int* G, const int4* wrun_info,
   k_seg_records<<<(P + 255) / 256, 256, 0, s>>>(seg_off, G, wrun_info, P, seg_rec);
 }
 
+// one thread idles for about ns nanoseconds (bounded: __nanosleep steps of
+// at most 1 us, ns / 1000 + 1 of them)
+__global__ void k_idle(unsigned ns) {
+  for (unsigned k = 0; k <= ns / 1000u; ++k) __nanosleep(1000u);
+}
+
+void launch_idle(unsigned ns, cudaStream_t s) { k_idle<<<1, 1, 0, s>>>(ns); }
+
 void launch_l2_flush(void* buf, size_t bytes, int fill, cudaStream_t s) {
   cudaMemsetAsync(buf, fill, bytes, s);
   // every byte equals fill: an even number of equal words xors to 0, never to 1
