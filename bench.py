@@ -473,6 +473,45 @@ def run_stages(a):
         pr.reweight(0.05, 1e-5)
         pr.set_ea_loss(F.FM_EA_COMPACT)
         out["epipolar_compact_a7_a8_a9"] = timed(F.FM_STAGE_EPIPOLAR, 1e-4)
+        # forward + backward split through the C ABI (buffers allocated once,
+        # calls back to back so that the device is the bottleneck), L1:
+        # pose-only with dL/dE kept against the focal lengths folded in (Sec. 3.3)
+        pr.set_ea_loss(F.FM_EA_L1)
+        p_t = torch.from_numpy(params.reshape(-1)).to(dev)
+        phi_t = torch.zeros(sc.n_cams, device=dev)
+        loss_t = torch.empty((), device=dev)
+        gl = torch.ones((), device=dev)
+        saved = torch.empty(9 * sc.n_pairs, device=dev)
+        grad = torch.empty_like(p_t)
+        gphi = torch.empty_like(phi_t)
+        L = F.lib()
+
+        def pose_only():
+            F._check(L.fm_ea_forward(pr.handle, p_t.data_ptr(), loss_t.data_ptr(), F.FM_EA_SAVE_DLDE,
+                                     saved.data_ptr()), pr.handle)
+            F._check(L.fm_ea_backward(pr.handle, p_t.data_ptr(), F.FM_EA_SAVE_DLDE, saved.data_ptr(),
+                                      gl.data_ptr(), grad.data_ptr()), pr.handle)
+
+        def focal():
+            F._check(L.fm_ea_focal_forward(pr.handle, p_t.data_ptr(), phi_t.data_ptr(), loss_t.data_ptr(),
+                                           saved.data_ptr()), pr.handle)
+            F._check(L.fm_ea_focal_backward(pr.handle, p_t.data_ptr(), phi_t.data_ptr(), saved.data_ptr(),
+                                            gl.data_ptr(), grad.data_ptr(), gphi.data_ptr()), pr.handle)
+
+        def split_us(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(iters):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return 1e3 * e0.elapsed_time(e1) / iters
+
+        out["split_fused_fwd_bwd_call"] = split_us(pose_only)
+        out["split_focal_fwd_bwd_call"] = split_us(focal)
     line = {"metric": "microseconds per optimiser iteration per stage (captured-graph replay)",
             "value": out["epipolar_direct_l1_a6_a9"], "unit": "us/iteration (direct epipolar step)",
             "n_gpus": 1, "steps": iters, "higher_is_better": False, "dtype": "f32", "data": "synthetic",

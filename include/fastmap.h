@@ -691,6 +691,27 @@ fm_status fm_autotune(fm_problem* problem, int32_t repeats, fm_tuning* best);
  * enable = 0 launches every kernel from the host.  Default on. */
 fm_status fm_graphs_enable(fm_problem* problem, int32_t enable);
 
+/* Focal lengths inside epipolar adjustment (Sec. 3.3, last paragraph of
+ * "Epipolar Adjustment": the focal lengths folded into the matrices, which
+ * become fundamental matrices).  phi_dev [N]: a log focal ratio per camera,
+ * f_c = f0_c exp(phi_c) with f0 the focal lengths the problem's keypoints are
+ * calibrated at; the objective is the direct one (the problem's loss, L1 or
+ * L2, and weights) at E'_n = S_j E_n S_i, S_c = diag(e^-phi_c, e^-phi_c, 1).
+ * Forward: loss_dev as fm_ea_forward, dlde_saved [P*9] (16-byte aligned)
+ * receives dL/dE'_n.  Backward: grad_dev [N*9] the poses' gradient (chain
+ * rule through dL/dE_n = S_j dL/dE'_n S_i), grad_phi_dev [N]
+ * dL/dphi_c = -s_c sum over the camera's image pairs of <dL/dE', S_j E D>
+ * (camera i) or <dL/dE', D E S_i> (camera j), D = diag(1, 1, 0), summed in a
+ * fixed order; grad_loss_dev [S] (or NULL) scales both.  All pointers are
+ * device pointers; no synchronisation.  With free focal lengths this
+ * objective drifts under pixel noise (smaller calibrated coordinates give
+ * smaller algebraic residuals): an option, not the default solve. */
+fm_status fm_ea_focal_forward(fm_problem* problem, const float* params_dev, const float* phi_dev, float* loss_dev,
+                              float* dlde_saved);
+fm_status fm_ea_focal_backward(fm_problem* problem, const float* params_dev, const float* phi_dev,
+                               const float* dlde_saved, const float* grad_loss_dev, float* grad_dev,
+                               float* grad_phi_dev);
+
 /* ---------------------------------------------------------- observability
  * (no counterpart in the paper, which times whole stages by wall clock) */
 

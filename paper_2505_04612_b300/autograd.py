@@ -79,3 +79,47 @@ class EpipolarLoss(torch.autograd.Function):
 def epipolar_loss(params, problem, mode="recompute"):
     """The epipolar loss of `problem` at `params` with the hand-written adjoint."""
     return EpipolarLoss.apply(params, problem, mode)
+
+
+class EpipolarFocalLoss(torch.autograd.Function):
+    """loss = EpipolarFocalLoss.apply(params [N, 9], phi [N], problem): the
+    direct epipolar objective with the focal lengths folded into the
+    matrices (Sec. 3.3, last paragraph of "Epipolar Adjustment"):
+    E'_n = S_j E_n S_i with S_c = diag(e^-phi_c, e^-phi_c, 1), phi_c the log
+    ratio of camera c's focal length to the one its keypoints were calibrated
+    at.  Forward keeps dL/dE'_n per image pair (``fm_ea_focal_forward``);
+    backward returns the poses' and the focal ratios' gradients
+    (``fm_ea_focal_backward``)."""
+
+    @staticmethod
+    def forward(ctx, params, phi, problem):
+        for name, t, n in (("params", params, 9 * problem.n_cams), ("phi", phi, problem.n_cams)):
+            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+            if t.numel() != n:
+                raise ValueError(f"{name} must hold {n} values")
+        S = getattr(problem, "S", 1)
+        loss = torch.empty(() if S == 1 else (S,), dtype=torch.float32, device=params.device)
+        saved = _saved_buffer(problem, F.FM_EA_SAVE_DLDE, params.device)
+        F._check(F.lib().fm_ea_focal_forward(problem.handle, params.data_ptr(), phi.data_ptr(), loss.data_ptr(),
+                                             saved.data_ptr()), problem.handle)
+        ctx.problem = problem
+        ctx.save_for_backward(params, phi, saved)
+        return loss
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        params, phi, saved = ctx.saved_tensors
+        g = grad_loss.detach().float().contiguous()
+        grad = torch.empty_like(params)
+        gphi = torch.empty_like(phi)
+        F._check(F.lib().fm_ea_focal_backward(ctx.problem.handle, params.data_ptr(), phi.data_ptr(),
+                                              saved.data_ptr(), g.data_ptr(), grad.data_ptr(), gphi.data_ptr()),
+                 ctx.problem.handle)
+        return grad, gphi, None
+
+
+def epipolar_focal_loss(params, phi, problem):
+    """The epipolar loss of `problem` at `params` with free log focal ratios
+    `phi` (hand-written adjoint for both)."""
+    return EpipolarFocalLoss.apply(params, phi, problem)

@@ -188,6 +188,8 @@ void release(fm_problem* pr) {
   pr->graphs.clear();
   if (pr->cap_stream) cudaStreamDestroy(pr->cap_stream);
   pr->cap_stream = nullptr;
+  dfree(pr->focal_G);
+  dfree(pr->focal_dphi);
   if (pr->aux_stream) cudaStreamDestroy(pr->aux_stream);
   if (pr->aux_fork) cudaEventDestroy(pr->aux_fork);
   if (pr->aux_join) cudaEventDestroy(pr->aux_join);
@@ -1594,6 +1596,83 @@ fm_status fm_ea_forward(fm_problem* pr, const float* params, float* loss_dev, in
     Timed t(pr, fm::kKLossSum);
     fm::launch_sum_fixed(pr->seg_loss, pr->P, 1, pr->sc_pair_off, pr->S, loss_dev, s);
   }
+  FM_LAUNCHED(pr);
+  return FM_OK;
+}
+
+fm_status fm_ea_focal_forward(fm_problem* pr, const float* params, const float* phi, float* loss_dev,
+                              float* dlde_saved) {
+  fm::g_plain_once = true;
+  if (!pr) return FM_ERR_INVALID_ARG;
+  fm_status e = ea_split_check(pr, params, FM_EA_SAVE_DLDE, dlde_saved);
+  if (e != FM_OK) return e;
+  if (!phi || !loss_dev) return fail(pr, FM_ERR_INVALID_ARG, "phi_dev and loss_dev are required");
+  cudaStream_t s = pr->stream;
+  {
+    Timed t(pr, fm::kKEaTables);
+    fm::launch_ea_tables(params, pr->pair_i, pr->pair_j, pr->seg_off, pr->P, pr->seg_tab, nullptr, s,
+                         phi);   // E'_n = S_j E_n S_i
+  }
+  FM_LAUNCHED(pr);
+  fm::SegArgs a = fm::seg_args(pr, params);
+  a.seg_grad = nullptr;
+  if (pr->n_wruns > 0) {
+    Timed t(pr, fm::kKEaDirect);
+    fm::launch_ea_direct(pr, pr->ea_w, pr->ea_loss, s);
+  }
+  a.g_scale = (pr->ea_loss == FM_EA_L1) ? 1.f : 2.f;
+  a.dlde_out = dlde_saved;   // dL/dE'_n
+  FM_LAUNCHED(pr);
+  {
+    Timed t(pr, fm::kKEaSegments);
+    fm::launch_ea_segments(a, s);
+  }
+  {
+    Timed t(pr, fm::kKLossSum);
+    fm::launch_sum_fixed(pr->seg_loss, pr->P, 1, pr->sc_pair_off, pr->S, loss_dev, s);
+  }
+  FM_LAUNCHED(pr);
+  return FM_OK;
+}
+
+fm_status fm_ea_focal_backward(fm_problem* pr, const float* params, const float* phi, const float* dlde_saved,
+                               const float* grad_loss, float* grad, float* grad_phi) {
+  fm::g_plain_once = true;
+  if (!pr) return FM_ERR_INVALID_ARG;
+  fm_status e = ea_split_check(pr, params, FM_EA_SAVE_DLDE, dlde_saved);
+  if (e != FM_OK) return e;
+  if (!phi || !grad || !grad_phi) return fail(pr, FM_ERR_INVALID_ARG, "phi_dev, grad_dev and grad_phi_dev are required");
+  cudaStream_t s = pr->stream;
+  if (!pr->focal_G) FM_ALLOC(pr, pr->focal_G, 9 * (size_t)std::max(pr->P, 1));
+  if (!pr->focal_dphi) FM_ALLOC(pr, pr->focal_dphi, 2 * (size_t)std::max(pr->P, 1));
+  fm::launch_focal_dlde(pr, params, dlde_saved, phi, grad_loss, pr->focal_G, pr->focal_dphi, s);
+  FM_LAUNCHED(pr);
+  fm::SegArgs a = fm::seg_args(pr, params);
+  a.seg_loss = nullptr;
+  a.grad_loss = grad_loss;
+  a.dlde_in = pr->focal_G;   // dL/dE_n = S_j G' S_i
+  {
+    Timed t(pr, fm::kKEaSegments);
+    fm::launch_ea_segments(a, s);
+  }
+  FM_LAUNCHED(pr);
+  fm::CamUpdate u{};
+  u.cam_seg_off = pr->cam_seg_off;
+  u.cam_seg = pr->cam_seg;
+  u.seg_grad = pr->seg_grad;
+  u.params = params;
+  u.params_out = nullptr;
+  u.grad_out = grad;
+  u.N = pr->N;
+  u.P = pr->P;
+  u.runs = 1;
+  u.seg_loss = pr->seg_loss;
+  u.loss_out = nullptr;
+  {
+    Timed t(pr, fm::kKCamUpdate);
+    fm::launch_cam_update(FM_STAGE_EPIPOLAR, u, s);
+  }
+  fm::launch_focal_cam(pr, pr->focal_dphi, grad_phi, s);
   FM_LAUNCHED(pr);
   return FM_OK;
 }

@@ -3,8 +3,9 @@
 //
 // One evaluation is three launches:
 //   k_ea_tables    per image pair n: E_n = [t^]_x R_ij from the two cameras'
-//                  parameters, packed with the end offset of n's keypoint
-//                  pairs (48 B per image pair);
+//                  parameters (with free focal lengths, S_j E_n S_i), packed
+//                  with the end offset of n's keypoint pairs (48 B per image
+//                  pair);
 //   k_ea_direct    streams the calibrated keypoint pairs (16 B each, plus 4 B
 //                  when weighted) once and emits, per (warp run, image pair),
 //                  the partial sums  sum rho'(r) x~2 x~1^T  (9 floats) and
@@ -51,7 +52,7 @@ constexpr unsigned FULL = 0xffffffffu;
 
 __global__ void k_ea_tables(const float* params, const int* __restrict__ pi,
                             const int* __restrict__ pj, const int* __restrict__ seg_off, int P,
-                            float4* __restrict__ tab, int* step_counter) {
+                            float4* __restrict__ tab, int* step_counter, const float* __restrict__ phi) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   pdl_trigger();
   int end = 0, ci = 0, cj = 0;
@@ -70,6 +71,13 @@ __global__ void k_ea_tables(const float* params, const int* __restrict__ pi,
   pair_geometry(qi, qj, g);
   float E[9];
   essential(g, E);
+  if (phi) {   // focal lengths folded in: E' = S_j E S_i, S = diag(e^-phi, e^-phi, 1)
+    const float si = __expf(-phi[ci]), sj = __expf(-phi[cj]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) E[3 * a + b] *= (a < 2 ? sj : 1.f) * (b < 2 ? si : 1.f);
+  }
   tab[3 * n + 0] = make_float4(E[0], E[1], E[2], E[3]);
   tab[3 * n + 1] = make_float4(E[4], E[5], E[6], E[7]);
   tab[3 * n + 2] = make_float4(E[8], __int_as_float(end), 0.f, 0.f);
@@ -489,9 +497,9 @@ __global__ void k_ea_segments(SegArgs a) {
 }  // namespace
 
 void launch_ea_tables(const float* params, const int* pi, const int* pj, const int* seg_off,
-                      int P, float4* seg_tab, int* step_counter, cudaStream_t s) {
+                      int P, float4* seg_tab, int* step_counter, cudaStream_t s, const float* phi) {
   launch_pdl(k_ea_tables, dim3((P + 127) / 128), dim3(128), 0, s, params, pi, pj, seg_off, P, seg_tab,
-             step_counter);
+             step_counter, phi);
 }
 
 template <int U, int LOSS, bool WEIGHTED, int MODE>

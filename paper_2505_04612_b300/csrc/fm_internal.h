@@ -204,6 +204,8 @@ struct fm_problem {
   cudaStream_t cap_stream = nullptr;
   cudaStream_t aux_stream = nullptr;   // second stream of the distortion scoring (created on first use)
   cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
+  float* focal_G = nullptr;      // [P*9] dL/dE of the focal backward (allocated on first use)
+  float* focal_dphi = nullptr;   // [P*2] per-pair focal terms
   cudaEvent_t graph_in = nullptr, graph_out = nullptr;   // orders replays by completion
   int64_t graph_replays = 0;
   // fm_loss_grad with host buffers: pinned staging of the parameters and the
@@ -284,7 +286,7 @@ void launch_exclusive_scan_info(int4* wrun_info, int n, int64_t* total_out_dev, 
 
 // epipolar (fm_ea.cu)
 void launch_ea_tables(const float* params, const int* pi, const int* pj, const int* seg_off,
-                      int P, float4* seg_tab, int* step_counter, cudaStream_t s);
+                      int P, float4* seg_tab, int* step_counter, cudaStream_t s, const float* phi = nullptr);
 void launch_ea_direct(const fm_problem* pr, const float* weights, int loss, cudaStream_t s);
 // the loss alone; coef_out (optional, Z floats) receives w drho/dr per pair
 void launch_ea_direct_loss(const fm_problem* pr, const float* weights, int loss, float* coef_out,
@@ -353,6 +355,13 @@ void launch_dist_errors(const fm_problem* pr, const float* scale, const int* idx
 void launch_dist_reduce(const float* err, int M, int K, float* out, cudaStream_t s);
 // kp <- undistorted at alpha [N] (scale [N] = f0 / half diagonal); *bad |= 1 where 1 + alpha r^2 <= 0
 void launch_undistort(const fm_problem* pr, const float* scale, const float* alpha, int* bad, cudaStream_t s);
+
+// focal lengths inside epipolar adjustment (fm_focal_ea.cu; E'_n in the
+// tables through launch_ea_tables' phi): G' -> S_j G' S_i and per-pair focal
+// terms [P][2]; per-camera sums
+void launch_focal_dlde(const fm_problem* pr, const float* params, const float* Gp, const float* phi,
+                       const float* grad_loss, float* G_out, float* dphi, cudaStream_t s);
+void launch_focal_cam(const fm_problem* pr, const float* dphi, float* gphi, cudaStream_t s);
 
 // learned weights (fm_mlp.cu)
 size_t mlp_grad_smem();
