@@ -587,23 +587,24 @@ def run_mlp(a):
     print(json.dumps(line), flush=True)
 
 
-DIST_OPS_PER_EVAL = 123   # FP32 operations per (candidate, keypoint pair) of k_dist_errors' three passes
-# (8 + 8 + 8) + (8 + 8 + 4 + 4 + 45) + (8 + 8 + 4 + 10) = 123
+DIST_OPS_PER_EVAL = 99    # FP32 operations per (candidate, keypoint pair) of k_dist_errors' two passes
+# (8 + 8 + 4 + 4 + 45) + (8 + 8 + 4 + 10) = 99
 
 
 def run_distortion(a):
     """--config distortion_c2_5m: the distortion interval search's scoring
     kernel on the c2_5m scene observed through a division-model lens
-    (alpha = -0.2), with verified matches (no gross outliers): one level of 32 candidates over all 15,631 image pairs
-    (fm_distortion_pair_errors: per candidate and image pair, Hartley
-    normalisation, moments, Cholesky + inverse iteration, rank-2 F, error
-    sum), and one whole search (3 levels).  value = candidate x keypoint-pair evaluations/s of
-    the kernel (event time).  Roofline: FP32 issue -- each evaluation costs
-    DIST_OPS_PER_EVAL operations in the three passes over the keypoints
-    (undistortion 2 x 8, centroid sums 8; normalisation 4, products 4,
-    moments 45; normalisation 4, line and residual 10), the per-(candidate,
-    image pair) eigenvector not counted; the peak is 148 SMs x 128 FP32 lanes x the measured
-    SM clock."""
+    (alpha = -0.2), with verified matches (no gross outliers): one level of
+    32 candidates over all 15,631 image pairs (fm_distortion_pair_errors: per
+    candidate and image pair, moments in a provisional frame, the exact
+    Hartley frame, Cholesky + inverse iteration, rank-2 F, error sum), and
+    one whole search (3 levels).  value = candidate x keypoint-pair
+    evaluations/s of the kernel (event time).  Roofline: FP32 issue -- each
+    evaluation costs DIST_OPS_PER_EVAL operations in the two passes over the
+    keypoints (undistortion 2 x 8, normalisation 4, products 4, moments 45;
+    undistortion 2 x 8, normalisation 4, line and residual 10), the per-warp
+    observed-point sums and the per-(candidate, image pair) eigenvector not
+    counted; the peak is 148 SMs x 128 FP32 lanes x the measured SM clock."""
     import torch
     from paper_2505_04612_b300 import build as B
     B.build()

@@ -6,17 +6,22 @@
 // (x_c = (pixel - centre) / f0), so x_d = s x_c with s = f0 / h per image.
 //
 // k_dist_errors: one warp per listed image pair, one lane per candidate
-// alpha (up to 32 per launch).  The warp streams the pair's keypoint pairs
-// three times, every lane reading the same pair (one broadcast request per
-// warp): the first pass gives each image's centroid and RMS radius of the
-// undistorted points (Hartley's normalisation T: centroid to the origin, RMS
-// distance sqrt(2)), the second accumulates the lane's moment matrix
-// W = sum a a^T of the normalised points (a = y_2 (x) y_1, packed upper
-// triangle in registers); a per-thread Cholesky factorisation and inverse
-// iteration give its smallest eigenvector F^, projected to rank 2 at unit
-// Frobenius norm; the third pass sums the epipolar errors |y_2^T F^ y_1| in
-// the normalised frame (scale-free: a candidate that shrinks the points does
-// not shrink the error).  One read of the keypoints
+// alpha (up to 32 per launch).
+//   * a provisional frame per image, the Hartley map of the observed points
+//     (centroid to the origin, RMS distance sqrt(2)), the same for all
+//     candidates: the lanes split the keypoint pairs (coalesced loads);
+//   * pass 1, every lane reading the same keypoint pair (one broadcast request
+//     per warp): the lane's moment matrix W0 = sum a a^T of its undistorted
+//     points in the provisional frame (a = y0_2 (x) y0_1, packed upper
+//     triangle in registers);
+//   * the exact Hartley frame of the undistorted points (y = A y0) is read off
+//     W0 (count, sums and sums of squares are entries of it), and a
+//     per-thread Cholesky factorisation of W0 with inverse iteration on
+//     W = K W0 K^T (K = A2 (x) A1, applied as x <- K^-T W0^-1 K^-1 x) gives
+//     the smallest eigenvector F^, projected to rank 2 at unit Frobenius norm;
+//   * pass 2: the epipolar errors |y_2^T F^ y_1| in the exact frame
+//     (scale-free: a candidate that shrinks the points does not shrink the
+//     error).  One read of the keypoints
 // serves all candidates, so the kernel is bound by FP32 issue, not by HBM.
 // A listed pair may fix one side's alpha (its camera is already estimated).
 #include "fm_device.cuh"
@@ -35,16 +40,56 @@ __host__ __device__ constexpr int sym9(int i, int j) {
   return i <= j ? i * 9 - (i * (i - 1)) / 2 + (j - i) : j * 9 - (j * (j - 1)) / 2 + (i - j);
 }
 
-// Eigenvector of the smallest eigenvalue of a symmetric positive
-// semi-definite 9 x 9 matrix held by one thread (packed upper triangle W,
-// overwritten): Cholesky factor W = U^T U (pivots floored at kPivotFloor of
-// their diagonal, so that a singular W still factors), then inverse
-// iteration x <- (U^T U)^-1 x from x = (1, ..., 1)/3 until no component moves
-// by more than kInvTol or kInvIters steps (warp-uniform loop).  Converges as
-// (lambda1 / lambda2)^k; where the two smallest eigenvalues nearly coincide
-// the eigenvector is not determined at float32 precision anyway.  Every index
-// is a compile-time constant after unrolling, so W stays in registers.
-__device__ __forceinline__ void smallest_eigenvector(float (&W)[45], float (&x)[9]) {
+// y = B y' for the homogeneous points of one image, B = [[s, 0, cx], [0, s,
+// cy], [0, 0, 1]] (the inverse of a Hartley map y' = k (y - c): s = 1/k)
+struct Inv {
+  float s, cx, cy;
+};
+
+// x <- (B2 (x) B1) x and x <- (B2 (x) B1)^T x for a 9-vector x = vec(X),
+// X[p][q] = x[3p + q] (p: image 2, q: image 1): B2 X B1^T and B2^T X B1
+__device__ __forceinline__ void kron_apply(const Inv& b2, const Inv& b1, float (&x)[9]) {
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const float x2 = x[3 * p + 2];
+    x[3 * p] = fmaf(b1.s, x[3 * p], b1.cx * x2);
+    x[3 * p + 1] = fmaf(b1.s, x[3 * p + 1], b1.cy * x2);
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float y2 = x[6 + q];
+    x[q] = fmaf(b2.s, x[q], b2.cx * y2);
+    x[3 + q] = fmaf(b2.s, x[3 + q], b2.cy * y2);
+  }
+}
+__device__ __forceinline__ void kron_apply_t(const Inv& b2, const Inv& b1, float (&x)[9]) {
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const float x0 = x[3 * p], x1 = x[3 * p + 1];
+    x[3 * p + 2] = fmaf(b1.cx, x0, fmaf(b1.cy, x1, x[3 * p + 2]));
+    x[3 * p] = b1.s * x0;
+    x[3 * p + 1] = b1.s * x1;
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float y0 = x[q], y1 = x[3 + q];
+    x[6 + q] = fmaf(b2.cx, y0, fmaf(b2.cy, y1, x[6 + q]));
+    x[q] = b2.s * y0;
+    x[3 + q] = b2.s * y1;
+  }
+}
+
+// Eigenvector of the smallest eigenvalue of W = K W0 K^T, K^-1 = B2 (x) B1,
+// for a symmetric positive semi-definite 9 x 9 W0 held by one thread (packed
+// upper triangle, overwritten): Cholesky factor W0 = U^T U (pivots floored at
+// kPivotFloor of their diagonal, so that a singular W0 still factors), then
+// inverse iteration x <- W^-1 x = K^-T W0^-1 K^-1 x from x = (1, ..., 1)/3
+// until no component moves by more than kInvTol or kInvIters steps
+// (warp-uniform loop).  Converges as (lambda1 / lambda2)^k; where the two
+// smallest eigenvalues nearly coincide the eigenvector is not determined at
+// float32 precision anyway.  Every index is a compile-time constant after
+// unrolling, so W0 stays in registers.
+__device__ __forceinline__ void smallest_eigenvector(float (&W)[45], const Inv& b2, const Inv& b1, float (&x)[9]) {
   float id[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
@@ -71,25 +116,30 @@ __device__ __forceinline__ void smallest_eigenvector(float (&W)[45], float (&x)[
   for (int it = 0; it < kInvIters; ++it) {
     if (active) {
       float z[9], y[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) y[i] = x[i];
+      kron_apply(b2, b1, y);
       float mz = 0.f;
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {   // U^T z = x
-        float v = x[i];
+      for (int i = 0; i < 9; ++i) {   // U^T z = K^-1 x
+        float v = y[i];
 #pragma unroll
         for (int k = 0; k < i; ++k) v = fmaf(-W[sym9(k, i)], z[k], v);
         z[i] = v * id[i];
         mz = fmaxf(mz, fabsf(z[i]));
       }
       const float sz = 1.f / mz;      // rescaled so that no solve overflows
-      float my = 0.f;
 #pragma unroll
-      for (int i = 8; i >= 0; --i) {  // U y = z
+      for (int i = 8; i >= 0; --i) {  // U v = z
         float v = z[i] * sz;
 #pragma unroll
         for (int j = i + 1; j < 9; ++j) v = fmaf(-W[sym9(i, j)], y[j], v);
         y[i] = v * id[i];
-        my = fmaxf(my, fabsf(y[i]));
       }
+      kron_apply_t(b2, b1, y);        // K^-T v
+      float my = 0.f;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) my = fmaxf(my, fabsf(y[i]));
       const float sy = 1.f / my;
       float nrm = 0.f, dot = 0.f;
 #pragma unroll
@@ -181,19 +231,27 @@ __device__ __forceinline__ void for_range(const float4* __restrict__ kp, int lo,
   for (; m < hi; ++m) f(__ldg(kp + m));
 }
 
-// pass 1: sums of x, y and x^2 + y^2 of the undistorted points of each image
-__device__ __forceinline__ void stats_range(const float4* kp, const PairCtx& p, int lo, int hi, float (&st)[6]) {
+// sums of x, y and x^2 + y^2 of the observed points x_d of each image over
+// keypoint pairs lo + lane, lo + lane + 32, ... < hi (the lanes split them:
+// coalesced loads), reduced over the warp by a fixed xor tree
+__device__ __forceinline__ void observed_sums(const float4* kp, const PairCtx& p, int lo, int hi, int lane,
+                                              float (&st)[6]) {
 #pragma unroll
   for (int k = 0; k < 6; ++k) st[k] = 0.f;
-  for_range(kp, lo, hi, [&](const float4& x) {
-    const float2 u1 = undistorted(x.x, x.y, p.si, p.ai), u2 = undistorted(x.z, x.w, p.sj, p.aj);
-    st[0] += u1.x;
-    st[1] += u1.y;
-    st[2] = fmaf(u1.x, u1.x, fmaf(u1.y, u1.y, st[2]));
-    st[3] += u2.x;
-    st[4] += u2.y;
-    st[5] = fmaf(u2.x, u2.x, fmaf(u2.y, u2.y, st[5]));
-  });
+  for (int m = lo + lane; m < hi; m += 32) {
+    const float4 x = __ldg(kp + m);
+    const float a = x.x * p.si, b = x.y * p.si, c = x.z * p.sj, d = x.w * p.sj;
+    st[0] += a;
+    st[1] += b;
+    st[2] = fmaf(a, a, fmaf(b, b, st[2]));
+    st[3] += c;
+    st[4] += d;
+    st[5] = fmaf(c, c, fmaf(d, d, st[5]));
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) st[k] += __shfl_xor_sync(0xffffffffu, st[k], o);
 }
 
 // Hartley normalisation from the sums over the pair's m keypoint pairs:
@@ -212,7 +270,29 @@ __device__ __forceinline__ Norm norm_from(const float (&st)[6], int m) {
   return z;
 }
 
-// pass 2: moments of the normalised points
+// The exact Hartley normalisation of the points y0 (provisional frame) read
+// off their moments: W0[8][8] = m, W0[6][8], W0[7][8] = sums of image 1's
+// coordinates, W0[6][6] + W0[7][7] = sum of their squares, W0[2][8],
+// W0[5][8], W0[2][2] + W0[5][5] the same for image 2
+__device__ __forceinline__ Norm exact_frame(const float (&W)[45]) {
+  const float st[6] = {W[sym9(6, 8)], W[sym9(7, 8)], W[sym9(6, 6)] + W[sym9(7, 7)],
+                       W[sym9(2, 8)], W[sym9(5, 8)], W[sym9(2, 2)] + W[sym9(5, 5)]};
+  return norm_from(st, (int)W[sym9(8, 8)]);
+}
+
+// y = k1 (k0 (x_u - c0) - c1) = (k1 k0) (x_u - (c0 + c1 / k0)) per image
+__device__ __forceinline__ Norm compose(const Norm& z0, const Norm& z1) {
+  Norm z;
+  z.k1 = z1.k1 * z0.k1;
+  z.c1x = z0.c1x + z1.c1x / z0.k1;
+  z.c1y = z0.c1y + z1.c1y / z0.k1;
+  z.k2 = z1.k2 * z0.k2;
+  z.c2x = z0.c2x + z1.c2x / z0.k2;
+  z.c2y = z0.c2y + z1.c2y / z0.k2;
+  return z;
+}
+
+// pass 1: moments of the provisionally normalised points
 __device__ __forceinline__ void moments_range(const float4* kp, const PairCtx& p, const Norm& z, int lo, int hi,
                                               float (&W)[45]) {
 #pragma unroll
@@ -225,11 +305,12 @@ __device__ __forceinline__ void moments_range(const float4* kp, const PairCtx& p
   });
 }
 
-// F^ from the moments: smallest eigenvector, rank 2 (F <- F - (F u) u^T with
+// F^ from the moments W0 of the provisionally normalised points (the exact
+// frame is y = B^-1 y0 per image): smallest eigenvector, rank 2 (F <- F - (F u) u^T with
 // u the right singular vector of the smallest singular value, the
 // eigenvector of F^T F), unit Frobenius norm
-__device__ __forceinline__ void fundamental(float (&W)[45], float (&F)[9]) {
-  smallest_eigenvector(W, F);
+__device__ __forceinline__ void fundamental(float (&W)[45], const Inv& b2, const Inv& b1, float (&F)[9]) {
+  smallest_eigenvector(W, b2, b1, F);
   float S[9], Q[9];
 #pragma unroll
   for (int c0 = 0; c0 < 3; ++c0)
@@ -263,7 +344,7 @@ __device__ __forceinline__ void fundamental(float (&W)[45], float (&F)[9]) {
   for (int k = 0; k < 9; ++k) F[k] *= inv;
 }
 
-// pass 3: sum of |y_2^T F^ y_1| in the normalised frame
+// pass 2: sum of |y_2^T F^ y_1| in the normalised frame
 __device__ __forceinline__ float error_range(const float4* kp, const PairCtx& p, const Norm& z, const float (&F)[9],
                                              int lo, int hi) {
   float sum = 0.f;
@@ -288,28 +369,32 @@ __global__ void __launch_bounds__(kDistWarps * 32) k_dist_errors(DistArgs a) {
   const int n = a.idx ? a.idx[q] : q;
   const int r = a.row ? a.row[q] : q;
   const PairCtx p = pair_ctx(a, n, r, lane);
-  if (p.e - p.b < 8) {
+  const int m = p.e - p.b;
+  if (m < 8) {
     if (lane < a.K) a.err[(size_t)r * a.K + lane] = 0.f;
     return;
   }
   float st[6];
-  stats_range(a.kp, p, p.b, p.e, st);
-  const Norm z = norm_from(st, p.e - p.b);
+  observed_sums(a.kp, p, p.b, p.e, lane, st);
+  const Norm z0 = norm_from(st, m);   // provisional frame: the observed points' Hartley map
   float W[45];
-  moments_range(a.kp, p, z, p.b, p.e, W);
+  moments_range(a.kp, p, z0, p.b, p.e, W);
+  const Norm z1 = exact_frame(W);
   float F[9];
-  fundamental(W, F);
-  const float sum = error_range(a.kp, p, z, F, p.b, p.e);
+  fundamental(W, Inv{1.f / z1.k2, z1.c2x, z1.c2y}, Inv{1.f / z1.k1, z1.c1x, z1.c1y}, F);
+  const float sum = error_range(a.kp, p, compose(z0, z1), F, p.b, p.e);
   if (lane < a.K) a.err[(size_t)r * a.K + lane] = sum;
 }
 
 // One CTA of kBigWarps warps per work item (image pairs of more than
 // kDistSplit keypoint pairs): warp w takes the w-th of kBigWarps contiguous
 // slices of the pair's keypoint pairs in every pass; the slices' sums meet
-// in shared memory in a fixed order, warp 0 solves for F.
+// in shared memory in a fixed order; warp 0 solves for F^ and hands F^ and
+// the exact frame of every lane (candidate) to the other warps.
 __global__ void __launch_bounds__(kBigWarps * 32) k_dist_errors_big(DistArgs a) {
-  __shared__ float red[kBigWarps * 45 * 32];   // per-warp moments (the first 6 rows: statistics)
+  __shared__ float red[kBigWarps * 45 * 32];   // per-warp moments (first: the observed sums)
   __shared__ float Fs[9 * 32];
+  __shared__ float Zs[6 * 32];                 // exact frame (c1x, c1y, k1, c2x, c2y, k2) per lane
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int q = blockIdx.x;
   const int n = a.idx ? a.idx[q] : q;
@@ -320,21 +405,22 @@ __global__ void __launch_bounds__(kBigWarps * 32) k_dist_errors_big(DistArgs a) 
   const int lo = min(p.b + wid * L, p.e), hi = min(lo + L, p.e);
 
   float st[6];
-  stats_range(a.kp, p, lo, hi, st);
+  observed_sums(a.kp, p, lo, hi, lane, st);
+  if (lane == 0)
 #pragma unroll
-  for (int k = 0; k < 6; ++k) red[(wid * 6 + k) * 32 + lane] = st[k];
+    for (int k = 0; k < 6; ++k) red[wid * 6 + k] = st[k];
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     float t = 0.f;
-    for (int w = 0; w < kBigWarps; ++w) t += red[(w * 6 + k) * 32 + lane];
+    for (int w = 0; w < kBigWarps; ++w) t += red[w * 6 + k];
     st[k] = t;
   }
-  const Norm z = norm_from(st, m);
-  __syncthreads();   // the statistics are read before the moments overwrite them
+  const Norm z0 = norm_from(st, m);   // provisional frame, the same for every lane
+  __syncthreads();   // the sums are read before the moments overwrite them
 
   float W[45];
-  moments_range(a.kp, p, z, lo, hi, W);
+  moments_range(a.kp, p, z0, lo, hi, W);
 #pragma unroll
   for (int k = 0; k < 45; ++k) red[(wid * 45 + k) * 32 + lane] = W[k];
   __syncthreads();
@@ -345,16 +431,30 @@ __global__ void __launch_bounds__(kBigWarps * 32) k_dist_errors_big(DistArgs a) 
       for (int w = 0; w < kBigWarps; ++w) t += red[(w * 45 + k) * 32 + lane];
       W[k] = t;
     }
+    const Norm z1 = exact_frame(W);
     float F[9];
-    fundamental(W, F);
+    fundamental(W, Inv{1.f / z1.k2, z1.c2x, z1.c2y}, Inv{1.f / z1.k1, z1.c1x, z1.c1y}, F);
 #pragma unroll
     for (int k = 0; k < 9; ++k) Fs[k * 32 + lane] = F[k];
+    Zs[0 * 32 + lane] = z1.c1x;
+    Zs[1 * 32 + lane] = z1.c1y;
+    Zs[2 * 32 + lane] = z1.k1;
+    Zs[3 * 32 + lane] = z1.c2x;
+    Zs[4 * 32 + lane] = z1.c2y;
+    Zs[5 * 32 + lane] = z1.k2;
   }
   __syncthreads();
   float F[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) F[k] = Fs[k * 32 + lane];
-  const float sum = error_range(a.kp, p, z, F, lo, hi);
+  Norm z1;
+  z1.c1x = Zs[0 * 32 + lane];
+  z1.c1y = Zs[1 * 32 + lane];
+  z1.k1 = Zs[2 * 32 + lane];
+  z1.c2x = Zs[3 * 32 + lane];
+  z1.c2y = Zs[4 * 32 + lane];
+  z1.k2 = Zs[5 * 32 + lane];
+  const float sum = error_range(a.kp, p, compose(z0, z1), F, lo, hi);
   red[wid * 32 + lane] = sum;   // the moments were consumed before the last barrier
   __syncthreads();
   if (wid == 0) {
