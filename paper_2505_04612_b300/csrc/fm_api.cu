@@ -815,22 +815,28 @@ struct Scratch {
 
 // work items of k_dist_errors: image pairs and their output rows, those of at
 // most kDistSplit keypoint pairs (one warp each) first, then the larger ones
-// (one CTA each); returns the number of small ones
+// (one CTA each), each class largest first so that the longest items start
+// first (the outputs do not depend on the order); returns the number of small
+// ones
 int split_by_size(const std::vector<int>& pairs, const std::vector<int>& off, std::vector<int>& idx,
                   std::vector<int>& row) {
-  idx.clear();
-  row.clear();
-  for (int big = 0; big < 2; ++big)
-    for (size_t q = 0; q < pairs.size(); ++q) {
-      const int n = pairs[q];
-      if ((off[n + 1] - off[n] > fm::kDistSplit) == (big == 1)) {
-        idx.push_back(n);
-        row.push_back((int)q);
-      }
-    }
+  // key: class (small 0, large 1), then the size descending, then the row
+  std::vector<uint64_t> key(pairs.size());
   int n_small = 0;
-  for (int n : idx)
-    if (off[n + 1] - off[n] <= fm::kDistSplit) ++n_small;
+  for (size_t q = 0; q < pairs.size(); ++q) {
+    const uint64_t m = (uint64_t)(off[pairs[q] + 1] - off[pairs[q]]);
+    const uint64_t big = m > (uint64_t)fm::kDistSplit;
+    n_small += big == 0;
+    key[q] = (big << 62) | ((0x7fffffffull - m) << 31) | (uint64_t)q;
+  }
+  std::sort(key.begin(), key.end());
+  idx.resize(pairs.size());
+  row.resize(pairs.size());
+  for (size_t k = 0; k < key.size(); ++k) {
+    const int q = (int)(key[k] & 0x7fffffffull);
+    idx[k] = pairs[q];
+    row[k] = q;
+  }
   return n_small;
 }
 
