@@ -335,21 +335,31 @@ __global__ void k_emit_tracks(const uint32_t* __restrict__ slabel, const uint32_
   }
 }
 
-__global__ void k_raw_flags(const int2* __restrict__ matches, int64_t M, const int* __restrict__ label,
-                            const int* __restrict__ bad, long long* __restrict__ flag) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < M; e += (int64_t)gridDim.x * blockDim.x)
-    flag[e] = bad[label[matches[e].x]] ? 1 : 0;
+// a match k_union accepted (both keypoints in [0, K), two images); the others
+// are flagged there and must not be dereferenced here either
+__device__ __forceinline__ bool valid_match(int2 m, int K, const int* __restrict__ img) {
+  return m.x >= 0 && m.x < K && m.y >= 0 && m.y < K && img[m.x] != img[m.y];
+}
+
+__global__ void k_raw_flags(const int2* __restrict__ matches, int64_t M, int K, const int* __restrict__ img,
+                            const int* __restrict__ label, const int* __restrict__ bad,
+                            long long* __restrict__ flag) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < M; e += (int64_t)gridDim.x * blockDim.x) {
+    const int2 m = matches[e];
+    flag[e] = (valid_match(m, K, img) && bad[label[m.x]]) ? 1 : 0;
+  }
 }
 
 // raw matches of inconsistent tracks, in input order, after the Z1 pairs of
 // the consistent tracks, oriented from the lower image
-__global__ void k_emit_raw(const int2* __restrict__ matches, int64_t M, const int* __restrict__ label,
+__global__ void k_emit_raw(const int2* __restrict__ matches, int64_t M, int K, const int* __restrict__ label,
                            const int* __restrict__ bad, const long long* __restrict__ pos, long long Z1,
                            const int* __restrict__ tid, const int* __restrict__ img, int N,
                            uint32_t* __restrict__ key, int* __restrict__ n1, int* __restrict__ n2,
                            int* __restrict__ trk) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < M; e += (int64_t)gridDim.x * blockDim.x) {
     const int2 m = matches[e];
+    if (!valid_match(m, K, img)) continue;
     const int r = label[m.x];
     if (!bad[r]) continue;
     const long long z = Z1 + pos[e];
@@ -656,7 +666,7 @@ fm_status fm_tracks_complete(int32_t n_images, const int32_t* kp_off, int64_t n_
       rflag = B.get<long long>(M);
       ce = B.ce;
       if (ce == cudaSuccess) {
-        k_raw_flags<<<grid_for(M), 256, 0, s>>>(d_match, M, label, bad, rflag);
+        k_raw_flags<<<grid_for(M), 256, 0, s>>>(d_match, M, K, img, label, bad, rflag);
         scan<long long>(B, rflag, rflag, M, tot + 1, s);
         ce = B.ce == cudaSuccess ? cudaGetLastError() : B.ce;
       }
@@ -696,7 +706,8 @@ fm_status fm_tracks_complete(int32_t n_images, const int32_t* kp_off, int64_t n_
         k_emit_tracks<<<grid_for(K), 256, 0, s>>>(skey, sval, K, start, size, bad, tid, nemit, img, N, key, n1, n2,
                                                    trk);
         if (M > 0 && Z > Z1)
-          k_emit_raw<<<grid_for(M), 256, 0, s>>>(d_match, M, label, bad, rflag, Z1, tid, img, N, key, n1, n2, trk);
+          k_emit_raw<<<grid_for(M), 256, 0, s>>>(d_match, M, K, label, bad, rflag, Z1, tid, img, N, key, n1, n2,
+                                                  trk);
         k_iota<<<grid_for(Z), 256, 0, s>>>(perm, Z);
         radix_sort(B, key, perm, Z, bits_for((uint64_t)N * N - 1), s);
         k_heads<<<grid_for(Z), 256, 0, s>>>(key, Z, head);

@@ -85,6 +85,10 @@ def test_empty_inputs_and_invalid_matches():
         _gpu([0, 2, 4], [[0, 1]])          # both keypoints in image 0
     with pytest.raises(FastMapError):
         _gpu([0, 2, 4], [[0, 4]])          # keypoint 4 does not exist
+    with pytest.raises(FastMapError):
+        _gpu([0, 2, 4], [[7, 1], [0, 3]])  # first keypoint out of range (never dereferenced)
+    with pytest.raises(FastMapError):
+        _gpu([0, 2, 4], [[-1, 3], [0, 3]])
 
 
 def test_larger_scene_against_independent_components():
