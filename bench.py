@@ -72,6 +72,24 @@ def args_():
     return ap.parse_args()
 
 
+def max_over_ranks(x, world, device=None):
+    """The largest of every rank's x (a float; all ranks call it when world >
+    1, over the initialised process group)."""
+    import torch
+    if world <= 1:
+        return float(x)
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, steps, total_ms):
+    """Whole-job units per second: every rank's units over the slowest rank's
+    time (the weak-scaling replicas each process units_per_rank per step)."""
+    return world * units_per_rank * steps / (total_ms * 1e-3)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -980,20 +998,14 @@ def main():
         if k >= max(a.warmup, 1):
             e2e_ms += 1e3 * dt
             e2e_calls.append(1e6 * dt)
-    e2 = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2, op=dist.ReduceOp.MAX)
-    e2e_ms = float(e2.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
     # pass A: the number (no per-kernel events inside the steps)
     pr.timing(False)
     with Clocks(local) as clk:
         total_ms = timed_pass()
     launches = pr.timing_read()
     gpu_launches = int(sum(v[0] for v in launches.values()))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     # pass B: per-kernel device time from the library's event pairs on its stream
     pr.timing(True)
     timed_pass()
@@ -1009,7 +1021,7 @@ def main():
         n_ea, ms_ea = kt.get("k_ea_direct", (0, 0.0))
         avg_ea = ms_ea / max(n_ea, 1)
         achieved = BYTES_PER_PAIR * Z / (avg_ea * 1e-3) / 1e9
-        value = world * Z * a.steps / (total_ms * 1e-3)
+        value = job_throughput(world, Z, a.steps, total_ms)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
@@ -1019,7 +1031,7 @@ def main():
                          "frac": achieved / peak, "traffic": profiled_traffic(),
                          "kernel": "k_ea_direct", "bytes_per_launch": BYTES_PER_PAIR * Z,
                          "avg_launch_us": avg_ea * 1e3, "peak_kind": f"{peak_kind} copy bandwidth"},
-            "e2e": {"value": world * Z * a.steps / (e2e_ms * 1e-3), "unit": UNIT,
+            "e2e": {"value": job_throughput(world, Z, a.steps, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": int(host_p.numel() * 4), "d2h_bytes_per_step": int(host_g.numel() * 4 + 4),
                     "call": "fm_loss_grad with host params / host loss and gradient",
                     "us_per_call_median": float(np.median(e2e_calls)) if e2e_calls else None,
