@@ -261,7 +261,7 @@ def _ptr(x):
         if isinstance(x, torch.Tensor):
             if not x.is_contiguous():
                 x = x.contiguous()
-            return x.data_ptr(), bool(x.is_cuda), x
+            return x.data_ptr(), x.is_cuda, x
     except ImportError:  # pragma: no cover
         pass
     a = np.ascontiguousarray(x)
@@ -274,6 +274,8 @@ def _as(x, dtype):
         import torch
         if isinstance(x, torch.Tensor):
             want = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+            if x.dtype == want and x.is_contiguous():   # nothing to convert: no dispatch
+                return x
             return x.to(want).contiguous()
     except ImportError:  # pragma: no cover
         pass
