@@ -533,6 +533,15 @@ typedef struct {
   int32_t learned_prune_passes; /* prune + re-estimate passes before the
                                  translation stage (2): each pass sees the
                                  relative translations of the previous one */
+  int32_t rot_given;          /* 1: start from the rotation-stage parameters
+                                 set on the problem (fm_set_params), with no
+                                 relative poses, rotation initialisation or
+                                 rotation steps -- e.g. rotations aligned on
+                                 the raw matches of another problem, the
+                                 translation and epipolar stages then run on
+                                 this problem's (completed) keypoint pairs
+                                 (Appendix "Tracks"); needs reestimate_rel_t
+                                 or rel_t; loss_rotation is then NaN (0) */
 } fm_solve_opts;
 
 void fm_solve_opts_default(fm_solve_opts* opts);

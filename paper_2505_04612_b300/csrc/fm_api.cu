@@ -2396,6 +2396,7 @@ fm_status fm_triangulate(fm_problem* pr, const fm_tri_opts* opts, float* points,
 
 void fm_solve_opts_default(fm_solve_opts* o) {
   if (!o) return;
+  o->rot_given = 0;
   o->rot_init_iters = 2000;
   o->rot_iters = 2000;
   o->rot_lr = 1e-3f;
@@ -2452,12 +2453,21 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
     for (float v : Lv) t += v;
     return t;
   };
-  // 0. relative poses from the keypoints when none were given
-  if (!pr->rel_R_set && (e = fm_relative_poses(pr, 0, o->ea_delta, nullptr)) != FM_OK) return e;
-  // 1-2. rotations
-  if ((e = fm_rotation_init(pr, o->rot_init_iters)) != FM_OK) return e;
-  if ((e = stepped(pr, FM_STAGE_ROTATION, o, o->rot_lr, o->rot_iters, Lv.data())) != FM_OK) return e;
-  res->loss_rotation = total();
+  if (o->rot_given) {
+    // rotations given (e.g. aligned on another problem's raw matches)
+    if (!pr->rot_params_set)
+      return fail(pr, FM_ERR_STATE, "rot_given needs the rotation-stage parameters (fm_set_params)");
+    if (!o->reestimate_rel_t && !pr->rel_t_set)
+      return fail(pr, FM_ERR_STATE, "rot_given needs reestimate_rel_t or rel_t");
+    res->loss_rotation = NAN;
+  } else {
+    // 0. relative poses from the keypoints when none were given
+    if (!pr->rel_R_set && (e = fm_relative_poses(pr, 0, o->ea_delta, nullptr)) != FM_OK) return e;
+    // 1-2. rotations
+    if ((e = fm_rotation_init(pr, o->rot_init_iters)) != FM_OK) return e;
+    if ((e = stepped(pr, FM_STAGE_ROTATION, o, o->rot_lr, o->rot_iters, Lv.data())) != FM_OK) return e;
+    res->loss_rotation = total();
+  }
   // 3. relative translations
   if (o->reestimate_rel_t) {
     if ((e = fm_relative_translations(pr, nullptr, 0)) != FM_OK) return e;

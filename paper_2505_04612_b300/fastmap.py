@@ -98,6 +98,7 @@ class fm_solve_opts(ctypes.Structure):
         ("tri_max_err_px", ctypes.c_float), ("tri_min_angle_deg", ctypes.c_float),
         ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
         ("learned", ctypes.c_int32), ("learned_p_min", ctypes.c_float), ("learned_prune_passes", ctypes.c_int32),
+        ("rot_given", ctypes.c_int32),
     ]
 
 
