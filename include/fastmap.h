@@ -577,7 +577,12 @@ typedef struct {
  * triangulation.  Each Adam loop runs in four equal phases with the learning
  * rate scaled by 1, 0.3, 0.1, 0.03.  Needs rel_t when reestimate_rel_t is 0
  * and rel_R was given.  The solution is defined up to a similarity of the
- * world frame.  Synchronises. */
+ * world frame; it is reported in a fixed gauge, per scene: the first valid
+ * camera (cam_valid) has R = I, and the valid cameras' centres have their
+ * centroid at the origin and unit mean norm (Appendix "Multiple
+ * Initializations" normalises the centres the same way).  The epipolar-stage
+ * parameters are left in that gauge and the points are triangulated in it.
+ * Synchronises. */
 fm_status fm_solve(fm_problem* problem, const fm_solve_opts* opts, fm_result* result);
 
 /* ------------------------------------------------- learned inlier weights

@@ -2436,6 +2436,92 @@ static fm_status stepped(fm_problem* pr, fm_stage st, const fm_solve_opts* o, fl
   return FM_OK;
 }
 
+namespace {
+
+// The output gauge of fm_solve, per scene, applied to the epipolar-stage
+// parameters themselves (so that the outputs and the triangulated points
+// share it): the world frame is rotated so that the scene's first valid
+// camera has R = I, then moved and scaled so that the valid cameras' centres
+// have their centroid at the origin and unit mean norm.  With G = R_ref, mu
+// and sigma the centroid and mean norm of G c_i: R_i' = R_i G^T and
+// t_i' = (R_i' mu + t_i) / sigma, so that c_i' = (G c_i - mu) / sigma.
+cudaError_t apply_output_gauge(fm_problem* pr) {
+  const int N = pr->N;
+  std::vector<float> P;
+  cudaError_t ce = fetch(P, pr->ea_params, (size_t)9 * N, true);
+  if (ce != cudaSuccess) return ce;
+  auto rot = [&](int c, double R[9]) {   // 6D (two columns) -> R, Gram-Schmidt
+    const float* a = &P[9 * (size_t)c];
+    double b1[3] = {a[0], a[1], a[2]}, b2[3] = {a[3], a[4], a[5]};
+    double n1 = std::sqrt(b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2]);
+    for (double& v : b1) v /= n1;
+    const double d = b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2];
+    for (int k = 0; k < 3; ++k) b2[k] -= d * b1[k];
+    const double n2 = std::sqrt(b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]);
+    for (double& v : b2) v /= n2;
+    const double b3[3] = {b1[1] * b2[2] - b1[2] * b2[1], b1[2] * b2[0] - b1[0] * b2[2], b1[0] * b2[1] - b1[1] * b2[0]};
+    for (int r = 0; r < 3; ++r) {
+      R[3 * r] = b1[r];
+      R[3 * r + 1] = b2[r];
+      R[3 * r + 2] = b3[r];
+    }
+  };
+  for (int q = 0; q < pr->S; ++q) {
+    const int b = pr->h_sc_cam_off[q], e = pr->h_sc_cam_off[q + 1];
+    int ref = -1;
+    for (int c = b; c < e && ref < 0; ++c)
+      if (pr->h_cam_valid[c]) ref = c;
+    if (ref < 0) continue;
+    double G[9];
+    rot(ref, G);
+    // centres G c_i of the valid cameras, c_i = -R_i^T t_i
+    std::vector<double> gc(3 * (size_t)(e - b), 0.0);
+    double mu[3] = {0, 0, 0};
+    int nv = 0;
+    for (int c = b; c < e; ++c) {
+      double R[9];
+      rot(c, R);
+      const float* t = &P[9 * (size_t)c + 6];
+      double ci[3];
+      for (int k = 0; k < 3; ++k) ci[k] = -(R[k] * t[0] + R[3 + k] * t[1] + R[6 + k] * t[2]);
+      for (int r = 0; r < 3; ++r) gc[3 * (c - b) + r] = G[3 * r] * ci[0] + G[3 * r + 1] * ci[1] + G[3 * r + 2] * ci[2];
+      if (pr->h_cam_valid[c]) {
+        for (int r = 0; r < 3; ++r) mu[r] += gc[3 * (c - b) + r];
+        ++nv;
+      }
+    }
+    for (double& v : mu) v /= nv;
+    double sigma = 0.0;
+    for (int c = b; c < e; ++c)
+      if (pr->h_cam_valid[c]) {
+        const double* g = &gc[3 * (c - b)];
+        sigma += std::sqrt((g[0] - mu[0]) * (g[0] - mu[0]) + (g[1] - mu[1]) * (g[1] - mu[1]) +
+                           (g[2] - mu[2]) * (g[2] - mu[2]));
+      }
+    sigma /= nv;
+    if (!(sigma > 1e-30)) sigma = 1.0;   // one valid camera: no scale to fix
+    for (int c = b; c < e; ++c) {
+      double R[9], Rn[9];
+      rot(c, R);
+      for (int r = 0; r < 3; ++r)   // R' = R G^T
+        for (int k = 0; k < 3; ++k) Rn[3 * r + k] = R[3 * r] * G[3 * k] + R[3 * r + 1] * G[3 * k + 1] + R[3 * r + 2] * G[3 * k + 2];
+      float* a = &P[9 * (size_t)c];
+      double tn[3];
+      for (int r = 0; r < 3; ++r) tn[r] = (Rn[3 * r] * mu[0] + Rn[3 * r + 1] * mu[1] + Rn[3 * r + 2] * mu[2] + a[6 + r]) / sigma;
+      for (int r = 0; r < 3; ++r) {
+        a[r] = (float)Rn[3 * r];
+        a[3 + r] = (float)Rn[3 * r + 1];
+        a[6 + r] = (float)tn[r];
+      }
+    }
+  }
+  ce = cudaMemcpyAsync(pr->ea_params, P.data(), sizeof(float) * 9 * N, cudaMemcpyHostToDevice, pr->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(pr->stream);
+  return ce;
+}
+
+}  // namespace
+
 fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
   if (!pr || !o || !res) return FM_ERR_INVALID_ARG;
   if (!res->R || !res->t) return fail(pr, FM_ERR_INVALID_ARG, "result R and t buffers are required");
@@ -2506,7 +2592,8 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
     if ((e = stepped(pr, FM_STAGE_EPIPOLAR, o, o->ea_lr, o->ea_iters, Lv.data())) != FM_OK) return e;
     res->loss_epipolar = total();
   }
-  // outputs
+  // outputs, in the output gauge
+  FM_CUDA(pr, apply_output_gauge(pr));
   float* dR = pr->scratch_params;     // [9N]
   float* dt = pr->scratch_grad;       // [3N]
   fm::launch_ea_to_Rt(pr->ea_params, pr->N, dR, dt, pr->stream);

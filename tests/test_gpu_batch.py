@@ -216,3 +216,32 @@ def test_connectivity_filter_marks_the_largest_component():
         assert pr.info().n_cams_connected == N + 20
         out = pr.solve(**opts)
     np.testing.assert_array_equal(out["cam_valid"], np.r_[want, np.ones(20, bool)])
+
+
+def test_solve_reports_the_output_gauge_per_scene():
+    """fm_solve's gauge, per scene: the first valid camera has R = I, the
+    valid cameras' centres have centroid 0 and mean norm 1, and the points
+    share the frame (in front of the cameras that see them)."""
+    scenes = _scenes()
+    b = concat_scenes(scenes)
+    R, _ = _rel(scenes)
+    T = int(b.kp_track.max()) + 1
+    with G.make_problem(b, rel_R=np.concatenate(R)) as pb:
+        out = pb.solve(n_tracks=T, rot_iters=200, trn_iters=200, trn_final_iters=100, ea_rounds=2, ea_iters=100)
+    Rs = out["R"].astype(np.float64)
+    c = -np.einsum("nba,nb->na", Rs, out["t"].astype(np.float64))
+    for k in range(len(scenes)):
+        c0, c1 = b.scene_cam_off[k], b.scene_cam_off[k + 1]
+        valid = np.nonzero(out["cam_valid"][c0:c1])[0] + c0
+        np.testing.assert_allclose(Rs[valid[0]], np.eye(3), atol=2e-6)
+        cv = c[valid]
+        np.testing.assert_allclose(cv.mean(0), 0.0, atol=2e-5)
+        assert abs(np.mean(np.linalg.norm(cv, axis=1)) - 1.0) < 2e-5
+    # points in the same frame: in front of the cameras that see them
+    pts, ok = out["points"], out["point_valid"]
+    assert ok.sum() > 0
+    m = np.nonzero(ok[b.kp_track])[0][:2000]
+    X = pts[b.kp_track[m]].astype(np.float64)
+    ci = b.pair_i[b.kp_img_pair[m]]
+    depth = np.einsum("nab,nb->na", Rs[ci], X)[:, 2] + out["t"].astype(np.float64)[ci, 2]
+    assert np.mean(depth > 0) > 0.99
