@@ -45,7 +45,10 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kItems = 8;
 constexpr int kTile = kThreads * kItems;   // 2048 elements per CTA in scans and sorts
-constexpr int kUfBound = 1 << 22;          // steps of one find / retries of one union at most
+// steps of one find / retries of one union at most: parent pointers only
+// decrease, so a find ends within K steps and a union's retries (each one a
+// root linked by another thread) are bounded by K as well
+__host__ __device__ constexpr int64_t uf_bound(int K) { return 2 * (int64_t)K + 64; }
 
 enum : int { kTrkBadMatch = 1, kTrkUfBound = 2 };
 
@@ -225,8 +228,9 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
 
 __device__ __forceinline__ int ld_parent(const int* p, int x) { return *((volatile const int*)(p + x)); }
 
-__device__ __forceinline__ int find_root(int* parent, int x, int* err) {
-  for (int it = 0; it < kUfBound; ++it) {
+__device__ __forceinline__ int find_root(int* parent, int x, int K, int* err) {
+  const int64_t bound = uf_bound(K);
+  for (int64_t it = 0; it < bound; ++it) {
     const int p = ld_parent(parent, x);
     if (p == x) return x;
     const int gp = ld_parent(parent, p);
@@ -259,20 +263,21 @@ __global__ void k_union(const int2* __restrict__ matches, int64_t M, int K, cons
       atomicOr(err, kTrkBadMatch);
       continue;
     }
-    int it = 0;
-    for (; it < kUfBound; ++it) {
-      const int ru = find_root(parent, m.x, err), rv = find_root(parent, m.y, err);
+    const int64_t bound = uf_bound(K);
+    int64_t it = 0;
+    for (; it < bound; ++it) {
+      const int ru = find_root(parent, m.x, K, err), rv = find_root(parent, m.y, K, err);
       if (ru == rv) break;
       const int hi = max(ru, rv), lo = min(ru, rv);
       if (atomicCAS(parent + hi, hi, lo) == hi) break;   // else hi was linked meanwhile: retry
     }
-    if (it == kUfBound) atomicOr(err, kTrkUfBound);
+    if (it == bound) atomicOr(err, kTrkUfBound);
   }
 }
 
 __global__ void k_label(int* parent, int K, int* __restrict__ label, int* __restrict__ size, int* err) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < K; v += gridDim.x * blockDim.x) {
-    const int r = find_root(parent, v, err);
+    const int r = find_root(parent, v, K, err);
     label[v] = r;
     atomicAdd(size + r, 1);
   }
