@@ -168,17 +168,24 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restr
 // Stable scatter of one 8-bit digit.  Warp w of the CTA owns elements
 // [tile + 256 w, tile + 256 (w + 1)) in 8 rounds of 32; ranks among equal
 // digits come from __match_any_sync in lane order, so the output keeps the
-// input order of equal digits.
+// input order of equal digits.  The tile is first ordered by digit in shared
+// memory, then written with consecutive threads on consecutive elements, so
+// that equal digits go out as contiguous runs (coalesced stores).
 __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
                                                             const uint32_t* __restrict__ vin,
                                                             uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                             int64_t n, int shift, int nblk,
                                                             const int* __restrict__ hist) {
   __shared__ int woff[kThreads / 32][256];
+  __shared__ int tile_off[256];   // first position of each digit inside the ordered tile
+  __shared__ int gbase[256];      // first global position of each digit of this tile
+  __shared__ int wsum[kThreads / 32];
+  __shared__ uint32_t sk[kTile], sv[kTile];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int d = lane; d < 256; d += 32) woff[w][d] = 0;
   __syncwarp();
-  const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)w * 256;
+  const int64_t tile = (int64_t)blockIdx.x * kTile;
+  const int64_t base = tile + (int64_t)w * 256;
   const unsigned lt = (1u << lane) - 1u;
   // per-warp digit counts
   for (int r = 0; r < 8; ++r) {
@@ -193,19 +200,35 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
     __syncwarp();
   }
   __syncthreads();
-  // starting position of every (warp, digit): the CTA's global offset plus
-  // the earlier warps' counts
+  // per digit (one thread each): the warps' exclusive offsets inside the
+  // digit, the digit's count, and an exclusive scan of the counts over the
+  // digits (warp shuffles, then the warps in order)
   {
     const int d = threadIdx.x;   // kThreads == 256 digits
-    int run = hist[(size_t)d * nblk + blockIdx.x];
+    gbase[d] = hist[(size_t)d * nblk + blockIdx.x];
+    int cnt = 0;
 #pragma unroll
     for (int k = 0; k < kThreads / 32; ++k) {
       const int c = woff[k][d];
-      woff[k][d] = run;
-      run += c;
+      woff[k][d] = cnt;
+      cnt += c;
     }
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    int off = inc - cnt;
+    for (int k = 0; k < w; ++k) off += wsum[k];
+    tile_off[d] = off;
+#pragma unroll
+    for (int k = 0; k < kThreads / 32; ++k) woff[k][d] += off;
   }
   __syncthreads();
+  // ordered tile in shared memory
   for (int r = 0; r < 8; ++r) {
     const int64_t k = base + r * 32 + lane;
     const bool ok = k < n;
@@ -215,12 +238,27 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint32_t* __re
       const unsigned d = (key >> shift) & 255u;
       const unsigned peers = __match_any_sync(act, d);
       const int pos = woff[w][d] + __popc(peers & lt);
-      kout[pos] = key;
-      vout[pos] = vin[k];
+      sk[pos] = key;
+      sv[pos] = vin[k];
       __syncwarp(act);
       if ((peers & lt) == 0) woff[w][d] += __popc(peers);
     }
     __syncwarp();
+  }
+  __syncthreads();
+  // coalesced write: element j of the ordered tile goes to its digit's global
+  // start plus its position inside the digit's run
+  const int valid = (n - tile < kTile) ? (int)(n - tile) : kTile;
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const int j = i * kThreads + threadIdx.x;
+    if (j < valid) {
+      const uint32_t key = sk[j];
+      const unsigned d = (key >> shift) & 255u;
+      const int pos = gbase[d] + (j - tile_off[d]);
+      kout[pos] = key;
+      vout[pos] = sv[j];
+    }
   }
 }
 
