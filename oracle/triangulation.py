@@ -7,7 +7,8 @@ large error are outliers, a point with fewer than 3 inlier keypoints is
 dropped, and so is a point whose largest triangulation angle is below a
 threshold.  The paper names no triangulation method, error threshold or
 angle threshold; the readings here:
-  * two-ray midpoint triangulation of each keypoint pair;
+  * two-ray midpoint triangulation of each keypoint pair; a pair whose rays
+    are within ~0.057 deg of parallel gives no point (PARALLEL_SIN2);
   * a track's keypoints are its distinct (camera, pixel) observations; an
     observation is an inlier if its reprojection error is <= max_err_px;
     the point needs inliers in >= 3 distinct cameras;
@@ -18,16 +19,26 @@ angle threshold; the readings here:
 import numpy as np
 
 
+# Rays closer than this to parallel (sin^2 of the angle between them) give
+# no point: their intersection is not determined at the float32 precision
+# of the inputs (an angle below ~0.057 deg).
+PARALLEL_SIN2 = 1e-6
+
+
 def midpoint(o1, d1, o2, d2):
-    """Midpoint of the shortest segment between rays o1 + s d1 and o2 + u d2."""
+    """Midpoint of the shortest segment between rays o1 + s d1 and o2 + u d2.
+    The normal equations of min |o1 + s d1 - o2 - u d2|^2 have determinant
+    |d1|^2 |d2|^2 - (d1.d2)^2 = |d1 x d2|^2 (Lagrange's identity); the cross
+    product form keeps it exact for parallel directions.  ok is False when
+    |d1 x d2|^2 <= PARALLEL_SIN2 |d1|^2 |d2|^2."""
     w0 = o1 - o2
     a = np.sum(d1 * d1, -1)
     b = np.sum(d1 * d2, -1)
     c = np.sum(d2 * d2, -1)
     d = np.sum(d1 * w0, -1)
     e = np.sum(d2 * w0, -1)
-    den = a * c - b * b
-    ok = den > 1e-15 * a * c
+    den = np.sum(np.cross(d1, d2) ** 2, -1)
+    ok = den > PARALLEL_SIN2 * a * c
     dd = np.where(ok, den, 1.0)
     s = np.where(ok, (b * e - c * d) / dd, 0.0)
     u = np.where(ok, (a * e - b * d) / dd, 0.0)
@@ -35,9 +46,14 @@ def midpoint(o1, d1, o2, d2):
 
 
 def triangulate(R, t, pair_i, pair_j, kp_img_pair, x1, x2, kp_track, n_tracks, focal,
-                max_err_px=4.0, min_angle_deg=2.0):
+                max_err_px=4.0, min_angle_deg=2.0, diag=False):
     """R [N,3,3], t [N,3] world-to-camera; x1, x2 calibrated [Z,3]; returns
-    (points [T,3], valid [T] bool, n_inlier_cams [T])."""
+    (points [T,3], valid [T] bool, n_inlier_cams [T]), and with diag=True a
+    fourth value: a dict of the intermediate quantities the decisions are
+    taken on (per keypoint pair: err1, err2 in pixels, angle_deg, pair_ok,
+    pair_sin2 = sin^2 of the angle between its rays;
+    per track: max_angle_deg), for tests that locate decisions lying within
+    rounding of a threshold."""
     R = np.asarray(R, np.float64)
     t = np.asarray(t, np.float64)
     o = -np.einsum("nba,nb->na", R, t)
@@ -79,4 +95,10 @@ def triangulate(R, t, pair_i, pair_j, kp_img_pair, x1, x2, kp_track, n_tracks, f
     max_ang = np.zeros(T)
     np.maximum.at(max_ang, kp_track, ang)
     valid = (cnt > 0) & (ncam >= 3) & (max_ang >= min_angle_deg)
+    if diag:
+        return pts, valid, ncam, {"err1": reproj_err(P, ci, x1), "err2": reproj_err(P, cj, x2),
+                                  "angle_deg": np.degrees(np.arccos(np.clip(cosang, -1.0, 1.0))),
+                                  "pair_ok": ok, "max_angle_deg": max_ang,
+                                  "pair_sin2": np.sum(np.cross(d1, d2) ** 2, 1) /
+                                               np.maximum(np.sum(d1 * d1, 1) * np.sum(d2 * d2, 1), 1e-300)}
     return pts, valid, ncam

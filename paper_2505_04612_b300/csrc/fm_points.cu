@@ -2,7 +2,8 @@
 // keypoint pair of a completed track, average per track, reject keypoints by
 // reprojection error, keep points with >= 3 inlier keypoints (distinct
 // cameras) and a large enough triangulation angle.  Readings (the paper names
-// no method or thresholds): two-ray midpoint; an observation is an inlier if
+// no method or thresholds): two-ray midpoint (rays within ~0.057 deg of
+// parallel give no point); an observation is an inlier if
 // its reprojection error is <= max_err_px; the triangulation angle of a pair
 // is the angle at the averaged point between the rays to the two camera
 // centres, and the largest over pairs whose two keypoints are inliers must be
@@ -98,14 +99,23 @@ __device__ __forceinline__ void ray(const Cam& k, float u, float v, float* d) {
   for (int a = 0; a < 3; ++a) d[a] = k.R[a] * u + k.R[3 + a] * v + k.R[6 + a];
 }
 
+// Midpoint of the shortest segment between rays o1 + s d1 and o2 + u d2.  The
+// determinant of the normal equations, |d1|^2 |d2|^2 - (d1.d2)^2, is taken in
+// the equal form |d1 x d2|^2 with rounded (uncontracted) products, so that
+// parallel directions give exactly 0 (a fused a*c - b*b leaves the rounding
+// error of b*b); rays closer than kParallelSin2 to parallel give no point.
+constexpr float kParallelSin2 = 1e-6f;
 __device__ __forceinline__ bool midpoint(const float* o1, const float* d1, const float* o2, const float* d2,
                                          float* X) {
   float w0[3];
   for (int a = 0; a < 3; ++a) w0[a] = o1[a] - o2[a];
   const float a = dot3(d1, d1), b = dot3(d1, d2), c = dot3(d2, d2);
   const float d = dot3(d1, w0), e = dot3(d2, w0);
-  const float den = a * c - b * b;
-  if (!(den > 1e-15f * a * c)) return false;
+  const float k0 = __fsub_rn(__fmul_rn(d1[1], d2[2]), __fmul_rn(d1[2], d2[1]));
+  const float k1 = __fsub_rn(__fmul_rn(d1[2], d2[0]), __fmul_rn(d1[0], d2[2]));
+  const float k2 = __fsub_rn(__fmul_rn(d1[0], d2[1]), __fmul_rn(d1[1], d2[0]));
+  const float den = k0 * k0 + k1 * k1 + k2 * k2;
+  if (!(den > kParallelSin2 * a * c)) return false;
   const float s = (b * e - c * d) / den, u = (a * e - b * d) / den;
   for (int k = 0; k < 3; ++k) X[k] = 0.5f * (o1[k] + s * d1[k] + o2[k] + u * d2[k]);
   return true;

@@ -33,3 +33,15 @@ def test_oracle_solve_recovers_noise_free_scene():
     assert S.centre_errors(out["centres"], sc.centers_gt).max() < 5e-3 * scale
     assert out["n_kept"] == sc.n_kp
     assert out["point_valid"].sum() > 0.3 * len(out["point_valid"])
+
+
+def test_hash_uniform_golden_vectors():
+    """Published MurmurHash3 empty-input vectors pin the finaliser's constants
+    and shifts; salts that cancel the Weyl step at k = 1, 5, 1000 pin the
+    multiplier and the mod-2^32 wrap (tests/golden/hash_uniform.json)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hash_uniform.json")))
+    for c in g["cases"]:
+        v = S.hash_uniform(c["k"] + 1, c["salt"])[c["k"]]
+        assert v == c["value"], (c, v)
