@@ -73,7 +73,8 @@ typedef enum {
   FM_ERR_OOM = 3,           /* device memory could not be allocated */
   FM_ERR_NAN = 4,           /* a non-finite value was produced or given */
   FM_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
-  FM_ERR_NOT_CONVERGED = 6,
+  FM_ERR_NOT_CONVERGED = 6,  /* reserved (kept for ABI stability): the method runs
+                               fixed iteration counts and has no convergence test */
   FM_ERR_STATE = 7          /* the call needs state that has not been set */
 } fm_status;
 
@@ -582,6 +583,9 @@ typedef struct {
  * centroid at the origin and unit mean norm (Appendix "Multiple
  * Initializations" normalises the centres the same way).  The epipolar-stage
  * parameters are left in that gauge and the points are triangulated in it.
+ * Divergence: each stage's final per-scene losses are checked on the host; a
+ * non-finite one ends the solve with FM_ERR_NAN (fm_last_error names the
+ * stage and the scene), and so do non-finite output poses.
  * Synchronises. */
 fm_status fm_solve(fm_problem* problem, const fm_solve_opts* opts, fm_result* result);
 
@@ -765,8 +769,10 @@ fm_status fm_loss_history(fm_problem* problem, float* out, int32_t capacity, int
  * latency-critical loops where an allocation could block or fail, and
  * deployments that must keep a fixed, known footprint.
  *
- * fm_ea_loss_grad_static evaluates the direct epipolar loss (Eq. 7 for
- * FM_EA_L1, Eqs. 8-9 for FM_EA_L2) and its gradient with the same kernels as
+ * fm_ea_loss_grad_static evaluates the direct epipolar loss of
+ * fm_loss_grad's FM_STAGE_EPIPOLAR -- the mean over keypoint pairs of the
+ * (optionally weighted) absolute algebraic epipolar error for FM_EA_L1, or of
+ * its square for FM_EA_L2 -- and its gradient, with the same kernels as
  * fm_loss_grad, without creating a problem and without allocating anything:
  * its temporary tables live in one 16 MiB array of device memory that the
  * library holds on every GPU that loads it, until the process exits.
@@ -775,8 +781,12 @@ fm_status fm_loss_history(fm_problem* problem, float* out, int32_t capacity, int
  *   kp_dev       [Z] float4 (x1, y1, x2, y2): calibrated coordinates
  *                K^-1 [u, v, 1]^T of the keypoint in image i_n and in j_n,
  *                grouped by image pair in index order
- *   seg_off_dev  [P+1] first keypoint pair of each image pair (seg_off[P] = Z)
- *   pair_i_dev, pair_j_dev  [P] camera indices of each image pair
+ *   seg_off_dev  [P+1] first keypoint pair of each image pair: seg_off[0] =
+ *                0, non-decreasing, seg_off[P] = Z (checked on the device,
+ *                see Errors)
+ *   pair_i_dev, pair_j_dev  [P] camera indices of each image pair, in
+ *                [0, n_cams) (not checked: an index outside it reads outside
+ *                params_dev)
  *   params_dev   [N*9] epipolar-stage parameters (6D rotation, t)
  *   weights_dev  [Z] per-pair weights, or NULL for unit weights
  * loss: FM_EA_L1 or FM_EA_L2; inv_z: the 1/Z normaliser.
@@ -788,16 +798,24 @@ fm_status fm_loss_history(fm_problem* problem, float* out, int32_t capacity, int
  * cuda_stream: the stream to enqueue on (NULL = default); the call returns
  * after enqueueing.
  *
+ * Errors: arguments are checked on the host (FM_ERR_INVALID_ARG with a
+ * message from fm_last_error(NULL), before any GPU work).  What only the
+ * kernels can see is reported through the loss, since the call does not wait
+ * for them: when seg_off_dev is not a CSR table of Z pairs (then no keypoint
+ * pair is read and the gradient blocks are zero) or when a bounded wait of
+ * the direct kernel runs out (the sums are then incomplete), *loss_dev is
+ * NaN.  Check the loss before using the gradient.
+ *
  * Limits and sharing: the tables need about 118 B per image pair plus 0.4 B
  * per keypoint pair; a problem that does not fit in 16 MiB (118 P + 0.4 Z
- * beyond 16.7M) is rejected with
- * FM_ERR_INVALID_ARG and a message from fm_last_error(NULL), before any GPU
- * work.  Every call on a device shares the one array and leaves its contents
- * behind; nothing in it needs to start at zero.  Calls whose GPU work
+ * beyond 16.7M) is rejected with FM_ERR_INVALID_ARG before any GPU work.
+ * Every call on a device shares the one array and leaves its contents
+ * behind; each call clears the one word that must start at zero (its error
+ * word) and writes every other entry before reading it.  Calls whose GPU work
  * overlaps (two streams, or two host threads) race on the array: serialise
  * them.  The first call on each device looks up the array's device address
- * (and sets the kernel's shared-memory limit); make that first call before
- * any stream capture. */
+ * and sets the kernel's shared-memory limit on that device; make that first
+ * call before any stream capture. */
 fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev,
                                  const int32_t* pair_i_dev, const int32_t* pair_j_dev,
                                  const float* params_dev, const float* weights_dev,

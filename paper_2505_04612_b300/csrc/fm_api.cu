@@ -2539,6 +2539,14 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
     for (float v : Lv) t += v;
     return t;
   };
+  // divergence: a stage whose final loss is not finite ends the solve
+  auto finite = [&](const std::vector<float>& L, const char* stage) -> fm_status {
+    for (size_t k = 0; k < L.size(); ++k)
+      if (!std::isfinite(L[k]))
+        return fail(pr, FM_ERR_NAN, std::string(stage) + " stage diverged: its final loss is not finite (scene " +
+                                        std::to_string(k % pr->S) + ")");
+    return FM_OK;
+  };
   if (o->rot_given) {
     // rotations given (e.g. aligned on another problem's raw matches)
     if (!pr->rot_params_set)
@@ -2552,6 +2560,7 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
     // 1-2. rotations
     if ((e = fm_rotation_init(pr, o->rot_init_iters)) != FM_OK) return e;
     if ((e = stepped(pr, FM_STAGE_ROTATION, o, o->rot_lr, o->rot_iters, Lv.data())) != FM_OK) return e;
+    if ((e = finite(Lv, "rotation")) != FM_OK) return e;
     res->loss_rotation = total();
   }
   // 3. relative translations
@@ -2573,6 +2582,7 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
   if ((e = stepped(pr, FM_STAGE_TRANSLATION, o, o->trn_lr, o->trn_iters, run_loss.data())) != FM_OK) return e;
   if ((e = fm_translation_merge(pr, nullptr)) != FM_OK) return e;
   if ((e = stepped(pr, FM_STAGE_TRANSLATION, o, o->trn_lr, o->trn_final_iters, Lv.data())) != FM_OK) return e;
+  if ((e = finite(Lv, "translation")) != FM_OK) return e;
   res->loss_translation = total();
   // 5. epipolar adjustment: IRLS / filtering rounds on the compact form
   if ((e = fm_epipolar_init_from_stages(pr)) != FM_OK) return e;
@@ -2590,6 +2600,7 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
     if (e != FM_OK) return e;
     res->n_kept = kept;
     if ((e = stepped(pr, FM_STAGE_EPIPOLAR, o, o->ea_lr, o->ea_iters, Lv.data())) != FM_OK) return e;
+    if ((e = finite(Lv, "epipolar")) != FM_OK) return e;
     res->loss_epipolar = total();
   }
   // outputs, in the output gauge
@@ -2603,6 +2614,9 @@ fm_status fm_solve(fm_problem* pr, const fm_solve_opts* o, fm_result* res) {
   FM_CUDA(pr, cudaMemcpyAsync(pr->h_err, pr->d_err, sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
   FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
   if (*pr->h_err) return check_err_bits(pr);
+  for (int64_t k = 0; k < 9 * (int64_t)pr->N; ++k)
+    if (!std::isfinite(res->R[k]) || (k < 3 * (int64_t)pr->N && !std::isfinite(res->t[k])))
+      return fail(pr, FM_ERR_NAN, "the solved poses are not finite (the last update diverged)");
   if (res->cam_valid)
     for (int c = 0; c < pr->N; ++c) res->cam_valid[c] = pr->h_cam_valid[c];
   res->n_tracks = 0;

@@ -22,26 +22,42 @@ template <> struct Layout<2> { static constexpr int PART = 12, PDIM = 9; static 
 constexpr int kCamThreads = 128;
 constexpr int kCamWarps = kCamThreads / 32;
 
-// fixed-order sum of the per-image-pair loss terms of one run (one CTA; four
-// independent accumulators per thread keep four loads in flight)
+// fixed-order sum of n per-image-pair loss terms (one CTA of kCamThreads):
+// scalar loads up to the first 16-B boundary, then float4 loads with eight in
+// flight per thread, then the scalar tail; per-thread partials in a fixed
+// order and a tree over the threads.  The order depends only on n and on the
+// address of x, so every launch over the same range adds in the same order.
 __device__ void loss_sum_cta(const float* x, int n, float* out) {
   __shared__ float part[kCamThreads];
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  int k = threadIdx.x;
-  for (; k + 3 * kCamThreads < n; k += 4 * kCamThreads) {
-    s0 += x[k];
-    s1 += x[k + kCamThreads];
-    s2 += x[k + 2 * kCamThreads];
-    s3 += x[k + 3 * kCamThreads];
+  constexpr int T = kCamThreads;
+  const int t = threadIdx.x;
+  const int head = min(n, (int)(((16u - (unsigned)(reinterpret_cast<uintptr_t>(x) & 15u)) & 15u) >> 2));
+  const float4* x4 = reinterpret_cast<const float4*>(x + head);
+  const int n4 = (n - head) >> 2;
+  float acc[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) acc[u] = 0.f;
+  int k = t;
+  for (; k + 7 * T < n4; k += 8 * T) {
+    float4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = x4[k + u * T];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] += (v[u].x + v[u].y) + (v[u].z + v[u].w);
   }
-  for (; k < n; k += kCamThreads) s0 += x[k];
-  part[threadIdx.x] = (s0 + s1) + (s2 + s3);
+  for (; k < n4; k += T) {
+    const float4 v = x4[k];
+    acc[0] += (v.x + v.y) + (v.z + v.w);
+  }
+  if (t < head) acc[1] += x[t];
+  for (int q = head + 4 * n4 + t; q < n; q += T) acc[2] += x[q];
+  part[t] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
   __syncthreads();
-  for (int d = kCamThreads / 2; d > 0; d >>= 1) {
-    if ((int)threadIdx.x < d) part[threadIdx.x] += part[threadIdx.x + d];
+  for (int d = T / 2; d > 0; d >>= 1) {
+    if (t < d) part[t] += part[t + d];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = part[0];
+  if (t == 0) *out = part[0];
 }
 
 template <int STAGE, bool ADAM>
@@ -149,23 +165,13 @@ __global__ void __launch_bounds__(kCamThreads) k_cam(CamUpdate u) {
 }
 
 // fixed-order sum of each scene's range of values per run (one CTA per
-// (scene, run))
-__global__ void k_sum_fixed(const float* __restrict__ x, int P, const int* __restrict__ sc_pair_off,
-                            float* __restrict__ out) {
-  __shared__ float part[1024];
+// (scene, run)); the same order as the loss CTAs of k_cam
+__global__ void __launch_bounds__(kCamThreads) k_sum_fixed(const float* __restrict__ x, int P,
+                                                           const int* __restrict__ sc_pair_off,
+                                                           float* __restrict__ out) {
   const int sc = blockIdx.x, run = blockIdx.y;
   const int b = sc_pair_off ? sc_pair_off[sc] : 0, e = sc_pair_off ? sc_pair_off[sc + 1] : P;
-  const float* xr = x + (size_t)run * P + b;
-  const int n = e - b;
-  float s = 0.f;
-  for (int k = threadIdx.x; k < n; k += 1024) s += xr[k];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int d = 512; d > 0; d >>= 1) {
-    if ((int)threadIdx.x < d) part[threadIdx.x] += part[threadIdx.x + d];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[(size_t)run * gridDim.x + sc] = part[0];
+  loss_sum_cta(x + (size_t)run * P + b, e - b, out + (size_t)run * gridDim.x + sc);
 }
 
 template <int STAGE>
@@ -185,7 +191,7 @@ void launch_cam_update(int stage, const CamUpdate& u, cudaStream_t s) {
 
 void launch_sum_fixed(const float* x, int P, int runs, const int* sc_pair_off, int S, float* out,
                       cudaStream_t s) {
-  k_sum_fixed<<<dim3(S, runs), 1024, 0, s>>>(x, P, sc_pair_off, out);
+  k_sum_fixed<<<dim3(S, runs), kCamThreads, 0, s>>>(x, P, sc_pair_off, out);
 }
 
 }  // namespace fm

@@ -40,6 +40,7 @@
 //   kFromCoef  dL/dE from stored coefficients: no residual is recomputed, but
 //              the pair's x~2 x~1^T still needs the keypoints (16 + 4 B).
 #include <algorithm>
+#include <atomic>
 
 #include "fm_device.cuh"
 #include "fm_internal.h"
@@ -443,6 +444,14 @@ __global__ void k_ea_segments(SegArgs a) {
     cj = a.pj[n];
   }
   pdl_wait();               // records come from k_ea_direct
+  // the cameras' parameters are needed by the chain rule after the sum:
+  // loaded now, with the records, rather than after the butterfly
+  const bool chain = valid && sub == 0 && a.seg_grad != nullptr && cnt > 0;
+  float qi[9], qj[9];
+  if (chain) {
+    load_plain(a.params + 9 * ci, qi, 9);
+    load_plain(a.params + 9 * cj, qj, 9);
+  }
   float G[10];
   for (int k = 0; k < 10; ++k) G[k] = 0.f;
   if (valid && !a.dlde_in) {
@@ -478,9 +487,6 @@ __global__ void k_ea_segments(SegArgs a) {
     const float gl = a.grad_loss[a.pair_scene ? a.pair_scene[n] : 0];
     for (int k = 0; k < 9; ++k) G[k] *= gl;
   }
-  float qi[9], qj[9];
-  load_plain(a.params + 9 * ci, qi, 9);
-  load_plain(a.params + 9 * cj, qj, 9);
   PairGeo g;
   pair_geometry(qi, qj, g);
   float o[kSegGradEa];
@@ -515,11 +521,17 @@ static void launch_direct_u(const fm_problem* pr, const float* weights, float* c
   a.err = pr->d_err;
   a.n_wruns = pr->n_wruns;
   const size_t smem = WARPS * smem_per_warp<U>(WEIGHTED);
-  static int per_sm = 0;   // resident CTAs per SM (one device per process)
+  // resident CTAs per SM of this instantiation, per device: the shared-memory
+  // limit is a per-device function attribute, set once on each device
+  constexpr int kDevices = 64;
+  static std::atomic<int> per_sm_dev[kDevices];
+  const int dev = (pr->device >= 0 && pr->device < kDevices) ? pr->device : 0;
+  int per_sm = per_sm_dev[dev].load(std::memory_order_relaxed);
   if (per_sm == 0) {
     cudaFuncSetAttribute(k_ea_direct<U, LOSS, WEIGHTED, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ea_direct<U, LOSS, WEIGHTED, MODE>, WARPS * 32, smem);
     if (per_sm < 1) per_sm = 1;
+    per_sm_dev[dev].store(per_sm, std::memory_order_relaxed);
   }
   const int want = pr->ea_ctas_per_sm > 0 ? std::min(pr->ea_ctas_per_sm, per_sm) : per_sm;
   int ctas = (pr->n_wruns + WARPS - 1) / WARPS;

@@ -55,6 +55,7 @@ enum : int {
   kErrParamNonFinite = 8,
   kErrMlpTimeout = 16,   // a bounded wait of the tensor-core network kernel ran out
   kErrEaTimeout = 32,    // a bounded wait of the direct epipolar kernel ran out
+  kErrSegOff = 64,       // keypoint-pair offsets not a valid CSR table (allocation-free entry)
 };
 
 enum KernelId : int {
@@ -272,7 +273,11 @@ void launch_seg_offsets(const int* kp_pair, int64_t Z, int P, int* seg_off, int*
 // image pair, *T = lanes in use; then the lane descriptors and run headers of
 // n_runs warp runs (n_runs >= ceil(T / 32); runs past the lanes in use are
 // empty), the record bases, and seg_rec
-void launch_lane_scan(const int* seg_off, int P, int U, int* G, int* T, cudaStream_t s);
+// With err != null the offsets are checked first (seg_off[0] = 0,
+// non-decreasing, seg_off[P] = Z): on a bad table err gets kErrSegOff and
+// G = 0, *T = 0, so that no later kernel reads a keypoint pair.
+void launch_lane_scan(const int* seg_off, int P, int U, int* G, int* T, cudaStream_t s, int64_t Z = -1,
+                      int* err = nullptr);
 void launch_lane_desc(const int* seg_off, const int* G, const int* T, int P, int U, int n_runs, int* desc,
                       int4* wrun_info, cudaStream_t s);
 void launch_seg_records(const int* seg_off, const int* G, const int4* wrun_info, int P, int* seg_rec,

@@ -60,12 +60,27 @@ __device__ __forceinline__ int lanes_of(const int* __restrict__ seg_off, int n, 
 }
 
 // G[n] = sum_{n' < n} L_n' for n in [0, P]; *T = G[P].  One CTA, fixed order.
+// With err != null the offsets are validated first; a bad table gives no
+// lanes at all (G = 0, T = 0) and the error bit kErrSegOff.
 __global__ void __launch_bounds__(1024) k_scan_lanes(const int* __restrict__ seg_off, int P, int U,
-                                                     int* __restrict__ G, int* __restrict__ T) {
+                                                     int* __restrict__ G, int* __restrict__ T, long long Z,
+                                                     int* err) {
   __shared__ int part[1024];
   const int t = threadIdx.x;
   const int per = (P + 1023) / 1024;
   const int b = min(t * per, P), e = min(b + per, P);
+  if (err) {
+    bool bad = (t == 0) && (seg_off[0] != 0 || (long long)seg_off[P] != Z);
+    for (int n = b; n < e; ++n) bad |= seg_off[n + 1] < seg_off[n];
+    if (__syncthreads_or(bad)) {
+      for (int n = t; n <= P; n += 1024) G[n] = 0;
+      if (t == 0) {
+        *T = 0;
+        atomicOr(err, kErrSegOff);
+      }
+      return;
+    }
+  }
   int s = 0;
   for (int n = b; n < e; ++n) s += lanes_of(seg_off, n, U);
   part[t] = s;
@@ -155,7 +170,7 @@ __global__ void k_seg_records(const int* __restrict__ seg_off, const int* __rest
                               const int4* __restrict__ info, int P, int* __restrict__ seg_rec) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= P) return;
-  if (seg_off[n] == seg_off[n + 1]) {
+  if (seg_off[n] == seg_off[n + 1] || G[n + 1] <= G[n]) {   // no pairs, or no lanes (rejected table)
     seg_rec[2 * n] = 0;
     seg_rec[2 * n + 1] = 0;
     return;
@@ -209,8 +224,8 @@ void launch_seg_offsets(const int* kp_pair, int64_t Z, int P, int* seg_off, int*
   k_seg_offsets<<<grid_for(Z, 256), 256, 0, s>>>(kp_pair, Z, P, seg_off, err);
 }
 
-void launch_lane_scan(const int* seg_off, int P, int U, int* G, int* T, cudaStream_t s) {
-  k_scan_lanes<<<1, 1024, 0, s>>>(seg_off, P, U, G, T);
+void launch_lane_scan(const int* seg_off, int P, int U, int* G, int* T, cudaStream_t s, int64_t Z, int* err) {
+  k_scan_lanes<<<1, 1024, 0, s>>>(seg_off, P, U, G, T, (long long)Z, err);
 }
 
 void launch_lane_desc(const int* seg_off, const int* G, const int* T, int P, int U, int n_runs, int* desc,

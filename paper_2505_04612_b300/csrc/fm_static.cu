@@ -10,11 +10,17 @@
 // exists on every GPU that loads it, from load until process exit.
 //
 // The array is shared by every call on a device and keeps whatever the last
-// call wrote.  Nothing in it has to start at zero: each call writes every
-// entry it later reads.  Two calls whose GPU work overlaps in time (different
-// streams, or different host threads) race on the array and corrupt each
-// other's results; order such calls on one stream or synchronise between
-// them.
+// call wrote.  Each call writes every table entry it later reads, and clears
+// its error word (the one thing that must start at zero) with a memset on
+// the stream.  Two calls whose GPU work overlaps in time (different streams,
+// or different host threads) race on the array and corrupt each other's
+// results; order such calls on one stream or synchronise between them.
+//
+// The call never waits for the GPU, so it cannot return a status for what the
+// kernels find: a keypoint-pair offset table that is not a CSR table of Z
+// pairs (checked before any keypoint is read; the lane tables are then left
+// empty, so nothing is read past the caller's arrays) or a bounded wait of
+// the direct kernel that ran out.  Either one makes the loss NaN.
 #include <mutex>
 
 #include "fm_internal.h"
@@ -50,6 +56,11 @@ cudaError_t scratch_address(int device, void** out) {
 }
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// the loss becomes NaN when a kernel of the call raised an error bit
+__global__ void k_nan_on_error(const int* err, float* loss) {
+  if (*err != 0) *loss = __int_as_float(0x7fc00000);
+}
 
 }  // namespace
 
@@ -99,6 +110,7 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
 
   // a problem view whose tables point into the static array (no allocation)
   fm_problem v;
+  v.device = dev;
   v.N = n_cams;
   v.P = P;
   v.Z = Z;
@@ -125,7 +137,7 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
   int* T = G + P + 1;
   p += b_g;
   long long* total = reinterpret_cast<long long*>(p);
-  v.d_err = reinterpret_cast<int*>(total + 1);   // error bits of bounded waits (not reported: the call is asynchronous)
+  v.d_err = reinterpret_cast<int*>(total + 1);   // error bits of this call (made a NaN loss at the end)
   v.seg_grad = pair_grad_dev;
   v.n_wruns = n_wruns;
   cudaStream_t s = v.stream;
@@ -140,9 +152,15 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
   const bool was = fm::g_capturing;
   fm::g_capturing = was || cap == cudaStreamCaptureStatusActive;
   fm::g_plain_once = true;
+  e = cudaMemsetAsync(v.d_err, 0, sizeof(int), s);
+  if (e != cudaSuccess) {
+    fm::g_capturing = was;
+    return static_fail(FM_ERR_CUDA, std::string("clearing the error word: ") + cudaGetErrorString(e));
+  }
   fm::launch_ea_tables(params_dev, v.pair_i, v.pair_j, v.seg_off, P, v.seg_tab, nullptr, s);
+  // the offsets are validated before any lane table is built from them
+  fm::launch_lane_scan(v.seg_off, P, U, G, T, s, Z, v.d_err);
   if (n_wruns > 0) {
-    fm::launch_lane_scan(v.seg_off, P, U, G, T, s);
     fm::launch_lane_desc(v.seg_off, G, T, P, U, n_wruns, v.lane_desc, v.wrun_info, s);
     fm::launch_exclusive_scan_info(v.wrun_info, n_wruns, reinterpret_cast<int64_t*>(total), s);
   }
@@ -154,6 +172,7 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
   sa.l_scale = inv_z;
   fm::launch_ea_segments(sa, s);
   fm::launch_sum_fixed(v.seg_loss, P, 1, nullptr, 1, loss_dev, s);
+  k_nan_on_error<<<1, 1, 0, s>>>(v.d_err, loss_dev);
   fm::g_capturing = was;
   e = cudaGetLastError();
   if (e != cudaSuccess) return static_fail(FM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));

@@ -413,11 +413,12 @@ def fm_loss_history(handle, capacity=4096):
 
 
 def fm_ea_loss_grad_static(kp, seg_off, pair_i, pair_j, params, weights, n_cams, loss, inv_z,
-                           loss_out, pair_grad_out, stream=None):
+                           loss_out, pair_grad_out, stream=None, n_kp_pairs=None):
     """Allocation-free direct epipolar loss + per-image-pair gradient blocks.
     Every array is a CUDA tensor (kp float32 [Z,4], seg_off int32 [P+1],
     pair_i/pair_j int32 [P], params float32 [N*9], weights float32 [Z] or
-    None, loss_out float32 [1], pair_grad_out float32 [P*24])."""
+    None, loss_out float32 [1], pair_grad_out float32 [P*24]).  Z is taken
+    from kp unless n_kp_pairs is given (at most the pairs kp holds)."""
     args = [_ptr(a) for a in (kp, seg_off, pair_i, pair_j, params, weights, loss_out, pair_grad_out)]
     for a, (addr, dev, _) in zip(("kp", "seg_off", "pair_i", "pair_j", "params", "weights", "loss_out",
                                   "pair_grad_out"), args):
@@ -425,6 +426,10 @@ def fm_ea_loss_grad_static(kp, seg_off, pair_i, pair_j, params, weights, n_cams,
             raise ValueError(f"{a} must be a CUDA tensor")
     P = int(pair_i.numel())
     Z = int(kp.numel() // 4)
+    if n_kp_pairs is not None:
+        if not 0 <= int(n_kp_pairs) <= Z:
+            raise ValueError("n_kp_pairs must lie in [0, the pairs kp holds]")
+        Z = int(n_kp_pairs)
     st = lib().fm_ea_loss_grad_static(args[0][0], args[1][0], args[2][0], args[3][0], args[4][0], args[5][0],
                                       int(n_cams), P, Z, int(loss), ctypes.c_float(inv_z), args[6][0],
                                       args[7][0], _stream_handle(stream))

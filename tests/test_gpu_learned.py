@@ -1,9 +1,10 @@
 """What the trained network gains over the method without it: trained on the
 method's own converged solves of small synthetic scenes (the library's
 trainer), the learned filter reaches a better rotation accuracy in one
-epipolar round than the plain filter in five, in less wall time, on a
-held-out scene; its kept pairs are cleaner against the generator's inlier
-flags."""
+epipolar round than the plain filter in five on a held-out scene; its kept
+pairs are cleaner against the generator's inlier flags.  (Wall time is
+measured by bench.py --config learned_c5, not asserted here: a timing
+comparison on a shared machine is not a parity check.)"""
 import time
 
 import numpy as np
@@ -73,4 +74,3 @@ def test_learned_filter_gains_over_the_plain_one():
     assert learned["rot"] < plain["rot"], (learned, plain)
     assert learned["ctr"] < 1.25 * plain["ctr"] + 0.01, (learned, plain)
     assert learned["precision"] > plain["precision"] - 0.005, (learned, plain)
-    assert learned["time"] < plain["time"], (learned, plain)

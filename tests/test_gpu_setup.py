@@ -243,3 +243,24 @@ def test_relative_translations_leave_out_zero_weight_pairs():
         assert e_g <= e_o * (1 + 1e-3) + 1e-7, (n, e_g, e_o)
         assert abs(err_g[n] - e_g) <= 1e-4 * e_g + 1e-7
         assert rp.cheirality_count(Rij, tg, x1[kept], x2[kept]) >= rp.cheirality_count(Rij, -tg, x1[kept], x2[kept])
+
+
+@pytest.mark.parametrize("stage,override", [("rotation", {"rot_lr": 1e38}),
+                                            ("translation", {"trn_lr": 1e38}),
+                                            ("epipolar", {"ea_lr": 1e38})])
+def test_solve_reports_divergence(stage, override):
+    """A learning rate that drives a stage's parameters to overflow (Adam's
+    first steps move each parameter by about lr) makes its final loss
+    non-finite; fm_solve stops there with FM_ERR_NAN and names the
+    stage (plain float arithmetic on the GPU: nothing faults)."""
+    from paper_2505_04612_b300 import fastmap as F
+    sc = scene("c1", 1)
+    Rij, tij = gt_relative_poses(sc, rot_noise_deg=1.0, seed=1)
+    with G.make_problem(sc, rel_R=Rij.astype(np.float32), rel_t=tij.astype(np.float32)) as pr:
+        with pytest.raises(F.FastMapError) as ei:
+            pr.solve(rot_iters=40, trn_iters=40, trn_final_iters=20, ea_rounds=1, ea_iters=40, **override)
+        assert ei.value.status == F.FM_ERR_NAN, str(ei.value)
+        assert stage in str(ei.value), str(ei.value)
+        # the problem stays usable: a normal solve afterwards succeeds
+        out = pr.solve(rot_iters=40, trn_iters=40, trn_final_iters=20, ea_rounds=1, ea_iters=40)
+        assert np.all(np.isfinite(out["R"]))
