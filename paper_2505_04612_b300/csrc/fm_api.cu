@@ -22,7 +22,7 @@ const char* const kKernelNames[kKCount] = {
     "k_ea_segments", "k_rot_pairs", "k_trn_targets", "k_trn_pairs", "k_cam", "k_sum_fixed",
     "k_ea_reweight", "k_w_build", "k_ea_compact", "k_mart_iter", "k_reltrans", "k_merge",
     "k_triangulate", "k_ea_direct_loss", "k_ea_direct_coef", "k_mlp_pair_tables", "k_mlp_infer",
-    "k_relpose", "k_focal_vote", "k_dist_errors", "k_dist_reduce"};
+    "k_relpose", "k_focal_vote", "k_dist_errors", "k_dist_reduce", "k_ea_finish"};
 }
 
 namespace {
@@ -143,6 +143,8 @@ fm_status check_err_bits(fm_problem* pr) {
   FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
   if (bits == 0) return FM_OK;
   FM_CUDA(pr, cudaMemsetAsync(pr->d_err, 0, sizeof(int), pr->stream));
+  // a launch cut short must not leave arrival counters behind
+  if (pr->cam_cnt) FM_CUDA(pr, cudaMemsetAsync(pr->cam_cnt, 0, sizeof(int) * ((size_t)pr->N + 1), pr->stream));
   std::string msg;
   if (bits & fm::kErrKpRange) msg += "kp_img_pair outside [0, n_img_pairs); ";
   if (bits & fm::kErrKpOrder) msg += "kp_img_pair is not non-decreasing; ";
@@ -174,7 +176,7 @@ void release(fm_problem* pr) {
   dfree(pr->rot_adam.m); dfree(pr->rot_adam.v); dfree(pr->rot_adam.t);
   dfree(pr->trn_target); dfree(pr->trn_params);
   dfree(pr->trn_adam.m); dfree(pr->trn_adam.v); dfree(pr->trn_adam.t);
-  dfree(pr->scratch_params); dfree(pr->scratch_grad); dfree(pr->d_loss); dfree(pr->d_err);
+  dfree(pr->scratch_params); dfree(pr->scratch_grad); dfree(pr->d_loss); dfree(pr->d_err); dfree(pr->cam_cnt);
   dfree(pr->loss_hist);
   dfree(pr->W);
   dfree(pr->d_kept);
@@ -410,6 +412,8 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   FM_ALLOC(pr, pr->cam_seg, 2 * (size_t)P);
   FM_ALLOC(pr, pr->seg_off, P + 1);
   FM_ALLOC(pr, pr->d_err, 1);
+  FM_ALLOC(pr, pr->cam_cnt, (size_t)N + 1);
+  FM_CUDA(pr, cudaMemsetAsync(pr->cam_cnt, 0, sizeof(int) * ((size_t)N + 1), s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->pair_i, hi.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->pair_j, hj.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->focal, hf.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s));
@@ -630,6 +634,50 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
       fm::launch_ea_direct(pr, pr->ea_w, pr->ea_loss, s);
     }
     FM_LAUNCHED(pr);
+    if (adam || grad_dev) {
+      // the per-image-pair and per-camera passes in one launch; the loss of a
+      // single scene is summed by its last CTA, that of several scenes below
+      fm::FinishArgs f;
+      f.s = fm::seg_args(pr, params);
+      f.s.g_scale = (pr->ea_loss == FM_EA_L1) ? 1.f : 2.f;
+      fm::CamUpdate& u = f.u;
+      u.cam_seg_off = pr->cam_seg_off;
+      u.cam_seg = pr->cam_seg;
+      u.seg_grad = pr->seg_grad;
+      u.params = params;
+      u.params_out = adam ? const_cast<float*>(params) : nullptr;
+      u.grad_out = grad_dev;
+      u.m = state ? state->m : nullptr;
+      u.v = state ? state->v : nullptr;
+      u.step = step;
+      u.lr = adam ? adam->lr : 0.f;
+      u.b1 = adam ? adam->beta1 : 0.f;
+      u.b2 = adam ? adam->beta2 : 0.f;
+      u.eps = adam ? adam->eps : 0.f;
+      u.N = N;
+      u.P = P;
+      u.runs = 1;
+      u.seg_loss = pr->seg_loss;
+      u.sc_pair_off = pr->sc_pair_off;
+      u.S = pr->S;
+      f.cam_cnt = pr->cam_cnt;
+      f.blk_cnt = pr->cam_cnt + N;
+      float* first = loss_a ? loss_a : loss_b;
+      f.cta_loss = first != nullptr && pr->S == 1;
+      u.loss_out = f.cta_loss ? first : nullptr;
+      {
+        Timed t(pr, fm::kKEaFinish);
+        fm::launch_ea_finish(f, s);
+      }
+      FM_LAUNCHED(pr);
+      for (float* dst : {loss_a, loss_b}) {
+        if (!dst || (f.cta_loss && dst == first)) continue;
+        Timed t(pr, fm::kKLossSum);
+        fm::launch_sum_fixed(pr->seg_loss, P, 1, pr->sc_pair_off, pr->S, dst, s);
+        FM_LAUNCHED(pr);
+      }
+      return FM_OK;
+    }
     {
       Timed t(pr, fm::kKEaSegments);
       fm::launch_ea_segments(pr, params, pr->ea_loss, s);

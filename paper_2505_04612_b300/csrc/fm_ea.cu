@@ -42,8 +42,7 @@
 #include <algorithm>
 #include <atomic>
 
-#include "fm_device.cuh"
-#include "fm_internal.h"
+#include "fm_step.cuh"
 
 namespace fm {
 namespace {
@@ -423,81 +422,16 @@ __global__ void __launch_bounds__(WARPS * 32, kEaMinCtas) k_ea_direct(DirectArgs
 }
 
 // per image pair: sum its records -- or take dL/dE_n from a saved copy --
-// scale, and apply the chain rule.  kSegLanes lanes share an image pair: they
-// sum its records with a stride of kSegLanes and combine them with a
-// butterfly inside the group (a fixed order), so that image pairs spanning
-// many warp runs are not summed by one thread; the group's first lane then
-// applies the chain rule.
-constexpr int kSegLanes = 8;
-
+// scale, and apply the chain rule (step::segment_pair, shared with the fused
+// k_ea_finish); kSegLanes lanes per image pair.
 __global__ void k_ea_segments(SegArgs a) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = gid / kSegLanes;
-  const int sub = gid % kSegLanes;
+  const int n = gid / step::kSegLanes;
+  const int sub = gid % step::kSegLanes;
   pdl_trigger();
-  const bool valid = n < a.P;
-  int r0 = 0, cnt = 0, ci = 0, cj = 0;
-  if (valid) {
-    r0 = a.seg_rec[2 * n];
-    cnt = a.seg_rec[2 * n + 1];
-    ci = a.pi[n];
-    cj = a.pj[n];
-  }
+  const step::SegStatic st = step::seg_static(a, n);   // static tables: before the wait
   pdl_wait();               // records come from k_ea_direct
-  // the cameras' parameters are needed by the chain rule after the sum:
-  // loaded now, with the records, rather than after the butterfly
-  const bool chain = valid && sub == 0 && a.seg_grad != nullptr && cnt > 0;
-  float qi[9], qj[9];
-  if (chain) {
-    load_plain(a.params + 9 * ci, qi, 9);
-    load_plain(a.params + 9 * cj, qj, 9);
-  }
-  float G[10];
-  for (int k = 0; k < 10; ++k) G[k] = 0.f;
-  if (valid && !a.dlde_in) {
-    for (int r = r0 + sub; r < r0 + cnt; r += kSegLanes) {
-      const float4 v0 = a.rec[3 * r], v1 = a.rec[3 * r + 1], v2 = a.rec[3 * r + 2];
-      G[0] += v0.x; G[1] += v0.y; G[2] += v0.z; G[3] += v0.w;
-      G[4] += v1.x; G[5] += v1.y; G[6] += v1.z; G[7] += v1.w;
-      G[8] += v2.x; G[9] += v2.y;
-    }
-  }
-#pragma unroll
-  for (int d = kSegLanes / 2; d > 0; d >>= 1)
-#pragma unroll
-    for (int k = 0; k < 10; ++k) G[k] += __shfl_xor_sync(0xffffffffu, G[k], d);
-  if (!valid || sub != 0) return;
-  const float ps = a.pair_scale ? a.pair_scale[n] : 1.f;
-  if (a.dlde_in) {
-    for (int k = 0; k < 9; ++k) G[k] = a.dlde_in[9 * (size_t)n + k];
-  } else {
-    const float gs = a.g_scale * ps;
-    for (int k = 0; k < 9; ++k) G[k] *= gs;
-  }
-  if (a.seg_loss) a.seg_loss[n] = G[9] * (a.l_scale * ps);
-  if (a.dlde_out)
-    for (int k = 0; k < 9; ++k) a.dlde_out[9 * (size_t)n + k] = G[k];
-  if (!a.seg_grad) return;
-  float* out = a.seg_grad + (size_t)kSegGradEa * n;
-  if (cnt == 0) {   // an image pair without keypoint pairs (its geometry may be degenerate)
-    for (int k = 0; k < kSegGradEa; ++k) out[k] = 0.f;
-    return;
-  }
-  if (a.grad_loss) {
-    const float gl = a.grad_loss[a.pair_scene ? a.pair_scene[n] : 0];
-    for (int k = 0; k < 9; ++k) G[k] *= gl;
-  }
-  PairGeo g;
-  pair_geometry(qi, qj, g);
-  float o[kSegGradEa];
-  pair_backward(g, G, o);
-  if ((reinterpret_cast<uintptr_t>(out) & 15u) == 0) {   // library buffers: 96-B rows, 16-B aligned
-    float4* o4 = reinterpret_cast<float4*>(out);
-#pragma unroll
-    for (int k = 0; k < kSegGradEa / 4; ++k) o4[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
-  } else {
-    for (int k = 0; k < kSegGradEa; ++k) out[k] = o[k];
-  }
+  step::segment_pair(a, n, sub, st);
 }
 
 }  // namespace
@@ -615,7 +549,7 @@ SegArgs seg_args(const fm_problem* pr, const float* params) {
 }
 
 void launch_ea_segments(const SegArgs& a, cudaStream_t s) {
-  const long long threads = (long long)a.P * kSegLanes;
+  const long long threads = (long long)a.P * step::kSegLanes;
   launch_pdl(k_ea_segments, dim3((unsigned)((threads + 127) / 128)), dim3(128), 0, s, a);
 }
 

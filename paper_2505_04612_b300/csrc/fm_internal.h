@@ -62,7 +62,7 @@ enum KernelId : int {
   kKCalibrate = 0, kKSegOffsets, kKRunTables, kKEaTables, kKEaDirect, kKEaSegments,
   kKRotPairs, kKTrnTargets, kKTrnPairs, kKCamUpdate, kKLossSum, kKEaReweight, kKWBuild,
   kKEaCompact, kKMartIter, kKRelTrans, kKMerge, kKTriangulate, kKEaDirectLoss, kKEaDirectCoef, kKMlpTables, kKMlpInfer,
-  kKRelpose, kKFocalVote, kKDistErrors, kKDistReduce, kKCount
+  kKRelpose, kKFocalVote, kKDistErrors, kKDistReduce, kKEaFinish, kKCount
 };
 extern const char* const kKernelNames[kKCount];
 
@@ -224,6 +224,7 @@ struct fm_problem {
   float* h_loss = nullptr;          // pinned [max(m,1)*S]
   int* h_err = nullptr;             // pinned copy of d_err
   int* d_err = nullptr;             // device error bits
+  int* cam_cnt = nullptr;           // [N+1] arrival counters of k_ea_finish (cameras, then CTAs)
 };
 
 namespace fm {
@@ -438,6 +439,19 @@ struct CamUpdate {
   int S;
 };
 void launch_cam_update(int stage, const CamUpdate& u, cudaStream_t s);
+// the epipolar step's per-image-pair and per-camera passes in one launch
+// (fm_cam.cu): s as for k_ea_segments (seg_grad required), u as for k_cam of
+// the epipolar stage with one run; cam_cnt [N] and blk_cnt [1] are zero
+// before the launch and zero again after it; cta_loss: the CTA that finishes
+// last sums seg_loss into u.loss_out (one scene)
+struct FinishArgs {
+  SegArgs s;
+  CamUpdate u;
+  int* cam_cnt;
+  int* blk_cnt;
+  bool cta_loss;
+};
+void launch_ea_finish(const FinishArgs& f, cudaStream_t s);
 // out[r*S + s] = fixed-order sum of x[r*P + sc_pair_off[s] .. sc_pair_off[s+1]);
 // sc_pair_off null: one range [0, P) (S = 1)
 void launch_sum_fixed(const float* x, int P, int runs, const int* sc_pair_off, int S, float* out,
