@@ -144,7 +144,8 @@ fm_status check_err_bits(fm_problem* pr) {
   if (bits == 0) return FM_OK;
   FM_CUDA(pr, cudaMemsetAsync(pr->d_err, 0, sizeof(int), pr->stream));
   // a launch cut short must not leave arrival counters behind
-  if (pr->cam_cnt) FM_CUDA(pr, cudaMemsetAsync(pr->cam_cnt, 0, sizeof(int) * ((size_t)pr->N + 1), pr->stream));
+  if (pr->cam_cnt)
+    FM_CUDA(pr, cudaMemsetAsync(pr->cam_cnt, 0, sizeof(int) * fm::kCamCntStride * (size_t)pr->N, pr->stream));
   std::string msg;
   if (bits & fm::kErrKpRange) msg += "kp_img_pair outside [0, n_img_pairs); ";
   if (bits & fm::kErrKpOrder) msg += "kp_img_pair is not non-decreasing; ";
@@ -412,8 +413,8 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   FM_ALLOC(pr, pr->cam_seg, 2 * (size_t)P);
   FM_ALLOC(pr, pr->seg_off, P + 1);
   FM_ALLOC(pr, pr->d_err, 1);
-  FM_ALLOC(pr, pr->cam_cnt, (size_t)N + 1);
-  FM_CUDA(pr, cudaMemsetAsync(pr->cam_cnt, 0, sizeof(int) * ((size_t)N + 1), s));
+  FM_ALLOC(pr, pr->cam_cnt, (size_t)fm::kCamCntStride * N);
+  FM_CUDA(pr, cudaMemsetAsync(pr->cam_cnt, 0, sizeof(int) * fm::kCamCntStride * (size_t)N, s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->pair_i, hi.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->pair_j, hj.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->focal, hf.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s));
@@ -635,8 +636,7 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
     }
     FM_LAUNCHED(pr);
     if (adam || grad_dev) {
-      // the per-image-pair and per-camera passes in one launch; the loss of a
-      // single scene is summed by its last CTA, that of several scenes below
+      // the per-image-pair and per-camera passes in one launch
       fm::FinishArgs f;
       f.s = fm::seg_args(pr, params);
       f.s.g_scale = (pr->ea_loss == FM_EA_L1) ? 1.f : 2.f;
@@ -657,25 +657,18 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
       u.N = N;
       u.P = P;
       u.runs = 1;
-      u.seg_loss = pr->seg_loss;
-      u.sc_pair_off = pr->sc_pair_off;
-      u.S = pr->S;
       f.cam_cnt = pr->cam_cnt;
-      f.blk_cnt = pr->cam_cnt + N;
-      float* first = loss_a ? loss_a : loss_b;
-      f.cta_loss = first != nullptr && pr->S == 1;
-      u.loss_out = f.cta_loss ? first : nullptr;
       {
         Timed t(pr, fm::kKEaFinish);
         fm::launch_ea_finish(f, s);
       }
       FM_LAUNCHED(pr);
-      for (float* dst : {loss_a, loss_b}) {
-        if (!dst || (f.cta_loss && dst == first)) continue;
+      if (loss_a || loss_b) {
         Timed t(pr, fm::kKLossSum);
-        fm::launch_sum_fixed(pr->seg_loss, P, 1, pr->sc_pair_off, pr->S, dst, s);
-        FM_LAUNCHED(pr);
+        fm::launch_sum_fixed(pr->seg_loss, P, 1, pr->sc_pair_off, pr->S, loss_a ? loss_a : loss_b, s,
+                             loss_a ? loss_b : nullptr);
       }
+      FM_LAUNCHED(pr);
       return FM_OK;
     }
     {
@@ -702,18 +695,7 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
     }
     FM_LAUNCHED(pr);
   }
-  // the loss of every run: the first destination is reduced by an extra CTA
-  // of the per-camera kernel, any other by its own launch
-  float* fused = loss_a ? loss_a : loss_b;
-  float* other = (loss_a && loss_b) ? loss_b : nullptr;
-  const bool cam = adam || grad_dev;
-  for (float* dst : {cam ? other : fused, cam ? nullptr : other}) {
-    if (!dst) continue;
-    Timed t(pr, fm::kKLossSum);
-    fm::launch_sum_fixed(pr->seg_loss, P, runs, pr->sc_pair_off, pr->S, dst, s);
-  }
-  FM_LAUNCHED(pr);
-  if (cam) {
+  if (adam || grad_dev) {
     fm::CamUpdate u;
     u.cam_seg_off = pr->cam_seg_off;
     u.cam_seg = pr->cam_seg;
@@ -731,16 +713,19 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
     u.N = N;
     u.P = P;
     u.runs = runs;
-    u.seg_loss = pr->seg_loss;
-    u.loss_out = fused;
-    u.sc_pair_off = pr->sc_pair_off;
-    u.S = pr->S;
     {
       Timed t(pr, fm::kKCamUpdate);
       fm::launch_cam_update((int)st, u, s);
     }
     FM_LAUNCHED(pr);
   }
+  // the loss of every run (one launch for both destinations)
+  if (loss_a || loss_b) {
+    Timed t(pr, fm::kKLossSum);
+    fm::launch_sum_fixed(pr->seg_loss, P, runs, pr->sc_pair_off, pr->S, loss_a ? loss_a : loss_b, s,
+                         loss_a ? loss_b : nullptr);
+  }
+  FM_LAUNCHED(pr);
   return FM_OK;
 }
 
@@ -1720,8 +1705,6 @@ fm_status fm_ea_focal_backward(fm_problem* pr, const float* params, const float*
   u.N = pr->N;
   u.P = pr->P;
   u.runs = 1;
-  u.seg_loss = pr->seg_loss;
-  u.loss_out = nullptr;
   {
     Timed t(pr, fm::kKCamUpdate);
     fm::launch_cam_update(FM_STAGE_EPIPOLAR, u, s);
@@ -1780,8 +1763,6 @@ fm_status fm_ea_backward(fm_problem* pr, const float* params, int32_t save, cons
   u.N = pr->N;
   u.P = pr->P;
   u.runs = 1;
-  u.seg_loss = pr->seg_loss;
-  u.loss_out = nullptr;
   {
     Timed t(pr, fm::kKCamUpdate);
     fm::launch_cam_update(FM_STAGE_EPIPOLAR, u, s);

@@ -5,8 +5,9 @@
 //
 // k_cam          one warp per camera (four per CTA): lanes stride over the
 //                incident image pairs, a butterfly combines them, lanes < 9
-//                apply the adjoint and Adam; extra CTAs sum the loss of each
-//                scene (fixed order).
+//                apply the adjoint and Adam.
+// k_sum_fixed    the loss of each (scene, run): one CTA of 1024 threads, a
+//                fixed order that depends on the number of terms only.
 // k_ea_finish    the epipolar step's per-image-pair pass (k_ea_segments) and
 //                per-camera pass (k_cam) in one launch (Sec. 3.4 fuses an
 //                iteration's passes into one kernel): eight lanes per image
@@ -15,9 +16,12 @@
 //                camera's count to its number of image pairs updates that
 //                camera right away, with the same sums in the same order as
 //                k_cam.  Camera updates thus overlap the image-pair pass
-//                instead of waiting for all of it; the CTA that finishes last
-//                sums the loss.  Counters are reset by whoever completes
-//                them, ready for the next launch.
+//                instead of waiting for all of it.  Each camera's counter
+//                has a 128-byte line of its own: counters sharing a line
+//                serialise each other's atomics (measured: 31k returning
+//                atomics on 300 adjacent counters cost ~9 us, spread over
+//                lines almost nothing).  Counters are reset by whoever
+//                completes them, ready for the next launch.
 #include "fm_step.cuh"
 
 namespace fm {
@@ -32,17 +36,7 @@ __global__ void __launch_bounds__(kThreads) k_cam(CamUpdate u) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int run = blockIdx.y;
-  const int cam_blocks = (u.N + kThreads / 32 - 1) / (kThreads / 32);
   pdl_trigger();
-  if ((int)blockIdx.x >= cam_blocks) {
-    // the S extra CTAs of the grid reduce the loss of each scene
-    __shared__ float part[kThreads];
-    const int sc = blockIdx.x - cam_blocks;
-    const int b = u.sc_pair_off[sc], e = u.sc_pair_off[sc + 1];
-    pdl_wait();
-    step::loss_sum_cta<false>(u.seg_loss + (size_t)run * u.P + b, e - b, u.loss_out + (size_t)run * u.S + sc, part);
-    return;
-  }
   const int c = blockIdx.x * (kThreads / 32) + warp;
   if (c >= u.N) return;
   const int b = u.cam_seg_off[c], e = u.cam_seg_off[c + 1];   // static: before the wait
@@ -53,14 +47,21 @@ __global__ void __launch_bounds__(kThreads) k_cam(CamUpdate u) {
 }
 
 // fixed-order sum of each scene's range of values per run (one CTA per
-// (scene, run)); the same order as the loss CTAs of k_cam
-__global__ void __launch_bounds__(kThreads) k_sum_fixed(const float* __restrict__ x, int P,
-                                                        const int* __restrict__ sc_pair_off,
-                                                        float* __restrict__ out) {
-  __shared__ float part[kThreads];
+// (scene, run)) into out (and out2 when not null)
+constexpr int kSumThreads = 1024;
+__global__ void __launch_bounds__(kSumThreads) k_sum_fixed(const float* __restrict__ x, int P,
+                                                           const int* __restrict__ sc_pair_off,
+                                                           float* __restrict__ out, float* __restrict__ out2) {
+  __shared__ float part[kSumThreads];
   const int sc = blockIdx.x, run = blockIdx.y;
+  pdl_trigger();
   const int b = sc_pair_off ? sc_pair_off[sc] : 0, e = sc_pair_off ? sc_pair_off[sc + 1] : P;
-  step::loss_sum_cta<false>(x + (size_t)run * P + b, e - b, out + (size_t)run * gridDim.x + sc, part);
+  pdl_wait();
+  const float v = step::loss_sum_cta<kSumThreads, false>(x + (size_t)run * P + b, e - b, part);
+  if (threadIdx.x == 0) {
+    out[(size_t)run * gridDim.x + sc] = v;
+    if (out2) out2[(size_t)run * gridDim.x + sc] = v;
+  }
 }
 
 template <bool ADAM>
@@ -68,8 +69,6 @@ __global__ void __launch_bounds__(kThreads) k_ea_finish(FinishArgs f) {
   constexpr int kGroups = kThreads / step::kSegLanes;   // image pairs per CTA
   __shared__ int list[2 * kGroups];                      // cameras completed by this CTA
   __shared__ int n_list;
-  __shared__ int last;
-  __shared__ float part[kThreads];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int gid = blockIdx.x * kThreads + t;
   const int n = gid / step::kSegLanes, sub = gid % step::kSegLanes;
@@ -93,21 +92,16 @@ __global__ void __launch_bounds__(kThreads) k_ea_finish(FinishArgs f) {
   __syncthreads();
   if (step::segment_pair(f.s, n, sub, st)) {
     __threadfence();        // this image pair's block before its counts
-    if (atomicAdd(f.cam_cnt + st.ci, 1) == deg_i - 1) {
+    if (atomicAdd(f.cam_cnt + kCamCntStride * st.ci, 1) == deg_i - 1) {
       __threadfence();
       list[atomicAdd(&n_list, 1)] = st.ci;
     }
-    if (atomicAdd(f.cam_cnt + st.cj, 1) == deg_j - 1) {
+    if (atomicAdd(f.cam_cnt + kCamCntStride * st.cj, 1) == deg_j - 1) {
       __threadfence();
       list[atomicAdd(&n_list, 1)] = st.cj;
     }
   }
-  if (f.cta_loss) __threadfence();   // this CTA's loss terms before the CTA count
   __syncthreads();
-  if (f.cta_loss && t == 0) {
-    last = atomicAdd(f.blk_cnt, 1) == (int)gridDim.x - 1;
-    __threadfence();
-  }
   const int nl = n_list;
   for (int q = warp; q < nl; q += kThreads / 32) {
     const int c = list[q];
@@ -115,22 +109,14 @@ __global__ void __launch_bounds__(kThreads) k_ea_finish(FinishArgs f) {
     float acc[12];
     step::cam_gather<12, true>(u.seg_grad, u.cam_seg, u.cam_seg_off[c], u.cam_seg_off[c + 1], lane, acc);
     step::cam_apply<2, ADAM>(u, c, 0, acc, lane);
-    if (lane == 0) f.cam_cnt[c] = 0;   // ready for the next launch
-  }
-  if (f.cta_loss) {
-    __syncthreads();
-    if (last) {
-      __threadfence();
-      step::loss_sum_cta<true>(u.seg_loss, f.s.P, u.loss_out, part);
-      if (t == 0) *f.blk_cnt = 0;
-    }
+    if (lane == 0) f.cam_cnt[kCamCntStride * c] = 0;   // ready for the next launch
   }
 }
 
 template <int STAGE>
 void launch_stage(const CamUpdate& u, cudaStream_t s) {
   const int cam_blocks = (u.N + kThreads / 32 - 1) / (kThreads / 32);
-  dim3 grid(cam_blocks + (u.loss_out ? u.S : 0), u.runs);
+  dim3 grid(cam_blocks, u.runs);
   if (u.params_out) launch_pdl(k_cam<STAGE, true>, grid, dim3(kThreads), 0, s, u);
   else launch_pdl(k_cam<STAGE, false>, grid, dim3(kThreads), 0, s, u);
 }
@@ -144,8 +130,8 @@ void launch_cam_update(int stage, const CamUpdate& u, cudaStream_t s) {
 }
 
 void launch_sum_fixed(const float* x, int P, int runs, const int* sc_pair_off, int S, float* out,
-                      cudaStream_t s) {
-  k_sum_fixed<<<dim3(S, runs), kThreads, 0, s>>>(x, P, sc_pair_off, out);
+                      cudaStream_t s, float* out2) {
+  launch_pdl(k_sum_fixed, dim3(S, runs), dim3(kSumThreads), 0, s, x, P, sc_pair_off, out, out2);
 }
 
 void launch_ea_finish(const FinishArgs& f, cudaStream_t s) {

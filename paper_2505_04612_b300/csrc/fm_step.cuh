@@ -197,7 +197,7 @@ __device__ __forceinline__ void cam_apply(const CamUpdate& u, int c, int run, co
   u.params_out[off + lane] = pv - u.lr * (m / bc1) / (sqrtf(v / bc2) + u.eps);
 }
 
-// Fixed-order sum of n per-image-pair loss terms by one CTA of kThreads.
+// Fixed-order sum of n per-image-pair loss terms by one CTA of T threads.
 // The order depends on n only -- not on where x starts, so that a scene's
 // loss inside a batch adds exactly as the same scene alone: chunks of four
 // consecutive terms, chunk c summed as (x0 + x1) + (x2 + x3) into thread
@@ -211,9 +211,8 @@ __device__ __forceinline__ float4 load_chunk(const float* x, int c, bool aligned
   return make_float4(ld1<CG>(x + 4 * c), ld1<CG>(x + 4 * c + 1), ld1<CG>(x + 4 * c + 2), ld1<CG>(x + 4 * c + 3));
 }
 
-template <bool CG>
-__device__ __forceinline__ void loss_sum_cta(const float* x, int n, float* out, float* part) {
-  constexpr int T = kThreads;
+template <int T, bool CG>
+__device__ __forceinline__ float loss_sum_cta(const float* x, int n, float* part) {
   const int t = threadIdx.x;
   const bool aligned = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
   const int n4 = n >> 2;
@@ -243,8 +242,9 @@ __device__ __forceinline__ void loss_sum_cta(const float* x, int n, float* out, 
     if (t < d) part[t] += part[t + d];
     __syncthreads();
   }
-  if (t == 0) *out = part[0];
+  const float r = part[0];
   __syncthreads();
+  return r;
 }
 
 }  // namespace step
