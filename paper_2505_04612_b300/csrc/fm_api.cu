@@ -22,7 +22,7 @@ const char* const kKernelNames[kKCount] = {
     "k_ea_segments", "k_rot_pairs", "k_trn_targets", "k_trn_pairs", "k_cam", "k_sum_fixed",
     "k_ea_reweight", "k_w_build", "k_ea_compact", "k_mart_iter", "k_reltrans", "k_merge",
     "k_triangulate", "k_ea_direct_loss", "k_ea_direct_coef", "k_mlp_pair_tables", "k_mlp_infer",
-    "k_relpose", "k_focal_vote", "k_dist_errors", "k_dist_reduce", "k_ea_finish"};
+    "k_relpose", "k_focal_vote", "k_dist_errors", "k_dist_reduce"};
 }
 
 namespace {
@@ -143,9 +143,6 @@ fm_status check_err_bits(fm_problem* pr) {
   FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
   if (bits == 0) return FM_OK;
   FM_CUDA(pr, cudaMemsetAsync(pr->d_err, 0, sizeof(int), pr->stream));
-  // a launch cut short must not leave arrival counters behind
-  if (pr->cam_cnt)
-    FM_CUDA(pr, cudaMemsetAsync(pr->cam_cnt, 0, sizeof(int) * fm::kCamCntStride * (size_t)pr->N, pr->stream));
   std::string msg;
   if (bits & fm::kErrKpRange) msg += "kp_img_pair outside [0, n_img_pairs); ";
   if (bits & fm::kErrKpOrder) msg += "kp_img_pair is not non-decreasing; ";
@@ -177,7 +174,7 @@ void release(fm_problem* pr) {
   dfree(pr->rot_adam.m); dfree(pr->rot_adam.v); dfree(pr->rot_adam.t);
   dfree(pr->trn_target); dfree(pr->trn_params);
   dfree(pr->trn_adam.m); dfree(pr->trn_adam.v); dfree(pr->trn_adam.t);
-  dfree(pr->scratch_params); dfree(pr->scratch_grad); dfree(pr->d_loss); dfree(pr->d_err); dfree(pr->cam_cnt);
+  dfree(pr->scratch_params); dfree(pr->scratch_grad); dfree(pr->d_loss); dfree(pr->d_err);
   dfree(pr->loss_hist);
   dfree(pr->W);
   dfree(pr->d_kept);
@@ -413,8 +410,6 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   FM_ALLOC(pr, pr->cam_seg, 2 * (size_t)P);
   FM_ALLOC(pr, pr->seg_off, P + 1);
   FM_ALLOC(pr, pr->d_err, 1);
-  FM_ALLOC(pr, pr->cam_cnt, (size_t)fm::kCamCntStride * N);
-  FM_CUDA(pr, cudaMemsetAsync(pr->cam_cnt, 0, sizeof(int) * fm::kCamCntStride * (size_t)N, s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->pair_i, hi.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->pair_j, hj.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->focal, hf.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s));
@@ -635,42 +630,6 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
       fm::launch_ea_direct(pr, pr->ea_w, pr->ea_loss, s);
     }
     FM_LAUNCHED(pr);
-    if (adam || grad_dev) {
-      // the per-image-pair and per-camera passes in one launch
-      fm::FinishArgs f;
-      f.s = fm::seg_args(pr, params);
-      f.s.g_scale = (pr->ea_loss == FM_EA_L1) ? 1.f : 2.f;
-      fm::CamUpdate& u = f.u;
-      u.cam_seg_off = pr->cam_seg_off;
-      u.cam_seg = pr->cam_seg;
-      u.seg_grad = pr->seg_grad;
-      u.params = params;
-      u.params_out = adam ? const_cast<float*>(params) : nullptr;
-      u.grad_out = grad_dev;
-      u.m = state ? state->m : nullptr;
-      u.v = state ? state->v : nullptr;
-      u.step = step;
-      u.lr = adam ? adam->lr : 0.f;
-      u.b1 = adam ? adam->beta1 : 0.f;
-      u.b2 = adam ? adam->beta2 : 0.f;
-      u.eps = adam ? adam->eps : 0.f;
-      u.N = N;
-      u.P = P;
-      u.runs = 1;
-      f.cam_cnt = pr->cam_cnt;
-      {
-        Timed t(pr, fm::kKEaFinish);
-        fm::launch_ea_finish(f, s);
-      }
-      FM_LAUNCHED(pr);
-      if (loss_a || loss_b) {
-        Timed t(pr, fm::kKLossSum);
-        fm::launch_sum_fixed(pr->seg_loss, P, 1, pr->sc_pair_off, pr->S, loss_a ? loss_a : loss_b, s,
-                             loss_a ? loss_b : nullptr);
-      }
-      FM_LAUNCHED(pr);
-      return FM_OK;
-    }
     {
       Timed t(pr, fm::kKEaSegments);
       fm::launch_ea_segments(pr, params, pr->ea_loss, s);
@@ -713,14 +672,19 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
     u.N = N;
     u.P = P;
     u.runs = runs;
+    // the loss is summed by extra CTAs of the same launch
+    u.seg_loss = pr->seg_loss;
+    u.loss_out = loss_a ? loss_a : loss_b;
+    u.loss_out2 = loss_a ? loss_b : nullptr;
+    u.sc_pair_off = pr->sc_pair_off;
+    u.S = pr->S;
     {
       Timed t(pr, fm::kKCamUpdate);
       fm::launch_cam_update((int)st, u, s);
     }
     FM_LAUNCHED(pr);
-  }
-  // the loss of every run (one launch for both destinations)
-  if (loss_a || loss_b) {
+  } else if (loss_a || loss_b) {
+    // the loss alone (one launch for both destinations)
     Timed t(pr, fm::kKLossSum);
     fm::launch_sum_fixed(pr->seg_loss, P, runs, pr->sc_pair_off, pr->S, loss_a ? loss_a : loss_b, s,
                          loss_a ? loss_b : nullptr);

@@ -422,8 +422,8 @@ __global__ void __launch_bounds__(WARPS * 32, kEaMinCtas) k_ea_direct(DirectArgs
 }
 
 // per image pair: sum its records -- or take dL/dE_n from a saved copy --
-// scale, and apply the chain rule (step::segment_pair, shared with the fused
-// k_ea_finish); kSegLanes lanes per image pair.
+// scale, and apply the chain rule (step::segment_pair); kSegLanes lanes per
+// image pair.
 __global__ void k_ea_segments(SegArgs a) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = gid / step::kSegLanes;

@@ -62,7 +62,7 @@ enum KernelId : int {
   kKCalibrate = 0, kKSegOffsets, kKRunTables, kKEaTables, kKEaDirect, kKEaSegments,
   kKRotPairs, kKTrnTargets, kKTrnPairs, kKCamUpdate, kKLossSum, kKEaReweight, kKWBuild,
   kKEaCompact, kKMartIter, kKRelTrans, kKMerge, kKTriangulate, kKEaDirectLoss, kKEaDirectCoef, kKMlpTables, kKMlpInfer,
-  kKRelpose, kKFocalVote, kKDistErrors, kKDistReduce, kKEaFinish, kKCount
+  kKRelpose, kKFocalVote, kKDistErrors, kKDistReduce, kKCount
 };
 extern const char* const kKernelNames[kKCount];
 
@@ -224,7 +224,6 @@ struct fm_problem {
   float* h_loss = nullptr;          // pinned [max(m,1)*S]
   int* h_err = nullptr;             // pinned copy of d_err
   int* d_err = nullptr;             // device error bits
-  int* cam_cnt = nullptr;           // [kCamCntStride N] arrival counters of k_ea_finish
 };
 
 namespace fm {
@@ -433,20 +432,13 @@ struct CamUpdate {
   const int* step;
   float lr, b1, b2, eps;
   int N, P, runs;
+  const float* seg_loss;   // [runs][P] per-image-pair loss terms
+  float* loss_out;         // [runs][S] fixed-order sums of seg_loss per scene, or null
+  float* loss_out2;        // a second destination of the same sums, or null
+  const int* sc_pair_off;  // [S+1] image-pair range of each scene
+  int S;
 };
 void launch_cam_update(int stage, const CamUpdate& u, cudaStream_t s);
-// the epipolar step's per-image-pair and per-camera passes in one launch
-// (fm_cam.cu): s as for k_ea_segments (seg_grad required), u as for k_cam of
-// the epipolar stage with one run; cam_cnt [kCamCntStride N] (camera c's
-// arrival counter at kCamCntStride c) is zero before the launch and zero
-// again after it
-constexpr int kCamCntStride = 32;   // one 128-byte line per counter
-struct FinishArgs {
-  SegArgs s;
-  CamUpdate u;
-  int* cam_cnt;
-};
-void launch_ea_finish(const FinishArgs& f, cudaStream_t s);
 // out[r*S + s] = fixed-order sum of x[r*P + sc_pair_off[s] .. sc_pair_off[s+1]);
 // sc_pair_off null: one range [0, P) (S = 1); out2 (optional) gets the same
 void launch_sum_fixed(const float* x, int P, int runs, const int* sc_pair_off, int S, float* out,

@@ -1,7 +1,5 @@
-// Device functions shared by the per-image-pair pass (k_ea_segments), the
-// per-camera pass (k_cam) and their fusion (k_ea_finish): each computes the
-// same values in the same order wherever it runs, so that every path of the
-// library gives bit-identical results.
+// Device functions of the per-image-pair pass (k_ea_segments) and the
+// per-camera pass (k_cam).
 #pragma once
 #include "fm_device.cuh"
 #include "fm_internal.h"
@@ -102,66 +100,67 @@ template <> struct Layout<0> { static constexpr int PART = 9, PDIM = 6; static c
 template <> struct Layout<1> { static constexpr int PART = 3, PDIM = 3; static constexpr bool ROT = false; };
 template <> struct Layout<2> { static constexpr int PART = 12, PDIM = 9; static constexpr bool ROT = true; };
 
-// loads of values another CTA of the same kernel wrote (after an arrival
-// counter said they are complete): L2, never a possibly stale L1 line
-template <bool CG>
-__device__ __forceinline__ float4 ld4(const float* p) {
-  return CG ? __ldcg(reinterpret_cast<const float4*>(p)) : *reinterpret_cast<const float4*>(p);
-}
-template <bool CG>
-__device__ __forceinline__ float ld1(const float* p) {
-  return CG ? __ldcg(p) : *p;
+// The first kCamPre incident image pairs of a lane (camera CSR entries b +
+// lane + 32 k, -1 past e): static, loaded before the dependency wait.
+constexpr int kCamPre = 4;
+__device__ __forceinline__ void cam_prefetch(const int* __restrict__ cam_seg, int b, int e, int lane, int* v) {
+#pragma unroll
+  for (int u = 0; u < kCamPre; ++u) v[u] = (b + lane + 32 * u < e) ? __ldg(cam_seg + b + lane + 32 * u) : -1;
 }
 
-// Sum of camera c's parts over its incident image pairs [b, e) of the camera
+template <int PART>
+__device__ __forceinline__ void cam_add(const float* sg, int entry, float* acc) {
+  const unsigned w = (unsigned)entry;
+  const int n = (int)(w & 0x7fffffffu);
+  const int role = (int)(w >> 31);
+  const float* g = sg + ((size_t)n * 2 + role) * PART;
+  if (PART % 4 == 0) {   // 48-B parts of a cudaMalloc'd buffer: 16-B aligned
+#pragma unroll
+    for (int q = 0; q < PART / 4; ++q) {
+      const float4 t = *reinterpret_cast<const float4*>(g + 4 * q);
+      acc[4 * q] += t.x;
+      acc[4 * q + 1] += t.y;
+      acc[4 * q + 2] += t.z;
+      acc[4 * q + 3] += t.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < PART; ++k) acc[k] += g[k];
+  }
+}
+
+// Sum of a camera's parts over its incident image pairs [b, e) of the camera
 // CSR, by one warp: lane l adds the entries b + l, b + l + 32, ... in that
-// order, then a butterfly gives every lane the total.  Four entries are
-// loaded per step (same order of additions as one at a time).
-template <int PART, bool CG>
+// order (the first kCamPre of them prefetched in pre), then a butterfly gives
+// every lane the total.
+template <int PART>
 __device__ __forceinline__ void cam_gather(const float* sg, const int* __restrict__ cam_seg, int b, int e, int lane,
-                                           float* acc) {
+                                           const int* pre, float* acc) {
 #pragma unroll
   for (int k = 0; k < PART; ++k) acc[k] = 0.f;
-  for (int i0 = b + lane; i0 < e; i0 += 128) {
-    int v[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = (i0 + 32 * u < e) ? __ldg(cam_seg + i0 + 32 * u) : -1;
+  for (int u = 0; u < kCamPre; ++u)
+    if (pre[u] != -1) cam_add<PART>(sg, pre[u], acc);
+  for (int i0 = b + lane + 32 * kCamPre; i0 < e; i0 += 32 * kCamPre) {
+    int v[kCamPre];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (v[u] == -1) continue;
-      const unsigned w = (unsigned)v[u];
-      const int n = (int)(w & 0x7fffffffu);
-      const int role = (int)(w >> 31);
-      const float* g = sg + ((size_t)n * 2 + role) * PART;
-      if (PART % 4 == 0) {   // 48-B parts of a cudaMalloc'd buffer: 16-B aligned
+    for (int u = 0; u < kCamPre; ++u) v[u] = (i0 + 32 * u < e) ? __ldg(cam_seg + i0 + 32 * u) : -1;
 #pragma unroll
-        for (int q = 0; q < PART / 4; ++q) {
-          const float4 t = ld4<CG>(g + 4 * q);
-          acc[4 * q] += t.x;
-          acc[4 * q + 1] += t.y;
-          acc[4 * q + 2] += t.z;
-          acc[4 * q + 3] += t.w;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < PART; ++k) acc[k] += ld1<CG>(g + k);
-      }
-    }
+    for (int u = 0; u < kCamPre; ++u)
+      if (v[u] != -1) cam_add<PART>(sg, v[u], acc);
   }
 #pragma unroll
   for (int k = 0; k < PART; ++k) acc[k] = warp_sum(acc[k]);
 }
 
-// Camera c of run `run` from its summed parts: the 6D adjoint for rotations,
-// then either the gradient or Adam (bias-corrected; the step counter was
-// advanced by this step's first kernel), by lanes < PDIM.
+// Camera c of run `run` from its summed parts, its parameters p and (Adam)
+// its moments m, v of lane's entry (all loaded beforehand): the 6D adjoint
+// for rotations, then either the gradient or Adam (bias-corrected; the step
+// counter was advanced by this step's first kernel), by lanes < PDIM.
 template <int STAGE, bool ADAM>
-__device__ __forceinline__ void cam_apply(const CamUpdate& u, int c, int run, const float* acc, int lane) {
+__device__ __forceinline__ void cam_apply(const CamUpdate& u, size_t off, const float* p, float m, float v,
+                                          const float* acc, int lane) {
   using L = Layout<STAGE>;
-  const size_t off = ((size_t)run * u.N + c) * L::PDIM;
-  float p[L::PDIM];
-#pragma unroll
-  for (int k = 0; k < L::PDIM; ++k) p[k] = u.params[off + k];
   float g[L::PDIM];
   if (L::ROT) {
     Rot6 s;
@@ -189,7 +188,6 @@ __device__ __forceinline__ void cam_apply(const CamUpdate& u, int c, int run, co
   const float t = (float)*u.step;
   const float bc1 = 1.f - powf(u.b1, t);
   const float bc2 = 1.f - powf(u.b2, t);
-  float m = u.m[off + lane], v = u.v[off + lane];
   m = u.b1 * m + (1.f - u.b1) * gv;
   v = u.b2 * v + (1.f - u.b2) * gv * gv;
   u.m[off + lane] = m;
@@ -205,13 +203,12 @@ __device__ __forceinline__ void cam_apply(const CamUpdate& u, int c, int run, co
 // the accumulators in a fixed order and a tree over the threads.  A chunk is
 // one float4 load when x is 16-B aligned, four scalar loads otherwise; eight
 // chunks per thread are in flight.  Every thread of the CTA must call it.
-template <bool CG>
 __device__ __forceinline__ float4 load_chunk(const float* x, int c, bool aligned) {
-  if (aligned) return ld4<CG>(x + 4 * c);
-  return make_float4(ld1<CG>(x + 4 * c), ld1<CG>(x + 4 * c + 1), ld1<CG>(x + 4 * c + 2), ld1<CG>(x + 4 * c + 3));
+  if (aligned) return reinterpret_cast<const float4*>(x)[c];
+  return make_float4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
 }
 
-template <int T, bool CG>
+template <int T>
 __device__ __forceinline__ float loss_sum_cta(const float* x, int n, float* part) {
   const int t = threadIdx.x;
   const bool aligned = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
@@ -223,19 +220,19 @@ __device__ __forceinline__ float loss_sum_cta(const float* x, int n, float* part
   for (; k + 7 * T < n4; k += 8 * T) {
     float4 v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = load_chunk<CG>(x, k + u * T, aligned);
+    for (int u = 0; u < 8; ++u) v[u] = load_chunk(x, k + u * T, aligned);
 #pragma unroll
     for (int u = 0; u < 8; ++u) acc[u] += (v[u].x + v[u].y) + (v[u].z + v[u].w);
   }
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     if (k < n4) {
-      const float4 v = load_chunk<CG>(x, k, aligned);
+      const float4 v = load_chunk(x, k, aligned);
       acc[u] += (v.x + v.y) + (v.z + v.w);
     }
     k += T;
   }
-  if (t < n - 4 * n4) acc[0] += ld1<CG>(x + 4 * n4 + t);
+  if (t < n - 4 * n4) acc[0] += x[4 * n4 + t];
   part[t] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
   __syncthreads();
   for (int d = T / 2; d > 0; d >>= 1) {

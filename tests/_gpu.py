@@ -79,3 +79,24 @@ def l1_grad_matches(sc, params, g_gpu, tol, weights=None, inv_z=None, xs=None, m
                          sign_override=dict(zip(amb.tolist(), signs)) if len(amb) else None)
         best = min(best, rel_err(g_gpu.reshape(g.shape), g))
     return best < tol, best, len(amb)
+
+
+def l1_grad_within_bound(sc, params, g_gpu, tol, weights=None, inv_z=None, xs=None):
+    """For scenes with too many sign-ambiguous pairs to enumerate: the GPU
+    gradient is within tol (relative) of the oracle's plus, for each pair with
+    |r| < GAMMA, the largest change its sign can make, 2 w_m inv_z
+    |d r_m / d params|.  Returns (ok, err, bound, n_ambiguous)."""
+    x1, x2 = xs if xs is not None else oracle_xs(sc)
+    p = f32(params).reshape(-1, 9)
+    _, go = ea_oracle(sc, params, "l1", weights, inv_z, xs)
+    amb = ambiguous_pairs(sc, params, xs)
+    iz = 1.0 / max(sc.n_kp, 1) if inv_z is None else inv_z
+    geo = ep.pair_geometry(p, sc.pair_i, sc.pair_j)
+    bound = 0.0
+    for m in amb:
+        wm = 1.0 if weights is None else float(weights[m])
+        Gm = np.zeros((sc.n_pairs, 3, 3))
+        Gm[sc.kp_img_pair[m]] = wm * iz * np.outer(x2[m], x1[m])
+        bound += 2.0 * np.linalg.norm(ep.backward_E(Gm, geo, p.shape[0], sc.pair_i, sc.pair_j, p))
+    err = np.linalg.norm(np.asarray(g_gpu, np.float64).reshape(go.shape) - go)
+    return err <= tol * np.linalg.norm(go) + bound, err, bound, len(amb)

@@ -157,6 +157,6 @@ def test_loss_trace_and_timing():
     assert len(hist) == 16 and hist[-1] == last
     assert hist[-1] < hist[0]
     assert kt["k_ea_direct"][0] == 20 and kt["k_ea_direct"][1] > 0
-    # the epipolar step's per-image-pair and per-camera passes are one launch
-    assert kt["k_ea_finish"][0] == 20 and "k_cam" not in kt and "k_ea_segments" not in kt
-    assert kt["k_sum_fixed"][0] == 20
+    assert kt["k_ea_segments"][0] == 20 and kt["k_cam"][0] == 20
+    # the loss trace and the returned loss are summed inside the camera pass
+    assert "k_sum_fixed" not in kt

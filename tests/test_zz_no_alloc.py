@@ -109,7 +109,9 @@ def _check_against_problem_and_oracle(pr, inp, p, loss, weighted):
         assert G.rel_err(g, go) < 1e-4
     else:
         res = G.l1_grad_matches(sc, p, g, 1e-4, w, float(inp.inv_z), xs)
-        assert res is not None and res[0], res
+        if res is None:   # too many sign-ambiguous pairs to enumerate: bound them
+            res = G.l1_grad_within_bound(sc, p, g, 1e-4, w, float(inp.inv_z), xs)
+        assert res[0], res
 
 
 def _with_empty_image_pairs(sc, every=7):
