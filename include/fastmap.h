@@ -109,9 +109,10 @@ typedef struct {
   int64_t n_kp_pairs;          /* Z >= 0, Z < 2^31 - 2^20 */
   const int32_t* pair_cam_i;   /* [P] first image of each image pair */
   const int32_t* pair_cam_j;   /* [P] second image; != pair_cam_i */
-  const int32_t* kp_img_pair;  /* [Z] image pair of each keypoint pair,
-                                  NON-DECREASING (keypoint pairs grouped by
-                                  image pair, image pairs in index order) */
+  const int32_t* kp_img_pair;  /* [Z] image pair of each keypoint pair, in
+                                  [0, P), in any order: the library keeps the
+                                  keypoint pairs sorted by (image pair,
+                                  track), see fm_kp_order */
   const float* kp1_px;         /* [Z*2] (u, v) of the keypoint in image i_n */
   const float* kp2_px;         /* [Z*2] (u, v) of the keypoint in image j_n */
   const int32_t* kp_track;     /* [Z] track id (>= 0), or NULL; needed by
@@ -156,13 +157,27 @@ typedef struct {
 
 /* Creates a problem on the current CUDA device.  Validates the description
  * (sizes, camera indices of the image pairs, intrinsics on the host side;
- * ordering and range of kp_img_pair and finiteness of the keypoints on the
- * device) and returns FM_ERR_INVALID_ARG / FM_ERR_NAN on bad input.
- * Calibrates the keypoints (Sec. 3.3, x~ = K^-1 [u, v, 1]^T) and builds the
- * image-pair and camera tables (Sec. 3.4: one fused evaluation per step).
- * Synchronises the stream.  On success *out owns device memory until
- * fm_problem_destroy. */
+ * range of kp_img_pair and finiteness of the keypoints on the device) and
+ * returns FM_ERR_INVALID_ARG / FM_ERR_NAN on bad input.  Copies the keypoint
+ * pairs in (image pair, track) order -- the set of keypoint pairs Q_n of
+ * image pair n (Sec. 3.3) contiguous, the data marshalled on the GPU (Sec. 4,
+ * setup): when the caller's order is not that one already, they are sorted
+ * on the device (stable: pairs with equal keys keep the caller's relative
+ * order; without kp_track the key is the image pair alone) and the
+ * permutation is kept.  Calibrates the keypoints (Sec. 3.3, x~ = K^-1 [u, v,
+ * 1]^T) and builds the image-pair and camera tables.  Synchronises the
+ * stream.  On success *out owns device memory until fm_problem_destroy. */
 fm_status fm_problem_create(const fm_problem_desc* desc, fm_problem** out);
+
+/* The library's order of the keypoint pairs: perm_out [Z] (host or device
+ * as flagged) receives, for each internal position k, the index in the
+ * caller's arrays of the keypoint pair held there (the identity when the
+ * caller's order was kept).  fm_ea_set_weights and fm_ea_get_weights take
+ * and give per-pair values in the caller's order; the per-pair device
+ * outputs of fm_mlp_eval / fm_mlp_eval_relative and the coefficients saved
+ * by fm_ea_forward are in the internal order (value k belongs to caller
+ * pair perm_out[k]).  Synchronises. */
+fm_status fm_kp_order(const fm_problem* problem, int32_t* perm_out, int32_t out_on_device);
 
 /* Releases every resource of the problem (NULL is a no-op).  Synchronises. */
 void fm_problem_destroy(fm_problem* problem);

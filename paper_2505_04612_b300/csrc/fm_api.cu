@@ -165,7 +165,7 @@ void release(fm_problem* pr) {
   cudaStreamSynchronize(pr->stream);
   dfree(pr->pair_i); dfree(pr->pair_j); dfree(pr->seg_off);
   dfree(pr->cam_seg_off); dfree(pr->cam_seg);
-  dfree(pr->kp); dfree(pr->kp_track); dfree(pr->focal); dfree(pr->cx); dfree(pr->cy);
+  dfree(pr->kp); dfree(pr->kp_perm); dfree(pr->kp_track); dfree(pr->focal); dfree(pr->cx); dfree(pr->cy);
   dfree(pr->lane_desc); dfree(pr->wrun_info); dfree(pr->seg_rec); dfree(pr->rec);
   dfree(pr->seg_tab); dfree(pr->seg_grad); dfree(pr->seg_loss);
   dfree(pr->ea_w); dfree(pr->ea_params);
@@ -457,6 +457,67 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
     FM_CUDA(pr, cudaMemcpyAsync(pr->kp_track, d->kp_track, sizeof(int) * Z,
                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   }
+  // the keypoint pairs in (image pair, track) order: the caller's order when
+  // it is one already, else sorted here (stable: equal keys keep the input
+  // order) with the permutation kept for per-pair inputs and outputs
+  float* srt1 = nullptr;
+  float* srt2 = nullptr;
+  int* srtp = nullptr;
+  auto free_sorted = [&]() {
+    if (srt1) { cudaFree(srt1); pr->device_bytes -= (int64_t)sizeof(float) * 2 * Z; srt1 = nullptr; }
+    if (srt2) { cudaFree(srt2); pr->device_bytes -= (int64_t)sizeof(float) * 2 * Z; srt2 = nullptr; }
+    if (srtp) { cudaFree(srtp); pr->device_bytes -= (int64_t)sizeof(int) * Z; srtp = nullptr; }
+  };
+  if (Z > 0) {
+    int flags[2] = {0, 0};
+    FM_CUDA(pr, cudaMemsetAsync(pr->d_err, 0, sizeof(int), s));
+    int* d_flags = nullptr;
+    FM_ALLOC(pr, d_flags, 2);
+    FM_CUDA(pr, cudaMemsetAsync(d_flags, 0, sizeof(int) * 2, s));
+    fm::launch_kp_order_check(kpp, pr->kp_track, Z, P, d_flags, s);
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(flags, d_flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    cudaFree(d_flags);
+    pr->device_bytes -= (int64_t)sizeof(int) * 2;
+    if (ce != cudaSuccess) return fail(pr, FM_ERR_CUDA, std::string("keypoint order: ") + cudaGetErrorString(ce));
+    if (flags[0] & 1) {
+      if (tmp1) { cudaFree(tmp1); cudaFree(tmp2); cudaFree(tmpp); }
+      return fail(pr, FM_ERR_INVALID_ARG, "kp_img_pair outside [0, n_img_pairs)");
+    }
+    if (flags[0] & 2) {
+      fm_status a = FM_OK;
+      if ((a = dalloc(pr, &pr->kp_perm, (size_t)Z)) != FM_OK || (a = dalloc(pr, &srt1, 2 * (size_t)Z)) != FM_OK ||
+          (a = dalloc(pr, &srt2, 2 * (size_t)Z)) != FM_OK || (a = dalloc(pr, &srtp, (size_t)Z)) != FM_OK) {
+        free_sorted();
+        return a;
+      }
+      int* srtt = nullptr;
+      if (pr->kp_track && (a = dalloc(pr, &srtt, (size_t)Z)) != FM_OK) {
+        free_sorted();
+        return a;
+      }
+      ce = fm::sort_kp_pairs(kpp, pr->kp_track, Z, P, flags[1], pr->kp_perm, s);
+      if (ce == cudaSuccess) {
+        fm::launch_kp_gather(pr->kp_perm, Z, kp1, kp2, kpp, pr->kp_track, srt1, srt2, srtp, srtt, s);
+        ce = cudaGetLastError();
+      }
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+      if (ce != cudaSuccess) {
+        free_sorted();
+        if (srtt) cudaFree(srtt);
+        return fail(pr, FM_ERR_CUDA, std::string("sorting the keypoint pairs: ") + cudaGetErrorString(ce));
+      }
+      kp1 = srt1;
+      kp2 = srt2;
+      kpp = srtp;
+      if (srtt) {   // the sorted tracks replace the caller's order
+        dfree(pr->kp_track);
+        pr->device_bytes -= (int64_t)sizeof(int) * Z;
+        pr->kp_track = srtt;
+      }
+    }
+  }
   {
     Timed t(pr, fm::kKCalibrate);
     fm::launch_calibrate(kp1, kp2, kpp, pr->pair_i, pr->pair_j, pr->focal, pr->cx, pr->cy, Z, P,
@@ -482,6 +543,7 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   if (tmp1) { cudaFree(tmp1); pr->device_bytes -= (int64_t)sizeof(float) * 2 * Z; }
   if (tmp2) { cudaFree(tmp2); pr->device_bytes -= (int64_t)sizeof(float) * 2 * Z; }
   if (tmpp) { cudaFree(tmpp); pr->device_bytes -= (int64_t)sizeof(int) * Z; }
+  free_sorted();
   if (st != FM_OK) return st;
 
   {
@@ -1363,9 +1425,28 @@ fm_status fm_ea_set_weights(fm_problem* pr, const float* w, int32_t on_device, f
   }
   if (!(std::isfinite(inv_z) && inv_z >= 0.f)) return fail(pr, FM_ERR_INVALID_ARG, "inv_z must be finite and >= 0");
   if (!pr->ea_w) FM_ALLOC(pr, pr->ea_w, (size_t)pr->Z);
-  if (pr->Z > 0) {
+  if (pr->Z > 0 && pr->kp_perm) {
+    // the caller's order -> the internal (sorted) order
+    const float* src = w;
+    float* tmp = nullptr;
+    if (!on_device) {
+      FM_ALLOC(pr, tmp, (size_t)pr->Z);
+      FM_CUDA(pr, cudaMemcpyAsync(tmp, w, sizeof(float) * pr->Z, cudaMemcpyHostToDevice, pr->stream));
+      src = tmp;
+    }
+    fm::launch_permute(src, pr->kp_perm, pr->Z, true, pr->ea_w, pr->stream);
+    cudaError_t ce = cudaGetLastError();
+    if (tmp) {
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(pr->stream);
+      cudaFree(tmp);
+      pr->device_bytes -= (int64_t)sizeof(float) * pr->Z;
+    }
+    if (ce != cudaSuccess) return fail(pr, FM_ERR_CUDA, std::string("weights: ") + cudaGetErrorString(ce));
+  } else if (pr->Z > 0) {
     FM_CUDA(pr, cudaMemcpyAsync(pr->ea_w, w, sizeof(float) * pr->Z,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, pr->stream));
+  }
+  if (pr->Z > 0) {
     fm::launch_check_finite(pr->ea_w, pr->Z, pr->d_err, fm::kErrParamNonFinite, pr->stream);
     FM_LAUNCHED(pr);
     fm_status e = check_err_bits(pr);
@@ -1423,11 +1504,47 @@ fm_status fm_ea_reweight(fm_problem* pr, float tau, float delta, int32_t irls, i
 fm_status fm_ea_get_weights(fm_problem* pr, float* out, int32_t on_device, float* inv_z) {
   if (!pr || !out) return FM_ERR_INVALID_ARG;
   if (!pr->ea_w) return fail(pr, FM_ERR_STATE, "no per-pair weights are set");
-  if (pr->Z > 0)
+  if (pr->Z > 0 && pr->kp_perm) {
+    // the internal (sorted) order -> the caller's order
+    float* dst = on_device ? out : nullptr;
+    if (!on_device) FM_ALLOC(pr, dst, (size_t)pr->Z);
+    fm::launch_permute(pr->ea_w, pr->kp_perm, pr->Z, false, dst, pr->stream);
+    cudaError_t ce = cudaGetLastError();
+    if (!on_device) {
+      if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(out, dst, sizeof(float) * pr->Z, cudaMemcpyDeviceToHost, pr->stream);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(pr->stream);
+      cudaFree(dst);
+      pr->device_bytes -= (int64_t)sizeof(float) * pr->Z;
+    }
+    if (ce != cudaSuccess) return fail(pr, FM_ERR_CUDA, std::string("weights: ") + cudaGetErrorString(ce));
+  } else if (pr->Z > 0) {
     FM_CUDA(pr, cudaMemcpyAsync(out, pr->ea_w, sizeof(float) * pr->Z,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, pr->stream));
+  }
   FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
   if (inv_z) *inv_z = pr->ea_inv_z;
+  return FM_OK;
+}
+
+fm_status fm_kp_order(const fm_problem* cpr, int32_t* perm_out, int32_t on_device) {
+  fm_problem* pr = const_cast<fm_problem*>(cpr);
+  if (!pr || !perm_out) return FM_ERR_INVALID_ARG;
+  if (pr->Z == 0) return FM_OK;
+  if (pr->kp_perm) {
+    FM_CUDA(pr, cudaMemcpyAsync(perm_out, pr->kp_perm, sizeof(int32_t) * pr->Z,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, pr->stream));
+    FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
+    return FM_OK;
+  }
+  if (!on_device) {
+    for (int64_t k = 0; k < pr->Z; ++k) perm_out[k] = (int32_t)k;
+    return FM_OK;
+  }
+  std::vector<int32_t> iota((size_t)pr->Z);
+  for (int64_t k = 0; k < pr->Z; ++k) iota[(size_t)k] = (int32_t)k;
+  FM_CUDA(pr, cudaMemcpyAsync(perm_out, iota.data(), sizeof(int32_t) * pr->Z, cudaMemcpyHostToDevice, pr->stream));
+  FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
   return FM_OK;
 }
 

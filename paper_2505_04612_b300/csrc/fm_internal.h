@@ -118,6 +118,7 @@ struct fm_problem {
 
   // keypoints
   float4* kp = nullptr;          // [Z] calibrated (x1, y1, x2, y2)
+  uint32_t* kp_perm = nullptr;   // [Z] input index of each internal position, or null (input order kept)
   int* kp_track = nullptr;       // [Z] or null
   int* kp_seg = nullptr;         // [Z] image pair of each keypoint pair (kept with tracks)
   int n_tracks = 0;
@@ -269,6 +270,19 @@ void launch_calibrate(const float* kp1, const float* kp2, const int* kp_pair, co
                       int64_t Z, int P, float4* out, int* err, cudaStream_t s);
 void launch_seg_offsets(const int* kp_pair, int64_t Z, int P, int* seg_off, int* err,
                         cudaStream_t s);
+// order of the caller's keypoint pairs (see k_kp_order_check): flags[0] bits
+// 1 index out of range, 2 not in (image pair, track) order, 4 negative
+// track; flags[1] the largest track (flags zeroed by the caller)
+void launch_kp_order_check(const int* kpp, const int* track, int64_t Z, int P, int* flags, cudaStream_t s);
+// perm [Z]: the input index of each position of the (image pair, track,
+// input index) order (fm_tracks.cu; scratch from the library's pool)
+cudaError_t sort_kp_pairs(const int* kp_img_pair, const int* kp_track, int64_t Z, int P, int max_track,
+                          uint32_t* perm, cudaStream_t s);
+// the inputs (kp1, kp2 [Z][2], kpp, track [Z] or null) in the order perm
+void launch_kp_gather(const uint32_t* perm, int64_t Z, const float* kp1, const float* kp2, const int* kpp,
+                      const int* track, float* o1, float* o2, int* okpp, int* otrack, cudaStream_t s);
+// per-pair values: to_internal out[k] = in[perm[k]], else out[perm[k]] = in[k]
+void launch_permute(const float* in, const uint32_t* perm, int64_t Z, bool to_internal, float* out, cudaStream_t s);
 // lane tables of the direct kernel: G [P+1] = exclusive scan of the lanes per
 // image pair, *T = lanes in use; then the lane descriptors and run headers of
 // n_runs warp runs (n_runs >= ceil(T / 32); runs past the lanes in use are

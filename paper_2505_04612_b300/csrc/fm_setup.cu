@@ -31,8 +31,60 @@ __global__ void k_calibrate(const float* __restrict__ kp1, const float* __restri
   }
 }
 
+// The order of the caller's keypoint pairs: flags[0] gets 1 when an image
+// pair index lies outside [0, P), 2 when the pairs are not in (image pair,
+// track) order (track compared only when given), 4 when a track is negative;
+// flags[1] the largest track.
+__global__ void k_kp_order_check(const int* __restrict__ kpp, const int* __restrict__ track, int64_t Z, int P,
+                                 int* flags) {
+  int bits = 0, tmax = 0;
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < Z; m += (int64_t)gridDim.x * blockDim.x) {
+    const int n = kpp[m];
+    if (n < 0 || n >= P) bits |= 1;
+    const int t = track ? track[m] : 0;
+    if (t < 0) bits |= 4;
+    tmax = max(tmax, t);
+    if (m > 0) {
+      const int n0 = kpp[m - 1];
+      if (n < n0 || (track && n == n0 && t < track[m - 1])) bits |= 2;
+    }
+  }
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  tmax = __reduce_max_sync(0xffffffffu, tmax);
+  if ((threadIdx.x & 31) == 0) {
+    if (bits) atomicOr(flags, bits);
+    if (track) atomicMax(flags + 1, tmax);
+  }
+}
+
+// the caller's keypoint-pair inputs in the order perm (position k takes input
+// perm[k]); track may be null
+__global__ void k_kp_gather(const uint32_t* __restrict__ perm, int64_t Z, const float2* __restrict__ kp1,
+                            const float2* __restrict__ kp2, const int* __restrict__ kpp, const int* __restrict__ track,
+                            float2* __restrict__ o1, float2* __restrict__ o2, int* __restrict__ okpp,
+                            int* __restrict__ otrack) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Z; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t m = perm[k];
+    o1[k] = kp1[m];
+    o2[k] = kp2[m];
+    okpp[k] = kpp[m];
+    if (track) otrack[k] = track[m];
+  }
+}
+
+// per-pair values between the caller's order and the internal one:
+// to_internal: out[k] = in[perm[k]]; else out[perm[k]] = in[k]
+__global__ void k_permute(const float* __restrict__ in, const uint32_t* __restrict__ perm, int64_t Z, int to_internal,
+                          float* __restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Z; k += (int64_t)gridDim.x * blockDim.x) {
+    if (to_internal) out[k] = in[perm[k]];
+    else out[perm[k]] = in[k];
+  }
+}
+
 // seg_off[n] = index of the first keypoint pair of image pair n (CSR); the
-// keypoint pairs must be grouped by image pair in index order.
+// keypoint pairs are grouped by image pair in index order (sorted at
+// creation when the caller's are not).
 __global__ void k_seg_offsets(const int* __restrict__ kp_pair, int64_t Z, int P,
                               int* __restrict__ seg_off, int* err) {
   for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < Z;
@@ -222,6 +274,25 @@ void launch_seg_offsets(const int* kp_pair, int64_t Z, int P, int* seg_off, int*
     return;
   }
   k_seg_offsets<<<grid_for(Z, 256), 256, 0, s>>>(kp_pair, Z, P, seg_off, err);
+}
+
+void launch_kp_order_check(const int* kpp, const int* track, int64_t Z, int P, int* flags, cudaStream_t s) {
+  if (Z == 0) return;
+  k_kp_order_check<<<grid_for(Z, 256), 256, 0, s>>>(kpp, track, Z, P, flags);
+}
+
+void launch_kp_gather(const uint32_t* perm, int64_t Z, const float* kp1, const float* kp2, const int* kpp,
+                      const int* track, float* o1, float* o2, int* okpp, int* otrack, cudaStream_t s) {
+  if (Z == 0) return;
+  k_kp_gather<<<grid_for(Z, 256), 256, 0, s>>>(perm, Z, reinterpret_cast<const float2*>(kp1),
+                                               reinterpret_cast<const float2*>(kp2), kpp, track,
+                                               reinterpret_cast<float2*>(o1), reinterpret_cast<float2*>(o2), okpp,
+                                               otrack);
+}
+
+void launch_permute(const float* in, const uint32_t* perm, int64_t Z, bool to_internal, float* out, cudaStream_t s) {
+  if (Z == 0) return;
+  k_permute<<<grid_for(Z, 256), 256, 0, s>>>(in, perm, Z, to_internal ? 1 : 0, out);
 }
 
 void launch_lane_scan(const int* seg_off, int P, int U, int* G, int* T, cudaStream_t s, int64_t Z, int* err) {

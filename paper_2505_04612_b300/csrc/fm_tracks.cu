@@ -577,7 +577,37 @@ int bits_for(uint64_t max_value) {
   return b;
 }
 
+// out[k] = (uint32) key[idx[k]] (idx null: key[k])
+__global__ void k_gather_key(const int* __restrict__ key, const uint32_t* __restrict__ idx, int64_t n,
+                             uint32_t* __restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = (uint32_t)key[idx ? idx[k] : k];
+}
+
 }  // namespace
+
+// The order of the keypoint pairs by (image pair, track, input index): two
+// stable radix sorts of the indices, by track, then by image pair.  perm [Z]
+// receives, for each position of that order, the input index.
+cudaError_t sort_kp_pairs(const int* kp_img_pair, const int* kp_track, int64_t Z, int P, int max_track,
+                          uint32_t* perm, cudaStream_t s) {
+  if (Z <= 0) return cudaSuccess;
+  Buffers B(s);
+  uint32_t* key = B.get<uint32_t>((size_t)Z);
+  uint32_t* val = B.get<uint32_t>((size_t)Z);
+  if (B.ce != cudaSuccess) return B.ce;
+  k_iota<<<grid_for(Z), 256, 0, s>>>(val, Z);
+  if (kp_track) {
+    k_gather_key<<<grid_for(Z), 256, 0, s>>>(kp_track, nullptr, Z, key);
+    radix_sort(B, key, val, Z, bits_for((uint64_t)(max_track > 0 ? max_track : 0)), s);
+  }
+  k_gather_key<<<grid_for(Z), 256, 0, s>>>(kp_img_pair, val, Z, key);
+  radix_sort(B, key, val, Z, bits_for((uint64_t)(P > 1 ? P - 1 : 0)), s);
+  if (B.ce != cudaSuccess) return B.ce;
+  cudaMemcpyAsync(perm, val, sizeof(uint32_t) * (size_t)Z, cudaMemcpyDeviceToDevice, s);
+  return cudaGetLastError();
+}
+
 }  // namespace fm
 
 namespace {

@@ -128,6 +128,7 @@ _SIGNATURES = {
     "fm_problem_destroy": (None, [ctypes.c_void_p]),
     "fm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "fm_problem_info_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fm_problem_info)]),
+    "fm_kp_order": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "fm_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int32]),
     "fm_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int32]),
     "fm_set_rel_poses": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
@@ -359,6 +360,14 @@ def fm_ea_reweight(handle, tau, delta, irls=True):
     _check(lib().fm_ea_reweight(handle, ctypes.c_float(tau), ctypes.c_float(delta), int(bool(irls)),
                                 ctypes.byref(kept)), handle)
     return kept.value
+
+
+def fm_kp_order(handle, out):
+    """The library's keypoint-pair order: out[k] = caller index of internal
+    position k (a numpy int32 array or a CUDA int32 tensor of Z entries)."""
+    p, dev, keep = _ptr(out)
+    _check(lib().fm_kp_order(handle, p, int(dev)), handle)
+    return out
 
 
 def fm_ea_get_weights(handle, out):
@@ -662,6 +671,11 @@ class Problem:
     def reweight(self, tau, delta, irls=True):
         """IRLS weights + filtering at the current epipolar parameters; returns #kept."""
         return fm_ea_reweight(self.handle, tau, delta, irls)
+
+    def kp_order(self):
+        """numpy int32 [Z]: the caller index of each internal keypoint-pair
+        position (fm_kp_order)."""
+        return fm_kp_order(self.handle, np.empty(self.n_kp, np.int32))
 
     def get_weights(self):
         import torch
