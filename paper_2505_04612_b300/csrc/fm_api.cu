@@ -734,19 +734,14 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
     u.N = N;
     u.P = P;
     u.runs = runs;
-    // the loss is summed by extra CTAs of the same launch
-    u.seg_loss = pr->seg_loss;
-    u.loss_out = loss_a ? loss_a : loss_b;
-    u.loss_out2 = loss_a ? loss_b : nullptr;
-    u.sc_pair_off = pr->sc_pair_off;
-    u.S = pr->S;
     {
       Timed t(pr, fm::kKCamUpdate);
       fm::launch_cam_update((int)st, u, s);
     }
     FM_LAUNCHED(pr);
-  } else if (loss_a || loss_b) {
-    // the loss alone (one launch for both destinations)
+  }
+  if (loss_a || loss_b) {
+    // the loss of every run (one launch for both destinations)
     Timed t(pr, fm::kKLossSum);
     fm::launch_sum_fixed(pr->seg_loss, P, runs, pr->sc_pair_off, pr->S, loss_a ? loss_a : loss_b, s,
                          loss_a ? loss_b : nullptr);

@@ -3,17 +3,18 @@
 // per-image-pair gradients; rotations then go through the adjoint of the 6D
 // map (Sec. 3.3), and Adam updates the camera's parameters in place.
 //
-// k_cam          one warp per camera (32 per CTA of 1024 threads): its
-//                first incident image pairs are read from the CSR before the
-//                dependency wait, its parameters and Adam moments right
+// k_cam          one warp per camera (four per CTA of 128 threads: small
+//                CTAs find room beside the preceding kernel's, so that under
+//                programmatic dependent launch they are resident before it
+//                ends; 1024-thread CTAs were measured 9 us slower per step):
+//                its first incident image pairs are read from the CSR before
+//                the dependency wait, its parameters and Adam moments right
 //                after it, together with the gathered parts; lanes stride
 //                over the incident image pairs, a butterfly combines them,
-//                lanes < 9 apply the adjoint and Adam.  When a loss is
-//                wanted, S x runs more CTAs of the same launch sum the loss
-//                of each (scene, run) meanwhile, in k_sum_fixed's order.
-// k_sum_fixed    the loss of each (scene, run) alone: one CTA of 1024
-//                threads, a fixed order that depends on the number of terms
-//                only.
+//                lanes < 9 apply the adjoint and Adam.
+// k_sum_fixed    the loss of each (scene, run): one CTA of 1024 threads (one
+//                round of loads), a fixed order that depends on the number of
+//                terms only.
 #include "fm_step.cuh"
 
 namespace fm {
@@ -21,7 +22,7 @@ namespace {
 
 using step::Layout;
 
-constexpr int kCamThreads = 1024;   // one warp per camera; also the loss CTAs' size
+constexpr int kCamThreads = 128;    // one warp per camera
 constexpr int kSumThreads = 1024;
 
 template <int STAGE, bool ADAM>
@@ -30,21 +31,7 @@ __global__ void __launch_bounds__(kCamThreads) k_cam(CamUpdate u) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int run = blockIdx.y;
-  const int cam_blocks = (u.N + kCamThreads / 32 - 1) / (kCamThreads / 32);
   pdl_trigger();
-  if ((int)blockIdx.x >= cam_blocks) {
-    // the S extra CTAs of each run sum the loss of each scene
-    __shared__ float part[kCamThreads];
-    const int sc = blockIdx.x - cam_blocks;
-    const int b = u.sc_pair_off[sc], e = u.sc_pair_off[sc + 1];
-    pdl_wait();
-    const float v = step::loss_sum_cta<kCamThreads>(u.seg_loss + (size_t)run * u.P + b, e - b, part);
-    if (threadIdx.x == 0) {
-      u.loss_out[(size_t)run * u.S + sc] = v;
-      if (u.loss_out2) u.loss_out2[(size_t)run * u.S + sc] = v;
-    }
-    return;
-  }
   const int c = blockIdx.x * (kCamThreads / 32) + warp;
   if (c >= u.N) return;
   // static: before the wait
@@ -68,8 +55,7 @@ __global__ void __launch_bounds__(kCamThreads) k_cam(CamUpdate u) {
 }
 
 // fixed-order sum of each scene's range of values per run (one CTA per
-// (scene, run)) into out (and out2 when not null); the order of k_cam's loss
-// CTAs
+// (scene, run)) into out (and out2 when not null)
 __global__ void __launch_bounds__(kSumThreads) k_sum_fixed(const float* __restrict__ x, int P,
                                                            const int* __restrict__ sc_pair_off,
                                                            float* __restrict__ out, float* __restrict__ out2) {
@@ -88,7 +74,7 @@ __global__ void __launch_bounds__(kSumThreads) k_sum_fixed(const float* __restri
 template <int STAGE>
 void launch_stage(const CamUpdate& u, cudaStream_t s) {
   const int cam_blocks = (u.N + kCamThreads / 32 - 1) / (kCamThreads / 32);
-  dim3 grid(cam_blocks + (u.loss_out ? u.S : 0), u.runs);
+  dim3 grid(cam_blocks, u.runs);
   if (u.params_out) launch_pdl(k_cam<STAGE, true>, grid, dim3(kCamThreads), 0, s, u);
   else launch_pdl(k_cam<STAGE, false>, grid, dim3(kCamThreads), 0, s, u);
 }

@@ -446,11 +446,6 @@ struct CamUpdate {
   const int* step;
   float lr, b1, b2, eps;
   int N, P, runs;
-  const float* seg_loss;   // [runs][P] per-image-pair loss terms
-  float* loss_out;         // [runs][S] fixed-order sums of seg_loss per scene, or null
-  float* loss_out2;        // a second destination of the same sums, or null
-  const int* sc_pair_off;  // [S+1] image-pair range of each scene
-  int S;
 };
 void launch_cam_update(int stage, const CamUpdate& u, cudaStream_t s);
 // out[r*S + s] = fixed-order sum of x[r*P + sc_pair_off[s] .. sc_pair_off[s+1]);

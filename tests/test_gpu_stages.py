@@ -158,5 +158,5 @@ def test_loss_trace_and_timing():
     assert hist[-1] < hist[0]
     assert kt["k_ea_direct"][0] == 20 and kt["k_ea_direct"][1] > 0
     assert kt["k_ea_segments"][0] == 20 and kt["k_cam"][0] == 20
-    # the loss trace and the returned loss are summed inside the camera pass
-    assert "k_sum_fixed" not in kt
+    # the loss trace and the returned loss come from one reduction per step
+    assert kt["k_sum_fixed"][0] == 20
