@@ -825,8 +825,9 @@ fm_status fm_loss_history(fm_problem* problem, float* out, int32_t capacity, int
  * per keypoint pair; a problem that does not fit in 16 MiB (118 P + 0.4 Z
  * beyond 16.7M) is rejected with FM_ERR_INVALID_ARG before any GPU work.
  * Every call on a device shares the one array and leaves its contents
- * behind; each call clears the one word that must start at zero (its error
- * word) and writes every other entry before reading it.  Calls whose GPU work
+ * behind; each call clears the words that must start at zero (its error
+ * word and an arrival counter) and writes every other entry before reading
+ * it.  Calls whose GPU work
  * overlaps (two streams, or two host threads) race on the array: serialise
  * them.  The first call on each device looks up the array's device address
  * and sets the kernel's shared-memory limit on that device; make that first

@@ -22,7 +22,7 @@ const char* const kKernelNames[kKCount] = {
     "k_ea_segments", "k_rot_pairs", "k_trn_targets", "k_trn_pairs", "k_cam", "k_sum_fixed",
     "k_ea_reweight", "k_w_build", "k_ea_compact", "k_mart_iter", "k_reltrans", "k_merge",
     "k_triangulate", "k_ea_direct_loss", "k_ea_direct_coef", "k_mlp_pair_tables", "k_mlp_infer",
-    "k_relpose", "k_focal_vote", "k_dist_errors", "k_dist_reduce"};
+    "k_relpose", "k_focal_vote", "k_dist_errors", "k_dist_reduce", "k_cam_ea"};
 }
 
 namespace {
@@ -143,6 +143,9 @@ fm_status check_err_bits(fm_problem* pr) {
   FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
   if (bits == 0) return FM_OK;
   FM_CUDA(pr, cudaMemsetAsync(pr->d_err, 0, sizeof(int), pr->stream));
+  // a launch cut short must not leave arrival counters behind
+  if (pr->loss_cnt)
+    FM_CUDA(pr, cudaMemsetAsync(pr->loss_cnt, 0, sizeof(int) * 64 * pr->S * fm::kLossCntStride, pr->stream));
   std::string msg;
   if (bits & fm::kErrKpRange) msg += "kp_img_pair outside [0, n_img_pairs); ";
   if (bits & fm::kErrKpOrder) msg += "kp_img_pair is not non-decreasing; ";
@@ -174,7 +177,7 @@ void release(fm_problem* pr) {
   dfree(pr->rot_adam.m); dfree(pr->rot_adam.v); dfree(pr->rot_adam.t);
   dfree(pr->trn_target); dfree(pr->trn_params);
   dfree(pr->trn_adam.m); dfree(pr->trn_adam.v); dfree(pr->trn_adam.t);
-  dfree(pr->scratch_params); dfree(pr->scratch_grad); dfree(pr->d_loss); dfree(pr->d_err);
+  dfree(pr->scratch_params); dfree(pr->scratch_grad); dfree(pr->d_loss); dfree(pr->d_err); dfree(pr->sc_slice_off); dfree(pr->loss_part); dfree(pr->loss_cnt);
   dfree(pr->loss_hist);
   dfree(pr->W);
   dfree(pr->d_kept);
@@ -428,6 +431,18 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   FM_ALLOC(pr, pr->mart_coef, 3 * (size_t)S);
   FM_CUDA(pr, cudaMemcpyAsync(pr->sc_cam_off, pr->h_sc_cam_off.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice, s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->sc_pair_off, pr->h_sc_pair_off.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice, s));
+  // loss slices: ceil(P_s / 1024) per scene, sums and arrival counters for up to 64 runs
+  pr->h_sc_slice_off.assign(S + 1, 0);
+  for (int q = 0; q < S; ++q)
+    pr->h_sc_slice_off[q + 1] = pr->h_sc_slice_off[q] +
+                                (pr->h_sc_pair_off[q + 1] - pr->h_sc_pair_off[q] + fm::kLossSlice - 1) / fm::kLossSlice;
+  pr->n_slices = pr->h_sc_slice_off[S];
+  FM_ALLOC(pr, pr->sc_slice_off, S + 1);
+  FM_ALLOC(pr, pr->loss_part, (size_t)64 * pr->n_slices);
+  FM_ALLOC(pr, pr->loss_cnt, (size_t)64 * S * fm::kLossCntStride);
+  FM_CUDA(pr, cudaMemcpyAsync(pr->sc_slice_off, pr->h_sc_slice_off.data(), sizeof(int) * (S + 1),
+                              cudaMemcpyHostToDevice, s));
+  FM_CUDA(pr, cudaMemsetAsync(pr->loss_cnt, 0, sizeof(int) * 64 * S * fm::kLossCntStride, s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->cam_scene, cam_scene.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->pair_scene, pair_scene.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->pair_inv_p, inv_p.data(), sizeof(float) * P, cudaMemcpyHostToDevice, s));
@@ -660,6 +675,44 @@ fm_status rebuild_W(fm_problem* pr, const float* centre) {
   return FM_OK;
 }
 
+// loss slices of the problem writing to out (and out2); out null: no loss
+fm::LossArgs loss_args(const fm_problem* pr, float* out, float* out2) {
+  fm::LossArgs L;
+  L.sc_pair_off = pr->sc_pair_off;
+  L.sc_slice_off = pr->sc_slice_off;
+  L.S = pr->S;
+  L.n_slices = pr->n_slices;
+  L.partial = pr->loss_part;
+  L.cnt = pr->loss_cnt;
+  L.out = out;
+  L.out2 = out ? out2 : nullptr;
+  return L;
+}
+
+fm::CamUpdate cam_update(fm_problem* pr, const float* params, float* grad_dev, const fm_adam_opts* adam,
+                         fm::AdamState* state, int* step, int runs) {
+  fm::CamUpdate u{};
+  u.cam_seg_off = pr->cam_seg_off;
+  u.cam_seg = pr->cam_seg;
+  u.seg_grad = pr->seg_grad;
+  u.params = params;
+  u.params_out = adam ? const_cast<float*>(params) : nullptr;
+  u.grad_out = grad_dev;
+  u.m = state ? state->m : nullptr;
+  u.v = state ? state->v : nullptr;
+  u.step = step;
+  u.lr = adam ? adam->lr : 0.f;
+  u.b1 = adam ? adam->beta1 : 0.f;
+  u.b2 = adam ? adam->beta2 : 0.f;
+  u.eps = adam ? adam->eps : 0.f;
+  u.N = pr->N;
+  u.P = pr->P;
+  u.runs = runs;
+  u.seg_loss = pr->seg_loss;
+  u.loss = loss_args(pr, nullptr, nullptr);
+  return u;
+}
+
 // One evaluation of a stage: per-image-pair pass, then the per-camera pass
 // (Adam when adam != null, else the gradient into grad_dev); the loss of every
 // run is reduced into loss_a and loss_b when they are not null.
@@ -692,6 +745,20 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
       fm::launch_ea_direct(pr, pr->ea_w, pr->ea_loss, s);
     }
     FM_LAUNCHED(pr);
+    if (adam || grad_dev) {
+      // the per-image-pair chain rule, the cameras and the loss in one launch
+      fm::EaCamArgs f;
+      f.s = fm::seg_args(pr, params);
+      f.s.g_scale = (pr->ea_loss == FM_EA_L1) ? 1.f : 2.f;
+      f.u = cam_update(pr, params, grad_dev, adam, state, step, 1);
+      f.u.loss = loss_args(pr, loss_a ? loss_a : loss_b, loss_a ? loss_b : nullptr);
+      {
+        Timed t(pr, fm::kKCamEa);
+        fm::launch_cam_ea(f, s);
+      }
+      FM_LAUNCHED(pr);
+      return FM_OK;
+    }
     {
       Timed t(pr, fm::kKEaSegments);
       fm::launch_ea_segments(pr, params, pr->ea_loss, s);
@@ -716,35 +783,20 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
     }
     FM_LAUNCHED(pr);
   }
+  float* first = loss_a ? loss_a : loss_b;
+  float* second = loss_a ? loss_b : nullptr;
   if (adam || grad_dev) {
-    fm::CamUpdate u;
-    u.cam_seg_off = pr->cam_seg_off;
-    u.cam_seg = pr->cam_seg;
-    u.seg_grad = pr->seg_grad;
-    u.params = params;
-    u.params_out = adam ? const_cast<float*>(params) : nullptr;
-    u.grad_out = grad_dev;
-    u.m = state ? state->m : nullptr;
-    u.v = state ? state->v : nullptr;
-    u.step = step;
-    u.lr = adam ? adam->lr : 0.f;
-    u.b1 = adam ? adam->beta1 : 0.f;
-    u.b2 = adam ? adam->beta2 : 0.f;
-    u.eps = adam ? adam->eps : 0.f;
-    u.N = N;
-    u.P = P;
-    u.runs = runs;
+    // the cameras, and the loss in slices of the same launch
+    fm::CamUpdate u = cam_update(pr, params, grad_dev, adam, state, step, runs);
+    u.loss = loss_args(pr, first, second);
     {
       Timed t(pr, fm::kKCamUpdate);
       fm::launch_cam_update((int)st, u, s);
     }
     FM_LAUNCHED(pr);
-  }
-  if (loss_a || loss_b) {
-    // the loss of every run (one launch for both destinations)
+  } else if (first) {
     Timed t(pr, fm::kKLossSum);
-    fm::launch_sum_fixed(pr->seg_loss, P, runs, pr->sc_pair_off, pr->S, loss_a ? loss_a : loss_b, s,
-                         loss_a ? loss_b : nullptr);
+    fm::launch_sum_fixed(pr->seg_loss, P, runs, loss_args(pr, first, second), s);
   }
   FM_LAUNCHED(pr);
   return FM_OK;
@@ -1709,7 +1761,7 @@ fm_status fm_ea_forward(fm_problem* pr, const float* params, float* loss_dev, in
   FM_LAUNCHED(pr);
   {
     Timed t(pr, fm::kKLossSum);
-    fm::launch_sum_fixed(pr->seg_loss, pr->P, 1, pr->sc_pair_off, pr->S, loss_dev, s);
+    fm::launch_sum_fixed(pr->seg_loss, pr->P, 1, loss_args(pr, loss_dev, nullptr), s);
   }
   FM_LAUNCHED(pr);
   return FM_OK;
@@ -1744,7 +1796,7 @@ fm_status fm_ea_focal_forward(fm_problem* pr, const float* params, const float* 
   }
   {
     Timed t(pr, fm::kKLossSum);
-    fm::launch_sum_fixed(pr->seg_loss, pr->P, 1, pr->sc_pair_off, pr->S, loss_dev, s);
+    fm::launch_sum_fixed(pr->seg_loss, pr->P, 1, loss_args(pr, loss_dev, nullptr), s);
   }
   FM_LAUNCHED(pr);
   return FM_OK;
@@ -1771,16 +1823,7 @@ fm_status fm_ea_focal_backward(fm_problem* pr, const float* params, const float*
     fm::launch_ea_segments(a, s);
   }
   FM_LAUNCHED(pr);
-  fm::CamUpdate u{};
-  u.cam_seg_off = pr->cam_seg_off;
-  u.cam_seg = pr->cam_seg;
-  u.seg_grad = pr->seg_grad;
-  u.params = params;
-  u.params_out = nullptr;
-  u.grad_out = grad;
-  u.N = pr->N;
-  u.P = pr->P;
-  u.runs = 1;
+  fm::CamUpdate u = cam_update(pr, params, grad, nullptr, nullptr, nullptr, 1);
   {
     Timed t(pr, fm::kKCamUpdate);
     fm::launch_cam_update(FM_STAGE_EPIPOLAR, u, s);
@@ -1829,16 +1872,7 @@ fm_status fm_ea_backward(fm_problem* pr, const float* params, int32_t save, cons
     fm::launch_ea_segments(a, s);
   }
   FM_LAUNCHED(pr);
-  fm::CamUpdate u{};
-  u.cam_seg_off = pr->cam_seg_off;
-  u.cam_seg = pr->cam_seg;
-  u.seg_grad = pr->seg_grad;
-  u.params = params;
-  u.params_out = nullptr;
-  u.grad_out = grad;
-  u.N = pr->N;
-  u.P = pr->P;
-  u.runs = 1;
+  fm::CamUpdate u = cam_update(pr, params, grad, nullptr, nullptr, nullptr, 1);
   {
     Timed t(pr, fm::kKCamUpdate);
     fm::launch_cam_update(FM_STAGE_EPIPOLAR, u, s);

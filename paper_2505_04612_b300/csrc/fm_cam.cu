@@ -3,80 +3,152 @@
 // per-image-pair gradients; rotations then go through the adjoint of the 6D
 // map (Sec. 3.3), and Adam updates the camera's parameters in place.
 //
-// k_cam          one warp per camera (four per CTA of 128 threads: small
-//                CTAs find room beside the preceding kernel's, so that under
-//                programmatic dependent launch they are resident before it
-//                ends; 1024-thread CTAs were measured 9 us slower per step):
-//                its first incident image pairs are read from the CSR before
-//                the dependency wait, its parameters and Adam moments right
-//                after it, together with the gathered parts; lanes stride
-//                over the incident image pairs, a butterfly combines them,
-//                lanes < 9 apply the adjoint and Adam.
-// k_sum_fixed    the loss of each (scene, run): one CTA of 1024 threads (one
-//                round of loads), a fixed order that depends on the number of
-//                terms only.
+// k_cam          one CTA per camera: thread t adds the incident image pairs
+//                t, t + 128, ... (the first read from the CSR before the
+//                dependency wait), warps combine by butterflies and in warp
+//                order, warp 0 applies the adjoint and Adam; its parameters
+//                and moments are loaded while the parts are gathered.  When a
+//                loss is wanted, more CTAs of the same launch sum it, one per
+//                slice of 1024 image pairs, while the cameras are updated.
+// k_sum_fixed    the same loss slices alone.
+// k_cam_ea       the epipolar step after k_ea_direct in one launch: one CTA
+//                per camera whose threads each take an incident image pair,
+//                add its records, apply the normalisers and the chain rule
+//                themselves (the per-image-pair pass folded in: every image
+//                pair's chain rule is evaluated by both of its cameras), then
+//                the camera's sum and Adam as in k_cam; the loss CTAs form
+//                each image pair's loss term from its records.  Same sums in
+//                the same order as k_ea_segments followed by k_cam, so the
+//                results are bit-identical; one launch and one dependency
+//                wait instead of three (measured on the 5M-pair scene: each
+//                wait after a predecessor's end costs ~1.1 us).
 #include "fm_step.cuh"
 
 namespace fm {
 namespace {
 
+using step::kThreads;
 using step::Layout;
 
-constexpr int kCamThreads = 128;    // one warp per camera
-constexpr int kSumThreads = 1024;
-
 template <int STAGE, bool ADAM>
-__global__ void __launch_bounds__(kCamThreads) k_cam(CamUpdate u) {
+__global__ void __launch_bounds__(kThreads) k_cam(CamUpdate u) {
   using L = Layout<STAGE>;
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
+  __shared__ float red[kThreads / 32][L::PART];
   const int run = blockIdx.y;
   pdl_trigger();
-  const int c = blockIdx.x * (kCamThreads / 32) + warp;
-  if (c >= u.N) return;
+  if ((int)blockIdx.x >= u.N) {   // loss slices
+    const int g = blockIdx.x - u.N;
+    const int sc = step::slice_scene(u.loss.sc_slice_off, u.loss.S, g);
+    const float* x = u.seg_loss + (size_t)run * u.P + u.loss.sc_pair_off[sc];
+    pdl_wait();
+    step::loss_slice(u.loss, sc, g, run, [&](int j) { return x[j]; });
+    return;
+  }
+  const int c = blockIdx.x, t = threadIdx.x, lane = t & 31;
   // static: before the wait
   const int b = u.cam_seg_off[c], e = u.cam_seg_off[c + 1];
-  int pre[step::kCamPre];
-  step::cam_prefetch(u.cam_seg, b, e, lane, pre);
+  const int pre = (b + t < e) ? __ldg(u.cam_seg + b + t) : -1;
   pdl_wait();
   // parameters and moments do not depend on the gather: loaded with it
   const size_t off = ((size_t)run * u.N + c) * L::PDIM;
   float p[L::PDIM];
-#pragma unroll
-  for (int k = 0; k < L::PDIM; ++k) p[k] = u.params[off + k];
   float m = 0.f, v = 0.f;
-  if (ADAM && lane < L::PDIM) {
-    m = u.m[off + lane];
-    v = u.v[off + lane];
+  if (t < 32) {
+#pragma unroll
+    for (int k = 0; k < L::PDIM; ++k) p[k] = u.params[off + k];
+    if (ADAM && lane < L::PDIM) {
+      m = u.m[off + lane];
+      v = u.v[off + lane];
+    }
   }
   float acc[L::PART];
-  step::cam_gather<L::PART>(u.seg_grad + (size_t)run * u.P * 2 * L::PART, u.cam_seg, b, e, lane, pre, acc);
-  step::cam_apply<STAGE, ADAM>(u, off, p, m, v, acc, lane);
+#pragma unroll
+  for (int k = 0; k < L::PART; ++k) acc[k] = 0.f;
+  const float* sg = u.seg_grad + (size_t)run * u.P * 2 * L::PART;
+  if (pre != -1) step::cam_add<L::PART>(sg, pre, acc);
+  for (int idx = b + t + kThreads; idx < e; idx += kThreads) step::cam_add<L::PART>(sg, __ldg(u.cam_seg + idx), acc);
+  step::cam_reduce<L::PART>(acc, red);
+  if (t < 32) step::cam_apply<STAGE, ADAM>(u, off, p, m, v, acc, lane);
 }
 
-// fixed-order sum of each scene's range of values per run (one CTA per
-// (scene, run)) into out (and out2 when not null)
-__global__ void __launch_bounds__(kSumThreads) k_sum_fixed(const float* __restrict__ x, int P,
-                                                           const int* __restrict__ sc_pair_off,
-                                                           float* __restrict__ out, float* __restrict__ out2) {
-  __shared__ float part[kSumThreads];
-  const int sc = blockIdx.x, run = blockIdx.y;
+// the loss slices alone: seg_loss summed per (scene, run)
+__global__ void __launch_bounds__(kThreads) k_sum_fixed(const float* __restrict__ x, int P, LossArgs L) {
+  const int g = blockIdx.x, run = blockIdx.y;
   pdl_trigger();
-  const int b = sc_pair_off ? sc_pair_off[sc] : 0, e = sc_pair_off ? sc_pair_off[sc + 1] : P;
+  const int sc = step::slice_scene(L.sc_slice_off, L.S, g);
+  const float* xs = x + (size_t)run * P + L.sc_pair_off[sc];
   pdl_wait();
-  const float v = step::loss_sum_cta<kSumThreads>(x + (size_t)run * P + b, e - b, part);
-  if (threadIdx.x == 0) {
-    out[(size_t)run * gridDim.x + sc] = v;
-    if (out2) out2[(size_t)run * gridDim.x + sc] = v;
+  step::loss_slice(L, sc, g, run, [&](int j) { return xs[j]; });
+}
+
+template <bool ADAM>
+__global__ void __launch_bounds__(kThreads) k_cam_ea(EaCamArgs f) {
+  __shared__ float red[kThreads / 32][12];
+  const SegArgs& s = f.s;
+  const CamUpdate& u = f.u;
+  pdl_trigger();
+  if ((int)blockIdx.x >= u.N) {   // loss slices: each image pair's loss term from its records
+    const int g = blockIdx.x - u.N;
+    const int sc = step::slice_scene(u.loss.sc_slice_off, u.loss.S, g);
+    const int n0 = u.loss.sc_pair_off[sc];
+    pdl_wait();
+    step::loss_slice(u.loss, sc, g, 0, [&](int j) {
+      const int n = n0 + j;
+      const float ps = s.pair_scale ? s.pair_scale[n] : 1.f;
+      return step::rec_loss_serial(s.rec, s.seg_rec[2 * n], s.seg_rec[2 * n + 1]) * (s.l_scale * ps);
+    });
+    return;
   }
+  const int c = blockIdx.x, t = threadIdx.x, lane = t & 31;
+  // static: the first incident image pair of this thread, before the wait
+  const int b = u.cam_seg_off[c], e = u.cam_seg_off[c + 1];
+  int entry = (b + t < e) ? __ldg(u.cam_seg + b + t) : -1;
+  step::SegStatic st = step::seg_static(s, entry == -1 ? s.P : (int)((unsigned)entry & 0x7fffffffu));
+  pdl_wait();
+  const size_t off = (size_t)c * 9;
+  float p[9];
+  float m = 0.f, v = 0.f;
+  if (t < 32) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) p[k] = u.params[off + k];
+    if (ADAM && lane < 9) {
+      m = u.m[off + lane];
+      v = u.v[off + lane];
+    }
+  }
+  float acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = 0.f;
+  for (int idx = b + t; idx < e; idx += kThreads) {
+    if (idx != b + t) {
+      entry = __ldg(u.cam_seg + idx);
+      st = step::seg_static(s, (int)((unsigned)entry & 0x7fffffffu));
+    }
+    const int n = (int)((unsigned)entry & 0x7fffffffu);
+    const bool role_j = ((unsigned)entry >> 31) != 0;
+    float qi[9], qj[9];
+    if (st.cnt > 0) {
+      load_plain(s.params + 9 * st.ci, qi, 9);
+      load_plain(s.params + 9 * st.cj, qj, 9);
+    }
+    float G[10];
+    step::rec_sum_serial(s.rec, st.r0, st.cnt, G);
+    const float gs = s.g_scale * (s.pair_scale ? s.pair_scale[n] : 1.f);
+    for (int k = 0; k < 9; ++k) G[k] *= gs;
+    float o[kSegGradEa];
+    step::pair_grad(s, n, st.cnt, G, qi, qj, o);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] += role_j ? o[12 + k] : o[k];
+  }
+  step::cam_reduce<12>(acc, red);
+  if (t < 32) step::cam_apply<2, ADAM>(u, off, p, m, v, acc, lane);
 }
 
 template <int STAGE>
 void launch_stage(const CamUpdate& u, cudaStream_t s) {
-  const int cam_blocks = (u.N + kCamThreads / 32 - 1) / (kCamThreads / 32);
-  dim3 grid(cam_blocks, u.runs);
-  if (u.params_out) launch_pdl(k_cam<STAGE, true>, grid, dim3(kCamThreads), 0, s, u);
-  else launch_pdl(k_cam<STAGE, false>, grid, dim3(kCamThreads), 0, s, u);
+  dim3 grid(u.N + (u.loss.out ? u.loss.n_slices : 0), u.runs);
+  if (u.params_out) launch_pdl(k_cam<STAGE, true>, grid, dim3(kThreads), 0, s, u);
+  else launch_pdl(k_cam<STAGE, false>, grid, dim3(kThreads), 0, s, u);
 }
 
 }  // namespace
@@ -87,9 +159,14 @@ void launch_cam_update(int stage, const CamUpdate& u, cudaStream_t s) {
   else launch_stage<2>(u, s);
 }
 
-void launch_sum_fixed(const float* x, int P, int runs, const int* sc_pair_off, int S, float* out,
-                      cudaStream_t s, float* out2) {
-  launch_pdl(k_sum_fixed, dim3(S, runs), dim3(kSumThreads), 0, s, x, P, sc_pair_off, out, out2);
+void launch_sum_fixed(const float* x, int P, int runs, const LossArgs& L, cudaStream_t s) {
+  launch_pdl(k_sum_fixed, dim3(L.n_slices, runs), dim3(kThreads), 0, s, x, P, L);
+}
+
+void launch_cam_ea(const EaCamArgs& f, cudaStream_t s) {
+  dim3 grid(f.u.N + (f.u.loss.out ? f.u.loss.n_slices : 0));
+  if (f.u.params_out) launch_pdl(k_cam_ea<true>, grid, dim3(kThreads), 0, s, f);
+  else launch_pdl(k_cam_ea<false>, grid, dim3(kThreads), 0, s, f);
 }
 
 }  // namespace fm

@@ -62,7 +62,7 @@ enum KernelId : int {
   kKCalibrate = 0, kKSegOffsets, kKRunTables, kKEaTables, kKEaDirect, kKEaSegments,
   kKRotPairs, kKTrnTargets, kKTrnPairs, kKCamUpdate, kKLossSum, kKEaReweight, kKWBuild,
   kKEaCompact, kKMartIter, kKRelTrans, kKMerge, kKTriangulate, kKEaDirectLoss, kKEaDirectCoef, kKMlpTables, kKMlpInfer,
-  kKRelpose, kKFocalVote, kKDistErrors, kKDistReduce, kKCount
+  kKRelpose, kKFocalVote, kKDistErrors, kKDistReduce, kKCamEa, kKCount
 };
 extern const char* const kKernelNames[kKCount];
 
@@ -225,6 +225,12 @@ struct fm_problem {
   float* h_loss = nullptr;          // pinned [max(m,1)*S]
   int* h_err = nullptr;             // pinned copy of d_err
   int* d_err = nullptr;             // device error bits
+  // loss slices (fm_step.cuh): per scene ceil(P_s / 1024) slices
+  std::vector<int> h_sc_slice_off;  // [S+1]
+  int n_slices = 0;
+  int* sc_slice_off = nullptr;      // [S+1]
+  float* loss_part = nullptr;       // [64][n_slices]
+  int* loss_cnt = nullptr;          // [64][S][kLossCntStride]
 };
 
 namespace fm {
@@ -433,6 +439,21 @@ void launch_trn_pairs(const float* o, const int* pi, const int* pj, const float*
                       int P, int runs, const float* pair_inv_p, float* seg_grad, float* seg_loss,
                       int* step_counter, cudaStream_t s);
 
+// loss reductions in slices of image pairs (fm_step.cuh): the loss of scene
+// s is summed by ceil(P_s / 1024) CTAs, the last of which adds their sums
+constexpr int kLossCntStride = 32;   // ints between two arrival counters: a 128-B line each
+constexpr int kLossSlice = 1024;     // image pairs per slice
+struct LossArgs {
+  const int* sc_pair_off;  // [S+1] image-pair range of each scene
+  const int* sc_slice_off; // [S+1] first slice of each scene
+  int S;
+  int n_slices;            // slices of all scenes (per run)
+  float* partial;          // [runs][n_slices] slice sums
+  int* cnt;                // [runs][S][kLossCntStride] arrival counters, zero between launches
+  float* out;              // [runs][S] losses, or null (no loss wanted)
+  float* out2;             // a second destination of the same losses, or null
+};
+
 // per-camera reduction, 6D adjoint and Adam (fm_cam.cu)
 struct CamUpdate {
   const int* cam_seg_off;
@@ -446,11 +467,19 @@ struct CamUpdate {
   const int* step;
   float lr, b1, b2, eps;
   int N, P, runs;
+  const float* seg_loss;   // [runs][P] per-image-pair loss terms (k_cam's loss slices)
+  LossArgs loss;           // loss.out null: no loss
 };
 void launch_cam_update(int stage, const CamUpdate& u, cudaStream_t s);
-// out[r*S + s] = fixed-order sum of x[r*P + sc_pair_off[s] .. sc_pair_off[s+1]);
-// sc_pair_off null: one range [0, P) (S = 1); out2 (optional) gets the same
-void launch_sum_fixed(const float* x, int P, int runs, const int* sc_pair_off, int S, float* out,
-                      cudaStream_t s, float* out2 = nullptr);
+// the epipolar step after k_ea_direct: s as for k_ea_segments (its seg_grad,
+// seg_loss, dlde_* unused), u as for k_cam of the epipolar stage (one run)
+struct EaCamArgs {
+  SegArgs s;
+  CamUpdate u;
+};
+void launch_cam_ea(const EaCamArgs& f, cudaStream_t s);
+// L.out[r*S + s] (and L.out2) = fixed-order sum of x[r*P + sc_pair_off[s] ..
+// sc_pair_off[s+1]) in the slices of L
+void launch_sum_fixed(const float* x, int P, int runs, const LossArgs& L, cudaStream_t s);
 
 }  // namespace fm

@@ -11,8 +11,9 @@
 //
 // The array is shared by every call on a device and keeps whatever the last
 // call wrote.  Each call writes every table entry it later reads, and clears
-// its error word (the one thing that must start at zero) with a memset on
-// the stream.  Two calls whose GPU work overlaps in time (different streams,
+// the words that must start at zero (its error word and the loss slices'
+// arrival counter) with a small kernel on the stream.  Two calls whose GPU
+// work overlaps in time (different streams,
 // or different host threads) race on the array and corrupt each other's
 // results; order such calls on one stream or synchronise between them.
 //
@@ -57,6 +58,20 @@ cudaError_t scratch_address(int device, void** out) {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// clears the error word and the arrival counter, writes the slice table of
+// one scene of P image pairs
+__global__ void k_static_init(int* err, int* lsl, int P, int n_slices) {
+  const int t = threadIdx.x;
+  if (t == 0) {
+    *err = 0;
+    lsl[0] = 0;
+    lsl[1] = P;
+    lsl[2] = 0;
+    lsl[3] = n_slices;
+  }
+  lsl[4 + t] = 0;   // the counter's line (32 ints)
+}
+
 // the loss becomes NaN when a kernel of the call raised an error bit
 __global__ void k_nan_on_error(const int* err, float* loss) {
   if (*err != 0) *loss = __int_as_float(0x7fc00000);
@@ -95,8 +110,11 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
   const size_t b_rec = align256(sizeof(float4) * 3 * ((size_t)P + (size_t)n_wruns));
   const size_t b_loss = align256(sizeof(float) * (size_t)P);
   const size_t b_g = align256(sizeof(int) * ((size_t)P + 2));
-  const size_t b_total = align256(sizeof(long long));
-  const size_t need = b_tab + b_run + b_info + b_srec + b_rec + b_loss + b_g + b_total;
+  const size_t b_total = align256(sizeof(long long) + sizeof(int));
+  // the loss slices of one scene: slice table, slice sums, arrival counter
+  const int n_slices = (P + fm::kLossSlice - 1) / fm::kLossSlice;
+  const size_t b_lsl = align256(sizeof(int) * (4 + fm::kLossCntStride) + sizeof(float) * (size_t)n_slices);
+  const size_t need = b_tab + b_run + b_info + b_srec + b_rec + b_loss + b_g + b_total + b_lsl;
   if (need > kStaticScratchBytes)
     return static_fail(FM_ERR_INVALID_ARG,
                        "problem needs " + std::to_string(need) + " bytes of scratch; the static array holds " +
@@ -138,6 +156,17 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
   p += b_g;
   long long* total = reinterpret_cast<long long*>(p);
   v.d_err = reinterpret_cast<int*>(total + 1);   // error bits of this call (made a NaN loss at the end)
+  p += b_total;
+  int* lsl = reinterpret_cast<int*>(p);          // {0, P} {0, n_slices}, counter, slice sums
+  fm::LossArgs la;
+  la.sc_pair_off = lsl;
+  la.sc_slice_off = lsl + 2;
+  la.S = 1;
+  la.n_slices = n_slices;
+  la.cnt = lsl + 4;
+  la.partial = reinterpret_cast<float*>(lsl + 4 + fm::kLossCntStride);
+  la.out = loss_dev;
+  la.out2 = nullptr;
   v.seg_grad = pair_grad_dev;
   v.n_wruns = n_wruns;
   cudaStream_t s = v.stream;
@@ -152,10 +181,13 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
   const bool was = fm::g_capturing;
   fm::g_capturing = was || cap == cudaStreamCaptureStatusActive;
   fm::g_plain_once = true;
-  e = cudaMemsetAsync(v.d_err, 0, sizeof(int), s);
+  // the words that must start at zero (error bits, arrival counter) and the
+  // slice table of this call
+  k_static_init<<<1, 32, 0, s>>>(v.d_err, lsl, P, n_slices);
+  e = cudaGetLastError();
   if (e != cudaSuccess) {
     fm::g_capturing = was;
-    return static_fail(FM_ERR_CUDA, std::string("clearing the error word: ") + cudaGetErrorString(e));
+    return static_fail(FM_ERR_CUDA, std::string("initialising the array: ") + cudaGetErrorString(e));
   }
   fm::launch_ea_tables(params_dev, v.pair_i, v.pair_j, v.seg_off, P, v.seg_tab, nullptr, s);
   // the offsets are validated before any lane table is built from them
@@ -171,7 +203,7 @@ fm_status fm_ea_loss_grad_static(const float* kp_dev, const int32_t* seg_off_dev
   sa.g_scale = (loss == FM_EA_L1) ? inv_z : 2.f * inv_z;
   sa.l_scale = inv_z;
   fm::launch_ea_segments(sa, s);
-  fm::launch_sum_fixed(v.seg_loss, P, 1, nullptr, 1, loss_dev, s);
+  fm::launch_sum_fixed(v.seg_loss, P, 1, la, s);
   k_nan_on_error<<<1, 1, 0, s>>>(v.d_err, loss_dev);
   fm::g_capturing = was;
   e = cudaGetLastError();

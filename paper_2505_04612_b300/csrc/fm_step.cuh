@@ -1,5 +1,9 @@
-// Device functions of the per-image-pair pass (k_ea_segments) and the
-// per-camera pass (k_cam).
+// Device functions of the passes that follow the per-keypoint-pair kernels:
+// the per-image-pair pass (k_ea_segments), the per-camera pass (k_cam), the
+// epipolar step's per-camera pass with the image pairs' chain rule folded in
+// (k_cam_ea) and the loss reductions.  Every quantity is formed in one fixed
+// order wherever it is computed, so that all paths of the library give
+// bit-identical results.
 #pragma once
 #include "fm_device.cuh"
 #include "fm_internal.h"
@@ -7,8 +11,91 @@
 namespace fm {
 namespace step {
 
-constexpr int kSegLanes = 8;      // lanes that share one image pair
-constexpr int kThreads = 128;     // CTA size of the per-image-pair and per-camera passes
+constexpr int kSegLanes = 8;      // lanes that share one image pair in k_ea_segments
+constexpr int kThreads = 128;     // CTA size of every pass here
+
+// ------------------------------------------------------------------ records
+// An image pair's records (one per warp run it touches; 10 values: the nine
+// terms of dL/dE_n and the loss) are added in a fixed order: blocks of eight
+// records q0..q7 (zero past the last), each block combined as
+// ((q0 + q4) + (q2 + q6)) + ((q1 + q5) + (q3 + q7)), the blocks added to a
+// running sum that starts at 0, in order.  Eight lanes form a block with a
+// xor butterfly; one thread with the same three pairwise steps.
+
+__device__ __forceinline__ void rec_load(const float4* rec, int r, bool ok, float* v) {
+  if (ok) {
+    const float4 a = rec[3 * r], b = rec[3 * r + 1], c = rec[3 * r + 2];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    v[8] = c.x; v[9] = c.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) v[k] = 0.f;
+  }
+}
+
+// eight lanes of one group (sub = 0..7; mask: the group's lanes); every lane
+// of the group ends with the sum
+__device__ __forceinline__ void rec_sum_lanes(const float4* rec, int r0, int cnt, int sub, unsigned mask, float* G) {
+#pragma unroll
+  for (int k = 0; k < 10; ++k) G[k] = 0.f;
+  for (int b0 = 0; b0 < cnt; b0 += kSegLanes) {
+    float v[10];
+    rec_load(rec, r0 + b0 + sub, b0 + sub < cnt, v);
+#pragma unroll
+    for (int d = kSegLanes / 2; d > 0; d >>= 1)
+#pragma unroll
+      for (int k = 0; k < 10; ++k) v[k] += __shfl_xor_sync(mask, v[k], d);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) G[k] += v[k];
+  }
+}
+
+__device__ __forceinline__ void add10(float* a, const float* b) {
+#pragma unroll
+  for (int k = 0; k < 10; ++k) a[k] += b[k];
+}
+
+// one thread, the same order
+__device__ __forceinline__ void rec_sum_serial(const float4* rec, int r0, int cnt, float* G) {
+#pragma unroll
+  for (int k = 0; k < 10; ++k) G[k] = 0.f;
+  for (int b0 = 0; b0 < cnt; b0 += kSegLanes) {
+    const int r = r0 + b0, left = cnt - b0;
+    float a[10], b[10], c[10], d[10];
+    rec_load(rec, r + 0, 0 < left, a);
+    rec_load(rec, r + 4, 4 < left, b);
+    add10(a, b);                        // q0 + q4
+    rec_load(rec, r + 2, 2 < left, c);
+    rec_load(rec, r + 6, 6 < left, b);
+    add10(c, b);                        // q2 + q6
+    add10(a, c);
+    rec_load(rec, r + 1, 1 < left, c);
+    rec_load(rec, r + 5, 5 < left, b);
+    add10(c, b);                        // q1 + q5
+    rec_load(rec, r + 3, 3 < left, d);
+    rec_load(rec, r + 7, 7 < left, b);
+    add10(d, b);                        // q3 + q7
+    add10(c, d);
+    add10(a, c);
+    add10(G, a);
+  }
+}
+
+// the loss term alone (value 9), the same order
+__device__ __forceinline__ float rec_loss_serial(const float4* rec, int r0, int cnt) {
+  float G = 0.f;
+  for (int b0 = 0; b0 < cnt; b0 += kSegLanes) {
+    const int r = r0 + b0, left = cnt - b0;
+    auto q = [&](int s) { return s < left ? rec[3 * (r + s) + 2].y : 0.f; };
+    const float a = (q(0) + q(4)) + (q(2) + q(6));
+    const float c = (q(1) + q(5)) + (q(3) + q(7));
+    G += a + c;
+  }
+  return G;
+}
+
+// ------------------------------------------------------------- image pairs
 
 // Static inputs of image pair n's pass, loaded before the dependency wait.
 struct SegStatic {
@@ -26,13 +113,31 @@ __device__ __forceinline__ SegStatic seg_static(const SegArgs& a, int n) {
   return s;
 }
 
+// dL/dE_n from its summed records G (scaled in place by the normalisers), and
+// the chain rule through E_n = [t^]_x R_ij to the two cameras (Sec. 3.3):
+// o = (dL/dR_i, dL/dt_i, dL/dR_j, dL/dt_j).  An image pair without keypoint
+// pairs (cnt 0; its geometry may be degenerate) gets zeros.
+__device__ __forceinline__ void pair_grad(const SegArgs& a, int n, int cnt, float* G, const float* qi,
+                                          const float* qj, float* o) {
+  if (cnt == 0) {
+#pragma unroll
+    for (int k = 0; k < kSegGradEa; ++k) o[k] = 0.f;
+    return;
+  }
+  if (a.grad_loss) {
+    const float gl = a.grad_loss[a.pair_scene ? a.pair_scene[n] : 0];
+    for (int k = 0; k < 9; ++k) G[k] *= gl;
+  }
+  PairGeo g;
+  pair_geometry(qi, qj, g);
+  pair_backward(g, G, o);
+}
+
 // Image pair n, shared by kSegLanes lanes (sub = lane index in the group):
-// the lanes sum its records with a stride of kSegLanes and combine them with
-// a butterfly inside the group (a fixed order), the group's first lane
-// scales the sum by the normalisers and applies the chain rule through
-// E_n = [t^]_x R_ij to the two cameras (Sec. 3.3).  Returns true on the lane
-// that wrote image pair n's outputs.  Every lane of the warp must call it.
-__device__ __forceinline__ bool segment_pair(const SegArgs& a, int n, int sub, const SegStatic& st) {
+// the records' sum in the fixed order, the normalisers, the loss term, and
+// the chain rule by the group's first lane.  Every lane of the warp must
+// call it.
+__device__ __forceinline__ void segment_pair(const SegArgs& a, int n, int sub, const SegStatic& st) {
   const bool valid = n < a.P;
   // the cameras' parameters are needed by the chain rule after the sum:
   // loaded now, with the records, rather than after the butterfly
@@ -42,21 +147,11 @@ __device__ __forceinline__ bool segment_pair(const SegArgs& a, int n, int sub, c
     load_plain(a.params + 9 * st.ci, qi, 9);
     load_plain(a.params + 9 * st.cj, qj, 9);
   }
+  const int lane = threadIdx.x & 31;
+  const unsigned mask = 0xffu << (lane & ~(kSegLanes - 1));
   float G[10];
-  for (int k = 0; k < 10; ++k) G[k] = 0.f;
-  if (valid && !a.dlde_in) {
-    for (int r = st.r0 + sub; r < st.r0 + st.cnt; r += kSegLanes) {
-      const float4 v0 = a.rec[3 * r], v1 = a.rec[3 * r + 1], v2 = a.rec[3 * r + 2];
-      G[0] += v0.x; G[1] += v0.y; G[2] += v0.z; G[3] += v0.w;
-      G[4] += v1.x; G[5] += v1.y; G[6] += v1.z; G[7] += v1.w;
-      G[8] += v2.x; G[9] += v2.y;
-    }
-  }
-#pragma unroll
-  for (int d = kSegLanes / 2; d > 0; d >>= 1)
-#pragma unroll
-    for (int k = 0; k < 10; ++k) G[k] += __shfl_xor_sync(0xffffffffu, G[k], d);
-  if (!valid || sub != 0) return false;
+  rec_sum_lanes(a.rec, st.r0, (valid && !a.dlde_in) ? st.cnt : 0, sub, mask, G);
+  if (!valid || sub != 0) return;
   const float ps = a.pair_scale ? a.pair_scale[n] : 1.f;
   if (a.dlde_in) {
     for (int k = 0; k < 9; ++k) G[k] = a.dlde_in[9 * (size_t)n + k];
@@ -67,20 +162,10 @@ __device__ __forceinline__ bool segment_pair(const SegArgs& a, int n, int sub, c
   if (a.seg_loss) a.seg_loss[n] = G[9] * (a.l_scale * ps);
   if (a.dlde_out)
     for (int k = 0; k < 9; ++k) a.dlde_out[9 * (size_t)n + k] = G[k];
-  if (!a.seg_grad) return true;
-  float* out = a.seg_grad + (size_t)kSegGradEa * n;
-  if (st.cnt == 0) {   // an image pair without keypoint pairs (its geometry may be degenerate)
-    for (int k = 0; k < kSegGradEa; ++k) out[k] = 0.f;
-    return true;
-  }
-  if (a.grad_loss) {
-    const float gl = a.grad_loss[a.pair_scene ? a.pair_scene[n] : 0];
-    for (int k = 0; k < 9; ++k) G[k] *= gl;
-  }
-  PairGeo g;
-  pair_geometry(qi, qj, g);
+  if (!a.seg_grad) return;
   float o[kSegGradEa];
-  pair_backward(g, G, o);
+  pair_grad(a, n, st.cnt, G, qi, qj, o);
+  float* out = a.seg_grad + (size_t)kSegGradEa * n;
   if ((reinterpret_cast<uintptr_t>(out) & 15u) == 0) {   // library buffers: 96-B rows, 16-B aligned
     float4* o4 = reinterpret_cast<float4*>(out);
 #pragma unroll
@@ -88,8 +173,9 @@ __device__ __forceinline__ bool segment_pair(const SegArgs& a, int n, int sub, c
   } else {
     for (int k = 0; k < kSegGradEa; ++k) out[k] = o[k];
   }
-  return true;
 }
+
+// ---------------------------------------------------------------- cameras
 
 // Per-stage layout of the per-camera pass.  STAGE 0 rotation (part 9: dR,
 // params 6D), 1 translation (part 3: do, params o), 2 epipolar (part 12: dR,
@@ -100,14 +186,8 @@ template <> struct Layout<0> { static constexpr int PART = 9, PDIM = 6; static c
 template <> struct Layout<1> { static constexpr int PART = 3, PDIM = 3; static constexpr bool ROT = false; };
 template <> struct Layout<2> { static constexpr int PART = 12, PDIM = 9; static constexpr bool ROT = true; };
 
-// The first kCamPre incident image pairs of a lane (camera CSR entries b +
-// lane + 32 k, -1 past e): static, loaded before the dependency wait.
-constexpr int kCamPre = 4;
-__device__ __forceinline__ void cam_prefetch(const int* __restrict__ cam_seg, int b, int e, int lane, int* v) {
-#pragma unroll
-  for (int u = 0; u < kCamPre; ++u) v[u] = (b + lane + 32 * u < e) ? __ldg(cam_seg + b + lane + 32 * u) : -1;
-}
-
+// adds the part of camera-CSR entry `entry` (image pair | role << 31) of the
+// per-image-pair gradients sg
 template <int PART>
 __device__ __forceinline__ void cam_add(const float* sg, int entry, float* acc) {
   const unsigned w = (unsigned)entry;
@@ -129,34 +209,34 @@ __device__ __forceinline__ void cam_add(const float* sg, int entry, float* acc) 
   }
 }
 
-// Sum of a camera's parts over its incident image pairs [b, e) of the camera
-// CSR, by one warp: lane l adds the entries b + l, b + l + 32, ... in that
-// order (the first kCamPre of them prefetched in pre), then a butterfly gives
-// every lane the total.
+// A camera's parts over its incident image pairs [b, e) of the camera CSR are
+// added in a fixed order by one CTA of kThreads: thread t adds the entries
+// b + t, b + t + kThreads, ... in that order, a xor butterfly combines each
+// warp, and the warps' sums are added in warp order.  cam_reduce does the
+// last two steps; warp 0 holds the total.
 template <int PART>
-__device__ __forceinline__ void cam_gather(const float* sg, const int* __restrict__ cam_seg, int b, int e, int lane,
-                                           const int* pre, float* acc) {
-#pragma unroll
-  for (int k = 0; k < PART; ++k) acc[k] = 0.f;
-#pragma unroll
-  for (int u = 0; u < kCamPre; ++u)
-    if (pre[u] != -1) cam_add<PART>(sg, pre[u], acc);
-  for (int i0 = b + lane + 32 * kCamPre; i0 < e; i0 += 32 * kCamPre) {
-    int v[kCamPre];
-#pragma unroll
-    for (int u = 0; u < kCamPre; ++u) v[u] = (i0 + 32 * u < e) ? __ldg(cam_seg + i0 + 32 * u) : -1;
-#pragma unroll
-    for (int u = 0; u < kCamPre; ++u)
-      if (v[u] != -1) cam_add<PART>(sg, v[u], acc);
-  }
+__device__ __forceinline__ void cam_reduce(float* acc, float (*red)[PART]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < PART; ++k) acc[k] = warp_sum(acc[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < PART; ++k) red[warp][k] = acc[k];
+  __syncthreads();
+  if (warp == 0)
+#pragma unroll
+    for (int k = 0; k < PART; ++k) {
+      float t = red[0][k];
+      for (int w = 1; w < kThreads / 32; ++w) t += red[w][k];
+      acc[k] = t;
+    }
 }
 
 // Camera c of run `run` from its summed parts, its parameters p and (Adam)
 // its moments m, v of lane's entry (all loaded beforehand): the 6D adjoint
 // for rotations, then either the gradient or Adam (bias-corrected; the step
-// counter was advanced by this step's first kernel), by lanes < PDIM.
+// counter was advanced by this step's first kernel), by lanes < PDIM of
+// warp 0.
 template <int STAGE, bool ADAM>
 __device__ __forceinline__ void cam_apply(const CamUpdate& u, size_t off, const float* p, float m, float v,
                                           const float* acc, int lane) {
@@ -195,53 +275,61 @@ __device__ __forceinline__ void cam_apply(const CamUpdate& u, size_t off, const 
   u.params_out[off + lane] = pv - u.lr * (m / bc1) / (sqrtf(v / bc2) + u.eps);
 }
 
-// Fixed-order sum of n per-image-pair loss terms by one CTA of T threads.
-// The order depends on n only -- not on where x starts, so that a scene's
-// loss inside a batch adds exactly as the same scene alone: chunks of four
-// consecutive terms, chunk c summed as (x0 + x1) + (x2 + x3) into thread
-// c % T's accumulator (c / T) % 8, the n % 4 last terms one per thread, then
-// the accumulators in a fixed order and a tree over the threads.  A chunk is
-// one float4 load when x is 16-B aligned, four scalar loads otherwise; eight
-// chunks per thread are in flight.  Every thread of the CTA must call it.
-__device__ __forceinline__ float4 load_chunk(const float* x, int c, bool aligned) {
-  if (aligned) return reinterpret_cast<const float4*>(x)[c];
-  return make_float4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+// ------------------------------------------------------------------- losses
+// A scene's loss, the sum of its image pairs' loss terms x_0 .. x_{n-1}, is
+// added in slices of kSlice terms: slice k (terms kSlice k ..) by one CTA,
+// thread t adding the terms t, t + kThreads, ... of the slice in order, a
+// tree over the threads; then the slices' sums in slice order.  One CTA per
+// slice; the last to finish (an arrival counter per (scene, run) on a line of
+// its own, reset by it) adds the slices.  The order depends on n only.
+constexpr int kSlice = kLossSlice;
+
+// the scene of global slice g: the largest s with sc_slice_off[s] <= g
+__device__ __forceinline__ int slice_scene(const int* sc_slice_off, int S, int g) {
+  int lo = 0, hi = S - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sc_slice_off[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
-template <int T>
-__device__ __forceinline__ float loss_sum_cta(const float* x, int n, float* part) {
+// Global slice g of run `run` (scene sc): the slice's sum from value(j) (term
+// j of the scene), then the combination.  Every thread of the CTA calls it.
+template <typename Value>
+__device__ __forceinline__ void loss_slice(const LossArgs& L, int sc, int g, int run, Value value) {
+  __shared__ float part[kThreads];
+  __shared__ int last;
   const int t = threadIdx.x;
-  const bool aligned = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
-  const int n4 = n >> 2;
-  float acc[8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u) acc[u] = 0.f;
-  int k = t;
-  for (; k + 7 * T < n4; k += 8 * T) {
-    float4 v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = load_chunk(x, k + u * T, aligned);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] += (v[u].x + v[u].y) + (v[u].z + v[u].w);
-  }
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    if (k < n4) {
-      const float4 v = load_chunk(x, k, aligned);
-      acc[u] += (v.x + v.y) + (v.z + v.w);
-    }
-    k += T;
-  }
-  if (t < n - 4 * n4) acc[0] += x[4 * n4 + t];
-  part[t] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  const int n = L.sc_pair_off[sc + 1] - L.sc_pair_off[sc];
+  const int j0 = (g - L.sc_slice_off[sc]) * kSlice, j1 = min(n, j0 + kSlice);
+  float acc = 0.f;
+  for (int j = j0 + t; j < j1; j += kThreads) acc += value(j);
+  part[t] = acc;
   __syncthreads();
-  for (int d = T / 2; d > 0; d >>= 1) {
+  for (int d = kThreads / 2; d > 0; d >>= 1) {
     if (t < d) part[t] += part[t + d];
     __syncthreads();
   }
-  const float r = part[0];
+  const int n_slices = L.sc_slice_off[sc + 1] - L.sc_slice_off[sc];
+  float* partial = L.partial + (size_t)run * L.n_slices;
+  int* cnt = L.cnt + ((size_t)run * L.S + sc) * kLossCntStride;
+  if (t == 0) {
+    partial[g] = part[0];
+    __threadfence();   // this slice's sum before its count
+    last = atomicAdd(cnt, 1) == n_slices - 1;
+    if (last) __threadfence();
+  }
   __syncthreads();
-  return r;
+  if (last && t == 0) {
+    const float* ps = partial + L.sc_slice_off[sc];
+    float s = 0.f;
+    for (int q = 0; q < n_slices; ++q) s += __ldcg(ps + q);
+    const size_t o = (size_t)run * L.S + sc;
+    L.out[o] = s;
+    if (L.out2) L.out2[o] = s;
+    *cnt = 0;   // ready for the next launch
+  }
 }
 
 }  // namespace step
