@@ -4,7 +4,7 @@
 // map (Sec. 3.3), and Adam updates the camera's parameters in place.
 //
 // k_cam          one CTA per camera: thread t adds the incident image pairs
-//                t, t + 128, ... (the first read from the CSR before the
+//                t, t + 256, ... (the first read from the CSR before the
 //                dependency wait), warps combine by butterflies and in warp
 //                order, warp 0 applies the adjoint and Adam; its parameters
 //                and moments are loaded while the parts are gathered.  When a
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kThreads) k_cam(CamUpdate u) {
     const int sc = step::slice_scene(u.loss.sc_slice_off, u.loss.S, g);
     const float* x = u.seg_loss + (size_t)run * u.P + u.loss.sc_pair_off[sc];
     pdl_wait();
-    step::loss_slice(u.loss, sc, g, run, [&](int j) { return x[j]; });
+    step::loss_slice(u.loss, sc, g, run, [&](int j, int k, float* v) { step::fill_stored(x, j, k, v); });
     return;
   }
   const int c = blockIdx.x, t = threadIdx.x, lane = t & 31;
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kThreads) k_sum_fixed(const float* __restrict_
   const int sc = step::slice_scene(L.sc_slice_off, L.S, g);
   const float* xs = x + (size_t)run * P + L.sc_pair_off[sc];
   pdl_wait();
-  step::loss_slice(L, sc, g, run, [&](int j) { return xs[j]; });
+  step::loss_slice(L, sc, g, run, [&](int j, int k, float* v) { step::fill_stored(xs, j, k, v); });
 }
 
 template <bool ADAM>
@@ -92,11 +92,7 @@ __global__ void __launch_bounds__(kThreads) k_cam_ea(EaCamArgs f) {
     const int sc = step::slice_scene(u.loss.sc_slice_off, u.loss.S, g);
     const int n0 = u.loss.sc_pair_off[sc];
     pdl_wait();
-    step::loss_slice(u.loss, sc, g, 0, [&](int j) {
-      const int n = n0 + j;
-      const float ps = s.pair_scale ? s.pair_scale[n] : 1.f;
-      return step::rec_loss_serial(s.rec, s.seg_rec[2 * n], s.seg_rec[2 * n + 1]) * (s.l_scale * ps);
-    });
+    step::loss_slice(u.loss, sc, g, 0, [&](int j, int k, float* v) { step::fill_from_records(s, n0, j, k, v); });
     return;
   }
   const int c = blockIdx.x, t = threadIdx.x, lane = t & 31;

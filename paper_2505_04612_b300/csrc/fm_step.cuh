@@ -12,7 +12,8 @@ namespace fm {
 namespace step {
 
 constexpr int kSegLanes = 8;      // lanes that share one image pair in k_ea_segments
-constexpr int kThreads = 128;     // CTA size of every pass here
+constexpr int kThreads = 256;     // CTA size of the per-camera passes and the loss slices
+                                  // (one incident image pair per thread up to degree 256)
 
 // ------------------------------------------------------------------ records
 // An image pair's records (one per warp run it touches; 10 values: the nine
@@ -159,7 +160,7 @@ __device__ __forceinline__ void segment_pair(const SegArgs& a, int n, int sub, c
     const float gs = a.g_scale * ps;
     for (int k = 0; k < 9; ++k) G[k] *= gs;
   }
-  if (a.seg_loss) a.seg_loss[n] = G[9] * (a.l_scale * ps);
+  if (a.seg_loss) a.seg_loss[n] = __fmul_rn(G[9], a.l_scale * ps);
   if (a.dlde_out)
     for (int k = 0; k < 9; ++k) a.dlde_out[9 * (size_t)n + k] = G[k];
   if (!a.seg_grad) return;
@@ -294,17 +295,25 @@ __device__ __forceinline__ int slice_scene(const int* sc_slice_off, int S, int g
   return lo;
 }
 
-// Global slice g of run `run` (scene sc): the slice's sum from value(j) (term
-// j of the scene), then the combination.  Every thread of the CTA calls it.
-template <typename Value>
-__device__ __forceinline__ void loss_slice(const LossArgs& L, int sc, int g, int run, Value value) {
+// Global slice g of run `run` (scene sc): the slice's sum, then the
+// combination.  fill(j, k, v) puts the thread's terms j, j + kThreads, ...
+// (k of them; the rest 0) into v, so that their loads can be issued
+// together.  Every thread of the CTA calls it.
+constexpr int kPerThread = kSlice / kThreads;
+
+template <typename Fill>
+__device__ __forceinline__ void loss_slice(const LossArgs& L, int sc, int g, int run, Fill fill) {
   __shared__ float part[kThreads];
   __shared__ int last;
   const int t = threadIdx.x;
   const int n = L.sc_pair_off[sc + 1] - L.sc_pair_off[sc];
   const int j0 = (g - L.sc_slice_off[sc]) * kSlice, j1 = min(n, j0 + kSlice);
+  const int k = (j1 - j0 - t + kThreads - 1) / kThreads;   // this thread's terms
+  float v[kPerThread];
+  fill(j0 + t, k > 0 ? k : 0, v);
   float acc = 0.f;
-  for (int j = j0 + t; j < j1; j += kThreads) acc += value(j);
+#pragma unroll
+  for (int u = 0; u < kPerThread; ++u) acc += v[u];   // terms past the slice are +0 (terms are >= 0)
   part[t] = acc;
   __syncthreads();
   for (int d = kThreads / 2; d > 0; d >>= 1) {
@@ -329,6 +338,32 @@ __device__ __forceinline__ void loss_slice(const LossArgs& L, int sc, int g, int
     L.out[o] = s;
     if (L.out2) L.out2[o] = s;
     *cnt = 0;   // ready for the next launch
+  }
+}
+
+// fill of loss terms stored in x
+__device__ __forceinline__ void fill_stored(const float* x, int j, int k, float* v) {
+#pragma unroll
+  for (int u = 0; u < kPerThread; ++u) v[u] = (u < k) ? x[j + u * kThreads] : 0.f;
+}
+
+// fill of image pairs' loss terms formed from their records, as
+// segment_pair forms seg_loss (the record sum's order, then an uncontracted
+// product with the normalisers): ranges first, then the records, so that
+// the loads of all k image pairs are in flight together
+__device__ __forceinline__ void fill_from_records(const SegArgs& s, int n0, int j, int k, float* v) {
+  int r0[kPerThread], cnt[kPerThread];
+#pragma unroll
+  for (int u = 0; u < kPerThread; ++u) {
+    const int n = n0 + j + u * kThreads;
+    r0[u] = (u < k) ? s.seg_rec[2 * n] : 0;
+    cnt[u] = (u < k) ? s.seg_rec[2 * n + 1] : 0;
+  }
+#pragma unroll
+  for (int u = 0; u < kPerThread; ++u) {
+    const int n = n0 + j + u * kThreads;
+    const float ps = (u < k && s.pair_scale) ? s.pair_scale[n] : 1.f;
+    v[u] = (u < k) ? __fmul_rn(rec_loss_serial(s.rec, r0[u], cnt[u]), s.l_scale * ps) : 0.f;
   }
 }
 
