@@ -4,7 +4,7 @@
 // map (Sec. 3.3), and Adam updates the camera's parameters in place.
 //
 // k_cam          one CTA per camera: thread t adds the incident image pairs
-//                t, t + 256, ... (the first read from the CSR before the
+//                t, t + 128, ... (the first read from the CSR before the
 //                dependency wait), warps combine by butterflies and in warp
 //                order, warp 0 applies the adjoint and Adam; its parameters
 //                and moments are loaded while the parts are gathered.  When a

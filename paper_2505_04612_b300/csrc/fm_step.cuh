@@ -12,8 +12,9 @@ namespace fm {
 namespace step {
 
 constexpr int kSegLanes = 8;      // lanes that share one image pair in k_ea_segments
-constexpr int kThreads = 256;     // CTA size of the per-camera passes and the loss slices
-                                  // (one incident image pair per thread up to degree 256)
+constexpr int kThreads = 128;     // CTA size of the per-camera passes and the loss slices
+                                  // (256-thread CTAs of k_cam_ea need 32k registers: two
+                                  // per SM, a second wave on 300 cameras, measured slower)
 
 // ------------------------------------------------------------------ records
 // An image pair's records (one per warp run it touches; 10 values: the nine
@@ -23,16 +24,16 @@ constexpr int kThreads = 256;     // CTA size of the per-camera passes and the l
 // running sum that starts at 0, in order.  Eight lanes form a block with a
 // xor butterfly; one thread with the same three pairwise steps.
 
+// record r's 10 values, or zeros when !ok (a predicated load, no branch: the
+// loads of several records can be in flight together)
 __device__ __forceinline__ void rec_load(const float4* rec, int r, bool ok, float* v) {
-  if (ok) {
-    const float4 a = rec[3 * r], b = rec[3 * r + 1], c = rec[3 * r + 2];
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    v[8] = c.x; v[9] = c.y;
-  } else {
-#pragma unroll
-    for (int k = 0; k < 10; ++k) v[k] = 0.f;
-  }
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 a = ok ? rec[3 * r] : z;
+  const float4 b = ok ? rec[3 * r + 1] : z;
+  const float4 c = ok ? rec[3 * r + 2] : z;
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  v[8] = c.x; v[9] = c.y;
 }
 
 // eight lanes of one group (sub = 0..7; mask: the group's lanes); every lane
@@ -83,17 +84,14 @@ __device__ __forceinline__ void rec_sum_serial(const float4* rec, int r0, int cn
   }
 }
 
-// the loss term alone (value 9), the same order
-__device__ __forceinline__ float rec_loss_serial(const float4* rec, int r0, int cnt) {
-  float G = 0.f;
-  for (int b0 = 0; b0 < cnt; b0 += kSegLanes) {
-    const int r = r0 + b0, left = cnt - b0;
-    auto q = [&](int s) { return s < left ? rec[3 * (r + s) + 2].y : 0.f; };
-    const float a = (q(0) + q(4)) + (q(2) + q(6));
-    const float c = (q(1) + q(5)) + (q(3) + q(7));
-    G += a + c;
-  }
-  return G;
+// the loss terms (value 9) of one block of eight records, the same order
+__device__ __forceinline__ float rec_loss_block(const float* q) {
+  return ((q[0] + q[4]) + (q[2] + q[6])) + ((q[1] + q[5]) + (q[3] + q[7]));
+}
+
+__device__ __forceinline__ void rec_loss_load(const float4* rec, int r, int left, float* q) {
+#pragma unroll
+  for (int s = 0; s < kSegLanes; ++s) q[s] = (s < left) ? rec[3 * (r + s) + 2].y : 0.f;
 }
 
 // ------------------------------------------------------------- image pairs
@@ -349,8 +347,10 @@ __device__ __forceinline__ void fill_stored(const float* x, int j, int k, float*
 
 // fill of image pairs' loss terms formed from their records, as
 // segment_pair forms seg_loss (the record sum's order, then an uncontracted
-// product with the normalisers): ranges first, then the records, so that
-// the loads of all k image pairs are in flight together
+// product with the normalisers): the ranges of all k image pairs first, then
+// the first block of records of every one of them, predicated loads with no
+// branch between them, so that they are all in flight together; further
+// blocks (image pairs of more than eight records) after that.
 __device__ __forceinline__ void fill_from_records(const SegArgs& s, int n0, int j, int k, float* v) {
   int r0[kPerThread], cnt[kPerThread];
 #pragma unroll
@@ -359,11 +359,20 @@ __device__ __forceinline__ void fill_from_records(const SegArgs& s, int n0, int 
     r0[u] = (u < k) ? s.seg_rec[2 * n] : 0;
     cnt[u] = (u < k) ? s.seg_rec[2 * n + 1] : 0;
   }
+  float q[kPerThread][kSegLanes];
+#pragma unroll
+  for (int u = 0; u < kPerThread; ++u) rec_loss_load(s.rec, r0[u], cnt[u], q[u]);
 #pragma unroll
   for (int u = 0; u < kPerThread; ++u) {
-    const int n = n0 + j + u * kThreads;
-    const float ps = (u < k && s.pair_scale) ? s.pair_scale[n] : 1.f;
-    v[u] = (u < k) ? __fmul_rn(rec_loss_serial(s.rec, r0[u], cnt[u]), s.l_scale * ps) : 0.f;
+    float G = 0.f;
+    G += rec_loss_block(q[u]);
+    for (int b0 = kSegLanes; b0 < cnt[u]; b0 += kSegLanes) {
+      float w[kSegLanes];
+      rec_loss_load(s.rec, r0[u] + b0, cnt[u] - b0, w);
+      G += rec_loss_block(w);
+    }
+    const float ps = (u < k && s.pair_scale) ? s.pair_scale[n0 + j + u * kThreads] : 1.f;
+    v[u] = (u < k) ? __fmul_rn(G, s.l_scale * ps) : 0.f;
   }
 }
 

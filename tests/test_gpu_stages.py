@@ -157,6 +157,7 @@ def test_loss_trace_and_timing():
     assert len(hist) == 16 and hist[-1] == last
     assert hist[-1] < hist[0]
     assert kt["k_ea_direct"][0] == 20 and kt["k_ea_direct"][1] > 0
-    assert kt["k_ea_segments"][0] == 20 and kt["k_cam"][0] == 20
-    # the loss trace and the returned loss come from one reduction per step
-    assert kt["k_sum_fixed"][0] == 20
+    # after the streaming kernel, one launch: the image pairs' chain rule, the
+    # cameras' Adam update and the loss (trace and returned value alike)
+    assert kt["k_cam_ea"][0] == 20 and kt["k_ea_tables"][0] == 20
+    assert not {"k_ea_segments", "k_cam", "k_sum_fixed"} & set(kt)
