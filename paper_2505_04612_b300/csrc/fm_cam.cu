@@ -9,7 +9,7 @@
 //                order, warp 0 applies the adjoint and Adam; its parameters
 //                and moments are loaded while the parts are gathered.  When a
 //                loss is wanted, more CTAs of the same launch sum it, one per
-//                slice of 1024 image pairs, while the cameras are updated.
+//                slice of 256 image pairs, while the cameras are updated.
 // k_sum_fixed    the same loss slices alone.
 // k_cam_ea       the epipolar step after k_ea_direct in one launch: one CTA
 //                per camera whose threads each take an incident image pair,
@@ -81,8 +81,50 @@ __global__ void __launch_bounds__(kThreads) k_sum_fixed(const float* __restrict_
   step::loss_slice(L, sc, g, run, [&](int j, int k, float* v) { step::fill_stored(xs, j, k, v); });
 }
 
+// one incident image pair of a camera in k_cam_ea: camera-CSR entry, role,
+// and its static inputs
+struct CamEntry {
+  int n = 0;
+  bool role_j = false;
+  bool ok = false;
+  step::SegStatic st;
+};
+
+__device__ __forceinline__ CamEntry cam_entry(const SegArgs& s, const int* __restrict__ cam_seg, int idx, int e) {
+  CamEntry c;
+  c.ok = idx < e;
+  const unsigned w = c.ok ? (unsigned)__ldg(cam_seg + idx) : 0u;
+  c.n = (int)(w & 0x7fffffffu);
+  c.role_j = (w >> 31) != 0;
+  c.st = step::seg_static(s, c.ok ? c.n : s.P);
+  return c;
+}
+
+// the part of camera entry c (dL/dR, dL/dt of its role) from records, with
+// the cameras' parameters qi, qj loaded beforehand
+__device__ __forceinline__ void cam_entry_part(const SegArgs& s, const CamEntry& c, const float* qi, const float* qj,
+                                               float* acc) {
+  float G[10];
+  step::rec_sum_serial(s.rec, c.st.r0, c.st.cnt, G);
+  const float gs = s.g_scale * (s.pair_scale ? s.pair_scale[c.n] : 1.f);
+  for (int k = 0; k < 9; ++k) G[k] *= gs;
+  float o[kSegGradEa];
+  step::pair_grad(s, c.n, c.st.cnt, G, qi, qj, o);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] += c.role_j ? o[12 + k] : o[k];
+}
+
+__device__ __forceinline__ void cam_entry_params(const SegArgs& s, const CamEntry& c, float* qi, float* qj) {
+  if (c.ok && c.st.cnt > 0) {
+    load_plain(s.params + 9 * c.st.ci, qi, 9);
+    load_plain(s.params + 9 * c.st.cj, qj, 9);
+  }
+}
+
+// 3 CTAs per SM: the 5M-pair scene's 300 camera CTAs and their loss CTAs run
+// in one wave
 template <bool ADAM>
-__global__ void __launch_bounds__(kThreads) k_cam_ea(EaCamArgs f) {
+__global__ void __launch_bounds__(kThreads, 3) k_cam_ea(EaCamArgs f) {
   __shared__ float red[kThreads / 32][12];
   const SegArgs& s = f.s;
   const CamUpdate& u = f.u;
@@ -90,16 +132,19 @@ __global__ void __launch_bounds__(kThreads) k_cam_ea(EaCamArgs f) {
   if ((int)blockIdx.x >= u.N) {   // loss slices: each image pair's loss term from its records
     const int g = blockIdx.x - u.N;
     const int sc = step::slice_scene(u.loss.sc_slice_off, u.loss.S, g);
-    const int n0 = u.loss.sc_pair_off[sc];
+    int j, k;
+    step::slice_terms(u.loss, sc, g, j, k);
+    step::RecRanges R;
+    step::rec_ranges(s, u.loss.sc_pair_off[sc], j, k, R);   // static: before the wait
     pdl_wait();
-    step::loss_slice(u.loss, sc, g, 0, [&](int j, int k, float* v) { step::fill_from_records(s, n0, j, k, v); });
+    step::loss_slice(u.loss, sc, g, 0, [&](int, int kk, float* v) { step::fill_from_records(s, R, kk, v); });
     return;
   }
   const int c = blockIdx.x, t = threadIdx.x, lane = t & 31;
-  // static: the first incident image pair of this thread, before the wait
+  // static: this thread's first two incident image pairs, before the wait
   const int b = u.cam_seg_off[c], e = u.cam_seg_off[c + 1];
-  int entry = (b + t < e) ? __ldg(u.cam_seg + b + t) : -1;
-  step::SegStatic st = step::seg_static(s, entry == -1 ? s.P : (int)((unsigned)entry & 0x7fffffffu));
+  const CamEntry e0 = cam_entry(s, u.cam_seg, b + t, e);
+  const CamEntry e1 = cam_entry(s, u.cam_seg, b + t + kThreads, e);
   pdl_wait();
   const size_t off = (size_t)c * 9;
   float p[9];
@@ -115,26 +160,18 @@ __global__ void __launch_bounds__(kThreads) k_cam_ea(EaCamArgs f) {
   float acc[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = 0.f;
-  for (int idx = b + t; idx < e; idx += kThreads) {
-    if (idx != b + t) {
-      entry = __ldg(u.cam_seg + idx);
-      st = step::seg_static(s, (int)((unsigned)entry & 0x7fffffffu));
-    }
-    const int n = (int)((unsigned)entry & 0x7fffffffu);
-    const bool role_j = ((unsigned)entry >> 31) != 0;
+  // both entries' parameters first, then their records and chain rules, in
+  // CSR order
+  float qi0[9], qj0[9], qi1[9], qj1[9];
+  cam_entry_params(s, e0, qi0, qj0);
+  cam_entry_params(s, e1, qi1, qj1);
+  if (e0.ok) cam_entry_part(s, e0, qi0, qj0, acc);
+  if (e1.ok) cam_entry_part(s, e1, qi1, qj1, acc);
+  for (int idx = b + t + 2 * kThreads; idx < e; idx += kThreads) {
+    const CamEntry en = cam_entry(s, u.cam_seg, idx, e);
     float qi[9], qj[9];
-    if (st.cnt > 0) {
-      load_plain(s.params + 9 * st.ci, qi, 9);
-      load_plain(s.params + 9 * st.cj, qj, 9);
-    }
-    float G[10];
-    step::rec_sum_serial(s.rec, st.r0, st.cnt, G);
-    const float gs = s.g_scale * (s.pair_scale ? s.pair_scale[n] : 1.f);
-    for (int k = 0; k < 9; ++k) G[k] *= gs;
-    float o[kSegGradEa];
-    step::pair_grad(s, n, st.cnt, G, qi, qj, o);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] += role_j ? o[12 + k] : o[k];
+    cam_entry_params(s, en, qi, qj);
+    cam_entry_part(s, en, qi, qj, acc);
   }
   step::cam_reduce<12>(acc, red);
   if (t < 32) step::cam_apply<2, ADAM>(u, off, p, m, v, acc, lane);

@@ -442,7 +442,7 @@ void launch_trn_pairs(const float* o, const int* pi, const int* pj, const float*
 // loss reductions in slices of image pairs (fm_step.cuh): the loss of scene
 // s is summed by ceil(P_s / 1024) CTAs, the last of which adds their sums
 constexpr int kLossCntStride = 32;   // ints between two arrival counters: a 128-B line each
-constexpr int kLossSlice = 1024;     // image pairs per slice
+constexpr int kLossSlice = 256;      // image pairs per slice (two per thread)
 struct LossArgs {
   const int* sc_pair_off;  // [S+1] image-pair range of each scene
   const int* sc_slice_off; // [S+1] first slice of each scene

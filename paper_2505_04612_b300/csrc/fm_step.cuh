@@ -345,35 +345,51 @@ __device__ __forceinline__ void fill_stored(const float* x, int j, int k, float*
   for (int u = 0; u < kPerThread; ++u) v[u] = (u < k) ? x[j + u * kThreads] : 0.f;
 }
 
-// fill of image pairs' loss terms formed from their records, as
-// segment_pair forms seg_loss (the record sum's order, then an uncontracted
-// product with the normalisers): the ranges of all k image pairs first, then
-// the first block of records of every one of them, predicated loads with no
-// branch between them, so that they are all in flight together; further
-// blocks (image pairs of more than eight records) after that.
-__device__ __forceinline__ void fill_from_records(const SegArgs& s, int n0, int j, int k, float* v) {
+// Loss terms formed from records, as segment_pair forms seg_loss (the record
+// sum's order, then an uncontracted product with the normalisers), in two
+// parts: rec_ranges reads the static range and normaliser of each of the
+// thread's k image pairs (before the dependency wait), fill_from_records the
+// records: the first block of every image pair with predicated loads and no
+// branch between them, so that they are all in flight together, then any
+// further blocks (image pairs of more than eight records).
+struct RecRanges {
   int r0[kPerThread], cnt[kPerThread];
+  float scale[kPerThread];
+};
+
+__device__ __forceinline__ void rec_ranges(const SegArgs& s, int n0, int j, int k, RecRanges& R) {
 #pragma unroll
   for (int u = 0; u < kPerThread; ++u) {
     const int n = n0 + j + u * kThreads;
-    r0[u] = (u < k) ? s.seg_rec[2 * n] : 0;
-    cnt[u] = (u < k) ? s.seg_rec[2 * n + 1] : 0;
+    R.r0[u] = (u < k) ? s.seg_rec[2 * n] : 0;
+    R.cnt[u] = (u < k) ? s.seg_rec[2 * n + 1] : 0;
+    R.scale[u] = s.l_scale * ((u < k && s.pair_scale) ? s.pair_scale[n] : 1.f);
   }
+}
+
+__device__ __forceinline__ void fill_from_records(const SegArgs& s, const RecRanges& R, int k, float* v) {
   float q[kPerThread][kSegLanes];
 #pragma unroll
-  for (int u = 0; u < kPerThread; ++u) rec_loss_load(s.rec, r0[u], cnt[u], q[u]);
+  for (int u = 0; u < kPerThread; ++u) rec_loss_load(s.rec, R.r0[u], R.cnt[u], q[u]);
 #pragma unroll
   for (int u = 0; u < kPerThread; ++u) {
     float G = 0.f;
     G += rec_loss_block(q[u]);
-    for (int b0 = kSegLanes; b0 < cnt[u]; b0 += kSegLanes) {
+    for (int b0 = kSegLanes; b0 < R.cnt[u]; b0 += kSegLanes) {
       float w[kSegLanes];
-      rec_loss_load(s.rec, r0[u] + b0, cnt[u] - b0, w);
+      rec_loss_load(s.rec, R.r0[u] + b0, R.cnt[u] - b0, w);
       G += rec_loss_block(w);
     }
-    const float ps = (u < k && s.pair_scale) ? s.pair_scale[n0 + j + u * kThreads] : 1.f;
-    v[u] = (u < k) ? __fmul_rn(G, s.l_scale * ps) : 0.f;
+    v[u] = (u < k) ? __fmul_rn(G, R.scale[u]) : 0.f;
   }
+}
+
+// the terms of global slice g held by this thread: first term j, count k
+__device__ __forceinline__ void slice_terms(const LossArgs& L, int sc, int g, int& j, int& k) {
+  const int n = L.sc_pair_off[sc + 1] - L.sc_pair_off[sc];
+  const int j0 = (g - L.sc_slice_off[sc]) * kSlice, j1 = min(n, j0 + kSlice);
+  j = j0 + (int)threadIdx.x;
+  k = max(0, (j1 - j + kThreads - 1) / kThreads);
 }
 
 }  // namespace step
