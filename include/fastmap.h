@@ -701,7 +701,7 @@ typedef struct {
                                   (a thread's pairs never cross an image-pair
                                   end; a warp run is 32 threads' pairs) */
   int32_t ctas_per_sm;         /* persistent CTAs per SM; 0 = as many as fit */
-  float us_per_eval;           /* fm_autotune: fastest time of the chosen one */
+  float us_per_eval;           /* fm_autotune: mean time of the chosen one */
 } fm_tuning;
 
 /* Sets / reads the configuration (changing pairs_per_lane rebuilds the
@@ -713,8 +713,9 @@ fm_status fm_get_tuning(const fm_problem* problem, fm_tuning* tuning);
  * epipolar parameters, or generated parameters when none are set) for the
  * three tiles and every CTA count per SM that fits, `repeats` times each
  * (CTA counts in round robin), every launch after an L2 flush and a 0.2 ms
- * device idle, and keeps the configuration with the fastest single launch
- * (noise only adds time).  The choice changes no result beyond the order of
+ * device idle, and keeps the configuration with the lowest mean time (event
+ * timestamps come in steps of about 2 us on the B300, so single fastest
+ * launches tie).  The choice changes no result beyond the order of
  * additions inside an image pair's records.  Synchronises. */
 fm_status fm_autotune(fm_problem* problem, int32_t repeats, fm_tuning* best);
 

@@ -2291,14 +2291,15 @@ fm_status fm_autotune(fm_problem* pr, int32_t repeats, fm_tuning* best_out) {
         pr->k_launches[fm::kKEaDirect] += 1;
       }
     cudaError_t ce = cudaStreamSynchronize(s);
-    // the fastest sample of each CTA count: noise only adds time
-    std::vector<float> fastest(max_c + 1, 3.4e38f);
+    // the mean over the samples of each CTA count: event timestamps come in
+    // steps of about 2 us on this part, so minima tie; means resolve below that
+    std::vector<float> fastest(max_c + 1, 0.f);
     q = 0;
     for (int k = 0; k < repeats && ce == cudaSuccess; ++k)
       for (int c = 1; c <= max_c && ce == cudaSuccess; ++c, q += 2) {
         float t = 0.f;
         ce = cudaEventElapsedTime(&t, ev[q], ev[q + 1]);
-        fastest[c] = std::min(fastest[c], 1000.f * t);
+        fastest[c] += 1000.f * t / (float)repeats;
       }
     if (ce != cudaSuccess) {
       st = fail(pr, FM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
