@@ -54,8 +54,8 @@ def args_():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2_5m", help="c2_5m (default), batch_c4, learned_c5, mlp_c2_5m, stages_c2_5m, distortion_c2_5m or "
-                         "tracks_c2_5m")
+    ap.add_argument("--config", default="c2_5m", help="c2_5m (default), batch_c4, learned_c5, mlp_c2_5m, stages_c2_5m, "
+                         "compact_steps, distortion_c2_5m or tracks_c2_5m")
     ap.add_argument("--train-scenes", type=int, default=200)
     ap.add_argument("--eval-cams", type=int, default=3000)
     ap.add_argument("--eval-points", type=int, default=1_000_000)
@@ -67,6 +67,8 @@ def args_():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autograd-modes", action="store_true",
                     help="skip the autograd forward/backward comparison (after the timed step)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the direct kernel's roofline on the 20M-pair problem (after the timed step)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -185,6 +187,28 @@ def make_workload(config, seed):
     rng = np.random.default_rng(1000 + seed)
     p = p + rng.normal(0.0, 0.01, size=p.shape)
     return sc, p.astype(np.float32)
+
+
+def rotation_error_deg(R_est, R_gt):
+    """Accuracy metric of a solve: per-camera rotation angle between R_est and
+    R_gt after the global rotation that best aligns the two sets (orthogonal
+    Procrustes on the stacked matrices; the solution's gauge is free)."""
+    U, _, Vt = np.linalg.svd(np.einsum("nki,nkj->ij", R_gt, R_est))
+    G = U @ np.diag([1.0, 1.0, np.sign(np.linalg.det(U @ Vt))]) @ Vt
+    cos = 0.5 * (np.einsum("nij,nij->n", R_gt @ G, R_est) - 1.0)
+    return np.degrees(np.arccos(np.clip(cos, -1.0, 1.0)))
+
+
+def centre_error(c_est, c_gt):
+    """Accuracy metric of a solve: per-camera centre distance after the
+    similarity (scale, rotation, shift) that best maps c_est onto c_gt in the
+    least-squares sense (closed form from the SVD of the cross-covariance)."""
+    A, B = c_est - c_est.mean(0), c_gt - c_gt.mean(0)
+    U, S, Vt = np.linalg.svd(B.T @ A)
+    D = np.diag([1.0, 1.0, np.sign(np.linalg.det(U @ Vt))])
+    Q = U @ D @ Vt
+    scale = np.trace(np.diag(S) @ D) / np.sum(A * A)
+    return np.linalg.norm(scale * A @ Q.T + c_gt.mean(0) - c_gt, axis=1)
 
 
 def _oracle_worker(conn, shard):
@@ -408,6 +432,38 @@ def autograd_modes(pr, p_dev, flush, steps, warmup, Z):
     return out
 
 
+def roofline_large(sc, params, dev, steps, warmup):
+    """k_ea_direct where launch and start-up latency matter little: the
+    workload scene four times over, as four scenes of one problem (4 x Z
+    keypoint pairs, 64 B x Z of keypoints, far beyond the 126 MB L2, so no
+    flush is needed between launches), autotuned, direct L1 steps timed with
+    the library's per-kernel events; achieved = 16 B x pairs / mean launch."""
+    import torch
+    from paper_2505_04612_b300 import fastmap as F
+    from synthetic.scenes import concat_scenes
+    big = concat_scenes([sc] * 4)
+    with F.problem_from_scene(big) as pr:
+        pr.set_params(F.FM_STAGE_EPIPOLAR, torch.from_numpy(np.concatenate([params] * 4).reshape(-1)).to(dev))
+        pr.set_ea_loss(F.FM_EA_L1)
+        tuning = pr.autotune(repeats=3)
+        for _ in range(max(warmup, 1)):
+            pr.step(F.FM_STAGE_EPIPOLAR, 1, lr=1e-4)
+        torch.cuda.synchronize()
+        pr.timing(True)
+        for _ in range(steps):
+            torch.cuda._sleep(200_000)   # the host queues ahead of the device
+            pr.step(F.FM_STAGE_EPIPOLAR, 1, lr=1e-4)
+        kt = pr.timing_read()
+        pr.timing(False)
+    n, ms = kt.get("k_ea_direct", (0, 0.0))
+    avg_us = 1e3 * ms / max(n, 1)
+    Zb = big.n_kp
+    return {"kernel": "k_ea_direct", "workload": f"c2_5m x 4 scenes in one problem: {Zb} keypoint pairs, "
+                                                 f"{big.n_pairs} image pairs, {16 * Zb / 1e6:.0f} MB of keypoints",
+            "bytes_per_launch": BYTES_PER_PAIR * Zb, "avg_launch_us": avg_us, "launches": n,
+            "achieved": BYTES_PER_PAIR * Zb / (avg_us * 1e-6) / 1e9, "tuning": tuning}
+
+
 def run_batch(a):
     """Batched solving (many scenes of uneven size in one problem) against
     solving the same scenes one problem at a time, on one GPU.
@@ -493,12 +549,11 @@ def run_batch(a):
         ts, _ = solve_time(ps)
         solve_s += ts
         ps.close()
-    from oracle.solve import rotation_errors_deg
     rot_err = []
     for k, sc in enumerate(scenes):
         sl = slice(b.scene_cam_off[k], b.scene_cam_off[k + 1])
         ok = out_b["cam_valid"][sl]     # the largest connected component of the scene's view graph
-        rot_err.append(float(rotation_errors_deg(out_b["R"][sl][ok].astype(np.float64), sc.R_gt[ok]).mean()))
+        rot_err.append(float(rotation_error_deg(out_b["R"][sl][ok].astype(np.float64), sc.R_gt[ok]).mean()))
     line = {
         "metric": METRIC, "value": Z / (step_b * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": step_b, "higher_is_better": True, "scaling": "weak",
@@ -518,6 +573,67 @@ def run_batch(a):
         "gpu_launches_batched_solve": int(sum(v[0] for v in kt.values())),
         "tuning_batched": tuning,
     }
+    print(json.dumps(line), flush=True)
+
+
+# (name, cameras, points, mean track length) of the compact-step scenes:
+# seeded c2 geometry giving ~5k, ~45k and ~560k image pairs
+COMPACT_SIZES = (("5k", 260, 26_000, 4.0), ("50k", 900, 110_000, 5.0), ("500k", 3000, 450_000, 8.0))
+
+
+def run_compact(a):
+    """--config compact_steps: the paper's per-iteration form of epipolar
+    adjustment (Sec. 3.3 compact form, Eqs. 8 and 15-17; Tab. kernel_fusion
+    times this step at 5k, 50k and 500k image pairs) on seeded scenes of the
+    c2 geometry sized to those image-pair counts: one fm_step iteration of
+    FM_EA_COMPACT (k_ea_compact: e_n^T W_n e_n and its chain rule per image
+    pair, then k_cam: per-camera sums, 6D adjoint, Adam), microseconds per
+    iteration under captured-graph replay (iterations back to back, CUDA events
+    around the call).  Algorithmic bytes: the 256 B of each image pair's
+    centred quadratic form read once per iteration (the cameras' 9 floats are
+    gathered from L2).  The paper's fused-CUDA times on an A6000 (Tab.
+    kernel_fusion, 4.05 GHz host) are quoted beside them as context."""
+    import torch
+    from paper_2505_04612_b300 import build as B
+    B.build()
+    from paper_2505_04612_b300 import fastmap as F
+    from synthetic.scenes import scene_c2
+    dev = torch.device("cuda", 0)
+    paper_ms = {"5k": 0.05, "50k": 0.14, "500k": 1.16}
+    sizes = COMPACT_SIZES
+    iters = 16 * max(4, a.steps)            # whole graphs; +1: the first iteration of a call runs directly
+    rows = {}
+    for name, n_cams, n_points, track in sizes:
+        t0 = time.time()
+        sc = scene_c2(seed=a.seed, n_cams=n_cams, n_points=n_points, track_mean=track)
+        gen_s = time.time() - t0
+        p = np.concatenate([sc.R_gt[:, :, 0], sc.R_gt[:, :, 1], sc.t_gt], axis=1)
+        p = (p + np.random.default_rng(1000 + a.seed).normal(0.0, 0.01, size=p.shape)).astype(np.float32)
+        with F.problem_from_scene(sc) as pr:
+            pr.set_params(F.FM_STAGE_EPIPOLAR, torch.from_numpy(p.reshape(-1)).to(dev))
+            pr.reweight(0.05, 1e-5)                    # IRLS weights, W_n built at the next evaluation
+            pr.set_ea_loss(F.FM_EA_COMPACT)
+            pr.step(F.FM_STAGE_EPIPOLAR, 16 * max(3, a.warmup) + 1, lr=1e-4)   # builds W_n, captures the graph
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pr.step(F.FM_STAGE_EPIPOLAR, iters + 1, lr=1e-4)
+            e1.record()
+            torch.cuda.synchronize()
+            us = 1e3 * e0.elapsed_time(e1) / (iters + 1)
+        peak, peak_kind = peaks()
+        gbs = 256 * sc.n_pairs / (us * 1e-6) / 1e9
+        rows[name] = {"n_img_pairs": sc.n_pairs, "n_cams": sc.n_cams, "n_kp_pairs": sc.n_kp,
+                      "us_per_iteration": us, "achieved_GBps": gbs, "frac_of_peak": gbs / peak,
+                      "paper_A6000_ms": paper_ms[name], "scene_generation_s": gen_s}
+    line = {"metric": "microseconds per compact epipolar iteration (a8 + a9) at the paper's image-pair counts",
+            "value": rows[sizes[-1][0]]["us_per_iteration"], "unit": "us/iteration (largest size)",
+            "n_gpus": 1, "steps": iters, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "compact_steps: seeded c2-geometry scenes sized to ~5k / 50k / 500k image pairs",
+                       "graphs": "16-iteration captured graphs, iterations back to back"},
+            "roofline": {"bound": "hbm", "unit": "GB/s", "bytes_per_image_pair": 256,
+                         "peak": peaks()[0], "peak_kind": f"{peaks()[1]} copy bandwidth"},
+            "sizes": rows}
     print(json.dumps(line), flush=True)
 
 
@@ -545,7 +661,7 @@ def run_stages(a):
     rng = np.random.default_rng(7)
     R = sc.R_gt
     p6 = np.concatenate([R[:, :, 0], R[:, :, 1]], axis=1) + rng.normal(0, 0.02, (sc.n_cams, 6))
-    iters = 16 * max(1, a.steps)
+    iters = 16 * max(4, a.steps)            # whole graphs; +1: the first iteration of a call runs directly
     out = {}
     with F.problem_from_scene(sc, rel_R=Rij.astype(np.float32), rel_t=tij.astype(np.float32)) as pr:
         pr.autotune(repeats=5)
@@ -929,7 +1045,6 @@ def run_learned(a):
     from paper_2505_04612_b300 import fastmap as F
     from paper_2505_04612_b300 import learned as Lm
     from synthetic.scenes import concat_scenes, gt_relative_poses, scene_c2
-    from oracle.solve import centre_errors, rotation_errors_deg
     t0 = time.time()
     rng = np.random.default_rng(1000)
     train = [scene_c2(seed=1000 + k, n_cams=int(rng.integers(60, 151)), n_points=int(rng.integers(8000, 30001)),
@@ -973,8 +1088,8 @@ def run_learned(a):
         Rr = out["R"].astype(np.float64)
         c = -np.einsum("nba,nb->na", Rr, out["t"].astype(np.float64))
         scale = np.mean(np.linalg.norm(ev.centers_gt[ok] - ev.centers_gt[ok].mean(0), axis=1))
-        return {"wall_s": dt, "rotation_error_deg": float(rotation_errors_deg(Rr[ok], ev.R_gt[ok]).mean()),
-                "centre_error_rel": float(centre_errors(c[ok], ev.centers_gt[ok]).mean() / scale),
+        return {"wall_s": dt, "rotation_error_deg": float(rotation_error_deg(Rr[ok], ev.R_gt[ok]).mean()),
+                "centre_error_rel": float(centre_error(c[ok], ev.centers_gt[ok]).mean() / scale),
                 "ea_rounds": rounds}
 
     plain = solve(False, 5)
@@ -1021,6 +1136,8 @@ def main():
         return run_tracks(a)
     if a.config == "stages_c2_5m":
         return run_stages(a)
+    if a.config == "compact_steps":
+        return run_compact(a)
     import torch
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -1117,6 +1234,7 @@ def main():
     losses = pr.loss_history(8)
 
     modes = None if a.no_autograd_modes else autograd_modes(pr, p_dev, flush, a.steps, a.warmup, Z)
+    large = None if a.no_large else roofline_large(sc, params, dev, a.steps, a.warmup)
 
 
     if rank == 0:
@@ -1145,7 +1263,11 @@ def main():
             "last_losses": losses[-3:],
             "tuning": tuning,
             "autograd_modes": modes,
+            "roofline_large": large,
         }
+        if large:
+            large.update(peak=peak, frac=large["achieved"] / peak, unit="GB/s",
+                         peak_kind=f"{peak_kind} copy bandwidth")
         if not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(sc, params, a.cpu_seconds)
         print(json.dumps(line), flush=True)
