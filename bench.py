@@ -802,6 +802,9 @@ def run_mlp(a):
             kt = pr.timing_read()
         pr.timing(False)
         pmean = float(prob.mean().item())
+        feat, _, _ = pr.mlp_eval(want_feat=True, want_resid=False, want_prob=False)
+    train = mlp_training_time(feat, (prob >= prob.median()).float(), a.steps, a.warmup, flush)
+    del feat
     n_t, ms_t = kt.get("k_mlp_pair_tables", (0, 0.0))
     n_i, ms_i = kt.get("k_mlp_infer", (0, 0.0))
     step_ms = (ms_t + ms_i) / max(a.steps, 1)
@@ -822,8 +825,51 @@ def run_mlp(a):
                          "flop_per_pair": flop_per_pair, "avg_launch_us": infer_us,
                          "note": "limited by the exact-erf GELUs on the FP32 pipe, not by the tensor cores"},
             "kernels_us_per_launch": {k: 1e3 * v[1] / max(v[0], 1) for k, v in kt.items()},
-            "gpu_launches": int(n_t + n_i), "clocks": clk.summary(), "mean_probability": pmean}
+            "gpu_launches": int(n_t + n_i), "clocks": clk.summary(), "mean_probability": pmean,
+            "training": train}
+    train["roofline"].update(peak=pk, frac=train["roofline"]["achieved"] / pk)
     print(json.dumps(line), flush=True)
+
+
+# network contractions per row: forward 2 (8*64 + 64*64), backward dh1 = dz2 W2^T
+# 2 (64*64), dW2 = h1^T dz2 2 (64*64), dW1 = x^T dz1 2 (8*64)
+MLP_TRAIN_FLOP_PER_ROW = 2 * (8 * 64 + 64 * 64) + 2 * (64 * 64) + 2 * (64 * 64) + 2 * (8 * 64)
+
+
+def mlp_training_time(x, y, steps, warmup, flush):
+    """The trainer's loss + gradient (k_mlp_grad_tc: the network forward and
+    backward on tcgen05, per-CTA partials; k_mlp_reduce: their fixed-order
+    sum) over all feature rows of the scene, CUDA events around each call
+    on the trainer's stream, L2 flushed before each."""
+    import torch
+    from paper_2505_04612_b300 import fastmap as F
+    B = int(y.numel())
+    tr = F.MlpTrainer(B)
+    from paper_2505_04612_b300 import learned as Lm
+    tr.set_params(Lm.init_params(3).astype(np.float32))
+    for _ in range(max(warmup, 1)):
+        tr.loss_grad(x, y)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(max(steps, 3)):
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        L, _ = tr.loss_grad(x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e3)
+    loss = float(L.item())
+    tr.close()
+    us = float(np.mean(times))
+    tiles = (B + 127) // 128
+    achieved = MLP_TRAIN_FLOP_PER_ROW * B / (us * 1e-6) / 1e12
+    return {"rows": B, "us_per_call": us, "us_per_call_min": float(np.min(times)), "rows_per_s": B / (us * 1e-6),
+            "tiles_of_128_rows": tiles, "loss": loss,
+            "roofline": {"bound": "tensor", "achieved": achieved, "unit": "TFLOP/s", "kernel": "k_mlp_grad_tc + k_mlp_reduce",
+                         "flop_per_row": MLP_TRAIN_FLOP_PER_ROW,
+                         "note": "the exact-erf GELUs and their derivatives (256 erf + 128 exp per row) on the "
+                                 "FP32 pipe bound it, not the tensor cores"}}
 
 
 DIST_OPS_PER_EVAL = 99    # FP32 operations per (candidate, keypoint pair) of k_dist_errors' two passes

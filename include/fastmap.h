@@ -630,8 +630,8 @@ fm_status fm_solve(fm_problem* problem, const fm_solve_opts* opts, fm_result* re
  * flat: W1 [8][64] (feature-major), b1 [64], W2 [64][64] (input-major),
  * b2 [64], w3 [64], b3 [1].  The products run on the tensor cores with
  * bfloat16 operands (x, W1, h1, W2; in training also dz2 and dz1) and
- * float32 accumulation: inference on tcgen05 (accumulators in tensor
- * memory), training on mma.sync. */
+ * float32 accumulation, inference and training alike on tcgen05
+ * (accumulators in tensor memory). */
 #define FM_MLP_N_PARAMS 4801
 #define FM_MLP_N_FEATURES 8
 
@@ -674,7 +674,10 @@ fm_status fm_mlp_reweight(fm_problem* problem, float iter_frac, float delta, flo
  * on feature rows x [B][8] and labels y [B] in {0, 1} (device pointers) with
  * the mean binary cross-entropy mean(softplus(o) - y o).  Errors are
  * reported by fm_last_error(NULL).  Gradients are deterministic (fixed-order
- * sums, no atomics). */
+ * sums, no atomics).  The loss and gradient run asynchronously: when a
+ * bounded wait of the tensor-core kernel runs out, the loss is NaN (and so
+ * are the parameters after a step), and the next fm_mlp_trainer_get_params
+ * to the host or fm_mlp_trainer_forward returns FM_ERR_TIMEOUT. */
 typedef struct fm_mlp_trainer fm_mlp_trainer;
 fm_status fm_mlp_trainer_create(int64_t max_batch, void* cuda_stream, fm_mlp_trainer** out);
 void fm_mlp_trainer_destroy(fm_mlp_trainer* trainer);

@@ -2927,8 +2927,18 @@ fm_status fm_mlp_trainer_get_params(fm_mlp_trainer* t, float* theta, int32_t on_
   if (!t || !theta) return trainer_fail(FM_ERR_INVALID_ARG, "trainer and theta are required");
   cudaError_t e = cudaMemcpyAsync(theta, t->theta, sizeof(float) * fm::kMlpParams,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, t->stream);
-  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(t->stream);
+  if (on_device) {
+    if (e != cudaSuccess) return trainer_fail(FM_ERR_CUDA, std::string("trainer: ") + cudaGetErrorString(e));
+    return FM_OK;
+  }
+  int bits = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, t->err, sizeof(int), cudaMemcpyDeviceToHost, t->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(t->stream);
   if (e != cudaSuccess) return trainer_fail(FM_ERR_CUDA, std::string("trainer: ") + cudaGetErrorString(e));
+  if (bits & fm::kErrMlpTimeout) {
+    cudaMemsetAsync(t->err, 0, sizeof(int), t->stream);
+    return trainer_fail(FM_ERR_TIMEOUT, "a bounded wait of the tensor-core network kernel ran out");
+  }
   return FM_OK;
 }
 
@@ -2944,7 +2954,7 @@ fm_status fm_mlp_trainer_loss_grad(fm_mlp_trainer* t, const float* x, const floa
   fm_status st = trainer_check_batch(t, x, B);
   if (st != FM_OK) return st;
   if (B > 0 && !y) return trainer_fail(FM_ERR_INVALID_ARG, "y_dev is NULL");
-  fm::launch_mlp_grad(t->theta, x, y, B, t->partial, grad_dev, loss_dev, t->stream);
+  fm::launch_mlp_grad(t->theta, x, y, B, t->partial, grad_dev, loss_dev, t->err, t->stream);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return trainer_fail(FM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   return FM_OK;
@@ -2957,7 +2967,7 @@ fm_status fm_mlp_trainer_step(fm_mlp_trainer* t, const float* x, const float* y,
   if (B > 0 && !y) return trainer_fail(FM_ERR_INVALID_ARG, "y_dev is NULL");
   if (!o || !(o->lr > 0.f && o->beta1 >= 0.f && o->beta1 < 1.f && o->beta2 >= 0.f && o->beta2 < 1.f && o->eps >= 0.f))
     return trainer_fail(FM_ERR_INVALID_ARG, "invalid Adam options");
-  fm::launch_mlp_grad(t->theta, x, y, B, t->partial, t->grad, loss_dev ? loss_dev : t->loss, t->stream);
+  fm::launch_mlp_grad(t->theta, x, y, B, t->partial, t->grad, loss_dev ? loss_dev : t->loss, t->err, t->stream);
   t->step += 1;
   fm::launch_mlp_adam(t->theta, t->grad, t->m, t->v, t->step, o->lr, o->beta1, o->beta2, o->eps, t->stream);
   cudaError_t e = cudaGetLastError();

@@ -389,9 +389,6 @@ void launch_focal_dlde(const fm_problem* pr, const float* params, const float* G
 void launch_focal_cam(const fm_problem* pr, const float* dphi, float* gphi, cudaStream_t s);
 
 // learned weights (fm_mlp.cu)
-size_t mlp_grad_smem();
-int mlp_grad_parts(int64_t B);
-int mlp_part_stride();
 void launch_mlp_pair_tables(const fm_problem* pr, const float* params, const float* rel_t, float* tab,
                             cudaStream_t s);
 void launch_mask_from_prob(const float* prob, int64_t Z, float p_min, float* w, cudaStream_t s);
@@ -404,8 +401,15 @@ struct InferArgs;
 void launch_mlp_infer_tc(const InferArgs& a, int* err, int sm_count, cudaStream_t s);
 void launch_mlp_forward_tc(const float* theta, const float* x, int64_t B, float* logit, int* err, int sm_count,
                            cudaStream_t s);
+// training on tcgen05 (fm_mlp_tc.cu): per-CTA partials of the loss and
+// gradient of a batch, [mlp_grad_parts(B)][mlp_part_stride()]
+int mlp_grad_parts(int64_t B);
+int mlp_part_stride();
+void launch_mlp_grad_tc(const float* theta, const float* x, const float* y, int64_t B, float* partial, int* err,
+                        cudaStream_t s);
+// the partials and their fixed-order sum into grad [kMlpParams] and loss
 void launch_mlp_grad(const float* theta, const float* x, const float* y, int64_t B, float* partial, float* grad,
-                     float* loss, cudaStream_t s);
+                     float* loss, int* err, cudaStream_t s);
 void launch_mlp_adam(float* theta, const float* grad, float* m, float* v, int step, float lr, float b1, float b2,
                      float eps, cudaStream_t s);
 

@@ -47,8 +47,11 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-@pytest.mark.parametrize("B", [1, 63, 64, 1000, 20000])
+@pytest.mark.parametrize("B", [1, 127, 128, 129, 1000, 20000, 100003])
 def test_loss_and_gradient_match_the_oracle(B):
+    """The tcgen05 training kernel: one row, a ragged tile, one full tile,
+    one row past it, and more 128-row tiles than resident CTAs (the weight
+    accumulators carried across a CTA's tiles in tensor memory)."""
     torch, F = _mods()
     G.lib_ready()
     x, y = _batch(B, B)
@@ -69,6 +72,17 @@ def test_loss_and_gradient_match_the_oracle(B):
     # the unquantised float64 gradient is within the bfloat16 error
     _, gf = M.loss_grad(th32, x32, y)
     assert G.rel_err(g, gf) < 3e-2
+    tr.close()
+
+
+def test_empty_batch_gives_zero_loss_and_gradient():
+    torch, F = _mods()
+    G.lib_ready()
+    tr = F.MlpTrainer(64)
+    tr.set_params(_theta(3))
+    L, g = tr.loss_grad(_dev(np.zeros((0, 8))), _dev(np.zeros(0)))
+    assert float(L.item()) == 0.0
+    assert not g.cpu().numpy().any()
     tr.close()
 
 
