@@ -18,6 +18,14 @@ another buffer, which evicts every input and leaves L2 holding clean, unrelated
 lines (a write alone would leave dirty lines whose write-back would then be
 charged to the timed kernel).
 
+After the timed steps the line gains sub-objects measured outside the timed
+interval: `autograd_modes` (the three forward/backward splits), `roofline_large`
+(k_ea_direct on four copies of the scene in one problem, 20M keypoint pairs,
+back to back), `time_to_accuracy` (the learned filter against the plain one:
+training on 50 small seeded scenes, then both solves of a 1000-camera,
+~6M-pair scene with 30% outliers, wall clock and accuracy) and
+`cpu_baseline` (the oracle on all host cores and on one).
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun (N > 1) every rank solves its own replica of the scene (the
@@ -69,6 +77,8 @@ def args_():
                     help="skip the autograd forward/backward comparison (after the timed step)")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the direct kernel's roofline on the 20M-pair problem (after the timed step)")
+    ap.add_argument("--no-tta", action="store_true",
+                    help="skip the learned-vs-plain time-to-accuracy comparison (after the timed step)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -621,11 +631,18 @@ def run_compact(a):
             e1.record()
             torch.cuda.synchronize()
             us = 1e3 * e0.elapsed_time(e1) / (iters + 1)
+            # per kernel, a second pass with the library's event pairs (plain
+            # launches: each pair brackets one kernel, ~4 us of event overhead)
+            pr.timing(True)
+            pr.step(F.FM_STAGE_EPIPOLAR, 16, lr=1e-4)
+            kt = pr.timing_read()
+            pr.timing(False)
         peak, peak_kind = peaks()
         gbs = 256 * sc.n_pairs / (us * 1e-6) / 1e9
         rows[name] = {"n_img_pairs": sc.n_pairs, "n_cams": sc.n_cams, "n_kp_pairs": sc.n_kp,
                       "us_per_iteration": us, "achieved_GBps": gbs, "frac_of_peak": gbs / peak,
-                      "paper_A6000_ms": paper_ms[name], "scene_generation_s": gen_s}
+                      "paper_A6000_ms": paper_ms[name], "scene_generation_s": gen_s,
+                      "kernels_us_per_launch": {k: 1e3 * v[1] / max(v[0], 1) for k, v in kt.items()}}
     line = {"metric": "microseconds per compact epipolar iteration (a8 + a9) at the paper's image-pair counts",
             "value": rows[sizes[-1][0]]["us_per_iteration"], "unit": "us/iteration (largest size)",
             "n_gpus": 1, "steps": iters, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
@@ -1067,34 +1084,41 @@ def cpu_distortion_baseline(sc, seconds):
             "sample": f"first {n} image pairs x 32 candidates ({done} evaluations) in {dt:.1f} s"}
 
 
-def run_learned(a):
+# the default line's time-to-accuracy comparison: 50 training scenes, an
+# evaluation scene of 1000 cameras and 100k points (~6M keypoint pairs, 30%
+# outliers); --config learned_c5 runs the full-size one
+TTA_TRAIN_SCENES, TTA_EVAL_CAMS, TTA_EVAL_POINTS = 50, 1000, 100_000
+
+
+def learned_vs_plain(seed, train_scenes, eval_cams, eval_points, eval_track, eval_outliers):
     """Time to accuracy, learned filter against the plain one (one GPU).
 
-    Training: `--train-scenes` seeded scenes with the geometry of scene_c2
+    Training: `train_scenes` seeded scenes with the geometry of scene_c2
     (N ~ U(60, 150) cameras, U(8k, 30k) points, 5-40% outliers, seeds from
     1000), solved with the plain method in batches; features captured where
     the learned solve evaluates the network, labels from the converged
     residuals; the network trained with the library's trainer.
-    Evaluation: one scene with N = `--eval-cams` cameras, `--eval-points`
-    points, track length 2 + Geometric (mean `--eval-track`), an outlier
-    fraction of `--eval-outliers` (default 0.3), relative rotations with 1 deg
-    noise.  The plain fm_solve (5 filtering
-    rounds) and the learned one (2 pruning passes, 1 round) are timed end to
-    end (wall clock around the call, after a warm-up solve); accuracy is the
-    mean rotation error and the mean camera-centre error (relative to the
-    scene's size, after a similarity alignment) over the connected cameras.
-    value = plain time / learned time when the learned solve is at least as
-    accurate on both, else null."""
+    Evaluation: one scene with N = `eval_cams` cameras, `eval_points`
+    points, track length 2 + Geometric (mean `eval_track`), an outlier
+    fraction of `eval_outliers`, relative rotations with 1 deg noise.  The
+    plain fm_solve (5 filtering rounds) and the learned one (2 pruning
+    passes, 1 round) are timed end to end (wall clock around the call, after
+    a warm-up solve); accuracy is the mean rotation error and the mean
+    camera-centre error (relative to the scene's size, after a similarity
+    alignment) over the connected cameras.  Returns a dict with the ratio
+    plain time / learned time when the learned solve is at least as accurate
+    on both, else None."""
     import torch
     from paper_2505_04612_b300 import build as B
     B.build()
     from paper_2505_04612_b300 import fastmap as F
     from paper_2505_04612_b300 import learned as Lm
     from synthetic.scenes import concat_scenes, gt_relative_poses, scene_c2
+    t_all = time.time()
     t0 = time.time()
     rng = np.random.default_rng(1000)
     train = [scene_c2(seed=1000 + k, n_cams=int(rng.integers(60, 151)), n_points=int(rng.integers(8000, 30001)),
-                      outlier_frac=float(rng.uniform(0.05, 0.4))) for k in range(a.train_scenes)]
+                      outlier_frac=float(rng.uniform(0.05, 0.4))) for k in range(train_scenes)]
     gen_train = time.time() - t0
     t0 = time.time()
     Xs, ys = [], []
@@ -1113,12 +1137,13 @@ def run_learned(a):
     torch.cuda.synchronize()
     train_s = time.time() - t0
     acc = float(((Lm.logits(theta, X) >= 0).float() == y).float().mean())
+    n_rows = int(y.numel())
     del X, y, Xs, ys
     t0 = time.time()
-    ev = scene_c2(seed=5000 + a.seed, n_cams=a.eval_cams, n_points=a.eval_points, outlier_frac=a.eval_outliers,
-                  track_mean=a.eval_track)
+    ev = scene_c2(seed=5000 + seed, n_cams=eval_cams, n_points=eval_points, outlier_frac=eval_outliers,
+                  track_mean=eval_track)
     gen_eval = time.time() - t0
-    R = gt_relative_poses(ev, rot_noise_deg=1.0, seed=a.seed)[0].astype(np.float32)
+    R = gt_relative_poses(ev, rot_noise_deg=1.0, seed=seed)[0].astype(np.float32)
 
     def solve(learned, rounds):
         with F.problem_from_scene(ev, rel_R=R) as pr:
@@ -1142,18 +1167,30 @@ def run_learned(a):
     learned = solve(True, 1)
     ok = (learned["rotation_error_deg"] <= plain["rotation_error_deg"] and
           learned["centre_error_rel"] <= plain["centre_error_rel"])
+    return {"speedup": plain["wall_s"] / learned["wall_s"] if ok else None,
+            "eval_scene": {"n_cams": ev.n_cams, "n_img_pairs": ev.n_pairs, "n_kp_pairs": ev.n_kp,
+                           "outlier_frac": eval_outliers, "n_points": eval_points},
+            "plain": plain, "learned": learned,
+            "training": {"scenes": len(train), "rows": n_rows, "rows_accuracy": acc,
+                         "bce_first_last": [losses[0], losses[-1]], "train_s": train_s, "data_s": data_s,
+                         "generation_s": gen_train + gen_eval},
+            "wall_s_total": time.time() - t_all}
+
+
+def run_learned(a):
+    """--config learned_c5: learned_vs_plain on the configured scene sizes."""
+    r = learned_vs_plain(a.seed, a.train_scenes, a.eval_cams, a.eval_points, a.eval_track, a.eval_outliers)
+    ev = r["eval_scene"]
     line = {
-        "metric": METRIC, "value": plain["wall_s"] / learned["wall_s"] if ok else None,
+        "metric": METRIC, "value": r["speedup"],
         "unit": "x (plain fm_solve wall time / learned fm_solve wall time, learned at least as accurate)",
         "n_gpus": 1, "higher_is_better": True, "dtype": "f32 (network: bf16 tensor cores, f32 accumulate)",
         "data": "synthetic",
-        "config": {"workload": f"learned_c5: eval scene {ev.n_cams} cameras, {ev.n_pairs} image pairs, "
-                               f"{ev.n_kp} keypoint pairs, {100 * a.eval_outliers:.0f}% outliers; "
-                               f"trained on {len(train)} scenes",
-                   "train_scenes": len(train), "train_rows": None},
-        "plain": plain, "learned": learned,
-        "training": {"rows_accuracy": acc, "bce_first_last": [losses[0], losses[-1]], "train_s": train_s,
-                     "data_s": data_s, "generation_s": gen_train + gen_eval},
+        "config": {"workload": f"learned_c5: eval scene {ev['n_cams']} cameras, {ev['n_img_pairs']} image pairs, "
+                               f"{ev['n_kp_pairs']} keypoint pairs, {100 * a.eval_outliers:.0f}% outliers; "
+                               f"trained on {r['training']['scenes']} scenes",
+                   "train_scenes": r["training"]["scenes"], "train_rows": r["training"]["rows"]},
+        "plain": r["plain"], "learned": r["learned"], "training": r["training"],
     }
     print(json.dumps(line), flush=True)
 
@@ -1245,7 +1282,11 @@ def main():
             pr.step(F.FM_STAGE_EPIPOLAR, 1, **adam)
             ev[k][1].record(stream)
         barrier()
-        return sum(e0.elapsed_time(e1) for e0, e1 in ev)
+        per_step.clear()
+        per_step.extend(e0.elapsed_time(e1) for e0, e1 in ev)
+        return sum(per_step)
+
+    per_step = []
 
     # end to end through the C ABI with pinned host buffers (params in, loss +
     # grad out), before the clock sampling below: once nvidia-smi has sampled
@@ -1272,6 +1313,7 @@ def main():
     launches = pr.timing_read()
     gpu_launches = int(sum(v[0] for v in launches.values()))
     total_ms = max_over_ranks(total_ms, world, dev)
+    step_ms = sorted(per_step)
     # pass B: per-kernel device time from the library's event pairs on its stream
     pr.timing(True)
     timed_pass()
@@ -1281,7 +1323,10 @@ def main():
 
     modes = None if a.no_autograd_modes else autograd_modes(pr, p_dev, flush, a.steps, a.warmup, Z)
     large = None if a.no_large else roofline_large(sc, params, dev, a.steps, a.warmup)
-
+    # time to accuracy, learned vs plain, at a size that fits about 25 s
+    tta = None
+    if rank == 0 and not a.no_tta:
+        tta = learned_vs_plain(a.seed, TTA_TRAIN_SCENES, TTA_EVAL_CAMS, TTA_EVAL_POINTS, 10.0, 0.3)
 
     if rank == 0:
         peak, peak_kind = peaks()
@@ -1294,6 +1339,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(sc, a),
+            "ms_per_step_min_median_max": [step_ms[0], step_ms[len(step_ms) // 2], step_ms[-1]],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": profiled_traffic(),
                          "kernel": "k_ea_direct", "bytes_per_launch": BYTES_PER_PAIR * Z,
@@ -1310,6 +1356,7 @@ def main():
             "tuning": tuning,
             "autograd_modes": modes,
             "roofline_large": large,
+            "time_to_accuracy": tta,
         }
         if large:
             large.update(peak=peak, frac=large["achieved"] / peak, unit="GB/s",

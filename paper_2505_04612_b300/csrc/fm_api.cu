@@ -603,7 +603,7 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   FM_ALLOC(pr, pr->scratch_params, 9 * (size_t)N);
   FM_ALLOC(pr, pr->scratch_grad, 9 * (size_t)N);
   FM_ALLOC(pr, pr->d_loss, (size_t)S);
-  FM_ALLOC(pr, pr->W, 64 * (size_t)P);
+  FM_ALLOC(pr, pr->W, 64 * (((size_t)P + 31) & ~(size_t)31));   // tiles of 32 image pairs
   FM_ALLOC(pr, pr->d_kept, (size_t)S);
   FM_ALLOC(pr, pr->merge_buf, 3 * (size_t)N + 4 * 64 * (size_t)S);
   FM_ALLOC(pr, pr->best_run, (size_t)N);

@@ -109,9 +109,16 @@ __global__ void k_pair_inv_from_counts(const unsigned long long* __restrict__ co
   inv[n] = c > 0 ? (float)(1.0 / (double)c) : 0.f;
 }
 
+// position of entry k (of 64) of image pair n in the tiled W
+__host__ __device__ __forceinline__ size_t w_index(int n, int k) {
+  return ((size_t)(n >> 5) * 64 + k) * 32 + (n & 31);
+}
+
 // one warp per image pair; lanes stride over its keypoint pairs, then a
 // butterfly reduction in fixed order.  Output per image pair (64 floats):
-// [0,45) W upper triangle, [45,54) b, [54] c, [55,64) e0.
+// [0,45) W upper triangle, [45,54) b, [54] c, [55,64) e0, stored tiled by 32
+// image pairs (w_index): entry k of the 32 pairs of a tile is one contiguous
+// 128-byte row, so k_ea_compact's warps read W with coalesced loads.
 __global__ void __launch_bounds__(128) k_w_build(const float4* __restrict__ kp, const float* __restrict__ w,
                                                  const int* __restrict__ seg_off,
                                                  const float4* __restrict__ seg_tab, int P,
@@ -152,7 +159,6 @@ __global__ void __launch_bounds__(128) k_w_build(const float4* __restrict__ kp, 
   }
 #pragma unroll
   for (int k = 0; k < 55; ++k) acc[k] = warp_sum(acc[k]);
-  float* out = W + (size_t)64 * n;
   // lanes write in parallel: lane l writes entries l and l + 32
   for (int k = lane; k < 64; k += 32) {
     float v = 0.f;
@@ -160,7 +166,7 @@ __global__ void __launch_bounds__(128) k_w_build(const float4* __restrict__ kp, 
     for (int j = 0; j < 55; ++j)
       if (j == k) v = acc[j];
     if (k >= 55) v = e0[k - 55];
-    out[k] = v;
+    W[w_index(n, k)] = v;
   }
 }
 
@@ -168,20 +174,32 @@ __device__ __forceinline__ int tri(int a, int c) {   // index of (a, c), a <= c,
   return a * 9 - (a * (a - 1)) / 2 + (c - a);
 }
 
+// one thread per image pair; a warp's 32 image pairs form one tile of W
+// (64 coalesced 128-byte rows), and the warp's 32 x 24 chain-rule outputs
+// leave through shared memory as one contiguous block
 template <bool STEP>
-__global__ void k_ea_compact(const float* __restrict__ W, const float* __restrict__ params,
-                             const int* __restrict__ pi, const int* __restrict__ pj, int P,
-                             const float* __restrict__ pair_inv_z, float* __restrict__ seg_grad,
-                             float* __restrict__ seg_loss, int* step_counter) {
+__global__ void __launch_bounds__(128) k_ea_compact(const float* __restrict__ W, const float* __restrict__ params,
+                                                    const int* __restrict__ pi, const int* __restrict__ pj, int P,
+                                                    const float* __restrict__ pair_inv_z,
+                                                    float* __restrict__ seg_grad, float* __restrict__ seg_loss,
+                                                    int* step_counter) {
+  __shared__ float stage[4][32 * (kSegGradEa + 1)];
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n0 = n - lane;   // the warp's first image pair
   if (STEP && step_counter && n == 0) *step_counter += 1;
-  if (n >= P) return;
-  const float inv_z = pair_inv_z[n];   // normaliser of the image pair's scene
+  if (n0 >= P) return;
+  const bool mine = n < P;
+  const int nn = mine ? n : n0;   // lanes past the end repeat the first pair; nothing of theirs is stored
+  const float inv_z = pair_inv_z[nn];   // normaliser of the image pair's scene
+  float Wn[64];
+  const float* Wt = W + w_index(nn, 0);
+#pragma unroll
+  for (int k = 0; k < 64; ++k) Wn[k] = Wt[32 * k];
   PairGeo g;
-  pair_geometry(params + 9 * pi[n], params + 9 * pj[n], g);
+  pair_geometry(params + 9 * pi[nn], params + 9 * pj[nn], g);
   float e[9];
   essential(g, e);
-  const float* Wn = W + (size_t)64 * n;
   float d[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) d[a] = e[a] - Wn[55 + a];
@@ -200,15 +218,19 @@ __global__ void k_ea_compact(const float* __restrict__ W, const float* __restric
     q = fmaf(d[a], Wd[a], q);
     lb = fmaf(d[a], Wn[45 + a], lb);
   }
-  seg_loss[n] = (Wn[54] + 2.f * lb + q) * inv_z;
+  if (mine) seg_loss[n] = (Wn[54] + 2.f * lb + q) * inv_z;
   float G[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) G[a] = 2.f * inv_z * (Wn[45 + a] + Wd[a]);
   float o[kSegGradEa];
   pair_backward(g, G, o);
-  float* out = seg_grad + (size_t)kSegGradEa * n;
+  float* st = stage[warp];
 #pragma unroll
-  for (int k = 0; k < kSegGradEa; ++k) out[k] = o[k];
+  for (int k = 0; k < kSegGradEa; ++k) st[lane * (kSegGradEa + 1) + k] = o[k];
+  __syncwarp();
+  const int cnt = min(32, P - n0) * kSegGradEa;
+  float* out = seg_grad + (size_t)kSegGradEa * n0;
+  for (int i = lane; i < cnt; i += 32) out[i] = st[(i / kSegGradEa) * (kSegGradEa + 1) + i % kSegGradEa];
 }
 
 }  // namespace
