@@ -704,7 +704,8 @@ typedef struct {
                                   (a thread's pairs never cross an image-pair
                                   end; a warp run is 32 threads' pairs) */
   int32_t ctas_per_sm;         /* persistent CTAs per SM; 0 = as many as fit */
-  float us_per_eval;           /* fm_autotune: mean time of the chosen one */
+  float us_per_eval;           /* fm_autotune: mean time of one evaluation
+                                  with the chosen one */
 } fm_tuning;
 
 /* Sets / reads the configuration (changing pairs_per_lane rebuilds the
@@ -712,14 +713,19 @@ typedef struct {
 fm_status fm_set_tuning(fm_problem* problem, const fm_tuning* tuning);
 fm_status fm_get_tuning(const fm_problem* problem, fm_tuning* tuning);
 
-/* Autotuner: times the direct kernel (L1, the problem's current weights and
- * epipolar parameters, or generated parameters when none are set) for the
- * three tiles and every CTA count per SM that fits, `repeats` times each
- * (CTA counts in round robin), every launch after an L2 flush and a 0.2 ms
- * device idle, and keeps the configuration with the lowest mean time (event
+/* Autotuner: times one gradient evaluation of the direct L1 objective as
+ * fm_step chains it -- the E tables, the direct kernel and the per-camera
+ * pass with the loss -- at the problem's current weights and epipolar
+ * parameters (or generated parameters when none are set), for the three
+ * tiles and every CTA count per SM that fits, `repeats` times each (CTA
+ * counts in round robin), every sample after an L2 flush and a 0.2 ms device
+ * idle, and keeps the configuration with the lowest mean time (event
  * timestamps come in steps of about 2 us on the B300, so single fastest
- * launches tie).  The choice changes no result beyond the order of
- * additions inside an image pair's records.  Synchronises. */
+ * samples tie).  The whole chain is timed because the direct kernel's
+ * configuration also sets how the next launch overlaps its end.  The loss
+ * chosen by fm_ea_set_loss is left as it was.  The choice changes no result
+ * beyond the order of additions inside an image pair's records.
+ * Synchronises. */
 fm_status fm_autotune(fm_problem* problem, int32_t repeats, fm_tuning* best);
 
 /* fm_step replays captured CUDA graphs of 16 iterations (one graph launch

@@ -426,6 +426,9 @@ void launch_merge(const fm_problem* pr, const float* o, int runs, float* stats, 
                   int* best_run, cudaStream_t s);
 void launch_reltrans(const fm_problem* pr, const float* rot6, float* rel_t, float* err_out, cudaStream_t s);
 cudaError_t build_track_table(fm_problem* pr, int* T_out);
+// (fm_tracks.cu) off: per-track counts in, exclusive scan out; idx: keypoint
+// pairs ordered by track, ascending inside a track
+cudaError_t track_table(const int* kp_track, int64_t Z, int T, int* off, int* idx, cudaStream_t s);
 void launch_triangulate(const fm_problem* pr, const float* params, float max_err_px, float min_angle_rad,
                         float* pts, int* valid, int* ncam, cudaStream_t s);
 // x <- x/|x| over each scene's cameras ([N][3])

@@ -192,10 +192,12 @@ __global__ void __launch_bounds__(128) k_ea_compact(const float* __restrict__ W,
   const bool mine = n < P;
   const int nn = mine ? n : n0;   // lanes past the end repeat the first pair; nothing of theirs is stored
   const float inv_z = pair_inv_z[nn];   // normaliser of the image pair's scene
+  // W is read once per iteration: streaming loads (evict-first), so that it
+  // does not push the chain-rule outputs, which k_cam gathers next, out of L2
   float Wn[64];
   const float* Wt = W + w_index(nn, 0);
 #pragma unroll
-  for (int k = 0; k < 64; ++k) Wn[k] = Wt[32 * k];
+  for (int k = 0; k < 64; ++k) Wn[k] = __ldcs(Wt + 32 * k);
   PairGeo g;
   pair_geometry(params + 9 * pi[nn], params + 9 * pj[nn], g);
   float e[9];

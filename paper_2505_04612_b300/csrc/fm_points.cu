@@ -10,8 +10,9 @@
 // >= min_angle.
 //
 // Track table (built once): keypoint pairs grouped by track id, in increasing
-// pair index inside a track (counting sort + per-track insertion sort, so the
-// order -- and every sum -- is deterministic).  One thread per track.
+// pair index inside a track (per-track counts, a multi-CTA scan and a stable
+// radix sort of the pair indices by track, so the order -- and every sum --
+// is deterministic).  One thread per track.
 #include "fm_device.cuh"
 #include "fm_internal.h"
 
@@ -32,54 +33,6 @@ __global__ void k_track_max(const int* __restrict__ track, int Z, int* out_max, 
 __global__ void k_track_count(const int* __restrict__ track, int Z, int* __restrict__ cnt) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m < Z) atomicAdd(cnt + track[m], 1);
-}
-
-// exclusive scan of n ints in place (one CTA, fixed order); total -> *total
-__global__ void k_scan_int(int* a, int n, int* total) {
-  __shared__ int part[1024];
-  const int t = threadIdx.x;
-  const int per = (n + 1023) / 1024;
-  const int b = t * per, e = min(b + per, n);
-  int s = 0;
-  for (int k = b; k < e; ++k) s += a[k];
-  part[t] = s;
-  __syncthreads();
-  for (int d = 1; d < 1024; d <<= 1) {
-    int v = (t >= d) ? part[t - d] : 0;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
-  }
-  int run = (t == 0) ? 0 : part[t - 1];
-  for (int k = b; k < e; ++k) {
-    const int v = a[k];
-    a[k] = run;
-    run += v;
-  }
-  if (t == 1023) *total = part[1023];
-}
-
-__global__ void k_track_fill(const int* __restrict__ track, int Z, const int* __restrict__ off,
-                             int* __restrict__ cursor, int* __restrict__ idx) {
-  int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= Z) return;
-  const int t = track[m];
-  idx[off[t] + atomicAdd(cursor + t, 1)] = m;
-}
-
-__global__ void k_track_sort(const int* __restrict__ off, int T, int* __restrict__ idx) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= T) return;
-  const int b = off[t], e = off[t + 1];
-  for (int i = b + 1; i < e; ++i) {
-    const int v = idx[i];
-    int j = i - 1;
-    while (j >= b && idx[j] > v) {
-      idx[j + 1] = idx[j];
-      --j;
-    }
-    idx[j + 1] = v;
-  }
 }
 
 struct Cam {
@@ -225,20 +178,14 @@ cudaError_t build_track_table(fm_problem* pr, int* T_out) {
   pr->n_tracks = T;
   e = cudaMalloc((void**)&pr->track_off, sizeof(int) * (size_t)(T + 1));
   if (e == cudaSuccess) e = cudaMalloc((void**)&pr->track_idx, sizeof(int) * (size_t)(Z > 0 ? Z : 1));
-  int* cursor = nullptr;
-  if (e == cudaSuccess) e = cudaMalloc((void**)&cursor, sizeof(int) * (size_t)(T + 1));
   if (e != cudaSuccess) { cudaFree(d_max); return e; }
   pr->device_bytes += (int64_t)sizeof(int) * (T + 1 + (Z > 0 ? Z : 1));
   cudaMemsetAsync(pr->track_off, 0, sizeof(int) * (size_t)(T + 1), s);
-  cudaMemsetAsync(cursor, 0, sizeof(int) * (size_t)(T + 1), s);
   if (Z > 0 && T > 0) {
-    k_track_count<<<(Z + 255) / 256, 256, 0, s>>>(pr->kp_track, Z, pr->track_off);
-    k_scan_int<<<1, 1024, 0, s>>>(pr->track_off, T + 1, d_max + 1);
-    k_track_fill<<<(Z + 255) / 256, 256, 0, s>>>(pr->kp_track, Z, pr->track_off, cursor, pr->track_idx);
-    k_track_sort<<<(T + 127) / 128, 128, 0, s>>>(pr->track_off, T, pr->track_idx);
+    k_track_count<<<(Z + 255) / 256, 256, 0, s>>>(pr->kp_track, Z, pr->track_off);   // integer counts
+    e = track_table(pr->kp_track, Z, T, pr->track_off, pr->track_idx, s);
   }
-  e = cudaStreamSynchronize(s);
-  cudaFree(cursor);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d_max);
   return e == cudaSuccess ? cudaGetLastError() : e;
 }

@@ -608,6 +608,25 @@ cudaError_t sort_kp_pairs(const int* kp_img_pair, const int* kp_track, int64_t Z
   return cudaGetLastError();
 }
 
+// The track table of a problem: off [T+1] the exclusive scan of the
+// keypoint pairs per track (counted into off by the caller), idx [Z] the
+// keypoint-pair indices ordered by track, ascending inside a track (one
+// stable radix sort of the indices by track).
+cudaError_t track_table(const int* kp_track, int64_t Z, int T, int* off, int* idx, cudaStream_t s) {
+  if (Z <= 0 || T <= 0) return cudaSuccess;
+  Buffers B(s);
+  uint32_t* key = B.get<uint32_t>((size_t)Z);
+  uint32_t* val = B.get<uint32_t>((size_t)Z);
+  if (B.ce != cudaSuccess) return B.ce;
+  scan<int>(B, off, off, (int64_t)T + 1, nullptr, s);
+  k_iota<<<grid_for(Z), 256, 0, s>>>(val, Z);
+  k_gather_key<<<grid_for(Z), 256, 0, s>>>(kp_track, nullptr, Z, key);
+  radix_sort(B, key, val, Z, bits_for((uint64_t)(T - 1)), s);
+  if (B.ce != cudaSuccess) return B.ce;
+  cudaMemcpyAsync(idx, val, sizeof(uint32_t) * (size_t)Z, cudaMemcpyDeviceToDevice, s);
+  return cudaGetLastError();
+}
+
 }  // namespace fm
 
 namespace {
