@@ -21,23 +21,26 @@ namespace fm {
 namespace {
 
 // y = x - (B x)/sigma with B = A/scaleP + (1/N) diag(c1 c1^T) (c1 may be
-// null); coef[3 s + {0,1,2}] = (1/sigma, 1/scaleP, 1/N) of scene s
-__global__ void __launch_bounds__(128) k_mart_iter(const int* __restrict__ cam_seg_off,
-                                                   const int* __restrict__ cam_seg,
-                                                   const int* __restrict__ pi, const int* __restrict__ pj,
-                                                   const float* __restrict__ relR, const float* __restrict__ x,
-                                                   const float* __restrict__ c1, float* __restrict__ y, int N,
-                                                   const int* __restrict__ cam_scene,
-                                                   const float* __restrict__ coef) {
-  const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (c >= N) return;
-  const int sc = cam_scene[c];
-  const float inv_sigma = coef[3 * sc], inv_scale_p = coef[3 * sc + 1], inv_n = coef[3 * sc + 2];
-  const float xc0 = x[3 * c], xc1 = x[3 * c + 1], xc2 = x[3 * c + 2];
+// null); coef[3 s + {0,1,2}] = (1/sigma, 1/scaleP, 1/N) of scene s.  One
+// CTA of 128 threads per camera: thread t adds the incident image pairs
+// t, t + 128, ... of the camera CSR, the warps reduce by butterflies and are
+// added in warp order (a fixed order), and thread 0 writes the camera's row.
+constexpr int kMartThreads = 128;
+
+__global__ void __launch_bounds__(kMartThreads) k_mart_iter(const int* __restrict__ cam_seg_off,
+                                                            const int* __restrict__ cam_seg,
+                                                            const int* __restrict__ pi, const int* __restrict__ pj,
+                                                            const float* __restrict__ relR,
+                                                            const float* __restrict__ x,
+                                                            const float* __restrict__ c1, float* __restrict__ y,
+                                                            int N, const int* __restrict__ cam_scene,
+                                                            const float* __restrict__ coef) {
+  __shared__ float part[kMartThreads / 32][3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x;
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   const int b = cam_seg_off[c], e = cam_seg_off[c + 1];
-  for (int idx = b + lane; idx < e; idx += 32) {
+  for (int idx = b + threadIdx.x; idx < e; idx += kMartThreads) {
     const unsigned v = (unsigned)cam_seg[idx];
     const int n = (int)(v & 0x7fffffffu);
     const float* R = relR + 9 * n;
@@ -59,6 +62,21 @@ __global__ void __launch_bounds__(128) k_mart_iter(const int* __restrict__ cam_s
   a1 = warp_sum(a1);
   a2 = warp_sum(a2);
   if (lane == 0) {
+    part[warp][0] = a0;
+    part[warp][1] = a1;
+    part[warp][2] = a2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a0 = a1 = a2 = 0.f;
+    for (int w = 0; w < kMartThreads / 32; ++w) {
+      a0 += part[w][0];
+      a1 += part[w][1];
+      a2 += part[w][2];
+    }
+    const int sc = cam_scene[c];
+    const float inv_sigma = coef[3 * sc], inv_scale_p = coef[3 * sc + 1], inv_n = coef[3 * sc + 2];
+    const float xc0 = x[3 * c], xc1 = x[3 * c + 1], xc2 = x[3 * c + 2];
     const float deg = (float)(e - b);
     float b0 = (a0 + deg * xc0) * inv_scale_p;
     float b1 = (a1 + deg * xc1) * inv_scale_p;
@@ -239,7 +257,8 @@ __global__ void __launch_bounds__(128) k_merge(const float* __restrict__ o, cons
 }  // namespace
 
 void launch_mart_iter(const fm_problem* pr, const float* x, const float* c1, float* y, cudaStream_t s) {
-  k_mart_iter<<<(pr->N + 3) / 4, 128, 0, s>>>(pr->cam_seg_off, pr->cam_seg, pr->pair_i, pr->pair_j,
+  if (pr->N <= 0) return;
+  k_mart_iter<<<pr->N, kMartThreads, 0, s>>>(pr->cam_seg_off, pr->cam_seg, pr->pair_i, pr->pair_j,
                                               pr->rel_R, x, c1, y, pr->N, pr->cam_scene, pr->mart_coef);
 }
 void launch_scale_to_unit(const fm_problem* pr, float* x, cudaStream_t s) {
