@@ -185,7 +185,7 @@ void release(fm_problem* pr) {
   dfree(pr->merge_buf); dfree(pr->best_run);
   dfree(pr->mlp_theta); dfree(pr->mlp_tab); dfree(pr->mlp_prob);
   dfree(pr->sc_cam_off); dfree(pr->sc_pair_off); dfree(pr->sc_kp_off); dfree(pr->cam_scene);
-  dfree(pr->pair_scene); dfree(pr->pair_inv_p); dfree(pr->pair_inv_z); dfree(pr->mart_coef);
+  dfree(pr->pair_scene); dfree(pr->pair_inv_p); dfree(pr->pair_inv_z); dfree(pr->mart_coef); dfree(pr->lattice0);
   for (auto& g : pr->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   pr->graphs.clear();
@@ -2422,6 +2422,11 @@ fm_status fm_relative_translations(fm_problem* pr, float* err_out, int32_t err_o
   if (!pr->rot_params_set) return fail(pr, FM_ERR_STATE, "the grid search needs rotation-stage parameters");
   float* err = nullptr;
   if (err_out) err = err_on_device ? err_out : pr->seg_loss;
+  if (!pr->lattice0) {
+    FM_ALLOC(pr, pr->lattice0, (size_t)fm::reltrans_lattice_points());
+    fm::launch_reltrans_lattice(pr->lattice0, pr->stream);
+    FM_LAUNCHED(pr);
+  }
   {
     Timed t(pr, fm::kKRelTrans);
     fm::launch_reltrans(pr, pr->rot_params, pr->rel_t, err, pr->stream);

@@ -104,6 +104,7 @@ struct fm_problem {
   float* pair_inv_p = nullptr;   // [P] 1/P_s: normaliser of the rotation and translation losses
   float* pair_inv_z = nullptr;   // [P] normaliser of the epipolar loss of the pair's scene
   float* mart_coef = nullptr;    // [3S] per-scene constants of the rotation initialisation
+  float4* lattice0 = nullptr;    // [4096] hemisphere candidates of the relative-translation search
 
   // image-pair graph
   int* pair_i = nullptr;         // [P]
@@ -425,6 +426,8 @@ void launch_hash_fill(const fm_problem* pr, float* x, int runs, unsigned salt, c
 void launch_merge(const fm_problem* pr, const float* o, int runs, float* stats, float* out,
                   int* best_run, cudaStream_t s);
 void launch_reltrans(const fm_problem* pr, const float* rot6, float* rel_t, float* err_out, cudaStream_t s);
+int reltrans_lattice_points();
+void launch_reltrans_lattice(float4* lat0, cudaStream_t s);   // fills pr->lattice0 (needed by launch_reltrans)
 cudaError_t build_track_table(fm_problem* pr, int* T_out);
 // (fm_tracks.cu) off: per-track counts in, exclusive scan out; idx: keypoint
 // pairs ordered by track, ascending inside a track

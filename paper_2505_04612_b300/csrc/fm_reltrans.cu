@@ -13,7 +13,11 @@
 // One CTA per image pair.  The a_m of a tile of keypoint pairs are formed in
 // shared memory; each thread scores its own candidates over the tile.  An ALU
 // kernel: 4 FP32 operations per (pair, candidate), no tensor-core shape
-// (inner dimension 3).
+// (inner dimension 3).  The hemisphere's 4096 points are the same for every
+// image pair: k_lattice0 writes them once per problem (the same function and
+// arguments as the per-CTA evaluation, so the same values), and an image pair
+// whose keypoint pairs fit in one tile forms its a_m once for all three
+// levels.
 #include "fm_device.cuh"
 #include "fm_internal.h"
 
@@ -72,31 +76,49 @@ __device__ __forceinline__ Best better(Best a, Best b) {
   return (b.e < a.e || (b.e == a.e && b.k < a.k)) ? b : a;
 }
 
+// a_m of keypoint pairs [base, base + n) into the tile
+__device__ __forceinline__ void fill_tile(const float4* __restrict__ kp, const float* __restrict__ w, int base,
+                                          int n, const float* Rij, float (*a_s)[kTile]) {
+  for (int m = threadIdx.x; m < n; m += kThreads) {
+    const float4 x = kp[base + m];
+    const float r0 = Rij[0] * x.x + Rij[1] * x.y + Rij[2];
+    const float r1 = Rij[3] * x.x + Rij[4] * x.y + Rij[5];
+    const float r2 = Rij[6] * x.x + Rij[7] * x.y + Rij[8];
+    // (R x1) x x2 with x2 = (x.z, x.w, 1); a left-out pair adds |t . 0| = 0
+    const float keep = (w == nullptr || w[base + m] > 0.f) ? 1.f : 0.f;
+    a_s[0][m] = keep * (r1 * 1.f - r2 * x.w);
+    a_s[1][m] = keep * (r2 * x.z - r0 * 1.f);
+    a_s[2][m] = keep * (r0 * x.w - r1 * x.z);
+  }
+}
+
+// candidates k = threadIdx.x + kThreads i from `table` (level 0) or the cap
+// lattice (K, H, Q); resident: the image pair's a_m already fill the tile
 template <int PER>
 __device__ Best score_level(const float4* __restrict__ kp, const float* __restrict__ w, int b, int e,
-                            const float* Rij, int K, float H, const float* Q, float (*a_s)[kTile]) {
+                            const float* Rij, int K, float H, const float* Q, const float4* __restrict__ table,
+                            bool resident, float (*a_s)[kTile]) {
   float t[PER][3];
   float acc[PER];
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
-    lattice_point(threadIdx.x + kThreads * i, K, H, Q, t[i]);
+    if (table) {
+      const float4 p = table[threadIdx.x + kThreads * i];
+      t[i][0] = p.x;
+      t[i][1] = p.y;
+      t[i][2] = p.z;
+    } else {
+      lattice_point(threadIdx.x + kThreads * i, K, H, Q, t[i]);
+    }
     acc[i] = 0.f;
   }
   for (int base = b; base < e; base += kTile) {
     const int n = min(kTile, e - base);
-    __syncthreads();
-    for (int m = threadIdx.x; m < n; m += kThreads) {
-      const float4 x = kp[base + m];
-      const float r0 = Rij[0] * x.x + Rij[1] * x.y + Rij[2];
-      const float r1 = Rij[3] * x.x + Rij[4] * x.y + Rij[5];
-      const float r2 = Rij[6] * x.x + Rij[7] * x.y + Rij[8];
-      // (R x1) x x2 with x2 = (x.z, x.w, 1); a left-out pair adds |t . 0| = 0
-      const float keep = (w == nullptr || w[base + m] > 0.f) ? 1.f : 0.f;
-      a_s[0][m] = keep * (r1 * 1.f - r2 * x.w);
-      a_s[1][m] = keep * (r2 * x.z - r0 * 1.f);
-      a_s[2][m] = keep * (r0 * x.w - r1 * x.z);
+    if (!resident) {
+      __syncthreads();
+      fill_tile(kp, w, base, n, Rij, a_s);
+      __syncthreads();
     }
-    __syncthreads();
     for (int m = 0; m < n; ++m) {
       const float a0 = a_s[0][m], a1 = a_s[1][m], a2 = a_s[2][m];
 #pragma unroll
@@ -144,6 +166,7 @@ __device__ __forceinline__ int positive_depths(const float4 x, const float* R, c
 __global__ void __launch_bounds__(kThreads) k_reltrans(const float4* __restrict__ kp, const int* __restrict__ seg_off,
                                                       const int* __restrict__ pi, const int* __restrict__ pj,
                                                       const float* __restrict__ rot6, const float* __restrict__ w_in,
+                                                      const float4* __restrict__ lat0,
                                                       float* __restrict__ rel_t, float* __restrict__ err_out) {
   __shared__ float a_s[3][kTile];
   __shared__ Best red[kThreads / 32];
@@ -184,10 +207,14 @@ __global__ void __launch_bounds__(kThreads) k_reltrans(const float4* __restrict_
     return;
   }
   const float I3[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+  const bool resident = e - b <= kTile;
+  if (resident) {
+    fill_tile(kp, w, b, e - b, Rij, a_s);
+    __syncthreads();
+  }
   // level 0: hemisphere
-  Best bst = block_best(score_level<kK0 / kThreads>(kp, w, b, e, Rij, kK0, 1.f, I3, a_s), red);
-  float t[3];
-  lattice_point(bst.k, kK0, 1.f, I3, t);
+  Best bst = block_best(score_level<kK0 / kThreads>(kp, w, b, e, Rij, kK0, 1.f, I3, lat0, resident, a_s), red);
+  float t[3] = {lat0[bst.k].x, lat0[bst.k].y, lat0[bst.k].z};
   float best_e = bst.e;
   float spacing = sqrtf(2.f * 3.14159265358979f * 1.f / kK0);
   for (int level = 0; level < 2; ++level) {
@@ -196,7 +223,7 @@ __global__ void __launch_bounds__(kThreads) k_reltrans(const float4* __restrict_
     const float H = 2.f * sh * sh;   // 1 - cos(radius)
     float Q[9];
     rotation_to(t, Q);
-    Best c = block_best(score_level<kK1 / kThreads>(kp, w, b, e, Rij, kK1, H, Q, a_s), red);
+    Best c = block_best(score_level<kK1 / kThreads>(kp, w, b, e, Rij, kK1, H, Q, nullptr, resident, a_s), red);
     if (c.e < best_e) {
       best_e = c.e;
       lattice_point(c.k, kK1, H, Q, t);
@@ -235,11 +262,26 @@ __global__ void __launch_bounds__(kThreads) k_reltrans(const float4* __restrict_
   }
 }
 
+// the hemisphere's kK0 points, as score_level forms them on the fly
+__global__ void k_lattice0(float4* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= kK0) return;
+  const float I3[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+  float t[3];
+  lattice_point(k, kK0, 1.f, I3, t);
+  out[k] = make_float4(t[0], t[1], t[2], 0.f);
+}
+
 }  // namespace
 
+int reltrans_lattice_points() { return kK0; }
+
+void launch_reltrans_lattice(float4* lat0, cudaStream_t s) { k_lattice0<<<kK0 / 256, 256, 0, s>>>(lat0); }
+
 void launch_reltrans(const fm_problem* pr, const float* rot6, float* rel_t, float* err_out, cudaStream_t s) {
-  k_reltrans<<<pr->P, kThreads, 0, s>>>(pr->kp, pr->seg_off, pr->pair_i, pr->pair_j, rot6, pr->ea_w, rel_t,
-                                        err_out);
+  if (pr->P <= 0) return;
+  k_reltrans<<<pr->P, kThreads, 0, s>>>(pr->kp, pr->seg_off, pr->pair_i, pr->pair_j, rot6, pr->ea_w, pr->lattice0,
+                                        rel_t, err_out);
 }
 
 }  // namespace fm
