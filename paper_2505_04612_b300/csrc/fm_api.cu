@@ -167,7 +167,7 @@ void release(fm_problem* pr) {
   if (!pr) return;
   cudaStreamSynchronize(pr->stream);
   dfree(pr->pair_i); dfree(pr->pair_j); dfree(pr->seg_off);
-  dfree(pr->cam_seg_off); dfree(pr->cam_seg);
+  dfree(pr->cam_seg_off); dfree(pr->cam_seg); dfree(pr->cam_pos);
   dfree(pr->kp); dfree(pr->kp_perm); dfree(pr->kp_track); dfree(pr->focal); dfree(pr->cx); dfree(pr->cy);
   dfree(pr->lane_desc); dfree(pr->wrun_info); dfree(pr->seg_rec); dfree(pr->rec);
   dfree(pr->seg_tab); dfree(pr->seg_grad); dfree(pr->seg_loss);
@@ -389,7 +389,7 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   }
 
   // camera -> incident image pairs, ordered by image pair (deterministic sums)
-  std::vector<int> coff(N + 1, 0), cseg(2 * (size_t)P);
+  std::vector<int> coff(N + 1, 0), cseg(2 * (size_t)P), cpos(2 * (size_t)P);
   for (int n = 0; n < P; ++n) { coff[hi[n] + 1]++; coff[hj[n] + 1]++; }
   for (int c = 0; c < N; ++c) pr->max_degree = std::max(pr->max_degree, coff[c + 1]);
   pr->h_sc_max_degree.assign(S, 0);
@@ -399,7 +399,9 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   {
     std::vector<int> fill(coff.begin(), coff.end() - 1);
     for (int n = 0; n < P; ++n) {
+      cpos[2 * (size_t)n] = fill[hi[n]];
       cseg[fill[hi[n]]++] = n;
+      cpos[2 * (size_t)n + 1] = fill[hj[n]];
       cseg[fill[hj[n]]++] = (int)((unsigned)n | 0x80000000u);
     }
   }
@@ -411,6 +413,7 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   FM_ALLOC(pr, pr->cy, N);
   FM_ALLOC(pr, pr->cam_seg_off, N + 1);
   FM_ALLOC(pr, pr->cam_seg, 2 * (size_t)P);
+  FM_ALLOC(pr, pr->cam_pos, 2 * (size_t)P);
   FM_ALLOC(pr, pr->seg_off, P + 1);
   FM_ALLOC(pr, pr->d_err, 1);
   FM_CUDA(pr, cudaMemcpyAsync(pr->pair_i, hi.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s));
@@ -420,6 +423,7 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   FM_CUDA(pr, cudaMemcpyAsync(pr->cy, hcy.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->cam_seg_off, coff.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, s));
   FM_CUDA(pr, cudaMemcpyAsync(pr->cam_seg, cseg.data(), sizeof(int) * 2 * (size_t)P, cudaMemcpyHostToDevice, s));
+  FM_CUDA(pr, cudaMemcpyAsync(pr->cam_pos, cpos.data(), sizeof(int) * 2 * (size_t)P, cudaMemcpyHostToDevice, s));
   FM_CUDA(pr, cudaMemsetAsync(pr->d_err, 0, sizeof(int), s));
   FM_ALLOC(pr, pr->sc_cam_off, S + 1);
   FM_ALLOC(pr, pr->sc_pair_off, S + 1);
@@ -789,6 +793,7 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
     // the cameras, and the loss in slices of the same launch
     fm::CamUpdate u = cam_update(pr, params, grad_dev, adam, state, step, runs);
     u.loss = loss_args(pr, first, second);
+    u.csr_order = (st == FM_STAGE_EPIPOLAR && pr->ea_loss == FM_EA_COMPACT);   // k_ea_compact's layout
     {
       Timed t(pr, fm::kKCamUpdate);
       fm::launch_cam_update((int)st, u, s);

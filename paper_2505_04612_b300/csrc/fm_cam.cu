@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kThreads) k_cam(CamUpdate u) {
   const int c = blockIdx.x, t = threadIdx.x, lane = t & 31;
   // static: before the wait
   const int b = u.cam_seg_off[c], e = u.cam_seg_off[c + 1];
-  const int pre = (b + t < e) ? __ldg(u.cam_seg + b + t) : -1;
+  const int pre = (b + t < e && !u.csr_order) ? __ldg(u.cam_seg + b + t) : -1;
   pdl_wait();
   // parameters and moments do not depend on the gather: loaded with it
   const size_t off = ((size_t)run * u.N + c) * L::PDIM;
@@ -65,8 +65,13 @@ __global__ void __launch_bounds__(kThreads) k_cam(CamUpdate u) {
 #pragma unroll
   for (int k = 0; k < L::PART; ++k) acc[k] = 0.f;
   const float* sg = u.seg_grad + (size_t)run * u.P * 2 * L::PART;
-  if (pre != -1) step::cam_add<L::PART>(sg, pre, acc);
-  for (int idx = b + t + kThreads; idx < e; idx += kThreads) step::cam_add<L::PART>(sg, __ldg(u.cam_seg + idx), acc);
+  if (u.csr_order) {   // the parts already in camera-CSR order: contiguous, same order of additions
+    for (int idx = b + t; idx < e; idx += kThreads) step::cam_add_part<L::PART>(sg + (size_t)idx * L::PART, acc);
+  } else {
+    if (pre != -1) step::cam_add<L::PART>(sg, pre, acc);
+    for (int idx = b + t + kThreads; idx < e; idx += kThreads)
+      step::cam_add<L::PART>(sg, __ldg(u.cam_seg + idx), acc);
+  }
   step::cam_reduce<L::PART>(acc, red);
   if (t < 32) step::cam_apply<STAGE, ADAM>(u, off, p, m, v, acc, lane);
 }

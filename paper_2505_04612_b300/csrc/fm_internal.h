@@ -105,6 +105,7 @@ struct fm_problem {
   float* pair_inv_z = nullptr;   // [P] normaliser of the epipolar loss of the pair's scene
   float* mart_coef = nullptr;    // [3S] per-scene constants of the rotation initialisation
   float4* lattice0 = nullptr;    // [4096] hemisphere candidates of the relative-translation search
+  int* cam_pos = nullptr;        // [2P] camera-CSR index of (image pair n, role i / j)
 
   // image-pair graph
   int* pair_i = nullptr;         // [P]
@@ -479,6 +480,7 @@ struct CamUpdate {
   int N, P, runs;
   const float* seg_loss;   // [runs][P] per-image-pair loss terms (k_cam's loss slices)
   LossArgs loss;           // loss.out null: no loss
+  bool csr_order;          // seg_grad holds the parts in camera-CSR order ([2P][part], one run)
 };
 void launch_cam_update(int stage, const CamUpdate& u, cudaStream_t s);
 // the epipolar step after k_ea_direct: s as for k_ea_segments (its seg_grad,

@@ -175,17 +175,18 @@ __device__ __forceinline__ int tri(int a, int c) {   // index of (a, c), a <= c,
 }
 
 // one thread per image pair; a warp's 32 image pairs form one tile of W
-// (64 coalesced 128-byte rows), and the warp's 32 x 24 chain-rule outputs
-// leave through shared memory as one contiguous block
+// (64 coalesced 128-byte rows).  The two 12-float parts of the chain rule go
+// to their positions in the camera CSR (cam_pos), so that k_cam reads each
+// camera's parts as one contiguous block instead of gathering them.
 template <bool STEP>
 __global__ void __launch_bounds__(128) k_ea_compact(const float* __restrict__ W, const float* __restrict__ params,
                                                     const int* __restrict__ pi, const int* __restrict__ pj, int P,
                                                     const float* __restrict__ pair_inv_z,
+                                                    const int* __restrict__ cam_pos,
                                                     float* __restrict__ seg_grad, float* __restrict__ seg_loss,
                                                     int* step_counter) {
-  __shared__ float stage[4][32 * (kSegGradEa + 1)];
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int n0 = n - lane;   // the warp's first image pair
   if (STEP && step_counter && n == 0) *step_counter += 1;
   if (n0 >= P) return;
@@ -226,13 +227,16 @@ __global__ void __launch_bounds__(128) k_ea_compact(const float* __restrict__ W,
   for (int a = 0; a < 9; ++a) G[a] = 2.f * inv_z * (Wn[45 + a] + Wd[a]);
   float o[kSegGradEa];
   pair_backward(g, G, o);
-  float* st = stage[warp];
+  if (mine) {
+    constexpr int kPart = kSegGradEa / 2;   // 48 B: 16-byte aligned parts
+    float4* oi = reinterpret_cast<float4*>(seg_grad + (size_t)kPart * cam_pos[2 * n]);
+    float4* oj = reinterpret_cast<float4*>(seg_grad + (size_t)kPart * cam_pos[2 * n + 1]);
 #pragma unroll
-  for (int k = 0; k < kSegGradEa; ++k) st[lane * (kSegGradEa + 1) + k] = o[k];
-  __syncwarp();
-  const int cnt = min(32, P - n0) * kSegGradEa;
-  float* out = seg_grad + (size_t)kSegGradEa * n0;
-  for (int i = lane; i < cnt; i += 32) out[i] = st[(i / kSegGradEa) * (kSegGradEa + 1) + i % kSegGradEa];
+    for (int q = 0; q < kPart / 4; ++q) {
+      oi[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+      oj[q] = make_float4(o[kPart + 4 * q], o[kPart + 4 * q + 1], o[kPart + 4 * q + 2], o[kPart + 4 * q + 3]);
+    }
+  }
 }
 
 }  // namespace
@@ -251,7 +255,7 @@ void launch_w_build(const fm_problem* pr, const float* w, float* W, cudaStream_t
 
 void launch_ea_compact(const fm_problem* pr, const float* params, int* step_counter, cudaStream_t s) {
   k_ea_compact<true><<<(pr->P + 127) / 128, 128, 0, s>>>(pr->W, params, pr->pair_i, pr->pair_j, pr->P,
-                                                         pr->pair_inv_z, pr->seg_grad, pr->seg_loss,
+                                                         pr->pair_inv_z, pr->cam_pos, pr->seg_grad, pr->seg_loss,
                                                          step_counter);
 }
 

@@ -185,14 +185,9 @@ template <> struct Layout<0> { static constexpr int PART = 9, PDIM = 6; static c
 template <> struct Layout<1> { static constexpr int PART = 3, PDIM = 3; static constexpr bool ROT = false; };
 template <> struct Layout<2> { static constexpr int PART = 12, PDIM = 9; static constexpr bool ROT = true; };
 
-// adds the part of camera-CSR entry `entry` (image pair | role << 31) of the
-// per-image-pair gradients sg
+// adds the part at g (PART floats)
 template <int PART>
-__device__ __forceinline__ void cam_add(const float* sg, int entry, float* acc) {
-  const unsigned w = (unsigned)entry;
-  const int n = (int)(w & 0x7fffffffu);
-  const int role = (int)(w >> 31);
-  const float* g = sg + ((size_t)n * 2 + role) * PART;
+__device__ __forceinline__ void cam_add_part(const float* g, float* acc) {
   if (PART % 4 == 0) {   // 48-B parts of a cudaMalloc'd buffer: 16-B aligned
 #pragma unroll
     for (int q = 0; q < PART / 4; ++q) {
@@ -206,6 +201,16 @@ __device__ __forceinline__ void cam_add(const float* sg, int entry, float* acc) 
 #pragma unroll
     for (int k = 0; k < PART; ++k) acc[k] += g[k];
   }
+}
+
+// adds the part of camera-CSR entry `entry` (image pair | role << 31) of the
+// per-image-pair gradients sg
+template <int PART>
+__device__ __forceinline__ void cam_add(const float* sg, int entry, float* acc) {
+  const unsigned w = (unsigned)entry;
+  const int n = (int)(w & 0x7fffffffu);
+  const int role = (int)(w >> 31);
+  cam_add_part<PART>(sg + ((size_t)n * 2 + role) * PART, acc);
 }
 
 // A camera's parts over its incident image pairs [b, e) of the camera CSR are
