@@ -442,8 +442,16 @@ __global__ void k_pairs(const uint32_t* __restrict__ key, const int* __restrict_
   }
 }
 
-__global__ void k_pair_keep(const int* __restrict__ pstart, int P, int64_t Z, int min_pairs, int* __restrict__ keep) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+// keep[p] for p < Pmax: 1 for image pairs with >= min_pairs keypoint pairs;
+// 0 past the image-pair count *P_dev (read on the device: no host round trip)
+__global__ void k_pair_keep(const int* __restrict__ pstart, const int* __restrict__ P_dev, int Pmax, int64_t Z,
+                            int min_pairs, int* __restrict__ keep) {
+  const int P = *P_dev;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < Pmax; p += gridDim.x * blockDim.x) {
+    if (p >= P) {
+      keep[p] = 0;
+      continue;
+    }
     const int64_t e = p + 1 < P ? pstart[p + 1] : Z;
     keep[p] = (e - pstart[p] >= min_pairs) ? 1 : 0;
   }
@@ -474,12 +482,16 @@ __global__ void k_gather(const uint32_t* __restrict__ perm, const int* __restric
   }
 }
 
+// the kept image pairs (all of them when keep is null) of the *P_dev found
 __global__ void k_pair_compact(const int* __restrict__ pi, const int* __restrict__ pj, const int* __restrict__ keep,
-                               const int* __restrict__ pos, int P, int* __restrict__ o_pi, int* __restrict__ o_pj) {
+                               const int* __restrict__ pos, const int* __restrict__ P_dev, int* __restrict__ o_pi,
+                               int* __restrict__ o_pj) {
+  const int P = *P_dev;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
-    if (keep[p]) {
-      o_pi[pos[p]] = pi[p];
-      o_pj[pos[p]] = pj[p];
+    if (!keep || keep[p]) {
+      const int q = keep ? pos[p] : p;
+      o_pi[q] = pi[p];
+      o_pj[q] = pj[p];
     }
 }
 
@@ -726,7 +738,7 @@ fm_status fm_tracks_complete(int32_t n_images, const int32_t* kp_off, int64_t n_
     uint32_t* sval = B.get<uint32_t>(K);
     int* err = B.get<int>(1);
     long long* tot = B.get<long long>(2);
-    int* itot = B.get<int>(2);
+    int* itot = B.get<int>(3);
     if (ce == cudaSuccess) ce = B.ce;
     if (ce == cudaSuccess) ce = cudaMemsetAsync(size, 0, sizeof(int) * std::max(K, 1), s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(bad, 0, sizeof(int) * std::max(K, 1), s);
@@ -806,83 +818,79 @@ fm_status fm_tracks_complete(int32_t n_images, const int32_t* kp_off, int64_t n_
         scan<int>(B, head, hscan, Z, itot + 1, s);
         ce = B.ce == cudaSuccess ? cudaGetLastError() : B.ce;
       }
-      int P = 0;
-      if (ce == cudaSuccess && Z > 0) {
-        ce = cudaMemcpyAsync(&P, itot + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-      }
+      // the image-pair count P stays on the device (itot[1]): buffers indexed
+      // by image pair are sized by the bound Pmax, and every count is read
+      // back once, at the end
+      const int64_t Pmax = std::max<int64_t>(1, std::min<int64_t>(Z, (int64_t)N * (N - 1) / 2));
       int* pi = nullptr;
       int* pj = nullptr;
       int* pstart = nullptr;
       if (ce == cudaSuccess && Z > 0) {
-        pi = B.get<int>(P);
-        pj = B.get<int>(P);
-        pstart = B.get<int>(P);
+        pi = B.get<int>(Pmax);
+        pj = B.get<int>(Pmax);
+        pstart = B.get<int>(Pmax);
         ce = B.ce;
         if (ce == cudaSuccess) k_pairs<<<grid_for(Z), 256, 0, s>>>(key, head, hscan, Z, N, ipair, pi, pj, pstart);
       }
-      // image pairs with fewer than min_pairs pairs dropped
+      // image pairs with fewer than min_pairs pairs dropped: kept counts in
+      // itot[0] (image pairs) and tot[0] (keypoint pairs)
       int* pkeep = nullptr;
       int* ppos = nullptr;
       long long* zpos = nullptr;
-      int P_out = P;
-      long long Z_out = Z;
-      if (ce == cudaSuccess && Z > 0 && min_pairs > 1) {
-        pkeep = B.get<int>(P);
-        ppos = B.get<int>(P);
+      const bool filter = Z > 0 && min_pairs > 1;
+      if (ce == cudaSuccess && filter) {
+        pkeep = B.get<int>(Pmax);
+        ppos = B.get<int>(Pmax);
         zpos = B.get<long long>(Z);
         ce = B.ce;
         if (ce == cudaSuccess) {
-          k_pair_keep<<<grid_for(P), 256, 0, s>>>(pstart, P, Z, min_pairs, pkeep);
-          scan<int>(B, pkeep, ppos, P, itot, s);
+          k_pair_keep<<<grid_for(Pmax), 256, 0, s>>>(pstart, itot + 1, (int)Pmax, Z, min_pairs, pkeep);
+          scan<int>(B, pkeep, ppos, Pmax, itot, s);
           k_keep_flags<<<grid_for(Z), 256, 0, s>>>(ipair, pkeep, Z, zpos);
           scan<long long>(B, zpos, zpos, Z, tot, s);
           ce = B.ce == cudaSuccess ? cudaGetLastError() : B.ce;
         }
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&P_out, itot, sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&Z_out, tot, sizeof(long long), cudaMemcpyDeviceToHost, s);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
       }
       if (ce == cudaSuccess) {
-        res->P = Z > 0 ? P_out : 0;
-        res->Z = Z > 0 ? Z_out : 0;
+        // outputs sized by the counts before filtering (bounds of the kept ones)
+        const int64_t Pcap = Z > 0 ? Pmax : 0;
         auto alloc = [&](auto*& p, size_t n) {
           if (ce == cudaSuccess)
             ce = cudaMallocFromPoolAsync((void**)&p, std::max<size_t>(n * sizeof(*p), 16), tracks_pool(), s);
         };
-        alloc(res->pair_i, res->P);
-        alloc(res->pair_j, res->P);
-        alloc(res->kp_img_pair, res->Z);
-        alloc(res->node1, res->Z);
-        alloc(res->node2, res->Z);
-        alloc(res->track, res->Z);
+        alloc(res->pair_i, Pcap);
+        alloc(res->pair_j, Pcap);
+        alloc(res->kp_img_pair, Z);
+        alloc(res->node1, Z);
+        alloc(res->node2, Z);
+        alloc(res->track, Z);
         if (d_px) {
-          alloc(res->px1, res->Z);
-          alloc(res->px2, res->Z);
+          alloc(res->px1, Z);
+          alloc(res->px2, Z);
         }
       }
       if (ce == cudaSuccess && Z > 0) {
         k_gather<<<grid_for(Z), 256, 0, s>>>(perm, ipair, Z, pkeep, ppos, zpos, n1, n2, trk, d_px,
                                               res->kp_img_pair, res->node1, res->node2, res->track, res->px1,
                                               res->px2);
-        if (pkeep)
-          k_pair_compact<<<grid_for(P), 256, 0, s>>>(pi, pj, pkeep, ppos, P, res->pair_i, res->pair_j);
-        else {
-          cudaMemcpyAsync(res->pair_i, pi, sizeof(int) * P, cudaMemcpyDeviceToDevice, s);
-          cudaMemcpyAsync(res->pair_j, pj, sizeof(int) * P, cudaMemcpyDeviceToDevice, s);
-        }
+        k_pair_compact<<<grid_for(Pmax), 256, 0, s>>>(pi, pj, pkeep, ppos, itot + 1, res->pair_i, res->pair_j);
         ce = cudaGetLastError();
       }
       // inconsistent tracks: the number of flags (a scan of bad into start,
-      // which is no longer needed)
-      int h_nb = 0;
+      // which is no longer needed), into itot[2]
       if (ce == cudaSuccess && K > 0) {
-        scan<int>(B, bad, start, K, itot, s);
+        scan<int>(B, bad, start, K, itot + 2, s);
         ce = B.ce == cudaSuccess ? cudaGetLastError() : B.ce;
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_nb, itot, sizeof(int), cudaMemcpyDeviceToHost, s);
       }
+      int h_cnt[3] = {0, 0, 0};
+      long long Z_out = Z;
+      if (ce == cudaSuccess && (Z > 0 || K > 0))
+        ce = cudaMemcpyAsync(h_cnt, itot, sizeof(int) * 3, cudaMemcpyDeviceToHost, s);
+      if (ce == cudaSuccess && filter) ce = cudaMemcpyAsync(&Z_out, tot, sizeof(long long), cudaMemcpyDeviceToHost, s);
       if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-      res->n_inconsistent = h_nb;
+      res->P = Z > 0 ? (filter ? h_cnt[0] : h_cnt[1]) : 0;
+      res->Z = Z > 0 ? Z_out : 0;
+      res->n_inconsistent = K > 0 ? h_cnt[2] : 0;
       if (ce != cudaSuccess) {
         st = ce == cudaErrorMemoryAllocation ? FM_ERR_OOM : FM_ERR_CUDA;
         msg = std::string("track completion: ") + cudaGetErrorString(ce);
