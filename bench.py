@@ -110,9 +110,17 @@ def peaks():
 
 
 def source_hash():
+    """Hash of what defines k_ea_direct: fm_ea.cu, fm_device.cuh and the
+    direct kernel's constants in fm_internal.h (tile, stages, CTAs, lane
+    descriptor, error bit).  A committed ncu summary whose source_sha differs
+    was taken on another kernel: its traffic is not reported."""
+    csrc = os.path.join(ROOT, "paper_2505_04612_b300", "csrc")
     h = hashlib.sha256()
-    for f in ["fm_ea.cu", "fm_internal.h", "fm_device.cuh"]:
-        h.update(open(os.path.join(ROOT, "paper_2505_04612_b300", "csrc", f), "rb").read())
+    for f in ["fm_ea.cu", "fm_device.cuh"]:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    for line in open(os.path.join(csrc, "fm_internal.h"), "rb"):
+        if any(t in line for t in (b"FM_EA_", b"kEa", b"kDesc", b"kErrEaTimeout")):
+            h.update(line)
     return h.hexdigest()[:16]
 
 
