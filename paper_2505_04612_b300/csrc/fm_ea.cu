@@ -361,10 +361,14 @@ __global__ void __launch_bounds__(WARPS * 32, kEaMinCtas) k_ea_direct(DirectArgs
   zero_buffers<U * S, WEIGHTED>(lane, kb, wb);
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   __syncwarp();
+  // static heads (descriptor and run info) are loaded two runs before the
+  // run's copy is issued: q[0 .. S-1] and far (run w + S stride)
   RunHead q[S];
+  RunHead far;
 #pragma unroll
   for (int k = 0; k < S; ++k)
     if (w + k * stride < a.n_wruns) load_static_head(a, w + k * stride, lane, q[k]);
+  if (w + S * stride < a.n_wruns) load_static_head(a, w + S * stride, lane, far);
   unsigned pending = 0;                    // buffers with a bulk copy not yet waited for
 #pragma unroll
   for (int k = 0; k < S - 1; ++k) {
@@ -391,7 +395,7 @@ __global__ void __launch_bounds__(WARPS * 32, kEaMinCtas) k_ea_direct(DirectArgs
     }
     if (WEIGHTED) asm volatile("cp.async.commit_group;\n" ::);
     RunHead fresh;
-    if (w + S * stride < a.n_wruns) load_static_head(a, w + S * stride, lane, fresh);
+    if (w + (S + 1) * stride < a.n_wruns) load_static_head(a, w + (S + 1) * stride, lane, fresh);
     if (w + stride < a.n_wruns) load_table_head(a, lane, q[1]);
     ok = bar_wait(smem_u32(bars + buf), (phase >> buf) & 1u);
     if (!__all_sync(FULL, ok)) { ok = false; break; }
@@ -407,7 +411,10 @@ __global__ void __launch_bounds__(WARPS * 32, kEaMinCtas) k_ea_direct(DirectArgs
     __syncwarp();
 #pragma unroll
     for (int k = 0; k < S - 1; ++k) q[k] = q[k + 1];
-    q[S - 1] = fresh;
+    q[S - 1].info = far.info;
+    q[S - 1].desc = far.desc;
+    far.info = fresh.info;
+    far.desc = fresh.desc;
     if (++buf == S) buf = 0;
   }
   if (!ok) {
