@@ -1617,7 +1617,7 @@ static fm_status wait_stream(fm_problem* pr) {
   FM_CUDA(pr, cudaStreamSynchronize(pr->stream));
   return FM_OK;
 }
-static fm_status capture_loss_grad(fm_problem* pr, fm_stage st, size_t count, size_t nl, bool want_loss,
+static fm_status capture_loss_grad(fm_problem* pr, fm_stage st, size_t count, bool want_loss,
                                    bool want_grad, fm_problem::GraphEntry* out);
 
 // fm_loss_grad with host buffers through a captured graph (from the second
@@ -1659,7 +1659,7 @@ static fm_status loss_grad_graph(fm_problem* pr, fm_stage st, const float* param
     e.kind = 1;
     e.flags = flags;
     e.epoch = pr->graph_epoch;
-    fm_status r = capture_loss_grad(pr, st, count, nl, loss != nullptr, grad != nullptr, &e);
+    fm_status r = capture_loss_grad(pr, st, count, loss != nullptr, grad != nullptr, &e);
     if (r != FM_OK) return r;
     pr->graphs.push_back(e);
     g = &pr->graphs.back();
@@ -1965,9 +1965,10 @@ static void evict_lru(fm_problem* pr) {
 }
 
 // fm_loss_grad with host buffers as one graph: parameters in from the pinned
-// staging buffer, the evaluation, gradient / loss / error word out to pinned
-// buffers.  Replaying it costs one launch instead of one per copy and kernel.
-static fm_status capture_loss_grad(fm_problem* pr, fm_stage st, size_t count, size_t nl, bool want_loss,
+// staging buffer, the evaluation writing gradient and loss into pinned
+// buffers, the error word out.  Replaying it costs one launch instead of one
+// per copy and kernel.
+static fm_status capture_loss_grad(fm_problem* pr, fm_stage st, size_t count, bool want_loss,
                                    bool want_grad, fm_problem::GraphEntry* out) {
   if (!pr->cap_stream) FM_CUDA(pr, cudaStreamCreateWithFlags(&pr->cap_stream, cudaStreamNonBlocking));
   int64_t before[fm::kKCount];
@@ -1981,13 +1982,12 @@ static fm_status capture_loss_grad(fm_problem* pr, fm_stage st, size_t count, si
   fm::g_capturing = true;
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(pr->scratch_params, pr->h_lg_in, sizeof(float) * count,
                                               cudaMemcpyHostToDevice, s);
+  // the last kernel writes the gradient and the loss straight into the
+  // pinned staging buffers (mapped into the device's address space), so no
+  // copy node follows it for them; the 4-byte error word is copied
   if (ce == cudaSuccess)
-    e = evaluate(pr, st, pr->scratch_params, want_grad ? pr->scratch_grad : nullptr, nullptr, nullptr,
-                 want_loss ? pr->d_loss : nullptr);
-  if (ce == cudaSuccess && e == FM_OK && want_grad)
-    ce = cudaMemcpyAsync(pr->h_lg_grad, pr->scratch_grad, sizeof(float) * count, cudaMemcpyDeviceToHost, s);
-  if (ce == cudaSuccess && e == FM_OK && want_loss)
-    ce = cudaMemcpyAsync(pr->h_loss, pr->d_loss, sizeof(float) * nl, cudaMemcpyDeviceToHost, s);
+    e = evaluate(pr, st, pr->scratch_params, want_grad ? pr->h_lg_grad : nullptr, nullptr, nullptr,
+                 want_loss ? pr->h_loss : nullptr);
   if (ce == cudaSuccess && e == FM_OK)
     ce = cudaMemcpyAsync(pr->h_err, pr->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
   fm::g_capturing = was;
