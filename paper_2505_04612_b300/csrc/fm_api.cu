@@ -177,7 +177,7 @@ void release(fm_problem* pr) {
   dfree(pr->rot_adam.m); dfree(pr->rot_adam.v); dfree(pr->rot_adam.t);
   dfree(pr->trn_target); dfree(pr->trn_params);
   dfree(pr->trn_adam.m); dfree(pr->trn_adam.v); dfree(pr->trn_adam.t);
-  dfree(pr->scratch_params); dfree(pr->scratch_grad); dfree(pr->d_loss); dfree(pr->d_err); dfree(pr->sc_slice_off); dfree(pr->loss_part); dfree(pr->loss_cnt);
+  dfree(pr->scratch_params); dfree(pr->scratch_grad); dfree(pr->param_snap); dfree(pr->d_loss); dfree(pr->d_err); dfree(pr->sc_slice_off); dfree(pr->loss_part); dfree(pr->loss_cnt);
   dfree(pr->loss_hist);
   dfree(pr->W);
   dfree(pr->d_kept);
@@ -606,6 +606,7 @@ fm_status build(fm_problem* pr, const fm_problem_desc* d) {
   if ((a = alloc_adam(pr, pr->trn_adam, 3 * (size_t)N)) != FM_OK) return a;
   FM_ALLOC(pr, pr->scratch_params, 9 * (size_t)N);
   FM_ALLOC(pr, pr->scratch_grad, 9 * (size_t)N);
+  FM_ALLOC(pr, pr->param_snap, 9 * (size_t)N);
   FM_ALLOC(pr, pr->d_loss, (size_t)S);
   FM_ALLOC(pr, pr->W, 64 * (((size_t)P + 31) & ~(size_t)31));   // tiles of 32 image pairs
   FM_ALLOC(pr, pr->d_kept, (size_t)S);
@@ -740,8 +741,12 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
     FM_LAUNCHED(pr);
   } else if (st == FM_STAGE_EPIPOLAR) {
     {
+      // an Adam step updates params in place while the camera pass still
+      // reads other cameras' parameters for the chain rule: that pass reads
+      // the copy taken here instead
       Timed t(pr, fm::kKEaTables);
-      fm::launch_ea_tables(params, pr->pair_i, pr->pair_j, pr->seg_off, P, pr->seg_tab, step, s);
+      fm::launch_ea_tables(params, pr->pair_i, pr->pair_j, pr->seg_off, P, pr->seg_tab, step, s, nullptr,
+                           adam ? pr->param_snap : nullptr, 9 * N);
     }
     FM_LAUNCHED(pr);
     if (pr->n_wruns > 0) {
@@ -752,7 +757,7 @@ fm_status evaluate(fm_problem* pr, fm_stage st, const float* params, float* grad
     if (adam || grad_dev) {
       // the per-image-pair chain rule, the cameras and the loss in one launch
       fm::EaCamArgs f;
-      f.s = fm::seg_args(pr, params);
+      f.s = fm::seg_args(pr, adam ? pr->param_snap : params);
       f.s.g_scale = (pr->ea_loss == FM_EA_L1) ? 1.f : 2.f;
       f.u = cam_update(pr, params, grad_dev, adam, state, step, 1);
       f.u.loss = loss_args(pr, loss_a ? loss_a : loss_b, loss_a ? loss_b : nullptr);

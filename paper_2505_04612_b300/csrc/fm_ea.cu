@@ -50,9 +50,13 @@ namespace {
 constexpr int WARPS = kEaWarpsPerCta;
 constexpr unsigned FULL = 0xffffffffu;
 
+// snap (when not null): a copy of the n_snap parameters, which the camera
+// pass of an Adam step reads for the image pairs' chain rule while it updates
+// params in place
 __global__ void k_ea_tables(const float* params, const int* __restrict__ pi,
                             const int* __restrict__ pj, const int* __restrict__ seg_off, int P,
-                            float4* __restrict__ tab, int* step_counter, const float* __restrict__ phi) {
+                            float4* __restrict__ tab, int* step_counter, const float* __restrict__ phi,
+                            float* __restrict__ snap, int n_snap) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   pdl_trigger();
   int end = 0, ci = 0, cj = 0;
@@ -63,6 +67,8 @@ __global__ void k_ea_tables(const float* params, const int* __restrict__ pi,
   }
   pdl_wait();               // params come from the previous step's update
   if (step_counter && n == 0) atomicAdd(step_counter, 1);
+  if (snap)
+    for (int k = n; k < n_snap; k += gridDim.x * blockDim.x) snap[k] = params[k];
   if (n >= P) return;
   float qi[9], qj[9];
   load_plain(params + 9 * ci, qi, 9);
@@ -444,9 +450,10 @@ __global__ void k_ea_segments(SegArgs a) {
 }  // namespace
 
 void launch_ea_tables(const float* params, const int* pi, const int* pj, const int* seg_off,
-                      int P, float4* seg_tab, int* step_counter, cudaStream_t s, const float* phi) {
-  launch_pdl(k_ea_tables, dim3((P + 127) / 128), dim3(128), 0, s, params, pi, pj, seg_off, P, seg_tab,
-             step_counter, phi);
+                      int P, float4* seg_tab, int* step_counter, cudaStream_t s, const float* phi, float* snap,
+                      int n_snap) {
+  launch_pdl(k_ea_tables, dim3((std::max(P, 1) + 127) / 128), dim3(128), 0, s, params, pi, pj, seg_off, P, seg_tab,
+             step_counter, phi, snap, n_snap);
 }
 
 template <int U, int LOSS, bool WEIGHTED, int MODE>

@@ -106,6 +106,7 @@ struct fm_problem {
   float* mart_coef = nullptr;    // [3S] per-scene constants of the rotation initialisation
   float4* lattice0 = nullptr;    // [4096] hemisphere candidates of the relative-translation search
   int* cam_pos = nullptr;        // [2P] camera-CSR index of (image pair n, role i / j)
+  float* param_snap = nullptr;   // [9N] epipolar parameters at the start of a direct Adam step
 
   // image-pair graph
   int* pair_i = nullptr;         // [P]
@@ -312,8 +313,11 @@ void launch_l2_flush(void* buf, size_t bytes, int fill, cudaStream_t s);
 void launch_exclusive_scan_info(int4* wrun_info, int n, int64_t* total_out_dev, cudaStream_t s);
 
 // epipolar (fm_ea.cu)
+// snap (optional): receives a copy of the n_snap parameters (read by the
+// camera pass of an Adam step, which updates params in place)
 void launch_ea_tables(const float* params, const int* pi, const int* pj, const int* seg_off,
-                      int P, float4* seg_tab, int* step_counter, cudaStream_t s, const float* phi = nullptr);
+                      int P, float4* seg_tab, int* step_counter, cudaStream_t s, const float* phi = nullptr,
+                      float* snap = nullptr, int n_snap = 0);
 void launch_ea_direct(const fm_problem* pr, const float* weights, int loss, cudaStream_t s);
 // the loss alone; coef_out (optional, Z floats) receives w drho/dr per pair
 void launch_ea_direct_loss(const fm_problem* pr, const float* weights, int loss, float* coef_out,

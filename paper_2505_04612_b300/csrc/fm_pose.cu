@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kPairThreads) k_rot_pairs(const float* __restr
       D[6] = -a * w1; D[7] = a * w0;  D[8] = b;
     } else {
       for (int k = 0; k < 9; ++k) D[k] = 0.f;
-  }
+    }
     // dL/dR_i = R_ij^T R_j D ;  dL/dR_j = K D^T
     float T[9];
     for (int r = 0; r < 3; ++r)

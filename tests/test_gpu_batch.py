@@ -245,3 +245,34 @@ def test_solve_reports_the_output_gauge_per_scene():
     ci = b.pair_i[b.kp_img_pair[m]]
     depth = np.einsum("nab,nb->na", Rs[ci], X)[:, 2] + out["t"].astype(np.float64)[ci, 2]
     assert np.mean(depth > 0) > 0.99
+
+
+@pytest.mark.parametrize("loss", ["l1", "l2"])
+def test_direct_adam_step_uses_the_start_parameters(loss):
+    """One direct epipolar Adam step over 2,400 cameras: the camera pass runs
+    in several waves of CTAs and updates the parameters in place while other
+    CTAs still form their image pairs' chain rule, which must use the
+    parameters the step started from.  With lr = 1 and eps = 1 the first Adam
+    update is -g / (|g| + 1) (bias-corrected moments m = g, v = g^2), so a
+    chain rule evaluated at partly updated parameters would move the result
+    by ~1e-2 relative; the step must reproduce fm_loss_grad's gradient at the
+    start within float32 rounding."""
+    import torch
+    F = _F()
+    scenes = [make_scene("c2", 10 + k, n_cams=300, n_points=6000) for k in range(8)]
+    b = concat_scenes(scenes)
+    p0 = _cat_params([perturbed_params_ea(sc, 20 + k) for k, sc in enumerate(scenes)])
+    with G.make_problem(b) as pr:
+        assert b.n_cams == 2400
+        pr.set_ea_loss(F.FM_EA_L1 if loss == "l1" else F.FM_EA_L2)
+        _, g = pr.loss_grad(F.FM_STAGE_EPIPOLAR, torch.from_numpy(p0).cuda())
+        g = g.cpu().numpy().astype(np.float64)
+        pr.set_params(F.FM_STAGE_EPIPOLAR, torch.from_numpy(p0).cuda())
+        pr.step(F.FM_STAGE_EPIPOLAR, 1, lr=1.0, beta1=0.9, beta2=0.999, eps=1.0)
+        p1 = pr.get_params(F.FM_STAGE_EPIPOLAR).cpu().numpy().astype(np.float64)
+    # Adam's first step in float64 from the float32 gradient
+    m, v = 0.1 * g, 0.001 * g * g
+    want = p0.astype(np.float64) - (m / 0.1) / (np.sqrt(v / 0.001) + 1.0)
+    err = np.abs(p1 - want)
+    scale = np.abs(p0.astype(np.float64) - want)
+    assert np.all(err <= 1e-5 * scale + 2e-7 * (1.0 + np.abs(want))), float(np.max(err))
