@@ -110,14 +110,19 @@ def peaks():
 
 
 def source_hash():
-    """Hash of what defines k_ea_direct: fm_ea.cu, fm_device.cuh and the
-    direct kernel's constants in fm_internal.h (tile, stages, CTAs, lane
-    descriptor, error bit).  A committed ncu summary whose source_sha differs
-    was taken on another kernel: its traffic is not reported."""
+    """Hash of what defines k_ea_direct: its part of fm_ea.cu (from the
+    DirectArgs struct to the next kernel, and its launcher), fm_device.cuh,
+    and the direct kernel's constants in fm_internal.h (tile, stages, CTAs,
+    lane descriptor, error bit).  A committed ncu summary whose source_sha
+    differs was taken on another kernel: its traffic is not reported."""
     csrc = os.path.join(ROOT, "paper_2505_04612_b300", "csrc")
     h = hashlib.sha256()
-    for f in ["fm_ea.cu", "fm_device.cuh"]:
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    ea = open(os.path.join(csrc, "fm_ea.cu"), "rb").read()
+    for a, b in ((b"struct DirectArgs {", b"__global__ void k_ea_segments"),
+                 (b"static void launch_direct_u", b"int direct_max_ctas_per_sm")):
+        i, j = ea.find(a), ea.find(b)
+        h.update(ea[i:j] if 0 <= i < j else ea)
+    h.update(open(os.path.join(csrc, "fm_device.cuh"), "rb").read())
     for line in open(os.path.join(csrc, "fm_internal.h"), "rb"):
         if any(t in line for t in (b"FM_EA_", b"kEa", b"kDesc", b"kErrEaTimeout")):
             h.update(line)
