@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(kThreads) k_cam(CamUpdate u) {
   const size_t off = ((size_t)run * u.N + c) * L::PDIM;
   float p[L::PDIM];
   float m = 0.f, v = 0.f;
+  step::CamPre cpre;
   if (t < 32) {
 #pragma unroll
     for (int k = 0; k < L::PDIM; ++k) p[k] = u.params[off + k];
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(kThreads) k_cam(CamUpdate u) {
       m = u.m[off + lane];
       v = u.v[off + lane];
     }
+    step::cam_pre<STAGE, ADAM>(u, p, cpre);
   }
   float acc[L::PART];
 #pragma unroll
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) k_cam(CamUpdate u) {
       step::cam_add<L::PART>(sg, __ldg(u.cam_seg + idx), acc);
   }
   step::cam_reduce<L::PART>(acc, red);
-  if (t < 32) step::cam_apply<STAGE, ADAM>(u, off, p, m, v, acc, lane);
+  if (t < 32) step::cam_apply<STAGE, ADAM>(u, off, p, m, v, acc, lane, cpre);
 }
 
 // the loss slices alone: seg_loss summed per (scene, run)
@@ -154,6 +156,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_cam_ea(EaCamArgs f) {
   const size_t off = (size_t)c * 9;
   float p[9];
   float m = 0.f, v = 0.f;
+  step::CamPre cpre;
   if (t < 32) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) p[k] = u.params[off + k];
@@ -161,6 +164,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_cam_ea(EaCamArgs f) {
       m = u.m[off + lane];
       v = u.v[off + lane];
     }
+    step::cam_pre<2, ADAM>(u, p, cpre);
   }
   float acc[12];
 #pragma unroll
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_cam_ea(EaCamArgs f) {
     cam_entry_part(s, en, qi, qj, acc);
   }
   step::cam_reduce<12>(acc, red);
-  if (t < 32) step::cam_apply<2, ADAM>(u, off, p, m, v, acc, lane);
+  if (t < 32) step::cam_apply<2, ADAM>(u, off, p, m, v, acc, lane, cpre);
 }
 
 template <int STAGE>

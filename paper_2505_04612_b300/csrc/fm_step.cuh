@@ -236,20 +236,36 @@ __device__ __forceinline__ void cam_reduce(float* acc, float (*red)[PART]) {
     }
 }
 
-// Camera c of run `run` from its summed parts, its parameters p and (Adam)
-// its moments m, v of lane's entry (all loaded beforehand): the 6D adjoint
-// for rotations, then either the gradient or Adam (bias-corrected; the step
-// counter was advanced by this step's first kernel), by lanes < PDIM of
-// warp 0.
+// What cam_apply needs besides the summed parts, formed from the camera's
+// parameters p as soon as they are loaded (off the critical path of the
+// gather and the reduction): the 6D map's forward state and Adam's bias
+// corrections (the step counter was advanced by this step's first kernel).
+struct CamPre {
+  Rot6 s;
+  float bc1, bc2;
+};
+
+template <int STAGE, bool ADAM>
+__device__ __forceinline__ void cam_pre(const CamUpdate& u, const float* p, CamPre& pre) {
+  if (Layout<STAGE>::ROT) rot6_forward(p, pre.s);
+  if (ADAM) {
+    const float t = (float)*u.step;
+    pre.bc1 = 1.f - powf(u.b1, t);
+    pre.bc2 = 1.f - powf(u.b2, t);
+  }
+}
+
+// Camera c of run `run` from its summed parts, its parameters p, cam_pre's
+// state and (Adam) its moments m, v of lane's entry (all loaded beforehand):
+// the 6D adjoint for rotations, then either the gradient or Adam
+// (bias-corrected), by lanes < PDIM of warp 0.
 template <int STAGE, bool ADAM>
 __device__ __forceinline__ void cam_apply(const CamUpdate& u, size_t off, const float* p, float m, float v,
-                                          const float* acc, int lane) {
+                                          const float* acc, int lane, const CamPre& pre) {
   using L = Layout<STAGE>;
   float g[L::PDIM];
   if (L::ROT) {
-    Rot6 s;
-    rot6_forward(p, s);
-    rot6_adjoint(p, s, acc, g);
+    rot6_adjoint(p, pre.s, acc, g);
     if (STAGE == 2) {
       g[6] = acc[9];
       g[7] = acc[10];
@@ -269,23 +285,21 @@ __device__ __forceinline__ void cam_apply(const CamUpdate& u, size_t off, const 
     return;
   }
   if (u.grad_out) u.grad_out[off + lane] = gv;
-  const float t = (float)*u.step;
-  const float bc1 = 1.f - powf(u.b1, t);
-  const float bc2 = 1.f - powf(u.b2, t);
   m = u.b1 * m + (1.f - u.b1) * gv;
   v = u.b2 * v + (1.f - u.b2) * gv * gv;
   u.m[off + lane] = m;
   u.v[off + lane] = v;
-  u.params_out[off + lane] = pv - u.lr * (m / bc1) / (sqrtf(v / bc2) + u.eps);
+  u.params_out[off + lane] = pv - u.lr * (m / pre.bc1) / (sqrtf(v / pre.bc2) + u.eps);
 }
 
 // ------------------------------------------------------------------- losses
 // A scene's loss, the sum of its image pairs' loss terms x_0 .. x_{n-1}, is
 // added in slices of kSlice terms: slice k (terms kSlice k ..) by one CTA,
 // thread t adding the terms t, t + kThreads, ... of the slice in order, a
-// tree over the threads; then the slices' sums in slice order.  One CTA per
-// slice; the last to finish (an arrival counter per (scene, run) on a line of
-// its own, reset by it) adds the slices.  The order depends on n only.
+// tree over the threads; then the slices' sums the same way (thread-strided
+// over the slices, then the tree).  One CTA per slice; the last to finish (an
+// arrival counter per (scene, run) on a line of its own, reset by it) adds
+// the slices.  The order depends on n only.
 constexpr int kSlice = kLossSlice;
 
 // the scene of global slice g: the largest s with sc_slice_off[s] <= g
@@ -333,14 +347,22 @@ __device__ __forceinline__ void loss_slice(const LossArgs& L, int sc, int g, int
     if (last) __threadfence();
   }
   __syncthreads();
-  if (last && t == 0) {
+  if (last) {   // the same value in every thread: the whole CTA adds the slices
     const float* ps = partial + L.sc_slice_off[sc];
     float s = 0.f;
-    for (int q = 0; q < n_slices; ++q) s += __ldcg(ps + q);
-    const size_t o = (size_t)run * L.S + sc;
-    L.out[o] = s;
-    if (L.out2) L.out2[o] = s;
-    *cnt = 0;   // ready for the next launch
+    for (int q = t; q < n_slices; q += kThreads) s += __ldcg(ps + q);
+    part[t] = s;
+    __syncthreads();
+    for (int d = kThreads / 2; d > 0; d >>= 1) {
+      if (t < d) part[t] += part[t + d];
+      __syncthreads();
+    }
+    if (t == 0) {
+      const size_t o = (size_t)run * L.S + sc;
+      L.out[o] = part[0];
+      if (L.out2) L.out2[o] = part[0];
+      *cnt = 0;   // ready for the next launch
+    }
   }
 }
 
