@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -508,28 +509,35 @@ int grid_for(int64_t n, int threads = 256) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 148 * 64));
 }
 
-// Stream-ordered memory pool of the track completion, owned by the library
-// and kept for the process (its memory is reused from call to call instead
-// of being mapped and unmapped with cudaMalloc / cudaFree, whose frees
-// synchronise the device).
+// Stream-ordered memory pools of the track completion and the device sorts,
+// one per device, owned by the library and kept for the process (their
+// memory is reused from call to call instead of being mapped and unmapped
+// with cudaMalloc / cudaFree, whose frees synchronise the device).
 cudaMemPool_t tracks_pool() {
-  static cudaMemPool_t pool = [] {
+  constexpr int kDevices = 64;
+  static std::mutex mu;
+  static cudaMemPool_t pools[kDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
     cudaMemPool_t p = nullptr;
-    int dev = 0;
-    cudaGetDevice(&dev);
     cudaMemPoolProps props = {};
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
     props.location.id = dev;
     if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
       cudaGetLastError();
-      return (cudaMemPool_t) nullptr;
+      return nullptr;
     }
     uint64_t keep = UINT64_MAX;
     cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
-    return p;
-  }();
-  return pool;
+    pools[dev] = p;
+  }
+  return pools[dev];
 }
 
 // scratch of one call: pool allocations on the call's stream, returned to
