@@ -276,14 +276,20 @@ __global__ void __launch_bounds__(kRows, 1) k_mlp_forward_tc(InferArgs a, int* e
 template <bool PAIRS>
 void launch_tc(const InferArgs& a, int* err, int sm_count, cudaStream_t s) {
   if (a.Z == 0) return;
-  static int per_sm = 0;   // resident CTAs per SM, bound by shared memory (one device per process)
+  // resident CTAs per SM, bound by shared memory; the shared-memory limit is
+  // a per-device setting, so both are kept per device
+  static std::atomic<int> per_sm_dev[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int slot = (dev >= 0 && dev < 64) ? dev : 0;
+  int per_sm = per_sm_dev[slot].load();
   if (per_sm == 0) {
     cudaFuncSetAttribute(k_mlp_forward_tc<PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn);
-    int dev = 0, smem_sm = 0, reserved = 0;
-    cudaGetDevice(&dev);
+    int smem_sm = 0, reserved = 0;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
     per_sm = std::max(1, std::min(kCtasPerSm, smem_sm / (kSmemDyn + reserved)));
+    per_sm_dev[slot].store(per_sm);
   }
   static_assert(kSmemUsed <= kSmemDyn, "shared memory layout");
   const int64_t tiles = (a.Z + kRows - 1) / kRows;
