@@ -898,7 +898,7 @@ def mlp_training_time(x, y, steps, warmup, flush):
             "tiles_of_128_rows": tiles, "loss": loss,
             "roofline": {"bound": "tensor", "achieved": achieved, "unit": "TFLOP/s", "kernel": "k_mlp_grad_tc + k_mlp_reduce",
                          "flop_per_row": MLP_TRAIN_FLOP_PER_ROW,
-                         "note": "the exact-erf GELUs and their derivatives (256 erf + 128 exp per row) on the "
+                         "note": "the exact-erf GELUs and their derivatives (128 erf + 128 exp per row) on the "
                                  "FP32 pipe bound it, not the tensor cores"}}
 
 

@@ -112,6 +112,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// v[0..15] into this warp's lanes, columns taddr .. taddr + 15; returns
+// after the stores are done
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
@@ -317,10 +332,12 @@ void launch_tc(const InferArgs& a, int* err, int sm_count, cudaStream_t s) {
 // whose accumulator DW (128 TMEM columns, kept across the CTA's tiles) holds
 // dW2 = h1^T dz2 in rows 0..63, columns 0..63 and dW1 = x^T dz1 in rows
 // 64..71, columns 64..127; its other blocks are not used.
-// The operands rounded to bf16 are those of the mma.sync definition: x, W1,
-// h1, W2 forward, dz2 and dz1 backward (with W2 and x, h1).  z1 stays in TMEM
-// for GELU'(z1); z2 is read twice (the logit first, then dz2 = dl w3 GELU'(z2)
-// once dl is known).  The bias gradients and dw3 are fp32 sums over the rows:
+// The operands rounded to bf16 are those of the oracle's definition: x, W1,
+// h1, W2 forward, dz2 and dz1 backward (with W2 and x, h1).  Each layer's
+// pre-activations are read from TMEM once, and one erf and one exp per
+// element give both GELU and GELU': h1 goes to RT and GELU'(z1) replaces z1
+// in TMEM; h2 stays in registers (the logit, then dw3 once dl is known) and
+// GELU'(z2) replaces z2 until dz2 = dl w3 GELU'(z2) is formed.  The bias gradients and dw3 are fp32 sums over the rows:
 // per warp, a fixed butterfly that leaves column c of each 16-column chunk in
 // lanes 2c, 2c + 1, accumulated over tiles per lane, then added over warps
 // in warp order.  Per-CTA partials are summed in CTA order by k_mlp_reduce:
@@ -349,8 +366,11 @@ constexpr uint32_t kIdescW = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (
 // byte offset of entry (row r, e) in an RT / GT tile
 __device__ __forceinline__ int rt_off(int r, int e) { return (r >> 3) * 2048 + (e >> 3) * 128 + (r & 7) * 16 + (e & 7) * 2; }
 
-__device__ __forceinline__ float gelu_grad_tc(float z) {
-  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+// GELU(z) = z Phi(z) (as gelu_tc) and GELU'(z) = Phi(z) + z phi(z), from one erf
+__device__ __forceinline__ void gelu_both(float z, float& h, float& g) {
+  const float e = erff(z * 0.70710678118654752f);
+  h = 0.5f * z * (1.f + e);
+  g = 0.5f * (1.f + e) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
 // the sum over the warp's lanes of v[0..15]; lane l returns the sum of
@@ -468,15 +488,16 @@ __global__ void __launch_bounds__(kRows, 1) k_mlp_grad_tc(TrainArgs a, int* err)
     phase ^= 1u;
     if (__syncthreads_or(!ok)) break;
     fence_after();
-    // ---- h1 = GELU(z1 + b1) into RT
+    // ---- h1 = GELU(z1 + b1) into RT; GELU'(z1 + b1) replaces z1 in TMEM
 #pragma unroll 1
     for (int c = 0; c < kN; c += 16) {
-      float v[16];
+      float v[16], g[16];
       tmem_ld16(tmem + lane_base + (uint32_t)c, v);
 #pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = gelu_tc(v[k] + par[c + k]);
+      for (int k = 0; k < 16; ++k) gelu_both(v[k] + par[c + k], v[k], g[k]);
       store_bf16x8(my_rt, (c >> 3) * 128, v);
       store_bf16x8(my_rt, (c >> 3) * 128 + 128, v + 8);
+      tmem_st16(tmem + lane_base + (uint32_t)c, g);
     }
     fence_async_smem();
     fence_before();
@@ -492,14 +513,20 @@ __global__ void __launch_bounds__(kRows, 1) k_mlp_grad_tc(TrainArgs a, int* err)
     phase ^= 1u;
     if (__syncthreads_or(!ok)) break;
     fence_after();
-    // ---- the logit, then dl = dL/do
+    // ---- the logit, then dl = dL/do; h2 stays in registers, GELU'(z2)
+    // replaces z2 in TMEM
     float o = 0.f;
-#pragma unroll 1
+    float h2[kN];
+#pragma unroll
     for (int c = 0; c < kN; c += 16) {
-      float v[16];
+      float v[16], g[16];
       tmem_ld16(tmem + lane_base + 64 + (uint32_t)c, v);
 #pragma unroll
-      for (int k = 0; k < 16; ++k) o = fmaf(gelu_tc(v[k] + par[kN + c + k]), par[2 * kN + c + k], o);
+      for (int k = 0; k < 16; ++k) {
+        gelu_both(v[k] + par[kN + c + k], h2[c + k], g[k]);
+        o = fmaf(h2[c + k], par[2 * kN + c + k], o);
+      }
+      tmem_st16(tmem + lane_base + 64 + (uint32_t)c, g);
     }
     o += par[3 * kN];
     const float dl = valid ? (1.f / (1.f + expf(-o)) - y) * a.inv_b : 0.f;
@@ -509,13 +536,12 @@ __global__ void __launch_bounds__(kRows, 1) k_mlp_grad_tc(TrainArgs a, int* err)
     // per-chunk accumulators stay in registers)
 #pragma unroll
     for (int c = 0; c < kN; c += 16) {
-      float v[16], dz[16], hw[16];
-      tmem_ld16(tmem + lane_base + 64 + (uint32_t)c, v);
+      float g[16], dz[16], hw[16];
+      tmem_ld16(tmem + lane_base + 64 + (uint32_t)c, g);
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        const float z = v[k] + par[kN + c + k];
-        dz[k] = dl * par[2 * kN + c + k] * gelu_grad_tc(z);
-        hw[k] = gelu_tc(z) * dl;
+        dz[k] = dl * par[2 * kN + c + k] * g[k];
+        hw[k] = h2[c + k] * dl;
       }
       store_bf16x8(my_gt, (c >> 3) * 128, dz);
       store_bf16x8(my_gt, (c >> 3) * 128 + 128, dz + 8);
@@ -539,11 +565,11 @@ __global__ void __launch_bounds__(kRows, 1) k_mlp_grad_tc(TrainArgs a, int* err)
     // ---- dz1 = dh1 GELU'(z1) into GT; db1 column sums
 #pragma unroll
     for (int c = 0; c < kN; c += 16) {
-      float dh[16], z1[16];
+      float dh[16], g1[16];
       tmem_ld16(tmem + lane_base + 64 + (uint32_t)c, dh);
-      tmem_ld16(tmem + lane_base + (uint32_t)c, z1);
+      tmem_ld16(tmem + lane_base + (uint32_t)c, g1);
 #pragma unroll
-      for (int k = 0; k < 16; ++k) dh[k] *= gelu_grad_tc(z1[k] + par[c + k]);
+      for (int k = 0; k < 16; ++k) dh[k] *= g1[k];
       store_bf16x8(my_gt, 8 * 128 + (c >> 3) * 128, dh);
       store_bf16x8(my_gt, 8 * 128 + (c >> 3) * 128 + 128, dh + 8);
       acc_b1[c >> 4] += col_sum16(dh);
