@@ -1115,8 +1115,9 @@ def learned_vs_plain(seed, train_scenes, eval_cams, eval_points, eval_track, eva
     points, track length 2 + Geometric (mean `eval_track`), an outlier
     fraction of `eval_outliers`, relative rotations with 1 deg noise.  The
     plain fm_solve (5 filtering rounds) and the learned one (2 pruning
-    passes, 1 round) are timed end to end (wall clock around the call, after
-    a warm-up solve); accuracy is the mean rotation error and the mean
+    passes, 1 round) are timed end to end (wall clock around the call, the
+    median of three after a warm-up solve); accuracy is the mean rotation
+    error and the mean
     camera-centre error (relative to the scene's size, after a similarity
     alignment) over the connected cameras.  Returns a dict with the ratio
     plain time / learned time when the learned solve is at least as accurate
