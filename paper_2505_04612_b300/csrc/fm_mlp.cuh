@@ -1,5 +1,5 @@
 // The features of a keypoint pair for the learned inlier network, shared by
-// the mma.sync and the tcgen05 kernels.  Definitions (readings) are those of
+// the feature-only kernel and the tcgen05 network kernel.  Definitions (readings) are those of
 // the learned-weights section of include/fastmap.h: the epipolar residual
 // over the image pair's mean residual, the log of the residual over its
 // Sampson scale, the log of the track length, the angle between the two
