@@ -115,3 +115,30 @@ def test_compact_adam_steps():
         x = opt.step(x, ep.compact_loss_grad(x, sc.pair_i, sc.pair_j, W, float(inv_z))[1])
     assert np.max(np.abs(got - x)) < 1e-5
     assert np.max(np.abs(got - G.f32(p0))) > 0.5 * lr
+
+
+def test_compact_at_scale_matches_oracle():
+    """The compact step on a 600-camera scene (thousands of image pairs: many
+    32-pair tiles of W, a ragged last one, camera passes over up to a few
+    hundred incident image pairs read in camera-CSR order) against the
+    oracle, unweighted and IRLS-weighted."""
+    from paper_2505_04612_b300 import fastmap as F
+    from synthetic.scenes import make_scene
+    sc = make_scene("c2", 7, n_cams=600, n_points=120000)
+    assert sc.n_pairs > 5000 and sc.n_pairs % 32 != 0
+    x1, x2 = G.oracle_xs(sc)
+    p0 = _near(sc, 7)
+    w, inv_z = _oracle_weights(sc, p0)
+    for weighted in (False, True):
+        W = ep.build_W(x1, x2, sc.kp_img_pair, sc.n_pairs, weights=G.f32(w) if weighted else None)
+        iz = float(inv_z) if weighted else 1.0 / sc.n_kp
+        with G.make_problem(sc) as pr:
+            pr.set_params(F.FM_STAGE_EPIPOLAR, p0.reshape(-1))
+            if weighted:
+                pr.set_ea_weights(w, inv_z)
+            pr.set_ea_loss(F.FM_EA_COMPACT)
+            p = (p0 + np.random.default_rng(8).normal(0, 1e-3, size=p0.shape)).astype(np.float32)
+            L, g = pr.loss_grad(F.FM_STAGE_EPIPOLAR, p.reshape(-1))
+        Lo, go, _ = ep.compact_loss_grad(G.f32(p), sc.pair_i, sc.pair_j, W, iz)
+        assert abs(L - Lo) <= LOSS_TOL * Lo, (weighted, L, Lo)
+        assert G.rel_err(np.asarray(g).reshape(go.shape), go) < GRAD_TOL

@@ -161,3 +161,34 @@ def test_loss_trace_and_timing():
     # cameras' Adam update and the loss (trace and returned value alike)
     assert kt["k_cam_ea"][0] == 20 and kt["k_ea_tables"][0] == 20
     assert not {"k_ea_segments", "k_cam", "k_sum_fixed"} & set(kt)
+
+
+def test_rotation_and_translation_at_scale():
+    """Both stages on a 600-camera scene (thousands of image pairs, up to a
+    few hundred per camera) against the oracle; the translation stage with 4
+    runs batched."""
+    torch = _torch()
+    from paper_2505_04612_b300 import fastmap as F
+    from synthetic.scenes import make_scene
+    sc = make_scene("c2", 8, n_cams=600, n_points=120000)
+    Rij, tij = gt_relative_poses(sc, rot_noise_deg=2.0, dir_noise_deg=2.0, seed=8)
+    Rij, tij = Rij.astype(np.float32), tij.astype(np.float32)
+    rng = np.random.default_rng(8)
+    p6 = (gt_params6(sc) + rng.normal(0, 0.05, size=(sc.n_cams, 6))).astype(np.float32)
+    runs = 4
+    o = np.stack([sc.centers_gt + rng.normal(0, 0.3, size=(sc.n_cams, 3)) for _ in range(runs)]).astype(np.float32)
+    with G.make_problem(sc, rel_R=Rij, rel_t=tij) as pr:
+        L, g = pr.loss_grad(F.FM_STAGE_ROTATION, torch.from_numpy(p6.reshape(-1)).cuda())
+        Lo, go = rot.loss_grad(G.f32(p6), sc.pair_i, sc.pair_j, G.f32(Rij))
+        assert abs(L - Lo) <= LOSS_TOL * Lo, (L, Lo)
+        assert G.rel_err(g.cpu().numpy().reshape(go.shape), go) < GRAD_TOL
+        pr.set_params(F.FM_STAGE_ROTATION, p6.reshape(-1))
+        pr.set_translation_runs(runs)
+        Lt, gt = pr.loss_grad(F.FM_STAGE_TRANSLATION, torch.from_numpy(o.reshape(-1)).cuda())
+    Lt = np.atleast_1d(Lt)
+    gt = gt.cpu().numpy().reshape(runs, sc.n_cams, 3)
+    tgt = trn.targets(rot_from_6d(G.f32(p6)), sc.pair_j, G.f32(tij))
+    for r in range(runs):
+        Lo, go = trn.loss_grad(G.f32(o[r]), sc.pair_i, sc.pair_j, tgt)
+        assert abs(Lt[r] - Lo) <= LOSS_TOL * Lo
+        assert G.rel_err(gt[r], go) < GRAD_TOL
