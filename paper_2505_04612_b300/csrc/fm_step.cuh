@@ -295,9 +295,9 @@ __device__ __forceinline__ void cam_apply(const CamUpdate& u, size_t off, const 
 // ------------------------------------------------------------------- losses
 // A scene's loss, the sum of its image pairs' loss terms x_0 .. x_{n-1}, is
 // added in slices of kSlice terms: slice k (terms kSlice k ..) by one CTA,
-// thread t adding the terms t, t + kThreads, ... of the slice in order, a
-// tree over the threads; then the slices' sums the same way (thread-strided
-// over the slices, then the tree).  One CTA per slice; the last to finish (an
+// thread t adding the terms t, t + kThreads, ... of the slice in order, xor
+// butterflies in each warp and the warps in order; then the slices' sums the
+// same way (thread-strided over the slices, butterflies, warps in order).  One CTA per slice; the last to finish (an
 // arrival counter per (scene, run) on a line of its own, reset by it) adds
 // the slices.  The order depends on n only.
 constexpr int kSlice = kLossSlice;
@@ -318,9 +318,22 @@ __device__ __forceinline__ int slice_scene(const int* sc_slice_off, int S, int g
 // together.  Every thread of the CTA calls it.
 constexpr int kPerThread = kSlice / kThreads;
 
+// the CTA's sum of one value per thread: xor butterflies in each warp, then
+// the warps' sums in warp order (thread 0 returns it; every thread calls it)
+__device__ __forceinline__ float cta_sum(float v, float* wpart) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) wpart[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float s = 0.f;
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) s += wpart[w];
+  return s;
+}
+
 template <typename Fill>
 __device__ __forceinline__ void loss_slice(const LossArgs& L, int sc, int g, int run, Fill fill) {
-  __shared__ float part[kThreads];
+  __shared__ float wpart[2][kThreads / 32];
   __shared__ int last;
   const int t = threadIdx.x;
   const int n = L.sc_pair_off[sc + 1] - L.sc_pair_off[sc];
@@ -331,17 +344,12 @@ __device__ __forceinline__ void loss_slice(const LossArgs& L, int sc, int g, int
   float acc = 0.f;
 #pragma unroll
   for (int u = 0; u < kPerThread; ++u) acc += v[u];   // terms past the slice are +0 (terms are >= 0)
-  part[t] = acc;
-  __syncthreads();
-  for (int d = kThreads / 2; d > 0; d >>= 1) {
-    if (t < d) part[t] += part[t + d];
-    __syncthreads();
-  }
+  const float slice = cta_sum(acc, wpart[0]);
   const int n_slices = L.sc_slice_off[sc + 1] - L.sc_slice_off[sc];
   float* partial = L.partial + (size_t)run * L.n_slices;
   int* cnt = L.cnt + ((size_t)run * L.S + sc) * kLossCntStride;
   if (t == 0) {
-    partial[g] = part[0];
+    partial[g] = slice;
     __threadfence();   // this slice's sum before its count
     last = atomicAdd(cnt, 1) == n_slices - 1;
     if (last) __threadfence();
@@ -349,18 +357,13 @@ __device__ __forceinline__ void loss_slice(const LossArgs& L, int sc, int g, int
   __syncthreads();
   if (last) {   // the same value in every thread: the whole CTA adds the slices
     const float* ps = partial + L.sc_slice_off[sc];
-    float s = 0.f;
-    for (int q = t; q < n_slices; q += kThreads) s += __ldcg(ps + q);
-    part[t] = s;
-    __syncthreads();
-    for (int d = kThreads / 2; d > 0; d >>= 1) {
-      if (t < d) part[t] += part[t + d];
-      __syncthreads();
-    }
+    float q = 0.f;
+    for (int i = t; i < n_slices; i += kThreads) q += __ldcg(ps + i);
+    const float total = cta_sum(q, wpart[1]);
     if (t == 0) {
       const size_t o = (size_t)run * L.S + sc;
-      L.out[o] = part[0];
-      if (L.out2) L.out2[o] = part[0];
+      L.out[o] = total;
+      if (L.out2) L.out2[o] = total;
       *cnt = 0;   // ready for the next launch
     }
   }
