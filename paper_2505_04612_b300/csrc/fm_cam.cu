@@ -4,7 +4,7 @@
 // map (Sec. 3.3), and Adam updates the camera's parameters in place.
 //
 // k_cam          one CTA per camera: thread t adds the incident image pairs
-//                t, t + 128, ... (the first read from the CSR before the
+//                t, t + 128, ... (the first two read from the CSR before the
 //                dependency wait), warps combine by butterflies and in warp
 //                order, warp 0 applies the adjoint and Adam; its parameters
 //                and moments are loaded while the parts are gathered.  When a
@@ -47,7 +47,9 @@ __global__ void __launch_bounds__(kThreads) k_cam(CamUpdate u) {
   const int c = blockIdx.x, t = threadIdx.x, lane = t & 31;
   // static: before the wait
   const int b = u.cam_seg_off[c], e = u.cam_seg_off[c + 1];
-  const int pre = (b + t < e && !u.csr_order) ? __ldg(u.cam_seg + b + t) : -1;
+  // this thread's first two camera-CSR entries, before the wait
+  const int pre0 = (b + t < e && !u.csr_order) ? __ldg(u.cam_seg + b + t) : -1;
+  const int pre1 = (b + t + kThreads < e && !u.csr_order) ? __ldg(u.cam_seg + b + t + kThreads) : -1;
   pdl_wait();
   // parameters and moments do not depend on the gather: loaded with it
   const size_t off = ((size_t)run * u.N + c) * L::PDIM;
@@ -70,8 +72,9 @@ __global__ void __launch_bounds__(kThreads) k_cam(CamUpdate u) {
   if (u.csr_order) {   // the parts already in camera-CSR order: contiguous, same order of additions
     for (int idx = b + t; idx < e; idx += kThreads) step::cam_add_part<L::PART>(sg + (size_t)idx * L::PART, acc);
   } else {
-    if (pre != -1) step::cam_add<L::PART>(sg, pre, acc);
-    for (int idx = b + t + kThreads; idx < e; idx += kThreads)
+    if (pre0 != -1) step::cam_add<L::PART>(sg, pre0, acc);
+    if (pre1 != -1) step::cam_add<L::PART>(sg, pre1, acc);
+    for (int idx = b + t + 2 * kThreads; idx < e; idx += kThreads)
       step::cam_add<L::PART>(sg, __ldg(u.cam_seg + idx), acc);
   }
   step::cam_reduce<L::PART>(acc, red);
