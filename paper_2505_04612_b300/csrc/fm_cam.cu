@@ -68,14 +68,15 @@ __global__ void __launch_bounds__(kThreads) k_cam(CamUpdate u) {
   float acc[L::PART];
 #pragma unroll
   for (int k = 0; k < L::PART; ++k) acc[k] = 0.f;
-  const float* sg = u.seg_grad + (size_t)run * u.P * 2 * L::PART;
+  const float* sg = u.seg_grad + (size_t)run * u.P * 2 * L::STRIDE;
   if (u.csr_order) {   // the parts already in camera-CSR order: contiguous, same order of additions
-    for (int idx = b + t; idx < e; idx += kThreads) step::cam_add_part<L::PART>(sg + (size_t)idx * L::PART, acc);
+    for (int idx = b + t; idx < e; idx += kThreads)
+      step::cam_add_part<L::PART, L::STRIDE>(sg + (size_t)idx * L::STRIDE, acc);
   } else {
-    if (pre0 != -1) step::cam_add<L::PART>(sg, pre0, acc);
-    if (pre1 != -1) step::cam_add<L::PART>(sg, pre1, acc);
+    if (pre0 != -1) step::cam_add<L::PART, L::STRIDE>(sg, pre0, acc);
+    if (pre1 != -1) step::cam_add<L::PART, L::STRIDE>(sg, pre1, acc);
     for (int idx = b + t + 2 * kThreads; idx < e; idx += kThreads)
-      step::cam_add<L::PART>(sg, __ldg(u.cam_seg + idx), acc);
+      step::cam_add<L::PART, L::STRIDE>(sg, __ldg(u.cam_seg + idx), acc);
   }
   step::cam_reduce<L::PART>(acc, red);
   if (t < 32) step::cam_apply<STAGE, ADAM>(u, off, p, m, v, acc, lane, cpre);

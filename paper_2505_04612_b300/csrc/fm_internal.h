@@ -44,8 +44,8 @@ constexpr int kMlpParams = 4801;   // W1 [8][64], b1, W2 [64][64], b2, w3, b3
 constexpr int kMlpFeatures = 8;
 static_assert(kEaPairsPerLane % 2 == 1, "lane-contiguous shared-memory reads need an odd stride");
 constexpr int kSegGradEa = 24;                   // dR_i, dt_i, dR_j, dt_j
-constexpr int kSegGradRot = 18;                  // dR_i, dR_j
-constexpr int kSegGradTrn = 6;                   // do_i, do_j
+constexpr int kSegGradRot = 24;                  // dR_i, dR_j: 9 floats each in a 48-byte slot
+constexpr int kSegGradTrn = 8;                   // do_i, do_j: 3 floats each in a 16-byte slot
 
 // error bits raised by device-side validation
 enum : int {
@@ -473,7 +473,7 @@ struct LossArgs {
 struct CamUpdate {
   const int* cam_seg_off;
   const int* cam_seg;
-  const float* seg_grad;   // [runs][P][2*part]
+  const float* seg_grad;   // [runs][P][2*stride]: two 16-byte-aligned slots per image pair
   const float* params;     // [runs][N][pdim] parameters the gradient was taken at
   float* params_out;       // Adam: updated in place (== params); else null
   float* grad_out;         // gradient output or null
@@ -484,7 +484,7 @@ struct CamUpdate {
   int N, P, runs;
   const float* seg_loss;   // [runs][P] per-image-pair loss terms (k_cam's loss slices)
   LossArgs loss;           // loss.out null: no loss
-  bool csr_order;          // seg_grad holds the parts in camera-CSR order ([2P][part], one run)
+  bool csr_order;          // seg_grad holds the parts in camera-CSR order ([2P][stride], one run)
 };
 void launch_cam_update(int stage, const CamUpdate& u, cudaStream_t s);
 // the epipolar step after k_ea_direct: s as for k_ea_segments (its seg_grad,

@@ -13,9 +13,9 @@ namespace {
 // in float32 near 0, where arccos of a value next to 1 does not.
 // dtheta/dM = (c [w]_x / (2|w|) - |w| I / 2) / (|w|^2 + c^2); 0 at |w| = 0.
 // A CTA's 128 image pairs read their relative rotations as one contiguous
-// block and write their 18-float gradients as one (through shared memory,
-// odd strides: no bank conflicts), instead of 9 and 18 strided accesses per
-// thread.
+// block and write their gradients (two 48-byte slots, 9 floats each) as one
+// (through shared memory, odd strides: no bank conflicts), instead of
+// strided accesses per thread.
 constexpr int kPairThreads = 128;
 
 // cnt rows of W floats between contiguous global memory and shared-memory
@@ -88,14 +88,15 @@ __global__ void __launch_bounds__(kPairThreads) k_rot_pairs(const float* __restr
       for (int cc = 0; cc < 3; ++cc)
         T[r * 3 + cc] = fmaf(Rij[0 * 3 + r], Rj[0 * 3 + cc],
                         fmaf(Rij[1 * 3 + r], Rj[1 * 3 + cc], Rij[2 * 3 + r] * Rj[2 * 3 + cc]));
-    float* out = out_s + kOutStride * threadIdx.x;
+    float* out = out_s + kOutStride * threadIdx.x;   // dR_i in [0, 9), dR_j in [12, 21), zeros between
     for (int r = 0; r < 3; ++r)
       for (int cc = 0; cc < 3; ++cc) {
         out[r * 3 + cc] = fmaf(T[r * 3 + 0], D[0 * 3 + cc],
                           fmaf(T[r * 3 + 1], D[1 * 3 + cc], T[r * 3 + 2] * D[2 * 3 + cc]));
-        out[9 + r * 3 + cc] = fmaf(K[r * 3 + 0], D[cc * 3 + 0],
-                              fmaf(K[r * 3 + 1], D[cc * 3 + 1], K[r * 3 + 2] * D[cc * 3 + 2]));
+        out[12 + r * 3 + cc] = fmaf(K[r * 3 + 0], D[cc * 3 + 0],
+                               fmaf(K[r * 3 + 1], D[cc * 3 + 1], K[r * 3 + 2] * D[cc * 3 + 2]));
       }
+    for (int k = 9; k < 12; ++k) out[k] = out[12 + k] = 0.f;
   }
   __syncthreads();
   if (cnt > 0) store_rows<kOut, kOutStride>(out_s, cnt, seg_grad + (size_t)kOut * n0);
@@ -117,7 +118,8 @@ __global__ void k_trn_targets(const float* __restrict__ rot, const int* __restri
 // L_t term (Eq. 6): || u - o^{i->j} ||_1 with u = (o_j - o_i)/|o_j - o_i|;
 // sign(0) = 0; |o_j - o_i| <= 1e-12 gives a zero gradient.
 // (image pair, run) items idx = run * P + n; a CTA's 128 items write their
-// 6-float gradients as one contiguous block (through shared memory)
+// gradients (two 16-byte slots, 3 floats each) as one contiguous block
+// (through shared memory)
 __global__ void __launch_bounds__(kPairThreads) k_trn_pairs(const float* __restrict__ o, const int* __restrict__ pi,
                                                             const int* __restrict__ pj,
                                                             const float* __restrict__ tgt, int N, int P, int runs,
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(kPairThreads) k_trn_pairs(const float* __restr
       float l = 0.f;
       for (int k = 0; k < 3; ++k) l += fabsf(tgt[3 * n + k]);
       seg_loss[idx] = l * inv_p;
-      for (int k = 0; k < 6; ++k) out[k] = 0.f;
+      for (int k = 0; k < 8; ++k) out[k] = 0.f;
     } else {
       const float inv = 1.f / nrm;
       float l = 0.f;
@@ -155,11 +157,12 @@ __global__ void __launch_bounds__(kPairThreads) k_trn_pairs(const float* __restr
       }
       seg_loss[idx] = l * inv_p;
       const float q = dot3(u, gu);
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < 3; ++k) {   // do_i in [0, 3), do_j in [4, 7), zeros between
         const float gd = (gu[k] - u[k] * q) * inv;
         out[k] = -gd;
-        out[3 + k] = gd;
+        out[4 + k] = gd;
       }
+      out[3] = out[7] = 0.f;
     }
   }
   __syncthreads();

@@ -181,36 +181,38 @@ __device__ __forceinline__ void segment_pair(const SegArgs& a, int n, int sub, c
 // dt; params 6D + t)
 template <int STAGE>
 struct Layout;
-template <> struct Layout<0> { static constexpr int PART = 9, PDIM = 6; static constexpr bool ROT = true; };
-template <> struct Layout<1> { static constexpr int PART = 3, PDIM = 3; static constexpr bool ROT = false; };
-template <> struct Layout<2> { static constexpr int PART = 12, PDIM = 9; static constexpr bool ROT = true; };
+// PART floats of a camera's part, stored in a slot of STRIDE floats (a
+// multiple of 4: 16-byte loads)
+template <> struct Layout<0> { static constexpr int PART = 9, STRIDE = 12, PDIM = 6; static constexpr bool ROT = true; };
+template <> struct Layout<1> { static constexpr int PART = 3, STRIDE = 4, PDIM = 3; static constexpr bool ROT = false; };
+template <> struct Layout<2> { static constexpr int PART = 12, STRIDE = 12, PDIM = 9; static constexpr bool ROT = true; };
 
-// adds the part at g (PART floats)
-template <int PART>
+// adds the part at g (PART floats of a slot of STRIDE floats, 16-byte
+// aligned in a cudaMalloc'd buffer)
+template <int PART, int STRIDE>
 __device__ __forceinline__ void cam_add_part(const float* g, float* acc) {
-  if (PART % 4 == 0) {   // 48-B parts of a cudaMalloc'd buffer: 16-B aligned
+  static_assert(STRIDE % 4 == 0 && PART <= STRIDE, "16-byte slots");
+  float v[STRIDE];
 #pragma unroll
-    for (int q = 0; q < PART / 4; ++q) {
-      const float4 t = *reinterpret_cast<const float4*>(g + 4 * q);
-      acc[4 * q] += t.x;
-      acc[4 * q + 1] += t.y;
-      acc[4 * q + 2] += t.z;
-      acc[4 * q + 3] += t.w;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < PART; ++k) acc[k] += g[k];
+  for (int q = 0; q < STRIDE / 4; ++q) {
+    const float4 t = *reinterpret_cast<const float4*>(g + 4 * q);
+    v[4 * q] = t.x;
+    v[4 * q + 1] = t.y;
+    v[4 * q + 2] = t.z;
+    v[4 * q + 3] = t.w;
   }
+#pragma unroll
+  for (int k = 0; k < PART; ++k) acc[k] += v[k];
 }
 
 // adds the part of camera-CSR entry `entry` (image pair | role << 31) of the
 // per-image-pair gradients sg
-template <int PART>
+template <int PART, int STRIDE>
 __device__ __forceinline__ void cam_add(const float* sg, int entry, float* acc) {
   const unsigned w = (unsigned)entry;
   const int n = (int)(w & 0x7fffffffu);
   const int role = (int)(w >> 31);
-  cam_add_part<PART>(sg + ((size_t)n * 2 + role) * PART, acc);
+  cam_add_part<PART, STRIDE>(sg + ((size_t)n * 2 + role) * STRIDE, acc);
 }
 
 // A camera's parts over its incident image pairs [b, e) of the camera CSR are
