@@ -17,7 +17,7 @@ namespace fm {
 #define FM_EA_PAIRS_PER_LANE 15
 #endif
 #ifndef FM_EA_WARPS_PER_CTA
-#define FM_EA_WARPS_PER_CTA 2
+#define FM_EA_WARPS_PER_CTA 4
 #endif
 constexpr int kEaPairsPerLane = FM_EA_PAIRS_PER_LANE;  // U: keypoint pairs per lane at most (odd)
 // the tiles U built into k_ea_direct (odd: stride-U float4 reads from shared
@@ -31,11 +31,12 @@ constexpr int kEaWarpsPerCta = FM_EA_WARPS_PER_CTA;
 #define FM_EA_STAGES 2
 #endif
 constexpr int kEaStages = FM_EA_STAGES;
-// register budget of k_ea_direct: at least this many CTAs per SM (shared
-// memory allows 7 at two warps per CTA, so 8 costs no occupancy and leaves
-// the compiler 128 registers to interleave a lane's pairs)
+// register budget of k_ea_direct: at least this many CTAs per SM, i.e. 128
+// registers a thread at four warps per CTA (room to interleave a lane's
+// pairs); at 11 pairs per lane 4 CTAs are resident, 16 warps per SM, as many
+// as 8 CTAs of two warps, in half as many CTAs to start
 #ifndef FM_EA_MIN_CTAS
-#define FM_EA_MIN_CTAS 8
+#define FM_EA_MIN_CTAS 4
 #endif
 constexpr int kEaMinCtas = FM_EA_MIN_CTAS;
 
