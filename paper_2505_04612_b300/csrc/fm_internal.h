@@ -47,6 +47,8 @@ static_assert(kEaPairsPerLane % 2 == 1, "lane-contiguous shared-memory reads nee
 constexpr int kSegGradEa = 24;                   // dR_i, dt_i, dR_j, dt_j
 constexpr int kSegGradRot = 24;                  // dR_i, dR_j: 9 floats each in a 48-byte slot
 constexpr int kSegGradTrn = 8;                   // do_i, do_j: 3 floats each in a 16-byte slot
+// the per-image-pair gradient buffer holds max(kSegGradEa P, kSegGradTrn P runs) floats
+static_assert(kSegGradRot <= kSegGradEa, "rotation parts must fit the epipolar stage's buffer");
 
 // error bits raised by device-side validation
 enum : int {
