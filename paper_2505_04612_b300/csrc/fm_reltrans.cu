@@ -12,8 +12,10 @@
 //
 // One CTA per image pair.  The a_m of a tile of keypoint pairs are formed in
 // shared memory; each thread scores its own candidates over the tile.  An ALU
-// kernel: 4 FP32 operations per (pair, candidate), no tensor-core shape
-// (inner dimension 3).  The hemisphere's 4096 points are the same for every
+// kernel: 4 FP32 operations per (pair, candidate), issued as packed f32x2
+// instructions for pairs of candidates (the multiply and the two fmas) and
+// two scalar adds of the absolute values; no tensor-core shape (inner
+// dimension 3).  The hemisphere's 4096 points are the same for every
 // image pair: k_lattice0 writes them once per problem (the same function and
 // arguments as the per-CTA evaluation, so the same values), and an image pair
 // whose keypoint pairs fit in one tile forms its a_m once for all three
@@ -26,6 +28,28 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kTile = 512;
+// each a_m entry twice, (a, a): one 64-bit shared-memory load gives the
+// operand that a packed f32x2 instruction applies to two candidates
+using TileT = float2;
+__device__ __forceinline__ TileT tile_val(float v) { return make_float2(v, v); }
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long r, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
 constexpr int kK0 = 4096, kK1 = 1024;
 constexpr unsigned kGolden32 = 0x61C88647u;   // round(2^32 (3 - sqrt 5)/2)
 
@@ -78,7 +102,7 @@ __device__ __forceinline__ Best better(Best a, Best b) {
 
 // a_m of keypoint pairs [base, base + n) into the tile
 __device__ __forceinline__ void fill_tile(const float4* __restrict__ kp, const float* __restrict__ w, int base,
-                                          int n, const float* Rij, float (*a_s)[kTile]) {
+                                          int n, const float* Rij, TileT (*a_s)[kTile]) {
   for (int m = threadIdx.x; m < n; m += kThreads) {
     const float4 x = kp[base + m];
     const float r0 = Rij[0] * x.x + Rij[1] * x.y + Rij[2];
@@ -86,9 +110,9 @@ __device__ __forceinline__ void fill_tile(const float4* __restrict__ kp, const f
     const float r2 = Rij[6] * x.x + Rij[7] * x.y + Rij[8];
     // (R x1) x x2 with x2 = (x.z, x.w, 1); a left-out pair adds |t . 0| = 0
     const float keep = (w == nullptr || w[base + m] > 0.f) ? 1.f : 0.f;
-    a_s[0][m] = keep * (r1 * 1.f - r2 * x.w);
-    a_s[1][m] = keep * (r2 * x.z - r0 * 1.f);
-    a_s[2][m] = keep * (r0 * x.w - r1 * x.z);
+    a_s[0][m] = tile_val(keep * (r1 * 1.f - r2 * x.w));
+    a_s[1][m] = tile_val(keep * (r2 * x.z - r0 * 1.f));
+    a_s[2][m] = tile_val(keep * (r0 * x.w - r1 * x.z));
   }
 }
 
@@ -97,7 +121,7 @@ __device__ __forceinline__ void fill_tile(const float4* __restrict__ kp, const f
 template <int PER>
 __device__ Best score_level(const float4* __restrict__ kp, const float* __restrict__ w, int b, int e,
                             const float* Rij, int K, float H, const float* Q, const float4* __restrict__ table,
-                            bool resident, float (*a_s)[kTile]) {
+                            bool resident, TileT (*a_s)[kTile]) {
   float t[PER][3];
   float acc[PER];
 #pragma unroll
@@ -112,6 +136,14 @@ __device__ Best score_level(const float4* __restrict__ kp, const float* __restri
     }
     acc[i] = 0.f;
   }
+  // |t . a| = |t0 a0 + (t1 a1 + t2 a2)| (a multiply and two fmas) for
+  // candidates 2i and 2i + 1 side by side, two per f32x2 instruction; the
+  // absolute values are added one by one
+  unsigned long long tp[PER / 2][3];
+#pragma unroll
+  for (int i = 0; i < PER / 2; ++i)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tp[i][c] = pk2(t[2 * i][c], t[2 * i + 1][c]);
   for (int base = b; base < e; base += kTile) {
     const int n = min(kTile, e - base);
     if (!resident) {
@@ -120,9 +152,17 @@ __device__ Best score_level(const float4* __restrict__ kp, const float* __restri
       __syncthreads();
     }
     for (int m = 0; m < n; ++m) {
-      const float a0 = a_s[0][m], a1 = a_s[1][m], a2 = a_s[2][m];
+      const unsigned long long a0 = *reinterpret_cast<const unsigned long long*>(&a_s[0][m]);
+      const unsigned long long a1 = *reinterpret_cast<const unsigned long long*>(&a_s[1][m]);
+      const unsigned long long a2 = *reinterpret_cast<const unsigned long long*>(&a_s[2][m]);
 #pragma unroll
-      for (int i = 0; i < PER; ++i) acc[i] += fabsf(fmaf(t[i][0], a0, fmaf(t[i][1], a1, t[i][2] * a2)));
+      for (int i = 0; i < PER / 2; ++i) {
+        const unsigned long long d = fma2(tp[i][0], a0, fma2(tp[i][1], a1, mul2(tp[i][2], a2)));
+        float lo, hi;
+        upk2(d, lo, hi);
+        acc[2 * i] += fabsf(lo);
+        acc[2 * i + 1] += fabsf(hi);
+      }
     }
   }
   Best best{3.4e38f, 0x7fffffff};
@@ -168,7 +208,7 @@ __global__ void __launch_bounds__(kThreads) k_reltrans(const float4* __restrict_
                                                       const float* __restrict__ rot6, const float* __restrict__ w_in,
                                                       const float4* __restrict__ lat0,
                                                       float* __restrict__ rel_t, float* __restrict__ err_out) {
-  __shared__ float a_s[3][kTile];
+  __shared__ TileT a_s[3][kTile];
   __shared__ Best red[kThreads / 32];
   __shared__ float Rij_s[9];
   __shared__ int cnt_s[2][kThreads / 32];
