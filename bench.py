@@ -1213,8 +1213,8 @@ def learned_vs_plain(seed, train_scenes, eval_cams, eval_points, eval_track, eva
     Evaluation: one scene with N = `eval_cams` cameras, `eval_points`
     points, track length 2 + Geometric (mean `eval_track`), an outlier
     fraction of `eval_outliers`, relative rotations with 1 deg noise.  The
-    plain fm_solve (5 filtering rounds) and the learned one (2 pruning
-    passes, 1 round) are timed end to end (wall clock around the call, the
+    plain fm_solve (5 filtering rounds) and the learned one (1 pruning
+    pass, 1 round) are timed end to end (wall clock around the call, the
     median of three after a warm-up solve); accuracy is the mean rotation
     error and the mean
     camera-centre error (relative to the scene's size, after a similarity

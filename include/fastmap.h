@@ -547,7 +547,7 @@ typedef struct {
                                  fm_mlp_set_params (0) */
   float learned_p_min;        /* inlier probability to keep a pair (0.5) */
   int32_t learned_prune_passes; /* prune + re-estimate passes before the
-                                 translation stage (2): each pass sees the
+                                 translation stage (1): each pass sees the
                                  relative translations of the previous one */
   int32_t rot_given;          /* 1: start from the rotation-stage parameters
                                  set on the problem (fm_set_params), with no

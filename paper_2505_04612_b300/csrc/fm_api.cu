@@ -2580,7 +2580,7 @@ void fm_solve_opts_default(fm_solve_opts* o) {
   o->eps = 1e-8f;
   o->learned = 0;
   o->learned_p_min = 0.5f;
-  o->learned_prune_passes = 2;
+  o->learned_prune_passes = 1;
 }
 
 // Adam steps in four equal phases with the learning rate scaled by
