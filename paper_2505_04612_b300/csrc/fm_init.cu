@@ -7,9 +7,10 @@
 // A_ii += I, A_jj += I, A_ji -= R_ij, A_ij -= R_ij^T (R_ij orthogonal).  The
 // first columns are the eigenvector of A's smallest eigenvalue (Eq. 12); the
 // second columns that of B = A/|P| + (1/|I|) blockdiag(c1_i c1_i^T) (Eq. 13).
-// Both are found by power iteration on I - A/sigma (sigma >= lambda_max by
-// Gershgorin: 2 max degree), whose spectrum lies in [0, 1] with the wanted
-// eigenvector at the top.  A problem holding several scenes is block
+// Both are found by power iteration on I - A/sigma with sigma = 1.05 d_max
+// (B: 1.05 (d_max/|P| + 1/|I|)): x^T A x <= 2 sum_i d_i |x_i|^2 bounds
+// lambda_max by 2 d_max, so the spectrum of I - A/sigma lies in [-0.905, 1]
+// with the wanted eigenvector at the top.  A problem holding several scenes is block
 // diagonal: every scene gets its own sigma, |P|, |I| and normalisation, so
 // each one converges as it would alone.  Any vector of
 // the (near-)null space is a valid answer (x_i = R_i v for some v), so only
